@@ -1,0 +1,175 @@
+/*
+ * hsc.h -- C ABI of the GB300 (sm_103a) spatial-spectral hyperspectral
+ * classifier hot path (libhsc.so).
+ *
+ * The method is the spatial-spectral classifier of Lazcano et al.,
+ * "Parallel Implementations Assessment of a Spatial-Spectral Classifier for
+ * Hyperspectral Clinical Applications" (arXiv 2404.10631), Section II.C and
+ * Fig. 2: a pixel-wise SVM (probability maps P) and a one-band PCA
+ * representation (I) are computed independently, then a KNN filter (Eq. 1,
+ * Eq. 2) averages each pixel's neighbours' probabilities into O and takes the
+ * argmax as the label.
+ *
+ * Conventions for every call below:
+ *   - Array arguments are DEVICE pointers to caller-owned memory (e.g. a torch
+ *     tensor's data_ptr()). The library never allocates, frees or retains
+ *     them beyond the call's stream work.
+ *   - Cube layout: B x H x W float32, band-sequential (each band is an H x W
+ *     image, row-major; the "each row is a band" matrix of Section III.A.2.a).
+ *     Linear pixel index p = r*W + c. Class maps are k x H x W float32.
+ *   - Calls are asynchronous on the context's stream. Argument errors are
+ *     detected on the host before any launch and returned synchronously;
+ *     device-side conditions (non-finite input, Jacobi not converged, an
+ *     internal bound hit) are recorded in a device status word that
+ *     hsc_sync() reads. Outputs are unspecified when a call or the following
+ *     hsc_sync() returns a status other than HSC_OK.
+ *   - Scratch memory belongs to the context: it is allocated on first use (or
+ *     by hsc_reserve) and grown as needed up to scratch_cap_bytes; a call that
+ *     needs more returns HSC_ERR_OOM. Growing the scratch synchronises the
+ *     device, so call hsc_reserve first when capturing CUDA graphs.
+ *   - A context may be used by one host thread at a time.
+ *   - hsc_last_error() returns a message for the last non-OK status.
+ */
+#ifndef HSC_H
+#define HSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HSC_OK = 0,
+    HSC_ERR_INVALID_ARG = 1,   /* bad sizes, null required pointer, K too large ... */
+    HSC_ERR_OOM = 2,           /* scratch would exceed the context's cap */
+    HSC_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in last_error) */
+    HSC_ERR_NOT_CONVERGED = 4, /* Jacobi / eigenvector refinement did not converge */
+    HSC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    HSC_ERR_UNSUPPORTED = 6,   /* valid request outside this build's limits */
+    HSC_ERR_NONFINITE = 7      /* NaN or Inf met in an input map */
+} hsc_status;
+
+typedef struct hsc_ctx hsc_ctx;
+
+/* One-vs-one linear SVM with Platt scaling (Section II.C.1; the training
+ * stage is offline and outside this library). M = k(k-1)/2 hyperplanes in
+ * lexicographic pair order (0,1),(0,2),...,(0,k-1),(1,2),...,(k-2,k-1).
+ * Decision value of pair m=(i,j) on pixel x: f = w_m . x + b_m (raw,
+ * un-centred spectrum). Binary probability r_ij = 1/(1+exp(A_m f + B_m)),
+ * clipped to [1e-7, 1-1e-7]; r_ji = 1 - r_ij. All arrays are device float32. */
+typedef struct {
+    int32_t n_classes;     /* k, 2 .. HSC_MAX_CLASSES */
+    int32_t n_bands;       /* B, must equal the cube's band count */
+    const float *w;        /* M x B row-major */
+    const float *b;        /* M */
+    const float *platt_a;  /* M (A) */
+    const float *platt_b;  /* M (B) */
+} hsc_svm_model;
+
+/* KNN filter parameters (Section II.C.3, Eq. 1; Section III.A.3).
+ *   k           number of neighbours K, 1 .. HSC_MAX_K
+ *   window_rows R >= 1: candidate rows r-floor(R/2) .. r+ceil(R/2)-1 of pixel
+ *               row r, truncated at the image edges, all columns (the paper
+ *               uses 14); the pixel itself is a candidate
+ *   lambda      >= 0: d = (I_p - I_q)^2 + lambda^2 ((r-i)^2 + (c-j)^2)
+ * Distance ties are broken by the smaller linear index; K must not exceed the
+ * smallest window, min(ceil(R/2), H) * W, or the call returns
+ * HSC_ERR_INVALID_ARG. */
+typedef struct {
+    int32_t k;
+    int32_t window_rows;
+    float lambda;
+} hsc_knn_params;
+
+#define HSC_MAX_CLASSES 8
+#define HSC_MAX_K 64
+#define HSC_MAX_WINDOW_ROWS 32
+#define HSC_MAX_BANDS 1024
+
+/* flags for hsc_pca_one_band */
+#define HSC_PCA_MINMAX 1u        /* write (I - min)/(max - min) in [0,1] (what the KNN uses) */
+/* flags for hsc_svm_probs / hsc_classify */
+#define HSC_SVM_COUPLE_F64 2u    /* solve the per-pixel coupling system in FP64 */
+
+/* Create a context on `device`. cuda_stream: a cudaStream_t to launch on, or
+ * NULL for a new stream owned by the context. scratch_cap_bytes: upper bound
+ * on the context's scratch (0 = no bound). */
+hsc_status hsc_ctx_create(int device, void *cuda_stream, size_t scratch_cap_bytes,
+                          hsc_ctx **out);
+/* Synchronise the stream and free the context's scratch and owned stream. */
+void hsc_ctx_destroy(hsc_ctx *ctx);
+/* Point the context at another stream (NULL = the context's own stream). */
+hsc_status hsc_set_stream(hsc_ctx *ctx, void *cuda_stream);
+/* Message for the last non-OK status of this context ("" if none). */
+const char *hsc_last_error(const hsc_ctx *ctx);
+/* Name of a status code. */
+const char *hsc_status_string(hsc_status st);
+/* Wait for the context's stream, then read and clear the device status word:
+ * returns the first device-side error of the work since the last hsc_sync. */
+hsc_status hsc_sync(hsc_ctx *ctx);
+/* Pre-allocate scratch for frames up to B x H x W with k classes. */
+hsc_status hsc_reserve(hsc_ctx *ctx, int B, int H, int W, int n_classes);
+/* Bytes of scratch the context currently holds. */
+size_t hsc_scratch_bytes(const hsc_ctx *ctx);
+
+/* One-band PCA, Section II.C.2 steps (i)-(iv): band means, covariance of the
+ * centred cube divided by the pixel count (Section III.A.2.b), Jacobi
+ * eigen-decomposition (Section II.C.2, III.A.2.c), projection of the centred
+ * pixels on the leading eigenvector. The eigenvector's sign is fixed so that
+ * its largest-magnitude component is positive.
+ *   cube     B x H x W float32 (device)
+ *   flags    HSC_PCA_MINMAX: one_band = (I - min I)/(max I - min I), or all
+ *            zeros when I is constant; otherwise the raw projection I.
+ *   one_band H x W float32 (device, required)
+ *   eigvec   B float64 (device, nullable): leading eigenvector v1
+ *   eigval   1 float64 (device, nullable): its eigenvalue lambda1 */
+hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W,
+                            unsigned flags, float *one_band, double *eigvec,
+                            double *eigval);
+
+/* Pixel-wise SVM probabilities, Section II.C.1 and III.A.1: decision values,
+ * Platt binary probabilities, and the pairwise coupling of Wu, Lin and Weng
+ * (the paper's reference [30], second method): p minimises
+ * sum_i sum_{j!=i} (r_ji p_i - r_ij p_j)^2 subject to sum p = 1 (the exact
+ * minimiser; the paper iterates towards it).
+ *   cube       B x H x W float32 (device); model->n_bands must equal B
+ *   probs      k x H x W float32 (device, required)
+ *   svm_labels H x W int32 (device, nullable): argmax_c probs (smaller c on ties)
+ *   flags      0 or HSC_SVM_COUPLE_F64 */
+hsc_status hsc_svm_probs(hsc_ctx *ctx, const float *cube, int B, int H, int W,
+                         const hsc_svm_model *model, unsigned flags, float *probs,
+                         int32_t *svm_labels);
+
+/* KNN filter, Section II.C.3 Eq. 1 and Eq. 2 with the row window of Section
+ * III.A.3: for each pixel the K window candidates with the smallest
+ * (distance, linear index) are found, their probabilities averaged into
+ * out_probs, and the argmax written to labels.
+ *   one_band  H x W float32 (device): the normalised one-band image
+ *   probs     n_classes x H x W float32 (device)
+ *   out_probs n_classes x H x W float32 (device, nullable): O
+ *   labels    H x W int32 (device, required): argmax_c O (smaller c on ties)
+ *   nbr_idx   H x W x K int32 (device, nullable): the selected neighbours'
+ *             linear indices, nearest first (debug output) */
+hsc_status hsc_knn_filter(hsc_ctx *ctx, const float *one_band, const float *probs,
+                          int n_classes, int H, int W, const hsc_knn_params *params,
+                          float *out_probs, int32_t *labels, int32_t *nbr_idx);
+
+/* The whole spatial-spectral classification of Fig. 2: PCA one-band (min-max
+ * normalised), SVM probabilities, KNN filter, labels.
+ *   labels    H x W int32 (device, required)
+ *   out_probs k x H x W float32 (device, nullable): O
+ *   one_band  H x W float32 (device, nullable): the normalised one-band image
+ *   probs     k x H x W float32 (device, nullable): the SVM maps P
+ *   flags     0 or HSC_SVM_COUPLE_F64 */
+hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
+                        const hsc_svm_model *model, const hsc_knn_params *params,
+                        unsigned flags, int32_t *labels, float *out_probs,
+                        float *one_band, float *probs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSC_H */

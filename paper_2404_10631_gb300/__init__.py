@@ -1,0 +1,229 @@
+"""Python binding of libhsc.so, the GB300 spatial-spectral HSI classifier.
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels. PyTorch provides device memory and streams. The functions keep
+the C names (``hsc_classify`` ...) and take CUDA tensors; ``Context`` owns an
+``hsc_ctx``. Importing this package does not load the library; the first call
+does, and it raises if ``libhsc.so`` has not been built (no CPU fallback).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhsc.so")
+
+HSC_OK = 0
+HSC_ERR_INVALID_ARG = 1
+HSC_ERR_OOM = 2
+HSC_ERR_CUDA = 3
+HSC_ERR_NOT_CONVERGED = 4
+HSC_ERR_TIMEOUT = 5
+HSC_ERR_UNSUPPORTED = 6
+HSC_ERR_NONFINITE = 7
+
+HSC_MAX_CLASSES = 8
+HSC_MAX_K = 64
+HSC_MAX_WINDOW_ROWS = 32
+HSC_MAX_BANDS = 1024
+HSC_PCA_MINMAX = 1
+HSC_SVM_COUPLE_F64 = 2
+
+EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_error",
+            "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
+            "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify")
+
+
+class hsc_svm_model(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int32), ("n_bands", ctypes.c_int32),
+                ("w", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("platt_a", ctypes.c_void_p), ("platt_b", ctypes.c_void_p)]
+
+
+class hsc_knn_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("window_rows", ctypes.c_int32),
+                ("lambda_", ctypes.c_float)]
+
+
+class HscError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (_status_name(status), message))
+        self.status = status
+
+
+_lib = None
+
+
+def _status_name(st: int) -> str:
+    names = {0: "HSC_OK", 1: "HSC_ERR_INVALID_ARG", 2: "HSC_ERR_OOM", 3: "HSC_ERR_CUDA",
+             4: "HSC_ERR_NOT_CONVERGED", 5: "HSC_ERR_TIMEOUT", 6: "HSC_ERR_UNSUPPORTED",
+             7: "HSC_ERR_NONFINITE"}
+    return names.get(st, "HSC_ERR_%d" % st)
+
+
+def lib():
+    """Load libhsc.so (raises when it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhsc.so is not built (run paper_2404_10631_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.hsc_ctx_create.argtypes = [i32, vp, sz, ctypes.POINTER(vp)]
+        L.hsc_ctx_destroy.argtypes = [vp]
+        L.hsc_ctx_destroy.restype = None
+        L.hsc_set_stream.argtypes = [vp, vp]
+        L.hsc_last_error.argtypes = [vp]
+        L.hsc_last_error.restype = ctypes.c_char_p
+        L.hsc_status_string.argtypes = [i32]
+        L.hsc_status_string.restype = ctypes.c_char_p
+        L.hsc_sync.argtypes = [vp]
+        L.hsc_reserve.argtypes = [vp, i32, i32, i32, i32]
+        L.hsc_scratch_bytes.argtypes = [vp]
+        L.hsc_scratch_bytes.restype = sz
+        L.hsc_pca_one_band.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
+        L.hsc_svm_probs.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
+                                    ctypes.c_uint, vp, vp]
+        L.hsc_knn_filter.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.POINTER(hsc_knn_params),
+                                     vp, vp, vp]
+        L.hsc_classify.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
+                                   ctypes.POINTER(hsc_knn_params), ctypes.c_uint, vp, vp, vp, vp]
+        for name in EXPORTED:
+            fn = getattr(L, name)
+            if name not in ("hsc_ctx_destroy", "hsc_last_error", "hsc_status_string",
+                            "hsc_scratch_bytes"):
+                fn.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+class Model:
+    """Device-resident OvO SVM model (float32 CUDA tensors)."""
+
+    def __init__(self, n_classes: int, w, b, platt_a, platt_b):
+        self.n_classes = int(n_classes)
+        self.w, self.b, self.platt_a, self.platt_b = w, b, platt_a, platt_b
+        self.n_bands = int(w.shape[1])
+
+    @classmethod
+    def from_host(cls, m, device="cuda"):
+        import torch
+        f = lambda a: torch.as_tensor(a, dtype=torch.float32).contiguous().to(device)
+        return cls(m.n_classes, f(m.w), f(m.b), f(m.platt_a), f(m.platt_b))
+
+    def struct(self) -> hsc_svm_model:
+        return hsc_svm_model(self.n_classes, self.n_bands, _ptr(self.w), _ptr(self.b),
+                             _ptr(self.platt_a), _ptr(self.platt_b))
+
+
+class Context:
+    """An ``hsc_ctx`` on one device and stream (None = a stream it owns)."""
+
+    def __init__(self, device: int = 0, stream=None, scratch_cap_bytes: int = 0):
+        L = lib()
+        h = ctypes.c_void_p()
+        sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        st = L.hsc_ctx_create(device, sp, scratch_cap_bytes, ctypes.byref(h))
+        if st != HSC_OK:
+            raise HscError(st, "hsc_ctx_create(device=%d)" % device)
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().hsc_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def check(self, st: int):
+        if st != HSC_OK:
+            raise HscError(st, lib().hsc_last_error(self.handle).decode())
+
+    def set_stream(self, stream=None):
+        sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self.check(lib().hsc_set_stream(self.handle, sp))
+
+    def sync(self):
+        self.check(lib().hsc_sync(self.handle))
+
+    def reserve(self, B, H, W, n_classes):
+        self.check(lib().hsc_reserve(self.handle, B, H, W, n_classes))
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(lib().hsc_scratch_bytes(self.handle))
+
+
+def hsc_pca_one_band(ctx: Context, cube, flags: int = HSC_PCA_MINMAX, one_band=None,
+                     eigvec=None, eigval=None):
+    """Returns the H x W one-band image (allocated when not given)."""
+    import torch
+    B, H, W = cube.shape
+    if one_band is None:
+        one_band = torch.empty((H, W), dtype=torch.float32, device=cube.device)
+    ctx.check(lib().hsc_pca_one_band(ctx.handle, _ptr(cube), B, H, W, flags, _ptr(one_band),
+                                     _ptr(eigvec), _ptr(eigval)))
+    return one_band
+
+
+def hsc_svm_probs(ctx: Context, cube, model: Model, flags: int = 0, probs=None,
+                  svm_labels=None):
+    import torch
+    B, H, W = cube.shape
+    if probs is None:
+        probs = torch.empty((model.n_classes, H, W), dtype=torch.float32, device=cube.device)
+    ms = model.struct()
+    ctx.check(lib().hsc_svm_probs(ctx.handle, _ptr(cube), B, H, W, ctypes.byref(ms), flags,
+                                  _ptr(probs), _ptr(svm_labels)))
+    return probs
+
+
+def hsc_knn_filter(ctx: Context, one_band, probs, K: int, window_rows: int, lam: float,
+                   out_probs=None, labels=None, nbr_idx=None):
+    import torch
+    k, H, W = probs.shape
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=probs.device)
+    prm = hsc_knn_params(K, window_rows, lam)
+    ctx.check(lib().hsc_knn_filter(ctx.handle, _ptr(one_band), _ptr(probs), k, H, W,
+                                   ctypes.byref(prm), _ptr(out_probs), _ptr(labels),
+                                   _ptr(nbr_idx)))
+    return labels
+
+
+def hsc_classify(ctx: Context, cube, model: Model, K: int, window_rows: int, lam: float,
+                 flags: int = 0, labels=None, out_probs=None, one_band=None, probs=None):
+    import torch
+    B, H, W = cube.shape
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=cube.device)
+    ms = model.struct()
+    prm = hsc_knn_params(K, window_rows, lam)
+    ctx.check(lib().hsc_classify(ctx.handle, _ptr(cube), B, H, W, ctypes.byref(ms),
+                                 ctypes.byref(prm), flags, _ptr(labels), _ptr(out_probs),
+                                 _ptr(one_band), _ptr(probs)))
+    return labels

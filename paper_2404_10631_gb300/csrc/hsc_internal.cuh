@@ -1,0 +1,91 @@
+// Internal declarations shared by the translation units of libhsc.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/hsc.h"
+
+namespace hsc {
+
+// Device status word bits (OR-ed by kernels, read and cleared by hsc_sync).
+enum : unsigned {
+    ST_NONFINITE_CUBE = 1u,   // NaN/Inf in the cube (moments / SVM pass)
+    ST_NOT_CONVERGED = 2u,    // eigenvector refinement did not converge
+    ST_KNN_SHORT = 4u,        // a pixel found fewer than K candidates (must not happen)
+    ST_NONFINITE_MAP = 8u,    // NaN/Inf in one_band given to the KNN
+};
+
+// Small control block at the start of the scratch.
+struct Control {
+    unsigned status;          // ST_* bits
+    unsigned imin_key;        // ordered-int key of min I (atomicMin)
+    unsigned imax_key;        // ordered-int key of max I (atomicMax)
+    unsigned pad[61];
+};
+
+// Float <-> order-preserving unsigned key (for atomic min/max of floats).
+__host__ __device__ inline unsigned float_to_key(float f) {
+    unsigned u;
+#ifdef __CUDA_ARCH__
+    u = __float_as_uint(f);
+#else
+    union { float f; unsigned u; } x; x.f = f; u = x.u;
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ inline float key_to_float(unsigned k) {
+    unsigned u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    union { float f; unsigned u; } x; x.u = u; return x.f;
+#endif
+}
+
+// Scratch carve-up for one frame (offsets in bytes, 256-aligned).
+struct PcaScratch {
+    Control *ctl;
+    float *shift;        // B: pilot shift per band
+    float *gram_part;    // n_part x B x B partial Gram of shifted pixels
+    float *sum_part;     // n_part x B partial sums of shifted pixels
+    double *C;           // B x B covariance
+    double *mu;          // B band means
+    double *v1;          // B leading eigenvector
+    double *lambda1;     // 1
+    float *v1f;          // B
+    float *muf;          // B
+    float *jac_A;        // Bp x Bp (only when it does not fit in shared memory)
+    float *jac_V;        // Bp x Bp
+    int n_part;
+};
+
+// ---- launchers (each returns cudaGetLastError() of its launches) ----
+
+// Pass 1 over the cube: pilot shift, partial Gram + sums, FP64 reduction into
+// C (covariance / N) and mu. Sets ST_NONFINITE_CUBE on NaN/Inf.
+cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s,
+                           int sm_count, cudaStream_t st);
+
+// Jacobi eigen-decomposition of C, FP64 refinement of the leading vector,
+// sign rule; writes v1, lambda1, v1f, muf and resets the I min/max keys.
+cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st);
+
+// Pass 2 over the cube: projection (if v1f != nullptr) + SVM decision values,
+// Platt, coupling (if probs != nullptr). I_raw min/max into ctl keys.
+cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
+                               const float *muf, float *I_raw, const hsc_svm_model *model,
+                               bool couple_f64, float *probs, int32_t *svm_labels,
+                               Control *ctl, int sm_count, cudaStream_t st);
+
+// I_norm = (I - min)/(max - min) (0 if max == min), min/max from ctl keys.
+cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,
+                             cudaStream_t st);
+
+// KNN filter (Eq. 1, Eq. 2) over all pixels.
+cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
+                       float lambda, float *O, int32_t *labels, int32_t *nbr,
+                       Control *ctl, cudaStream_t st);
+
+}  // namespace hsc

@@ -1,0 +1,329 @@
+// Step (iii) of the PCA (Section II.C.2, III.A.2.c): Jacobi eigen-decomposition
+// of the B x B covariance, leading eigenvector kept.
+//
+// GB300 design (one CTA, the matrix never leaves the SM):
+//  1. Parallel cyclic Jacobi in FP32: each round applies B/2 disjoint plane
+//     rotations at once (round-robin "circle" pairing, every pair (p,q) met
+//     once per sweep). Each rotation is the symmetric Schur rotation that
+//     zeroes a_pq (the same rotation the paper's classical Jacobi applies to
+//     its pivot); the update A <- J^T A J is done per 2x2 block of pairs so a
+//     round is one pass over A and V. A and V live in shared memory.
+//  2. FP64 refinement of the leading vector against the FP64 covariance:
+//     with (theta_j, V_j) the FP32 eigenpairs and v the current leading
+//     vector, r = C v - rho v (rho = v^T C v) and
+//        v <- v + sum_{j != lead} V_j (V_j^T r) / (rho - theta_j),
+//     i.e. the small-angle Jacobi rotations of the leading pair against every
+//     other pair, taken in FP64 where it matters (C v and the residual).
+//     Repeated until ||r|| <= 1e-13 ||C||, so v1 carries FP64 accuracy while
+//     the O(B^3) sweeps run on the FP32 pipe (GB300's FP64 rate is a small
+//     fraction of its FP32 rate).
+//  3. Sign rule: the largest-magnitude component of v1 is made positive.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hsc_internal.cuh"
+
+namespace hsc {
+namespace {
+
+constexpr int kJacThreads = 1024;
+constexpr int kMaxPairs = 512;           // Bp <= 1024
+constexpr int kMaxRefine = 12;
+constexpr size_t kJacSmemLimit = 190 * 1024;  // + ~33 KB static shared
+
+struct JacParams {
+    int B, n;            // n = B rounded up to even
+    int max_sweeps;
+    float rot_tol;       // rotate (p,q) when |a_pq| > rot_tol (A scaled to max diag 1)
+    int use_smem;
+};
+
+__device__ __forceinline__ void pair_of(int t, int k, int n, int &p, int &q)
+{
+    int a, b;
+    if (k == 0) {
+        a = t;
+        b = n - 1;
+    } else {
+        a = (t + k) % (n - 1);
+        b = (t - k + n - 1) % (n - 1);
+    }
+    p = a < b ? a : b;
+    q = a < b ? b : a;
+}
+
+// block index idx in [0, P(P+1)/2) -> (k, l), k <= l, row-major upper triangle
+__device__ __forceinline__ void tri_of(int idx, int P, int &k, int &l)
+{
+    float fP = (float)(2 * P + 1);
+    int kk = (int)((fP - sqrtf(fP * fP - 8.f * (float)idx)) * 0.5f);
+    if (kk < 0) kk = 0;
+    if (kk > P - 1) kk = P - 1;
+    while (kk > 0 && kk * P - kk * (kk - 1) / 2 > idx) --kk;
+    while (kk + 1 < P && (kk + 1) * P - (kk + 1) * kk / 2 <= idx) ++kk;
+    k = kk;
+    l = k + (idx - (k * P - k * (k - 1) / 2));
+}
+
+__device__ double block_sum(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+__device__ float block_maxf(float v, float *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+    return t;
+}
+
+__global__ void __launch_bounds__(kJacThreads, 1)
+jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restrict__ mu,
+              double *__restrict__ v1_out, double *__restrict__ lambda1_out,
+              float *__restrict__ v1f, float *__restrict__ muf, float *gA, float *gV,
+              Control *ctl)
+{
+    extern __shared__ float smem[];
+    const int B = prm.B, n = prm.n, P = n / 2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    float *A = prm.use_smem ? smem : gA;
+    float *V = prm.use_smem ? smem + (size_t)n * n : gV;
+
+    __shared__ float cs[kMaxPairs], sn[kMaxPairs];
+    __shared__ int pp[kMaxPairs], qq[kMaxPairs];
+    __shared__ double red[32];
+    __shared__ float fred[32];
+    __shared__ int any_rot;
+    __shared__ double s_scale;
+
+    // ---- load A = C / scale (scale = largest diagonal entry), V = I
+    float dmax = 0.f;
+    for (int i = tid; i < B; i += nthr) dmax = fmaxf(dmax, (float)fabs(C[(size_t)i * B + i]));
+    dmax = block_maxf(dmax, fred);
+    if (tid == 0) s_scale = dmax > 0.f ? (double)dmax : 1.0;
+    __syncthreads();
+    const double scale = s_scale;
+    const double inv_scale = 1.0 / scale;
+    for (int idx = tid; idx < n * n; idx += nthr) {
+        int i = idx / n, j = idx % n;
+        A[idx] = (i < B && j < B) ? (float)(C[(size_t)i * B + j] * inv_scale) : 0.f;
+        V[idx] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+
+    // ---- 1. FP32 parallel cyclic sweeps
+    for (int sweep = 0; sweep < prm.max_sweeps; ++sweep) {
+        if (tid == 0) any_rot = 0;
+        __syncthreads();
+        for (int t = 0; t < n - 1; ++t) {
+            for (int k = tid; k < P; k += nthr) {
+                int p, q;
+                pair_of(t, k, n, p, q);
+                float app = A[p * n + p], aqq = A[q * n + q], apq = A[p * n + q];
+                float c = 1.f, s = 0.f;
+                if (fabsf(apq) > prm.rot_tol) {
+                    float tau = (aqq - app) / (2.f * apq);
+                    float tt;
+                    if (fabsf(tau) > 1e18f) tt = 0.5f / tau;
+                    else tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+                    c = 1.f / sqrtf(1.f + tt * tt);
+                    s = tt * c;
+                    any_rot = 1;
+                }
+                pp[k] = p;
+                qq[k] = q;
+                cs[k] = c;
+                sn[k] = s;
+            }
+            __syncthreads();
+            // A <- J^T A J, one 2x2 block (k, l), k <= l, per work item
+            const int nblk = P * (P + 1) / 2;
+            for (int idx = tid; idx < nblk; idx += nthr) {
+                int k, l;
+                tri_of(idx, P, k, l);
+                float ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
+                if (sk == 0.f && sl == 0.f) continue;
+                int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+                float x00 = A[pk * n + pl], x01 = A[pk * n + ql];
+                float x10 = A[qk * n + pl], x11 = A[qk * n + ql];
+                float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
+                float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
+                float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
+                float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
+                if (k == l) {
+                    A[pk * n + pk] = z00;
+                    A[qk * n + qk] = z11;
+                    A[pk * n + qk] = 0.f;
+                    A[qk * n + pk] = 0.f;
+                } else {
+                    A[pk * n + pl] = z00;
+                    A[pk * n + ql] = z01;
+                    A[qk * n + pl] = z10;
+                    A[qk * n + ql] = z11;
+                    A[pl * n + pk] = z00;
+                    A[ql * n + pk] = z01;
+                    A[pl * n + qk] = z10;
+                    A[ql * n + qk] = z11;
+                }
+            }
+            // V <- V J
+            for (int idx = tid; idx < n * P; idx += nthr) {
+                int i = idx / P, k = idx % P;
+                float s = sn[k];
+                if (s == 0.f) continue;
+                float c = cs[k];
+                int p = pp[k], q = qq[k];
+                float vp = V[i * n + p], vq = V[i * n + q];
+                V[i * n + p] = c * vp - s * vq;
+                V[i * n + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+        int rotated = any_rot;
+        __syncthreads();  // everyone has read the flag before thread 0 resets it
+        if (!rotated) break;
+    }
+
+    // ---- 2. FP64 refinement of the leading vector
+    __shared__ double sv[HSC_MAX_BANDS], sw[HSC_MAX_BANDS], stt[HSC_MAX_BANDS];
+    __shared__ float sr[HSC_MAX_BANDS];
+    __shared__ int s_lead;
+    __shared__ double s_rho, s_rn;
+    if (tid == 0) {
+        int lead = 0;
+        for (int j = 1; j < B; ++j)
+            if (A[j * n + j] > A[lead * n + lead]) lead = j;
+        s_lead = lead;
+    }
+    __syncthreads();
+    const int lead = s_lead;
+    for (int i = tid; i < B; i += nthr) sv[i] = (double)V[i * n + lead];
+    __syncthreads();
+    {
+        double nn = 0.0;
+        for (int i = tid; i < B; i += nthr) nn += sv[i] * sv[i];
+        nn = block_sum(nn, red);
+        double inv = 1.0 / sqrt(nn);
+        __syncthreads();
+        for (int i = tid; i < B; i += nthr) sv[i] *= inv;
+        __syncthreads();
+    }
+    const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
+    bool converged = false;
+    for (int it = 0; it <= kMaxRefine; ++it) {
+        // w = C v
+        for (int i = warp; i < B; i += nwarp) {
+            double a = 0.0;
+            for (int j = lane; j < B; j += 32) a += C[(size_t)i * B + j] * sv[j];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) sw[i] = a;
+        }
+        __syncthreads();
+        double rho = 0.0;
+        for (int i = tid; i < B; i += nthr) rho += sv[i] * sw[i];
+        rho = block_sum(rho, red);
+        double rn = 0.0;
+        for (int i = tid; i < B; i += nthr) {
+            double ri = sw[i] - rho * sv[i];
+            sw[i] = ri;  // w now holds the residual r
+            rn += ri * ri;
+        }
+        rn = sqrt(block_sum(rn, red));
+        if (tid == 0) {
+            s_rho = rho;
+            s_rn = rn;
+        }
+        double cnorm = fabs(rho) > scale ? fabs(rho) : scale;
+        if (rn <= 1e-13 * cnorm || rn == 0.0) {
+            converged = true;
+            break;
+        }
+        if (it == kMaxRefine) break;
+        // unit residual direction in FP32 (the correction's direction only)
+        const double inv_rn = 1.0 / rn;
+        for (int i = tid; i < B; i += nthr) sr[i] = (float)(sw[i] * inv_rn);
+        __syncthreads();
+        // t_j = (V_j^T r) / (rho - theta_j)
+        for (int j = tid; j < B; j += nthr) {
+            float g = 0.f;
+            for (int i = 0; i < B; ++i) g = fmaf(V[i * n + j], sr[i], g);
+            double th = (double)A[j * n + j] * scale;
+            double den = rho - th;
+            stt[j] = (j == lead || fabs(den) <= 1e-12 * cnorm) ? 0.0 : rn * (double)g / den;
+        }
+        __syncthreads();
+        // v += sum_j t_j V_j
+        for (int i = warp; i < B; i += nwarp) {
+            double a = 0.0;
+            for (int j = lane; j < B; j += 32) a += stt[j] * (double)V[i * n + j];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) sv[i] += a;
+        }
+        __syncthreads();
+        double nn = 0.0;
+        for (int i = tid; i < B; i += nthr) nn += sv[i] * sv[i];
+        nn = block_sum(nn, red);
+        double inv = 1.0 / sqrt(nn);
+        for (int i = tid; i < B; i += nthr) sv[i] *= inv;
+        __syncthreads();
+    }
+    __syncthreads();
+    // ---- 3. sign rule and outputs
+    if (tid == 0) {
+        int big = 0;
+        for (int i = 1; i < B; ++i)
+            if (fabs(sv[i]) > fabs(sv[big])) big = i;
+        s_lead = (sv[big] < 0.0) ? -1 : 1;
+        *lambda1_out = s_rho;
+        if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
+        ctl->imin_key = float_to_key(INFINITY);
+        ctl->imax_key = float_to_key(-INFINITY);
+    }
+    __syncthreads();
+    const double sgn = (double)s_lead;
+    for (int i = tid; i < B; i += nthr) {
+        double v = sgn * sv[i];
+        v1_out[i] = v;
+        v1f[i] = (float)v;
+        muf[i] = (float)mu[i];
+    }
+}
+
+}  // namespace
+
+size_t jacobi_global_floats(int B)
+{
+    int n = B + (B & 1);
+    size_t need = 2 * (size_t)n * n * sizeof(float);
+    return need <= kJacSmemLimit ? 0 : (size_t)n * n;
+}
+
+cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
+{
+    JacParams prm;
+    prm.B = B;
+    prm.n = B + (B & 1);
+    if (prm.n < 2) prm.n = 2;
+    prm.max_sweeps = 16;
+    prm.rot_tol = 1e-5f;
+    size_t need = 2 * (size_t)prm.n * prm.n * sizeof(float);
+    prm.use_smem = need <= kJacSmemLimit;
+    size_t smem = prm.use_smem ? need : 0;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    jacobi_kernel<<<1, kJacThreads, smem, st>>>(prm, s.C, s.mu, s.v1, s.lambda1, s.v1f, s.muf,
+                                                s.jac_A, s.jac_V, s.ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace hsc

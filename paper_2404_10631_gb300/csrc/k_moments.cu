@@ -1,0 +1,185 @@
+// Pass 1 over the cube: band means and covariance (Section II.C.2 steps (i)
+// and (ii); covariance divided by the pixel count, Section III.A.2.b).
+//
+// One HBM read of the cube. Pixels are shifted by a pilot mean s_b (a
+// strided sample of the band) so that the one-pass Gram loses no digits:
+//   y_p = x_p - s,  G = sum_p y_p y_p^T,  delta = (1/N) sum_p y_p,
+//   mu = s + delta,  C = G/N - delta delta^T   (exact algebra).
+// Each CTA accumulates G over a contiguous pixel range in FP32 and writes a
+// partial; the partials are summed in FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hsc_internal.cuh"
+
+namespace hsc {
+namespace {
+
+constexpr int kGramThreads = 256;
+constexpr int kGramChunk = 32;   // pixels staged per step
+constexpr int kTile = 8;         // 8x8 accumulator tile per thread
+
+__global__ void pilot_shift_kernel(const float *__restrict__ cube, int B, long N,
+                                   float *__restrict__ shift, Control *ctl)
+{
+    const int b = blockIdx.x;
+    const long S = N < 4096 ? N : 4096;
+    double acc = 0.0;
+    bool bad = false;
+    for (long s = threadIdx.x; s < S; s += blockDim.x) {
+        long p = (s * N) / S;
+        float x = cube[(size_t)b * (size_t)N + p];
+        bad |= !isfinite(x);
+        acc += (double)x;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        shift[b] = (float)(t / (double)S);
+    }
+}
+
+// grid.x = pixel partitions, grid.y = groups of 256 output tiles (B > 128).
+// Shared: Yt[kGramChunk][Bp + 4] (pixel-major, shifted values).
+__global__ void __launch_bounds__(kGramThreads)
+gram_partial_kernel(const float *__restrict__ cube, int B, int Bp, long N,
+                    const float *__restrict__ shift, float *__restrict__ gram_part,
+                    float *__restrict__ sum_part, Control *ctl)
+{
+    extern __shared__ float smem[];
+    const int ld = Bp + 4;
+    float *Yt = smem;                                 // kGramChunk x ld
+    float *sh = smem + kGramChunk * ld;               // Bp
+    const int tid = threadIdx.x;
+    const int nt = Bp / kTile;                        // tiles per side
+    const int tile = blockIdx.y * kGramThreads + tid;
+    const bool has_tile = tile < nt * nt;
+    const int ti = has_tile ? tile / nt : 0, tj = has_tile ? tile % nt : 0;
+    const bool do_sums = (blockIdx.y == 0);
+
+    for (int b = tid; b < Bp; b += kGramThreads) sh[b] = (b < B) ? shift[b] : 0.f;
+
+    long per = (N + gridDim.x - 1) / gridDim.x;
+    long p0 = (long)blockIdx.x * per, p1 = p0 + per;
+    if (p1 > N) p1 = N;
+
+    float acc[kTile][kTile];
+#pragma unroll
+    for (int a = 0; a < kTile; ++a)
+#pragma unroll
+        for (int c = 0; c < kTile; ++c) acc[a][c] = 0.f;
+    float bsum = 0.f;  // thread tid < Bp: running sum of band tid
+    bool bad = false;
+
+    for (long pc = p0; pc < p1; pc += kGramChunk) {
+        __syncthreads();
+        for (int idx = tid; idx < Bp * kGramChunk; idx += kGramThreads) {
+            int b = idx / kGramChunk, pp = idx % kGramChunk;
+            long p = pc + pp;
+            float y = 0.f;
+            if (b < B && p < p1) {
+                float x = cube[(size_t)b * (size_t)N + p];
+                bad |= !isfinite(x);
+                y = x - sh[b];
+            }
+            Yt[pp * ld + b] = y;
+        }
+        __syncthreads();
+        if (do_sums && tid < Bp) {
+            float s = 0.f;
+            for (int pp = 0; pp < kGramChunk; ++pp) s += Yt[pp * ld + tid];
+            bsum += s;
+        }
+        if (has_tile) {
+#pragma unroll 4
+            for (int pp = 0; pp < kGramChunk; ++pp) {
+                const float4 *ra = reinterpret_cast<const float4 *>(Yt + pp * ld + ti * kTile);
+                const float4 *rb = reinterpret_cast<const float4 *>(Yt + pp * ld + tj * kTile);
+                float4 a0 = ra[0], a1 = ra[1], b0 = rb[0], b1 = rb[1];
+                float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int a = 0; a < kTile; ++a)
+#pragma unroll
+                    for (int c = 0; c < kTile; ++c) acc[a][c] = fmaf(av[a], bv[c], acc[a][c]);
+            }
+        }
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+
+    float *out = gram_part + (size_t)blockIdx.x * (size_t)B * (size_t)B;
+    if (has_tile) {
+#pragma unroll
+        for (int a = 0; a < kTile; ++a) {
+            int b = ti * kTile + a;
+            if (b >= B) continue;
+#pragma unroll
+            for (int c = 0; c < kTile; ++c) {
+                int cc = tj * kTile + c;
+                if (cc < B) out[(size_t)b * B + cc] = acc[a][c];
+            }
+        }
+    }
+    if (do_sums && tid < B) sum_part[(size_t)blockIdx.x * B + tid] = bsum;
+}
+
+// delta_b = (1/N) sum of partial sums; mu_b = shift_b + delta_b.
+__global__ void band_mean_kernel(int B, long N, int n_part, const float *__restrict__ shift,
+                                 const float *__restrict__ sum_part, double *__restrict__ delta,
+                                 double *__restrict__ mu)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double s = 0.0;
+    for (int i = 0; i < n_part; ++i) s += (double)sum_part[(size_t)i * B + b];
+    double d = s / (double)N;
+    delta[b] = d;
+    mu[b] = (double)shift[b] + d;
+}
+
+// C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored.
+__global__ void gram_reduce_kernel(int B, long N, int n_part, const float *__restrict__ gram_part,
+                                   const double *__restrict__ delta, double *__restrict__ C)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = blockIdx.y;
+    if (c >= B || c < b) return;
+    double g = 0.0;
+    for (int i = 0; i < n_part; ++i) g += (double)gram_part[((size_t)i * B + b) * B + c];
+    double v = g / (double)N - delta[b] * delta[c];
+    C[(size_t)b * B + c] = v;
+    C[(size_t)c * B + b] = v;
+}
+
+}  // namespace
+
+int moments_partitions(int sm_count) { return 2 * sm_count; }
+
+cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s, int sm_count,
+                           cudaStream_t st)
+{
+    (void)sm_count;
+    pilot_shift_kernel<<<B, 256, 0, st>>>(cube, B, N, s.shift, s.ctl);
+    const int Bp = (B + kTile - 1) / kTile * kTile;
+    const int nt = Bp / kTile;
+    const int groups = (nt * nt + kGramThreads - 1) / kGramThreads;
+    size_t smem = sizeof(float) * ((size_t)kGramChunk * (Bp + 4) + Bp);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    dim3 grid(s.n_part, groups);
+    gram_partial_kernel<<<grid, kGramThreads, smem, st>>>(cube, B, Bp, N, s.shift, s.gram_part,
+                                                          s.sum_part, s.ctl);
+    band_mean_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, N, s.n_part, s.shift, s.sum_part,
+                                                      s.v1 /* delta lives in v1 until Jacobi */,
+                                                      s.mu);
+    dim3 rg((B + 127) / 128, B);
+    gram_reduce_kernel<<<rg, 128, 0, st>>>(B, N, s.n_part, s.gram_part, s.v1, s.C);
+    return cudaGetLastError();
+}
+
+}  // namespace hsc

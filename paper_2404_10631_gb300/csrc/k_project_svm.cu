@@ -1,0 +1,294 @@
+// Pass 2 over the cube: PCA step (iv) projection (Section II.C.2) fused with
+// the pixel-wise SVM of Section II.C.1 / III.A.1.
+//
+// Per pixel x (B bands, read once from HBM, 4 consecutive pixels of one band
+// per 16-byte load, bands in sequence):
+//   I   = sum_b v1_b (x_b - mu_b)                         (projection)
+//   f_m = w_m . x + b_m,  m < M = k(k-1)/2                (decision values)
+//   r_ij = clip(1/(1+exp(A_m f_m + B_m)), 1e-7, 1-1e-7),  r_ji = 1 - r_ij
+//   p   = minimiser of sum_i sum_{j!=i} (r_ji p_i - r_ij p_j)^2, sum p = 1
+//         (coupling of the paper's reference [30], second method)
+// The minimiser solves Q p = b e, e^T p = 1 with Q_ii = sum_{j!=i} r_ji^2,
+// Q_ij = -r_ji r_ij. Q is only positive semi-definite, but Q + e e^T is
+// positive definite and (Q + e e^T) y = e gives p = y / sum(y), so an LDL^T
+// factorisation without pivoting solves it (FP32 by default; its condition
+// number is below ~25 for r in [1e-7, 1-1e-7], FP64 on request).
+// The block min/max of I feeds the min-max normalisation.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "hsc_internal.cuh"
+
+namespace hsc {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int KC, typename CT>
+__device__ __forceinline__ void couple_solve(const float *r /* M, pair order */, float *p)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    CT R[KC][KC];
+    {
+        int m = 0;
+#pragma unroll
+        for (int i = 0; i < KC; ++i)
+#pragma unroll
+            for (int j = i + 1; j < KC; ++j, ++m) {
+                CT rij = (CT)r[m];
+                R[i][j] = rij;
+                R[j][i] = (CT)1 - rij;
+            }
+    }
+    (void)M;
+    // A = Q + e e^T (symmetric), stored lower part in L with D separate
+    CT L[KC][KC], D[KC], invD[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {
+        CT d = (CT)1;
+#pragma unroll
+        for (int j = 0; j < KC; ++j)
+            if (j != i) d += R[j][i] * R[j][i];
+        L[i][i] = d;
+#pragma unroll
+        for (int j = 0; j < i; ++j) L[i][j] = (CT)1 - R[j][i] * R[i][j];
+    }
+    // LDL^T in place
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+        CT d = L[j][j];
+#pragma unroll
+        for (int m = 0; m < j; ++m) d -= L[j][m] * L[j][m] * D[m];
+        D[j] = d;
+        invD[j] = (CT)1 / d;
+#pragma unroll
+        for (int i = j + 1; i < KC; ++i) {
+            CT t = L[i][j];
+#pragma unroll
+            for (int m = 0; m < j; ++m) t -= L[i][m] * L[j][m] * D[m];
+            L[i][j] = t * invD[j];
+        }
+    }
+    CT y[KC];
+#pragma unroll
+    for (int i = 0; i < KC; ++i) {  // L z = e
+        CT t = (CT)1;
+#pragma unroll
+        for (int m = 0; m < i; ++m) t -= L[i][m] * y[m];
+        y[i] = t;
+    }
+#pragma unroll
+    for (int i = 0; i < KC; ++i) y[i] *= invD[i];
+#pragma unroll
+    for (int i = KC - 1; i >= 0; --i) {  // L^T x = D^-1 z
+        CT t = y[i];
+#pragma unroll
+        for (int m = i + 1; m < KC; ++m) t -= L[m][i] * y[m];
+        y[i] = t;
+    }
+    CT s = (CT)0;
+#pragma unroll
+    for (int i = 0; i < KC; ++i) s += y[i];
+    CT inv = (CT)1 / s;
+#pragma unroll
+    for (int i = 0; i < KC; ++i) p[i] = (float)(y[i] * inv);
+}
+
+// KC = 0: projection only. PX = pixels per thread (4 with 16-byte loads).
+template <int KC, int PX>
+__global__ void __launch_bounds__(kThreads)
+project_svm_kernel(const float *__restrict__ cube, int B, long N,
+                   const float *__restrict__ v1f, const float *__restrict__ muf,
+                   const float *__restrict__ w, const float *__restrict__ bias,
+                   const float *__restrict__ pa, const float *__restrict__ pb,
+                   float *__restrict__ I_raw, float *__restrict__ probs,
+                   int32_t *__restrict__ labels, int couple_f64, Control *ctl)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    constexpr int MA = M > 0 ? M : 1;
+    constexpr int S = M + 2;  // per band: w_0..w_{M-1}, v1, mu
+    extern __shared__ float ws[];
+    __shared__ float sbias[MA], sa[MA], sb[MA];
+    const bool do_pca = (v1f != nullptr);
+
+    for (int idx = threadIdx.x; idx < B * S; idx += blockDim.x) {
+        int b = idx / S, m = idx % S;
+        float v;
+        if (m < M) v = w[(size_t)m * B + b];
+        else if (m == M) v = do_pca ? v1f[b] : 0.f;
+        else v = do_pca ? muf[b] : 0.f;
+        ws[idx] = v;
+    }
+    if constexpr (M > 0)
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            sbias[m] = bias[m];
+            sa[m] = pa[m];
+            sb[m] = pb[m];
+        }
+    __syncthreads();
+
+    float lmin = INFINITY, lmax = -INFINITY;
+    bool bad = false;
+    const long ngroups = (N + PX - 1) / PX;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+         g += (long)gridDim.x * blockDim.x) {
+        const long p0 = g * PX;
+        float acc[MA][PX];
+        float accI[PX];
+#pragma unroll
+        for (int u = 0; u < PX; ++u) {
+            accI[u] = 0.f;
+#pragma unroll
+            for (int m = 0; m < MA; ++m) acc[m][u] = 0.f;
+        }
+#pragma unroll 4
+        for (int b = 0; b < B; ++b) {
+            float x[PX];
+            const float *src = cube + (size_t)b * (size_t)N + p0;
+            if constexpr (PX == 4) {
+                float4 v = __ldcs(reinterpret_cast<const float4 *>(src));
+                x[0] = v.x;
+                x[1] = v.y;
+                x[2] = v.z;
+                x[3] = v.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < PX; ++u) x[u] = (p0 + u < N) ? __ldcs(src + u) : 0.f;
+            }
+            const float *wr = ws + b * S;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                float wm = wr[m];
+#pragma unroll
+                for (int u = 0; u < PX; ++u) acc[m][u] = fmaf(wm, x[u], acc[m][u]);
+            }
+            const float vb = wr[M], mb = wr[M + 1];
+#pragma unroll
+            for (int u = 0; u < PX; ++u) accI[u] = fmaf(vb, x[u] - mb, accI[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < PX; ++u) {
+            const long p = p0 + u;
+            if (p >= N) break;
+            if (do_pca) {
+                float I = accI[u];
+                bad |= !isfinite(I);
+                I_raw[p] = I;
+                lmin = fminf(lmin, I);
+                lmax = fmaxf(lmax, I);
+            }
+            if constexpr (M > 0) {
+                float r[MA];
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    float f = acc[m][u] + sbias[m];
+                    bad |= !isfinite(f);
+                    float rr = 1.f / (1.f + expf(fmaf(sa[m], f, sb[m])));
+                    r[m] = fminf(fmaxf(rr, 1e-7f), 1.f - 1e-7f);
+                }
+                float pr[KC > 0 ? KC : 1];
+                if (couple_f64) couple_solve<KC, double>(r, pr);
+                else couple_solve<KC, float>(r, pr);
+                int best = 0;
+                float bv = pr[0];
+#pragma unroll
+                for (int c = 0; c < KC; ++c) {
+                    probs[(size_t)c * (size_t)N + p] = pr[c];
+                    if (pr[c] > bv) {
+                        bv = pr[c];
+                        best = c;
+                    }
+                }
+                if (labels) labels[p] = best;
+            }
+        }
+    }
+    // block min/max of I -> ordered-int atomics
+    if (do_pca) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+            lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        }
+        if ((threadIdx.x & 31) == 0 && lmin <= lmax) {
+            atomicMin(&ctl->imin_key, float_to_key(lmin));
+            atomicMax(&ctl->imax_key, float_to_key(lmax));
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+}
+
+__global__ void normalize_kernel(const float *__restrict__ I_raw, float *__restrict__ I_norm,
+                                 long N, const Control *__restrict__ ctl)
+{
+    const float mn = key_to_float(ctl->imin_key), mx = key_to_float(ctl->imax_key);
+    const float range = mx - mn;
+    for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (long)gridDim.x * blockDim.x)
+        I_norm[p] = (range > 0.f) ? (I_raw[p] - mn) / range : 0.f;
+}
+
+template <int KC, int PX>
+cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const float *muf,
+                      float *I_raw, const hsc_svm_model *m, bool f64, float *probs,
+                      int32_t *labels, Control *ctl, int sm_count, cudaStream_t st)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    size_t smem = sizeof(float) * (size_t)B * (M + 2);
+    auto kern = project_svm_kernel<KC, PX>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    long groups = (N + PX - 1) / PX;
+    long blocks = (groups + kThreads - 1) / kThreads;
+    long cap = (long)sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, kThreads, smem, st>>>(
+        cube, B, N, v1f, muf, m ? m->w : nullptr, m ? m->b : nullptr, m ? m->platt_a : nullptr,
+        m ? m->platt_b : nullptr, I_raw, probs, labels, f64 ? 1 : 0, ctl);
+    return cudaGetLastError();
+}
+
+template <int PX>
+cudaError_t dispatch_k(int k, const float *cube, int B, long N, const float *v1f,
+                       const float *muf, float *I_raw, const hsc_svm_model *m, bool f64,
+                       float *probs, int32_t *labels, Control *ctl, int sm, cudaStream_t st)
+{
+    switch (k) {
+    case 0: return launch_kc<0, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 2: return launch_kc<2, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 3: return launch_kc<3, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 4: return launch_kc<4, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 5: return launch_kc<5, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 6: return launch_kc<6, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 7: return launch_kc<7, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 8: return launch_kc<8, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
+                               const float *muf, float *I_raw, const hsc_svm_model *model,
+                               bool couple_f64, float *probs, int32_t *svm_labels, Control *ctl,
+                               int sm_count, cudaStream_t st)
+{
+    const int k = (probs != nullptr && model != nullptr) ? model->n_classes : 0;
+    const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0);
+    if (vec)
+        return dispatch_k<4>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs, svm_labels,
+                             ctl, sm_count, st);
+    return dispatch_k<1>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs, svm_labels, ctl,
+                         sm_count, st);
+}
+
+cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,
+                             cudaStream_t st)
+{
+    long blocks = (N + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    normalize_kernel<<<(unsigned)blocks, 256, 0, st>>>(I_raw, I_norm, N, ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace hsc

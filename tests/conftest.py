@@ -17,3 +17,28 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="session")
+def hsc(torch_cuda):
+    """The CUDA binding with libhsc.so built in-tree (fails when it cannot be)."""
+    import paper_2404_10631_gb300 as pkg
+    from paper_2404_10631_gb300 import build
+    build.build()
+    pkg.lib()
+    return pkg
+
+
+@pytest.fixture(scope="session")
+def ctx(hsc):
+    c = hsc.Context(0)
+    yield c
+    c.close()

@@ -1,0 +1,126 @@
+"""KNN filter (Eq. 1, Eq. 2) on the GPU through the C ABI against the FP64
+oracle, on the same float inputs: neighbour sets exact outside strong
+near-ties, O within 1e-5, labels exact."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import check_knn, sample_rows
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def run_knn(hsc, ctx, I, P, K, R, lam):
+    import torch
+    dev = torch.device("cuda")
+    It = torch.as_tensor(np.ascontiguousarray(I, dtype=np.float32), device=dev)
+    Pt = torch.as_tensor(np.ascontiguousarray(P, dtype=np.float32), device=dev)
+    k, H, W = Pt.shape
+    O = torch.full((k, H, W), -1.0, dtype=torch.float32, device=dev)
+    lab = torch.full((H, W), -1, dtype=torch.int32, device=dev)
+    nbr = torch.full((H, W, K), -1, dtype=torch.int32, device=dev)
+    hsc.hsc_knn_filter(ctx, It, Pt, K, R, lam, out_probs=O, labels=lab, nbr_idx=nbr)
+    ctx.sync()
+    return nbr.cpu().numpy(), O.cpu().numpy(), lab.cpu().numpy()
+
+
+def rand_maps(H, W, k, seed, dyadic=False):
+    rng = np.random.default_rng(seed)
+    if dyadic:
+        I = (rng.integers(0, 64, size=(H, W)) / 64.0).astype(np.float32)
+    else:
+        I = rng.random((H, W)).astype(np.float32)
+    P = rng.random((k, H, W))
+    P = (P / P.sum(axis=0)).astype(np.float32)
+    return I, P
+
+
+@pytest.mark.parametrize("name", ["knn_line5.json", "knn_window_ties.json"])
+def test_golden_hand_examples(hsc, ctx, name):
+    g = json.load(open(os.path.join(GOLDEN, name)))
+    I = np.asarray(g["I"], dtype=np.float32)
+    P = np.asarray(g["P"], dtype=np.float32)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, g["K"], g["R"], g["lambda"])
+    np.testing.assert_array_equal(nbr.reshape(-1, g["K"]), g["nbr"])
+    np.testing.assert_allclose(O, g["O"], atol=1e-7)
+    np.testing.assert_array_equal(lab, g["labels"])
+
+
+@pytest.mark.parametrize("H,W,K,R,lam,k", [
+    (32, 32, 8, 5, 1.0, 4),      # the tiny configuration's sizes
+    (37, 45, 40, 14, 1.0, 4),    # paper's K and window, ragged width
+    (20, 130, 64, 32, 1.0, 3),   # maximum K and window
+    (9, 600, 17, 7, 0.5, 5),     # two shared-memory chunks, lambda != 1
+    (5, 1030, 3, 3, 2.0, 2),     # three chunks, ragged tail
+    (1, 70, 4, 1, 1.0, 8),       # one row, eight classes
+    (40, 7, 12, 4, 1.0, 4),      # narrower than a warp, even window
+    (6, 50, 150, 9, 1.0, 3),     # K above 64 is rejected (checked below)
+])
+def test_random_maps_against_oracle(hsc, ctx, H, W, K, R, lam, k):
+    I, P = rand_maps(H, W, k, seed=H * 1000 + W + K)
+    if K > hsc.HSC_MAX_K:
+        with pytest.raises(hsc.HscError) as e:
+            run_knn(hsc, ctx, I, P, K, R, lam)
+        assert e.value.status == hsc.HSC_ERR_UNSUPPORTED
+        return
+    nbr, O, lab = run_knn(hsc, ctx, I, P, K, R, lam)
+    st = check_knn(I, P, K, R, lam, nbr, O, lab)
+    assert st["exact_sets"] >= 0.99 * st["pixels"]
+
+
+def test_k1_window1_returns_own_probabilities(hsc, ctx):
+    I, P = rand_maps(33, 71, 4, seed=3)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, 1, 1, 1.0)
+    np.testing.assert_array_equal(O, P)
+    np.testing.assert_array_equal(lab, np.argmax(P, axis=0))
+    np.testing.assert_array_equal(nbr.reshape(-1), np.arange(33 * 71))
+
+
+def test_lambda0_constant_image_tie_rule(hsc, ctx):
+    """All distances 0: the K smallest linear indices of the window win."""
+    H, W, R, K = 12, 40, 5, 30
+    I = np.full((H, W), 0.25, dtype=np.float32)
+    _, P = rand_maps(H, W, 3, seed=4)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, K, R, 0.0)
+    for p in range(H * W):
+        lo = max(0, p // W - R // 2)
+        np.testing.assert_array_equal(nbr.reshape(-1, K)[p], lo * W + np.arange(K))
+
+
+def test_dyadic_image_exact_ties(hsc, ctx):
+    """Coarse grey levels make many exactly equal distances: the tie rule
+    (smaller linear index) must match the oracle everywhere."""
+    I, P = rand_maps(24, 50, 3, seed=5, dyadic=True)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, 20, 6, 1.0)
+    st = check_knn(I, P, 20, 6, 1.0, nbr, O, lab)
+    assert st["exact_sets"] == st["pixels"]
+
+
+def test_whole_window_box_filter(hsc, ctx):
+    H, W = 3, 21
+    I, P = rand_maps(H, W, 4, seed=6)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, H * W, 6, 1.0)
+    mean = P.astype(np.float64).reshape(4, -1).mean(axis=1)
+    np.testing.assert_allclose(O.reshape(4, -1), np.repeat(mean[:, None], H * W, axis=1), atol=1e-6)
+
+
+def test_neuro_size_sampled_rows(hsc, ctx):
+    """416 x 512 frame, K = 40, 14-row window: the oracle's own normalised
+    one-band image and probabilities as inputs, rows at both borders and
+    inside checked pixel by pixel."""
+    f = synth.make_config(2)
+    pca = oracle.pca_one_band(f.cube)
+    P, _, _ = oracle.svm_probs(f.cube, f.model)
+    I32 = pca["I_norm"].astype(np.float32)
+    P32 = P.astype(np.float32)
+    nbr, O, lab = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0)
+    H, W = I32.shape
+    st = check_knn(I32, P32, 40, 14, 1.0, nbr, O, lab,
+                   pixels=sample_rows(H, W, [0, 1, 6, 7, 200, 408, 409, 415]))
+    assert st["exact_sets"] >= 0.99 * st["pixels"]

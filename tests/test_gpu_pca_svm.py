@@ -1,0 +1,138 @@
+"""PCA one-band and SVM probability stages on the GPU through the C ABI
+against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+# Tolerances. The GPU accumulates the covariance in FP32 per pixel block
+# (relative error ~1e-6 of C), so the leading eigenvector differs from the
+# FP64 oracle's by about ||dC|| / gap: 1e-5 in angle covers the synthetic
+# cubes (eigengap >= 10% of lambda1). The normalised one-band image then
+# differs by about angle * max|x - mu| / range: 2e-5 absolute.
+V1_ANGLE = 1e-5
+I_TOL = 2e-5
+P_TOL = 1e-4  # the FP32-path bound on probability maps
+
+
+def to_dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def gpu_pca(hsc, ctx, cube, flags=1):
+    import torch
+    c = to_dev(cube.astype(np.float32))
+    B = cube.shape[0]
+    v = torch.zeros(B, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+    I = hsc.hsc_pca_one_band(ctx, c, flags=flags, eigvec=v, eigval=lam)
+    ctx.sync()
+    return I.cpu().numpy(), v.cpu().numpy(), float(lam.cpu()[0])
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_pca_against_oracle(hsc, ctx, cfg):
+    f = synth.make_config(cfg)
+    ref = oracle.pca_one_band(f.cube)
+    I, v, lam = gpu_pca(hsc, ctx, f.cube)
+    cos = abs(float(v @ ref["v1"]))
+    assert np.sqrt(max(0.0, 1 - cos * cos)) < V1_ANGLE
+    assert float(v @ ref["v1"]) > 0  # same sign rule
+    assert lam == pytest.approx(ref["lambda1"], rel=1e-5)
+    assert np.abs(I - ref["I_norm"]).max() < I_TOL
+    assert I.min() == 0.0 and I.max() == 1.0
+
+
+def test_pca_raw_projection(hsc, ctx):
+    f = synth.make_config(1)
+    ref = oracle.pca_one_band(f.cube)
+    I, v, lam = gpu_pca(hsc, ctx, f.cube, flags=0)
+    np.testing.assert_allclose(I, ref["I_raw"], atol=1e-5 * np.abs(ref["I_raw"]).max())
+
+
+def test_pca_rank_one_closed_form(hsc, ctx):
+    """x_p = m + a_p u exactly in float32: v1 = u/||u|| (closed form)."""
+    rng = np.random.default_rng(2)
+    B, H, W = 40, 33, 35
+    u = rng.integers(-4, 5, size=B).astype(np.float64)
+    u[7] = 9.0
+    m = rng.integers(8, 24, size=B) / 32.0
+    a = rng.integers(-8, 9, size=H * W) / 64.0
+    cube = (m[:, None] + u[:, None] * a[None, :]).reshape(B, H, W).astype(np.float32)
+    I, v, lam = gpu_pca(hsc, ctx, cube)
+    np.testing.assert_allclose(v, u / np.linalg.norm(u), atol=1e-6)
+    assert lam == pytest.approx(np.var(a) * (u @ u), rel=1e-6)
+    In = (a - a.min()) / (a.max() - a.min())
+    np.testing.assert_allclose(I.ravel(), In, atol=2e-6)
+
+
+def test_pca_flat_cube(hsc, ctx):
+    cube = np.full((8, 10, 12), 0.375, dtype=np.float32)
+    I, v, lam = gpu_pca(hsc, ctx, cube)
+    assert np.all(I == 0.0)
+    assert lam == 0.0
+
+
+def test_pca_odd_band_count_and_ragged_pixels(hsc, ctx):
+    f = synth.make_frame(77, 23, 29, 33, sigma=0.03)   # N odd: scalar loads
+    ref = oracle.pca_one_band(f.cube)
+    I, v, lam = gpu_pca(hsc, ctx, f.cube)
+    cos = abs(float(v @ ref["v1"]))
+    assert np.sqrt(max(0.0, 1 - cos * cos)) < V1_ANGLE
+    assert np.abs(I - ref["I_norm"]).max() < I_TOL
+
+
+def gpu_svm(hsc, ctx, cube, model, flags=0):
+    import torch
+    c = to_dev(cube.astype(np.float32))
+    m = hsc.Model.from_host(model)
+    B, H, W = cube.shape
+    lab = torch.full((H, W), -1, dtype=torch.int32, device="cuda")
+    P = hsc.hsc_svm_probs(ctx, c, m, flags=flags, svm_labels=lab)
+    ctx.sync()
+    return P.cpu().numpy(), lab.cpu().numpy()
+
+
+@pytest.mark.parametrize("cfg,flags", [(1, 0), (2, 0), (2, 2)])
+def test_svm_against_oracle(hsc, ctx, cfg, flags):
+    f = synth.make_config(cfg)
+    Pref, lref, _ = oracle.svm_probs(f.cube, f.model)
+    P, lab = gpu_svm(hsc, ctx, f.cube, f.model, flags)
+    err = np.abs(P - Pref).max()
+    assert err < P_TOL, err
+    top = np.sort(Pref, axis=0)
+    clear = (top[-1] - top[-2]) > 2 * P_TOL
+    np.testing.assert_array_equal(lab[clear], lref[clear])
+    np.testing.assert_allclose(P.sum(axis=0), 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 6, 7, 8])
+def test_svm_class_counts(hsc, ctx, k):
+    f = synth.make_frame(100 + k, 17, 31, 24, k=k, sigma=0.05, fractions=None)
+    Pref, lref, _ = oracle.svm_probs(f.cube, f.model)
+    for flags in (0, 2):
+        P, lab = gpu_svm(hsc, ctx, f.cube, f.model, flags)
+        assert np.abs(P - Pref).max() < P_TOL
+        top = np.sort(Pref, axis=0)
+        clear = (top[-1] - top[-2]) > 2 * P_TOL
+        np.testing.assert_array_equal(lab[clear], lref[clear])
+
+
+def test_svm_consistent_closed_form(hsc, ctx):
+    """w = 0 and b = f with consistent pairwise probabilities: p = p*."""
+    import json, os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "svm_k3_consistent.json")))
+    cube = np.tile(np.asarray(g["x"], dtype=np.float32)[:, None, None], (1, 4, 4))
+    m = synth.SvmModel(n_classes=3, w=np.asarray(g["w"], dtype=np.float32),
+                       b=np.asarray(g["b"], dtype=np.float32),
+                       platt_a=np.asarray(g["platt_a"], dtype=np.float32),
+                       platt_b=np.asarray(g["platt_b"], dtype=np.float32))
+    P, lab = gpu_svm(hsc, ctx, cube, m)
+    np.testing.assert_allclose(P.reshape(3, -1), np.repeat(np.asarray(g["p"])[:, None], 16, 1),
+                               atol=g["tol"])
+    assert np.all(lab == 0)
