@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Throughput of the spatial-spectral classification hot path on GB300.
+
+One step = one hsc_classify call (PCA one-band, SVM probabilities, KNN
+filter, labels) on a 416 x 512 x 128 float32 neurosurgery-scale frame,
+K = 40, 14-row window, lambda = 1. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (rank 0 only). Under torchrun each rank runs an
+independent replica on its own GPU (frames are independent: weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+CFG = 2
+METRIC = "KNN-filtered pixels/s (whole classification path) on 1 GB300"
+UNIT = "pixels/s"
+N_ROTATING = 4  # distinct cube copies (4 x 109 MB > 129 MB L2)
+
+
+def workload_config(f, extra=None):
+    B, H, W = f.cube.shape
+    cfg = {"workload": "neurosurgery-scale frame %dx%dx%d float32, 4 classes, K=%d, %d-row "
+                       "window, lambda=%g" % (H, W, B, f.K, f.window_rows, f.lam),
+           "H": H, "W": W, "B": B, "classes": f.model.n_classes, "K": f.K,
+           "window_rows": f.window_rows, "lambda": f.lam,
+           "l2": "%d rotating cube copies (%.0f MB) > 129 MB L2" % (
+               N_ROTATING, N_ROTATING * f.cube.nbytes / 1e6),
+           "parallelism": "replicas"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline --
+def knn_pairs(H, W, R):
+    """(pixel, window candidate) pairs: each of the W pixels of row r has
+    W * (rows of its window) candidates."""
+    rows = 0
+    for r in range(H):
+        lo = max(0, r - R // 2)
+        hi = min(H - 1, r + (R + 1) // 2 - 1)
+        rows += hi - lo + 1
+    return rows * W * W
+
+
+def stage_work(f):
+    """Algorithmic work per launch of each stage (bytes for HBM-bound stages,
+    FP32 ops for the KNN) and its bound."""
+    B, H, W = f.cube.shape
+    N = H * W
+    k = f.model.n_classes
+    return {
+        # one read of the cube (the partial Gram outputs are a few MB)
+        "moments": ("hbm", 4.0 * B * N),
+        # cube read + I (4 B) and P (4k B) written
+        "project_svm": ("hbm", 4.0 * B * N + 4.0 * N + 4.0 * k * N),
+        # I read + written
+        "normalize": ("hbm", 8.0 * N),
+        # 4 FP32-pipe ops per (pixel, window candidate) pair
+        "knn": ("alu", 4.0 * knn_pairs(H, W, f.window_rows)),
+        "jacobi": ("latency", None),
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_pipe_peak_tops(sm_count, mhz):
+    """FP32 pipe lane-operations per second: 128 FP32 lanes per SM."""
+    return sm_count * 128 * mhz * 1e6 / 1e12
+
+
+def kernel_source_sha(stage):
+    files = {"knn": "k_knn.cu", "project_svm": "k_project_svm.cu", "moments": "k_moments.cu",
+             "jacobi": "k_jacobi.cu", "normalize": "k_project_svm.cu"}
+    path = os.path.join(ROOT, "paper_2404_10631_gb300", "csrc", files[stage])
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def traffic_from_profiles(stage):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kernel_source_sha(stage)
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 3 and parts[0] == stage and parts[1] == sha:
+            return float(parts[2])
+    return None
+
+
+# ----------------------------------------------------------------- oracle --
+def oracle_sample(f, rows, state=None):
+    """FP64 oracle on a row sample of the frame; returns (seconds per frame,
+    description). Per-pixel stages are timed on the sampled rows and scaled
+    by H / len(rows); the per-frame Jacobi is timed whole."""
+    import oracle
+    B, H, W = f.cube.shape
+    if state is None:
+        state = {}
+    if "C" not in state:  # full-frame inputs of the per-frame / later stages
+        mu = oracle.band_means(f.cube)
+        state["C"] = oracle.covariance(f.cube, mu)
+        pca = oracle.pca_one_band(f.cube)
+        P, _, _ = oracle.svm_probs(f.cube, f.model)
+        state.update(mu=mu, v1=pca["v1"], I32=pca["I_norm"].astype(np.float32),
+                     P32=P.astype(np.float32))
+    sub = np.ascontiguousarray(f.cube[:, rows, :])
+    t0 = time.perf_counter()
+    mu_s = oracle.band_means(sub)
+    oracle.covariance(sub, mu_s)
+    t1 = time.perf_counter()
+    oracle.jacobi(state["C"])
+    t2 = time.perf_counter()
+    oracle.project(sub, state["mu"], state["v1"])
+    oracle.svm_probs(sub, f.model)
+    t3 = time.perf_counter()
+    for r in rows:
+        oracle.knn(state["I32"], state["P32"], f.K, f.window_rows, f.lam, r * W, (r + 1) * W)
+    t4 = time.perf_counter()
+    scale = H / float(len(rows))
+    per_frame = (t1 - t0 + t3 - t2 + t4 - t3) * scale + (t2 - t1)
+    desc = ("oracle (single-threaded C, FP64) on %d of %d rows: band means + covariance, "
+            "projection, SVM + coupling and KNN timed on the rows and scaled by %.1f; "
+            "full-frame Jacobi timed whole" % (len(rows), H, scale))
+    return per_frame, desc, state
+
+
+def run_reference(args, f):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    B, H, W = f.cube.shape
+    N = H * W
+    # keep the whole run to a few minutes: ~1.3 s per step with 4 rows
+    n_rows = 4 if args.steps + args.warmup <= 60 else 2
+    rng = np.random.default_rng(0)
+    state = None
+    for _ in range(args.warmup):
+        rows = np.sort(rng.choice(H, n_rows, replace=False))
+        _, desc, state = oracle_sample(f, rows, state)
+    t_total = 0.0
+    for _ in range(args.steps):
+        rows = np.sort(rng.choice(H, n_rows, replace=False))
+        t, desc, state = oracle_sample(f, rows, state)
+        t_total += t
+    value = N * args.steps / t_total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(f),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours --
+def run_ours(args, f):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2404_10631_gb300 as hsc
+    from paper_2404_10631_gb300 import build as hbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        hbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    dev = torch.device("cuda", local)
+    B, H, W = f.cube.shape
+    N = H * W
+    k = f.model.n_classes
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = hsc.Context(local, stream=stream)
+    ctx.reserve(B, H, W, k)
+    cubes = [torch.as_tensor(f.cube, device=dev).clone() for _ in range(N_ROTATING)]
+    model = hsc.Model.from_host(f.model, device=dev)
+    I = torch.empty((H, W), dtype=torch.float32, device=dev)
+    P = torch.empty((k, H, W), dtype=torch.float32, device=dev)
+    O = torch.empty((k, H, W), dtype=torch.float32, device=dev)
+    lab = torch.empty((H, W), dtype=torch.int32, device=dev)
+
+    def step(i):
+        hsc.hsc_classify(ctx, cubes[i % N_ROTATING], model, f.K, f.window_rows, f.lam,
+                         labels=lab, out_probs=O, one_band=I, probs=P)
+
+    for i in range(args.warmup):
+        step(i)
+    ctx.sync()
+
+    # ---- device-resident timed region
+    ctx.profile(True)
+    ctx.profile_read()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step(i)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ctx.sync()
+    stage_ms, stage_kernels, dropped = ctx.profile_read()
+    ctx.profile(False)
+    sweeps, refine_iters = ctx.pca_diagnostics()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    elapsed = ev[0].elapsed_time(ev[args.steps])
+    t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_max = float(t.item())
+    value = world * N * args.steps / (elapsed_max / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    host_cube = torch.empty((B, H, W), dtype=torch.float32).pin_memory()
+    host_cube.copy_(torch.from_numpy(f.cube))
+    host_lab = torch.empty((H, W), dtype=torch.int32).pin_memory()
+    host_model = [torch.from_numpy(a).pin_memory() for a in
+                  (f.model.w, f.model.b, f.model.platt_a, f.model.platt_b)]
+    dev_cube = cubes[0]
+    dev_model = [model.w, model.b, model.platt_a, model.platt_b]
+    h2d = host_cube.numel() * 4 + sum(a.numel() * 4 for a in host_model)
+    d2h = host_lab.numel() * 4
+    n_e2e = max(1, min(args.steps, 20))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        dev_cube.copy_(host_cube, non_blocking=True)
+        for d, h in zip(dev_model, host_model):
+            d.copy_(h, non_blocking=True)
+        hsc.hsc_classify(ctx, dev_cube, model, f.K, f.window_rows, f.lam, labels=lab)
+        host_lab.copy_(lab, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * N * n_e2e / float(t.item())
+    ctx.sync()
+
+    # ---- roofline of the dominant stage
+    peaks, peak_src = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    work = stage_work(f)
+    stages = {}
+    for name, ms in stage_ms.items():
+        launches = max(1, args.steps)
+        avg_ms = ms / launches
+        bound, units = work[name]
+        entry = {"ms_per_launch": avg_ms, "share": ms / max(1e-12, sum(stage_ms.values())),
+                 "kernels_per_launch": stage_kernels[name] / launches, "bound": bound}
+        if bound == "hbm":
+            ach = units / (avg_ms / 1e3) / 1e9
+            entry.update(achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                         frac=ach / peaks["hbm_gbs"], algorithmic=units)
+        elif bound == "alu":
+            peak = fp32_pipe_peak_tops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+            ach = units / (avg_ms / 1e3) / 1e12
+            entry.update(achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                         algorithmic=units)
+        stages[name] = entry
+    dom = max((s for s in stages if stages[s]["bound"] in ("hbm", "alu")),
+              key=lambda s: stages[s]["ms_per_launch"])
+    d = stages[dom]
+    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
+                "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
+                "traffic": traffic_from_profiles(dom),
+                "peak_source": ("%s (%s)" % ("FP32 pipe: SMs x 128 lanes x max SM clock",
+                                             peak_src) if d["bound"] == "alu"
+                                else "hbm_gbs, %s" % peak_src),
+                "work_per_launch": d["algorithmic"]}
+
+    lat = sorted(per_step)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": workload_config(f, {"frames_per_step_per_gpu": 1}),
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1,
+                                                                     int(0.99 * len(lat)))]},
+            "roofline": roofline,
+            "stages": stages,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": n_e2e},
+            "gpu_launches": int(sum(stage_kernels.values())),
+            "jacobi": {"fp32_sweeps": sweeps, "fp64_refine_iters": refine_iters},
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = np.linspace(0, H - 1, 16).astype(int)
+        t_frame, desc, _ = oracle_sample(f, rows)
+        line["cpu_baseline"] = {"value": N / t_frame, "unit": UNIT, "cores": 1,
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    f = synth.make_config(CFG)
+    if args.impl == "reference":
+        run_reference(args, f)
+    else:
+        run_ours(args, f)
+
+
+if __name__ == "__main__":
+    main()

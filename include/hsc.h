@@ -168,6 +168,31 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                         unsigned flags, int32_t *labels, float *out_probs,
                         float *one_band, float *probs);
 
+/* ---- stage timing (no counterpart in the paper; its Section IV times each
+ * algorithm separately, and this is how the library exposes the same split).
+ * While enabled, every stage launch of the context is bracketed by two CUDA
+ * events recorded on the context's stream; hsc_profile_read waits for the
+ * stream, adds up the elapsed times per stage since the last read, and
+ * clears them. At most HSC_PROFILE_MAX_RECORDS stage launches are kept
+ * between reads (older ones are dropped and counted in `dropped`). */
+enum {
+    HSC_STAGE_MOMENTS = 0,    /* pilot shift, partial Gram, FP64 reductions (4 kernels) */
+    HSC_STAGE_JACOBI = 1,     /* Jacobi + FP64 refinement (1 kernel) */
+    HSC_STAGE_PROJECT_SVM = 2,/* projection + SVM + coupling (1 kernel) */
+    HSC_STAGE_NORMALIZE = 3,  /* min-max normalisation (1 kernel) */
+    HSC_STAGE_KNN = 4,        /* KNN filter (1 kernel) */
+    HSC_N_STAGES = 5
+};
+#define HSC_PROFILE_MAX_RECORDS 8192
+
+hsc_status hsc_profile_enable(hsc_ctx *ctx, int enable);
+/* Diagnostics of the context's last PCA (waits for the stream): FP32 Jacobi
+ * sweeps run and FP64 refinement iterations of the leading eigenvector. */
+hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_iters);
+/* ms[HSC_N_STAGES]: summed milliseconds; kernels[HSC_N_STAGES]: kernel
+ * launches per stage; dropped (nullable): records lost to the cap. */
+hsc_status hsc_profile_read(hsc_ctx *ctx, double *ms, int64_t *kernels, int64_t *dropped);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc -O2 (no fast-math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -48,16 +48,17 @@ def _load():
         lib.oracle_pca_one_band.argtypes = [f32p, c_int, c_int, c_int, c_double,
                                             f64p, f64p, f64p, f64p, f64p, f64p,
                                             f64p, f64p, i64p]
+        lib.oracle_project.argtypes = [f32p, c_int, c_long, f64p, f64p, f64p, f64p]
         lib.oracle_couple.argtypes = [f64p, c_int, f64p]
         lib.oracle_svm_probs.argtypes = [f32p, c_int, c_long, c_int, f32p, f32p,
                                          f32p, f32p, f64p, i32p, f64p]
         lib.oracle_knn_min_candidates.argtypes = [c_int, c_int, c_int]
         lib.oracle_knn_min_candidates.restype = c_long
         lib.oracle_knn.argtypes = [f32p, f32p, c_int, c_int, c_int, c_int, c_int,
-                                   c_double, c_long, c_long, f64p, i32p, i32p,
+                                   c_double, c_int, c_long, c_long, f64p, i32p, i32p,
                                    f64p, f64p, f64p]
         for name in ("oracle_band_means", "oracle_covariance", "oracle_jacobi",
-                     "oracle_pca_one_band", "oracle_couple", "oracle_svm_probs",
+                     "oracle_pca_one_band", "oracle_project", "oracle_couple", "oracle_svm_probs",
                      "oracle_knn"):
             getattr(lib, name).restype = c_int
         _lib = lib
@@ -113,6 +114,21 @@ def jacobi(C: np.ndarray, tol: float = 1e-13, max_rot: int = 0):
     st = _load().oracle_jacobi(_p(C, ctypes.c_double), B, tol, max_rot, _p(ev, ctypes.c_double),
                                _p(V, ctypes.c_double), ctypes.byref(nrot))
     return ev, V, int(nrot.value), st
+
+
+def project(cube: np.ndarray, mu: np.ndarray, v1: np.ndarray):
+    """Step (iv): (I_raw, I_norm) of the cube's pixels on v1."""
+    cube = np.ascontiguousarray(cube, dtype=np.float32)
+    B = cube.shape[0]
+    N = cube.size // B
+    I = np.empty(N)
+    In = np.empty(N)
+    d = ctypes.c_double
+    _check(_load().oracle_project(_p(cube, ctypes.c_float), B, N,
+                                  _p(np.ascontiguousarray(mu, dtype=np.float64), d),
+                                  _p(np.ascontiguousarray(v1, dtype=np.float64), d),
+                                  _p(I, d), _p(In, d)), "oracle_project")
+    return I, In
 
 
 def pca_one_band(cube: np.ndarray, tol: float = 1e-13) -> Dict[str, np.ndarray]:
@@ -173,8 +189,13 @@ def knn_min_candidates(H: int, W: int, R: int) -> int:
 
 
 def knn(I_norm: np.ndarray, P: np.ndarray, K: int, R: int, lam: float,
-        p0: int = 0, p1: Optional[int] = None, want_nbr: bool = False):
+        p0: int = 0, p1: Optional[int] = None, want_nbr: bool = False,
+        float_keys: bool = False):
     """KNN filter on pixels [p0, p1) of the float inputs (Eq. 1, Eq. 2).
+
+    float_keys: take the selection on the float terms of Eq. 1 (fl(I_p-I_q)^2
+    and fl(lambda^2)(dr^2+dc^2), each rounded to float, summed exactly)
+    instead of on FP64 distances.
 
     Returns dict with O[k, n], labels[n], nbr[n, K+1] (if asked: the first
     K+1 candidates in (distance, index) order, -1 padded), dK, dK1, gapO.
@@ -192,7 +213,7 @@ def knn(I_norm: np.ndarray, P: np.ndarray, K: int, R: int, lam: float,
     dK, dK1, gap = np.empty(n), np.empty(n), np.empty(n)
     d = ctypes.c_double
     st = _load().oracle_knn(_p(I_norm, ctypes.c_float), _p(P, ctypes.c_float), H, W, k, K, R,
-                            float(lam), p0, p1, _p(O, d), _p(lab, ctypes.c_int),
+                            float(lam), 1 if float_keys else 0, p0, p1, _p(O, d), _p(lab, ctypes.c_int),
                             _p(nbr, ctypes.c_int), _p(dK, d), _p(dK1, d), _p(gap, d))
     _check(st, "oracle_knn")
     return dict(O=O, labels=lab, nbr=nbr, dK=dK, dK1=dK1, gapO=gap)

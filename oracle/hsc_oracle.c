@@ -158,6 +158,28 @@ int oracle_jacobi(const double *C, int B, double tol, long max_rot,
     return status;
 }
 
+/* Step (iv): projection of the centred pixels on the first eigenvector,
+ * I_p = v1^T (x_p - mu), then the min-max normalisation (I - min)/(max - min)
+ * (all zeros when I is constant). I_norm is nullable. */
+int oracle_project(const float *cube, int B, long N, const double *mu, const double *v1,
+                   double *I_raw, double *I_norm)
+{
+    if (!cube || !mu || !v1 || !I_raw || B <= 0 || N <= 0) return ORC_INVALID;
+    double mn = INFINITY, mx = -INFINITY;
+    for (long p = 0; p < N; ++p) {
+        double acc = 0.0;
+        for (int b = 0; b < B; ++b)
+            acc += v1[b] * ((double)cube[(size_t)b * (size_t)N + p] - mu[b]);
+        I_raw[p] = acc;
+        if (acc < mn) mn = acc;
+        if (acc > mx) mx = acc;
+    }
+    if (I_norm)
+        for (long p = 0; p < N; ++p)
+            I_norm[p] = (mx > mn) ? (I_raw[p] - mn) / (mx - mn) : 0.0;
+    return ORC_OK;
+}
+
 /* Whole one-band PCA (steps (i)-(iv) plus the min-max normalisation that the
  * KNN's "normalized pixel value" needs). Outputs (all caller-allocated):
  *   mu[B], C[B*B], evals[B], V[B*B], v1[B], *lambda1,
@@ -182,18 +204,7 @@ int oracle_pca_one_band(const float *cube, int B, int H, int W, double tol,
     for (int b = 1; b < B; ++b) if (fabs(v1[b]) > fabs(v1[big])) big = b;
     if (v1[big] < 0.0) for (int b = 0; b < B; ++b) v1[b] = -v1[b];
     *lambda1 = evals[lead];
-    /* step (iv): projection of the centred pixel on the first eigenvector */
-    double mn = INFINITY, mx = -INFINITY;
-    for (long p = 0; p < N; ++p) {
-        double acc = 0.0;
-        for (int b = 0; b < B; ++b)
-            acc += v1[b] * ((double)cube[(size_t)b * (size_t)N + p] - mu[b]);
-        I_raw[p] = acc;
-        if (acc < mn) mn = acc;
-        if (acc > mx) mx = acc;
-    }
-    for (long p = 0; p < N; ++p)
-        I_norm[p] = (mx > mn) ? (I_raw[p] - mn) / (mx - mn) : 0.0;
+    oracle_project(cube, B, N, mu, v1, I_raw, I_norm);
     return st;
 }
 
@@ -301,14 +312,41 @@ int oracle_svm_probs(const float *cube, int B, long N, int k, const float *w,
 
 /* ---------------------------------------------------------------- KNN --- */
 
-typedef struct { double d; long q; } cand_t;
+/* A candidate's sort key: (d, lo, q). In the FP64 mode lo = 0 and d is the
+ * distance. In the float mode (d, lo) is the exact sum s + e of the float
+ * terms as an unevaluated pair (hi = fl(s + e), lo = the rounding error), so
+ * ordering by (d, lo) orders the real values s + e. */
+typedef struct { double d; double lo; long q; } cand_t;
 
 static int cand_cmp(const void *a, const void *b)
 {
     const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
     if (x->d < y->d) return -1;
     if (x->d > y->d) return 1;
+    if (x->lo < y->lo) return -1;
+    if (x->lo > y->lo) return 1;
     return (x->q < y->q) ? -1 : (x->q > y->q);
+}
+
+/* Eq. 1 with float terms, as the paper's GPU and manycore KNN compute it in
+ * float (Section III.B.3): dI = fl(I_p - I_q), e = fl(dI^2),
+ * s = fl(fl(lambda^2) (dr^2 + dc^2)), and the sum s + e taken exactly
+ * (Knuth's two-sum) so that comparing two candidates compares the real sums.
+ * Each float operation is a separately rounded ISO C float operation
+ * (compiled without floating-point contraction). */
+static void float_key(float Ip, float Iq, float l2, int dr, int dc, double *hi, double *lo)
+{
+    volatile float dI = Ip - Iq;
+    volatile float e = dI * dI;
+    volatile float s = l2 * (float)(dr * dr + dc * dc);
+    volatile float h = s + e;
+    volatile float bb = h - s;
+    volatile float t1 = h - bb;
+    volatile float t2 = s - t1;
+    volatile float t3 = e - bb;
+    volatile float l = t2 + t3;
+    *hi = (double)h;
+    *lo = (double)l;
 }
 
 /* Smallest number of window candidates over all rows: K must not exceed it. */
@@ -330,8 +368,8 @@ long oracle_knn_min_candidates(int H, int W, int R)
  * when the window holds only K), dK[t] = K-th distance, dK1[t] = (K+1)-th
  * (inf if none), gapO[t] = largest minus second largest O. */
 int oracle_knn(const float *I_norm, const float *P, int H, int W, int k, int K,
-               int R, double lambda, long p0, long p1, double *O, int *labels,
-               int *nbr, double *dK, double *dK1, double *gapO)
+               int R, double lambda, int float_keys, long p0, long p1, double *O,
+               int *labels, int *nbr, double *dK, double *dK1, double *gapO)
 {
     if (!I_norm || !P || !O || H <= 0 || W <= 0 || k < 1 || K < 1 || R < 1 ||
         !(lambda >= 0.0) || p0 < 0 || p1 > (long)H * W || p1 < p0)
@@ -339,6 +377,8 @@ int oracle_knn(const float *I_norm, const float *P, int H, int W, int k, int K,
     if ((long)K > oracle_knn_min_candidates(H, W, R)) return ORC_INVALID;
     long N = (long)H * W, np = p1 - p0;
     double l2 = lambda * lambda;
+    volatile float lamf = (float)lambda;
+    volatile float l2f = lamf * lamf;
     cand_t *cand = (cand_t *)malloc(sizeof(cand_t) * (size_t)R * (size_t)W);
     if (!cand) return ORC_INVALID;
     for (long p = p0; p < p1; ++p) {
@@ -352,9 +392,14 @@ int oracle_knn(const float *I_norm, const float *P, int H, int W, int k, int K,
         for (int i = lo; i <= hi; ++i)
             for (int j = 0; j < W; ++j) {
                 long q = (long)i * W + j;
-                double dI = Ip - (double)I_norm[q];
-                double dr = (double)(r - i), dc = (double)(c - j);
-                cand[n].d = dI * dI + l2 * (dr * dr + dc * dc);
+                if (float_keys) {
+                    float_key(I_norm[p], I_norm[q], l2f, r - i, c - j, &cand[n].d, &cand[n].lo);
+                } else {
+                    double dI = Ip - (double)I_norm[q];
+                    double dr = (double)(r - i), dc = (double)(c - j);
+                    cand[n].d = dI * dI + l2 * (dr * dr + dc * dc);
+                    cand[n].lo = 0.0;
+                }
                 cand[n].q = q;
                 ++n;
             }
@@ -373,8 +418,8 @@ int oracle_knn(const float *I_norm, const float *P, int H, int W, int k, int K,
         if (nbr)
             for (int m = 0; m <= K; ++m)
                 nbr[t * (K + 1) + m] = (m < n) ? (int)cand[m].q : -1;
-        if (dK) dK[t] = cand[K - 1].d;
-        if (dK1) dK1[t] = (n > K) ? cand[K].d : INFINITY;
+        if (dK) dK[t] = cand[K - 1].d + cand[K - 1].lo;
+        if (dK1) dK1[t] = (n > K) ? cand[K].d + cand[K].lo : INFINITY;
         if (gapO) gapO[t] = (k > 1) ? top1 - top2 : INFINITY;
     }
     free(cand);

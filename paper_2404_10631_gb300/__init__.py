@@ -34,7 +34,9 @@ HSC_SVM_COUPLE_F64 = 2
 
 EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_error",
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
-            "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify")
+            "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
+            "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics")
+STAGES = ("moments", "jacobi", "project_svm", "normalize", "knn")
 
 
 class hsc_svm_model(ctypes.Structure):
@@ -91,6 +93,11 @@ def lib():
                                      vp, vp, vp]
         L.hsc_classify.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
                                    ctypes.POINTER(hsc_knn_params), ctypes.c_uint, vp, vp, vp, vp]
+        L.hsc_profile_enable.argtypes = [vp, i32]
+        L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]
+        L.hsc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         for name in EXPORTED:
             fn = getattr(L, name)
             if name not in ("hsc_ctx_destroy", "hsc_last_error", "hsc_status_string",
@@ -98,6 +105,19 @@ def lib():
                 fn.restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
+def _stream_handle(stream) -> Optional[int]:
+    """cudaStream_t of a torch stream (or raw handle). Handle 0 is the legacy
+    default stream, which the C API must receive as cudaStreamLegacy because
+    NULL there means "a stream owned by the context"."""
+    if stream is None:
+        return None
+    h = int(getattr(stream, "cuda_stream", stream))
+    return CUDA_STREAM_LEGACY if h == 0 else h
 
 
 def _ptr(t) -> Optional[int]:
@@ -135,8 +155,7 @@ class Context:
     def __init__(self, device: int = 0, stream=None, scratch_cap_bytes: int = 0):
         L = lib()
         h = ctypes.c_void_p()
-        sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
-        st = L.hsc_ctx_create(device, sp, scratch_cap_bytes, ctypes.byref(h))
+        st = L.hsc_ctx_create(device, _stream_handle(stream), scratch_cap_bytes, ctypes.byref(h))
         if st != HSC_OK:
             raise HscError(st, "hsc_ctx_create(device=%d)" % device)
         self.handle = h
@@ -164,14 +183,33 @@ class Context:
             raise HscError(st, lib().hsc_last_error(self.handle).decode())
 
     def set_stream(self, stream=None):
-        sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
-        self.check(lib().hsc_set_stream(self.handle, sp))
+        self.check(lib().hsc_set_stream(self.handle, _stream_handle(stream)))
 
     def sync(self):
         self.check(lib().hsc_sync(self.handle))
 
     def reserve(self, B, H, W, n_classes):
         self.check(lib().hsc_reserve(self.handle, B, H, W, n_classes))
+
+    def profile(self, enable: bool = True):
+        """Bracket every stage launch with CUDA events on the context's stream."""
+        self.check(lib().hsc_profile_enable(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """Wait for the stream; per-stage (ms, kernel launches) since the last read."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        kern = (ctypes.c_int64 * n)()
+        dropped = ctypes.c_int64(0)
+        self.check(lib().hsc_profile_read(self.handle, ms, kern, ctypes.byref(dropped)))
+        return ({STAGES[i]: float(ms[i]) for i in range(n)},
+                {STAGES[i]: int(kern[i]) for i in range(n)}, int(dropped.value))
+
+    def pca_diagnostics(self):
+        """(FP32 Jacobi sweeps, FP64 refinement iterations) of the last PCA."""
+        a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        self.check(lib().hsc_pca_diagnostics(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return int(a.value), int(b.value)
 
     @property
     def scratch_bytes(self) -> int:

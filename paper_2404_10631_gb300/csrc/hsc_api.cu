@@ -26,12 +26,41 @@ struct hsc_ctx {
     unsigned host_status = 0;      // status bits saved across a scratch reallocation
     unsigned *h_status = nullptr;  // pinned readback word
     std::string last_error;
+    // stage timing
+    bool profiling = false;
+    cudaEvent_t *ev = nullptr;     // 2 * HSC_PROFILE_MAX_RECORDS events
+    int *rec_stage = nullptr;      // stage of each record
+    int n_rec = 0;
+    int64_t kernels[HSC_N_STAGES] = {0, 0, 0, 0, 0};
+    int64_t dropped = 0;
 };
 
 namespace {
 
 using hsc::Control;
 using hsc::PcaScratch;
+
+// Brackets one stage launch with events when the context is profiling.
+struct StageTimer {
+    hsc_ctx *ctx;
+    int slot = -1;
+    StageTimer(hsc_ctx *c, int stage, int n_kernels) : ctx(c)
+    {
+        if (!ctx->profiling) return;
+        ctx->kernels[stage] += n_kernels;
+        if (ctx->n_rec >= HSC_PROFILE_MAX_RECORDS) {
+            ++ctx->dropped;
+            return;
+        }
+        slot = ctx->n_rec++;
+        ctx->rec_stage[slot] = stage;
+        cudaEventRecord(ctx->ev[2 * slot], ctx->stream);
+    }
+    ~StageTimer()
+    {
+        if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], ctx->stream);
+    }
+};
 
 constexpr int kMaxW = 4096;    // KNN: (W-1)^2 + (R/2)^2 stays exact in float32
 constexpr int kMaxH = 65535;   // KNN grid.y
@@ -257,11 +286,81 @@ hsc_status hsc_ctx_create(int device, void *cuda_stream, size_t scratch_cap_byte
     return HSC_OK;
 }
 
+hsc_status hsc_profile_enable(hsc_ctx *ctx, int enable)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if (enable && !ctx->ev) {
+        ctx->ev = new cudaEvent_t[2 * HSC_PROFILE_MAX_RECORDS];
+        ctx->rec_stage = new int[HSC_PROFILE_MAX_RECORDS];
+        for (int i = 0; i < 2 * HSC_PROFILE_MAX_RECORDS; ++i) {
+            cudaError_t e = cudaEventCreate(&ctx->ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->ev[j]);
+                delete[] ctx->ev;
+                delete[] ctx->rec_stage;
+                ctx->ev = nullptr;
+                ctx->rec_stage = nullptr;
+                return cuda_fail(ctx, e, "cudaEventCreate");
+            }
+        }
+    }
+    ctx->profiling = enable != 0 && ctx->ev != nullptr;
+    return HSC_OK;
+}
+
+hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_iters)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!sweeps || !refine_iters)
+        return fail(ctx, HSC_ERR_INVALID_ARG, "sweeps and refine_iters are required%s");
+    *sweeps = -1;
+    *refine_iters = -1;
+    if (!ctx->scratch) return HSC_OK;
+    Control c;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&c, ctx->scratch, sizeof c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_pca_diagnostics");
+    *sweeps = (int32_t)c.jacobi_sweeps;
+    *refine_iters = (int32_t)c.refine_iters;
+    return HSC_OK;
+}
+
+hsc_status hsc_profile_read(hsc_ctx *ctx, double *ms, int64_t *kernels, int64_t *dropped)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!ms || !kernels) return fail(ctx, HSC_ERR_INVALID_ARG, "ms and kernels are required%s");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    for (int i = 0; i < HSC_N_STAGES; ++i) {
+        ms[i] = 0.0;
+        kernels[i] = ctx->kernels[i];
+        ctx->kernels[i] = 0;
+    }
+    for (int r = 0; r < ctx->n_rec; ++r) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, ctx->ev[2 * r], ctx->ev[2 * r + 1]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventElapsedTime");
+        ms[ctx->rec_stage[r]] += (double)t;
+    }
+    ctx->n_rec = 0;
+    if (dropped) *dropped = ctx->dropped;
+    ctx->dropped = 0;
+    return HSC_OK;
+}
+
 void hsc_ctx_destroy(hsc_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->ev) {
+        for (int i = 0; i < 2 * HSC_PROFILE_MAX_RECORDS; ++i) cudaEventDestroy(ctx->ev[i]);
+        delete[] ctx->ev;
+        delete[] ctx->rec_stage;
+    }
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -332,13 +431,24 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     Layout L = make_layout(ctx, B, N, 0, true, false, false);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
-    cudaError_t e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
-    if (e == cudaSuccess) e = hsc::launch_jacobi(B, s, ctx->stream);
-    if (e == cudaSuccess)
+    cudaError_t e;
+    {
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_JACOBI, 1);
+        e = hsc::launch_jacobi(B, s, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_PROJECT_SVM, 1);
         e = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, one_band, nullptr, false, nullptr,
                                     nullptr, s.ctl, ctx->sm_count, ctx->stream);
-    if (e == cudaSuccess && (flags & HSC_PCA_MINMAX))
+    }
+    if (e == cudaSuccess && (flags & HSC_PCA_MINMAX)) {
+        StageTimer t(ctx, HSC_STAGE_NORMALIZE, 1);
         e = hsc::launch_normalize(one_band, one_band, N, s.ctl, ctx->stream);
+    }
     if (e == cudaSuccess && eigvec)
         e = cudaMemcpyAsync(eigvec, s.v1, sizeof(double) * B, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e == cudaSuccess && eigval)
@@ -361,6 +471,7 @@ hsc_status hsc_svm_probs(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     Layout L = make_layout(ctx, B, N, model->n_classes, false, false, false);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
+    StageTimer t(ctx, HSC_STAGE_PROJECT_SVM, 1);
     cudaError_t e = hsc::launch_project_svm(cube, B, N, nullptr, nullptr, nullptr, model,
                                             (flags & HSC_SVM_COUPLE_F64) != 0, probs, svm_labels,
                                             s.ctl, ctx->sm_count, ctx->stream);
@@ -380,6 +491,7 @@ hsc_status hsc_knn_filter(hsc_ctx *ctx, const float *one_band, const float *prob
     Layout L = make_layout(ctx, 1, (long)H * W, n_classes, false, false, false);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
+    StageTimer t(ctx, HSC_STAGE_KNN, 1);
     cudaError_t e = hsc::launch_knn(one_band, probs, n_classes, H, W, params->k,
                                     params->window_rows, params->lambda, out_probs, labels, nbr_idx,
                                     s.ctl, ctx->stream);
@@ -406,16 +518,30 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     char *base = static_cast<char *>(ctx->scratch);
     float *I = one_band ? one_band : reinterpret_cast<float *>(base + L.tmpI);
     float *Pm = probs ? probs : reinterpret_cast<float *>(base + L.tmpP);
-    cudaError_t e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
-    if (e == cudaSuccess) e = hsc::launch_jacobi(B, s, ctx->stream);
-    if (e == cudaSuccess)
+    cudaError_t e;
+    {
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_JACOBI, 1);
+        e = hsc::launch_jacobi(B, s, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_PROJECT_SVM, 1);
         e = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model,
                                     (flags & HSC_SVM_COUPLE_F64) != 0, Pm, nullptr, s.ctl,
                                     ctx->sm_count, ctx->stream);
-    if (e == cudaSuccess) e = hsc::launch_normalize(I, I, N, s.ctl, ctx->stream);
-    if (e == cudaSuccess)
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_NORMALIZE, 1);
+        e = hsc::launch_normalize(I, I, N, s.ctl, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_KNN, 1);
         e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
                             out_probs, labels, nullptr, s.ctl, ctx->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_classify launch");
     return HSC_OK;
 }

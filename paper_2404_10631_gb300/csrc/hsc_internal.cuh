@@ -22,7 +22,9 @@ struct Control {
     unsigned status;          // ST_* bits
     unsigned imin_key;        // ordered-int key of min I (atomicMin)
     unsigned imax_key;        // ordered-int key of max I (atomicMax)
-    unsigned pad[61];
+    unsigned jacobi_sweeps;   // diagnostics of the last Jacobi launch
+    unsigned refine_iters;
+    unsigned pad[59];
 };
 
 // Float <-> order-preserving unsigned key (for atomic min/max of floats).

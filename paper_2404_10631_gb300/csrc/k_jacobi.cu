@@ -28,13 +28,15 @@ namespace {
 
 constexpr int kJacThreads = 1024;
 constexpr int kMaxPairs = 512;           // Bp <= 1024
-constexpr int kMaxRefine = 12;
+constexpr int kMaxRefine = 24;
 constexpr size_t kJacSmemLimit = 190 * 1024;  // + ~33 KB static shared
 
 struct JacParams {
     int B, n;            // n = B rounded up to even
     int max_sweeps;
     float rot_tol;       // rotate (p,q) when |a_pq| > rot_tol (A scaled to max diag 1)
+    float stop_tol;      // end the sweeps once every |a_pq| seen in one is <= stop_tol
+    float stop_tol_final;  // tighter tolerance for a second round if refinement stalls
     int use_smem;
 };
 
@@ -95,15 +97,15 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
 {
     extern __shared__ float smem[];
     const int B = prm.B, n = prm.n, P = n / 2;
+    const int ld = n + 1;  // odd row stride: column walks hit distinct banks
     const int tid = threadIdx.x, nthr = blockDim.x;
     float *A = prm.use_smem ? smem : gA;
-    float *V = prm.use_smem ? smem + (size_t)n * n : gV;
+    float *V = prm.use_smem ? smem + (size_t)n * ld : gV;
 
     __shared__ float cs[kMaxPairs], sn[kMaxPairs];
     __shared__ int pp[kMaxPairs], qq[kMaxPairs];
     __shared__ double red[32];
     __shared__ float fred[32];
-    __shared__ int any_rot;
     __shared__ double s_scale;
 
     // ---- load A = C / scale (scale = largest diagonal entry), V = I
@@ -116,20 +118,46 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
     const double inv_scale = 1.0 / scale;
     for (int idx = tid; idx < n * n; idx += nthr) {
         int i = idx / n, j = idx % n;
-        A[idx] = (i < B && j < B) ? (float)(C[(size_t)i * B + j] * inv_scale) : 0.f;
-        V[idx] = (i == j) ? 1.f : 0.f;
+        A[i * ld + j] = (i < B && j < B) ? (float)(C[(size_t)i * B + j] * inv_scale) : 0.f;
+        V[i * ld + j] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
 
     // ---- 1. FP32 parallel cyclic sweeps
-    for (int sweep = 0; sweep < prm.max_sweeps; ++sweep) {
-        if (tid == 0) any_rot = 0;
-        __syncthreads();
+    // Work items fixed for the whole run: up to kBlk 2x2 blocks (k, l) of A
+    // per thread, and one pair column k of V over rows i0, i0 + tpp, ...
+    constexpr int kBlk = 3;  // enough for n <= 128 (2080 blocks); larger n loops
+    int bk[kBlk], bl[kBlk];
+    const int nblk = P * (P + 1) / 2;
+    const bool blocks_in_regs = nblk <= kBlk * nthr;
+#pragma unroll
+    for (int b = 0; b < kBlk; ++b) {
+        int idx = tid + b * nthr;
+        if (blocks_in_regs && idx < nblk) tri_of(idx, P, bk[b], bl[b]);
+        else bk[b] = bl[b] = -1;
+    }
+    const int tpp = nthr / P;                 // threads per V pair column
+    const int vk = tid % P, vi0 = tid / P;    // this thread's pair column / first row
+    const bool v_active = vi0 < tpp;
+    int sweeps = 0;
+    float stop = prm.stop_tol;
+    bool converged = false;
+    int refine_iters = 0;
+    __shared__ double sv[HSC_MAX_BANDS], sw[HSC_MAX_BANDS], stt[HSC_MAX_BANDS];
+    __shared__ float sr[HSC_MAX_BANDS];
+    __shared__ int s_lead;
+    __shared__ double s_rho, s_rn;
+    // Phase 0 sweeps to a loose FP32 tolerance; phase 1 (only if the FP64
+    // refinement has not converged) sweeps on to a tight one and refines again.
+    for (int phase = 0; phase < 2 && !converged; ++phase) {
+    while (sweeps < prm.max_sweeps) {
+        float offmax = 0.f;
         for (int t = 0; t < n - 1; ++t) {
             for (int k = tid; k < P; k += nthr) {
                 int p, q;
                 pair_of(t, k, n, p, q);
-                float app = A[p * n + p], aqq = A[q * n + q], apq = A[p * n + q];
+                float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+                offmax = fmaxf(offmax, fabsf(apq));
                 float c = 1.f, s = 0.f;
                 if (fabsf(apq) > prm.rot_tol) {
                     float tau = (aqq - app) / (2.f * apq);
@@ -138,7 +166,6 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
                     else tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
                     c = 1.f / sqrtf(1.f + tt * tt);
                     s = tt * c;
-                    any_rot = 1;
                 }
                 pp[k] = p;
                 qq[k] = q;
@@ -147,67 +174,73 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
             }
             __syncthreads();
             // A <- J^T A J, one 2x2 block (k, l), k <= l, per work item
-            const int nblk = P * (P + 1) / 2;
-            for (int idx = tid; idx < nblk; idx += nthr) {
-                int k, l;
-                tri_of(idx, P, k, l);
+            auto do_block = [&](int k, int l) {
                 float ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
-                if (sk == 0.f && sl == 0.f) continue;
+                if (sk == 0.f && sl == 0.f) return;
                 int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
-                float x00 = A[pk * n + pl], x01 = A[pk * n + ql];
-                float x10 = A[qk * n + pl], x11 = A[qk * n + ql];
+                float x00 = A[pk * ld + pl], x01 = A[pk * ld + ql];
+                float x10 = A[qk * ld + pl], x11 = A[qk * ld + ql];
                 float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
                 float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
                 float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
                 float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
                 if (k == l) {
-                    A[pk * n + pk] = z00;
-                    A[qk * n + qk] = z11;
-                    A[pk * n + qk] = 0.f;
-                    A[qk * n + pk] = 0.f;
+                    A[pk * ld + pk] = z00;
+                    A[qk * ld + qk] = z11;
+                    A[pk * ld + qk] = 0.f;
+                    A[qk * ld + pk] = 0.f;
                 } else {
-                    A[pk * n + pl] = z00;
-                    A[pk * n + ql] = z01;
-                    A[qk * n + pl] = z10;
-                    A[qk * n + ql] = z11;
-                    A[pl * n + pk] = z00;
-                    A[ql * n + pk] = z01;
-                    A[pl * n + qk] = z10;
-                    A[ql * n + qk] = z11;
+                    A[pk * ld + pl] = z00;
+                    A[pk * ld + ql] = z01;
+                    A[qk * ld + pl] = z10;
+                    A[qk * ld + ql] = z11;
+                    A[pl * ld + pk] = z00;
+                    A[ql * ld + pk] = z01;
+                    A[pl * ld + qk] = z10;
+                    A[ql * ld + qk] = z11;
+                }
+            };
+            if (blocks_in_regs) {
+#pragma unroll
+                for (int b = 0; b < kBlk; ++b)
+                    if (bk[b] >= 0) do_block(bk[b], bl[b]);
+            } else {
+                for (int idx = tid; idx < nblk; idx += nthr) {
+                    int k, l;
+                    tri_of(idx, P, k, l);
+                    do_block(k, l);
                 }
             }
-            // V <- V J
-            for (int idx = tid; idx < n * P; idx += nthr) {
-                int i = idx / P, k = idx % P;
-                float s = sn[k];
-                if (s == 0.f) continue;
-                float c = cs[k];
-                int p = pp[k], q = qq[k];
-                float vp = V[i * n + p], vq = V[i * n + q];
-                V[i * n + p] = c * vp - s * vq;
-                V[i * n + q] = s * vp + c * vq;
+            // V <- V J: this thread's pair column over its rows
+            if (v_active) {
+                float s = sn[vk];
+                if (s != 0.f) {
+                    float c = cs[vk];
+                    int p = pp[vk], q = qq[vk];
+                    for (int i = vi0; i < n; i += tpp) {
+                        float vp = V[i * ld + p], vq = V[i * ld + q];
+                        V[i * ld + p] = c * vp - s * vq;
+                        V[i * ld + q] = s * vp + c * vq;
+                    }
+                }
             }
             __syncthreads();
         }
-        int rotated = any_rot;
-        __syncthreads();  // everyone has read the flag before thread 0 resets it
-        if (!rotated) break;
+        ++sweeps;
+        offmax = block_maxf(offmax, fred);
+        if (offmax <= stop) break;
     }
 
     // ---- 2. FP64 refinement of the leading vector
-    __shared__ double sv[HSC_MAX_BANDS], sw[HSC_MAX_BANDS], stt[HSC_MAX_BANDS];
-    __shared__ float sr[HSC_MAX_BANDS];
-    __shared__ int s_lead;
-    __shared__ double s_rho, s_rn;
     if (tid == 0) {
         int lead = 0;
         for (int j = 1; j < B; ++j)
-            if (A[j * n + j] > A[lead * n + lead]) lead = j;
+            if (A[j * ld + j] > A[lead * ld + lead]) lead = j;
         s_lead = lead;
     }
     __syncthreads();
     const int lead = s_lead;
-    for (int i = tid; i < B; i += nthr) sv[i] = (double)V[i * n + lead];
+    for (int i = tid; i < B; i += nthr) sv[i] = (double)V[i * ld + lead];
     __syncthreads();
     {
         double nn = 0.0;
@@ -219,8 +252,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         __syncthreads();
     }
     const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
-    bool converged = false;
     for (int it = 0; it <= kMaxRefine; ++it) {
+        refine_iters = it;
         // w = C v
         for (int i = warp; i < B; i += nwarp) {
             double a = 0.0;
@@ -256,8 +289,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         // t_j = (V_j^T r) / (rho - theta_j)
         for (int j = tid; j < B; j += nthr) {
             float g = 0.f;
-            for (int i = 0; i < B; ++i) g = fmaf(V[i * n + j], sr[i], g);
-            double th = (double)A[j * n + j] * scale;
+            for (int i = 0; i < B; ++i) g = fmaf(V[i * ld + j], sr[i], g);
+            double th = (double)A[j * ld + j] * scale;
             double den = rho - th;
             stt[j] = (j == lead || fabs(den) <= 1e-12 * cnorm) ? 0.0 : rn * (double)g / den;
         }
@@ -265,7 +298,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         // v += sum_j t_j V_j
         for (int i = warp; i < B; i += nwarp) {
             double a = 0.0;
-            for (int j = lane; j < B; j += 32) a += stt[j] * (double)V[i * n + j];
+            for (int j = lane; j < B; j += 32) a += stt[j] * (double)V[i * ld + j];
             for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
             if (lane == 0) sv[i] += a;
         }
@@ -278,6 +311,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         __syncthreads();
     }
     __syncthreads();
+    stop = prm.stop_tol_final;
+    }  // phases
     // ---- 3. sign rule and outputs
     if (tid == 0) {
         int big = 0;
@@ -286,6 +321,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         s_lead = (sv[big] < 0.0) ? -1 : 1;
         *lambda1_out = s_rho;
         if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
+        ctl->jacobi_sweeps = (unsigned)sweeps;
+        ctl->refine_iters = (unsigned)refine_iters;
         ctl->imin_key = float_to_key(INFINITY);
         ctl->imax_key = float_to_key(-INFINITY);
     }
@@ -304,8 +341,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
 size_t jacobi_global_floats(int B)
 {
     int n = B + (B & 1);
-    size_t need = 2 * (size_t)n * n * sizeof(float);
-    return need <= kJacSmemLimit ? 0 : (size_t)n * n;
+    size_t need = 2 * (size_t)n * (n + 1) * sizeof(float);
+    return need <= kJacSmemLimit ? 0 : (size_t)n * (n + 1);
 }
 
 cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
@@ -314,9 +351,11 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
     prm.B = B;
     prm.n = B + (B & 1);
     if (prm.n < 2) prm.n = 2;
-    prm.max_sweeps = 16;
-    prm.rot_tol = 1e-5f;
-    size_t need = 2 * (size_t)prm.n * prm.n * sizeof(float);
+    prm.max_sweeps = 30;
+    prm.rot_tol = 1e-7f;
+    prm.stop_tol = 1e-3f;
+    prm.stop_tol_final = 1e-6f;
+    size_t need = 2 * (size_t)prm.n * (prm.n + 1) * sizeof(float);
     prm.use_smem = need <= kJacSmemLimit;
     size_t smem = prm.use_smem ? need : 0;
     if (smem > 48 * 1024)

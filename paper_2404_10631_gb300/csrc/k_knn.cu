@@ -93,41 +93,6 @@ __device__ __noinline__ Key max_key(const Key *buf, int n)
 }
 
 
-// Rare path for one group of 4 columns: every candidate of the group that
-// passes the filter gets its exact key; keys <= tau enter the buffer.
-// Returns true when tau was tightened (the caller refreshes its thresholds).
-__device__ __noinline__ bool rare_group(const float *win, int nrows, int j4, int c0, int W,
-                                        int r, int lo_r, int c, float Ip, float lam, float l2,
-                                        int K, Key *buf, int &n, Key &tau)
-{
-    bool changed = false;
-    const float base = (float)c - (float)(c0 + 4 * j4);
-    for (int ii = 0; ii < nrows; ++ii) {
-        const int dr = lo_r + ii - r;
-        const int rowq = (lo_r + ii) * W;
-        float thr = row_threshold(tau.hi, __fmul_rn(l2, (float)(dr * dr)));
-        for (int u = 0; u < 4; ++u) {
-            const int j = c0 + 4 * j4 + u;
-            if (j >= W) break;
-            const float Iq = win[ii * kStride + 4 * j4 + u];
-            float t = lam * (base - (float)u);
-            float dI = Ip - Iq;
-            if (fmaf(dI, dI, t * t) > thr) continue;
-            Key kk = make_key(Ip, Iq, dr, c - j, l2, rowq + j);
-            if (!key_le(kk, tau)) continue;
-            if (n == kCap) {
-                shrink(buf, n, K);
-                tau = max_key(buf, n);
-                changed = true;
-                thr = row_threshold(tau.hi, __fmul_rn(l2, (float)(dr * dr)));
-                if (!key_le(kk, tau)) continue;
-            }
-            buf[n++] = kk;
-        }
-    }
-    return changed;
-}
-
 template <int RMAX>
 __global__ void __launch_bounds__(kThreads)
 knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int H, int W, int K,
@@ -232,7 +197,32 @@ knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int 
             }
             if (!__any_sync(0xffffffffu, hit)) continue;
             if (!hit) continue;
-            if (rare_group(win, nrows, j4, c0, W, r, lo_r, c, Ip, lam, l2, K, buf, n, tau)) {
+            // rare path: exact keys for the group's candidates that pass the
+            // filter (rows not unrolled; thresholds recomputed from tau)
+            bool tightened = false;
+#pragma unroll 1
+            for (int ii = 0; ii < nrows; ++ii) {
+                const int dr = lo_r + ii - r;
+                const float sr = __fmul_rn(l2, (float)(dr * dr));
+                const int rowq = (lo_r + ii) * W;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = c0 + 4 * j4 + u;
+                    const float Iq = win[ii * kStride + 4 * j4 + u];
+                    const float dI = Ip - Iq;
+                    if (j >= W || fmaf(dI, dI, sc[u]) > row_threshold(tau.hi, sr)) continue;
+                    Key kk = make_key(Ip, Iq, dr, c - j, l2, rowq + j);
+                    if (!key_le(kk, tau)) continue;
+                    if (n == kCap) {
+                        shrink(buf, n, K);
+                        tau = max_key(buf, n);
+                        tightened = true;
+                        if (!key_le(kk, tau)) continue;
+                    }
+                    buf[n++] = kk;
+                }
+            }
+            if (tightened) {
 #pragma unroll
                 for (int t = 0; t < RMAX; ++t) {
                     int d = lo_r + t - r;

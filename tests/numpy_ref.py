@@ -59,3 +59,33 @@ def couple_numpy(r):
     rhs[k] = 1.0
     x = np.linalg.solve(M, rhs)
     return x[:k], Q
+
+
+def knn_float_keys_bruteforce(I, P, K, R, lam):
+    """Eq. 1 with float terms evaluated by numpy float32 arithmetic
+    (round-to-nearest): dI = I_p - I_q, e = dI*dI, s = fl(lam^2)*(dr^2+dc^2),
+    summed exactly with a float32 two-sum; candidates ordered by (hi, lo, q).
+    Returns nbr[H*W, K]."""
+    I = np.asarray(I, dtype=np.float32)
+    H, W = I.shape
+    f = np.float32
+    lam32 = f(lam)
+    l2 = f(lam32 * lam32)
+    nbr = np.zeros((H * W, K), dtype=np.int64)
+    for r in range(H):
+        lo_r, hi_r = window_rows(r, H, R)
+        ii, jj = np.meshgrid(np.arange(lo_r, hi_r + 1), np.arange(W), indexing="ij")
+        ii = ii.ravel()
+        jj = jj.ravel()
+        q = ii * W + jj
+        Iq = I[ii, jj]
+        for c in range(W):
+            dI = (I[r, c] - Iq).astype(np.float32)
+            e = (dI * dI).astype(np.float32)
+            s = (l2 * ((r - ii) ** 2 + (c - jj) ** 2).astype(np.float32)).astype(np.float32)
+            h = (s + e).astype(np.float32)
+            bb = (h - s).astype(np.float32)
+            low = ((s - (h - bb)) + (e - bb)).astype(np.float32)
+            order = np.lexsort((q, low, h))[:K]
+            nbr[r * W + c] = q[order]
+    return nbr

@@ -1,15 +1,12 @@
 """Parity helpers: GPU results against the FP64 oracle with the tolerance
 masks of the method.
 
-KNN selection. The GPU compares distances exactly as s + e (s the FP32
-spatial term lambda^2 (dr^2 + dc^2), e = fl((I_p - I_q)^2) from the rounded
-difference), so on the same float inputs its order differs from the FP64
-order only when two candidates' FP64 distances are within the FP32 rounding
-of their e and s terms: |e32 - e| <= 3 * 2^-24 e and |s32 - s| <= 2^-24 s. A
-pixel is a "strong near-tie" when its oracle K-th and (K+1)-th distances are
-closer than twice that bound; everywhere else the neighbour set must be
-identical. The task's own rule (labels exact except where d_K+1 - d_K <
-1e-6 d_K+1) is checked as well.
+KNN selection is index work decided by floating point, so the GPU and the
+oracle take it in the same precision: the kernel forms the float terms of
+Eq. 1 (as the paper's float KNN does) and compares their sums exactly; the
+oracle's float-key mode does the same, and the neighbour sets must then be
+identical at every pixel. The FP64 selection is checked with the task's
+near-tie rule.
 """
 
 from __future__ import annotations
@@ -18,86 +15,45 @@ import numpy as np
 
 import oracle
 
-U = 2.0 ** -24
-
-
-def _parts(I64, W, lam, p, q):
-    r, c = divmod(int(p), W)
-    qi, qj = np.divmod(np.asarray(q, dtype=np.int64), W)
-    e = (I64.ravel()[p] - I64.ravel()[q]) ** 2
-    s = lam * lam * ((r - qi) ** 2 + (c - qj) ** 2)
-    return e, s
-
-
-def strong_tol(e, s):
-    return 8 * U * e + 4 * U * s + 1e-300
-
-
-def window_candidates(H, W, R, p):
-    r = p // W
-    lo = max(0, r - R // 2)
-    hi = min(H - 1, r + (R + 1) // 2 - 1)
-    return np.arange(lo * W, (hi + 1) * W, dtype=np.int64)
-
-
 def check_knn(I, P, K, R, lam, nbr_gpu, O_gpu, lab_gpu, pixels=None, o_tol=1e-5):
     """Compare GPU KNN outputs (full H x W arrays) with the oracle on
     ``pixels`` (contiguous ranges as (p0, p1) tuples; default: all).
+
+    * neighbour sets: identical to the oracle's selection taken in the
+      kernel's precision (float terms, exact comparison), at every pixel;
+    * O: within o_tol of the FP64 mean over that set; labels equal where the
+      top two O differ by more than 2 o_tol;
+    * the task's rule against the FP64-distance selection: labels equal
+      except where d_K+1 - d_K < 1e-6 d_K+1 (near-ties) or O nearly ties.
     Returns a dict of counts; raises AssertionError on a violation."""
     I = np.ascontiguousarray(I, dtype=np.float32)
     P = np.ascontiguousarray(P, dtype=np.float32)
     H, W = I.shape
     k = P.shape[0]
     N = H * W
-    I64 = I.astype(np.float64)
     nbr_gpu = np.asarray(nbr_gpu).reshape(N, K)
     O_gpu = np.asarray(O_gpu).reshape(k, N)
     lab_gpu = np.asarray(lab_gpu).reshape(N)
     if pixels is None:
         pixels = [(0, N)]
-    stats = dict(pixels=0, exact_sets=0, strong_near_ties=0, official_near_ties=0)
+    stats = dict(pixels=0, official_near_ties=0, fp64_set_differs=0)
     for p0, p1 in pixels:
-        out = oracle.knn(I, P, K, R, lam, p0, p1, want_nbr=True)
-        for t, p in enumerate(range(p0, p1)):
-            stats["pixels"] += 1
-            on = out["nbr"][t]
-            eK, sK = _parts(I64, W, lam, p, on[K - 1])
-            official_tie = out["dK1"][t] - out["dK"][t] < 1e-6 * out["dK1"][t]
-            stats["official_near_ties"] += int(official_tie)
-            if on[K] >= 0:
-                eK1, sK1 = _parts(I64, W, lam, p, on[K])
-                strong_tie = (out["dK1"][t] - out["dK"][t]) < 2 * (strong_tol(eK, sK) + strong_tol(eK1, sK1))
-            else:
-                strong_tie = False
-            g = np.sort(nbr_gpu[p])
-            assert np.all(g >= 0), "pixel %d: GPU returned fewer than K neighbours" % p
-            assert len(np.unique(g)) == K, "pixel %d: duplicate neighbours" % p
-            cand = window_candidates(H, W, R, p)
-            assert np.all(np.isin(g, cand)), "pixel %d: neighbour outside the window" % p
-            if strong_tie:
-                stats["strong_near_ties"] += 1
-                # the GPU set must still be a valid K-nearest set within rounding
-                e, s = _parts(I64, W, lam, p, cand)
-                d = e + s
-                tol = strong_tol(e, s)
-                sel = np.isin(cand, g)
-                if (~sel).any():
-                    worst_in = (d[sel] - tol[sel]).max()
-                    best_out = (d[~sel] + tol[~sel]).min()
-                    assert worst_in <= best_out, \
-                        "pixel %d: GPU neighbour set is not a K-nearest set" % p
-                O_ref = P.reshape(k, N)[:, g].astype(np.float64).mean(axis=1)
-                np.testing.assert_allclose(O_gpu[:, p], O_ref, atol=o_tol)
-            else:
-                assert np.array_equal(g, np.sort(on[:K])), \
-                    "pixel %d: neighbour set differs from the oracle's (gap %.3g)" % (
-                        p, out["dK1"][t] - out["dK"][t])
-                stats["exact_sets"] += 1
-                np.testing.assert_allclose(O_gpu[:, p], out["O"][:, t], atol=o_tol)
-                if out["gapO"][t] > 2 * o_tol:
-                    assert lab_gpu[p] == out["labels"][t], "pixel %d: label differs" % p
-            if not official_tie and out["gapO"][t] > 2 * o_tol:
-                assert lab_gpu[p] == out["labels"][t], "pixel %d: label differs (official rule)" % p
+        fk = oracle.knn(I, P, K, R, lam, p0, p1, want_nbr=True, float_keys=True)
+        d64 = oracle.knn(I, P, K, R, lam, p0, p1, want_nbr=True)
+        g = np.sort(nbr_gpu[p0:p1], axis=1)
+        ref = np.sort(fk["nbr"][:, :K], axis=1)
+        bad = np.nonzero(np.any(g != ref, axis=1))[0]
+        assert bad.size == 0, "pixels %s: neighbour set differs from the oracle's" % (
+            (bad[:10] + p0).tolist())
+        np.testing.assert_allclose(O_gpu[:, p0:p1], fk["O"], atol=o_tol)
+        clear = fk["gapO"] > 2 * o_tol
+        np.testing.assert_array_equal(lab_gpu[p0:p1][clear], fk["labels"][clear])
+        tie = (d64["dK1"] - d64["dK"]) < 1e-6 * d64["dK1"]
+        ok = ~tie & (d64["gapO"] > 2 * o_tol)
+        np.testing.assert_array_equal(lab_gpu[p0:p1][ok], d64["labels"][ok])
+        stats["pixels"] += p1 - p0
+        stats["official_near_ties"] += int(tie.sum())
+        stats["fp64_set_differs"] += int(np.any(np.sort(d64["nbr"][:, :K], 1) != ref, axis=1).sum())
     return stats
 
 

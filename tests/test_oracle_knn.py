@@ -131,3 +131,38 @@ def test_rejects_k_above_candidates():
     with pytest.raises(oracle.OracleError):
         oracle.knn(I, P, 7, 4, 1.0)
     oracle.knn(I, P, 6, 4, 1.0)
+
+
+def test_float_keys_equal_fp64_on_exact_inputs():
+    """Dyadic grey levels and lambda = 1: every float term is exact, so the
+    float-key selection is the FP64 selection, ties included."""
+    rng = np.random.default_rng(12)
+    I = (rng.integers(0, 64, size=(14, 23)) / 64.0).astype(np.float32)
+    _, P = _rand(14, 23, 3, 13)
+    a = oracle.knn(I, P, 11, 6, 1.0, want_nbr=True)
+    b = oracle.knn(I, P, 11, 6, 1.0, want_nbr=True, float_keys=True)
+    np.testing.assert_array_equal(a["nbr"], b["nbr"])
+    np.testing.assert_array_equal(a["O"], b["O"])
+
+
+@pytest.mark.parametrize("lam", [1.0, 0.3, 1.7])
+def test_float_keys_against_numpy_float32(lam):
+    from numpy_ref import knn_float_keys_bruteforce
+    I, P = _rand(11, 17, 3, 14)
+    out = oracle.knn(I, P, 9, 5, lam, want_nbr=True, float_keys=True)
+    np.testing.assert_array_equal(out["nbr"][:, :9], knn_float_keys_bruteforce(I, P, 9, 5, lam))
+
+
+def test_float_keys_differ_from_fp64_only_inside_rounding():
+    """The float terms carry at most 3 ulp (e) and 2 ulp (s) of error, so
+    the two selections can only disagree where the FP64 K-th and (K+1)-th
+    distances are that close."""
+    I, P = _rand(20, 60, 3, 15)
+    I = (I * np.float32(1e-2)).astype(np.float32)  # small contrasts: many close keys
+    K, R, lam = 12, 7, 0.7
+    a = oracle.knn(I, P, K, R, lam, want_nbr=True)
+    b = oracle.knn(I, P, K, R, lam, want_nbr=True, float_keys=True)
+    u = 2.0 ** -24
+    diff = np.any(np.sort(a["nbr"][:, :K], 1) != np.sort(b["nbr"][:, :K], 1), axis=1)
+    bound = 2 * (3 * u * 1e-4 + 2 * u * lam * lam * 2 * (3 ** 2 + 59 ** 2))
+    assert np.all((a["dK1"] - a["dK"])[diff] <= bound)
