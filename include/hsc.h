@@ -193,6 +193,32 @@ hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_it
  * launches per stage; dropped (nullable): records lost to the cap. */
 hsc_status hsc_profile_read(hsc_ctx *ctx, double *ms, int64_t *kernels, int64_t *dropped);
 
+/* ---- one-band PCA without any allocation (the paper has no counterpart:
+ * this is an integration aid). For callers that cannot allocate GPU memory
+ * while they run -- a host that has already sized or captured all of its
+ * device memory, a real-time loop where cudaMalloc could stall on the device,
+ * a plugin that does not own the allocator. Same computation and outputs as
+ * hsc_pca_one_band, but no context: the scratch lives in one fixed
+ * __device__ array inside libhsc.so (about 4.3 MB, held on every GPU that
+ * loads the library until the process exits), sized for at most
+ * HSC_NOALLOC_MAX_BANDS bands (any H, W with H*W < 2^31).
+ *   cuda_stream  cudaStream_t to launch on (NULL = the legacy default stream)
+ *   other arguments as hsc_pca_one_band (device pointers, caller-owned).
+ * Returns HSC_ERR_UNSUPPORTED when B > HSC_NOALLOC_MAX_BANDS, HSC_ERR_INVALID_ARG
+ * for bad arguments, HSC_ERR_CUDA when a launch fails. Calls no cudaMalloc,
+ * cudaFree or allocating library routine. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture. Every call
+ * shares the one array and each call clears the part that must start at
+ * zero, so calls whose GPU work overlaps (two streams, two host threads)
+ * race and give undefined results; order them on one stream. Device-side
+ * conditions (NaN input, eigenvector not converged) are not reported by this
+ * entry point: the outputs are then unspecified. */
+#define HSC_NOALLOC_MAX_BANDS 128
+hsc_status hsc_pca_one_band_noalloc(void *cuda_stream, const float *cube, int B, int H, int W,
+                                    unsigned flags, float *one_band, double *eigvec,
+                                    double *eigval);
+
 #ifdef __cplusplus
 }
 #endif

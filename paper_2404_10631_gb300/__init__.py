@@ -35,7 +35,9 @@ HSC_SVM_COUPLE_F64 = 2
 EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_error",
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
             "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
-            "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics")
+            "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics",
+            "hsc_pca_one_band_noalloc")
+HSC_NOALLOC_MAX_BANDS = 128
 STAGES = ("moments", "jacobi", "project_svm", "normalize", "knn")
 
 
@@ -93,6 +95,7 @@ def lib():
                                      vp, vp, vp]
         L.hsc_classify.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
                                    ctypes.POINTER(hsc_knn_params), ctypes.c_uint, vp, vp, vp, vp]
+        L.hsc_pca_one_band_noalloc.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_profile_enable.argtypes = [vp, i32]
         L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]
@@ -225,6 +228,25 @@ def hsc_pca_one_band(ctx: Context, cube, flags: int = HSC_PCA_MINMAX, one_band=N
         one_band = torch.empty((H, W), dtype=torch.float32, device=cube.device)
     ctx.check(lib().hsc_pca_one_band(ctx.handle, _ptr(cube), B, H, W, flags, _ptr(one_band),
                                      _ptr(eigvec), _ptr(eigval)))
+    return one_band
+
+
+def hsc_pca_one_band_noalloc(cube, flags: int = HSC_PCA_MINMAX, one_band=None, eigvec=None,
+                             eigval=None, stream=None):
+    """The allocation-free one-band PCA on ``stream`` (torch stream or handle;
+    None = torch's current stream). All outputs must be passed in by callers
+    that cannot allocate; those left as None are allocated here by torch for
+    convenience. Raises HscError on a non-OK status."""
+    import torch
+    B, H, W = cube.shape
+    if one_band is None:
+        one_band = torch.empty((H, W), dtype=torch.float32, device=cube.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(cube.device)
+    st = lib().hsc_pca_one_band_noalloc(_stream_handle(stream), _ptr(cube), B, H, W, flags,
+                                        _ptr(one_band), _ptr(eigvec), _ptr(eigval))
+    if st != HSC_OK:
+        raise HscError(st, "hsc_pca_one_band_noalloc")
     return one_band
 
 

@@ -1,0 +1,64 @@
+"""hsc_pca_one_band_noalloc: the one-band PCA for callers that cannot
+allocate GPU memory while running. Checked through the C ABI against
+hsc_pca_one_band on the same cube, on two calls in a row (the second call
+reuses the fixed scratch the first one left behind), within the PCA
+tolerances of the other GPU tests. Collected last on purpose."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+V1_ANGLE = 1e-5
+I_TOL = 2e-5
+
+
+def test_noalloc_pca_matches_the_context_entry_point(hsc, ctx):
+    import torch
+    L = hsc.lib()
+    f = synth.make_config(2)  # 416 x 512 x 128: the largest band count it takes
+    B, H, W = f.cube.shape
+    cube = torch.as_tensor(f.cube, device="cuda")
+    ref_v = torch.zeros(B, dtype=torch.float64, device="cuda")
+    ref_l = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ref_I = hsc.hsc_pca_one_band(ctx, cube, eigvec=ref_v, eigval=ref_l)
+    ctx.sync()
+    stream = torch.cuda.Stream()
+    outs = []
+    for call in range(2):
+        I = torch.full((H, W), -7.0, dtype=torch.float32, device="cuda")
+        v = torch.zeros(B, dtype=torch.float64, device="cuda")
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        st = L.hsc_pca_one_band_noalloc(ctypes.c_void_p(stream.cuda_stream), cube.data_ptr(), B, H, W,
+                                        hsc.HSC_PCA_MINMAX, I.data_ptr(), v.data_ptr(), lam.data_ptr())
+        assert st == hsc.HSC_OK
+        stream.synchronize()
+        if call == 1:  # after the first call's one-time set-up nothing is allocated
+            assert torch.cuda.mem_get_info()[0] >= free_before - (1 << 20)
+        outs.append((I.cpu().numpy(), v.cpu().numpy(), float(lam.cpu()[0])))
+    rI, rv, rl = ref_I.cpu().numpy(), ref_v.cpu().numpy(), float(ref_l.cpu()[0])
+    for I, v, lam in outs:
+        cos = float(v @ rv)
+        assert cos > 0 and np.sqrt(max(0.0, 1 - cos * cos)) < V1_ANGLE
+        assert lam == pytest.approx(rl, rel=1e-5)
+        assert np.abs(I - rI).max() < I_TOL
+    # the two calls in a row give the same answer
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(hsc):
+    import torch
+    L = hsc.lib()
+    B = hsc.HSC_NOALLOC_MAX_BANDS + 1
+    cube = torch.zeros((B, 4, 4), dtype=torch.float32, device="cuda")
+    I = torch.empty((4, 4), dtype=torch.float32, device="cuda")
+    st = L.hsc_pca_one_band_noalloc(None, cube.data_ptr(), B, 4, 4, 1, I.data_ptr(), None, None)
+    assert st == hsc.HSC_ERR_UNSUPPORTED
+    st = L.hsc_pca_one_band_noalloc(None, None, 8, 4, 4, 1, I.data_ptr(), None, None)
+    assert st == hsc.HSC_ERR_INVALID_ARG
