@@ -90,6 +90,8 @@ typedef struct {
 
 /* flags for hsc_pca_one_band */
 #define HSC_PCA_MINMAX 1u        /* write (I - min)/(max - min) in [0,1] (what the KNN uses) */
+/* flags for hsc_pca_covariance */
+#define HSC_COV_FP32_PIPE 4u     /* compute the Gram on the FP32 pipe instead of the tensor cores */
 /* flags for hsc_svm_probs / hsc_classify */
 #define HSC_SVM_COUPLE_F64 2u    /* solve the per-pixel coupling system in FP64 */
 
@@ -128,6 +130,19 @@ size_t hsc_scratch_bytes(const hsc_ctx *ctx);
 hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                             unsigned flags, float *one_band, double *eigvec,
                             double *eigval);
+
+/* Steps (i) and (ii) of the PCA alone (Section II.C.2, III.A.2.a-b): band
+ * means and the covariance of the centred cube divided by the pixel count.
+ *   cube  B x H x W float32 (device)
+ *   mean  B float64 (device, required)
+ *   cov   B x B float64 row-major, symmetric (device, required)
+ *   flags 0 or HSC_COV_FP32_PIPE. The Gram runs on the tensor cores (FP16
+ *         hi/lo split of the shifted pixels, FP32 accumulation) when B <= 128,
+ *         H*W is a multiple of 4 and cube is 16-byte aligned; otherwise, or
+ *         with HSC_COV_FP32_PIPE, on the FP32 pipe. Both sum per-CTA partials
+ *         in FP64. */
+hsc_status hsc_pca_covariance(hsc_ctx *ctx, const float *cube, int B, int H, int W,
+                              unsigned flags, double *mean, double *cov);
 
 /* Pixel-wise SVM probabilities, Section II.C.1 and III.A.1: decision values,
  * Platt binary probabilities, and the pairwise coupling of Wu, Lin and Weng

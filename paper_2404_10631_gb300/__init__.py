@@ -36,7 +36,8 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
             "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
             "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics",
-            "hsc_pca_one_band_noalloc")
+            "hsc_pca_one_band_noalloc", "hsc_pca_covariance")
+HSC_COV_FP32_PIPE = 4
 HSC_NOALLOC_MAX_BANDS = 128
 STAGES = ("moments", "jacobi", "project_svm", "normalize", "knn")
 
@@ -95,6 +96,7 @@ def lib():
                                      vp, vp, vp]
         L.hsc_classify.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
                                    ctypes.POINTER(hsc_knn_params), ctypes.c_uint, vp, vp, vp, vp]
+        L.hsc_pca_covariance.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp]
         L.hsc_pca_one_band_noalloc.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_profile_enable.argtypes = [vp, i32]
         L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
@@ -229,6 +231,19 @@ def hsc_pca_one_band(ctx: Context, cube, flags: int = HSC_PCA_MINMAX, one_band=N
     ctx.check(lib().hsc_pca_one_band(ctx.handle, _ptr(cube), B, H, W, flags, _ptr(one_band),
                                      _ptr(eigvec), _ptr(eigval)))
     return one_band
+
+
+def hsc_pca_covariance(ctx: Context, cube, flags: int = 0, mean=None, cov=None):
+    """Band means (B, f64) and covariance (B x B, f64) of the cube."""
+    import torch
+    B, H, W = cube.shape
+    if mean is None:
+        mean = torch.empty(B, dtype=torch.float64, device=cube.device)
+    if cov is None:
+        cov = torch.empty((B, B), dtype=torch.float64, device=cube.device)
+    ctx.check(lib().hsc_pca_covariance(ctx.handle, _ptr(cube), B, H, W, flags, _ptr(mean),
+                                       _ptr(cov)))
+    return mean, cov
 
 
 def hsc_pca_one_band_noalloc(cube, flags: int = HSC_PCA_MINMAX, one_band=None, eigvec=None,

@@ -404,6 +404,8 @@ hsc_status hsc_sync(hsc_ctx *ctx)
     if (bits & hsc::ST_NOT_CONVERGED)
         return fail(ctx, HSC_ERR_NOT_CONVERGED,
                     "the leading eigenvector did not converge (degenerate or tiny eigengap)%s");
+    if (bits & hsc::ST_TIMEOUT)
+        return fail(ctx, HSC_ERR_TIMEOUT, "a bounded wait inside a kernel ran out%s");
     if (bits & hsc::ST_KNN_SHORT)
         return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: a pixel found fewer than K candidates%s");
     return HSC_OK;
@@ -454,6 +456,32 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     if (e == cudaSuccess && eigval)
         e = cudaMemcpyAsync(eigval, s.lambda1, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_pca_one_band launch");
+    return HSC_OK;
+}
+
+hsc_status hsc_pca_covariance(hsc_ctx *ctx, const float *cube, int B, int H, int W,
+                              unsigned flags, double *mean, double *cov)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if ((st = check_cube(ctx, cube, B, H, W))) return st;
+    if (!mean || !cov) return fail(ctx, HSC_ERR_INVALID_ARG, "mean and cov are required%s");
+    if (flags & ~(unsigned)HSC_COV_FP32_PIPE) return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
+    const long N = (long)H * W;
+    Layout L = make_layout(ctx, B, N, 0, true, false, false);
+    if ((st = ensure_scratch(ctx, L.total))) return st;
+    PcaScratch s = carve(ctx, L);
+    cudaError_t e;
+    {
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream,
+                                (flags & HSC_COV_FP32_PIPE) != 0);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mean, s.mu, sizeof(double) * B, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cov, s.C, sizeof(double) * B * B, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_pca_covariance launch");
     return HSC_OK;
 }
 

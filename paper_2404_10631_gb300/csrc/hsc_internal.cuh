@@ -15,6 +15,7 @@ enum : unsigned {
     ST_NOT_CONVERGED = 2u,    // eigenvector refinement did not converge
     ST_KNN_SHORT = 4u,        // a pixel found fewer than K candidates (must not happen)
     ST_NONFINITE_MAP = 8u,    // NaN/Inf in one_band given to the KNN
+    ST_TIMEOUT = 16u,         // a bounded wait inside a kernel ran out
 };
 
 // Small control block at the start of the scratch.
@@ -66,9 +67,14 @@ struct PcaScratch {
 // ---- launchers (each returns cudaGetLastError() of its launches) ----
 
 // Pass 1 over the cube: pilot shift, partial Gram + sums, FP64 reduction into
-// C (covariance / N) and mu. Sets ST_NONFINITE_CUBE on NaN/Inf.
+// C (covariance / N) and mu. Sets ST_NONFINITE_CUBE on NaN/Inf. The Gram runs
+// on the tensor cores (k_gram_tc.cu) when gram_tc_supported(), unless
+// force_simt; otherwise on the FP32 pipe.
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s,
-                           int sm_count, cudaStream_t st);
+                           int sm_count, cudaStream_t st, bool force_simt = false);
+bool gram_tc_supported(const float *cube, int B, long N);
+cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s,
+                           cudaStream_t st);
 
 // Jacobi eigen-decomposition of C, FP64 refinement of the leading vector,
 // sign rule; writes v1, lambda1, v1f, muf and resets the I min/max keys.

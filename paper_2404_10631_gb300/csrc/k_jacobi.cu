@@ -7,7 +7,9 @@
 //     once per sweep). Each rotation is the symmetric Schur rotation that
 //     zeroes a_pq (the same rotation the paper's classical Jacobi applies to
 //     its pivot); the update A <- J^T A J is done per 2x2 block of pairs so a
-//     round is one pass over A and V. A and V live in shared memory.
+//     round is one pass over A (upper triangle) and V, both in shared memory.
+//     The sweeps stop once every off-diagonal entry met in a sweep is below
+//     half the largest diagonal entry (two sweeps on the synthetic cubes).
 //  2. FP64 refinement of the leading vector against the FP64 covariance:
 //     with (theta_j, V_j) the FP32 eigenpairs and v the current leading
 //     vector, r = C v - rho v (rho = v^T C v) and
@@ -16,7 +18,8 @@
 //     other pair, taken in FP64 where it matters (C v and the residual).
 //     Repeated until ||r|| <= 1e-13 ||C||, so v1 carries FP64 accuracy while
 //     the O(B^3) sweeps run on the FP32 pipe (GB300's FP64 rate is a small
-//     fraction of its FP32 rate).
+//     fraction of its FP32 rate). If the refinement has not converged after
+//     40 steps (a small eigengap), the sweeps resume to 1e-2 and it restarts.
 //  3. Sign rule: the largest-magnitude component of v1 is made positive.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -28,7 +31,7 @@ namespace {
 
 constexpr int kJacThreads = 1024;
 constexpr int kMaxPairs = 512;           // Bp <= 1024
-constexpr int kMaxRefine = 24;
+constexpr int kMaxRefine = 40;
 constexpr size_t kJacSmemLimit = 190 * 1024;  // + ~33 KB static shared
 
 struct JacParams {
@@ -40,6 +43,10 @@ struct JacParams {
     int use_smem;
 };
 
+// Round-robin ("circle") pairing: in round t (0 <= t < n-1) pair k joins
+// (t+k) and (t-k) modulo n-1, and pair 0 joins t with n-1; every pair of
+// indices meets exactly once per sweep. t + k and t - k + n - 1 stay below
+// 2(n-1), so one conditional subtraction replaces the modulo.
 __device__ __forceinline__ void pair_of(int t, int k, int n, int &p, int &q)
 {
     int a, b;
@@ -47,12 +54,17 @@ __device__ __forceinline__ void pair_of(int t, int k, int n, int &p, int &q)
         a = t;
         b = n - 1;
     } else {
-        a = (t + k) % (n - 1);
-        b = (t - k + n - 1) % (n - 1);
+        a = t + k;
+        if (a >= n - 1) a -= n - 1;
+        b = t - k + n - 1;
+        if (b >= n - 1) b -= n - 1;
     }
     p = a < b ? a : b;
     q = a < b ? b : a;
 }
+
+// A is kept as its upper triangle (i <= j) in a row-major n x ld array.
+__device__ __forceinline__ int up(int i, int j, int ld) { return i < j ? i * ld + j : j * ld + i; }
 
 // block index idx in [0, P(P+1)/2) -> (k, l), k <= l, row-major upper triangle
 __device__ __forceinline__ void tri_of(int idx, int P, int &k, int &l)
@@ -156,15 +168,17 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
             for (int k = tid; k < P; k += nthr) {
                 int p, q;
                 pair_of(t, k, n, p, q);
-                float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[p * ld + q];
+                float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[up(p, q, ld)];
                 offmax = fmaxf(offmax, fabsf(apq));
                 float c = 1.f, s = 0.f;
                 if (fabsf(apq) > prm.rot_tol) {
-                    float tau = (aqq - app) / (2.f * apq);
+                    // symmetric Schur rotation; FP32 intrinsics are enough here
+                    // because the leading vector is refined in FP64 afterwards
+                    float tau = __fdividef(aqq - app, 2.f * apq);
                     float tt;
-                    if (fabsf(tau) > 1e18f) tt = 0.5f / tau;
-                    else tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-                    c = 1.f / sqrtf(1.f + tt * tt);
+                    if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
+                    else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
+                    c = rsqrtf(fmaf(tt, tt, 1.f));
                     s = tt * c;
                 }
                 pp[k] = p;
@@ -178,26 +192,23 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
                 float ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
                 if (sk == 0.f && sl == 0.f) return;
                 int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
-                float x00 = A[pk * ld + pl], x01 = A[pk * ld + ql];
-                float x10 = A[qk * ld + pl], x11 = A[qk * ld + ql];
+                const int i00 = up(pk, pl, ld), i01 = up(pk, ql, ld);
+                const int i10 = up(qk, pl, ld), i11 = up(qk, ql, ld);
+                float x00 = A[i00], x01 = A[i01];
+                float x10 = A[i10], x11 = A[i11];
                 float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
                 float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
                 float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
                 float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
                 if (k == l) {
-                    A[pk * ld + pk] = z00;
-                    A[qk * ld + qk] = z11;
-                    A[pk * ld + qk] = 0.f;
-                    A[qk * ld + pk] = 0.f;
+                    A[i00] = z00;   // (pk, pk)
+                    A[i11] = z11;   // (qk, qk)
+                    A[i01] = 0.f;   // (pk, qk), zeroed by the rotation
                 } else {
-                    A[pk * ld + pl] = z00;
-                    A[pk * ld + ql] = z01;
-                    A[qk * ld + pl] = z10;
-                    A[qk * ld + ql] = z11;
-                    A[pl * ld + pk] = z00;
-                    A[ql * ld + pk] = z01;
-                    A[pl * ld + qk] = z10;
-                    A[ql * ld + qk] = z11;
+                    A[i00] = z00;
+                    A[i01] = z01;
+                    A[i10] = z10;
+                    A[i11] = z11;
                 }
             };
             if (blocks_in_regs) {
@@ -353,8 +364,8 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
     if (prm.n < 2) prm.n = 2;
     prm.max_sweeps = 30;
     prm.rot_tol = 1e-7f;
-    prm.stop_tol = 1e-3f;
-    prm.stop_tol_final = 1e-6f;
+    prm.stop_tol = 0.5f;
+    prm.stop_tol_final = 1e-2f;
     size_t need = 2 * (size_t)prm.n * (prm.n + 1) * sizeof(float);
     prm.use_smem = need <= kJacSmemLimit;
     size_t smem = prm.use_smem ? need : 0;

@@ -182,7 +182,7 @@ knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int 
                 float t = lam * (base - (float)u);
                 sc[u] = t * t;
             }
-            bool hit = false;
+            unsigned hits = 0u;  // bit ii: some candidate of row ii passes the filter
 #pragma unroll
             for (int ii = 0; ii < RMAX; ++ii) {
                 if (ii < nrows) {
@@ -192,16 +192,19 @@ knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int 
                     d1 = fmaf(d1, d1, sc[1]);
                     d2 = fmaf(d2, d2, sc[2]);
                     d3 = fmaf(d3, d3, sc[3]);
-                    hit |= (d0 <= tr[ii]) | (d1 <= tr[ii]) | (d2 <= tr[ii]) | (d3 <= tr[ii]);
+                    const float m = fminf(fminf(d0, d1), fminf(d2, d3));
+                    hits |= (m <= tr[ii]) ? (1u << ii) : 0u;
                 }
             }
-            if (!__any_sync(0xffffffffu, hit)) continue;
-            if (!hit) continue;
+            if (!__any_sync(0xffffffffu, hits != 0u)) continue;
+            if (hits == 0u) continue;
             // rare path: exact keys for the group's candidates that pass the
             // filter (rows not unrolled; thresholds recomputed from tau)
             bool tightened = false;
 #pragma unroll 1
-            for (int ii = 0; ii < nrows; ++ii) {
+            while (hits) {
+                const int ii = __ffs(hits) - 1;
+                hits &= hits - 1u;
                 const int dr = lo_r + ii - r;
                 const float sr = __fmul_rn(l2, (float)(dr * dr));
                 const int rowq = (lo_r + ii) * W;

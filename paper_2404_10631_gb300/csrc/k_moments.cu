@@ -157,13 +157,26 @@ __global__ void gram_reduce_kernel(int B, long N, int n_part, const float *__res
 
 }  // namespace
 
+// Partial-Gram partitions: one CTA per SM for the tensor-core Gram (it holds
+// 160 KB of shared memory), two for the FP32 one; the scratch is sized for
+// the larger count.
 int moments_partitions(int sm_count) { return 2 * sm_count; }
 
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s, int sm_count,
-                           cudaStream_t st)
+                           cudaStream_t st, bool force_simt)
 {
-    (void)sm_count;
     pilot_shift_kernel<<<B, 256, 0, st>>>(cube, B, N, s.shift, s.ctl);
+    if (!force_simt && gram_tc_supported(cube, B, N)) {
+        PcaScratch t = s;
+        t.n_part = s.n_part < sm_count ? s.n_part : sm_count;  // one CTA per SM
+        cudaError_t e = launch_gram_tc(cube, B, N, t, st);
+        if (e != cudaSuccess) return e;
+        band_mean_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, N, t.n_part, s.shift, s.sum_part, s.v1,
+                                                          s.mu);
+        dim3 rg((B + 127) / 128, B);
+        gram_reduce_kernel<<<rg, 128, 0, st>>>(B, N, t.n_part, s.gram_part, s.v1, s.C);
+        return cudaGetLastError();
+    }
     const int Bp = (B + kTile - 1) / kTile * kTile;
     const int nt = Bp / kTile;
     const int groups = (nt * nt + kGramThreads - 1) / kGramThreads;
