@@ -3,7 +3,11 @@
 
 One step = one hsc_classify call (PCA one-band, SVM probabilities, KNN
 filter, labels) on a 416 x 512 x 128 float32 neurosurgery-scale frame,
-K = 40, 14-row window, lambda = 1. Prints one JSON line.
+K = 40, 14-row window, lambda = 1, with the library's default (pruned, exact)
+KNN search. The full-window KNN (every window candidate, the paper's
+procedure; same neighbour sets) is timed on the same maps afterwards and
+reported with its FP32-pipe roofline under "knn_full_window". Prints one
+JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -119,12 +123,16 @@ def knn_pairs(H, W, R):
     return rows * W * W
 
 
-def stage_work(f):
+def stage_work(f, knn_pairs_per_launch=None):
     """Algorithmic work per launch of each stage (bytes for HBM-bound stages,
-    FP32 ops for the KNN) and its bound."""
+    FP32 ops for the KNN) and its bound. The KNN counts 4 FP32 ops per
+    (pixel, candidate) pair it evaluates: the whole window for the full scan,
+    the measured count for the pruned walk."""
     B, H, W = f.cube.shape
     N = H * W
     k = f.model.n_classes
+    if knn_pairs_per_launch is None:
+        knn_pairs_per_launch = knn_pairs(H, W, f.window_rows)
     return {
         # one read of the cube (the partial Gram outputs are a few MB)
         "moments": ("hbm", 4.0 * B * N),
@@ -132,8 +140,8 @@ def stage_work(f):
         "project_svm": ("hbm", 4.0 * B * N + 4.0 * N + 4.0 * k * N),
         # I read + written
         "normalize": ("hbm", 8.0 * N),
-        # 4 FP32-pipe ops per (pixel, window candidate) pair
-        "knn": ("alu", 4.0 * knn_pairs(H, W, f.window_rows)),
+        # 4 FP32-pipe ops per (pixel, candidate) pair evaluated
+        "knn": ("alu", 4.0 * knn_pairs_per_launch),
         "jacobi": ("latency", None),
     }
 
@@ -303,7 +311,19 @@ def run_ours(args, f):
     ctx.sync()
     stage_ms, stage_kernels, dropped = ctx.profile_read()
     ctx.profile(False)
-    sweeps, refine_iters = ctx.pca_diagnostics()
+    sweeps, refine_iters, sweep_cyc, refine_cyc = ctx.pca_diagnostics(cycles=True)
+    knn_evals = ctx.knn_candidates_evaluated()  # pruned walk, warm-up + timed steps
+    knn_evals_per_launch = knn_evals / float(args.warmup + args.steps)
+
+    # ---- the paper's full-window KNN on the same maps (timed on its own)
+    ctx.profile(True)
+    ctx.profile_read()
+    for i in range(args.steps):
+        hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam, out_probs=O, labels=lab,
+                           search=hsc.HSC_KNN_SEARCH_FULL)
+    full_ms, _, _ = ctx.profile_read()
+    ctx.profile(False)
+    full_ms_launch = full_ms["knn"] / args.steps
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     elapsed = ev[0].elapsed_time(ev[args.steps])
     t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
@@ -344,7 +364,7 @@ def run_ours(args, f):
     # ---- roofline of the dominant stage
     peaks, peak_src = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    work = stage_work(f)
+    work = stage_work(f, knn_evals_per_launch)
     stages = {}
     for name, ms in stage_ms.items():
         launches = max(1, args.steps)
@@ -373,6 +393,20 @@ def run_ours(args, f):
                                 else "hbm_gbs, %s" % peak_src),
                 "work_per_launch": d["algorithmic"]}
 
+    fp32_peak = fp32_pipe_peak_tops(sm_count, peaks.get("sm_max_mhz", 2070.0))
+    full_ops = 4.0 * knn_pairs(H, W, f.window_rows)
+    full_ach = full_ops / (full_ms_launch / 1e3) / 1e12
+    knn_full = {"search": "full window (the paper's procedure: every window candidate)",
+                "bound": "alu", "ms_per_launch": full_ms_launch, "achieved": full_ach,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": full_ach / fp32_peak,
+                "work_per_launch": full_ops,
+                "traffic": traffic_from_profiles("knn"),
+                "note": "same neighbour sets as the pruned walk used in the step"}
+    knn_pruned = {"search": "pruned walk (exact)", "candidates_per_launch": knn_evals_per_launch,
+                  "window_pairs_per_launch": knn_pairs(H, W, f.window_rows),
+                  "ms_per_launch": stages["knn"]["ms_per_launch"],
+                  "frac_on_evaluated_pairs": stages["knn"].get("frac")}
+
     lat = sorted(per_step)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps,
@@ -383,10 +417,13 @@ def run_ours(args, f):
                                                                      int(0.99 * len(lat)))]},
             "roofline": roofline,
             "stages": stages,
+            "knn_full_window": knn_full,
+            "knn_pruned": knn_pruned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": n_e2e},
             "gpu_launches": int(sum(stage_kernels.values())),
-            "jacobi": {"fp32_sweeps": sweeps, "fp64_refine_iters": refine_iters},
+            "jacobi": {"fp32_sweeps": sweeps, "fp64_refine_iters": refine_iters,
+                       "sweep_cycles": sweep_cyc, "refine_cycles": refine_cyc},
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = np.linspace(0, H - 1, 16).astype(int)

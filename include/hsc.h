@@ -74,6 +74,12 @@ typedef struct {
  *               row r, truncated at the image edges, all columns (the paper
  *               uses 14); the pixel itself is a candidate
  *   lambda      >= 0: d = (I_p - I_q)^2 + lambda^2 ((r-i)^2 + (c-j)^2)
+ *   search      how the K nearest are found; both give the same neighbour sets:
+ *               HSC_KNN_SEARCH_FULL evaluates every window candidate (the
+ *               paper's procedure); HSC_KNN_SEARCH_PRUNED walks only the
+ *               candidates whose spatial term alone does not exceed a proven
+ *               bound on the K-th distance (needs lambda > 0);
+ *               HSC_KNN_SEARCH_AUTO (0) = PRUNED when lambda > 0, else FULL.
  * Distance ties are broken by the smaller linear index; K must not exceed the
  * smallest window, min(ceil(R/2), H) * W, or the call returns
  * HSC_ERR_INVALID_ARG. */
@@ -81,7 +87,12 @@ typedef struct {
     int32_t k;
     int32_t window_rows;
     float lambda;
+    int32_t search;
 } hsc_knn_params;
+
+#define HSC_KNN_SEARCH_AUTO 0
+#define HSC_KNN_SEARCH_FULL 1
+#define HSC_KNN_SEARCH_PRUNED 2
 
 #define HSC_MAX_CLASSES 8
 #define HSC_MAX_K 64
@@ -202,8 +213,13 @@ enum {
 
 hsc_status hsc_profile_enable(hsc_ctx *ctx, int enable);
 /* Diagnostics of the context's last PCA (waits for the stream): FP32 Jacobi
- * sweeps run and FP64 refinement iterations of the leading eigenvector. */
-hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_iters);
+ * sweeps run, FP64 refinement iterations of the leading eigenvector, and the
+ * SM clock cycles spent in each part (cycle pointers nullable). */
+hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_iters,
+                               int64_t *sweep_cycles, int64_t *refine_cycles);
+/* Diagnostics of the pruned KNN search (waits for the stream): candidates
+ * whose distance it computed since the previous call (then reset to 0). */
+hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated);
 /* ms[HSC_N_STAGES]: summed milliseconds; kernels[HSC_N_STAGES]: kernel
  * launches per stage; dropped (nullable): records lost to the cap. */
 hsc_status hsc_profile_read(hsc_ctx *ctx, double *ms, int64_t *kernels, int64_t *dropped);

@@ -36,7 +36,7 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
             "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
             "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics",
-            "hsc_pca_one_band_noalloc", "hsc_pca_covariance")
+            "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics")
 HSC_COV_FP32_PIPE = 4
 HSC_NOALLOC_MAX_BANDS = 128
 STAGES = ("moments", "jacobi", "project_svm", "normalize", "knn")
@@ -50,7 +50,12 @@ class hsc_svm_model(ctypes.Structure):
 
 class hsc_knn_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("window_rows", ctypes.c_int32),
-                ("lambda_", ctypes.c_float)]
+                ("lambda_", ctypes.c_float), ("search", ctypes.c_int32)]
+
+
+HSC_KNN_SEARCH_AUTO = 0
+HSC_KNN_SEARCH_FULL = 1
+HSC_KNN_SEARCH_PRUNED = 2
 
 
 class HscError(RuntimeError):
@@ -96,11 +101,14 @@ def lib():
                                      vp, vp, vp]
         L.hsc_classify.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
                                    ctypes.POINTER(hsc_knn_params), ctypes.c_uint, vp, vp, vp, vp]
+        L.hsc_knn_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.hsc_pca_covariance.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp]
         L.hsc_pca_one_band_noalloc.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_profile_enable.argtypes = [vp, i32]
         L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
-                                          ctypes.POINTER(ctypes.c_int32)]
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]
         L.hsc_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         for name in EXPORTED:
@@ -210,11 +218,22 @@ class Context:
         return ({STAGES[i]: float(ms[i]) for i in range(n)},
                 {STAGES[i]: int(kern[i]) for i in range(n)}, int(dropped.value))
 
-    def pca_diagnostics(self):
-        """(FP32 Jacobi sweeps, FP64 refinement iterations) of the last PCA."""
+    def pca_diagnostics(self, cycles: bool = False):
+        """(FP32 Jacobi sweeps, FP64 refinement iterations) of the last PCA,
+        plus (sweep cycles, refinement cycles) when ``cycles``."""
         a, b = ctypes.c_int32(0), ctypes.c_int32(0)
-        self.check(lib().hsc_pca_diagnostics(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        c, d = ctypes.c_int64(0), ctypes.c_int64(0)
+        self.check(lib().hsc_pca_diagnostics(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.byref(c), ctypes.byref(d)))
+        if cycles:
+            return int(a.value), int(b.value), int(c.value), int(d.value)
         return int(a.value), int(b.value)
+
+    def knn_candidates_evaluated(self) -> int:
+        """Candidates the pruned KNN search evaluated since the last call."""
+        v = ctypes.c_int64(0)
+        self.check(lib().hsc_knn_diagnostics(self.handle, ctypes.byref(v)))
+        return int(v.value)
 
     @property
     def scratch_bytes(self) -> int:
@@ -278,12 +297,12 @@ def hsc_svm_probs(ctx: Context, cube, model: Model, flags: int = 0, probs=None,
 
 
 def hsc_knn_filter(ctx: Context, one_band, probs, K: int, window_rows: int, lam: float,
-                   out_probs=None, labels=None, nbr_idx=None):
+                   out_probs=None, labels=None, nbr_idx=None, search: int = HSC_KNN_SEARCH_AUTO):
     import torch
     k, H, W = probs.shape
     if labels is None:
         labels = torch.empty((H, W), dtype=torch.int32, device=probs.device)
-    prm = hsc_knn_params(K, window_rows, lam)
+    prm = hsc_knn_params(K, window_rows, lam, search)
     ctx.check(lib().hsc_knn_filter(ctx.handle, _ptr(one_band), _ptr(probs), k, H, W,
                                    ctypes.byref(prm), _ptr(out_probs), _ptr(labels),
                                    _ptr(nbr_idx)))
@@ -291,13 +310,14 @@ def hsc_knn_filter(ctx: Context, one_band, probs, K: int, window_rows: int, lam:
 
 
 def hsc_classify(ctx: Context, cube, model: Model, K: int, window_rows: int, lam: float,
-                 flags: int = 0, labels=None, out_probs=None, one_band=None, probs=None):
+                 flags: int = 0, labels=None, out_probs=None, one_band=None, probs=None,
+                 search: int = HSC_KNN_SEARCH_AUTO):
     import torch
     B, H, W = cube.shape
     if labels is None:
         labels = torch.empty((H, W), dtype=torch.int32, device=cube.device)
     ms = model.struct()
-    prm = hsc_knn_params(K, window_rows, lam)
+    prm = hsc_knn_params(K, window_rows, lam, search)
     ctx.check(lib().hsc_classify(ctx.handle, _ptr(cube), B, H, W, ctypes.byref(ms),
                                  ctypes.byref(prm), flags, _ptr(labels), _ptr(out_probs),
                                  _ptr(one_band), _ptr(probs)))

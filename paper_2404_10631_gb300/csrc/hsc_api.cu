@@ -232,6 +232,10 @@ hsc_status check_knn(hsc_ctx *ctx, const hsc_knn_params *p, int n_classes, int H
         return fail(ctx, HSC_ERR_UNSUPPORTED, "KNN: window_rows exceeds HSC_MAX_WINDOW_ROWS%s");
     if (!(p->lambda >= 0.f) || !isfinite(p->lambda) || p->lambda > 1e6f)
         return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: lambda must be finite, >= 0 and <= 1e6%s");
+    if (p->search < HSC_KNN_SEARCH_AUTO || p->search > HSC_KNN_SEARCH_PRUNED)
+        return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: unknown search mode%s");
+    if (p->search == HSC_KNN_SEARCH_PRUNED && !(p->lambda > 0.f))
+        return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: the pruned search needs lambda > 0%s");
     long up = (p->window_rows + 1) / 2;
     long min_cand = std::min<long>(up, H) * (long)W;
     if ((long)p->k > min_cand)
@@ -309,7 +313,8 @@ hsc_status hsc_profile_enable(hsc_ctx *ctx, int enable)
     return HSC_OK;
 }
 
-hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_iters)
+hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_iters,
+                               int64_t *sweep_cycles, int64_t *refine_cycles)
 {
     hsc_status st = check_ctx(ctx);
     if (st) return st;
@@ -324,6 +329,26 @@ hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_it
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_pca_diagnostics");
     *sweeps = (int32_t)c.jacobi_sweeps;
     *refine_iters = (int32_t)c.refine_iters;
+    if (sweep_cycles) *sweep_cycles = (int64_t)c.jacobi_sweep_cycles;
+    if (refine_cycles) *refine_cycles = (int64_t)c.jacobi_refine_cycles;
+    return HSC_OK;
+}
+
+hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!candidates_evaluated) return fail(ctx, HSC_ERR_INVALID_ARG, "output pointer is NULL%s");
+    *candidates_evaluated = 0;
+    if (!ctx->scratch) return HSC_OK;
+    Control c;
+    unsigned long long *dev = &reinterpret_cast<Control *>(ctx->scratch)->knn_evals;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&c, ctx->scratch, sizeof c, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, sizeof(*dev), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_knn_diagnostics");
+    *candidates_evaluated = (int64_t)c.knn_evals;
     return HSC_OK;
 }
 
@@ -522,7 +547,7 @@ hsc_status hsc_knn_filter(hsc_ctx *ctx, const float *one_band, const float *prob
     StageTimer t(ctx, HSC_STAGE_KNN, 1);
     cudaError_t e = hsc::launch_knn(one_band, probs, n_classes, H, W, params->k,
                                     params->window_rows, params->lambda, out_probs, labels, nbr_idx,
-                                    s.ctl, ctx->stream);
+                                    s.ctl, ctx->stream, params->search != HSC_KNN_SEARCH_FULL);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_knn_filter launch");
     return HSC_OK;
 }
@@ -568,7 +593,8 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     if (e == cudaSuccess) {
         StageTimer t(ctx, HSC_STAGE_KNN, 1);
         e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
-                            out_probs, labels, nullptr, s.ctl, ctx->stream);
+                            out_probs, labels, nullptr, s.ctl, ctx->stream,
+                            params->search != HSC_KNN_SEARCH_FULL);
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_classify launch");
     return HSC_OK;

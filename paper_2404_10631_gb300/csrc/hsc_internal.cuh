@@ -25,7 +25,11 @@ struct Control {
     unsigned imax_key;        // ordered-int key of max I (atomicMax)
     unsigned jacobi_sweeps;   // diagnostics of the last Jacobi launch
     unsigned refine_iters;
-    unsigned pad[59];
+    unsigned pad0;
+    unsigned long long knn_evals;  // candidates evaluated by the pruned KNN since last read
+    unsigned long long jacobi_sweep_cycles;   // SM clock cycles in the FP32 sweeps
+    unsigned long long jacobi_refine_cycles;  // SM clock cycles in the FP64 refinement
+    unsigned pad[52];
 };
 
 // Float <-> order-preserving unsigned key (for atomic min/max of floats).
@@ -91,9 +95,10 @@ cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,
                              cudaStream_t st);
 
-// KNN filter (Eq. 1, Eq. 2) over all pixels.
+// KNN filter (Eq. 1, Eq. 2) over all pixels: the full-window scan, or (pruned
+// and lambda > 0) the exact spatially pruned walk; both select the same sets.
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr,
-                       Control *ctl, cudaStream_t st);
+                       Control *ctl, cudaStream_t st, bool pruned);
 
 }  // namespace hsc

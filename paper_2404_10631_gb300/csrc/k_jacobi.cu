@@ -8,8 +8,9 @@
 //     zeroes a_pq (the same rotation the paper's classical Jacobi applies to
 //     its pivot); the update A <- J^T A J is done per 2x2 block of pairs so a
 //     round is one pass over A (upper triangle) and V, both in shared memory.
-//     The sweeps stop once every off-diagonal entry met in a sweep is below
-//     half the largest diagonal entry (two sweeps on the synthetic cubes).
+//     The first round of sweeps stops after two sweeps (or earlier once every
+//     off-diagonal entry is at most the largest diagonal entry): an FP32
+//     sweep costs about as much as ten FP64 refinement steps below.
 //  2. FP64 refinement of the leading vector against the FP64 covariance:
 //     with (theta_j, V_j) the FP32 eigenpairs and v the current leading
 //     vector, r = C v - rho v (rho = v^T C v) and
@@ -40,6 +41,7 @@ struct JacParams {
     float rot_tol;       // rotate (p,q) when |a_pq| > rot_tol (A scaled to max diag 1)
     float stop_tol;      // end the sweeps once every |a_pq| seen in one is <= stop_tol
     float stop_tol_final;  // tighter tolerance for a second round if refinement stalls
+    int phase0_sweeps;     // the first round of sweeps ends after this many at most
     int use_smem;
 };
 
@@ -161,7 +163,9 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
     __shared__ double s_rho, s_rn;
     // Phase 0 sweeps to a loose FP32 tolerance; phase 1 (only if the FP64
     // refinement has not converged) sweeps on to a tight one and refines again.
+    long long t_sweep = 0, t_refine = 0;
     for (int phase = 0; phase < 2 && !converged; ++phase) {
+    long long t0 = clock64();
     while (sweeps < prm.max_sweeps) {
         float offmax = 0.f;
         for (int t = 0; t < n - 1; ++t) {
@@ -239,9 +243,11 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         }
         ++sweeps;
         offmax = block_maxf(offmax, fred);
-        if (offmax <= stop) break;
+        if (offmax <= stop || (phase == 0 && sweeps >= prm.phase0_sweeps)) break;
     }
 
+    long long t1 = clock64();
+    t_sweep += t1 - t0;
     // ---- 2. FP64 refinement of the leading vector
     if (tid == 0) {
         int lead = 0;
@@ -322,6 +328,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         __syncthreads();
     }
     __syncthreads();
+    t_refine += clock64() - t1;
     stop = prm.stop_tol_final;
     }  // phases
     // ---- 3. sign rule and outputs
@@ -334,6 +341,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
         if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
         ctl->jacobi_sweeps = (unsigned)sweeps;
         ctl->refine_iters = (unsigned)refine_iters;
+        ctl->jacobi_sweep_cycles = (unsigned long long)t_sweep;
+        ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
         ctl->imin_key = float_to_key(INFINITY);
         ctl->imax_key = float_to_key(-INFINITY);
     }
@@ -364,8 +373,9 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
     if (prm.n < 2) prm.n = 2;
     prm.max_sweeps = 30;
     prm.rot_tol = 1e-7f;
-    prm.stop_tol = 0.5f;
+    prm.stop_tol = 1.0f;
     prm.stop_tol_final = 1e-2f;
+    prm.phase0_sweeps = 2;
     size_t need = 2 * (size_t)prm.n * (prm.n + 1) * sizeof(float);
     prm.use_smem = need <= kJacSmemLimit;
     size_t smem = prm.use_smem ? need : 0;

@@ -93,6 +93,41 @@ __device__ __noinline__ Key max_key(const Key *buf, int n)
 }
 
 
+// Writes the pixel's outputs from its K selected keys: neighbour indices
+// nearest first (optional), O = mean of the neighbours' probabilities, label.
+__device__ __noinline__ void finish_pixel(Key *buf, int n, int K, const float *__restrict__ P, int k,
+                                          long N, long p, float *__restrict__ O,
+                                          int32_t *__restrict__ labels, int32_t *__restrict__ nbr)
+{
+    if (nbr) {  // nearest first (selection sort; debug output)
+        for (int a = 0; a < n; ++a) {
+            int im = a;
+            for (int b = a + 1; b < n; ++b)
+                if (key_lt(buf[b], buf[im])) im = b;
+            Key t = buf[a];
+            buf[a] = buf[im];
+            buf[im] = t;
+            nbr[p * K + a] = buf[a].q;
+        }
+        for (int a = n; a < K; ++a) nbr[p * K + a] = -1;
+    }
+    const float invK = 1.f / (float)K;
+    int best = 0;
+    float bestv = -INFINITY;
+    for (int cl = 0; cl < k; ++cl) {
+        const float *Pc = P + (size_t)cl * (size_t)N;
+        float s = 0.f;
+        for (int a = 0; a < n; ++a) s += __ldg(Pc + buf[a].q);
+        float o = s * invK;
+        if (O) O[(size_t)cl * (size_t)N + p] = o;
+        if (o > bestv) {
+            bestv = o;
+            best = cl;
+        }
+    }
+    labels[p] = best;
+}
+
 template <int RMAX>
 __global__ void __launch_bounds__(kThreads)
 knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int H, int W, int K,
@@ -239,35 +274,103 @@ knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int 
     if (n < K) atomicOr(&ctl->status, ST_KNN_SHORT);
     shrink(buf, n, K);
 
-    const long p = (long)r * W + c;
-    if (nbr) {  // nearest first (selection sort; debug output)
-        for (int a = 0; a < n; ++a) {
-            int im = a;
-            for (int b = a + 1; b < n; ++b)
-                if (key_lt(buf[b], buf[im])) im = b;
-            Key t = buf[a];
-            buf[a] = buf[im];
-            buf[im] = t;
-            nbr[p * K + a] = buf[a].q;
-        }
-        for (int a = n; a < K; ++a) nbr[p * K + a] = -1;
-    }
-    const float invK = 1.f / (float)K;
-    int best = 0;
-    float bestv = -INFINITY;
-    for (int cl = 0; cl < k; ++cl) {
-        const float *Pc = P + (size_t)cl * (size_t)N;
-        float s = 0.f;
-        for (int a = 0; a < n; ++a) s += __ldg(Pc + buf[a].q);
-        float o = s * invK;
-        if (O) O[(size_t)cl * (size_t)N + p] = o;
-        if (o > bestv) {
-            bestv = o;
-            best = cl;
-        }
-    }
-    labels[p] = best;
+    finish_pixel(buf, n, K, P, k, N, (long)r * W + c, O, labels, nbr);
     (void)lane;
+}
+
+// Exact, spatially pruned variant. Every key is at least fl(lambda^2) *
+// (dr^2 + dc^2) (rounded down by at most one ulp), and the seed bounds the
+// K-th smallest key by tau, so only candidates with dr^2 + dc^2 <=
+// tau (1 + 2^-20) / fl(lambda^2) can be among the K nearest. Each lane walks
+// exactly that disk of its own pixel (truncated to the window), keeps keys
+// <= tau, and selects the best K as the full-window kernel does: the result
+// is the same set. Lanes of a warp share (dr, dc), so their loads of I are
+// consecutive. Requires lambda > 0.
+__global__ void __launch_bounds__(kThreads)
+knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int H, int W,
+                  int K, int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
+                  int32_t *__restrict__ nbr, Control *ctl)
+{
+    const int r = blockIdx.y;
+    const int c = blockIdx.x * kThreads + threadIdx.x;
+    const bool active = c < W;
+    const int lo_r = max(0, r - R / 2);
+    const int hi_r = min(H - 1, r + (R + 1) / 2 - 1);
+    const float l2 = lam * lam;
+    const long N = (long)H * W;
+    const float Ip = active ? I[(long)r * W + c] : 0.f;
+    bool bad = !isfinite(Ip);
+
+    // seed: the K spatially nearest valid candidates bound the K-th key
+    Key tau;
+    tau.hi = -1.f;
+    tau.lo = 0.f;
+    tau.q = -1;
+    int cnt = active ? 0 : K;
+    {
+        const int dlo = lo_r - r, dhi = hi_r - r;
+        const int smax = max(dlo * dlo, dhi * dhi) + (W - 1) * (W - 1);
+        for (int s = 0; s <= smax; ++s) {
+            for (int dr = dlo; dr <= dhi; ++dr) {
+                int m = s - dr * dr;
+                if (m < 0) continue;
+                int dc = (int)sqrtf((float)m);
+                while (dc * dc > m) --dc;
+                while ((dc + 1) * (dc + 1) <= m) ++dc;
+                if (dc * dc != m) continue;
+#pragma unroll
+                for (int sg = 0; sg < 2; ++sg) {
+                    if (sg == 1 && dc == 0) break;
+                    int j = sg ? c - dc : c + dc;
+                    if (cnt < K && j >= 0 && j < W) {
+                        int q = (r + dr) * W + j;
+                        Key kk = make_key(Ip, __ldg(I + q), dr, dc, l2, q);
+                        if (cnt == 0 || key_lt(tau, kk)) tau = kk;
+                        ++cnt;
+                    }
+                }
+            }
+            if (__all_sync(0xffffffffu, cnt >= K)) break;
+        }
+    }
+    if (active && cnt < K) atomicOr(&ctl->status, ST_KNN_SHORT);
+    unsigned evals = active ? (unsigned)cnt : 0u;
+
+    // collect every candidate of the disk whose key is <= tau
+    Key buf[kCap];
+    int n = 0;
+    const float smax_f = active ? __fdiv_ru(tau.hi * (1.f + 1.f / 1048576.f), l2) : -1.f;
+    for (int i = lo_r; i <= hi_r; ++i) {
+        const int dr = i - r;
+        const float rem = smax_f - (float)(dr * dr);
+        if (rem < 0.f) continue;
+        const int cm = (int)sqrtf(rem) + 1;
+        const int j0 = max(0, c - cm), j1 = min(W - 1, c + cm);
+        evals += (unsigned)max(0, j1 - j0 + 1);
+        for (int j = j0; j <= j1; ++j) {
+            const int q = i * W + j;
+            const float Iq = __ldg(I + q);
+            bad |= !isfinite(Iq);
+            Key kk = make_key(Ip, Iq, dr, c - j, l2, q);
+            if (!key_le(kk, tau)) continue;
+            if (n == kCap) {
+                shrink(buf, n, K);
+                tau = max_key(buf, n);
+                if (!key_le(kk, tau)) continue;
+            }
+            buf[n++] = kk;
+        }
+    }
+    if (bad) atomicOr(&ctl->status, ST_NONFINITE_MAP);
+    {
+        unsigned long long e = evals;
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&ctl->knn_evals, e);
+    }
+    if (!active) return;
+    if (n < K) atomicOr(&ctl->status, ST_KNN_SHORT);
+    shrink(buf, n, K);
+    finish_pixel(buf, n, K, P, k, N, (long)r * W + c, O, labels, nbr);
 }
 
 template <int RMAX>
@@ -289,8 +392,14 @@ cudaError_t launch_rmax(const float *I, const float *P, int k, int H, int W, int
 
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr, Control *ctl,
-                       cudaStream_t st)
+                       cudaStream_t st, bool pruned)
 {
+    if (pruned && lambda > 0.f) {
+        dim3 grid((W + kThreads - 1) / kThreads, H);
+        knn_pruned_kernel<<<grid, kThreads, 0, st>>>(I, P, k, H, W, K, R, lambda, O, labels, nbr,
+                                                     ctl);
+        return cudaGetLastError();
+    }
     if (R <= 8) return launch_rmax<8>(I, P, k, H, W, K, R, lambda, O, labels, nbr, ctl, st);
     if (R <= 16) return launch_rmax<16>(I, P, k, H, W, K, R, lambda, O, labels, nbr, ctl, st);
     return launch_rmax<32>(I, P, k, H, W, K, R, lambda, O, labels, nbr, ctl, st);

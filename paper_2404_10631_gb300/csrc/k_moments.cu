@@ -19,18 +19,35 @@ constexpr int kGramThreads = 256;
 constexpr int kGramChunk = 32;   // pixels staged per step
 constexpr int kTile = 8;         // 8x8 accumulator tile per thread
 
+// Pilot shift: the mean of a 4096-pixel sample of each band, read as 16
+// runs of 256 consecutive pixels spread over the band (coalesced). Any shift
+// close to the mean works: the moments are exact in it.
 __global__ void pilot_shift_kernel(const float *__restrict__ cube, int B, long N,
                                    float *__restrict__ shift, Control *ctl)
 {
     const int b = blockIdx.x;
-    const long S = N < 4096 ? N : 4096;
+    constexpr int kRuns = 16, kRun = 256;
+    const float *band = cube + (size_t)b * (size_t)N;
     double acc = 0.0;
+    long count = 0;
     bool bad = false;
-    for (long s = threadIdx.x; s < S; s += blockDim.x) {
-        long p = (s * N) / S;
-        float x = cube[(size_t)b * (size_t)N + p];
-        bad |= !isfinite(x);
-        acc += (double)x;
+    if (N <= (long)kRuns * kRun) {
+        for (long p = threadIdx.x; p < N; p += blockDim.x) {
+            float x = band[p];
+            bad |= !isfinite(x);
+            acc += (double)x;
+        }
+        count = N;
+    } else {
+        for (int r = 0; r < kRuns; ++r) {
+            long p = ((long)r * (N - kRun)) / (kRuns - 1) + threadIdx.x;
+            if (threadIdx.x < kRun) {
+                float x = band[p];
+                bad |= !isfinite(x);
+                acc += (double)x;
+            }
+        }
+        count = (long)kRuns * kRun;
     }
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -39,7 +56,7 @@ __global__ void pilot_shift_kernel(const float *__restrict__ cube, int B, long N
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        shift[b] = (float)(t / (double)S);
+        shift[b] = (float)(t / (double)count);
     }
 }
 
@@ -127,32 +144,54 @@ gram_partial_kernel(const float *__restrict__ cube, int B, int Bp, long N,
     if (do_sums && tid < B) sum_part[(size_t)blockIdx.x * B + tid] = bsum;
 }
 
-// delta_b = (1/N) sum of partial sums; mu_b = shift_b + delta_b.
+// delta_b = (1/N) sum of partial sums; mu_b = shift_b + delta_b. One CTA per
+// band, the partials split over the threads, FP64 throughout.
 __global__ void band_mean_kernel(int B, long N, int n_part, const float *__restrict__ shift,
                                  const float *__restrict__ sum_part, double *__restrict__ delta,
                                  double *__restrict__ mu)
 {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
+    const int b = blockIdx.x;
     double s = 0.0;
-    for (int i = 0; i < n_part; ++i) s += (double)sum_part[(size_t)i * B + b];
-    double d = s / (double)N;
-    delta[b] = d;
-    mu[b] = (double)shift[b] + d;
+    for (int i = threadIdx.x; i < n_part; i += blockDim.x) s += (double)sum_part[(size_t)i * B + b];
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        double d = t / (double)N;
+        delta[b] = d;
+        mu[b] = (double)shift[b] + d;
+    }
 }
 
-// C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored.
-__global__ void gram_reduce_kernel(int B, long N, int n_part, const float *__restrict__ gram_part,
-                                   const double *__restrict__ delta, double *__restrict__ C)
+// C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored. A CTA
+// takes 32 consecutive entries e = b*B + c; its 8 warps each sum every 8th
+// partial (coalesced across the 32 entries), then the 8 slices are added.
+constexpr int kRedEntries = 32, kRedSlices = 8;
+__global__ void __launch_bounds__(kRedEntries * kRedSlices)
+gram_reduce_kernel(int B, long N, int n_part, const float *__restrict__ gram_part,
+                   const double *__restrict__ delta, double *__restrict__ C)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int b = blockIdx.y;
-    if (c >= B || c < b) return;
+    const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+    const long e = (long)blockIdx.x * kRedEntries + lane;
+    const long BB = (long)B * B;
+    const int b = e < BB ? (int)(e / B) : 0, c = e < BB ? (int)(e % B) : 0;
+    const bool active = e < BB && c >= b;
     double g = 0.0;
-    for (int i = 0; i < n_part; ++i) g += (double)gram_part[((size_t)i * B + b) * B + c];
-    double v = g / (double)N - delta[b] * delta[c];
-    C[(size_t)b * B + c] = v;
-    C[(size_t)c * B + b] = v;
+    if (active)
+        for (int i = slice; i < n_part; i += kRedSlices) g += (double)gram_part[(size_t)i * BB + e];
+    __shared__ double part[kRedSlices][kRedEntries];
+    part[slice][lane] = g;
+    __syncthreads();
+    if (slice == 0 && active) {
+        double t = 0.0;
+        for (int k = 0; k < kRedSlices; ++k) t += part[k][lane];
+        double v = t / (double)N - delta[b] * delta[c];
+        C[(size_t)b * B + c] = v;
+        C[(size_t)c * B + b] = v;
+    }
 }
 
 }  // namespace
@@ -161,6 +200,17 @@ __global__ void gram_reduce_kernel(int B, long N, int n_part, const float *__res
 // 160 KB of shared memory), two for the FP32 one; the scratch is sized for
 // the larger count.
 int moments_partitions(int sm_count) { return 2 * sm_count; }
+
+// FP64 means and covariance from n_part partials (delta lives in v1 until
+// the Jacobi kernel overwrites it with the eigenvector).
+static cudaError_t launch_reductions(int B, long N, int n_part, const PcaScratch &s, cudaStream_t st)
+{
+    band_mean_kernel<<<B, 128, 0, st>>>(B, N, n_part, s.shift, s.sum_part, s.v1, s.mu);
+    const long BB = (long)B * B;
+    gram_reduce_kernel<<<(unsigned)((BB + kRedEntries - 1) / kRedEntries), kRedEntries * kRedSlices,
+                         0, st>>>(B, N, n_part, s.gram_part, s.v1, s.C);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s, int sm_count,
                            cudaStream_t st, bool force_simt)
@@ -171,11 +221,7 @@ cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s
         t.n_part = s.n_part < sm_count ? s.n_part : sm_count;  // one CTA per SM
         cudaError_t e = launch_gram_tc(cube, B, N, t, st);
         if (e != cudaSuccess) return e;
-        band_mean_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, N, t.n_part, s.shift, s.sum_part, s.v1,
-                                                          s.mu);
-        dim3 rg((B + 127) / 128, B);
-        gram_reduce_kernel<<<rg, 128, 0, st>>>(B, N, t.n_part, s.gram_part, s.v1, s.C);
-        return cudaGetLastError();
+        return launch_reductions(B, N, t.n_part, s, st);
     }
     const int Bp = (B + kTile - 1) / kTile * kTile;
     const int nt = Bp / kTile;
@@ -187,12 +233,7 @@ cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s
     dim3 grid(s.n_part, groups);
     gram_partial_kernel<<<grid, kGramThreads, smem, st>>>(cube, B, Bp, N, s.shift, s.gram_part,
                                                           s.sum_part, s.ctl);
-    band_mean_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, N, s.n_part, s.shift, s.sum_part,
-                                                      s.v1 /* delta lives in v1 until Jacobi */,
-                                                      s.mu);
-    dim3 rg((B + 127) / 128, B);
-    gram_reduce_kernel<<<rg, 128, 0, st>>>(B, N, s.n_part, s.gram_part, s.v1, s.C);
-    return cudaGetLastError();
+    return launch_reductions(B, N, s.n_part, s, st);
 }
 
 }  // namespace hsc

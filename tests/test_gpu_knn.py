@@ -15,9 +15,10 @@ from parity import check_knn, sample_rows
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SEARCHES = [1, 2]  # full-window scan, pruned walk
 
 
-def run_knn(hsc, ctx, I, P, K, R, lam):
+def run_knn(hsc, ctx, I, P, K, R, lam, search=1):
     import torch
     dev = torch.device("cuda")
     It = torch.as_tensor(np.ascontiguousarray(I, dtype=np.float32), device=dev)
@@ -26,7 +27,8 @@ def run_knn(hsc, ctx, I, P, K, R, lam):
     O = torch.full((k, H, W), -1.0, dtype=torch.float32, device=dev)
     lab = torch.full((H, W), -1, dtype=torch.int32, device=dev)
     nbr = torch.full((H, W, K), -1, dtype=torch.int32, device=dev)
-    hsc.hsc_knn_filter(ctx, It, Pt, K, R, lam, out_probs=O, labels=lab, nbr_idx=nbr)
+    hsc.hsc_knn_filter(ctx, It, Pt, K, R, lam, out_probs=O, labels=lab, nbr_idx=nbr,
+                       search=search)
     ctx.sync()
     return nbr.cpu().numpy(), O.cpu().numpy(), lab.cpu().numpy()
 
@@ -43,16 +45,18 @@ def rand_maps(H, W, k, seed, dyadic=False):
 
 
 @pytest.mark.parametrize("name", ["knn_line5.json", "knn_window_ties.json"])
-def test_golden_hand_examples(hsc, ctx, name):
+@pytest.mark.parametrize("search", SEARCHES)
+def test_golden_hand_examples(hsc, ctx, name, search):
     g = json.load(open(os.path.join(GOLDEN, name)))
     I = np.asarray(g["I"], dtype=np.float32)
     P = np.asarray(g["P"], dtype=np.float32)
-    nbr, O, lab = run_knn(hsc, ctx, I, P, g["K"], g["R"], g["lambda"])
+    nbr, O, lab = run_knn(hsc, ctx, I, P, g["K"], g["R"], g["lambda"], search)
     np.testing.assert_array_equal(nbr.reshape(-1, g["K"]), g["nbr"])
     np.testing.assert_allclose(O, g["O"], atol=1e-7)
     np.testing.assert_array_equal(lab, g["labels"])
 
 
+@pytest.mark.parametrize("search", SEARCHES)
 @pytest.mark.parametrize("H,W,K,R,lam,k", [
     (32, 32, 8, 5, 1.0, 4),      # the tiny configuration's sizes
     (37, 45, 40, 14, 1.0, 4),    # paper's K and window, ragged width
@@ -63,21 +67,22 @@ def test_golden_hand_examples(hsc, ctx, name):
     (40, 7, 12, 4, 1.0, 4),      # narrower than a warp, even window
     (6, 50, 150, 9, 1.0, 3),     # K above 64 is rejected (checked below)
 ])
-def test_random_maps_against_oracle(hsc, ctx, H, W, K, R, lam, k):
+def test_random_maps_against_oracle(hsc, ctx, H, W, K, R, lam, k, search):
     I, P = rand_maps(H, W, k, seed=H * 1000 + W + K)
     if K > hsc.HSC_MAX_K:
         with pytest.raises(hsc.HscError) as e:
-            run_knn(hsc, ctx, I, P, K, R, lam)
+            run_knn(hsc, ctx, I, P, K, R, lam, search)
         assert e.value.status == hsc.HSC_ERR_UNSUPPORTED
         return
-    nbr, O, lab = run_knn(hsc, ctx, I, P, K, R, lam)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, K, R, lam, search)
     st = check_knn(I, P, K, R, lam, nbr, O, lab)
     assert st["pixels"] == H * W
 
 
-def test_k1_window1_returns_own_probabilities(hsc, ctx):
+@pytest.mark.parametrize("search", SEARCHES)
+def test_k1_window1_returns_own_probabilities(hsc, ctx, search):
     I, P = rand_maps(33, 71, 4, seed=3)
-    nbr, O, lab = run_knn(hsc, ctx, I, P, 1, 1, 1.0)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, 1, 1, 1.0, search)
     np.testing.assert_array_equal(O, P)
     np.testing.assert_array_equal(lab, np.argmax(P, axis=0))
     np.testing.assert_array_equal(nbr.reshape(-1), np.arange(33 * 71))
@@ -94,24 +99,27 @@ def test_lambda0_constant_image_tie_rule(hsc, ctx):
         np.testing.assert_array_equal(nbr.reshape(-1, K)[p], lo * W + np.arange(K))
 
 
-def test_dyadic_image_exact_ties(hsc, ctx):
+@pytest.mark.parametrize("search", SEARCHES)
+def test_dyadic_image_exact_ties(hsc, ctx, search):
     """Coarse grey levels make many exactly equal distances: the tie rule
     (smaller linear index) must match the oracle everywhere."""
     I, P = rand_maps(24, 50, 3, seed=5, dyadic=True)
-    nbr, O, lab = run_knn(hsc, ctx, I, P, 20, 6, 1.0)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, 20, 6, 1.0, search)
     st = check_knn(I, P, 20, 6, 1.0, nbr, O, lab)
     assert st["official_near_ties"] > 0 and st["fp64_set_differs"] == 0
 
 
-def test_whole_window_box_filter(hsc, ctx):
+@pytest.mark.parametrize("search", SEARCHES)
+def test_whole_window_box_filter(hsc, ctx, search):
     H, W = 3, 21
     I, P = rand_maps(H, W, 4, seed=6)
-    nbr, O, lab = run_knn(hsc, ctx, I, P, H * W, 6, 1.0)
+    nbr, O, lab = run_knn(hsc, ctx, I, P, H * W, 6, 1.0, search)
     mean = P.astype(np.float64).reshape(4, -1).mean(axis=1)
     np.testing.assert_allclose(O.reshape(4, -1), np.repeat(mean[:, None], H * W, axis=1), atol=1e-6)
 
 
-def test_neuro_size_sampled_rows(hsc, ctx):
+@pytest.mark.parametrize("search", SEARCHES)
+def test_neuro_size_sampled_rows(hsc, ctx, search):
     """416 x 512 frame, K = 40, 14-row window: the oracle's own normalised
     one-band image and probabilities as inputs, rows at both borders and
     inside checked pixel by pixel."""
@@ -120,8 +128,29 @@ def test_neuro_size_sampled_rows(hsc, ctx):
     P, _, _ = oracle.svm_probs(f.cube, f.model)
     I32 = pca["I_norm"].astype(np.float32)
     P32 = P.astype(np.float32)
-    nbr, O, lab = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0)
+    nbr, O, lab = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0, search)
     H, W = I32.shape
     st = check_knn(I32, P32, 40, 14, 1.0, nbr, O, lab,
                    pixels=sample_rows(H, W, [0, 1, 6, 7, 200, 408, 409, 415]))
     assert st["pixels"] == 8 * W
+
+
+def test_pruned_equals_full_window(hsc, ctx):
+    """Both searches select the same sets: identical outputs bit for bit."""
+    f = synth.make_config(2)
+    pca = oracle.pca_one_band(f.cube)
+    P, _, _ = oracle.svm_probs(f.cube, f.model)
+    I32 = pca["I_norm"].astype(np.float32)
+    P32 = P.astype(np.float32)
+    a = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0, 1)
+    b = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0, 2)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_pruned_search_rejects_lambda_zero(hsc, ctx):
+    I, P = rand_maps(8, 40, 3, seed=9)
+    with pytest.raises(hsc.HscError) as e:
+        run_knn(hsc, ctx, I, P, 4, 3, 0.0, 2)
+    assert e.value.status == hsc.HSC_ERR_INVALID_ARG
+    run_knn(hsc, ctx, I, P, 4, 3, 0.0, 0)  # auto falls back to the full scan
