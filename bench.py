@@ -361,6 +361,14 @@ def run_ours(args, f):
     e2e_value = world * N * n_e2e / float(t.item())
     ctx.sync()
 
+    # ---- batched uneven frames vs the plain per-frame path (same GPU)
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(hsc, ctx, stream, dev, args)
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = run_serving(hsc, ctx, stream, dev, args)
+
     # ---- roofline of the dominant stage
     peaks, peak_src = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -419,6 +427,8 @@ def run_ours(args, f):
             "stages": stages,
             "knn_full_window": knn_full,
             "knn_pruned": knn_pruned,
+            "batch": batch,
+            "serving": serving,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": n_e2e},
             "gpu_launches": int(sum(stage_kernels.values())),
@@ -437,6 +447,155 @@ def run_ours(args, f):
         dist.destroy_process_group()
 
 
+def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
+    """256 square snapshot frames (sides 40-64 px, 125 bands, shared model,
+    K=16, 7-row window): one hsc_classify_batch call (CUDA-graph replay) per
+    step against hsc_classify called frame by frame on the same GPU."""
+    import torch
+    frames = synth.make_batch(n_frames)
+    f0 = frames[0]
+    k = f0.model.n_classes
+    model = hsc.Model.from_host(f0.model, device=dev)
+    cubes = [torch.as_tensor(f.cube, device=dev) for f in frames]
+    labs = [torch.empty(f.cube.shape[1:], dtype=torch.int32, device=dev) for f in frames]
+    px = sum(f.cube.shape[1] * f.cube.shape[2] for f in frames)
+
+    def batched():
+        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
+                               flags=hsc.HSC_BATCH_GRAPH, labels=labs)
+
+    def per_frame():
+        for c, l in zip(cubes, labs):
+            hsc.hsc_classify(ctx, c, model, f0.K, f0.window_rows, f0.lam, labels=l)
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        ctx.sync()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        ev[0].record(stream)
+        for i in range(n):
+            fn()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(n))
+        return ev[0].elapsed_time(ev[n]) / n, per
+
+    b_ms, b_per = timed(batched, reps)
+    p_ms, p_per = timed(per_frame, 3)
+    return {"workload": "%d square snapshot frames, sides 40-64 px, 125 bands float32, "
+                        "4 classes (shared model), K=16, 7-row window, lambda=1" % n_frames,
+            "pixels_per_batch": px,
+            "batched": {"value": px / (b_ms / 1e3), "unit": UNIT, "ms_per_batch": b_ms,
+                        "p50_ms": b_per[len(b_per) // 2], "p99_ms": b_per[-1],
+                        "api": "hsc_classify_batch, CUDA-graph replay"},
+            "plain_per_frame": {"value": px / (p_ms / 1e3), "unit": UNIT, "ms_per_batch": p_ms,
+                                "api": "hsc_classify once per frame, one stream"},
+            "speedup": p_ms / b_ms}
+
+
+def run_serving(hsc, ctx, stream, dev, args, rates=(200.0, 400.0, 800.0, 1600.0),
+                n_req=400, max_inflight=16):
+    """Serving stream: Poisson arrivals of 70% snapshot cubes (40-64 px square,
+    125 bands) and 30% pushbroom cubes (384-640 x 320-512 px, 128 bands), each
+    with its own SVM model and K in {16, 40}; host cube in, host labels out.
+    The native server (continuous batching under an HBM budget) against the
+    plain per-frame path (copy in, hsc_classify, copy out, wait; one request
+    at a time) on the same arrivals; 'saturation' submits all at time 0."""
+    import queue
+    import threading
+
+    import torch
+    n_snap, n_push = 24, 6
+    pool = synth.make_serving_pool(n_snap, n_push)
+    cubes = [torch.from_numpy(f.cube).pin_memory() for f in pool]
+    models = [hsc.Model.from_host(f.model, device=dev) for f in pool]
+    dcubes = [torch.empty(f.cube.shape, dtype=torch.float32, device=dev) for f in pool]
+    dlabs = [torch.empty(f.cube.shape[1:], dtype=torch.int32, device=dev) for f in pool]
+    outs = {i: [torch.empty(pool[i].cube.shape[1:], dtype=torch.int32).pin_memory()
+                for _ in range(4)] for i in range(len(pool))}
+    px_of = [f.cube.shape[1] * f.cube.shape[2] for f in pool]
+
+    def server_run(srv, t_arr, idx):
+        q = queue.Queue()
+        t0 = time.perf_counter()
+
+        def feeder():
+            for j in range(len(idx)):
+                dt = t_arr[j] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                i = int(idx[j])
+                f = pool[i]
+                ts = time.perf_counter() - t0
+                q.put((j, ts, srv.submit(cubes[i], models[i], f.K, f.window_rows, f.lam,
+                                         outs[i][j % 4])))
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        lat, done = [], []
+        for _ in range(len(idx)):
+            j, ts, t = q.get()
+            ms = srv.wait(t)
+            # latency from the arrival time (the feeder can only be late)
+            lat.append(ms + 1e3 * (ts - t_arr[j]))
+            done.append(ts + ms / 1e3)
+        th.join()
+        return lat, max(done)
+
+    def per_frame_run(t_arr, idx):
+        lat, t0 = [], time.perf_counter()
+        for j in range(len(idx)):
+            now = time.perf_counter() - t0
+            if t_arr[j] > now:
+                time.sleep(t_arr[j] - now)
+            i = int(idx[j])
+            f = pool[i]
+            dcubes[i].copy_(cubes[i], non_blocking=True)
+            hsc.hsc_classify(ctx, dcubes[i], models[i], f.K, f.window_rows, f.lam,
+                             labels=dlabs[i])
+            outs[i][j % 4].copy_(dlabs[i], non_blocking=True)
+            stream.synchronize()
+            lat.append(1e3 * (time.perf_counter() - t0 - t_arr[j]))
+        ctx.sync()
+        return lat, time.perf_counter() - t0
+
+    def summary(lat, span, idx):
+        lat = sorted(lat)
+        px = sum(px_of[int(i)] for i in idx)
+        return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1,
+                                                               int(0.99 * len(lat)))],
+                "max_ms": lat[-1], "value": px / span, "unit": UNIT, "requests": len(lat)}
+
+    # warm-up: every pool frame once through both paths
+    warm_t, warm_i = np.zeros(len(pool)), np.arange(len(pool))
+    srv = hsc.Server(dev.index or 0, max_inflight=max_inflight)
+    server_run(srv, warm_t, warm_i)
+    per_frame_run(warm_t, warm_i)
+    rows = []
+    for r in list(rates) + [None]:
+        t_arr, idx = synth.serving_arrivals(n_req, r or 1.0, n_snap, n_push)
+        if r is None:
+            t_arr = np.zeros(n_req)
+        lat_s, span_s = server_run(srv, t_arr, idx)
+        lat_p, span_p = per_frame_run(t_arr, idx)
+        rows.append({"offered_hz": r if r else "saturation",
+                     "server": summary(lat_s, span_s, idx),
+                     "plain_per_frame": summary(lat_p, span_p, idx)})
+    st = srv.stats()
+    srv.close()
+    return {"workload": "Poisson arrivals, 70%% snapshot cubes (40-64 px square, 125 bands) / "
+                        "30%% pushbroom cubes (384-640 x 320-512 px, 128 bands), float32, "
+                        "4 classes, own model per request, K in {16, 40}; %d requests per rate; "
+                        "host cube in, host labels out" % n_req,
+            "server": "hsc_server (max_inflight %d, HBM budget 80%% of free memory)"
+                      % max_inflight,
+            "plain_per_frame": "H2D copy + hsc_classify + D2H copy + wait, one request at a time",
+            "rates": rows, "server_peak_inflight": st["peak_inflight"],
+            "server_peak_bytes": st["peak_bytes"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,6 +603,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

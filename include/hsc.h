@@ -194,6 +194,85 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                         unsigned flags, int32_t *labels, float *out_probs,
                         float *one_band, float *probs);
 
+/* ---- many frames in one call (batching; an extension beyond the paper,
+ * which processes one image at a time). Every frame gets the whole path of
+ * hsc_classify: its own PCA (means, covariance, Jacobi, projection), the SVM
+ * with the shared model, the KNN filter. Frames run concurrently on up to 64
+ * library-owned streams that fork from and join back into the context's
+ * stream, each with its own scratch slot, so one frame's single-SM Jacobi
+ * overlaps the other frames' work. A frame's outputs are bit-identical to
+ * what hsc_classify gives for it alone.
+ *   frames    host array of n_frames descriptors (device pointers inside)
+ *   B, model, params, flags: shared by all frames (as hsc_classify)
+ *   flags     also HSC_BATCH_GRAPH: capture the batch's launches in a CUDA
+ *             graph; while later calls pass the same frames (pointers and
+ *             sizes) and parameters, the graph is replayed instead of
+ *             relaunching, which removes the per-launch host cost. */
+typedef struct {
+    const float *cube;   /* B x H x W float32 */
+    int32_t H, W;
+    int32_t *labels;     /* H x W int32 (required) */
+    float *out_probs;    /* k x H x W float32 (nullable) */
+    float *one_band;     /* H x W float32 (nullable) */
+    float *probs;        /* k x H x W float32 (nullable) */
+} hsc_frame;
+
+#define HSC_BATCH_GRAPH 8u
+
+hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frames, int B,
+                              const hsc_svm_model *model, const hsc_knn_params *params,
+                              unsigned flags);
+
+/* ---- serving (continuous batching; an extension beyond the paper). A server
+ * owns a device, a dispatcher thread, a pool of streams and an HBM budget.
+ * Requests (host cube of any size, its own model and KNN parameters, host
+ * output buffers) are queued by hsc_server_submit; the dispatcher admits the
+ * oldest waiting request as soon as a stream slot is free and its device
+ * memory fits in the budget, copies its cube in, runs the whole path
+ * (hsc_classify's kernels), copies the labels (and O) out, and frees its
+ * memory when the GPU is done -- so requests that arrive while others run are
+ * admitted as slots and memory free up, and their work overlaps on the GPU.
+ * Results are bit-identical to hsc_classify on the same frame. */
+typedef struct hsc_server hsc_server;
+
+typedef struct {
+    const float *cube;            /* HOST B x H x W float32 (pinned memory lets the copy overlap) */
+    int32_t B, H, W;
+    hsc_svm_model model;          /* device arrays; must stay valid until the request completes */
+    hsc_knn_params params;
+    unsigned flags;               /* 0 or HSC_SVM_COUPLE_F64 */
+    int32_t *labels;              /* HOST H x W int32 output (pinned, or the dispatcher blocks
+                                     on the copy and requests stop overlapping) */
+    float *out_probs;             /* HOST k x H x W float32 output (nullable; pinned as labels) */
+} hsc_request;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t pixels;               /* pixels of the completed requests */
+    double p50_ms, p99_ms, max_ms;/* submit-to-completion latency of the completed requests */
+    double busy_s;                /* first submit to last completion */
+    int32_t peak_inflight;        /* most requests on the GPU at once */
+    size_t peak_bytes;            /* most device memory held by admitted requests */
+} hsc_server_stats;
+
+/* device: CUDA device; hbm_budget_bytes: device memory the admitted requests
+ * may hold at once (0 = 80% of the free memory at creation); max_inflight:
+ * stream slots, 1..64. */
+hsc_status hsc_server_create(int device, size_t hbm_budget_bytes, int max_inflight,
+                             hsc_server **out);
+/* Validates and queues a request; returns its ticket. HSC_ERR_OOM when the
+ * request alone exceeds the budget. Thread-safe. */
+hsc_status hsc_server_submit(hsc_server *srv, const hsc_request *req, uint64_t *ticket);
+/* Blocks until the request is done; returns its status (the request's
+ * outputs are valid when HSC_OK) and its latency in ms (nullable). Each
+ * ticket is waited on once (a second wait gives HSC_ERR_INVALID_ARG); the
+ * server keeps a finished request's record until then. */
+hsc_status hsc_server_wait(hsc_server *srv, uint64_t ticket, double *latency_ms);
+/* Statistics of the requests completed so far (clears nothing). */
+hsc_status hsc_server_stats_get(hsc_server *srv, hsc_server_stats *out);
+/* Waits for every queued request, stops the dispatcher, frees everything. */
+void hsc_server_destroy(hsc_server *srv);
+
 /* ---- stage timing (no counterpart in the paper; its Section IV times each
  * algorithm separately, and this is how the library exposes the same split).
  * While enabled, every stage launch of the context is bracketed by two CUDA

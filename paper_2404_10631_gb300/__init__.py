@@ -36,7 +36,10 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
             "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
             "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics",
-            "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics")
+            "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics",
+            "hsc_classify_batch", "hsc_server_create", "hsc_server_submit",
+            "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy")
+HSC_BATCH_GRAPH = 8
 HSC_COV_FP32_PIPE = 4
 HSC_NOALLOC_MAX_BANDS = 128
 STAGES = ("moments", "jacobi", "project_svm", "normalize", "knn")
@@ -56,6 +59,27 @@ class hsc_knn_params(ctypes.Structure):
 HSC_KNN_SEARCH_AUTO = 0
 HSC_KNN_SEARCH_FULL = 1
 HSC_KNN_SEARCH_PRUNED = 2
+
+
+class hsc_frame(ctypes.Structure):
+    _fields_ = [("cube", ctypes.c_void_p), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("labels", ctypes.c_void_p), ("out_probs", ctypes.c_void_p),
+                ("one_band", ctypes.c_void_p), ("probs", ctypes.c_void_p)]
+
+
+class hsc_request(ctypes.Structure):
+    _fields_ = [("cube", ctypes.c_void_p), ("B", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("model", hsc_svm_model), ("params", hsc_knn_params),
+                ("flags", ctypes.c_uint), ("labels", ctypes.c_void_p),
+                ("out_probs", ctypes.c_void_p)]
+
+
+class hsc_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("pixels", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("peak_inflight", ctypes.c_int32), ("peak_bytes", ctypes.c_size_t)]
 
 
 class HscError(RuntimeError):
@@ -101,6 +125,16 @@ def lib():
                                      vp, vp, vp]
         L.hsc_classify.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
                                    ctypes.POINTER(hsc_knn_params), ctypes.c_uint, vp, vp, vp, vp]
+        L.hsc_classify_batch.argtypes = [vp, ctypes.POINTER(hsc_frame), i32, i32,
+                                         ctypes.POINTER(hsc_svm_model),
+                                         ctypes.POINTER(hsc_knn_params), ctypes.c_uint]
+        L.hsc_server_create.argtypes = [i32, sz, i32, ctypes.POINTER(vp)]
+        L.hsc_server_submit.argtypes = [vp, ctypes.POINTER(hsc_request),
+                                        ctypes.POINTER(ctypes.c_uint64)]
+        L.hsc_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+        L.hsc_server_stats_get.argtypes = [vp, ctypes.POINTER(hsc_server_stats)]
+        L.hsc_server_destroy.argtypes = [vp]
+        L.hsc_server_destroy.restype = None
         L.hsc_knn_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
         L.hsc_pca_covariance.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp]
         L.hsc_pca_one_band_noalloc.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
@@ -322,3 +356,104 @@ def hsc_classify(ctx: Context, cube, model: Model, K: int, window_rows: int, lam
                                  ctypes.byref(prm), flags, _ptr(labels), _ptr(out_probs),
                                  _ptr(one_band), _ptr(probs)))
     return labels
+
+
+def hsc_classify_batch(ctx: Context, cubes, model: Model, K: int, window_rows: int, lam: float,
+                       flags: int = 0, labels=None, out_probs=None, one_bands=None, probs=None,
+                       search: int = HSC_KNN_SEARCH_AUTO):
+    """Classify a list of B x H_i x W_i cubes in one call. Returns the list of
+    label maps (allocated when not given); optional per-frame output lists."""
+    import torch
+    n = len(cubes)
+    B = int(cubes[0].shape[0])
+    if labels is None:
+        labels = [torch.empty((c.shape[1], c.shape[2]), dtype=torch.int32, device=c.device)
+                  for c in cubes]
+    arr = (hsc_frame * n)()
+    for i, c in enumerate(cubes):
+        if int(c.shape[0]) != B:
+            raise ValueError("all cubes need the same band count")
+        arr[i] = hsc_frame(_ptr(c), int(c.shape[1]), int(c.shape[2]), _ptr(labels[i]),
+                           _ptr(out_probs[i]) if out_probs else None,
+                           _ptr(one_bands[i]) if one_bands else None,
+                           _ptr(probs[i]) if probs else None)
+    ms = model.struct()
+    prm = hsc_knn_params(K, window_rows, lam, search)
+    ctx.check(lib().hsc_classify_batch(ctx.handle, arr, n, B, ctypes.byref(ms),
+                                       ctypes.byref(prm), flags))
+    return labels
+
+
+def _host_ptr(a, dtype_name: str) -> int:
+    """Address of a C-contiguous host array (numpy or CPU torch tensor)."""
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor")
+        if str(a.dtype) != "torch." + dtype_name:
+            raise ValueError("expected %s" % dtype_name)
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"] or str(a.dtype) != dtype_name:
+        raise ValueError("expected a C-contiguous %s array" % dtype_name)
+    return a.ctypes.data
+
+
+class Server:
+    """An ``hsc_server``: requests with HOST cubes and HOST outputs, queued
+    and admitted by a native dispatcher under an HBM budget (see
+    hsc_server_create). ``submit`` returns a ticket, ``wait`` blocks on it."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_inflight: int = 8):
+        h = ctypes.c_void_p()
+        st = lib().hsc_server_create(device, hbm_budget_bytes, max_inflight, ctypes.byref(h))
+        if st != HSC_OK:
+            raise HscError(st, "hsc_server_create(device=%d)" % device)
+        self.handle = h
+        self._keep = {}  # ticket -> host buffers and model, alive until waited on
+
+    def submit(self, cube, model: Model, K: int, window_rows: int, lam: float, labels,
+               out_probs=None, flags: int = 0, search: int = HSC_KNN_SEARCH_AUTO) -> int:
+        B, H, W = (int(x) for x in cube.shape)
+        req = hsc_request(_host_ptr(cube, "float32"), B, H, W, model.struct(),
+                          hsc_knn_params(K, window_rows, lam, search), flags,
+                          _host_ptr(labels, "int32"),
+                          _host_ptr(out_probs, "float32") if out_probs is not None else None)
+        t = ctypes.c_uint64(0)
+        st = lib().hsc_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        if st != HSC_OK:
+            raise HscError(st, "hsc_server_submit")
+        self._keep[int(t.value)] = (cube, model, labels, out_probs)
+        return int(t.value)
+
+    def wait(self, ticket: int) -> float:
+        """Blocks until the request is done; returns its latency in ms."""
+        ms = ctypes.c_double(0.0)
+        st = lib().hsc_server_wait(self.handle, ticket, ctypes.byref(ms))
+        self._keep.pop(ticket, None)
+        if st != HSC_OK:
+            raise HscError(st, "request %d" % ticket)
+        return float(ms.value)
+
+    def stats(self) -> dict:
+        s = hsc_server_stats()
+        st = lib().hsc_server_stats_get(self.handle, ctypes.byref(s))
+        if st != HSC_OK:
+            raise HscError(st, "hsc_server_stats_get")
+        return {name: getattr(s, name) for name, _ in hsc_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().hsc_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

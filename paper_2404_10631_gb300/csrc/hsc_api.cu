@@ -6,7 +6,15 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "hsc_internal.cuh"
 
@@ -33,6 +41,16 @@ struct hsc_ctx {
     int n_rec = 0;
     int64_t kernels[HSC_N_STAGES] = {0, 0, 0, 0, 0};
     int64_t dropped = 0;
+    // batch pool: streams, per-slot scratch (control blocks first, contiguous)
+    int n_slots = 0;
+    cudaStream_t slot_streams[64] = {};
+    cudaEvent_t slot_events[64] = {};
+    cudaEvent_t fork_event = nullptr;
+    void *batch_scratch = nullptr;
+    size_t batch_scratch_size = 0;
+    // cached CUDA graph of the last graph-mode batch and its signature
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<long long> batch_sig;
 };
 
 namespace {
@@ -41,6 +59,9 @@ using hsc::Control;
 using hsc::PcaScratch;
 
 // Brackets one stage launch with events when the context is profiling.
+struct StageTimer;
+hsc_ctx g_untimed;  // never profiling: stage launches that are not timed
+
 struct StageTimer {
     hsc_ctx *ctx;
     int slot = -1;
@@ -104,7 +125,12 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
     };
     L.ctl = take(sizeof(Control));
     if (need_pca) {
+        // at least kMinPartPixels pixels per partial Gram: a small frame
+        // gets few partials instead of one per SM, whose reduction would
+        // read more bytes than the frame itself
+        constexpr long kMinPartPixels = 2048;
         int np = hsc::moments_partitions(ctx->sm_count);
+        np = (int)std::min<long>(np, std::max<long>(1, (N + kMinPartPixels - 1) / kMinPartPixels));
         size_t per = (size_t)B * B * sizeof(float);
         size_t budget = (size_t)64 << 20;
         if ((size_t)np * per > budget) np = (int)std::max<size_t>(1, budget / per);
@@ -242,6 +268,45 @@ hsc_status check_knn(hsc_ctx *ctx, const hsc_knn_params *p, int n_classes, int H
         return fail(ctx, HSC_ERR_INVALID_ARG,
                     "KNN: K exceeds the smallest window (min(ceil(R/2), H) * W candidates)%s");
     return HSC_OK;
+}
+
+constexpr int kMaxSlots = 64;
+
+// The whole path for one frame on one stream with one scratch carve-up.
+cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float *cube, int B,
+                                  int H, int W, const hsc_svm_model *model,
+                                  const hsc_knn_params *params, unsigned flags, int32_t *labels,
+                                  float *out_probs, float *I, float *Pm, cudaStream_t st,
+                                  bool timed)
+{
+    const long N = (long)H * W;
+    const int k = model->n_classes;
+    cudaError_t e;
+    {
+        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_MOMENTS, 4);
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, st);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_JACOBI, 1);
+        e = hsc::launch_jacobi(B, s, st);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_PROJECT_SVM, 1);
+        e = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model,
+                                    (flags & HSC_SVM_COUPLE_F64) != 0, Pm, nullptr, s.ctl,
+                                    ctx->sm_count, st);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_NORMALIZE, 1);
+        e = hsc::launch_normalize(I, I, N, s.ctl, st);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_KNN, 1);
+        e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
+                            out_probs, labels, nullptr, s.ctl, st,
+                            params->search != HSC_KNN_SEARCH_FULL);
+    }
+    return e;
 }
 
 }  // namespace
@@ -386,6 +451,14 @@ void hsc_ctx_destroy(hsc_ctx *ctx)
         delete[] ctx->ev;
         delete[] ctx->rec_stage;
     }
+    for (int i = 0; i < ctx->n_slots; ++i) {
+        cudaStreamSynchronize(ctx->slot_streams[i]);
+        cudaStreamDestroy(ctx->slot_streams[i]);
+        cudaEventDestroy(ctx->slot_events[i]);
+    }
+    if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
+    if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
+    if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -423,6 +496,20 @@ hsc_status hsc_sync(hsc_ctx *ctx)
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "status readback");
         bits |= *ctx->h_status;
+    }
+    if (ctx->batch_scratch) {
+        Control ctl[kMaxSlots];
+        e = cudaMemcpy(ctl, ctx->batch_scratch, sizeof ctl, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            for (int i = 0; i < kMaxSlots; ++i) bits |= ctl[i].status;
+        if (e == cudaSuccess) {
+            for (int i = 0; i < kMaxSlots && e == cudaSuccess; ++i)
+                if (ctl[i].status)
+                    e = cudaMemsetAsync(&reinterpret_cast<Control *>(ctx->batch_scratch)[i].status, 0,
+                                        sizeof(unsigned), ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch status readback");
     }
     if (bits & (hsc::ST_NONFINITE_CUBE | hsc::ST_NONFINITE_MAP))
         return fail(ctx, HSC_ERR_NONFINITE, "a NaN or Inf was found in an input map%s");
@@ -571,33 +658,503 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     char *base = static_cast<char *>(ctx->scratch);
     float *I = one_band ? one_band : reinterpret_cast<float *>(base + L.tmpI);
     float *Pm = probs ? probs : reinterpret_cast<float *>(base + L.tmpP);
-    cudaError_t e;
-    {
-        StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
-        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
-    }
-    if (e == cudaSuccess) {
-        StageTimer t(ctx, HSC_STAGE_JACOBI, 1);
-        e = hsc::launch_jacobi(B, s, ctx->stream);
-    }
-    if (e == cudaSuccess) {
-        StageTimer t(ctx, HSC_STAGE_PROJECT_SVM, 1);
-        e = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model,
-                                    (flags & HSC_SVM_COUPLE_F64) != 0, Pm, nullptr, s.ctl,
-                                    ctx->sm_count, ctx->stream);
-    }
-    if (e == cudaSuccess) {
-        StageTimer t(ctx, HSC_STAGE_NORMALIZE, 1);
-        e = hsc::launch_normalize(I, I, N, s.ctl, ctx->stream);
-    }
-    if (e == cudaSuccess) {
-        StageTimer t(ctx, HSC_STAGE_KNN, 1);
-        e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
-                            out_probs, labels, nullptr, s.ctl, ctx->stream,
-                            params->search != HSC_KNN_SEARCH_FULL);
-    }
+    cudaError_t e = launch_classify_frame(ctx, s, cube, B, H, W, model, params, flags, labels,
+                                          out_probs, I, Pm, ctx->stream, true);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_classify launch");
     return HSC_OK;
+}
+
+
+hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frames, int B,
+                              const hsc_svm_model *model, const hsc_knn_params *params,
+                              unsigned flags)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!frames || n_frames < 1) return fail(ctx, HSC_ERR_INVALID_ARG, "no frames%s");
+    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_BATCH_GRAPH))
+        return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
+    if ((st = check_model(ctx, model, B))) return st;
+    const int k = model->n_classes;
+    size_t slot_bytes = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const hsc_frame &fr = frames[f];
+        if ((st = check_cube(ctx, fr.cube, B, fr.H, fr.W))) return st;
+        if ((st = check_knn(ctx, params, k, fr.H, fr.W))) return st;
+        if (!fr.labels) return fail(ctx, HSC_ERR_INVALID_ARG, "a frame has no labels buffer%s");
+        Layout L = make_layout(ctx, B, (long)fr.H * fr.W, k, true, true, true);
+        slot_bytes = std::max(slot_bytes, L.total);
+    }
+    const int S = std::min(n_frames, kMaxSlots);
+    const size_t ctl_bytes = align_up((size_t)kMaxSlots * sizeof(Control));
+    const size_t need = ctl_bytes + (size_t)S * slot_bytes;
+    cudaError_t e;
+    // streams and events of the pool
+    for (int i = ctx->n_slots; i < S; ++i) {
+        e = cudaStreamCreateWithFlags(&ctx->slot_streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->slot_events[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch stream pool");
+        ctx->n_slots = i + 1;
+    }
+    if (!ctx->fork_event) {
+        e = cudaEventCreateWithFlags(&ctx->fork_event, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch fork event");
+    }
+    if (need > ctx->batch_scratch_size) {
+        if (ctx->cap && need + ctx->scratch_size > ctx->cap) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "batch scratch of %zu bytes exceeds the cap", need);
+            ctx->last_error = buf;
+            return HSC_ERR_OOM;
+        }
+        e = cudaStreamSynchronize(ctx->stream);
+        for (int i = 0; i < ctx->n_slots && e == cudaSuccess; ++i) e = cudaStreamSynchronize(ctx->slot_streams[i]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch scratch sync");
+        if (ctx->batch_scratch) {
+            Control old[kMaxSlots];
+            e = cudaMemcpy(old, ctx->batch_scratch, sizeof old, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "batch status readback");
+            for (int i = 0; i < kMaxSlots; ++i) ctx->host_status |= old[i].status;
+            cudaFree(ctx->batch_scratch);
+            ctx->batch_scratch = nullptr;
+            ctx->batch_scratch_size = 0;
+        }
+        if (ctx->batch_exec) {
+            cudaGraphExecDestroy(ctx->batch_exec);
+            ctx->batch_exec = nullptr;
+            ctx->batch_sig.clear();
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HSC_ERR_OOM, "cudaMalloc of the batch scratch failed%s");
+        }
+        e = cudaMemsetAsync(p, 0, ctl_bytes, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+        ctx->batch_scratch = p;
+        ctx->batch_scratch_size = need;
+    }
+    // signature of this call (graph mode replays only an identical batch)
+    std::vector<long long> sig;
+    if (flags & HSC_BATCH_GRAPH) {
+        sig.reserve(16 + 8 * (size_t)n_frames);
+        sig.push_back(n_frames);
+        sig.push_back(B);
+        sig.push_back((long long)flags);
+        sig.push_back(reinterpret_cast<long long>(model->w));
+        sig.push_back(reinterpret_cast<long long>(model->b));
+        sig.push_back(reinterpret_cast<long long>(model->platt_a));
+        sig.push_back(reinterpret_cast<long long>(model->platt_b));
+        sig.push_back(k);
+        sig.push_back(params->k);
+        sig.push_back(params->window_rows);
+        int lam_bits;
+        memcpy(&lam_bits, &params->lambda, sizeof lam_bits);
+        sig.push_back(lam_bits);
+        sig.push_back(params->search);
+        sig.push_back(reinterpret_cast<long long>(ctx->stream));
+        sig.push_back(reinterpret_cast<long long>(ctx->batch_scratch));
+        for (int f = 0; f < n_frames; ++f) {
+            const hsc_frame &fr = frames[f];
+            sig.push_back(reinterpret_cast<long long>(fr.cube));
+            sig.push_back(((long long)fr.H << 32) | (unsigned)fr.W);
+            sig.push_back(reinterpret_cast<long long>(fr.labels));
+            sig.push_back(reinterpret_cast<long long>(fr.out_probs));
+            sig.push_back(reinterpret_cast<long long>(fr.one_band));
+            sig.push_back(reinterpret_cast<long long>(fr.probs));
+        }
+        if (ctx->batch_exec && sig == ctx->batch_sig) {
+            e = cudaGraphLaunch(ctx->batch_exec, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+            return HSC_OK;
+        }
+        e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+    }
+    // fork, one frame per slot in turn, join
+    e = cudaEventRecord(ctx->fork_event, ctx->stream);
+    for (int i = 0; i < S && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(ctx->slot_streams[i], ctx->fork_event, 0);
+    char *base = static_cast<char *>(ctx->batch_scratch);
+    for (int f = 0; f < n_frames && e == cudaSuccess; ++f) {
+        const hsc_frame &fr = frames[f];
+        const int slot = f % S;
+        const long N = (long)fr.H * fr.W;
+        Layout L = make_layout(ctx, B, N, k, true, true, true);
+        // carve the slot: its control block lives in the contiguous array
+        hsc_ctx view;
+        view.scratch = base + ctl_bytes + (size_t)slot * slot_bytes;
+        PcaScratch s = carve(&view, L);
+        view.scratch = nullptr;
+        s.ctl = reinterpret_cast<Control *>(base) + slot;
+        char *sb = base + ctl_bytes + (size_t)slot * slot_bytes;
+        float *I = fr.one_band ? fr.one_band : reinterpret_cast<float *>(sb + L.tmpI);
+        float *Pm = fr.probs ? fr.probs : reinterpret_cast<float *>(sb + L.tmpP);
+        e = launch_classify_frame(ctx, s, fr.cube, B, fr.H, fr.W, model, params, flags, fr.labels,
+                                  fr.out_probs, I, Pm, ctx->slot_streams[slot], false);
+    }
+    for (int i = 0; i < S && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(ctx->slot_events[i], ctx->slot_streams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->slot_events[i], 0);
+    }
+    if (flags & HSC_BATCH_GRAPH) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) {
+            if (ctx->batch_exec) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(ctx->batch_exec, graph, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(ctx->batch_exec);
+                    ctx->batch_exec = nullptr;
+                }
+            }
+            if (!ctx->batch_exec) e = cudaGraphInstantiate(&ctx->batch_exec, graph, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ctx->batch_exec, ctx->stream);
+            if (e == cudaSuccess) ctx->batch_sig = sig;
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_classify_batch launch");
+    return HSC_OK;
+}
+
+}  // extern "C"
+
+// ===================================================================== serving
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServerReq {
+    uint64_t ticket = 0;
+    hsc_request req{};
+    size_t bytes = 0;
+    double t_submit = 0.0, t_done = 0.0;
+    hsc_status status = HSC_OK;
+    bool done = false;
+    void *dev = nullptr;
+};
+
+}  // namespace
+
+struct hsc_server {
+    int device = 0;
+    size_t budget = 0;
+    int n_slots = 0;
+    hsc_ctx ctx;  // device properties and the launch helpers; no scratch of its own
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t streams[kMaxSlots] = {};
+    cudaEvent_t events[kMaxSlots] = {};
+    unsigned *h_status = nullptr;  // pinned, one status word per slot
+    std::vector<std::shared_ptr<ServerReq>> slots;
+    std::deque<std::shared_ptr<ServerReq>> queue;
+    std::map<uint64_t, std::shared_ptr<ServerReq>> live;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread th;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    size_t bytes_in_use = 0, peak_bytes = 0;
+    int inflight = 0, peak_inflight = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, pixels = 0;
+    double t_first = -1.0, t_last = 0.0;
+    std::vector<double> lat_ms;
+};
+
+namespace {
+
+struct ReqLayout {
+    Layout L;
+    size_t cube, I, P, O, lab, scratch, total;
+};
+
+ReqLayout request_layout(hsc_server *srv, const hsc_request &r)
+{
+    ReqLayout R{};
+    const long N = (long)r.H * r.W;
+    const int k = r.model.n_classes;
+    R.L = make_layout(&srv->ctx, r.B, N, k, true, false, false);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off = align_up(off + b);
+        return o;
+    };
+    R.cube = take(sizeof(float) * (size_t)r.B * N);
+    R.I = take(sizeof(float) * (size_t)N);
+    R.P = take(sizeof(float) * (size_t)k * N);
+    R.O = take(sizeof(float) * (size_t)k * N);
+    R.lab = take(sizeof(int32_t) * (size_t)N);
+    R.scratch = take(R.L.total);
+    R.total = off;
+    return R;
+}
+
+// Enqueue one admitted request on its slot's stream (dispatcher thread).
+void launch_request(hsc_server *srv, int slot, ServerReq &q)
+{
+    const hsc_request &r = q.req;
+    cudaStream_t st = srv->streams[slot];
+    ReqLayout R = request_layout(srv, r);
+    const long N = (long)r.H * r.W;
+    const int k = r.model.n_classes;
+    cudaError_t e = cudaMallocFromPoolAsync(&q.dev, R.total, srv->pool, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        q.dev = nullptr;
+        q.status = HSC_ERR_OOM;
+        cudaEventRecord(srv->events[slot], st);
+        return;
+    }
+    char *b = static_cast<char *>(q.dev);
+    hsc_ctx view;
+    view.scratch = b + R.scratch;
+    PcaScratch s = carve(&view, R.L);
+    view.scratch = nullptr;
+    float *cube = reinterpret_cast<float *>(b + R.cube);
+    float *I = reinterpret_cast<float *>(b + R.I);
+    float *P = reinterpret_cast<float *>(b + R.P);
+    float *O = reinterpret_cast<float *>(b + R.O);
+    int32_t *lab = reinterpret_cast<int32_t *>(b + R.lab);
+    e = cudaMemsetAsync(s.ctl, 0, sizeof(Control), st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cube, r.cube, sizeof(float) * (size_t)r.B * N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_classify_frame(&srv->ctx, s, cube, r.B, r.H, r.W, &r.model, &r.params, r.flags,
+                                  lab, r.out_probs ? O : nullptr, I, P, st, false);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r.labels, lab, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && r.out_probs)
+        e = cudaMemcpyAsync(r.out_probs, O, sizeof(float) * (size_t)k * N, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&srv->h_status[slot], &s.ctl->status, sizeof(unsigned),
+                            cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        q.status = HSC_ERR_CUDA;
+    }
+    cudaFreeAsync(q.dev, st);
+    cudaEventRecord(srv->events[slot], st);
+}
+
+hsc_status status_from_bits(unsigned bits)
+{
+    if (bits & (hsc::ST_NONFINITE_CUBE | hsc::ST_NONFINITE_MAP)) return HSC_ERR_NONFINITE;
+    if (bits & hsc::ST_NOT_CONVERGED) return HSC_ERR_NOT_CONVERGED;
+    if (bits & hsc::ST_TIMEOUT) return HSC_ERR_TIMEOUT;
+    if (bits & hsc::ST_KNN_SHORT) return HSC_ERR_INVALID_ARG;
+    return HSC_OK;
+}
+
+void dispatcher(hsc_server *srv)
+{
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    for (;;) {
+        bool progressed = false;
+        // retire requests whose GPU work has finished
+        for (int i = 0; i < srv->n_slots; ++i) {
+            auto &q = srv->slots[i];
+            if (!q) continue;
+            cudaError_t e = cudaEventQuery(srv->events[i]);
+            if (e == cudaErrorNotReady) continue;
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                if (q->status == HSC_OK) q->status = HSC_ERR_CUDA;
+            } else if (q->status == HSC_OK) {
+                q->status = status_from_bits(srv->h_status[i]);
+            }
+            q->t_done = now_s();
+            q->done = true;
+            srv->bytes_in_use -= q->bytes;
+            --srv->inflight;
+            if (q->status == HSC_OK) {
+                ++srv->completed;
+                srv->pixels += (int64_t)q->req.H * q->req.W;
+                srv->lat_ms.push_back(1e3 * (q->t_done - q->t_submit));
+                srv->t_last = q->t_done;
+            } else {
+                ++srv->failed;
+            }
+            q.reset();
+            progressed = true;
+        }
+        if (progressed) srv->cv_done.notify_all();
+        // admit the oldest waiting requests while a slot and memory are free
+        while (!srv->queue.empty()) {
+            auto q = srv->queue.front();
+            if (srv->bytes_in_use + q->bytes > srv->budget) break;
+            int slot = -1;
+            for (int i = 0; i < srv->n_slots; ++i)
+                if (!srv->slots[i]) {
+                    slot = i;
+                    break;
+                }
+            if (slot < 0) break;
+            srv->queue.pop_front();
+            srv->slots[slot] = q;
+            srv->bytes_in_use += q->bytes;
+            srv->peak_bytes = std::max(srv->peak_bytes, srv->bytes_in_use);
+            ++srv->inflight;
+            srv->peak_inflight = std::max(srv->peak_inflight, srv->inflight);
+            lk.unlock();
+            launch_request(srv, slot, *q);
+            lk.lock();
+            progressed = true;
+        }
+        if (srv->stop && srv->queue.empty() && srv->inflight == 0) break;
+        if (!progressed) {
+            if (srv->inflight > 0) {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                lk.lock();
+            } else {
+                srv->cv_work.wait(lk, [&] { return srv->stop || !srv->queue.empty(); });
+            }
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+hsc_status hsc_server_create(int device, size_t hbm_budget_bytes, int max_inflight,
+                             hsc_server **out)
+{
+    if (!out || max_inflight < 1 || max_inflight > kMaxSlots) return HSC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HSC_ERR_INVALID_ARG;
+    }
+    std::unique_ptr<hsc_server> srv(new hsc_server());
+    srv->device = device;
+    srv->n_slots = max_inflight;
+    srv->slots.resize(max_inflight);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&srv->ctx.sm_count, cudaDevAttrMultiProcessorCount, device);
+    srv->ctx.device = device;
+    size_t free_b = 0, total_b = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    srv->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.8 * (double)free_b);
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (e == cudaSuccess) e = cudaMemPoolCreate(&srv->pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t keep = srv->budget;
+        e = cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    for (int i = 0; i < max_inflight && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&srv->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&srv->events[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaMallocHost(&srv->h_status, sizeof(unsigned) * kMaxSlots);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (int i = 0; i < max_inflight; ++i) {
+            if (srv->streams[i]) cudaStreamDestroy(srv->streams[i]);
+            if (srv->events[i]) cudaEventDestroy(srv->events[i]);
+        }
+        if (srv->pool) cudaMemPoolDestroy(srv->pool);
+        return HSC_ERR_CUDA;
+    }
+    srv->th = std::thread(dispatcher, srv.get());
+    *out = srv.release();
+    return HSC_OK;
+}
+
+hsc_status hsc_server_submit(hsc_server *srv, const hsc_request *req, uint64_t *ticket)
+{
+    if (!srv || !req || !ticket) return HSC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    hsc_ctx *c = &srv->ctx;
+    hsc_status st;
+    if ((st = check_cube(c, req->cube, req->B, req->H, req->W))) return st;
+    if ((st = check_model(c, &req->model, req->B))) return st;
+    if ((st = check_knn(c, &req->params, req->model.n_classes, req->H, req->W))) return st;
+    if (!req->labels) return HSC_ERR_INVALID_ARG;
+    if (req->flags & ~(unsigned)HSC_SVM_COUPLE_F64) return HSC_ERR_INVALID_ARG;
+    auto q = std::make_shared<ServerReq>();
+    q->req = *req;
+    q->bytes = request_layout(srv, *req).total;
+    if (q->bytes > srv->budget) return HSC_ERR_OOM;
+    q->ticket = srv->next_ticket++;
+    q->t_submit = now_s();
+    if (srv->t_first < 0.0) srv->t_first = q->t_submit;
+    ++srv->submitted;
+    srv->queue.push_back(q);
+    srv->live[q->ticket] = q;
+    *ticket = q->ticket;
+    srv->cv_work.notify_one();
+    return HSC_OK;
+}
+
+hsc_status hsc_server_wait(hsc_server *srv, uint64_t ticket, double *latency_ms)
+{
+    if (!srv) return HSC_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->live.find(ticket);
+    if (it == srv->live.end()) return HSC_ERR_INVALID_ARG;
+    std::shared_ptr<ServerReq> q = it->second;
+    srv->cv_done.wait(lk, [&] { return q->done; });
+    if (latency_ms) *latency_ms = 1e3 * (q->t_done - q->t_submit);
+    srv->live.erase(ticket);
+    return q->status;
+}
+
+hsc_status hsc_server_stats_get(hsc_server *srv, hsc_server_stats *out)
+{
+    if (!srv || !out) return HSC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    hsc_server_stats st{};
+    st.submitted = srv->submitted;
+    st.completed = srv->completed;
+    st.failed = srv->failed;
+    st.pixels = srv->pixels;
+    std::vector<double> l = srv->lat_ms;
+    std::sort(l.begin(), l.end());
+    if (!l.empty()) {
+        st.p50_ms = l[l.size() / 2];
+        st.p99_ms = l[std::min(l.size() - 1, (size_t)(0.99 * (double)l.size()))];
+        st.max_ms = l.back();
+    }
+    st.busy_s = srv->t_first >= 0.0 ? srv->t_last - srv->t_first : 0.0;
+    st.peak_inflight = srv->peak_inflight;
+    st.peak_bytes = srv->peak_bytes;
+    *out = st;
+    return HSC_OK;
+}
+
+void hsc_server_destroy(hsc_server *srv)
+{
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv_work.notify_all();
+    if (srv->th.joinable()) srv->th.join();
+    cudaSetDevice(srv->device);
+    for (int i = 0; i < srv->n_slots; ++i) {
+        cudaStreamSynchronize(srv->streams[i]);
+        cudaStreamDestroy(srv->streams[i]);
+        cudaEventDestroy(srv->events[i]);
+    }
+    if (srv->h_status) cudaFreeHost(srv->h_status);
+    if (srv->pool) cudaMemPoolDestroy(srv->pool);
+    delete srv;
 }
 
 }  // extern "C"

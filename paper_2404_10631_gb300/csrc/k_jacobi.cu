@@ -8,9 +8,9 @@
 //     zeroes a_pq (the same rotation the paper's classical Jacobi applies to
 //     its pivot); the update A <- J^T A J is done per 2x2 block of pairs so a
 //     round is one pass over A (upper triangle) and V, both in shared memory.
-//     The first round of sweeps stops after two sweeps (or earlier once every
+//     The first round of sweeps stops after one sweep (or earlier once every
 //     off-diagonal entry is at most the largest diagonal entry): an FP32
-//     sweep costs about as much as ten FP64 refinement steps below.
+//     sweep costs more than the dozen FP64 refinement steps it saves.
 //  2. FP64 refinement of the leading vector against the FP64 covariance:
 //     with (theta_j, V_j) the FP32 eigenpairs and v the current leading
 //     vector, r = C v - rho v (rho = v^T C v) and
@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kJacThreads = 1024;
 constexpr int kMaxPairs = 512;           // Bp <= 1024
-constexpr int kMaxRefine = 40;
+constexpr int kMaxRefine = 64;
 constexpr size_t kJacSmemLimit = 190 * 1024;  // + ~33 KB static shared
 
 struct JacParams {
@@ -81,17 +81,6 @@ __device__ __forceinline__ void tri_of(int idx, int P, int &k, int &l)
     l = k + (idx - (k * P - k * (k - 1) / 2));
 }
 
-__device__ double block_sum(double v, double *red)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    return t;
-}
-
 __device__ float block_maxf(float v, float *red)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -118,7 +107,6 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
 
     __shared__ float cs[kMaxPairs], sn[kMaxPairs];
     __shared__ int pp[kMaxPairs], qq[kMaxPairs];
-    __shared__ double red[32];
     __shared__ float fred[32];
     __shared__ double s_scale;
 
@@ -157,10 +145,10 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
     float stop = prm.stop_tol;
     bool converged = false;
     int refine_iters = 0;
-    __shared__ double sv[HSC_MAX_BANDS], sw[HSC_MAX_BANDS], stt[HSC_MAX_BANDS];
-    __shared__ float sr[HSC_MAX_BANDS];
-    __shared__ int s_lead;
-    __shared__ double s_rho, s_rn;
+    __shared__ double sv[HSC_MAX_BANDS], sw[HSC_MAX_BANDS];
+    __shared__ float sr[HSC_MAX_BANDS], stf[HSC_MAX_BANDS];
+    __shared__ int s_lead, flag_conv;
+    __shared__ double s_rho, s_rn, s_inv_rn;
     // Phase 0 sweeps to a loose FP32 tolerance; phase 1 (only if the FP64
     // refinement has not converged) sweeps on to a tight one and refines again.
     long long t_sweep = 0, t_refine = 0;
@@ -249,6 +237,13 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
     long long t1 = clock64();
     t_sweep += t1 - t0;
     // ---- 2. FP64 refinement of the leading vector
+    // GB300's FP64 pipe is narrow and its divide/sqrt are long dependent
+    // chains, so FP64 is spent only where it matters: C v (eight threads per
+    // row), v^T v, v^T w and ||r||^2 (one warp), and the update of v. The
+    // Rayleigh quotient uses a Newton-Raphson reciprocal (FP32 seed, two FP64
+    // Newton steps y <- y (2 - x y)); v is not renormalised between steps
+    // (rho divides by v^T v), convergence is tested on squared norms, and the
+    // correction's direction and length are FP32.
     if (tid == 0) {
         int lead = 0;
         for (int j = 1; j < B; ++j)
@@ -257,76 +252,110 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restr
     }
     __syncthreads();
     const int lead = s_lead;
+    const int warp = tid >> 5, lane = tid & 31;
+    auto warp0_sum = [&](auto f) -> double {  // warp 0 only; all its lanes get the sum
+        double part = 0.0;
+        for (int i = lane; i < B; i += 32) part += f(i);
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        return part;
+    };
+    auto recip = [](double x) -> double {  // Newton-Raphson reciprocal
+        double y = (double)(1.0f / (float)x);
+        y = y * fma(-x, y, 2.0);
+        y = y * fma(-x, y, 2.0);
+        return y;
+    };
     for (int i = tid; i < B; i += nthr) sv[i] = (double)V[i * ld + lead];
     __syncthreads();
-    {
-        double nn = 0.0;
-        for (int i = tid; i < B; i += nthr) nn += sv[i] * sv[i];
-        nn = block_sum(nn, red);
-        double inv = 1.0 / sqrt(nn);
-        __syncthreads();
-        for (int i = tid; i < B; i += nthr) sv[i] *= inv;
-        __syncthreads();
-    }
-    const int warp = tid >> 5, lane = tid & 31, nwarp = nthr >> 5;
+    // Per step: C v in FP64, v^T v and v^T w in one fused FP64 reduction, the
+    // residual's elements in FP64 but its squared norm in FP32.
+    const int row_sub = tid & 7;
     for (int it = 0; it <= kMaxRefine; ++it) {
         refine_iters = it;
-        // w = C v
-        for (int i = warp; i < B; i += nwarp) {
+        // w = C v: eight threads per row (three shuffle levels), so the FP64
+        // instruction count stays near the B^2 / 32 floor
+        for (int i0 = 0; i0 < B; i0 += nthr / 8) {
+            const int i = i0 + (tid >> 3);
             double a = 0.0;
-            for (int j = lane; j < B; j += 32) a += C[(size_t)i * B + j] * sv[j];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) sw[i] = a;
+            if (i < B)  // C symmetric: C[j][i], consecutive i across threads
+                for (int j = row_sub; j < B; j += 8) a = fma(C[(size_t)j * B + i], sv[j], a);
+            a += __shfl_xor_sync(0xffffffffu, a, 1);
+            a += __shfl_xor_sync(0xffffffffu, a, 2);
+            a += __shfl_xor_sync(0xffffffffu, a, 4);
+            if (i < B && row_sub == 0) sw[i] = a;
         }
         __syncthreads();
-        double rho = 0.0;
-        for (int i = tid; i < B; i += nthr) rho += sv[i] * sw[i];
-        rho = block_sum(rho, red);
-        double rn = 0.0;
-        for (int i = tid; i < B; i += nthr) {
-            double ri = sw[i] - rho * sv[i];
-            sw[i] = ri;  // w now holds the residual r
-            rn += ri * ri;
+        if (warp == 0) {
+            double vv = 0.0, vw = 0.0;
+            for (int i = lane; i < B; i += 32) {
+                vv = fma(sv[i], sv[i], vv);
+                vw = fma(sv[i], sw[i], vw);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vv += __shfl_xor_sync(0xffffffffu, vv, o);
+                vw += __shfl_xor_sync(0xffffffffu, vw, o);
+            }
+            const double rho = vw * recip(vv);
+            float r2 = 0.f;
+            for (int i = lane; i < B; i += 32) {
+                const float ri = (float)fma(-rho, sv[i], sw[i]);
+                r2 = fmaf(ri, ri, r2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+            if (lane == 0) {
+                const double cnorm = fabs(rho) > scale ? fabs(rho) : scale;
+                const float tol = (float)(1e-13 * cnorm);
+                s_rho = rho;
+                s_rn = (double)r2;
+                flag_conv = ((double)r2 <= (double)tol * (double)tol * vv) ? 1 : 0;
+            }
         }
-        rn = sqrt(block_sum(rn, red));
-        if (tid == 0) {
-            s_rho = rho;
-            s_rn = rn;
-        }
-        double cnorm = fabs(rho) > scale ? fabs(rho) : scale;
-        if (rn <= 1e-13 * cnorm || rn == 0.0) {
+        __syncthreads();
+        if (flag_conv) {
             converged = true;
             break;
         }
         if (it == kMaxRefine) break;
+        const double rho = s_rho;
+        const float rn = sqrtf((float)s_rn);
+        const float inv_rn = 1.0f / rn;
         // unit residual direction in FP32 (the correction's direction only)
-        const double inv_rn = 1.0 / rn;
-        for (int i = tid; i < B; i += nthr) sr[i] = (float)(sw[i] * inv_rn);
+        for (int i = tid; i < B; i += nthr) sr[i] = (float)fma(-rho, sv[i], sw[i]) * inv_rn;
         __syncthreads();
-        // t_j = (V_j^T r) / (rho - theta_j)
+        // t_j = (V_j^T r) / (rho - theta_j), FP32, relative to ||r|| / scale
+        const float rho_s = (float)(rho / scale);
         for (int j = tid; j < B; j += nthr) {
             float g = 0.f;
             for (int i = 0; i < B; ++i) g = fmaf(V[i * ld + j], sr[i], g);
-            double th = (double)A[j * ld + j] * scale;
-            double den = rho - th;
-            stt[j] = (j == lead || fabs(den) <= 1e-12 * cnorm) ? 0.0 : rn * (double)g / den;
+            const float den = rho_s - A[j * ld + j];  // in the scaled units of A
+            stf[j] = (j == lead || fabsf(den) <= 1e-6f * fmaxf(fabsf(rho_s), 1.f))
+                         ? 0.f : __fdividef(g, den);
         }
         __syncthreads();
-        // v += sum_j t_j V_j
-        for (int i = warp; i < B; i += nwarp) {
-            double a = 0.0;
-            for (int j = lane; j < B; j += 32) a += stt[j] * (double)V[i * ld + j];
-            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-            if (lane == 0) sv[i] += a;
+        // v += (||r|| / scale) sum_j t_j V_j : FP32 sum per row, FP64 update
+        const double step = (double)(rn / (float)scale);
+        for (int i = tid; i < B; i += nthr) {
+            float a = 0.f;
+            for (int j = 0; j < B; ++j) a = fmaf(stf[j], V[i * ld + j], a);
+            sv[i] = fma(step, (double)a, sv[i]);
         }
-        __syncthreads();
-        double nn = 0.0;
-        for (int i = tid; i < B; i += nthr) nn += sv[i] * sv[i];
-        nn = block_sum(nn, red);
-        double inv = 1.0 / sqrt(nn);
-        for (int i = tid; i < B; i += nthr) sv[i] *= inv;
         __syncthreads();
     }
+    // normalise once: inverse square root by Newton-Raphson (FP32 seed, two
+    // FP64 steps y <- y (3 - x y^2) / 2)
+    if (warp == 0) {
+        const double vv = warp0_sum([&](int i) { return sv[i] * sv[i]; });
+        if (lane == 0) {
+            double y = (double)rsqrtf((float)vv);
+            y = y * fma(-0.5 * vv * y, y, 1.5);
+            y = y * fma(-0.5 * vv * y, y, 1.5);
+            s_inv_rn = y;
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < B; i += nthr) sv[i] *= s_inv_rn;
     __syncthreads();
     t_refine += clock64() - t1;
     stop = prm.stop_tol_final;
@@ -375,7 +404,7 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
     prm.rot_tol = 1e-7f;
     prm.stop_tol = 1.0f;
     prm.stop_tol_final = 1e-2f;
-    prm.phase0_sweeps = 2;
+    prm.phase0_sweeps = 1;
     size_t need = 2 * (size_t)prm.n * (prm.n + 1) * sizeof(float);
     prm.use_smem = need <= kJacSmemLimit;
     size_t smem = prm.use_smem ? need : 0;

@@ -46,7 +46,8 @@ def main(argv=None):
         else:
             hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam)
     ctx.sync()
-    print("ok", a.op, ctx.pca_diagnostics())
+    print("ok", a.op, "jacobi sweeps, refine iters, sweep cycles, refine cycles:",
+          ctx.pca_diagnostics(cycles=True))
 
 
 if __name__ == "__main__":

@@ -9,12 +9,16 @@ sharing any of the method.
 
 from .hsi import (  # noqa: F401
     CONFIGS,
+    SEEDS,
     Frame,
     SvmModel,
     endmembers,
+    make_batch,
     make_frame,
     make_config,
+    make_serving_pool,
     ovo_pairs,
+    serving_arrivals,
     svm_from_endmembers,
     voronoi_labels,
 )

@@ -203,3 +203,41 @@ def make_batch(n_frames: int = 256, seed: int = SEEDS[3], side_lo: int = 40,
     return [make_frame(seed * 1000 + f, int(s), int(s), B, k=k, sigma=sigma,
                        K=16, window_rows=7, lam=1.0, spectra=spectra)
             for f, s in enumerate(sides)]
+
+
+def make_serving_pool(n_snapshot: int = 24, n_pushbroom: int = 6, seed: int = SEEDS[5],
+                      k: int = 4, pushbroom_scale: float = 1.0) -> List[Frame]:
+    """Request frames of the serving stream, each with its own class spectra
+    (hence its own SVM model) and K drawn from {16, 40}: snapshot cubes
+    (40-64 px square, 125 bands, sigma 0.03, window 7 rows) and pushbroom
+    cubes (H 384-640 x W 320-512 px scaled by ``pushbroom_scale``, 128 bands,
+    sigma 0.02, window 14 rows). The first ``n_snapshot`` are snapshots."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_snapshot + n_pushbroom):
+        K = int(rng.choice([16, 40]))
+        if i < n_snapshot:
+            s = int(rng.integers(40, 65))
+            out.append(make_frame(seed * 1000 + i, s, s, 125, k=k, sigma=0.03, K=K,
+                                  window_rows=7, lam=1.0))
+        else:
+            H = max(16, int(round(int(rng.integers(384, 641)) * pushbroom_scale)))
+            W = max(16, int(round(int(rng.integers(320, 513)) * pushbroom_scale)))
+            out.append(make_frame(seed * 1000 + i, H, W, 128, k=k, sigma=0.02, K=K,
+                                  window_rows=14, lam=1.0))
+    return out
+
+
+def serving_arrivals(n_requests: int, rate_hz: float, n_snapshot: int, n_pushbroom: int,
+                     snapshot_share: float = 0.7, seed: int = SEEDS[5]):
+    """Poisson arrival times (seconds from 0) at ``rate_hz`` and, per request,
+    the index of its frame in a serving pool: a snapshot with probability
+    ``snapshot_share``, else a pushbroom cube, uniform within each kind."""
+    rng = np.random.Generator(np.random.PCG64(seed + 17))
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_requests))
+    snap = rng.random(n_requests) < snapshot_share
+    idx = np.where(snap, rng.integers(0, n_snapshot, size=n_requests),
+                   n_snapshot + rng.integers(0, max(1, n_pushbroom), size=n_requests))
+    if n_pushbroom == 0:
+        idx = rng.integers(0, n_snapshot, size=n_requests)
+    return t, idx

@@ -1,0 +1,114 @@
+"""hsc_classify_batch: every frame's outputs are bit-identical to what
+hsc_classify gives for that frame alone (uneven snapshot frames, shared
+model), with and without CUDA-graph replay."""
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def frames_to_device(frames):
+    import torch
+    return [torch.as_tensor(f.cube, device="cuda") for f in frames]
+
+
+def outputs(frames, k):
+    import torch
+    labs = [torch.full(f.cube.shape[1:], -1, dtype=torch.int32, device="cuda") for f in frames]
+    O = [torch.full((k,) + f.cube.shape[1:], -1.0, device="cuda") for f in frames]
+    I = [torch.full(f.cube.shape[1:], -1.0, device="cuda") for f in frames]
+    P = [torch.full((k,) + f.cube.shape[1:], -1.0, device="cuda") for f in frames]
+    return labs, O, I, P
+
+
+def alone(hsc, ctx, f, cube, model):
+    import torch
+    k = f.model.n_classes
+    lab = torch.empty(f.cube.shape[1:], dtype=torch.int32, device="cuda")
+    O = torch.empty((k,) + f.cube.shape[1:], device="cuda")
+    I = torch.empty(f.cube.shape[1:], device="cuda")
+    P = torch.empty((k,) + f.cube.shape[1:], device="cuda")
+    hsc.hsc_classify(ctx, cube, model, f.K, f.window_rows, f.lam, labels=lab, out_probs=O,
+                     one_band=I, probs=P)
+    ctx.sync()  # the context's stream does not order with torch's
+    return lab, O, I, P
+
+
+def assert_same(a, b):
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_frames_alone(hsc, ctx, graph):
+    frames = synth.make_batch(12)
+    # two frames whose pixel count is not a multiple of 4 (scalar loads,
+    # FP32-pipe covariance)
+    frames += [synth.make_frame(77, 41, 43, 125, sigma=0.03, K=16, window_rows=7,
+                                spectra=frames[0].spectra),
+               synth.make_frame(78, 9, 61, 125, sigma=0.03, K=16, window_rows=7,
+                                spectra=frames[0].spectra)]
+    f0 = frames[0]
+    model = hsc.Model.from_host(f0.model)
+    cubes = frames_to_device(frames)
+    labs, O, I, P = outputs(frames, 4)
+    flags = hsc.HSC_BATCH_GRAPH if graph else 0
+    for rep in range(2):  # the second call replays the graph
+        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, flags=flags,
+                               labels=labs, out_probs=O, one_bands=I, probs=P)
+        ctx.sync()
+        for i, f in enumerate(frames):
+            assert_same((labs[i], O[i], I[i], P[i]), alone(hsc, ctx, f, cubes[i], model))
+        ctx.sync()
+
+
+def test_graph_replay_sees_new_data(hsc, ctx):
+    import torch
+    frames = synth.make_batch(6)
+    f0 = frames[0]
+    model = hsc.Model.from_host(f0.model)
+    cubes = frames_to_device(frames)
+    labs, O, I, P = outputs(frames, 4)
+    args = dict(labels=labs, out_probs=O, one_bands=I, probs=P, flags=hsc.HSC_BATCH_GRAPH)
+    hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, **args)
+    ctx.sync()
+    # new contents in the same buffers: the replayed graph must read them
+    other = synth.make_batch(6, seed=4242)
+    for c, f2 in zip(cubes, other):
+        if tuple(c.shape) == f2.cube.shape:
+            c.copy_(torch.as_tensor(f2.cube, device="cuda"))
+        else:
+            c.copy_(torch.flip(c, dims=[1]))
+    hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, **args)
+    ctx.sync()
+    for i, f in enumerate(frames):
+        assert_same((labs[i], O[i], I[i], P[i]), alone(hsc, ctx, f, cubes[i], model))
+
+
+def test_more_frames_than_streams(hsc, ctx):
+    frames = synth.make_batch(70)
+    f0 = frames[0]
+    model = hsc.Model.from_host(f0.model)
+    cubes = frames_to_device(frames)
+    labs = hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam)
+    ctx.sync()
+    for i in (0, 1, 63, 64, 65, 69):
+        ref = alone(hsc, ctx, frames[i], cubes[i], model)[0]
+        np.testing.assert_array_equal(labs[i].cpu().numpy(), ref.cpu().numpy())
+    # labels follow the synthetic regions
+    acc = np.mean([(l.cpu().numpy() == f.truth).mean() for l, f in zip(labs, frames)])
+    assert acc > 0.95
+
+
+def test_batch_rejects_bad_frame(hsc, ctx):
+    import torch
+    frames = synth.make_batch(3)
+    f0 = frames[0]
+    model = hsc.Model.from_host(f0.model)
+    cubes = frames_to_device(frames)
+    cubes[1] = cubes[1][:100].contiguous()  # band count differs
+    with pytest.raises(ValueError):
+        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam)
