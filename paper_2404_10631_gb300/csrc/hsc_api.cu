@@ -109,7 +109,7 @@ hsc_status cuda_fail(hsc_ctx *ctx, cudaError_t e, const char *where)
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, jV, tmpI, tmpP, total;
+    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, total;
     int n_part;
 };
 
@@ -139,14 +139,13 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
         L.gram = take((size_t)np * per);
         L.sums = take(sizeof(float) * (size_t)np * B);
         L.C = take(sizeof(double) * (size_t)B * B);
+        L.C2 = take(sizeof(float) * 2 * (size_t)B * B);
         L.mu = take(sizeof(double) * B);
         L.v1 = take(sizeof(double) * B);
         L.lambda1 = take(sizeof(double));
         L.v1f = take(sizeof(float) * B);
         L.muf = take(sizeof(float) * B);
-        size_t jf = hsc::jacobi_global_floats(B);
-        L.jA = take(sizeof(float) * jf);
-        L.jV = take(sizeof(float) * jf);
+        L.jA = take(sizeof(float) * hsc::jacobi_global_floats(B));
     }
     if (need_I) L.tmpI = take(sizeof(float) * (size_t)N);
     if (need_P) L.tmpP = take(sizeof(float) * (size_t)k * N);
@@ -199,13 +198,13 @@ PcaScratch carve(hsc_ctx *ctx, const Layout &L)
     s.gram_part = reinterpret_cast<float *>(b + L.gram);
     s.sum_part = reinterpret_cast<float *>(b + L.sums);
     s.C = reinterpret_cast<double *>(b + L.C);
+    s.C2 = reinterpret_cast<float2 *>(b + L.C2);
     s.mu = reinterpret_cast<double *>(b + L.mu);
     s.v1 = reinterpret_cast<double *>(b + L.v1);
     s.lambda1 = reinterpret_cast<double *>(b + L.lambda1);
     s.v1f = reinterpret_cast<float *>(b + L.v1f);
     s.muf = reinterpret_cast<float *>(b + L.muf);
     s.jac_A = reinterpret_cast<float *>(b + L.jA);
-    s.jac_V = reinterpret_cast<float *>(b + L.jV);
     s.n_part = L.n_part;
     return s;
 }

@@ -58,13 +58,13 @@ struct PcaScratch {
     float *gram_part;    // n_part x B x B partial Gram of shifted pixels
     float *sum_part;     // n_part x B partial sums of shifted pixels
     double *C;           // B x B covariance
+    float2 *C2;          // B x B covariance as FP32 pairs (hi, lo), hi + lo = C to 2^-48
     double *mu;          // B band means
     double *v1;          // B leading eigenvector
     double *lambda1;     // 1
     float *v1f;          // B
     float *muf;          // B
-    float *jac_A;        // Bp x Bp (only when it does not fit in shared memory)
-    float *jac_V;        // Bp x Bp
+    float *jac_A;        // Jacobi work area (only when it does not fit in shared memory)
     int n_part;
 };
 

@@ -31,7 +31,8 @@ constexpr size_t kShift = 256;
 constexpr size_t kGram = kShift + 256 * ((kMaxBands * 4 + 255) / 256);
 constexpr size_t kSums = kGram + (size_t)kParts * kMaxBands * kMaxBands * 4;
 constexpr size_t kC = kSums + 256 * (((size_t)kParts * kMaxBands * 4 + 255) / 256);
-constexpr size_t kMu = kC + (size_t)kMaxBands * kMaxBands * 8;
+constexpr size_t kC2 = kC + (size_t)kMaxBands * kMaxBands * 8;
+constexpr size_t kMu = kC2 + (size_t)kMaxBands * kMaxBands * 8;
 constexpr size_t kV1 = kMu + 256 * ((kMaxBands * 8 + 255) / 256);
 constexpr size_t kLam = kV1 + 256 * ((kMaxBands * 8 + 255) / 256);
 constexpr size_t kV1f = kLam + 256;
@@ -91,13 +92,13 @@ extern "C" hsc_status hsc_pca_one_band_noalloc(void *cuda_stream, const float *c
     s.gram_part = reinterpret_cast<float *>(base + kGram);
     s.sum_part = reinterpret_cast<float *>(base + kSums);
     s.C = reinterpret_cast<double *>(base + kC);
+    s.C2 = reinterpret_cast<float2 *>(base + kC2);
     s.mu = reinterpret_cast<double *>(base + kMu);
     s.v1 = reinterpret_cast<double *>(base + kV1);
     s.lambda1 = reinterpret_cast<double *>(base + kLam);
     s.v1f = reinterpret_cast<float *>(base + kV1f);
     s.muf = reinterpret_cast<float *>(base + kMuf);
-    s.jac_A = nullptr;  // B <= 128: A and V live in shared memory
-    s.jac_V = nullptr;
+    s.jac_A = nullptr;  // B <= 128: the Jacobi work area lives in shared memory
     s.n_part = kParts;
     (void)up256;
     // the control block keeps the previous call's contents: start from zero

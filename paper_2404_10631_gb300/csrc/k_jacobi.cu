@@ -2,26 +2,32 @@
 // of the B x B covariance, leading eigenvector kept.
 //
 // GB300 design (one CTA, the matrix never leaves the SM):
-//  1. Parallel cyclic Jacobi in FP32: each round applies B/2 disjoint plane
-//     rotations at once (round-robin "circle" pairing, every pair (p,q) met
-//     once per sweep). Each rotation is the symmetric Schur rotation that
-//     zeroes a_pq (the same rotation the paper's classical Jacobi applies to
-//     its pivot); the update A <- J^T A J is done per 2x2 block of pairs so a
-//     round is one pass over A (upper triangle) and V, both in shared memory.
-//     The first round of sweeps stops after one sweep (or earlier once every
-//     off-diagonal entry is at most the largest diagonal entry): an FP32
-//     sweep costs more than the dozen FP64 refinement steps it saves.
+//  1. One sweep of parallel cyclic Jacobi in FP32 on A = C / max diag: each
+//     round applies B/2 disjoint plane rotations at once (round-robin
+//     "circle" pairing, every pair met once per sweep), each the symmetric
+//     Schur rotation that zeroes its a_pq (the rotation the paper's classical
+//     Jacobi applies to its pivot). The update A <- J^T A J is done per 2x2
+//     block of pairs, one pass over the upper triangle of A per round; each
+//     pair's own diagonal block is updated in closed form with its angle. The
+//     eigenvector matrix V = J_0 J_1 ... is NOT accumulated: the round's
+//     (c, s) are logged instead (B^2/2 floats), and after the sweep only the
+//     columns of V for the m = 16 largest diagonal entries of A are rebuilt
+//     by applying the logged rotations to unit vectors, last round first.
 //  2. FP64 refinement of the leading vector against the FP64 covariance:
-//     with (theta_j, V_j) the FP32 eigenpairs and v the current leading
-//     vector, r = C v - rho v (rho = v^T C v) and
-//        v <- v + sum_{j != lead} V_j (V_j^T r) / (rho - theta_j),
-//     i.e. the small-angle Jacobi rotations of the leading pair against every
-//     other pair, taken in FP64 where it matters (C v and the residual).
-//     Repeated until ||r|| <= 1e-13 ||C||, so v1 carries FP64 accuracy while
-//     the O(B^3) sweeps run on the FP32 pipe (GB300's FP64 rate is a small
-//     fraction of its FP32 rate). If the refinement has not converged after
-//     40 steps (a small eigengap), the sweeps resume to 1e-2 and it restarts.
-//  3. Sign rule: the largest-magnitude component of v1 is made positive.
+//     with (theta_j, V_j) the rebuilt eigenpairs, v the current leading
+//     vector, r = C v - rho v (rho = v^T C v) and g_j = V_j^T r,
+//        v <- v + sum_{j != lead} V_j g_j / (rho - theta_j)
+//               + (r - sum_j V_j g_j) / (rho - theta_c),
+//     the last term treating the unrebuilt directions as one cluster at
+//     theta_c, the mean of the other diagonal entries of A (they hold the
+//     small eigenvalues, so this is where the exact correction is cheapest
+//     to approximate). Repeated until ||r|| <= 1e-13 ||C||: v1 carries FP64
+//     accuracy while the O(B^3) work runs on the FP32 pipe (GB300's FP64
+//     rate is a small fraction of its FP32 rate).
+//  3. Fallback when the refinement has not converged after 64 steps (a
+//     small eigengap): sweeps restart from C with V accumulated in full
+//     until every |a_pq| <= 1e-2, and the refinement reruns on all columns.
+//  4. Sign rule: the largest-magnitude component of v1 is made positive.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -31,44 +37,119 @@ namespace hsc {
 namespace {
 
 constexpr int kJacThreads = 1024;
-constexpr int kMaxPairs = 512;           // Bp <= 1024
+constexpr int kMaxPairs = 512;           // n <= 1024
 constexpr int kMaxRefine = 64;
-constexpr size_t kJacSmemLimit = 190 * 1024;  // + ~33 KB static shared
+constexpr int kBasis = 16;               // columns of V rebuilt for the refinement
+constexpr size_t kJacSmemLimit = 184 * 1024;  // + ~41 KB static shared <= 227 KB
 
 struct JacParams {
     int B, n;            // n = B rounded up to even
-    int max_sweeps;
+    int max_sweeps;      // fallback sweeps at most
     float rot_tol;       // rotate (p,q) when |a_pq| > rot_tol (A scaled to max diag 1)
-    float stop_tol;      // end the sweeps once every |a_pq| seen in one is <= stop_tol
-    float stop_tol_final;  // tighter tolerance for a second round if refinement stalls
-    int phase0_sweeps;     // the first round of sweeps ends after this many at most
+    float stop_tol_final;  // fallback sweeps end once every |a_pq| seen in one is below
     int use_smem;
 };
 
-// Round-robin ("circle") pairing: in round t (0 <= t < n-1) pair k joins
-// (t+k) and (t-k) modulo n-1, and pair 0 joins t with n-1; every pair of
-// indices meets exactly once per sweep. t + k and t - k + n - 1 stay below
-// 2(n-1), so one conditional subtraction replaces the modulo.
-__device__ __forceinline__ void pair_of(int t, int k, int n, int &p, int &q)
+// j-slices of the double-float C v: each thread sums at most 16 products
+__host__ __device__ inline int jac_slices(int n) { return (n + 15) / 16 < 8 ? 8 : (n + 15) / 16; }
+
+// Work area (floats, row stride ld = n + 1): A (n rows), then the rotation
+// log of the first sweep ((n - 1) rounds x n/2 (c, s) pairs), whose space
+// the fallback reuses for V^T (n rows), then the kBasis rebuilt columns,
+// then the slice partials of C v. Once the first sweep's columns are
+// rebuilt, A and the log are dead and their space holds C as (hi, lo) pairs.
+__host__ __device__ inline size_t jac_work_floats(int n)
 {
-    int a, b;
+    const size_t ld = (size_t)n + 1;
+    return 2 * (size_t)n * ld + (size_t)kBasis * ld + 2 * (size_t)jac_slices(n) * n;
+}
+
+// ---- double-float arithmetic: a value is an unevaluated sum h + l of two
+// FP32 numbers with |l| <= ulp(h)/2 (Dekker 1971; Knuth's TwoSum). The
+// intrinsics keep the compiler from contracting or reassociating.
+struct dfl {
+    float h, l;
+};
+
+// Knuth's TwoSum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + e == a + b exactly when |a| >= |b| (Dekker's Fast2Sum)
+__device__ __forceinline__ dfl fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ dfl df_add(dfl x, dfl y)
+{
+    float s, e;
+    two_sum(x.h, y.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(x.l, y.l));
+    return fast_two_sum(s, e);
+}
+
+// x * y: the product of the heads split exactly by an FMA (two-product),
+// plus the cross terms
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y)
+{
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return fast_two_sum(p, e);
+}
+
+// x / y by one correction of the FP32 quotient (the long-division step of
+// double-length arithmetic): q1 = x/y, q2 = (x - q1 y)/y
+__device__ __forceinline__ dfl df_div(dfl x, dfl y)
+{
+    const float q1 = __fdiv_rn(x.h, y.h);
+    const dfl p = df_mul({q1, 0.f}, y);
+    const dfl r = df_add(x, {-p.h, -p.l});
+    const float q2 = __fdiv_rn(r.h, y.h);
+    return fast_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ dfl df_warp_sum(dfl x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const dfl y = {__shfl_xor_sync(0xffffffffu, x.h, o), __shfl_xor_sync(0xffffffffu, x.l, o)};
+        x = df_add(x, y);
+    }
+    return x;
+}
+
+// Round-robin ("circle") pairing: in round t (0 <= t < n-1) pair k joins
+// a = (t + k) and b = (t - k) modulo n-1, and pair 0 joins t with n-1; every
+// pair of indices meets exactly once per sweep. The pair is kept in this
+// (a, b) orientation, not sorted: then a warp's blocks (k, l..l+31) touch
+// A entries whose banks (a_k + a_l, a_k + b_l, ... mod 32 for an odd row
+// stride) are consecutive, i.e. conflict-free.
+__device__ __forceinline__ void pair_ab(int t, int k, int n, int &a, int &b)
+{
     if (k == 0) {
         a = t;
         b = n - 1;
-    } else {
-        a = t + k;
-        if (a >= n - 1) a -= n - 1;
-        b = t - k + n - 1;
-        if (b >= n - 1) b -= n - 1;
+        return;
     }
-    p = a < b ? a : b;
-    q = a < b ? b : a;
+    a = t + k;
+    if (a >= n - 1) a -= n - 1;
+    b = t - k + n - 1;
+    if (b >= n - 1) b -= n - 1;
 }
 
 // A is kept as its upper triangle (i <= j) in a row-major n x ld array.
 __device__ __forceinline__ int up(int i, int j, int ld) { return i < j ? i * ld + j : j * ld + i; }
 
-// block index idx in [0, P(P+1)/2) -> (k, l), k <= l, row-major upper triangle
+// block index idx in [0, P(P+1)/2) -> (k, l), k <= l < P, row-major upper
+// triangle (with P - 1 and l + 1: the strict upper triangle of P)
 __device__ __forceinline__ void tri_of(int idx, int P, int &k, int &l)
 {
     float fP = (float)(2 * P + 1);
@@ -92,306 +173,463 @@ __device__ float block_maxf(float v, float *red)
     return t;
 }
 
+__device__ float block_sumf(float v, float *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
 __global__ void __launch_bounds__(kJacThreads, 1)
-jacobi_kernel(JacParams prm, const double *__restrict__ C, const double *__restrict__ mu,
+jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restrict__ C2,
+              const double *__restrict__ mu,
               double *__restrict__ v1_out, double *__restrict__ lambda1_out,
-              float *__restrict__ v1f, float *__restrict__ muf, float *gA, float *gV,
-              Control *ctl)
+              float *__restrict__ v1f, float *__restrict__ muf, float *gwork, Control *ctl)
 {
     extern __shared__ float smem[];
     const int B = prm.B, n = prm.n, P = n / 2;
     const int ld = n + 1;  // odd row stride: column walks hit distinct banks
     const int tid = threadIdx.x, nthr = blockDim.x;
-    float *A = prm.use_smem ? smem : gA;
-    float *V = prm.use_smem ? smem + (size_t)n * ld : gV;
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
+    float *work = prm.use_smem ? smem : gwork;
+    float *A = work;                                   // n x ld, upper triangle
+    float2 *rlog = reinterpret_cast<float2 *>(work + (size_t)n * ld);  // (n-1) x P
+    float *Vt = work + (size_t)n * ld;                 // fallback: V^T, n x ld
+    float *X = work + 2 * (size_t)n * ld;              // kBasis x ld, rebuilt columns
+    float2 *part = reinterpret_cast<float2 *>(X + (size_t)kBasis * ld);  // slices x n
+    float2 *Cs2 = reinterpret_cast<float2 *>(work);    // refinement: C as (hi, lo), B x B
+    const int nsl = jac_slices(n);
 
-    __shared__ float cs[kMaxPairs], sn[kMaxPairs];
-    __shared__ int pp[kMaxPairs], qq[kMaxPairs];
+    __shared__ float2 cs2[kMaxPairs];
     __shared__ float fred[32];
-    __shared__ double s_scale;
+    __shared__ float vh[HSC_MAX_BANDS], vl[HSC_MAX_BANDS];   // v = vh + vl
+    __shared__ float wh[HSC_MAX_BANDS], wl[HSC_MAX_BANDS];   // w = C v (scaled)
+    __shared__ float sr[HSC_MAX_BANDS], th[HSC_MAX_BANDS], coef[HSC_MAX_BANDS];
+    __shared__ int basis_idx[HSC_MAX_BANDS];
+    __shared__ float4 red4[32];          // per-warp (v^T v, v^T w) double-float sums
+    __shared__ float red_r2[32];
+    __shared__ dfl s_rho, s_vv;
+    __shared__ int s_lead, s_sign;
+    __shared__ double s_inv_norm;
 
-    // ---- load A = C / scale (scale = largest diagonal entry), V = I
+    // ---- A = C / 2^e, 2^e the power of two at or above half the largest
+    // diagonal entry: an exact scaling, so the double-float C v below needs
+    // no rescaling of its pairs and everything stays in FP32 range
     float dmax = 0.f;
-    for (int i = tid; i < B; i += nthr) dmax = fmaxf(dmax, (float)fabs(C[(size_t)i * B + i]));
+    for (int i = tid; i < B; i += nthr) dmax = fmaxf(dmax, C2[(size_t)i * B + i].x);
     dmax = block_maxf(dmax, fred);
-    if (tid == 0) s_scale = dmax > 0.f ? (double)dmax : 1.0;
-    __syncthreads();
-    const double scale = s_scale;
-    const double inv_scale = 1.0 / scale;
-    for (int idx = tid; idx < n * n; idx += nthr) {
-        int i = idx / n, j = idx % n;
-        A[i * ld + j] = (i < B && j < B) ? (float)(C[(size_t)i * B + j] * inv_scale) : 0.f;
-        V[i * ld + j] = (i == j) ? 1.f : 0.f;
-    }
+    int e2 = 0;
+    if (dmax > 0.f) frexpf(dmax, &e2);
+    e2 = e2 < -100 ? -100 : (e2 > 100 ? 100 : e2);
+    const float inv_p2 = ldexpf(1.f, -e2);
+    const float dmax_s = dmax * inv_p2;
+    auto load_A = [&]() {  // FP32 is all the sweeps use: the hi parts suffice
+        for (int idx = tid; idx < n * n; idx += nthr) {
+            int i = idx / n, j = idx % n;
+            A[i * ld + j] = (i < B && j < B) ? C2[(size_t)i * B + j].x * inv_p2 : 0.f;
+        }
+    };
+    load_A();
     __syncthreads();
 
-    // ---- 1. FP32 parallel cyclic sweeps
-    // Work items fixed for the whole run: up to kBlk 2x2 blocks (k, l) of A
-    // per thread, and one pair column k of V over rows i0, i0 + tpp, ...
-    constexpr int kBlk = 3;  // enough for n <= 128 (2080 blocks); larger n loops
+    // Work items fixed for the whole run: up to kBlk off-diagonal 2x2 blocks
+    // (k, l), k < l, of A per thread (row-major over the strict upper
+    // triangle of pair blocks; the diagonal blocks go with the angles).
+    constexpr int kBlk = 3;  // 2 for n <= 128, 3 up to n = 156; larger n loops
     int bk[kBlk], bl[kBlk];
-    const int nblk = P * (P + 1) / 2;
+    const int nblk = P * (P - 1) / 2;
     const bool blocks_in_regs = nblk <= kBlk * nthr;
 #pragma unroll
     for (int b = 0; b < kBlk; ++b) {
         int idx = tid + b * nthr;
-        if (blocks_in_regs && idx < nblk) tri_of(idx, P, bk[b], bl[b]);
-        else bk[b] = bl[b] = -1;
+        if (blocks_in_regs && idx < nblk) {
+            tri_of(idx, P - 1, bk[b], bl[b]);
+            bl[b] += 1;
+        } else {
+            bk[b] = bl[b] = -1;
+        }
     }
-    const int tpp = nthr / P;                 // threads per V pair column
-    const int vk = tid % P, vi0 = tid / P;    // this thread's pair column / first row
-    const bool v_active = vi0 < tpp;
-    int sweeps = 0;
-    float stop = prm.stop_tol;
-    bool converged = false;
-    int refine_iters = 0;
-    __shared__ double sv[HSC_MAX_BANDS], sw[HSC_MAX_BANDS];
-    __shared__ float sr[HSC_MAX_BANDS], stf[HSC_MAX_BANDS];
-    __shared__ int s_lead, flag_conv;
-    __shared__ double s_rho, s_rn, s_inv_rn;
-    // Phase 0 sweeps to a loose FP32 tolerance; phase 1 (only if the FP64
-    // refinement has not converged) sweeps on to a tight one and refines again.
-    long long t_sweep = 0, t_refine = 0;
-    for (int phase = 0; phase < 2 && !converged; ++phase) {
-    long long t0 = clock64();
-    while (sweeps < prm.max_sweeps) {
+    const int nch = (n + 31) / 32;  // 32-row chunks of a V^T row (fallback)
+
+    // One round t: rotation angles of the P pairs, then A <- J^T A J and,
+    // in the fallback, V <- V J. Returns this thread's max |a_pq| seen.
+    auto jac_round = [&](int t, bool log_rot, bool with_v) -> float {
         float offmax = 0.f;
-        for (int t = 0; t < n - 1; ++t) {
-            for (int k = tid; k < P; k += nthr) {
-                int p, q;
-                pair_of(t, k, n, p, q);
-                float app = A[p * ld + p], aqq = A[q * ld + q], apq = A[up(p, q, ld)];
-                offmax = fmaxf(offmax, fabsf(apq));
-                float c = 1.f, s = 0.f;
-                if (fabsf(apq) > prm.rot_tol) {
-                    // symmetric Schur rotation; FP32 intrinsics are enough here
-                    // because the leading vector is refined in FP64 afterwards
-                    float tau = __fdividef(aqq - app, 2.f * apq);
-                    float tt;
-                    if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
-                    else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
-                    c = rsqrtf(fmaf(tt, tt, 1.f));
-                    s = tt * c;
+        for (int k = tid; k < P; k += nthr) {
+            int a, b;
+            pair_ab(t, k, n, a, b);
+            float app = A[a * ld + a], aqq = A[b * ld + b], apq = A[up(a, b, ld)];
+            offmax = fmaxf(offmax, fabsf(apq));
+            float c = 1.f, s = 0.f;
+            if (fabsf(apq) > prm.rot_tol) {
+                // symmetric Schur rotation; FP32 intrinsics are enough here
+                // because the leading vector is refined in FP64 afterwards
+                float tau = __fdividef(aqq - app, 2.f * apq);
+                float tt;
+                if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
+                else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
+                c = rsqrtf(fmaf(tt, tt, 1.f));
+                s = tt * c;
+                // the pair's own 2x2 diagonal block depends on this rotation
+                // alone: a_pp - t a_pq, a_qq + t a_pq, and a_pq = 0
+                A[a * ld + a] = fmaf(-tt, apq, app);
+                A[b * ld + b] = fmaf(tt, apq, aqq);
+                A[up(a, b, ld)] = 0.f;
+            }
+            cs2[k] = make_float2(c, s);
+            if (log_rot) rlog[(size_t)t * P + k] = make_float2(c, s);
+        }
+        __syncthreads();
+        auto do_block = [&](int k, int l) {
+            const float2 rk = cs2[k], rl = cs2[l];
+            const float ck = rk.x, sk = rk.y, cl = rl.x, sl = rl.y;
+            if (sk == 0.f && sl == 0.f) return;
+            int ak, bk_, al, bl_;
+            pair_ab(t, k, n, ak, bk_);
+            pair_ab(t, l, n, al, bl_);
+            const int i00 = up(ak, al, ld), i01 = up(ak, bl_, ld);
+            const int i10 = up(bk_, al, ld), i11 = up(bk_, bl_, ld);
+            float x00 = A[i00], x01 = A[i01];
+            float x10 = A[i10], x11 = A[i11];
+            float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
+            float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
+            A[i00] = cl * y00 - sl * y01;
+            A[i01] = sl * y00 + cl * y01;
+            A[i10] = cl * y10 - sl * y11;
+            A[i11] = sl * y10 + cl * y11;
+        };
+        if (blocks_in_regs) {
+#pragma unroll
+            for (int b = 0; b < kBlk; ++b)
+                if (bk[b] >= 0) do_block(bk[b], bl[b]);
+        } else {
+            for (int idx = tid; idx < nblk; idx += nthr) {
+                int k, l;
+                tri_of(idx, P - 1, k, l);
+                do_block(k, l + 1);
+            }
+        }
+        if (with_v) {
+            // V^T rows a, b: one warp per (pair, 32-row chunk), conflict-free
+            for (int task = warp; task < P * nch; task += nwarps) {
+                const int k = task / nch, i = (task % nch) * 32 + lane;
+                const float2 r = cs2[k];
+                if (r.y == 0.f || i >= n) continue;
+                int a, b;
+                pair_ab(t, k, n, a, b);
+                const float va = Vt[a * ld + i], vb = Vt[b * ld + i];
+                Vt[a * ld + i] = r.x * va - r.y * vb;
+                Vt[b * ld + i] = r.y * va + r.x * vb;
+            }
+        }
+        __syncthreads();
+        return offmax;
+    };
+
+    // Refinement of the leading vector to FP64-level accuracy on m basis
+    // columns (column c at basis + c * ld, its theta in th[c], the lead at
+    // column lc), C given as (hi, lo) pairs c2 (shared or global), v = vh + vl
+    // the start vector. Returns the iterations taken (kMaxRefine + 1 when
+    // not converged).
+    // GB300's FP64 pipe does under 2 FMA per clock per SM with a 64-cycle
+    // latency, so the refinement runs in double-float on the FP32 pipe. In
+    // C v each product hi*vh is split exactly by an FMA, the products are
+    // summed exactly by TwoSum and the small terms (product and sum errors,
+    // hi*vl, lo*vh) are accumulated in FP32 over at most 16 terms per thread;
+    // the slices are combined the same way. v^T v, v^T w, rho = v^T w / v^T v
+    // and r = w - rho v are double-float (the residual's cancellation is
+    // exact in TwoSum), so the computed r carries about 2^-44 of |C| |v| of
+    // error, well below the 1e-13 stopping tolerance. v is not renormalised
+    // between steps; the correction's direction and length are FP32 and are
+    // added to v exactly (TwoSum). All in the scaled units of A.
+    auto refine = [&](const float *basis, int m, int lc, bool deflate, float theta_c,
+                      const float2 *c2) -> int {
+        const int nchunk = (B + 31) / 32;  // warps holding rows i = tid < B
+        const int i = tid;
+        const bool row = i < B;
+        for (int it = 0; it <= kMaxRefine; ++it) {
+            // w = C v: slice sl of the j's for 32 consecutive i per warp
+            // (C symmetric: C[j][i], conflict-free)
+            for (int task = warp; task < nsl * nchunk; task += nwarps) {
+                const int sl = task % nsl, ii = (task / nsl) * 32 + lane;
+                if (ii >= B) continue;
+                float sum = 0.f, lo = 0.f;
+#pragma unroll 4
+                for (int j = sl; j < B; j += nsl) {
+                    const float2 c = c2[(size_t)j * B + ii];
+                    const float h = vh[j];
+                    const float p = __fmul_rn(c.x, h);
+                    const float pe = __fmaf_rn(c.x, h, -p);
+                    float e;
+                    two_sum(sum, p, sum, e);
+                    lo = __fadd_rn(lo, e);
+                    lo = __fadd_rn(lo, pe);
+                    lo = __fmaf_rn(c.x, vl[j], lo);
+                    lo = __fmaf_rn(c.y, h, lo);
                 }
-                pp[k] = p;
-                qq[k] = q;
-                cs[k] = c;
-                sn[k] = s;
+                part[(size_t)sl * n + ii] = make_float2(sum, lo);
             }
             __syncthreads();
-            // A <- J^T A J, one 2x2 block (k, l), k <= l, per work item
-            auto do_block = [&](int k, int l) {
-                float ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
-                if (sk == 0.f && sl == 0.f) return;
-                int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
-                const int i00 = up(pk, pl, ld), i01 = up(pk, ql, ld);
-                const int i10 = up(qk, pl, ld), i11 = up(qk, ql, ld);
-                float x00 = A[i00], x01 = A[i01];
-                float x10 = A[i10], x11 = A[i11];
-                float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
-                float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
-                float z00 = cl * y00 - sl * y01, z01 = sl * y00 + cl * y01;
-                float z10 = cl * y10 - sl * y11, z11 = sl * y10 + cl * y11;
-                if (k == l) {
-                    A[i00] = z00;   // (pk, pk)
-                    A[i11] = z11;   // (qk, qk)
-                    A[i01] = 0.f;   // (pk, qk), zeroed by the rotation
-                } else {
-                    A[i00] = z00;
-                    A[i01] = z01;
-                    A[i10] = z10;
-                    A[i11] = z11;
+            // rows: w_i, then v^T v and v^T w
+            dfl tvv = {0.f, 0.f}, tvw = {0.f, 0.f};
+            if (row) {
+                float sum = 0.f, lo = 0.f;
+                for (int sl = 0; sl < nsl; ++sl) {
+                    const float2 q = part[(size_t)sl * n + i];
+                    float e;
+                    two_sum(sum, q.x, sum, e);
+                    lo = __fadd_rn(lo, __fadd_rn(e, q.y));
                 }
-            };
-            if (blocks_in_regs) {
-#pragma unroll
-                for (int b = 0; b < kBlk; ++b)
-                    if (bk[b] >= 0) do_block(bk[b], bl[b]);
-            } else {
-                for (int idx = tid; idx < nblk; idx += nthr) {
-                    int k, l;
-                    tri_of(idx, P, k, l);
-                    do_block(k, l);
+                dfl w = fast_two_sum(sum, lo);
+                w.h = __fmul_rn(w.h, inv_p2);  // exact: a power of two
+                w.l = __fmul_rn(w.l, inv_p2);
+                wh[i] = w.h;
+                wl[i] = w.l;
+                const dfl v = {vh[i], vl[i]};
+                tvv = df_mul(v, v);
+                tvw = df_mul(v, w);
+            }
+            if (warp < nchunk) {
+                tvv = df_warp_sum(tvv);
+                tvw = df_warp_sum(tvw);
+                if (lane == 0) red4[warp] = make_float4(tvv.h, tvv.l, tvw.h, tvw.l);
+            }
+            __syncthreads();
+            // rho and the residual r = w - rho v (each row thread forms the
+            // same rho from the same partials, in the same order)
+            float r2 = 0.f;
+            if (row) {
+                dfl vv = {red4[0].x, red4[0].y}, vw = {red4[0].z, red4[0].w};
+                for (int w = 1; w < nchunk; ++w) {
+                    vv = df_add(vv, {red4[w].x, red4[w].y});
+                    vw = df_add(vw, {red4[w].z, red4[w].w});
+                }
+                const dfl rho = df_div(vw, vv);
+                const dfl pv = df_mul(rho, {vh[i], vl[i]});
+                const dfl r = df_add({wh[i], wl[i]}, {-pv.h, -pv.l});
+                const float ri = __fadd_rn(r.h, r.l);
+                sr[i] = ri;
+                r2 = ri * ri;
+                if (i == 0) {
+                    s_rho = rho;
+                    s_vv = vv;
                 }
             }
-            // V <- V J: this thread's pair column over its rows
-            if (v_active) {
-                float s = sn[vk];
-                if (s != 0.f) {
-                    float c = cs[vk];
-                    int p = pp[vk], q = qq[vk];
-                    for (int i = vi0; i < n; i += tpp) {
-                        float vp = V[i * ld + p], vq = V[i * ld + q];
-                        V[i * ld + p] = c * vp - s * vq;
-                        V[i * ld + q] = s * vp + c * vq;
-                    }
+            if (warp < nchunk) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+                if (lane == 0) red_r2[warp] = r2;
+            }
+            __syncthreads();
+            // convergence: ||r|| <= 1e-13 max(|rho|, max diag) ||v|| (uniform)
+            float rr = 0.f;
+            for (int w = 0; w < nchunk; ++w) rr += red_r2[w];
+            const float rho_s = s_rho.h;
+            const float cn = fmaxf(fabsf(rho_s), dmax_s);
+            const float tol = 1e-13f * cn;
+            if (rr <= tol * tol * s_vv.h) return it;
+            if (it == kMaxRefine) break;
+            // g_c = basis_c^T r (one warp per column), then the column's
+            // coefficient
+            const float inv_dc = deflate ? 1.f / (rho_s - theta_c) : 0.f;
+            for (int c = warp; c < m; c += nwarps) {
+                float g = 0.f;
+                for (int ii = lane; ii < B; ii += 32) g = fmaf(basis[(size_t)c * ld + ii], sr[ii], g);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+                if (lane == 0) {
+                    const float den = rho_s - th[c];
+                    const float own = (c == lc || fabsf(den) <= 1e-6f * fmaxf(fabsf(rho_s), 1.f))
+                                          ? 0.f : __fdividef(g, den);
+                    coef[c] = own - g * inv_dc;
                 }
+            }
+            __syncthreads();
+            // v += sum_c coef_c basis_c + r / (rho - theta_c), added exactly
+            if (row) {
+                float acc = sr[i] * inv_dc;
+                for (int c = 0; c < m; ++c) acc = fmaf(coef[c], basis[(size_t)c * ld + i], acc);
+                float sum, e;
+                two_sum(vh[i], acc, sum, e);
+                const dfl nv = fast_two_sum(sum, __fadd_rn(vl[i], e));
+                vh[i] = nv.h;
+                vl[i] = nv.l;
             }
             __syncthreads();
         }
-        ++sweeps;
-        offmax = block_maxf(offmax, fred);
-        if (offmax <= stop || (phase == 0 && sweeps >= prm.phase0_sweeps)) break;
-    }
+        return kMaxRefine + 1;
+    };
 
+    long long t_sweep = 0, t_refine = 0;
+    int sweeps = 0, refine_iters = 0;
+    bool converged = false;
+
+    // ---- phase 0: one logged sweep, rebuilt leading columns, refinement
+    long long t0 = clock64();
+    for (int t = 0; t < n - 1; ++t) jac_round(t, true, false);
+    sweeps = 1;
+    const int m = B < kBasis ? B : kBasis;
+    // rank the diagonal (ties: smaller index first); the m largest form the
+    // basis, the mean of the rest is theta_c
+    float rest = 0.f;
+    for (int j = tid; j < B; j += nthr) {
+        const float dj = A[j * ld + j];
+        int rank = 0;
+        for (int i = 0; i < B; ++i) {
+            const float di = A[i * ld + i];
+            rank += (di > dj || (di == dj && i < j)) ? 1 : 0;
+        }
+        if (rank < m) {
+            basis_idx[rank] = j;
+            th[rank] = dj;
+        } else {
+            rest += dj;
+        }
+    }
+    rest = block_sumf(rest, fred);
+    const bool deflate = B > m;
+    const float theta_c = deflate ? rest / (float)(B - m) : 0.f;
+    // X_c = J_0 J_1 ... J_{n-2} e_{basis_idx[c]}: one warp per column applies
+    // the logged rounds last to first, x <- J_t x on rows (a, b); a lane's
+    // two pairs of a round are disjoint, so both are loaded before either
+    // is stored
+    for (int c = warp; c < m; c += nwarps) {
+        float *x = X + (size_t)c * ld;
+        const int j0 = basis_idx[c];
+        for (int ii = lane; ii < n; ii += 32) x[ii] = (ii == j0) ? 1.f : 0.f;
+        __syncwarp();
+        for (int t = n - 2; t >= 0; --t) {
+            const float2 *lg = rlog + (size_t)t * P;
+            for (int k = lane; k < P; k += 64) {
+                const int k2 = k + 32;
+                const bool has2 = k2 < P;
+                const float2 r1 = lg[k];
+                const float2 r2 = has2 ? lg[k2] : make_float2(1.f, 0.f);
+                int a1, b1, a2 = 0, b2 = 0;
+                pair_ab(t, k, n, a1, b1);
+                if (has2) pair_ab(t, k2, n, a2, b2);
+                const float xa1 = x[a1], xb1 = x[b1];
+                const float xa2 = has2 ? x[a2] : 0.f, xb2 = has2 ? x[b2] : 0.f;
+                if (r1.y != 0.f) {
+                    x[a1] = r1.x * xa1 + r1.y * xb1;
+                    x[b1] = r1.x * xb1 - r1.y * xa1;
+                }
+                if (r2.y != 0.f) {
+                    x[a2] = r2.x * xa2 + r2.y * xb2;
+                    x[b2] = r2.x * xb2 - r2.y * xa2;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int ii = tid; ii < B; ii += nthr) {  // column 0: the lead
+        vh[ii] = X[ii];
+        vl[ii] = 0.f;
+    }
+    // A and the log are dead: stage C's (hi, lo) pairs in their space
+    if (prm.use_smem) {
+        const float4 *src = reinterpret_cast<const float4 *>(C2);
+        float4 *dst = reinterpret_cast<float4 *>(Cs2);
+        const int n4 = (B * B) / 2;
+        constexpr int kU = 8;
+        for (int q0 = tid; q0 < n4; q0 += kU * nthr) {
+            float4 tmp[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (q0 + u * nthr < n4) tmp[u] = src[q0 + u * nthr];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (q0 + u * nthr < n4) dst[q0 + u * nthr] = tmp[u];
+        }
+        if ((B * B) & 1 && tid == 0) Cs2[B * B - 1] = C2[B * B - 1];
+    }
+    __syncthreads();
     long long t1 = clock64();
     t_sweep += t1 - t0;
-    // ---- 2. FP64 refinement of the leading vector
-    // GB300's FP64 pipe is narrow and its divide/sqrt are long dependent
-    // chains, so FP64 is spent only where it matters: C v (eight threads per
-    // row), v^T v, v^T w and ||r||^2 (one warp), and the update of v. The
-    // Rayleigh quotient uses a Newton-Raphson reciprocal (FP32 seed, two FP64
-    // Newton steps y <- y (2 - x y)); v is not renormalised between steps
-    // (rho divides by v^T v), convergence is tested on squared norms, and the
-    // correction's direction and length are FP32.
-    if (tid == 0) {
-        int lead = 0;
-        for (int j = 1; j < B; ++j)
-            if (A[j * ld + j] > A[lead * ld + lead]) lead = j;
-        s_lead = lead;
-    }
-    __syncthreads();
-    const int lead = s_lead;
-    const int warp = tid >> 5, lane = tid & 31;
-    auto warp0_sum = [&](auto f) -> double {  // warp 0 only; all its lanes get the sum
-        double part = 0.0;
-        for (int i = lane; i < B; i += 32) part += f(i);
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        return part;
-    };
-    auto recip = [](double x) -> double {  // Newton-Raphson reciprocal
-        double y = (double)(1.0f / (float)x);
-        y = y * fma(-x, y, 2.0);
-        y = y * fma(-x, y, 2.0);
-        return y;
-    };
-    for (int i = tid; i < B; i += nthr) sv[i] = (double)V[i * ld + lead];
-    __syncthreads();
-    // Per step: C v in FP64, v^T v and v^T w in one fused FP64 reduction, the
-    // residual's elements in FP64 but its squared norm in FP32.
-    const int row_sub = tid & 7;
-    for (int it = 0; it <= kMaxRefine; ++it) {
-        refine_iters = it;
-        // w = C v: eight threads per row (three shuffle levels), so the FP64
-        // instruction count stays near the B^2 / 32 floor
-        for (int i0 = 0; i0 < B; i0 += nthr / 8) {
-            const int i = i0 + (tid >> 3);
-            double a = 0.0;
-            if (i < B)  // C symmetric: C[j][i], consecutive i across threads
-                for (int j = row_sub; j < B; j += 8) a = fma(C[(size_t)j * B + i], sv[j], a);
-            a += __shfl_xor_sync(0xffffffffu, a, 1);
-            a += __shfl_xor_sync(0xffffffffu, a, 2);
-            a += __shfl_xor_sync(0xffffffffu, a, 4);
-            if (i < B && row_sub == 0) sw[i] = a;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double vv = 0.0, vw = 0.0;
-            for (int i = lane; i < B; i += 32) {
-                vv = fma(sv[i], sv[i], vv);
-                vw = fma(sv[i], sw[i], vw);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                vv += __shfl_xor_sync(0xffffffffu, vv, o);
-                vw += __shfl_xor_sync(0xffffffffu, vw, o);
-            }
-            const double rho = vw * recip(vv);
-            float r2 = 0.f;
-            for (int i = lane; i < B; i += 32) {
-                const float ri = (float)fma(-rho, sv[i], sw[i]);
-                r2 = fmaf(ri, ri, r2);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-            if (lane == 0) {
-                const double cnorm = fabs(rho) > scale ? fabs(rho) : scale;
-                const float tol = (float)(1e-13 * cnorm);
-                s_rho = rho;
-                s_rn = (double)r2;
-                flag_conv = ((double)r2 <= (double)tol * (double)tol * vv) ? 1 : 0;
-            }
-        }
-        __syncthreads();
-        if (flag_conv) {
-            converged = true;
-            break;
-        }
-        if (it == kMaxRefine) break;
-        const double rho = s_rho;
-        const float rn = sqrtf((float)s_rn);
-        const float inv_rn = 1.0f / rn;
-        // unit residual direction in FP32 (the correction's direction only)
-        for (int i = tid; i < B; i += nthr) sr[i] = (float)fma(-rho, sv[i], sw[i]) * inv_rn;
-        __syncthreads();
-        // t_j = (V_j^T r) / (rho - theta_j), FP32, relative to ||r|| / scale
-        const float rho_s = (float)(rho / scale);
-        for (int j = tid; j < B; j += nthr) {
-            float g = 0.f;
-            for (int i = 0; i < B; ++i) g = fmaf(V[i * ld + j], sr[i], g);
-            const float den = rho_s - A[j * ld + j];  // in the scaled units of A
-            stf[j] = (j == lead || fabsf(den) <= 1e-6f * fmaxf(fabsf(rho_s), 1.f))
-                         ? 0.f : __fdividef(g, den);
-        }
-        __syncthreads();
-        // v += (||r|| / scale) sum_j t_j V_j : FP32 sum per row, FP64 update
-        const double step = (double)(rn / (float)scale);
-        for (int i = tid; i < B; i += nthr) {
-            float a = 0.f;
-            for (int j = 0; j < B; ++j) a = fmaf(stf[j], V[i * ld + j], a);
-            sv[i] = fma(step, (double)a, sv[i]);
-        }
-        __syncthreads();
-    }
-    // normalise once: inverse square root by Newton-Raphson (FP32 seed, two
-    // FP64 steps y <- y (3 - x y^2) / 2)
-    if (warp == 0) {
-        const double vv = warp0_sum([&](int i) { return sv[i] * sv[i]; });
-        if (lane == 0) {
-            double y = (double)rsqrtf((float)vv);
-            y = y * fma(-0.5 * vv * y, y, 1.5);
-            y = y * fma(-0.5 * vv * y, y, 1.5);
-            s_inv_rn = y;
-        }
-    }
-    __syncthreads();
-    for (int i = tid; i < B; i += nthr) sv[i] *= s_inv_rn;
-    __syncthreads();
+    refine_iters = refine(X, m, 0, deflate, theta_c, prm.use_smem ? Cs2 : C2);
+    converged = refine_iters <= kMaxRefine;
     t_refine += clock64() - t1;
-    stop = prm.stop_tol_final;
-    }  // phases
-    // ---- 3. sign rule and outputs
+
+    // ---- fallback: sweeps from C with V accumulated, refinement on all columns
+    if (!converged) {
+        t0 = clock64();
+        load_A();
+        for (int idx = tid; idx < n * ld; idx += nthr) Vt[idx] = (idx % ld == idx / ld) ? 1.f : 0.f;
+        __syncthreads();
+        int fb = 0;
+        while (fb < prm.max_sweeps) {
+            float offmax = 0.f;
+            for (int t = 0; t < n - 1; ++t) offmax = fmaxf(offmax, jac_round(t, false, true));
+            ++fb;
+            offmax = block_maxf(offmax, fred);
+            if (offmax <= prm.stop_tol_final) break;
+        }
+        sweeps += fb;
+        if (tid == 0) {
+            int lead = 0;
+            for (int j = 1; j < B; ++j)
+                if (A[j * ld + j] > A[lead * ld + lead]) lead = j;
+            s_lead = lead;
+        }
+        for (int j = tid; j < B; j += nthr) th[j] = A[j * ld + j];
+        __syncthreads();
+        const int lead = s_lead;
+        for (int ii = tid; ii < B; ii += nthr) {
+            vh[ii] = Vt[(size_t)lead * ld + ii];
+            vl[ii] = 0.f;
+        }
+        __syncthreads();
+        t1 = clock64();
+        t_sweep += t1 - t0;
+        refine_iters = refine(Vt, B, lead, false, 0.f, C2);
+        converged = refine_iters <= kMaxRefine;
+        t_refine += clock64() - t1;
+    }
+
+    // ---- outputs: v / ||v|| (||v||^2 = the last v^T v, which belongs to the
+    // returned v), the sign rule (largest |v_i| positive), lambda1 = rho 2^e
     if (tid == 0) {
-        int big = 0;
-        for (int i = 1; i < B; ++i)
-            if (fabs(sv[i]) > fabs(sv[big])) big = i;
-        s_lead = (sv[big] < 0.0) ? -1 : 1;
-        *lambda1_out = s_rho;
+        const double vv = (double)s_vv.h + (double)s_vv.l;
+        s_inv_norm = vv > 0.0 ? 1.0 / sqrt(vv) : 1.0;
+        double bv = 0.0;  // the first component of largest magnitude
+        for (int ii = 0; ii < B; ++ii) {
+            const double x = (double)vh[ii] + (double)vl[ii];
+            if (fabs(x) > fabs(bv)) bv = x;
+        }
+        s_sign = (bv < 0.0) ? -1 : 1;
+        *lambda1_out = ldexp((double)s_rho.h + (double)s_rho.l, e2);
         if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
         ctl->jacobi_sweeps = (unsigned)sweeps;
-        ctl->refine_iters = (unsigned)refine_iters;
+        ctl->refine_iters = (unsigned)(refine_iters > kMaxRefine ? kMaxRefine : refine_iters);
         ctl->jacobi_sweep_cycles = (unsigned long long)t_sweep;
         ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
         ctl->imin_key = float_to_key(INFINITY);
         ctl->imax_key = float_to_key(-INFINITY);
     }
     __syncthreads();
-    const double sgn = (double)s_lead;
-    for (int i = tid; i < B; i += nthr) {
-        double v = sgn * sv[i];
-        v1_out[i] = v;
-        v1f[i] = (float)v;
-        muf[i] = (float)mu[i];
+    const double scl = (double)s_sign * s_inv_norm;
+    for (int ii = tid; ii < B; ii += nthr) {
+        const double v = scl * ((double)vh[ii] + (double)vl[ii]);
+        v1_out[ii] = v;
+        v1f[ii] = (float)v;
+        muf[ii] = (float)mu[ii];
     }
 }
 
 }  // namespace
 
+// Global work area of the Jacobi kernel (floats); 0 when it fits in shared memory.
 size_t jacobi_global_floats(int B)
 {
     int n = B + (B & 1);
-    size_t need = 2 * (size_t)n * (n + 1) * sizeof(float);
-    return need <= kJacSmemLimit ? 0 : (size_t)n * (n + 1);
+    if (n < 2) n = 2;
+    const size_t f = jac_work_floats(n);
+    return f * sizeof(float) <= kJacSmemLimit ? 0 : f;
 }
 
 cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
@@ -402,16 +640,15 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
     if (prm.n < 2) prm.n = 2;
     prm.max_sweeps = 30;
     prm.rot_tol = 1e-7f;
-    prm.stop_tol = 1.0f;
     prm.stop_tol_final = 1e-2f;
-    prm.phase0_sweeps = 1;
-    size_t need = 2 * (size_t)prm.n * (prm.n + 1) * sizeof(float);
+    const size_t need = jac_work_floats(prm.n) * sizeof(float);
     prm.use_smem = need <= kJacSmemLimit;
-    size_t smem = prm.use_smem ? need : 0;
+    const size_t smem = prm.use_smem ? need : 0;
+    if (!prm.use_smem && !s.jac_A) return cudaErrorInvalidValue;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    jacobi_kernel<<<1, kJacThreads, smem, st>>>(prm, s.C, s.mu, s.v1, s.lambda1, s.v1f, s.muf,
-                                                s.jac_A, s.jac_V, s.ctl);
+    jacobi_kernel<<<1, kJacThreads, smem, st>>>(prm, s.C, s.C2, s.mu, s.v1, s.lambda1, s.v1f,
+                                                s.muf, s.jac_A, s.ctl);
     return cudaGetLastError();
 }
 

@@ -166,13 +166,15 @@ __global__ void band_mean_kernel(int B, long N, int n_part, const float *__restr
     }
 }
 
-// C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored. A CTA
+// C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored, in
+// FP64 and as FP32 (hi, lo) pairs. A CTA
 // takes 32 consecutive entries e = b*B + c; its 8 warps each sum every 8th
 // partial (coalesced across the 32 entries), then the 8 slices are added.
 constexpr int kRedEntries = 32, kRedSlices = 8;
 __global__ void __launch_bounds__(kRedEntries * kRedSlices)
 gram_reduce_kernel(int B, long N, int n_part, const float *__restrict__ gram_part,
-                   const double *__restrict__ delta, double *__restrict__ C)
+                   const double *__restrict__ delta, double *__restrict__ C,
+                   float2 *__restrict__ C2)
 {
     const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const long e = (long)blockIdx.x * kRedEntries + lane;
@@ -191,6 +193,12 @@ gram_reduce_kernel(int B, long N, int n_part, const float *__restrict__ gram_par
         double v = t / (double)N - delta[b] * delta[c];
         C[(size_t)b * B + c] = v;
         C[(size_t)c * B + b] = v;
+        // the same value as an unevaluated FP32 sum hi + lo (for the
+        // eigensolver's double-float products)
+        const float hi = __double2float_rn(v);
+        const float2 pr = make_float2(hi, __double2float_rn(v - (double)hi));
+        C2[(size_t)b * B + c] = pr;
+        C2[(size_t)c * B + b] = pr;
     }
 }
 
@@ -208,7 +216,7 @@ static cudaError_t launch_reductions(int B, long N, int n_part, const PcaScratch
     band_mean_kernel<<<B, 128, 0, st>>>(B, N, n_part, s.shift, s.sum_part, s.v1, s.mu);
     const long BB = (long)B * B;
     gram_reduce_kernel<<<(unsigned)((BB + kRedEntries - 1) / kRedEntries), kRedEntries * kRedSlices,
-                         0, st>>>(B, N, n_part, s.gram_part, s.v1, s.C);
+                         0, st>>>(B, N, n_part, s.gram_part, s.v1, s.C, s.C2);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,42 @@ def test_pca_odd_band_count_and_ragged_pixels(hsc, ctx):
     assert np.abs(I - ref["I_norm"]).max() < I_TOL
 
 
+def decaying_spectrum_cube(B=96, H=64, W=64, seed=9):
+    """x_p = m + sum_j sqrt(1/j) z_jp q_j: a covariance whose eigenvalues
+    fall off only as 1/j (a hard case for a truncated eigenbasis)."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((B, B)))
+    z = rng.standard_normal((B, H * W))
+    x = 0.5 + 0.01 * (Q * np.sqrt(1.0 / np.arange(1, B + 1))) @ z
+    return x.reshape(B, H, W).astype(np.float32)
+
+
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "snapshot", "b37", "b200", "decay"])
+def test_eigenpair_fp64_residual(hsc, ctx, case):
+    """The refinement's claim: (v1, lambda1) is an eigenpair of the GPU's own
+    FP64 covariance to ||C v - lambda v|| <= 2e-13 ||C|| (checked in FP64 on
+    the host), whether the work area sits in shared memory (B <= 142) or in
+    global memory (B = 200), and on a slowly decaying spectrum."""
+    if case.startswith("cfg"):
+        cube = synth.make_config(int(case[3])).cube
+    elif case == "snapshot":
+        cube = synth.make_batch(1)[0].cube
+    elif case == "b37":
+        cube = synth.make_frame(5, 31, 33, 37, sigma=0.03).cube
+    elif case == "b200":
+        cube = synth.make_frame(6, 40, 48, 200, sigma=0.03).cube
+    else:
+        cube = decaying_spectrum_cube()
+    _, v, lam = gpu_pca(hsc, ctx, cube)
+    _, C = hsc.hsc_pca_covariance(ctx, to_dev(cube))
+    ctx.sync()
+    C = C.cpu().numpy()
+    r = C @ v - lam * v
+    cn = max(abs(lam), np.abs(np.diag(C)).max())
+    assert abs(np.linalg.norm(v) - 1.0) < 1e-14
+    assert np.linalg.norm(r) <= 2e-13 * cn, np.linalg.norm(r) / cn
+
+
 def gpu_svm(hsc, ctx, cube, model, flags=0):
     import torch
     c = to_dev(cube.astype(np.float32))
