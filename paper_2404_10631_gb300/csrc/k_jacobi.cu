@@ -40,7 +40,7 @@ constexpr int kJacThreads = 1024;
 constexpr int kMaxPairs = 512;           // n <= 1024
 constexpr int kMaxRefine = 64;
 constexpr int kBasis = 16;               // columns of V rebuilt for the refinement
-constexpr size_t kJacSmemLimit = 184 * 1024;  // + ~41 KB static shared <= 227 KB
+constexpr size_t kJacSmemLimit = 176 * 1024;  // + ~49 KB static shared <= 227 KB
 
 struct JacParams {
     int B, n;            // n = B rounded up to even
@@ -204,7 +204,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     float2 *Cs2 = reinterpret_cast<float2 *>(work);    // refinement: C as (hi, lo), B x B
     const int nsl = jac_slices(n);
 
-    __shared__ float2 cs2[kMaxPairs];
+    __shared__ float2 cs2[2][kMaxPairs];   // (c, s) of the round's pairs, double-buffered
+    __shared__ int2 ab2[2][kMaxPairs];     // (a, b) of the round's pairs
     __shared__ float fred[32];
     __shared__ float vh[HSC_MAX_BANDS], vl[HSC_MAX_BANDS];   // v = vh + vl
     __shared__ float wh[HSC_MAX_BANDS], wl[HSC_MAX_BANDS];   // w = C v (scaled)
@@ -238,95 +239,154 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     // Work items fixed for the whole run: up to kBlk off-diagonal 2x2 blocks
     // (k, l), k < l, of A per thread (row-major over the strict upper
-    // triangle of pair blocks; the diagonal blocks go with the angles).
+    // triangle of pair blocks; the diagonal blocks go with the angles), each
+    // packed with the pair of the next round whose angle it owns:
+    // k | l << 10 | (owner + 1) << 20, or -1.
     constexpr int kBlk = 3;  // 2 for n <= 128, 3 up to n = 156; larger n loops
-    int bk[kBlk], bl[kBlk];
     const int nblk = P * (P - 1) / 2;
     const bool blocks_in_regs = nblk <= kBlk * nthr;
+    // One barrier per round: the a_pq of round t+1's pair k' sits in exactly
+    // one off-diagonal block of round t, (k'-1, k'+1) (ends: (0,1), (0,2),
+    // (P-2,P-1)); its diagonal entries belong to no off-diagonal block. The
+    // thread rotating that block computes the next angle and the next
+    // diagonal block right away, into the other (c, s) buffer. Needs P >= 3.
+    const bool one_sync = P >= 3;
+    auto owner_of = [&](int k, int l) -> int {
+        if (k == 0 && l == 1) return 0;
+        if (k == 0 && l == 2) return 1;
+        if (k == P - 2 && l == P - 1) return P - 1;
+        if (l == k + 2 && k >= 1 && k + 1 <= P - 2) return k + 1;
+        return -1;
+    };
+    // Thread k' < P takes the owner block of pair k' (so the angles run in
+    // converged warps); the other blocks, row-major with the owners skipped,
+    // follow over all threads: global slot g = tid + b * nthr, block P + r.
+    auto rowstart = [&](int k) { return k * (P - 1) - k * (k - 1) / 2; };
+    auto owners_upto = [&](int idx) {  // owner blocks with row-major index <= idx
+        int k, l;
+        tri_of(idx, P - 1, k, l);
+        const int pos = idx - rowstart(k);
+        if (k == 0) return (pos < 1 ? pos : 1) + 1;
+        if (k <= P - 3) return 2 + (k - 1) + (pos >= 1 ? 1 : 0);
+        return P;
+    };
+    int slot[kBlk];
 #pragma unroll
     for (int b = 0; b < kBlk; ++b) {
-        int idx = tid + b * nthr;
-        if (blocks_in_regs && idx < nblk) {
-            tri_of(idx, P - 1, bk[b], bl[b]);
-            bl[b] += 1;
-        } else {
-            bk[b] = bl[b] = -1;
+        const int g = tid + b * nthr;
+        slot[b] = -1;
+        if (!blocks_in_regs || g >= nblk) continue;
+        int k, l, o = -1;
+        if (!one_sync) {
+            tri_of(g, P - 1, k, l);
+            l += 1;
+        } else if (g < P) {  // owner block of pair o = g
+            o = g;
+            k = o == 0 ? 0 : (o == 1 ? 0 : (o == P - 1 ? P - 2 : o - 1));
+            l = o == 0 ? 1 : (o == 1 ? 2 : (o == P - 1 ? P - 1 : o + 1));
+        } else {  // the (g - P)-th block that owns no angle
+            const int r = g - P;
+            int idx = r;
+            for (int it = 0; it < 8; ++it) {  // fixed point: idx = r + owners_upto(idx)
+                const int nx = r + owners_upto(idx);
+                if (nx == idx) break;
+                idx = nx;
+            }
+            tri_of(idx, P - 1, k, l);
+            l += 1;
         }
+        slot[b] = k | (l << 10) | ((o + 1) << 20);
     }
     const int nch = (n + 31) / 32;  // 32-row chunks of a V^T row (fallback)
 
-    // One round t: rotation angles of the P pairs, then A <- J^T A J and,
-    // in the fallback, V <- V J. Returns this thread's max |a_pq| seen.
-    auto jac_round = [&](int t, bool log_rot, bool with_v) -> float {
+    // Rotation of pair k in round t: the symmetric Schur angle from the
+    // current A, the pair's own 2x2 diagonal block in closed form (a_pp -
+    // t a_pq, a_qq + t a_pq, a_pq = 0: it depends on this rotation alone),
+    // (c, s) and (a, b) published in buffer buf, and the log. Returns |a_pq|.
+    auto angle_pair = [&](int t, int k, int buf, bool log_rot) -> float {
+        int a, b;
+        pair_ab(t, k, n, a, b);
+        const int iab = up(a, b, ld);
+        const float app = A[a * ld + a], aqq = A[b * ld + b], apq = A[iab];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > prm.rot_tol) {
+            // FP32 intrinsics are enough here: the leading vector is refined
+            // to FP64 accuracy afterwards
+            float tau = __fdividef(aqq - app, 2.f * apq);
+            float tt;
+            if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
+            else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
+            c = rsqrtf(fmaf(tt, tt, 1.f));
+            s = tt * c;
+            A[a * ld + a] = fmaf(-tt, apq, app);
+            A[b * ld + b] = fmaf(tt, apq, aqq);
+            A[iab] = 0.f;
+        }
+        cs2[buf][k] = make_float2(c, s);
+        ab2[buf][k] = make_int2(a, b);
+        if (log_rot) rlog[(size_t)t * P + k] = make_float2(c, s);
+        return fabsf(apq);
+    };
+
+    // One sweep: A <- J^T A J per round and, in the fallback, V <- V J.
+    // Returns this thread's max |a_pq| seen.
+    auto sweep = [&](bool log_rot, bool with_v) -> float {
         float offmax = 0.f;
-        for (int k = tid; k < P; k += nthr) {
-            int a, b;
-            pair_ab(t, k, n, a, b);
-            float app = A[a * ld + a], aqq = A[b * ld + b], apq = A[up(a, b, ld)];
-            offmax = fmaxf(offmax, fabsf(apq));
-            float c = 1.f, s = 0.f;
-            if (fabsf(apq) > prm.rot_tol) {
-                // symmetric Schur rotation; FP32 intrinsics are enough here
-                // because the leading vector is refined in FP64 afterwards
-                float tau = __fdividef(aqq - app, 2.f * apq);
-                float tt;
-                if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
-                else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
-                c = rsqrtf(fmaf(tt, tt, 1.f));
-                s = tt * c;
-                // the pair's own 2x2 diagonal block depends on this rotation
-                // alone: a_pp - t a_pq, a_qq + t a_pq, and a_pq = 0
-                A[a * ld + a] = fmaf(-tt, apq, app);
-                A[b * ld + b] = fmaf(tt, apq, aqq);
-                A[up(a, b, ld)] = 0.f;
-            }
-            cs2[k] = make_float2(c, s);
-            if (log_rot) rlog[(size_t)t * P + k] = make_float2(c, s);
-        }
+        for (int k = tid; k < P; k += nthr) offmax = fmaxf(offmax, angle_pair(0, k, 0, log_rot));
         __syncthreads();
-        auto do_block = [&](int k, int l) {
-            const float2 rk = cs2[k], rl = cs2[l];
-            const float ck = rk.x, sk = rk.y, cl = rl.x, sl = rl.y;
-            if (sk == 0.f && sl == 0.f) return;
-            int ak, bk_, al, bl_;
-            pair_ab(t, k, n, ak, bk_);
-            pair_ab(t, l, n, al, bl_);
-            const int i00 = up(ak, al, ld), i01 = up(ak, bl_, ld);
-            const int i10 = up(bk_, al, ld), i11 = up(bk_, bl_, ld);
-            float x00 = A[i00], x01 = A[i01];
-            float x10 = A[i10], x11 = A[i11];
-            float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
-            float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
-            A[i00] = cl * y00 - sl * y01;
-            A[i01] = sl * y00 + cl * y01;
-            A[i10] = cl * y10 - sl * y11;
-            A[i11] = sl * y10 + cl * y11;
-        };
-        if (blocks_in_regs) {
+        for (int t = 0; t < n - 1; ++t) {
+            const int cur = t & 1, nxt = cur ^ 1;
+            const bool next_in = t + 1 < n - 1;
+            auto do_block = [&](int k, int l, int own) {
+                const float2 rk = cs2[cur][k], rl = cs2[cur][l];
+                const float ck = rk.x, sk = rk.y, cl = rl.x, sl = rl.y;
+                if (sk != 0.f || sl != 0.f) {
+                    const int2 pk = ab2[cur][k], pl = ab2[cur][l];
+                    const int i00 = up(pk.x, pl.x, ld), i01 = up(pk.x, pl.y, ld);
+                    const int i10 = up(pk.y, pl.x, ld), i11 = up(pk.y, pl.y, ld);
+                    const float x00 = A[i00], x01 = A[i01];
+                    const float x10 = A[i10], x11 = A[i11];
+                    const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
+                    const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
+                    A[i00] = cl * y00 - sl * y01;
+                    A[i01] = sl * y00 + cl * y01;
+                    A[i10] = cl * y10 - sl * y11;
+                    A[i11] = sl * y10 + cl * y11;
+                }
+                if (own >= 0 && next_in) offmax = fmaxf(offmax, angle_pair(t + 1, own, nxt, log_rot));
+            };
+            if (blocks_in_regs) {
 #pragma unroll
-            for (int b = 0; b < kBlk; ++b)
-                if (bk[b] >= 0) do_block(bk[b], bl[b]);
-        } else {
-            for (int idx = tid; idx < nblk; idx += nthr) {
-                int k, l;
-                tri_of(idx, P - 1, k, l);
-                do_block(k, l + 1);
+                for (int b = 0; b < kBlk; ++b) {
+                    const int sb = slot[b];
+                    if (sb >= 0) do_block(sb & 1023, (sb >> 10) & 1023, (sb >> 20) - 1);
+                }
+            } else {
+                for (int idx = tid; idx < nblk; idx += nthr) {
+                    int k, l;
+                    tri_of(idx, P - 1, k, l);
+                    do_block(k, l + 1, one_sync ? owner_of(k, l + 1) : -1);
+                }
+            }
+            if (with_v) {
+                // V^T rows a, b: one warp per (pair, 32-row chunk), conflict-free
+                for (int task = warp; task < P * nch; task += nwarps) {
+                    const int k = task / nch, i = (task % nch) * 32 + lane;
+                    const float2 r = cs2[cur][k];
+                    if (r.y == 0.f || i >= n) continue;
+                    const int2 pk = ab2[cur][k];
+                    const float va = Vt[pk.x * ld + i], vb = Vt[pk.y * ld + i];
+                    Vt[pk.x * ld + i] = r.x * va - r.y * vb;
+                    Vt[pk.y * ld + i] = r.y * va + r.x * vb;
+                }
+            }
+            __syncthreads();
+            if (!one_sync && next_in) {
+                for (int k = tid; k < P; k += nthr)
+                    offmax = fmaxf(offmax, angle_pair(t + 1, k, nxt, log_rot));
+                __syncthreads();
             }
         }
-        if (with_v) {
-            // V^T rows a, b: one warp per (pair, 32-row chunk), conflict-free
-            for (int task = warp; task < P * nch; task += nwarps) {
-                const int k = task / nch, i = (task % nch) * 32 + lane;
-                const float2 r = cs2[k];
-                if (r.y == 0.f || i >= n) continue;
-                int a, b;
-                pair_ab(t, k, n, a, b);
-                const float va = Vt[a * ld + i], vb = Vt[b * ld + i];
-                Vt[a * ld + i] = r.x * va - r.y * vb;
-                Vt[b * ld + i] = r.y * va + r.x * vb;
-            }
-        }
-        __syncthreads();
         return offmax;
     };
 
@@ -470,7 +530,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     // ---- phase 0: one logged sweep, rebuilt leading columns, refinement
     long long t0 = clock64();
-    for (int t = 0; t < n - 1; ++t) jac_round(t, true, false);
+    sweep(true, false);
     sweeps = 1;
     const int m = B < kBasis ? B : kBasis;
     // rank the diagonal (ties: smaller index first); the m largest form the
@@ -563,8 +623,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         __syncthreads();
         int fb = 0;
         while (fb < prm.max_sweeps) {
-            float offmax = 0.f;
-            for (int t = 0; t < n - 1; ++t) offmax = fmaxf(offmax, jac_round(t, false, true));
+            float offmax = sweep(false, true);
             ++fb;
             offmax = block_maxf(offmax, fred);
             if (offmax <= prm.stop_tol_final) break;

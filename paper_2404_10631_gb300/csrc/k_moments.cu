@@ -21,43 +21,62 @@ constexpr int kTile = 8;         // 8x8 accumulator tile per thread
 
 // Pilot shift: the mean of a 4096-pixel sample of each band, read as 16
 // runs of 256 consecutive pixels spread over the band (coalesced). Any shift
-// close to the mean works: the moments are exact in it.
-__global__ void pilot_shift_kernel(const float *__restrict__ cube, int B, long N,
-                                   float *__restrict__ shift, Control *ctl)
+// close to the mean works (the moments are exact in it), so the sample is
+// summed in FP32, with its 16 loads per thread issued together.
+__global__ void __launch_bounds__(256)
+pilot_shift_kernel(const float *__restrict__ cube, int B, long N, float *__restrict__ shift,
+                   Control *ctl)
 {
     const int b = blockIdx.x;
     constexpr int kRuns = 16, kRun = 256;
     const float *band = cube + (size_t)b * (size_t)N;
-    double acc = 0.0;
-    long count = 0;
+    float acc = 0.f;
+    long count;
     bool bad = false;
     if (N <= (long)kRuns * kRun) {
         for (long p = threadIdx.x; p < N; p += blockDim.x) {
-            float x = band[p];
+            const float x = band[p];
             bad |= !isfinite(x);
-            acc += (double)x;
+            acc += x;
         }
         count = N;
     } else {
+        float x[kRuns];
+#pragma unroll
+        for (int r = 0; r < kRuns; ++r)
+            x[r] = __ldg(band + ((long)r * (N - kRun)) / (kRuns - 1) + threadIdx.x);
+#pragma unroll
         for (int r = 0; r < kRuns; ++r) {
-            long p = ((long)r * (N - kRun)) / (kRuns - 1) + threadIdx.x;
-            if (threadIdx.x < kRun) {
-                float x = band[p];
-                bad |= !isfinite(x);
-                acc += (double)x;
-            }
+            bad |= !isfinite(x[r]);
+            acc += x[r];
         }
         count = (long)kRuns * kRun;
     }
-    __shared__ double red[32];
+    __shared__ float red[8];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        shift[b] = (float)(t / (double)count);
+        float t = 0.f;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        shift[b] = t / (float)count;
     }
+}
+
+// Double-float accumulation (Knuth's TwoSum keeps each addition's rounding
+// error; GB300's FP64 pipe is too narrow for these reductions).
+__device__ __forceinline__ void df_acc(float &s, float &lo, float x)
+{
+    const float t = __fadd_rn(s, x);
+    const float bb = __fsub_rn(t, s);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(x, bb)));
+    s = t;
+}
+
+__device__ __forceinline__ void df_acc2(float &s, float &lo, float xs, float xlo)
+{
+    df_acc(s, lo, xs);
+    lo = __fadd_rn(lo, xlo);
 }
 
 // grid.x = pixel partitions, grid.y = groups of 256 output tiles (B > 128).
@@ -144,35 +163,34 @@ gram_partial_kernel(const float *__restrict__ cube, int B, int Bp, long N,
     if (do_sums && tid < B) sum_part[(size_t)blockIdx.x * B + tid] = bsum;
 }
 
-// delta_b = (1/N) sum of partial sums; mu_b = shift_b + delta_b. One CTA per
-// band, the partials split over the threads, FP64 throughout.
-__global__ void band_mean_kernel(int B, long N, int n_part, const float *__restrict__ shift,
-                                 const float *__restrict__ sum_part, double *__restrict__ delta,
-                                 double *__restrict__ mu)
+// delta_b = (1/N) sum of partial sums; mu_b = shift_b + delta_b. One warp
+// per band: the partials are summed in double-float, then scaled in FP64.
+constexpr int kMeanWarps = 8;
+__global__ void __launch_bounds__(32 * kMeanWarps)
+band_mean_kernel(int B, double inv_N, int n_part, const float *__restrict__ shift,
+                 const float *__restrict__ sum_part, double *__restrict__ delta,
+                 double *__restrict__ mu)
 {
-    const int b = blockIdx.x;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n_part; i += blockDim.x) s += (double)sum_part[(size_t)i * B + b];
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        double d = t / (double)N;
+    const int b = blockIdx.x * kMeanWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= B) return;
+    float s = 0.f, lo = 0.f;
+    for (int i = lane; i < n_part; i += 32) df_acc(s, lo, sum_part[(size_t)i * B + b]);
+    for (int o = 16; o > 0; o >>= 1)
+        df_acc2(s, lo, __shfl_xor_sync(0xffffffffu, s, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    if (lane == 0) {
+        const double d = ((double)s + (double)lo) * inv_N;
         delta[b] = d;
         mu[b] = (double)shift[b] + d;
     }
 }
 
 // C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored, in
-// FP64 and as FP32 (hi, lo) pairs. A CTA
-// takes 32 consecutive entries e = b*B + c; its 8 warps each sum every 8th
-// partial (coalesced across the 32 entries), then the 8 slices are added.
+// FP64 and as FP32 (hi, lo) pairs. A CTA takes 32 consecutive entries
+// e = b*B + c; its 8 warps each sum every 8th partial (coalesced across the
+// 32 entries) in double-float, then the 8 slices are added.
 constexpr int kRedEntries = 32, kRedSlices = 8;
 __global__ void __launch_bounds__(kRedEntries * kRedSlices)
-gram_reduce_kernel(int B, long N, int n_part, const float *__restrict__ gram_part,
+gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gram_part,
                    const double *__restrict__ delta, double *__restrict__ C,
                    float2 *__restrict__ C2)
 {
@@ -181,16 +199,15 @@ gram_reduce_kernel(int B, long N, int n_part, const float *__restrict__ gram_par
     const long BB = (long)B * B;
     const int b = e < BB ? (int)(e / B) : 0, c = e < BB ? (int)(e % B) : 0;
     const bool active = e < BB && c >= b;
-    double g = 0.0;
+    float s = 0.f, lo = 0.f;
     if (active)
-        for (int i = slice; i < n_part; i += kRedSlices) g += (double)gram_part[(size_t)i * BB + e];
-    __shared__ double part[kRedSlices][kRedEntries];
-    part[slice][lane] = g;
+        for (int i = slice; i < n_part; i += kRedSlices) df_acc(s, lo, gram_part[(size_t)i * BB + e]);
+    __shared__ float2 part[kRedSlices][kRedEntries];
+    part[slice][lane] = make_float2(s, lo);
     __syncthreads();
     if (slice == 0 && active) {
-        double t = 0.0;
-        for (int k = 0; k < kRedSlices; ++k) t += part[k][lane];
-        double v = t / (double)N - delta[b] * delta[c];
+        for (int k = 1; k < kRedSlices; ++k) df_acc2(s, lo, part[k][lane].x, part[k][lane].y);
+        const double v = fma(-delta[b], delta[c], ((double)s + (double)lo) * inv_N);
         C[(size_t)b * B + c] = v;
         C[(size_t)c * B + b] = v;
         // the same value as an unevaluated FP32 sum hi + lo (for the
@@ -213,10 +230,12 @@ int moments_partitions(int sm_count) { return 2 * sm_count; }
 // the Jacobi kernel overwrites it with the eigenvector).
 static cudaError_t launch_reductions(int B, long N, int n_part, const PcaScratch &s, cudaStream_t st)
 {
-    band_mean_kernel<<<B, 128, 0, st>>>(B, N, n_part, s.shift, s.sum_part, s.v1, s.mu);
+    const double inv_N = 1.0 / (double)N;
+    band_mean_kernel<<<(B + kMeanWarps - 1) / kMeanWarps, 32 * kMeanWarps, 0, st>>>(
+        B, inv_N, n_part, s.shift, s.sum_part, s.v1, s.mu);
     const long BB = (long)B * B;
     gram_reduce_kernel<<<(unsigned)((BB + kRedEntries - 1) / kRedEntries), kRedEntries * kRedSlices,
-                         0, st>>>(B, N, n_part, s.gram_part, s.v1, s.C, s.C2);
+                         0, st>>>(B, inv_N, n_part, s.gram_part, s.v1, s.C, s.C2);
     return cudaGetLastError();
 }
 
