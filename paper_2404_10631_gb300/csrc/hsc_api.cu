@@ -343,6 +343,7 @@ hsc_status hsc_ctx_create(int device, void *cuda_stream, size_t scratch_cap_byte
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess && !cuda_stream) e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = hsc::knn_init(device);
     if (e != cudaSuccess) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
         delete ctx;
@@ -1060,6 +1061,7 @@ hsc_status hsc_server_create(int device, size_t hbm_budget_bytes, int max_inflig
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&srv->events[i], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaMallocHost(&srv->h_status, sizeof(unsigned) * kMaxSlots);
+    if (e == cudaSuccess) e = hsc::knn_init(device);
     if (e != cudaSuccess) {
         cudaGetLastError();
         for (int i = 0; i < max_inflight; ++i) {

@@ -29,7 +29,9 @@ struct Control {
     unsigned long long knn_evals;  // candidates evaluated by the pruned KNN since last read
     unsigned long long jacobi_sweep_cycles;   // SM clock cycles in the FP32 sweeps
     unsigned long long jacobi_refine_cycles;  // SM clock cycles in the FP64 refinement
-    unsigned pad[52];
+    unsigned knn_redo;        // pixels the pruned KNN left to its redo pass (reset by it)
+    unsigned knn_redo_ctas;   // redo CTAs finished (reset with knn_redo)
+    unsigned pad[50];
 };
 
 // Float <-> order-preserving unsigned key (for atomic min/max of floats).
@@ -97,6 +99,9 @@ cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control 
 
 // KNN filter (Eq. 1, Eq. 2) over all pixels: the full-window scan, or (pruned
 // and lambda > 0) the exact spatially pruned walk; both select the same sets.
+// Uploads the pruned walk's offset table to the current device (once).
+cudaError_t knn_init(int device);
+
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr,
                        Control *ctl, cudaStream_t st, bool pruned);

@@ -25,6 +25,11 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+#include <array>
+#include <mutex>
+#include <vector>
+
 #include "hsc_internal.cuh"
 
 namespace hsc {
@@ -278,99 +283,510 @@ knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int 
     (void)lane;
 }
 
-// Exact, spatially pruned variant. Every key is at least fl(lambda^2) *
-// (dr^2 + dc^2) (rounded down by at most one ulp), and the seed bounds the
-// K-th smallest key by tau, so only candidates with dr^2 + dc^2 <=
-// tau (1 + 2^-20) / fl(lambda^2) can be among the K nearest. Each lane walks
-// exactly that disk of its own pixel (truncated to the window), keeps keys
-// <= tau, and selects the best K as the full-window kernel does: the result
-// is the same set. Lanes of a warp share (dr, dc), so their loads of I are
-// consecutive. Requires lambda > 0.
-__global__ void __launch_bounds__(kThreads)
-knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int H, int W,
-                  int K, int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
-                  int32_t *__restrict__ nbr, Control *ctl)
+// ---- exact, spatially pruned variant (lambda > 0)
+//
+// Every key is at least s_term = fl(lambda^2 (dr^2 + dc^2)), which grows with
+// the squared spatial distance s = dr^2 + dc^2. Let s_K be the K-th smallest
+// s among the pixel's valid candidates and L = fl(lambda^2 s_K): K candidates
+// have s_term <= L and every key is >= its s_term, so the K-th smallest key
+// lies in [L, tau] for any upper bound tau. Then:
+//  * tau: for a pixel whose K spatially nearest offsets (the first K of a
+//    table of offsets sorted by s) all lie in the window, tau = L + e_max,
+//    rounded up, with e_max = (max I - min I)^2 over the CTA's I tile; near
+//    the image edges, the largest key of the first K valid offsets of the
+//    table (a walk with validity checks);
+//  * the disk s_term <= tau is walked row by row from the I tile staged in
+//    shared memory (beyond it every key exceeds tau: a float s_term above
+//    tau.hi is at least tau.hi + ulp). A key below L is strictly below the
+//    K-th smallest, so it is one of the K nearest: its probabilities are
+//    summed at once, with no storage (at most K - 1 such). Keys in [L, tau]
+//    go to a small per-lane buffer (compacted to the best K - m when full,
+//    which tightens tau), and its K - m smallest (m the count of the first
+//    kind) complete the set: the same set as the full-window scan.
+// A pixel that cannot finish this way (its disk leaves the tile, the buffer
+// cannot hold the undecided keys, fewer than K valid offsets in the table,
+// or neighbour-index output) gets the sentinel label kRedoLabel and
+// knn_redo_kernel completes it with an unbounded walk.
+constexpr int kWalkThreads = 64;
+constexpr int kTabR2 = 400;            // table: dr^2 + dc^2 <= 400
+constexpr int kTabDr = 16;             // |dr| <= 16: windows of up to 32 rows
+constexpr int kTabDc = 20;             // |dc| <= 20 follows from kTabR2
+constexpr int kTabCap = 1200;
+constexpr int kBnd = 32;               // undecided keys per lane
+constexpr int kRedoLabel = -2147483647 - 1;
+constexpr int kRedoThreads = 32;
+constexpr int kRedoExtra = 32;         // redo buffer slots beyond K
+__constant__ char2 c_knn_tab[kTabCap];
+__constant__ int c_knn_tab_n;
+// extent of the first K table offsets (K = 1..64): max |dr| above and below,
+// max |dc|, and s of the K-th
+__constant__ char4 c_knn_pref[HSC_MAX_K + 1];
+
+// Key buffer of one lane: column `lane` of [cap][stride] arrays in shared
+// memory (consecutive lanes, consecutive words).
+struct LaneBuf {
+    float *hi, *lo;
+    int *q;
+    int stride;
+    __device__ Key get(int i) const
+    {
+        const int o = i * stride;
+        return Key{hi[o], lo[o], q[o]};
+    }
+    __device__ void put(int i, const Key &k) const
+    {
+        const int o = i * stride;
+        hi[o] = k.hi;
+        lo[o] = k.lo;
+        q[o] = k.q;
+    }
+};
+
+// Move the `want` smallest of buf[0..n) to buf[0..want) (Hoare quickselect;
+// keys are distinct, ties being broken by q).
+__device__ __noinline__ void select_k(const LaneBuf &buf, int n, int want)
 {
-    const int r = blockIdx.y;
-    const int c = blockIdx.x * kThreads + threadIdx.x;
+    int lo = 0, hi = n - 1;
+    const int target = want - 1;
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        const Key a = buf.get(lo), b = buf.get(mid), c = buf.get(hi);
+        const Key piv = key_lt(a, b) ? (key_lt(b, c) ? b : (key_lt(a, c) ? c : a))
+                                     : (key_lt(a, c) ? a : (key_lt(b, c) ? c : b));
+        int i = lo, j = hi;
+        while (i <= j) {
+            while (key_lt(buf.get(i), piv)) ++i;
+            while (key_lt(piv, buf.get(j))) --j;
+            if (i <= j) {
+                const Key t = buf.get(i);
+                buf.put(i, buf.get(j));
+                buf.put(j, t);
+                ++i;
+                --j;
+            }
+        }
+        if (target <= j) hi = j;
+        else if (target >= i) lo = i;
+        else break;
+    }
+}
+
+__device__ __noinline__ Key buf_max(const LaneBuf &buf, int n)
+{
+    Key m = buf.get(0);
+    for (int i = 1; i < n; ++i) {
+        const Key k = buf.get(i);
+        if (key_lt(m, k)) m = k;
+    }
+    return m;
+}
+
+// Adds the probabilities of the KC classes of candidate q to acc.
+template <int KC>
+__device__ __forceinline__ void add_probs(float (&acc)[KC], const float *__restrict__ P, long N,
+                                          int q)
+{
+#pragma unroll
+    for (int cl = 0; cl < KC; ++cl) acc[cl] += __ldg(P + (size_t)cl * (size_t)N + q);
+}
+
+template <int KC>
+__device__ __forceinline__ void write_pixel(const float (&acc)[KC], int K, long N, long p,
+                                            float *__restrict__ O, int32_t *__restrict__ labels)
+{
+    const float invK = 1.f / (float)K;
+    int best = 0;
+    float bestv = -INFINITY;
+#pragma unroll
+    for (int cl = 0; cl < KC; ++cl) {
+        const float o = acc[cl] * invK;
+        if (O) O[(size_t)cl * (size_t)N + p] = o;
+        if (o > bestv) {
+            bestv = o;
+            best = cl;
+        }
+    }
+    labels[p] = best;
+}
+
+template <int KC>
+__global__ void __launch_bounds__(kWalkThreads)
+knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
+                  int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
+                  bool redo_all, Control *ctl)
+{
+    extern __shared__ float sm[];
+    __shared__ float s_min[kWalkThreads / 32], s_max[kWalkThreads / 32];
+    const int r = blockIdx.y, lane = threadIdx.x;
+    const int c0 = blockIdx.x * kWalkThreads, c = c0 + lane;
     const bool active = c < W;
     const int lo_r = max(0, r - R / 2);
     const int hi_r = min(H - 1, r + (R + 1) / 2 - 1);
+    const int nrows = hi_r - lo_r + 1;
+    const int tw = kWalkThreads + 2 * kTabDc, tcol0 = c0 - kTabDc;
+    float *tile = sm;  // nrows x tw
+    LaneBuf bnd;
+    bnd.stride = kWalkThreads;
+    bnd.hi = tile + nrows * tw + lane;
+    bnd.lo = bnd.hi + kBnd * kWalkThreads;
+    bnd.q = reinterpret_cast<int *>(bnd.lo + kBnd * kWalkThreads);
     const float l2 = lam * lam;
     const long N = (long)H * W;
-    const float Ip = active ? I[(long)r * W + c] : 0.f;
-    bool bad = !isfinite(Ip);
 
-    // seed: the K spatially nearest valid candidates bound the K-th key
-    Key tau;
-    tau.hi = -1.f;
-    tau.lo = 0.f;
-    tau.q = -1;
-    int cnt = active ? 0 : K;
-    {
-        const int dlo = lo_r - r, dhi = hi_r - r;
-        const int smax = max(dlo * dlo, dhi * dhi) + (W - 1) * (W - 1);
-        for (int s = 0; s <= smax; ++s) {
-            for (int dr = dlo; dr <= dhi; ++dr) {
-                int m = s - dr * dr;
-                if (m < 0) continue;
-                int dc = (int)sqrtf((float)m);
-                while (dc * dc > m) --dc;
-                while ((dc + 1) * (dc + 1) <= m) ++dc;
-                if (dc * dc != m) continue;
+    // stage the window rows x (64 + 2 * 20) columns: asynchronous 4-byte
+    // copies, all in flight at once (out-of-image columns are zero-filled)
+    for (int ii = 0; ii < nrows; ++ii) {
+        const float *row = I + (long)(lo_r + ii) * W;
+        for (int jj = lane; jj < tw; jj += kWalkThreads) {
+            const int col = tcol0 + jj;
+            const bool in = col >= 0 && col < W;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ii * tw + jj);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst),
+                         "l"(in ? row + col : row), "r"(in ? 4 : 0)
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    bool bad = false;
+    float vmin = INFINITY, vmax = -INFINITY;
+    for (int ii = 0; ii < nrows; ++ii) {
+        for (int jj = lane; jj < tw; jj += kWalkThreads) {
+            const int col = tcol0 + jj;
+            if (col < 0 || col >= W) continue;
+            const float v = tile[ii * tw + jj];
+            bad |= !isfinite(v);
+            vmin = fminf(vmin, v);
+            vmax = fmaxf(vmax, v);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    if ((lane & 31) == 0) {
+        s_min[lane >> 5] = vmin;
+        s_max[lane >> 5] = vmax;
+    }
+    __syncthreads();
+    vmin = s_min[0];
+    vmax = s_max[0];
+    for (int w = 1; w < kWalkThreads / 32; ++w) {
+        vmin = fminf(vmin, s_min[w]);
+        vmax = fmaxf(vmax, s_max[w]);
+    }
+
+    const float Ip = active ? tile[(r - lo_r) * tw + (c - tcol0)] : 0.f;
+    unsigned evals = 0;
+    bool redo = active && redo_all;
+
+    // the bound tau and s_K
+    const char4 pf = c_knn_pref[K];  // (max dr above, max dr below, max |dc|, s of the K-th)
+    const bool inner = r - pf.x >= lo_r && r + pf.y <= hi_r && c - pf.z >= 0 && c + pf.z < W;
+    Key tau = {-1.f, 0.f, -1};
+    int sK = pf.w;
+    if (inner) {
+        // every key of the K nearest is <= L + e_max (exact sum, rounded up)
+        const float dI = __fsub_ru(vmax, vmin);  // >= |fl(I_p - I_q)| in the tile
+        const float em = __fmul_ru(dI, dI);
+        tau.hi = __fadd_ru(__fmul_rn(l2, (float)sK), em);
+        tau.lo = 0.f;
+        tau.q = 0x7fffffff;
+    } else {
+        int cnt = 0;
+        bool done = !active || redo;
+        const int ntab = c_knn_tab_n;
+        for (int t = 0; t < ntab && !done; ++t) {
+            const char2 o = c_knn_tab[t];
+            const int dr = o.x, dc = o.y;
+            const int i = r + dr, j = c + dc;
+            if (i < lo_r || i > hi_r || j < 0 || j >= W) continue;
+            const Key kk = make_key(Ip, tile[(i - lo_r) * tw + (j - tcol0)], dr, dc, l2, i * W + j);
+            if (cnt == 0 || key_lt(tau, kk)) tau = kk;
+            if (++cnt == K) {
+                sK = dr * dr + dc * dc;
+                done = true;
+            }
+        }
+        evals += (unsigned)cnt;
+        if (active && cnt < K) redo = true;
+    }
+    const float L = __fmul_rn(l2, (float)sK);
+
+    // the disk s_term <= tau, row by row over the tile. The rounded sum
+    // h = fl(s_term + e) decides almost every candidate on its own (rounding
+    // is monotone: h < L means s_term + e < L, h > tau.hi means the key
+    // exceeds tau); the exact low part is formed only when h meets a bound.
+    float acc[KC];
 #pragma unroll
-                for (int sg = 0; sg < 2; ++sg) {
-                    if (sg == 1 && dc == 0) break;
-                    int j = sg ? c - dc : c + dc;
-                    if (cnt < K && j >= 0 && j < W) {
-                        int q = (r + dr) * W + j;
-                        Key kk = make_key(Ip, __ldg(I + q), dr, dc, l2, q);
-                        if (cnt == 0 || key_lt(tau, kk)) tau = kk;
-                        ++cnt;
-                    }
+    for (int cl = 0; cl < KC; ++cl) acc[cl] = 0.f;
+    int m = 0, nb = 0;
+    if (active && !redo) {
+        const float smax = __fdiv_ru(tau.hi * (1.f + 1.f / 1048576.f), l2);
+        for (int i = lo_r; i <= hi_r && !redo; ++i) {
+            const int dr = i - r;
+            const float rem = smax - (float)(dr * dr);
+            if (rem < 0.f) continue;
+            const int cm = (int)sqrtf(rem) + 1;
+            if (cm > kTabDc) {  // the disk leaves the tile
+                redo = true;
+                break;
+            }
+            const int j0 = max(0, c - cm), j1 = min(W - 1, c + cm);
+            const float *trow = tile + (i - lo_r) * tw - tcol0;
+            const int dr2 = dr * dr, qrow = i * W;
+            for (int j = j0; j <= j1; ++j) {
+                ++evals;
+                const int dc = c - j;
+                const float dI = __fsub_rn(Ip, trow[j]);
+                const float e = __fmul_rn(dI, dI);
+                const float st = __fmul_rn(l2, (float)(dr2 + dc * dc));
+                const float h = __fadd_rn(st, e);
+                if (h < L) {  // one of the K nearest
+                    ++m;
+                    add_probs(acc, P, N, qrow + j);
+                    continue;
                 }
-            }
-            if (__all_sync(0xffffffffu, cnt >= K)) break;
-        }
-    }
-    if (active && cnt < K) atomicOr(&ctl->status, ST_KNN_SHORT);
-    unsigned evals = active ? (unsigned)cnt : 0u;
-
-    // collect every candidate of the disk whose key is <= tau
-    Key buf[kCap];
-    int n = 0;
-    const float smax_f = active ? __fdiv_ru(tau.hi * (1.f + 1.f / 1048576.f), l2) : -1.f;
-    for (int i = lo_r; i <= hi_r; ++i) {
-        const int dr = i - r;
-        const float rem = smax_f - (float)(dr * dr);
-        if (rem < 0.f) continue;
-        const int cm = (int)sqrtf(rem) + 1;
-        const int j0 = max(0, c - cm), j1 = min(W - 1, c + cm);
-        evals += (unsigned)max(0, j1 - j0 + 1);
-        for (int j = j0; j <= j1; ++j) {
-            const int q = i * W + j;
-            const float Iq = __ldg(I + q);
-            bad |= !isfinite(Iq);
-            Key kk = make_key(Ip, Iq, dr, c - j, l2, q);
-            if (!key_le(kk, tau)) continue;
-            if (n == kCap) {
-                shrink(buf, n, K);
-                tau = max_key(buf, n);
+                if (h > tau.hi) continue;
+                const float bb = __fsub_rn(h, st);
+                const float lo = __fadd_rn(__fsub_rn(st, __fsub_rn(h, bb)), __fsub_rn(e, bb));
+                const Key kk = {h, lo, qrow + j};
+                if (h == L && lo < 0.f) {
+                    ++m;
+                    add_probs(acc, P, N, qrow + j);
+                    continue;
+                }
                 if (!key_le(kk, tau)) continue;
+                if (nb == kBnd) {
+                    if (K - m >= kBnd) {  // cannot make room: leave the pixel to the redo pass
+                        redo = true;
+                        break;
+                    }
+                    select_k(bnd, nb, K - m);
+                    nb = K - m;
+                    tau = buf_max(bnd, nb);
+                    if (!key_le(kk, tau)) continue;
+                }
+                bnd.put(nb++, kk);
             }
-            buf[n++] = kk;
         }
     }
-    if (bad) atomicOr(&ctl->status, ST_NONFINITE_MAP);
+    bad |= active && !isfinite(Ip);
+    if (__syncthreads_or(bad) && lane == 0) atomicOr(&ctl->status, ST_NONFINITE_MAP);
+    const unsigned nredo = __syncthreads_count(redo);
+    if (lane == 0 && nredo) atomicAdd(&ctl->knn_redo, nredo);
     {
         unsigned long long e = evals;
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(&ctl->knn_evals, e);
+        if ((lane & 31) == 0) atomicAdd(&ctl->knn_evals, e);
     }
     if (!active) return;
+    const long p = (long)r * W + c;
+    if (redo) {
+        labels[p] = kRedoLabel;
+        return;
+    }
+    const int need = K - m;
+    if (need > nb) {  // cannot happen: the K-th smallest key is <= tau
+        labels[p] = kRedoLabel;
+        atomicAdd(&ctl->knn_redo, 1u);
+        return;
+    }
+    // the need smallest undecided keys: need passes of a minimum search
+    // (need is small: the K nearest are mostly decided by h < L)
+    for (int a = 0; a < need; ++a) {
+        int im = a;
+        Key best = bnd.get(a);
+        for (int b = a + 1; b < nb; ++b) {
+            const float hb = bnd.hi[b * kWalkThreads];
+            if (hb > best.hi) continue;
+            const Key kb = bnd.get(b);
+            if (key_lt(kb, best)) {
+                best = kb;
+                im = b;
+            }
+        }
+        if (im != a) bnd.put(im, bnd.get(a));
+        add_probs(acc, P, N, best.q);
+    }
+    write_pixel(acc, K, N, p, O, labels);
+}
+
+template <int KC>
+__device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float *__restrict__ P,
+                                        int H, int W, int K, int R, float lam,
+                                        float *__restrict__ O, int32_t *__restrict__ labels,
+                                        int32_t *__restrict__ nbr, Control *ctl, long p, float *sm)
+{
+    const long N = (long)H * W;
+    const int cap = K + kRedoExtra;
+    LaneBuf buf;
+    buf.stride = kRedoThreads;
+    buf.hi = sm + threadIdx.x;
+    buf.lo = buf.hi + cap * kRedoThreads;
+    buf.q = reinterpret_cast<int *>(buf.lo + cap * kRedoThreads);
+    const int r = (int)(p / W), c = (int)(p - (long)r * W);
+    const int lo_r = max(0, r - R / 2);
+    const int hi_r = min(H - 1, r + (R + 1) / 2 - 1);
+    const float l2 = lam * lam;
+    const float Ip = __ldg(I + p);
+    bool bad = !isfinite(Ip);
+    Key tau = {-1.f, 0.f, -1};
+    int n = 0;
+    bool have = false;
+    unsigned long long evals = 0;
+    auto consider = [&](const Key &kk) {
+        ++evals;
+        if (!have) {
+            buf.put(n++, kk);
+            if (n == 1 || key_lt(tau, kk)) tau = kk;
+            if (n == K) have = true;
+            return;
+        }
+        if (!key_le(kk, tau)) return;
+        if (n == cap) {
+            select_k(buf, n, K);
+            n = K;
+            tau = buf_max(buf, n);
+            if (!key_le(kk, tau)) return;
+        }
+        buf.put(n++, kk);
+    };
+    bool stopped = false;
+    const int ntab = c_knn_tab_n;
+    for (int t = 0; t < ntab; ++t) {
+        const char2 o = c_knn_tab[t];
+        const int dr = o.x, dc = o.y;
+        if (have && __fmul_rn(l2, (float)(dr * dr + dc * dc)) > tau.hi) {
+            stopped = true;
+            break;
+        }
+        const int i = r + dr, j = c + dc;
+        if (i < lo_r || i > hi_r || j < 0 || j >= W) continue;
+        const int q = i * W + j;
+        const float Iq = __ldg(I + q);
+        bad |= !isfinite(Iq);
+        consider(make_key(Ip, Iq, dr, dc, l2, q));
+    }
+    if (!stopped) {
+        // beyond the table: every remaining candidate while fewer than K are
+        // in, else the disk s_term <= tau; offsets the table covered skipped
+        for (int i = lo_r; i <= hi_r; ++i) {
+            const int dr = i - r;
+            int j0 = 0, j1 = W - 1;
+            if (have) {
+                const float rem = __fdiv_ru(tau.hi * (1.f + 1.f / 1048576.f), l2) - (float)(dr * dr);
+                if (rem < 0.f) continue;
+                const int cm = (int)sqrtf(rem) + 1;
+                j0 = max(0, c - cm);
+                j1 = min(W - 1, c + cm);
+            }
+            for (int j = j0; j <= j1; ++j) {
+                const int dc = j - c;
+                if (dr >= -kTabDr && dr <= kTabDr && dr * dr + dc * dc <= kTabR2) continue;
+                const int q = i * W + j;
+                const float Iq = __ldg(I + q);
+                bad |= !isfinite(Iq);
+                consider(make_key(Ip, Iq, dr, dc, l2, q));
+            }
+        }
+    }
+    if (bad) atomicOr(&ctl->status, ST_NONFINITE_MAP);
+    atomicAdd(&ctl->knn_evals, evals);
     if (n < K) atomicOr(&ctl->status, ST_KNN_SHORT);
-    shrink(buf, n, K);
-    finish_pixel(buf, n, K, P, k, N, (long)r * W + c, O, labels, nbr);
+    if (n > K) {
+        select_k(buf, n, K);
+        n = K;
+    }
+    if (nbr) {  // nearest first (selection sort; debug output)
+        for (int a = 0; a < n; ++a) {
+            int im = a;
+            Key best = buf.get(a);
+            for (int b = a + 1; b < n; ++b) {
+                const Key kb = buf.get(b);
+                if (key_lt(kb, best)) {
+                    best = kb;
+                    im = b;
+                }
+            }
+            if (im != a) {
+                buf.put(im, buf.get(a));
+                buf.put(a, best);
+            }
+            nbr[p * K + a] = best.q;
+        }
+        for (int a = n; a < K; ++a) nbr[p * K + a] = -1;
+    }
+    float acc[KC];
+#pragma unroll
+    for (int cl = 0; cl < KC; ++cl) acc[cl] = 0.f;
+    for (int a = 0; a < n; ++a) add_probs(acc, P, N, buf.q[a * kRedoThreads]);
+    write_pixel(acc, K, N, p, O, labels);
+}
+
+
+// Completes the pixels knn_pruned_kernel left with the sentinel label: a walk
+// from global memory (the table in increasing s, then row by row over the
+// rest of the window, or of the disk s_term <= tau once K are in), keeping
+// every key <= tau in a buffer of K + 32 (compacted to the best K when full),
+// then the best K. A persistent grid; when the pruned kernel flagged nothing
+// its CTAs exit at once, otherwise they scan the labels for the sentinel and
+// the last CTA to finish resets the counters.
+template <int KC>
+__global__ void __launch_bounds__(kRedoThreads)
+knn_redo_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
+                int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
+                int32_t *__restrict__ nbr, Control *ctl)
+{
+    extern __shared__ float sm[];
+    const long N = (long)H * W;
+    if (*(volatile unsigned *)&ctl->knn_redo == 0u) return;
+    for (long base = (long)blockIdx.x * kRedoThreads; base < N;
+         base += (long)gridDim.x * kRedoThreads) {
+        const long p = base + threadIdx.x;
+        if (p < N && labels[p] == kRedoLabel)
+            redo_pixel<KC>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, p, sm);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl->knn_redo_ctas, 1u) == gridDim.x - 1) {
+            ctl->knn_redo = 0u;
+            ctl->knn_redo_ctas = 0u;
+            __threadfence();
+        }
+    }
+}
+
+size_t pruned_smem_bytes(int R, int H)
+{
+    const int nrows = R < H ? R : H;
+    return sizeof(float) *
+           ((size_t)nrows * (kWalkThreads + 2 * kTabDc) + 3 * (size_t)kBnd * kWalkThreads);
+}
+
+size_t redo_smem_bytes(int K) { return sizeof(float) * 3 * (size_t)(K + kRedoExtra) * kRedoThreads; }
+
+template <int KC>
+cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, int R, float lam,
+                          float *O, int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st)
+{
+    const size_t smem = pruned_smem_bytes(R, H);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(knn_pruned_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    dim3 grid((W + kWalkThreads - 1) / kWalkThreads, H);
+    knn_pruned_kernel<KC><<<grid, kWalkThreads, smem, st>>>(I, P, H, W, K, R, lam, O, labels,
+                                                            nbr != nullptr, ctl);
+    const long N = (long)H * W;
+    const size_t rsmem = redo_smem_bytes(K);
+    if (rsmem > 48 * 1024)
+        cudaFuncSetAttribute(knn_redo_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rsmem);
+    const long rgrid = (N + kRedoThreads - 1) / kRedoThreads;  // persistent: at most 64 CTAs
+    knn_redo_kernel<KC><<<(unsigned)(rgrid < 64 ? rgrid : 64), kRedoThreads, rsmem, st>>>(
+        I, P, H, W, K, R, lam, O, labels, nbr, ctl);
+    return cudaGetLastError();
 }
 
 template <int RMAX>
@@ -390,15 +806,59 @@ cudaError_t launch_rmax(const float *I, const float *P, int k, int H, int W, int
 
 }  // namespace
 
+// The offset table of the pruned walk: every (dr, dc) with |dr| <= 16 and
+// dr^2 + dc^2 <= 400, sorted by (dr^2 + dc^2, dr, dc), and the extent of its
+// first K entries; uploaded once per device (outside any stream capture:
+// context and server creation).
+cudaError_t knn_init(int device)
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[device]) return cudaSuccess;
+    std::vector<std::array<int, 3>> v;
+    for (int dr = -kTabDr; dr <= kTabDr; ++dr)
+        for (int dc = -kTabDc; dc <= kTabDc; ++dc)
+            if (dr * dr + dc * dc <= kTabR2) v.push_back({dr * dr + dc * dc, dr, dc});
+    std::sort(v.begin(), v.end());
+    if (v.size() > (size_t)kTabCap) return cudaErrorInvalidValue;
+    std::vector<char2> tab(v.size());
+    for (size_t i = 0; i < v.size(); ++i) tab[i] = make_char2((char)v[i][1], (char)v[i][2]);
+    const int nt = (int)v.size();
+    // extent of the first K offsets, K = 1..HSC_MAX_K
+    std::vector<char4> pref(HSC_MAX_K + 1, make_char4(0, 0, 0, 0));
+    int up = 0, down = 0, side = 0;
+    for (int K = 1; K <= HSC_MAX_K; ++K) {
+        const auto &e = v[K - 1];
+        up = std::max(up, -e[1]);
+        down = std::max(down, e[1]);
+        side = std::max(side, std::abs(e[2]));
+        pref[K] = make_char4((char)up, (char)down, (char)side, (char)e[0]);
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_knn_tab, tab.data(), sizeof(char2) * tab.size());
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_knn_tab_n, &nt, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_knn_pref, pref.data(), sizeof(char4) * pref.size());
+    if (e == cudaSuccess) done[device] = true;
+    return e;
+}
+
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr, Control *ctl,
                        cudaStream_t st, bool pruned)
 {
     if (pruned && lambda > 0.f) {
-        dim3 grid((W + kThreads - 1) / kThreads, H);
-        knn_pruned_kernel<<<grid, kThreads, 0, st>>>(I, P, k, H, W, K, R, lambda, O, labels, nbr,
-                                                     ctl);
-        return cudaGetLastError();
+        switch (k) {
+        case 1: return launch_pruned<1>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 2: return launch_pruned<2>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 3: return launch_pruned<3>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 4: return launch_pruned<4>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 5: return launch_pruned<5>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 6: return launch_pruned<6>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 7: return launch_pruned<7>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 8: return launch_pruned<8>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        default: return cudaErrorInvalidValue;
+        }
     }
     if (R <= 8) return launch_rmax<8>(I, P, k, H, W, K, R, lambda, O, labels, nbr, ctl, st);
     if (R <= 16) return launch_rmax<16>(I, P, k, H, W, K, R, lambda, O, labels, nbr, ctl, st);
