@@ -64,8 +64,10 @@ hsc_ctx g_untimed;  // never profiling: stage launches that are not timed
 
 struct StageTimer {
     hsc_ctx *ctx;
+    cudaStream_t st;
     int slot = -1;
-    StageTimer(hsc_ctx *c, int stage, int n_kernels) : ctx(c)
+    StageTimer(hsc_ctx *c, int stage, int n_kernels, cudaStream_t on = nullptr)
+        : ctx(c), st(on ? on : c->stream)
     {
         if (!ctx->profiling) return;
         ctx->kernels[stage] += n_kernels;
@@ -75,11 +77,11 @@ struct StageTimer {
         }
         slot = ctx->n_rec++;
         ctx->rec_stage[slot] = stage;
-        cudaEventRecord(ctx->ev[2 * slot], ctx->stream);
+        cudaEventRecord(ctx->ev[2 * slot], st);
     }
     ~StageTimer()
     {
-        if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], ctx->stream);
+        if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], st);
     }
 };
 
@@ -127,8 +129,9 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
     if (need_pca) {
         // at least kMinPartPixels pixels per partial Gram: a small frame
         // gets few partials instead of one per SM, whose reduction would
-        // read more bytes than the frame itself
-        constexpr long kMinPartPixels = 2048;
+        // read more bytes than the frame itself (a 416 x 512 frame still
+        // gets one tensor-core CTA per SM)
+        constexpr long kMinPartPixels = 1024;
         int np = hsc::moments_partitions(ctx->sm_count);
         np = (int)std::min<long>(np, std::max<long>(1, (N + kMinPartPixels - 1) / kMinPartPixels));
         size_t per = (size_t)B * B * sizeof(float);
@@ -280,27 +283,28 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
 {
     const long N = (long)H * W;
     const int k = model->n_classes;
+    hsc_ctx *tc = timed ? ctx : &g_untimed;
     cudaError_t e;
     {
-        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_MOMENTS, 4);
+        StageTimer t(tc, HSC_STAGE_MOMENTS, 4, st);
         e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, st);
     }
     if (e == cudaSuccess) {
-        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_JACOBI, 1);
+        StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);
         e = hsc::launch_jacobi(B, s, st);
     }
     if (e == cudaSuccess) {
-        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_PROJECT_SVM, 1);
+        StageTimer t(tc, HSC_STAGE_PROJECT_SVM, 1, st);
         e = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model,
                                     (flags & HSC_SVM_COUPLE_F64) != 0, Pm, nullptr, s.ctl,
                                     ctx->sm_count, st);
     }
     if (e == cudaSuccess) {
-        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_NORMALIZE, 1);
+        StageTimer t(tc, HSC_STAGE_NORMALIZE, 1, st);
         e = hsc::launch_normalize(I, I, N, s.ctl, st);
     }
     if (e == cudaSuccess) {
-        StageTimer t(timed ? ctx : &g_untimed, HSC_STAGE_KNN, 1);
+        StageTimer t(tc, HSC_STAGE_KNN, 2, st);
         e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
                             out_probs, labels, nullptr, s.ctl, st,
                             params->search != HSC_KNN_SEARCH_FULL);

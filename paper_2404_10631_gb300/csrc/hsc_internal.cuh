@@ -91,7 +91,7 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st);
 cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
                                const float *muf, float *I_raw, const hsc_svm_model *model,
                                bool couple_f64, float *probs, int32_t *svm_labels,
-                               Control *ctl, int sm_count, cudaStream_t st);
+                               Control *ctl, int sm_count, cudaStream_t st, int max_blocks = 0);
 
 // I_norm = (I - min)/(max - min) (0 if max == min), min/max from ctl keys.
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,

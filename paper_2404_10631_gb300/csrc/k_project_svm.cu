@@ -141,7 +141,9 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
 #pragma unroll
             for (int m = 0; m < MA; ++m) acc[m][u] = 0.f;
         }
-#pragma unroll 4
+        // deep unrolling keeps many independent loads in flight per thread
+        constexpr int kUnroll = PX == 1 ? 16 : 8;
+#pragma unroll kUnroll
         for (int b = 0; b < B; ++b) {
             float x[PX];
             const float *src = cube + (size_t)b * (size_t)N + p0;
@@ -230,7 +232,7 @@ __global__ void normalize_kernel(const float *__restrict__ I_raw, float *__restr
 template <int KC, int PX>
 cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const float *muf,
                       float *I_raw, const hsc_svm_model *m, bool f64, float *probs,
-                      int32_t *labels, Control *ctl, int sm_count, cudaStream_t st)
+                      int32_t *labels, Control *ctl, int sm_count, cudaStream_t st, int max_blocks)
 {
     constexpr int M = KC * (KC - 1) / 2;
     size_t smem = sizeof(float) * (size_t)B * (M + 2);
@@ -239,7 +241,7 @@ cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const 
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     long groups = (N + PX - 1) / PX;
     long blocks = (groups + kThreads - 1) / kThreads;
-    long cap = (long)sm_count * 8;
+    long cap = max_blocks > 0 ? (long)max_blocks : (long)sm_count * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, kThreads, smem, st>>>(
@@ -251,17 +253,18 @@ cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const 
 template <int PX>
 cudaError_t dispatch_k(int k, const float *cube, int B, long N, const float *v1f,
                        const float *muf, float *I_raw, const hsc_svm_model *m, bool f64,
-                       float *probs, int32_t *labels, Control *ctl, int sm, cudaStream_t st)
+                       float *probs, int32_t *labels, Control *ctl, int sm, cudaStream_t st,
+                       int mb)
 {
     switch (k) {
-    case 0: return launch_kc<0, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
-    case 2: return launch_kc<2, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
-    case 3: return launch_kc<3, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
-    case 4: return launch_kc<4, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
-    case 5: return launch_kc<5, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
-    case 6: return launch_kc<6, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
-    case 7: return launch_kc<7, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
-    case 8: return launch_kc<8, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st);
+    case 0: return launch_kc<0, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 2: return launch_kc<2, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 3: return launch_kc<3, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 4: return launch_kc<4, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 5: return launch_kc<5, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 6: return launch_kc<6, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 7: return launch_kc<7, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 8: return launch_kc<8, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -271,15 +274,15 @@ cudaError_t dispatch_k(int k, const float *cube, int B, long N, const float *v1f
 cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
                                const float *muf, float *I_raw, const hsc_svm_model *model,
                                bool couple_f64, float *probs, int32_t *svm_labels, Control *ctl,
-                               int sm_count, cudaStream_t st)
+                               int sm_count, cudaStream_t st, int max_blocks)
 {
     const int k = (probs != nullptr && model != nullptr) ? model->n_classes : 0;
     const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0);
     if (vec)
         return dispatch_k<4>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs, svm_labels,
-                             ctl, sm_count, st);
+                             ctl, sm_count, st, max_blocks);
     return dispatch_k<1>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs, svm_labels, ctl,
-                         sm_count, st);
+                         sm_count, st, max_blocks);
 }
 
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,

@@ -1,0 +1,110 @@
+"""Summaries of ncu CSV logs for the profiles folder.
+
+    python -m paper_2404_10631_gb300.ncu_summary launches LOG.csv
+        per kernel: launches, total time, time per launch, share (markdown)
+    python -m paper_2404_10631_gb300.ncu_summary traffic LOG.csv STAGE_LAUNCHES
+        per pipeline stage: DRAM bytes (read + write) per stage launch, as
+        "stage source_sha bytes" lines (the format bench.py reads), with
+        STAGE_LAUNCHES the number of times each stage ran in the capture
+
+LOG.csv comes from ``ncu --csv --log-file LOG.csv --metrics ...``.
+"""
+
+from __future__ import annotations
+
+import collections
+import csv
+import hashlib
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# kernel name prefix -> pipeline stage, and the source file each stage's
+# kernels live in (its hash tags the numbers with the code they measured)
+STAGE_OF = (("pilot_shift_kernel", "moments"), ("gram_tc_kernel", "moments"),
+            ("gram_partial_kernel", "moments"), ("band_mean_kernel", "moments"),
+            ("gram_reduce_kernel", "moments"), ("jacobi_kernel", "jacobi"),
+            ("project_svm_kernel", "project_svm"), ("normalize_kernel", "normalize"),
+            ("knn_pruned_kernel", "knn"), ("knn_redo_kernel", "knn"),
+            ("knn_kernel", "knn_full"))
+SOURCE_OF = {"moments": "k_moments.cu", "jacobi": "k_jacobi.cu",
+             "project_svm": "k_project_svm.cu", "normalize": "k_project_svm.cu",
+             "knn": "k_knn.cu", "knn_full": "k_knn.cu"}
+
+
+def source_sha(stage: str) -> str:
+    path = os.path.join(HERE, "csrc", SOURCE_OF[stage])
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def kernel_base(name: str) -> str:
+    """'void (anonymous namespace)::knn_kernel<16>(...)' -> 'knn_kernel<16>'"""
+    n = name.split("(")[0] if "(" in name and not name.startswith("(") else name
+    n = n.replace("void ", "")
+    if "::" in n:
+        n = n.split("::")[-1]
+    return n.strip()
+
+
+def read(path: str):
+    rows = [r for r in csv.reader(open(path)) if len(r) > 5]
+    hdr = rows[0]
+    ki, mi, vi = hdr.index("Kernel Name"), hdr.index("Metric Name"), hdr.index("Metric Value")
+    idi = hdr.index("ID")
+    launches = collections.OrderedDict()
+    for r in rows[1:]:
+        key = int(r[idi])
+        d = launches.setdefault(key, {"kernel": kernel_base(r[ki])})
+        d[r[mi]] = float(r[vi].replace(",", ""))
+    return list(launches.values())
+
+
+def stage_of(kernel: str):
+    for prefix, st in STAGE_OF:
+        if kernel.startswith(prefix):
+            return st
+    return None
+
+
+def launches_table(path: str) -> str:
+    tot = collections.OrderedDict()
+    cnt = collections.Counter()
+    for d in read(path):
+        t = d.get("gpu__time_duration.sum")
+        if t is None:
+            continue
+        tot[d["kernel"]] = tot.get(d["kernel"], 0.0) + t
+        cnt[d["kernel"]] += 1
+    all_t = sum(tot.values())
+    out = ["| kernel | launches | total us | us / launch | share |", "|---|---|---|---|---|"]
+    for k, t in sorted(tot.items(), key=lambda x: -x[1]):
+        out.append("| %s | %d | %.1f | %.1f | %.1f%% |" % (k, cnt[k], t / 1e3, t / 1e3 / cnt[k],
+                                                          100.0 * t / all_t))
+    return "\n".join(out)
+
+
+def traffic_lines(path: str, stage_launches: int) -> str:
+    tot = collections.defaultdict(float)
+    for d in read(path):
+        st = stage_of(d["kernel"])
+        if st is None:
+            continue
+        tot[st] += d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
+    return "\n".join("%s %s %.0f" % (st, source_sha(st), b / stage_launches)
+                     for st, b in sorted(tot.items()))
+
+
+def main(argv):
+    if len(argv) >= 2 and argv[0] == "launches":
+        print(launches_table(argv[1]))
+    elif len(argv) >= 3 and argv[0] == "traffic":
+        print(traffic_lines(argv[1], int(argv[2])))
+    else:
+        print(__doc__)
+        return 2
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

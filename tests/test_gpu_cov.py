@@ -9,8 +9,8 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-# FP32 accumulation of 1400-2048 pixels per partial (relative ~2e-6; frames
-# are cut into partials of at least 2048 pixels, at most one per SM pair),
+# FP32 accumulation of 1024-2048 pixels per partial (relative ~2e-6; frames
+# are cut into partials of at least 1024 pixels, at most one per SM pair),
 # FP16 hi/lo split of the shifted pixels (~2^-22 per product): 1e-5 of max|C|.
 C_TOL = 1e-5
 MU_TOL = 1e-6
