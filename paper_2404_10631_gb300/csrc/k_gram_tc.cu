@@ -1,5 +1,14 @@
 // Covariance Gram on the 5th-generation tensor cores (Section II.C.2 step (ii),
-// III.A.2.b): G = sum_p y_p y_p^T over the shifted pixels y = x - s, B <= 128.
+// III.A.2.b): G = sum_p y_p y_p^T over the shifted pixels y = x - s, B <= 256.
+//
+// B <= 128 (the description below): one launch, M = N = B. 128 < B <= 256:
+// two launches, one per 128-band half of the rows of G (rows 0-127 x every
+// column, rows 128-255 x columns 128-255: the upper triangle is all the
+// reduction reads); each converts all B bands of a chunk and multiplies the
+// half's rows by the columns it needs (N <= 256). There a single hi.hi^T
+// accumulator and the cross-term accumulator fill the 512 TMEM columns, the
+// staging ring has 2 stages and the operands 1, to fit 256-row tiles in
+// shared memory; the cube is read once per launch.
 //
 // Per CTA (one per SM, a contiguous range of 64-pixel chunks):
 //   warp 0   TMA producer: each chunk is two 32-pixel x B-band FP32 boxes
@@ -14,7 +23,9 @@
 //   warps 2-5 converters: y = 16 (x - s) split into FP16 hi + lo (hi + lo
 //            carries y to ~2^-22), written in the 128-byte-swizzled K-major
 //            operand layout; band sums of y; then the epilogue reads the
-//            accumulator (tcgen05.ld) and writes this CTA's partial Gram.
+//            accumulator (tcgen05.ld) and adds it into this CTA's partial
+//            Gram, stored transposed (entry (b, c) at c * B + b), every 24
+//            chunks per accumulator.
 // The dropped lo.lo^T term is below 2^-22 of each product. Accumulation is
 // FP32 in TMEM; the partials are summed in FP64 by gram_reduce_kernel. Every
 // mbarrier wait is bounded: on expiry the kernel flags ST_TIMEOUT, stops
@@ -30,16 +41,32 @@ namespace {
 
 constexpr int kThreads = 192;
 constexpr int kChunk = 64;               // pixels per chunk (one 128-byte fp16 row)
-constexpr int kStages = 3;               // TMA staging ring
 constexpr int kBoxPx = 32;               // pixels per TMA box (128 bytes of fp32)
-constexpr int kRows = 128;               // MMA M (bands, zero padded)
-constexpr uint32_t kBoxBytes = kRows * 128;           // 16 KB per box slot
-constexpr uint32_t kStageBytes = 2 * kBoxBytes;       // two boxes per chunk
-constexpr uint32_t kOpBytes = kRows * 128;            // one fp16 operand tile
+constexpr int kM = 128;                  // MMA M (bands of one half, zero padded)
 constexpr uint32_t kWaitLimit = 1u << 22;
 constexpr float kScale = 16.f;                        // y scaled into fp16's sweet spot
-constexpr int kAccHH = 3;                             // accumulators for hi.hi^T
-constexpr uint32_t kTmemCols = 512;                   // 4 accumulators x 128 columns
+constexpr uint32_t kTmemCols = 512;
+
+// B <= 128: 128 converted rows, 3 staging stages, 2 operand stages, three
+// hi.hi^T accumulators (columns 0, 128, 256) and the cross terms at 384.
+// 128 < B <= 256: 256 rows, 2 + 1 stages, hi.hi^T at 0 and cross at 256.
+template <bool kWide>
+struct Cfg {
+    static constexpr int kRows = kWide ? 256 : 128;
+    static constexpr int kStages = kWide ? 2 : 3;
+    static constexpr int kOpStages = kWide ? 1 : 2;
+    static constexpr int kAccHH = kWide ? 1 : 3;
+    static constexpr uint32_t kXCol = kWide ? 256u : 384u;
+    static constexpr uint32_t kBoxBytes = kRows * 128;      // one 32-pixel box slot
+    static constexpr uint32_t kStageBytes = 2 * kBoxBytes;  // two boxes per chunk
+    static constexpr uint32_t kOpBytes = kRows * 128;       // one fp16 operand tile
+    static constexpr size_t kSmem =
+        1024 + (size_t)kStages * kStageBytes + (size_t)kOpStages * 2 * kOpBytes;
+    // chunks per segment: after each segment the accumulators are added into
+    // the CTA's partial Gram (FP32) and restart, so no TMEM accumulator takes
+    // more than 24 chunks (96 MMA steps) of additions
+    static constexpr int kSegChunks = 24 * kAccHH;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -145,21 +172,33 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+template <bool kWide>
 struct __align__(8) Bars {
-    uint64_t full[kStages], empty[kStages], op_full[2], op_empty[2], done;
+    uint64_t full[Cfg<kWide>::kStages], empty[Cfg<kWide>::kStages];
+    uint64_t op_full[Cfg<kWide>::kOpStages], op_empty[Cfg<kWide>::kOpStages];
+    uint64_t done;     // a segment's MMAs have completed (one commit per segment)
+    uint64_t drained;  // the epilogue has read a segment's accumulators (128 arrivals)
 };
 
+// Rows row_base..row_base+127 of this launch's block of G times columns
+// col_base..col_base+Nn-1 (Nn a multiple of 16); band sums when write_sums.
+template <bool kWide>
 __global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int Np /* N rounded to 16 cols */,
-               long N, long total_chunks, const float *__restrict__ shift,
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, int col_base, int Nn,
+               int write_sums, long N, long total_chunks, const float *__restrict__ shift,
                float *__restrict__ gram_part, float *__restrict__ sum_part, Control *ctl)
 {
+    using G = Cfg<kWide>;
+    constexpr int kRows = G::kRows, kStages = G::kStages, kOpStages = G::kOpStages;
+    constexpr int kAccHH = G::kAccHH;
+    constexpr uint32_t kBoxBytes = G::kBoxBytes, kStageBytes = G::kStageBytes;
+    constexpr uint32_t kOpBytes = G::kOpBytes;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    unsigned char *staging = base;                                 // kStages x 32 KB
-    unsigned char *ops = base + kStages * kStageBytes;             // 2 stages x (hi, lo)
-    __shared__ Bars bars;
+    unsigned char *staging = base;                                 // kStages x 2 boxes
+    unsigned char *ops = base + kStages * kStageBytes;             // kOpStages x (hi, lo)
+    __shared__ Bars<kWide> bars;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ float sh[kRows];
@@ -176,15 +215,16 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int Np /* N roun
             mbar_init(&bars.full[s], 1);
             mbar_init(&bars.empty[s], 128);
         }
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < kOpStages; ++t) {
             mbar_init(&bars.op_full[t], 128);
             mbar_init(&bars.op_empty[t], 1);
         }
         mbar_init(&bars.done, 1);
+        mbar_init(&bars.drained, 128);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (tid < kRows) sh[tid] = tid < B ? shift[tid] : 0.f;
+    for (int r = tid; r < kRows; r += kThreads) sh[r] = r < B ? shift[r] : 0.f;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
@@ -197,6 +237,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int Np /* N roun
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     volatile int *abort_p = &abort_flag;
+    int ncommit = 0;  // commits to bars.done by the MMA issuer
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -224,52 +265,129 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int Np /* N roun
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0 && nchunks > 0) {
-            // instruction descriptor: D f32, A/B f16, both K-major, N = Np, M = 128
-            const uint32_t idesc = (1u << 4) | ((uint32_t)(Np >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+            // instruction descriptor: D f32, A/B f16, both K-major, N = Nn, M = 128
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(Nn >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            int seg = 0, seg_start = 0;
             for (int i = 0; i < nchunks; ++i) {
-                const int t = i & 1;
-                if (!mbar_wait(&bars.op_full[t], (i >> 1) & 1, abort_p)) break;
+                if (i == seg_start + G::kSegChunks) {  // a new segment: accumulators drained?
+                    mma_commit(&bars.done);
+                    ++ncommit;
+                    if (!mbar_wait(&bars.drained, seg & 1, abort_p)) break;
+                    tc_fence_after();
+                    ++seg;
+                    seg_start = i;
+                }
+                const int j = i - seg_start;  // chunk within the segment
+                const int t = i % kOpStages;
+                if (!mbar_wait(&bars.op_full[t], (i / kOpStages) & 1, abort_p)) break;
                 tc_fence_after();
                 const uint32_t hi = smem_u32(ops + t * 2 * kOpBytes);
                 const uint32_t lo = hi + kOpBytes;
-                const uint64_t dh = smem_desc(hi), dl = smem_desc(lo);
-                const uint32_t d_hh = tmem + (uint32_t)(i % kAccHH) * 128u;
-                const uint32_t d_x = tmem + (uint32_t)kAccHH * 128u;
+                // A: this launch's 128 rows; B: its Nn columns (rows of the tile)
+                const uint64_t ah = smem_desc(hi + (uint32_t)row_base * 128u);
+                const uint64_t al = smem_desc(lo + (uint32_t)row_base * 128u);
+                const uint64_t bh = smem_desc(hi + (uint32_t)col_base * 128u);
+                const uint64_t bl = smem_desc(lo + (uint32_t)col_base * 128u);
+                const uint32_t d_hh = tmem + (uint32_t)(j % kAccHH) * 128u;
+                const uint32_t d_x = tmem + G::kXCol;
 #pragma unroll
                 for (int k = 0; k < kChunk / 16; ++k) {
                     const uint64_t off = (uint64_t)((k * 32) >> 4);  // 16 fp16 = 32 bytes along K
-                    mma_f16(d_hh, dh + off, dh + off, idesc, (i >= kAccHH || k > 0) ? 1u : 0u);
-                    mma_f16(d_x, dh + off, dl + off, idesc, (i > 0 || k > 0) ? 1u : 0u);
-                    mma_f16(d_x, dl + off, dh + off, idesc, 1u);
+                    mma_f16(d_hh, ah + off, bh + off, idesc, (j >= kAccHH || k > 0) ? 1u : 0u);
+                    mma_f16(d_x, ah + off, bl + off, idesc, (j > 0 || k > 0) ? 1u : 0u);
+                    mma_f16(d_x, al + off, bh + off, idesc, 1u);
                 }
                 mma_commit(&bars.op_empty[t]);
             }
             mma_commit(&bars.done);  // arrives when every MMA issued above has completed
+            ++ncommit;
         }
     } else {
-        // ---------------- converters (128 threads, one band row each)
-        const int b = tid - 64;
-        const int sw = b & 7;
-        float bsum = 0.f;
+        // ---------------- converters (128 threads, kRows / 128 band rows each)
+        constexpr int kRpt = kRows / 128;
+        const int b0 = tid - 64;
+        const int sw = b0 & 7;  // (b0 + 128) & 7 too
+        float bsum[kRpt];
         bool bad = false;
-        if (b >= B) {  // rows beyond B stay zero in both operand stages
-            for (int t = 0; t < 2; ++t)
-                for (int u = 0; u < 8; ++u) {
-                    uint4 z = make_uint4(0, 0, 0, 0);
-                    *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + b * 128 + u * 16) = z;
-                    *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + kOpBytes + b * 128 + u * 16) = z;
-                }
+#pragma unroll
+        for (int r = 0; r < kRpt; ++r) {
+            bsum[r] = 0.f;
+            const int b = b0 + 128 * r;
+            if (b >= B) {  // rows beyond B stay zero in every operand stage
+                for (int t = 0; t < kOpStages; ++t)
+                    for (int u = 0; u < 8; ++u) {
+                        uint4 z = make_uint4(0, 0, 0, 0);
+                        *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + b * 128 + u * 16) = z;
+                        *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + kOpBytes + b * 128 + u * 16) = z;
+                    }
+            }
         }
-        const float s_b = sh[b < kRows ? b : 0];
+        float *out = gram_part + (size_t)blockIdx.x * B * B;
+        const int q = warp & 3;  // TMEM lane quarter this warp may read
+        const int m = row_base + q * 32 + lane;  // the band of this accumulator row
+        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+        // accumulators of segment seg (chunks seg_start..i-1) -> out (= or +=)
+        auto drain = [&](int seg, int seg_start, int i) -> bool {
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars.done, seg & 1, abort_p));
+            tc_fence_after();
+            for (int c0 = 0; c0 < Nn; c0 += 16) {
+                float v[16];
+                if (ok) {
+                    tmem_ld16(lane_addr + G::kXCol + (uint32_t)c0, v);  // cross terms
+                    for (int a = 0; a < kAccHH && a < i - seg_start; ++a) {
+                        float w[16];
+                        tmem_ld16(lane_addr + (uint32_t)a * 128u + (uint32_t)c0, w);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] += w[e];
+                    }
+                }
+                if (m < B) {
+                    // transposed (G symmetric): lanes = consecutive rows m hit
+                    // consecutive words; the 16 earlier values are loaded
+                    // together, then added and stored
+                    float prev[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int col = col_base + c0 + e;
+                        prev[e] = (seg > 0 && col < B) ? out[(size_t)col * B + m] : 0.f;
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int col = col_base + c0 + e;
+                        if (col < B)
+                            out[(size_t)col * B + m] =
+                                prev[e] + (ok ? v[e] * (1.f / (kScale * kScale)) : 0.f);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bars.drained);
+            return ok;
+        };
+        int seg = 0, seg_start = 0, done_i = 0;
         for (int i = 0; i < nchunks; ++i) {
-            const int s = i % kStages, t = i & 1;
-            if (!mbar_wait(&bars.full[s], (i / kStages) & 1, abort_p)) break;
-            if (i >= 2 && !mbar_wait(&bars.op_empty[t], ((i >> 1) - 1) & 1, abort_p)) break;
-            if (b < B) {
+            if (i == seg_start + G::kSegChunks) {
+                if (!drain(seg, seg_start, i)) break;
+                ++seg;
+                seg_start = i;
+            }
+            const int s = i % kStages, t = i % kOpStages;
+            // warp-uniform exits: the drains below use warp-collective TMEM loads
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars.full[s], (i / kStages) & 1, abort_p)))
+                break;
+            if (i >= kOpStages &&
+                !__all_sync(0xffffffffu,
+                            mbar_wait(&bars.op_empty[t], ((i / kOpStages) - 1) & 1, abort_p)))
+                break;
+            const long px0 = (c_begin + i) * kChunk;
+#pragma unroll
+            for (int r = 0; r < kRpt; ++r) {
+                const int b = b0 + 128 * r;
+                if (b >= B) continue;
+                const float s_b = sh[b];
                 const unsigned char *st = staging + s * kStageBytes;
                 unsigned char *ohi = ops + t * 2 * kOpBytes + b * 128;
                 unsigned char *olo = ohi + kOpBytes;
-                const long px0 = (c_begin + i) * kChunk;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int box = u >> 2;
@@ -284,7 +402,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int Np /* N roun
                         const long p = px0 + u * 8 + e;
                         bad |= !isfinite(x[e]);
                         float y = (p < N) ? (x[e] - s_b) * kScale : 0.f;
-                        bsum += y;
+                        bsum[r] += y;
                         h[e] = __float2half_rn(y);
                         l[e] = __float2half_rn(y - __half2float(h[e]));
                     }
@@ -295,40 +413,29 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int Np /* N roun
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&bars.op_full[t]);
             mbar_arrive(&bars.empty[s]);
+            done_i = i + 1;
         }
         if (bad) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
-        // ---------------- epilogue: accumulator rows -> partial Gram
-        const bool ok = __all_sync(0xffffffffu, nchunks > 0 && mbar_wait(&bars.done, 0, abort_p));
-        tc_fence_after();
-        const int q = warp & 3;  // TMEM lane quarter this warp may read
-        const int m = q * 32 + lane;
-        float *out = gram_part + (size_t)blockIdx.x * B * B;
-        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-        for (int c0 = 0; c0 < Np; c0 += 16) {
-            float v[16];
-            if (ok) {
-                tmem_ld16(lane_addr + (uint32_t)kAccHH * 128u + (uint32_t)c0, v);  // cross terms
-                for (int a = 0; a < kAccHH && a < nchunks; ++a) {
-                    float w[16];
-                    tmem_ld16(lane_addr + (uint32_t)a * 128u + (uint32_t)c0, w);
+        // ---------------- the last segment (or zeros when there are no chunks)
+        if (nchunks > 0 && done_i == nchunks) {
+            drain(seg, seg_start, nchunks);
+        } else if (nchunks == 0 && m < B) {
+            for (int col = col_base; col < col_base + Nn && col < B; ++col) out[(size_t)col * B + m] = 0.f;
+        }
+        if (write_sums) {
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) v[e] += w[e];
-                }
-            }
-            if (m < B) {
-#pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    if (c0 + e < B) out[(size_t)m * B + c0 + e] = ok ? v[e] * (1.f / (kScale * kScale)) : 0.f;
+            for (int r = 0; r < kRpt; ++r) {
+                const int b = b0 + 128 * r;
+                if (b < B) sum_part[(size_t)blockIdx.x * B + b] = bsum[r] * (1.f / kScale);
             }
         }
-        if (b < B) sum_part[(size_t)blockIdx.x * B + b] = bsum * (1.f / kScale);
     }
     if (*abort_p && tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
-    if (tid == 32 && nchunks > 0) {
+    if (tid == 32 && ncommit > 0) {
         // every MMA must have completed before the accumulator is freed, also
         // after an abort: wait (bounded) for the final commit
         for (uint32_t k = 0; k < kWaitLimit; ++k)
-            if (mbar_try(&bars.done, 0)) break;
+            if (mbar_try(&bars.done, (ncommit - 1) & 1)) break;
     }
     tc_fence_before();
     __syncthreads();
@@ -367,11 +474,11 @@ EncodeTiledFn encode_fn()
 
 bool gram_tc_supported(const float *cube, int B, long N)
 {
-    return B >= 1 && B <= kRows && N % 4 == 0 && N < (1L << 31) &&
+    return B >= 1 && B <= 256 && N % 4 == 0 && N < (1L << 31) &&
            (reinterpret_cast<uintptr_t>(cube) & 15u) == 0 && encode_fn() != nullptr;
 }
 
-size_t gram_tc_smem_bytes() { return 1024 + kStages * kStageBytes + 2 * 2 * kOpBytes; }
+size_t gram_tc_smem_bytes() { return Cfg<false>::kSmem; }
 
 cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s, cudaStream_t st)
 {
@@ -387,10 +494,22 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     const int Np = (B + 15) / 16 * 16;
     const long total = (N + kChunk - 1) / kChunk;
-    const size_t smem = gram_tc_smem_bytes();
-    cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    gram_tc_kernel<<<s.n_part, kThreads, smem, st>>>(map, B, Np, N, total, s.shift, s.gram_part,
-                                                     s.sum_part, s.ctl);
+    if (B <= 128) {
+        const size_t smem = Cfg<false>::kSmem;
+        cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        gram_tc_kernel<false><<<s.n_part, kThreads, smem, st>>>(
+            map, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+        return cudaGetLastError();
+    }
+    const size_t smem = Cfg<true>::kSmem;
+    cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    // rows 0-127 x every column, then rows 128-255 x columns 128-255
+    gram_tc_kernel<true><<<s.n_part, kThreads, smem, st>>>(map, B, 0, 0, Np, 1, N, total, s.shift,
+                                                           s.gram_part, s.sum_part, s.ctl);
+    gram_tc_kernel<true><<<s.n_part, kThreads, smem, st>>>(
+        map, B, 128, 128, Np - 128, 0, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
     return cudaGetLastError();
 }
 

@@ -47,7 +47,7 @@ struct JacParams {
     int max_sweeps;      // fallback sweeps at most
     float rot_tol;       // rotate (p,q) when |a_pq| > rot_tol (A scaled to max diag 1)
     float stop_tol_final;  // fallback sweeps end once every |a_pq| seen in one is below
-    int use_smem;
+    int use_smem;          // 1: the whole work area in shared memory (n <= 140)
 };
 
 // j-slices of the double-float C v: each thread sums at most 16 products
@@ -62,6 +62,19 @@ __host__ __device__ inline size_t jac_work_floats(int n)
 {
     const size_t ld = (size_t)n + 1;
     return 2 * (size_t)n * ld + (size_t)kBasis * ld + 2 * (size_t)jac_slices(n) * n;
+}
+
+// Packed form for larger n: A as its packed upper triangle (rounded up to a
+// multiple of 4 floats) and the basis columns in shared memory; the slice
+// partials reuse A's space once A is dead; the log and the fallback's V^T in
+// global memory (n x ld floats).
+__host__ __device__ inline size_t jac_packed_a_floats(int n)
+{
+    return (((size_t)n * (n + 1) / 2) + 3) & ~(size_t)3;
+}
+__host__ __device__ inline size_t jac_packed_smem_floats(int n)
+{
+    return jac_packed_a_floats(n) + (size_t)kBasis * ((size_t)n + 1);
 }
 
 // ---- double-float arithmetic: a value is an unevaluated sum h + l of two
@@ -145,8 +158,6 @@ __device__ __forceinline__ void pair_ab(int t, int k, int n, int &a, int &b)
     if (b >= n - 1) b -= n - 1;
 }
 
-// A is kept as its upper triangle (i <= j) in a row-major n x ld array.
-__device__ __forceinline__ int up(int i, int j, int ld) { return i < j ? i * ld + j : j * ld + i; }
 
 // block index idx in [0, P(P+1)/2) -> (k, l), k <= l < P, row-major upper
 // triangle (with P - 1 and l + 1: the strict upper triangle of P)
@@ -184,6 +195,7 @@ __device__ float block_sumf(float v, float *red)
     return t;
 }
 
+template <bool kPacked>
 __global__ void __launch_bounds__(kJacThreads, 1)
 jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restrict__ C2,
               const double *__restrict__ mu,
@@ -196,12 +208,27 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nwarps = nthr >> 5;
     float *work = prm.use_smem ? smem : gwork;
-    float *A = work;                                   // n x ld, upper triangle
-    float2 *rlog = reinterpret_cast<float2 *>(work + (size_t)n * ld);  // (n-1) x P
-    float *Vt = work + (size_t)n * ld;                 // fallback: V^T, n x ld
-    float *X = work + 2 * (size_t)n * ld;              // kBasis x ld, rebuilt columns
-    float2 *part = reinterpret_cast<float2 *>(X + (size_t)kBasis * ld);  // slices x n
+    float *A, *Vt, *X;
+    float2 *rlog, *part;
+    if (kPacked) {
+        A = smem;                                      // packed upper triangle
+        X = smem + jac_packed_a_floats(n);             // kBasis x ld
+        part = reinterpret_cast<float2 *>(smem);       // slices x n, once A is dead
+        rlog = reinterpret_cast<float2 *>(gwork);      // (n-1) x P
+        Vt = gwork;                                    // fallback: V^T, n x ld
+    } else {
+        A = work;                                      // n x ld, upper triangle
+        rlog = reinterpret_cast<float2 *>(work + (size_t)n * ld);  // (n-1) x P
+        Vt = work + (size_t)n * ld;                    // fallback: V^T, n x ld
+        X = work + 2 * (size_t)n * ld;                 // kBasis x ld, rebuilt columns
+        part = reinterpret_cast<float2 *>(X + (size_t)kBasis * ld);  // slices x n
+    }
     float2 *Cs2 = reinterpret_cast<float2 *>(work);    // refinement: C as (hi, lo), B x B
+    // storage index of A's entry (i, j), either order (upper triangle)
+    auto aix = [n, ld](int i, int j) -> int {
+        const int lo = i < j ? i : j, hi = i < j ? j : i;
+        return kPacked ? lo * n - ((lo * (lo - 1)) >> 1) + (hi - lo) : lo * ld + hi;
+    };
     const int nsl = jac_slices(n);
 
     __shared__ float2 cs2[2][kMaxPairs];   // (c, s) of the round's pairs, double-buffered
@@ -231,7 +258,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     auto load_A = [&]() {  // FP32 is all the sweeps use: the hi parts suffice
         for (int idx = tid; idx < n * n; idx += nthr) {
             int i = idx / n, j = idx % n;
-            A[i * ld + j] = (i < B && j < B) ? C2[(size_t)i * B + j].x * inv_p2 : 0.f;
+            if (j < i) continue;
+            A[aix(i, j)] = (i < B && j < B) ? C2[(size_t)i * B + j].x * inv_p2 : 0.f;
         }
     };
     load_A();
@@ -242,7 +270,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // triangle of pair blocks; the diagonal blocks go with the angles), each
     // packed with the pair of the next round whose angle it owns:
     // k | l << 10 | (owner + 1) << 20, or -1.
-    constexpr int kBlk = 3;  // 2 for n <= 128, 3 up to n = 156; larger n loops
+    constexpr int kBlk = kPacked ? 8 : 3;  // blocks held per thread: n <= 156 / n <= 256
     const int nblk = P * (P - 1) / 2;
     const bool blocks_in_regs = nblk <= kBlk * nthr;
     // One barrier per round: the a_pq of round t+1's pair k' sits in exactly
@@ -306,8 +334,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     auto angle_pair = [&](int t, int k, int buf, bool log_rot) -> float {
         int a, b;
         pair_ab(t, k, n, a, b);
-        const int iab = up(a, b, ld);
-        const float app = A[a * ld + a], aqq = A[b * ld + b], apq = A[iab];
+        const int iab = aix(a, b), iaa = aix(a, a), ibb = aix(b, b);
+        const float app = A[iaa], aqq = A[ibb], apq = A[iab];
         float c = 1.f, s = 0.f;
         if (fabsf(apq) > prm.rot_tol) {
             // FP32 intrinsics are enough here: the leading vector is refined
@@ -318,8 +346,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
             else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
             c = rsqrtf(fmaf(tt, tt, 1.f));
             s = tt * c;
-            A[a * ld + a] = fmaf(-tt, apq, app);
-            A[b * ld + b] = fmaf(tt, apq, aqq);
+            A[iaa] = fmaf(-tt, apq, app);
+            A[ibb] = fmaf(tt, apq, aqq);
             A[iab] = 0.f;
         }
         cs2[buf][k] = make_float2(c, s);
@@ -342,8 +370,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
                 const float ck = rk.x, sk = rk.y, cl = rl.x, sl = rl.y;
                 if (sk != 0.f || sl != 0.f) {
                     const int2 pk = ab2[cur][k], pl = ab2[cur][l];
-                    const int i00 = up(pk.x, pl.x, ld), i01 = up(pk.x, pl.y, ld);
-                    const int i10 = up(pk.y, pl.x, ld), i11 = up(pk.y, pl.y, ld);
+                    const int i00 = aix(pk.x, pl.x), i01 = aix(pk.x, pl.y);
+                    const int i10 = aix(pk.y, pl.x), i11 = aix(pk.y, pl.y);
                     const float x00 = A[i00], x01 = A[i01];
                     const float x10 = A[i10], x11 = A[i11];
                     const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
@@ -537,10 +565,10 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // basis, the mean of the rest is theta_c
     float rest = 0.f;
     for (int j = tid; j < B; j += nthr) {
-        const float dj = A[j * ld + j];
+        const float dj = A[aix(j, j)];
         int rank = 0;
         for (int i = 0; i < B; ++i) {
-            const float di = A[i * ld + i];
+            const float di = A[aix(i, i)];
             rank += (di > dj || (di == dj && i < j)) ? 1 : 0;
         }
         if (rank < m) {
@@ -632,10 +660,10 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         if (tid == 0) {
             int lead = 0;
             for (int j = 1; j < B; ++j)
-                if (A[j * ld + j] > A[lead * ld + lead]) lead = j;
+                if (A[aix(j, j)] > A[aix(lead, lead)]) lead = j;
             s_lead = lead;
         }
-        for (int j = tid; j < B; j += nthr) th[j] = A[j * ld + j];
+        for (int j = tid; j < B; j += nthr) th[j] = A[aix(j, j)];
         __syncthreads();
         const int lead = s_lead;
         for (int ii = tid; ii < B; ii += nthr) {
@@ -682,13 +710,16 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
 }  // namespace
 
-// Global work area of the Jacobi kernel (floats); 0 when it fits in shared memory.
+// Global work area of the Jacobi kernel (floats): none when all of it fits in
+// shared memory, the log / V^T in the packed form, everything otherwise.
 size_t jacobi_global_floats(int B)
 {
     int n = B + (B & 1);
     if (n < 2) n = 2;
     const size_t f = jac_work_floats(n);
-    return f * sizeof(float) <= kJacSmemLimit ? 0 : f;
+    if (f * sizeof(float) <= kJacSmemLimit) return 0;
+    if (jac_packed_smem_floats(n) * sizeof(float) <= kJacSmemLimit) return (size_t)n * (n + 1);
+    return f;
 }
 
 cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
@@ -701,13 +732,23 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
     prm.rot_tol = 1e-7f;
     prm.stop_tol_final = 1e-2f;
     const size_t need = jac_work_floats(prm.n) * sizeof(float);
+    const size_t need_packed = jac_packed_smem_floats(prm.n) * sizeof(float);
     prm.use_smem = need <= kJacSmemLimit;
-    const size_t smem = prm.use_smem ? need : 0;
+    const bool packed = !prm.use_smem && need_packed <= kJacSmemLimit;
     if (!prm.use_smem && !s.jac_A) return cudaErrorInvalidValue;
+    if (packed) {
+        cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)need_packed);
+        jacobi_kernel<true><<<1, kJacThreads, need_packed, st>>>(
+            prm, s.C, s.C2, s.mu, s.v1, s.lambda1, s.v1f, s.muf, s.jac_A, s.ctl);
+        return cudaGetLastError();
+    }
+    const size_t smem = prm.use_smem ? need : 0;
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    jacobi_kernel<<<1, kJacThreads, smem, st>>>(prm, s.C, s.C2, s.mu, s.v1, s.lambda1, s.v1f,
-                                                s.muf, s.jac_A, s.ctl);
+        cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    jacobi_kernel<false><<<1, kJacThreads, smem, st>>>(prm, s.C, s.C2, s.mu, s.v1, s.lambda1,
+                                                       s.v1f, s.muf, s.jac_A, s.ctl);
     return cudaGetLastError();
 }
 

@@ -185,9 +185,11 @@ band_mean_kernel(int B, double inv_N, int n_part, const float *__restrict__ shif
 }
 
 // C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored, in
-// FP64 and as FP32 (hi, lo) pairs. A CTA takes 32 consecutive entries
-// e = b*B + c; its 8 warps each sum every 8th partial (coalesced across the
-// 32 entries) in double-float, then the 8 slices are added.
+// FP64 and as FP32 (hi, lo) pairs. Each partial holds entry (b, c) at
+// c * B + b (the tensor-core Gram writes that half of its block; the FP32
+// version writes the whole symmetric matrix). A CTA takes 32 consecutive
+// positions e = c*B + b; its 8 warps each sum every 8th partial (coalesced
+// across the 32 positions) in double-float, then the 8 slices are added.
 constexpr int kRedEntries = 32, kRedSlices = 8;
 __global__ void __launch_bounds__(kRedEntries * kRedSlices)
 gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gram_part,
@@ -197,7 +199,7 @@ gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gr
     const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const long e = (long)blockIdx.x * kRedEntries + lane;
     const long BB = (long)B * B;
-    const int b = e < BB ? (int)(e / B) : 0, c = e < BB ? (int)(e % B) : 0;
+    const int c = e < BB ? (int)(e / B) : 0, b = e < BB ? (int)(e % B) : 0;
     const bool active = e < BB && c >= b;
     float s = 0.f, lo = 0.f;
     if (active)

@@ -33,7 +33,8 @@ def check(hsc, ctx, cube, flags):
 
 @pytest.mark.parametrize("flags", [0, 4])
 @pytest.mark.parametrize("shape", [(16, 32, 32), (128, 416, 512), (125, 50, 52), (100, 33, 36),
-                                   (37, 9, 13), (128, 7, 9), (1, 12, 12), (200, 20, 20)])
+                                   (37, 9, 13), (128, 7, 9), (1, 12, 12), (200, 20, 20),
+                                   (256, 48, 64), (129, 40, 40), (250, 64, 100)])
 def test_covariance_against_oracle(hsc, ctx, flags, shape):
     B, H, W = shape
     if shape == (128, 416, 512):
