@@ -150,3 +150,22 @@ def test_projection_matches_dot_and_sign_rule():
     # the normalised image does not depend on the eigenvector's sign
     In = (-I - (-I).min()) / ((-I).max() - (-I).min())
     np.testing.assert_allclose(1.0 - out["I_norm"].ravel(), In, atol=1e-13)
+
+
+def test_covariance_matmul_equals_two_pass_and_closed_form():
+    """The chunked-matmul covariance is the same definition as the C two-pass
+    one: equal on random cubes (uneven chunks), and exact on a dyadic rank-one
+    cube (C = var(a) u u^T)."""
+    rng = np.random.default_rng(11)
+    cube = rng.random((23, 17, 19)).astype(np.float32)
+    mu = oracle.band_means(cube)
+    C2 = oracle.covariance(cube, mu)
+    Cm = oracle.covariance_matmul(cube, mu, chunk=37)
+    assert np.abs(Cm - C2).max() <= 1e-13 * np.abs(C2).max()
+    B, H, W = 12, 16, 16
+    u = rng.integers(-4, 5, size=B).astype(np.float64)
+    m = rng.integers(8, 24, size=B) / 32.0
+    a = rng.integers(-8, 9, size=H * W) / 64.0
+    cube = (m[:, None] + u[:, None] * a[None, :]).reshape(B, H, W).astype(np.float32)
+    Cm = oracle.covariance_matmul(cube, oracle.band_means(cube), chunk=100)
+    np.testing.assert_allclose(Cm, np.var(a) * np.outer(u, u), rtol=0, atol=1e-15)
