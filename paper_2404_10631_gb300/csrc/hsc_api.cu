@@ -138,7 +138,7 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
         size_t budget = (size_t)64 << 20;
         if ((size_t)np * per > budget) np = (int)std::max<size_t>(1, budget / per);
         L.n_part = np;
-        L.shift = take(sizeof(float) * B);
+        L.shift = take(sizeof(float) * 2 * B);
         L.gram = take((size_t)np * per);
         L.sums = take(sizeof(float) * (size_t)np * B);
         L.C = take(sizeof(double) * (size_t)B * B);

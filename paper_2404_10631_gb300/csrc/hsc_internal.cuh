@@ -56,7 +56,7 @@ __host__ __device__ inline float key_to_float(unsigned k) {
 // Scratch carve-up for one frame (offsets in bytes, 256-aligned).
 struct PcaScratch {
     Control *ctl;
-    float *shift;        // B: pilot shift per band
+    float *shift;        // 2B: pilot shift per band, then the tensor-core scale per band
     float *gram_part;    // n_part x B x B partial Gram of shifted pixels
     float *sum_part;     // n_part x B partial sums of shifted pixels
     double *C;           // B x B covariance

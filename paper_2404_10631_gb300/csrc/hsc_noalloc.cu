@@ -28,7 +28,7 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the carved regions for the largest supported B.
 constexpr size_t kCtl = 0;
 constexpr size_t kShift = 256;
-constexpr size_t kGram = kShift + 256 * ((kMaxBands * 4 + 255) / 256);
+constexpr size_t kGram = kShift + 256 * ((kMaxBands * 8 + 255) / 256);  // shift, scale
 constexpr size_t kSums = kGram + (size_t)kParts * kMaxBands * kMaxBands * 4;
 constexpr size_t kC = kSums + 256 * (((size_t)kParts * kMaxBands * 4 + 255) / 256);
 constexpr size_t kC2 = kC + (size_t)kMaxBands * kMaxBands * 8;

@@ -12,7 +12,7 @@
 //
 // Per CTA (one per SM, a contiguous range of 64-pixel chunks):
 //   warp 0   TMA producer: each chunk is two 32-pixel x B-band FP32 boxes
-//            (128-byte swizzled) into a 3-stage shared ring;
+//            (128-byte swizzled) into a 4-stage shared ring;
 //   warp 1   TMEM owner and MMA issuer: for every chunk, 4 K-steps of
 //            tcgen05.mma kind::f16 (M = 128 bands, N = B bands, K = 16 pixels)
 //            for each of hi.hi^T, hi.lo^T, lo.hi^T into FP32 TMEM accumulators:
@@ -20,16 +20,24 @@
 //            cross terms share a fourth, so no accumulator takes more than a
 //            third of the additions (the tensor cores' FP32 accumulation error
 //            grows with the number of additions into one accumulator);
-//   warps 2-5 converters: y = 16 (x - s) split into FP16 hi + lo (hi + lo
-//            carries y to ~2^-22), written in the 128-byte-swizzled K-major
-//            operand layout; band sums of y; then the epilogue reads the
-//            accumulator (tcgen05.ld) and adds it into this CTA's partial
-//            Gram, stored transposed (entry (b, c) at c * B + b), every 24
-//            chunks per accumulator.
+//   warps 2-9 converters, two per band row (one 32-pixel box each):
+//            y = c_b (x - s_b), c_b a power of two per band (from the pilot
+//            sample), split into FP16 hi + lo by Veltkamp's splitting (hi = y
+//            rounded to 11 significant bits, exact in FP16; lo = y - hi exactly,
+//            rounded to FP16: hi + lo carries y to ~2^-23), written in the
+//            128-byte-swizzled K-major operand layout; band sums of y; then the
+//            epilogue reads the accumulators (tcgen05.ld, the two warps of a
+//            TMEM lane quarter taking alternate 16-column blocks), removes the
+//            scales and adds them into this CTA's partial Gram, stored
+//            transposed (entry (b, c) at c * B + b), every 24 chunks per
+//            accumulator.
 // The dropped lo.lo^T term is below 2^-22 of each product. Accumulation is
-// FP32 in TMEM; the partials are summed in FP64 by gram_reduce_kernel. Every
-// mbarrier wait is bounded: on expiry the kernel flags ST_TIMEOUT, stops
-// issuing work, waits (bounded) for its own copies and MMAs, frees TMEM.
+// FP32 in TMEM; the partials are summed in FP64 by gram_reduce_kernel. A CTA
+// that meets a scaled value outside FP16's range (a pixel 256 times further
+// from the band's mean than any pixel of the pilot sample) recomputes its
+// partial Gram and sums on the FP32 pipe from the cube. Every mbarrier wait is
+// bounded: on expiry the kernel flags ST_TIMEOUT, stops issuing work, waits
+// (bounded) for its own copies and MMAs, frees TMEM.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -39,23 +47,28 @@
 namespace hsc {
 namespace {
 
-constexpr int kThreads = 192;
 constexpr int kChunk = 64;               // pixels per chunk (one 128-byte fp16 row)
 constexpr int kBoxPx = 32;               // pixels per TMA box (128 bytes of fp32)
 constexpr int kM = 128;                  // MMA M (bands of one half, zero padded)
 constexpr uint32_t kWaitLimit = 1u << 22;
-constexpr float kScale = 16.f;                        // y scaled into fp16's sweet spot
 constexpr uint32_t kTmemCols = 512;
+constexpr float kFp16Max = 65504.f;
+constexpr int kFbAcc = 8;                // FP32 recompute: entries per thread per pass
+constexpr int kFbLd = kChunk + 1;        // FP32 recompute: padded staging row
 
-// B <= 128: 128 converted rows, 3 staging stages, 2 operand stages, three
-// hi.hi^T accumulators (columns 0, 128, 256) and the cross terms at 384.
-// 128 < B <= 256: 256 rows, 2 + 1 stages, hi.hi^T at 0 and cross at 256.
+// B <= 128: 128 converted rows, 4 staging stages, 2 operand stages, three
+// hi.hi^T accumulators (columns 0, 128, 256) and the cross terms at 384, 8
+// converter warps. 128 < B <= 256: 256 rows, 2 + 1 stages, hi.hi^T at 0 and
+// cross at 256, 4 converter warps (one thread per band row and half).
 template <bool kWide>
 struct Cfg {
     static constexpr int kRows = kWide ? 256 : 128;
-    static constexpr int kStages = kWide ? 2 : 3;
+    static constexpr int kStages = kWide ? 2 : 4;
     static constexpr int kOpStages = kWide ? 1 : 2;
     static constexpr int kAccHH = kWide ? 1 : 3;
+    static constexpr int kConvWarps = kWide ? 4 : 8;
+    static constexpr int kThreads = 64 + 32 * kConvWarps;
+    static constexpr int kParts = kConvWarps / 4;           // threads per band row
     static constexpr uint32_t kXCol = kWide ? 256u : 384u;
     static constexpr uint32_t kBoxBytes = kRows * 128;      // one 32-pixel box slot
     static constexpr uint32_t kStageBytes = 2 * kBoxBytes;  // two boxes per chunk
@@ -66,6 +79,8 @@ struct Cfg {
     // the CTA's partial Gram (FP32) and restart, so no TMEM accumulator takes
     // more than 24 chunks (96 MMA steps) of additions
     static constexpr int kSegChunks = 24 * kAccHH;
+    static_assert((size_t)kRows * kFbLd * 4 <= (size_t)kStages * kStageBytes,
+                  "the FP32 recompute stages into the TMA ring");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -180,17 +195,55 @@ struct __align__(8) Bars {
     uint64_t drained;  // the epilogue has read a segment's accumulators (128 arrivals)
 };
 
+// Two floats to packed FP16 (first in the low half, at the lower address).
+__device__ __forceinline__ uint32_t pack_half2(float first, float second)
+{
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
+    return r;
+}
+
+// One 8-pixel unit of a band row: scaled shifted values y = fma(x, c, -s c)
+// (one rounding: c is a power of two), Veltkamp's split y = hi + lo with hi on
+// 11 significant bits (c = 2^13 + 1), both packed to FP16; band sum and
+// largest |y|. kTail: the chunk runs past the last pixel (lim pixels left).
+template <bool kTail>
+__device__ __forceinline__ void convert_unit(const float4 xa, const float4 xb, float c, float nsc,
+                                             int u, int lim, float &bsum, float &ymax,
+                                             uint4 &hi, uint4 &lo)
+{
+    const float x[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+    float h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        float y = fmaf(x[e], c, nsc);
+        if (kTail && u * 8 + e >= lim) y = 0.f;
+        ymax = fmaxf(ymax, fabsf(y));
+        bsum += y;
+        const float t = __fmul_rn(y, 8193.f);
+        h[e] = __fsub_rn(t, __fsub_rn(t, y));
+        l[e] = __fsub_rn(y, h[e]);
+    }
+    hi = make_uint4(pack_half2(h[0], h[1]), pack_half2(h[2], h[3]), pack_half2(h[4], h[5]),
+                    pack_half2(h[6], h[7]));
+    lo = make_uint4(pack_half2(l[0], l[1]), pack_half2(l[2], l[3]), pack_half2(l[4], l[5]),
+                    pack_half2(l[6], l[7]));
+}
+
 // Rows row_base..row_base+127 of this launch's block of G times columns
 // col_base..col_base+Nn-1 (Nn a multiple of 16); band sums when write_sums.
+// shift: 2B floats, the pilot shift s_b then the scale c_b of each band.
 template <bool kWide>
-__global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, int col_base, int Nn,
-               int write_sums, long N, long total_chunks, const float *__restrict__ shift,
-               float *__restrict__ gram_part, float *__restrict__ sum_part, Control *ctl)
+__global__ void __launch_bounds__(Cfg<kWide>::kThreads, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ cube, int B,
+               int row_base, int col_base, int Nn, int write_sums, long N, long total_chunks,
+               const float *__restrict__ shift, float *__restrict__ gram_part,
+               float *__restrict__ sum_part, Control *ctl)
 {
     using G = Cfg<kWide>;
     constexpr int kRows = G::kRows, kStages = G::kStages, kOpStages = G::kOpStages;
-    constexpr int kAccHH = G::kAccHH;
+    constexpr int kAccHH = G::kAccHH, kThreads = G::kThreads, kParts = G::kParts;
+    constexpr int kConv = 32 * G::kConvWarps;
     constexpr uint32_t kBoxBytes = G::kBoxBytes, kStageBytes = G::kStageBytes;
     constexpr uint32_t kOpBytes = G::kOpBytes;
     extern __shared__ unsigned char smem_raw[];
@@ -200,8 +253,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, in
     unsigned char *ops = base + kStages * kStageBytes;             // kOpStages x (hi, lo)
     __shared__ Bars<kWide> bars;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag;
-    __shared__ float sh[kRows];
+    __shared__ int abort_flag, range_flag;
+    __shared__ float sh[kRows], sc[kRows], isc[kRows];
+    __shared__ float bsum_sh[kParts > 1 ? kRows : 1];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long per = (total_chunks + gridDim.x - 1) / gridDim.x;
@@ -213,18 +267,23 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, in
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&bars.full[s], 1);
-            mbar_init(&bars.empty[s], 128);
+            mbar_init(&bars.empty[s], G::kConvWarps);
         }
         for (int t = 0; t < kOpStages; ++t) {
-            mbar_init(&bars.op_full[t], 128);
+            mbar_init(&bars.op_full[t], G::kConvWarps);
             mbar_init(&bars.op_empty[t], 1);
         }
         mbar_init(&bars.done, 1);
-        mbar_init(&bars.drained, 128);
+        mbar_init(&bars.drained, G::kConvWarps);
         abort_flag = 0;
+        range_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int r = tid; r < kRows; r += kThreads) sh[r] = r < B ? shift[r] : 0.f;
+    for (int r = tid; r < kRows; r += kThreads) {
+        sh[r] = r < B ? shift[r] : 0.f;
+        sc[r] = r < B ? shift[B + r] : 1.f;
+        isc[r] = __frcp_rn(sc[r]);  // exact: a power of two
+    }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base)),
@@ -238,6 +297,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, in
     const uint32_t tmem = tmem_base;
     volatile int *abort_p = &abort_flag;
     int ncommit = 0;  // commits to bars.done by the MMA issuer
+    // converter state, kept past the final barrier for the band sums
+    constexpr int kRpt = kRows / 128;      // band rows per converter thread
+    const int cv = tid - 64;               // converter index
+    const int b0 = cv & 127;               // its first band row
+    const int part = cv >> 7;              // which 32-pixel box of a chunk it converts
+    float bsum[kRpt];
+#pragma unroll
+    for (int r = 0; r < kRpt; ++r) bsum[r] = 0.f;
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -303,34 +370,36 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, in
             ++ncommit;
         }
     } else {
-        // ---------------- converters (128 threads, kRows / 128 band rows each)
-        constexpr int kRpt = kRows / 128;
-        const int b0 = tid - 64;
+        // ---------------- converters: kRpt band rows x one box (kParts = 2)
+        // or both boxes (kParts = 1) of every chunk
+        constexpr int kUnits = 8 / kParts;  // 8-pixel fp16 units per thread per chunk
+        const int u0 = part * kUnits;
         const int sw = b0 & 7;  // (b0 + 128) & 7 too
-        float bsum[kRpt];
-        bool bad = false;
+        float ymax = 0.f;
 #pragma unroll
         for (int r = 0; r < kRpt; ++r) {
-            bsum[r] = 0.f;
             const int b = b0 + 128 * r;
             if (b >= B) {  // rows beyond B stay zero in every operand stage
                 for (int t = 0; t < kOpStages; ++t)
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = u0; u < u0 + kUnits; ++u) {
                         uint4 z = make_uint4(0, 0, 0, 0);
-                        *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + b * 128 + u * 16) = z;
-                        *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + kOpBytes + b * 128 + u * 16) = z;
+                        *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + b * 128 + ((u ^ sw) << 4)) = z;
+                        *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + kOpBytes + b * 128 +
+                                                   ((u ^ sw) << 4)) = z;
                     }
             }
         }
         float *out = gram_part + (size_t)blockIdx.x * B * B;
-        const int q = warp & 3;  // TMEM lane quarter this warp may read
+        const int q = warp & 3;           // TMEM lane quarter this warp may read
+        const int cpart = (warp - 2) >> 2;  // which alternate 16-column blocks it drains
         const int m = row_base + q * 32 + lane;  // the band of this accumulator row
+        const float isc_m = m < B ? isc[m] : 0.f;
         const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
         // accumulators of segment seg (chunks seg_start..i-1) -> out (= or +=)
         auto drain = [&](int seg, int seg_start, int i) -> bool {
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars.done, seg & 1, abort_p));
             tc_fence_after();
-            for (int c0 = 0; c0 < Nn; c0 += 16) {
+            for (int c0 = 16 * cpart; c0 < Nn; c0 += 16 * kParts) {
                 float v[16];
                 if (ok) {
                     tmem_ld16(lane_addr + G::kXCol + (uint32_t)c0, v);  // cross terms
@@ -356,12 +425,13 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, in
                         const int col = col_base + c0 + e;
                         if (col < B)
                             out[(size_t)col * B + m] =
-                                prev[e] + (ok ? v[e] * (1.f / (kScale * kScale)) : 0.f);
+                                prev[e] + (ok ? v[e] * (isc_m * isc[col]) : 0.f);
                     }
                 }
             }
             tc_fence_before();
-            mbar_arrive(&bars.drained);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.drained);
             return ok;
         };
         int seg = 0, seg_start = 0, done_i = 0;
@@ -380,55 +450,55 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, in
                             mbar_wait(&bars.op_empty[t], ((i / kOpStages) - 1) & 1, abort_p)))
                 break;
             const long px0 = (c_begin + i) * kChunk;
+            const bool tail = px0 + kChunk > N;
+            const int lim = tail ? (int)(N - px0) : kChunk;
 #pragma unroll
             for (int r = 0; r < kRpt; ++r) {
                 const int b = b0 + 128 * r;
                 if (b >= B) continue;
-                const float s_b = sh[b];
+                const float c = sc[b], nsc = -sh[b] * c;  // exact: c is a power of two
                 const unsigned char *st = staging + s * kStageBytes;
                 unsigned char *ohi = ops + t * 2 * kOpBytes + b * 128;
                 unsigned char *olo = ohi + kOpBytes;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int uu = 0; uu < kUnits; ++uu) {
+                    const int u = u0 + uu;
                     const int box = u >> 2;
                     const int j0 = (u & 3) * 2;  // 16-byte units (4 px) within the box row
                     const unsigned char *row = st + box * kBoxBytes + b * 128;
                     const float4 xa = *reinterpret_cast<const float4 *>(row + ((j0 ^ sw) << 4));
                     const float4 xb = *reinterpret_cast<const float4 *>(row + (((j0 + 1) ^ sw) << 4));
-                    float x[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
-                    __align__(16) __half h[8], l[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const long p = px0 + u * 8 + e;
-                        bad |= !isfinite(x[e]);
-                        float y = (p < N) ? (x[e] - s_b) * kScale : 0.f;
-                        bsum[r] += y;
-                        h[e] = __float2half_rn(y);
-                        l[e] = __float2half_rn(y - __half2float(h[e]));
-                    }
-                    *reinterpret_cast<uint4 *>(ohi + ((u ^ sw) << 4)) = *reinterpret_cast<uint4 *>(h);
-                    *reinterpret_cast<uint4 *>(olo + ((u ^ sw) << 4)) = *reinterpret_cast<uint4 *>(l);
+                    uint4 hv, lv;
+                    if (tail)
+                        convert_unit<true>(xa, xb, c, nsc, u, lim, bsum[r], ymax, hv, lv);
+                    else
+                        convert_unit<false>(xa, xb, c, nsc, u, lim, bsum[r], ymax, hv, lv);
+                    *reinterpret_cast<uint4 *>(ohi + ((u ^ sw) << 4)) = hv;
+                    *reinterpret_cast<uint4 *>(olo + ((u ^ sw) << 4)) = lv;
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&bars.op_full[t]);
-            mbar_arrive(&bars.empty[s]);
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&bars.op_full[t]);
+                mbar_arrive(&bars.empty[s]);
+            }
             done_i = i + 1;
         }
+        bool bad = false;
+#pragma unroll
+        for (int r = 0; r < kRpt; ++r) bad |= !isfinite(bsum[r]);
         if (bad) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+        if (!(ymax < kFp16Max)) range_flag = 1;
         // ---------------- the last segment (or zeros when there are no chunks)
         if (nchunks > 0 && done_i == nchunks) {
             drain(seg, seg_start, nchunks);
         } else if (nchunks == 0 && m < B) {
-            for (int col = col_base; col < col_base + Nn && col < B; ++col) out[(size_t)col * B + m] = 0.f;
+            for (int col = col_base + 16 * cpart; col < col_base + Nn && col < B; ++col)
+                if (((col - col_base) >> 4) % kParts == cpart) out[(size_t)col * B + m] = 0.f;
         }
-        if (write_sums) {
-#pragma unroll
-            for (int r = 0; r < kRpt; ++r) {
-                const int b = b0 + 128 * r;
-                if (b < B) sum_part[(size_t)blockIdx.x * B + b] = bsum[r] * (1.f / kScale);
-            }
-        }
+        if (kParts > 1 && part == 1 && write_sums)
+            for (int r = 0; r < kRpt; ++r) bsum_sh[b0 + 128 * r] = bsum[r];
     }
     if (*abort_p && tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
     if (tid == 32 && ncommit > 0) {
@@ -445,6 +515,64 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, int B, int row_base, in
                      "r"(kTmemCols)
                      : "memory");
     }
+    if (write_sums && warp >= 2 && part == 0) {
+#pragma unroll
+        for (int r = 0; r < kRpt; ++r) {
+            const int b = b0 + 128 * r;
+            if (b < B)
+                sum_part[(size_t)blockIdx.x * B + b] =
+                    (kParts > 1 ? bsum[r] + bsum_sh[b] : bsum[r]) * isc[b];
+        }
+    }
+    if (!range_flag || *abort_p || nchunks == 0) return;
+
+    // ---------------- FP32 recompute of this CTA's block (rare): 64-pixel
+    // chunks of x - s staged in the TMA ring, kFbAcc entries per thread per
+    // pass over the CTA's pixels (which L2 still holds)
+    __syncthreads();
+    float *ys = reinterpret_cast<float *>(staging);
+    float *out = gram_part + (size_t)blockIdx.x * B * B;
+    const long p_begin = c_begin * kChunk;
+    const long p_end = c_end * kChunk < N ? c_end * kChunk : N;
+    const int nrow = B - row_base < kM ? B - row_base : kM;
+    const int ncol = B - col_base < Nn ? B - col_base : Nn;
+    const int ent = nrow * ncol;
+    for (int e0 = 0; e0 < ent; e0 += kThreads * kFbAcc) {
+        float acc[kFbAcc];
+#pragma unroll
+        for (int k = 0; k < kFbAcc; ++k) acc[k] = 0.f;
+        for (long p0 = p_begin; p0 < p_end; p0 += kChunk) {
+            __syncthreads();
+            for (int i = tid; i < B * kChunk; i += kThreads) {
+                const int b = i / kChunk, j = i % kChunk;
+                const long p = p0 + j;
+                ys[b * kFbLd + j] = p < p_end ? cube[(size_t)b * N + p] - sh[b] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kFbAcc; ++k) {
+                const int e = e0 + k * kThreads + tid;
+                if (e < ent) {
+                    const float *ya = ys + (row_base + e / ncol) * kFbLd;
+                    const float *yb = ys + (col_base + e % ncol) * kFbLd;
+                    float a = acc[k];
+                    for (int j = 0; j < kChunk; ++j) a = fmaf(ya[j], yb[j], a);
+                    acc[k] = a;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kFbAcc; ++k) {
+            const int e = e0 + k * kThreads + tid;
+            if (e < ent) out[(size_t)(col_base + e % ncol) * B + row_base + e / ncol] = acc[k];
+        }
+    }
+    if (write_sums)
+        for (int b = tid; b < B; b += kThreads) {
+            float t = 0.f;
+            for (long p = p_begin; p < p_end; ++p) t += cube[(size_t)b * N + p] - sh[b];
+            sum_part[(size_t)blockIdx.x * B + b] = t;
+        }
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver at run time (the library
@@ -498,18 +626,18 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
         const size_t smem = Cfg<false>::kSmem;
         cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
-        gram_tc_kernel<false><<<s.n_part, kThreads, smem, st>>>(
-            map, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+        gram_tc_kernel<false><<<s.n_part, Cfg<false>::kThreads, smem, st>>>(
+            map, cube, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
         return cudaGetLastError();
     }
     const size_t smem = Cfg<true>::kSmem;
     cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     // rows 0-127 x every column, then rows 128-255 x columns 128-255
-    gram_tc_kernel<true><<<s.n_part, kThreads, smem, st>>>(map, B, 0, 0, Np, 1, N, total, s.shift,
-                                                           s.gram_part, s.sum_part, s.ctl);
-    gram_tc_kernel<true><<<s.n_part, kThreads, smem, st>>>(
-        map, B, 128, 128, Np - 128, 0, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+    gram_tc_kernel<true><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
+        map, cube, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+    gram_tc_kernel<true><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
+        map, cube, B, 128, 128, Np - 128, 0, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,11 @@ constexpr int kTile = 8;         // 8x8 accumulator tile per thread
 // runs of 256 consecutive pixels spread over the band (coalesced). Any shift
 // close to the mean works (the moments are exact in it), so the sample is
 // summed in FP32, with its 16 loads per thread issued together.
+// shift[B + b] receives the tensor-core path's scale for band b: the power of
+// two that brings the sample's largest |x - s_b| into [128, 256), so that a
+// pixel must deviate 256 times further than anything in the sample before its
+// scaled value leaves FP16's range (65504); the Gram kernel checks every value
+// and recomputes a partial on the FP32 pipe when one does.
 __global__ void __launch_bounds__(256)
 pilot_shift_kernel(const float *__restrict__ cube, int B, long N, float *__restrict__ shift,
                    Control *ctl)
@@ -30,18 +35,19 @@ pilot_shift_kernel(const float *__restrict__ cube, int B, long N, float *__restr
     const int b = blockIdx.x;
     constexpr int kRuns = 16, kRun = 256;
     const float *band = cube + (size_t)b * (size_t)N;
+    const bool small = N <= (long)kRuns * kRun;
     float acc = 0.f;
     long count;
     bool bad = false;
-    if (N <= (long)kRuns * kRun) {
+    float x[kRuns];
+    if (small) {
         for (long p = threadIdx.x; p < N; p += blockDim.x) {
-            const float x = band[p];
-            bad |= !isfinite(x);
-            acc += x;
+            const float v = band[p];
+            bad |= !isfinite(v);
+            acc += v;
         }
         count = N;
     } else {
-        float x[kRuns];
 #pragma unroll
         for (int r = 0; r < kRuns; ++r)
             x[r] = __ldg(band + ((long)r * (N - kRun)) / (kRuns - 1) + threadIdx.x);
@@ -53,13 +59,42 @@ pilot_shift_kernel(const float *__restrict__ cube, int B, long N, float *__restr
         count = (long)kRuns * kRun;
     }
     __shared__ float red[8];
+    __shared__ float s_sh;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < 8; ++w) t += red[w];
-        shift[b] = t / (float)count;
+        s_sh = t / (float)count;
+        shift[b] = s_sh;
+    }
+    __syncthreads();
+    const float s = s_sh;
+    float dev = 0.f;
+    if (small) {
+        for (long p = threadIdx.x; p < N; p += blockDim.x) dev = fmaxf(dev, fabsf(band[p] - s));
+    } else {
+#pragma unroll
+        for (int r = 0; r < kRuns; ++r) dev = fmaxf(dev, fabsf(x[r] - s));
+    }
+    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    __syncthreads();  // red[] is reused
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dev;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w]);
+        // a constant sample says nothing about the spread: take |s| (or 1)
+        const float ref = m > 0.f ? m : (fabsf(s) > 0.f ? fabsf(s) : 1.f);
+        int e = 4;  // 16 for a non-finite band (flagged above)
+        if (isfinite(ref)) {
+            int ex;
+            frexpf(ref, &ex);  // ref in [2^(ex-1), 2^ex)
+            e = 8 - ex;
+            e = e < -60 ? -60 : (e > 60 ? 60 : e);
+        }
+        shift[B + b] = ldexpf(1.f, e);
     }
 }
 

@@ -58,3 +58,41 @@ def test_covariance_exact_rank_one(hsc, ctx):
     ctx.sync()
     ref = np.var(a) * np.outer(u, u)
     assert np.abs(C.cpu().numpy() - ref).max() < C_TOL * np.abs(ref).max()
+
+
+def test_covariance_raw_counts(hsc, ctx):
+    """A cube in raw sensor counts (offset 1000, a band gain in [0.5, 2], values
+    up to ~20000): shifted deviations reach ~10^4, beyond FP16 once scaled by a
+    fixed factor; the per-band power-of-two scale of the tensor-core path keeps
+    the FP16 parts in range."""
+    B, H, W = 128, 96, 128
+    f = synth.make_frame(31, H, W, B, sigma=0.03).cube.astype(np.float64)
+    gain = np.random.default_rng(5).uniform(0.5, 2.0, size=B)[:, None, None]
+    cube = (1000.0 + 20000.0 * gain * f).astype(np.float32)
+    check(hsc, ctx, cube, 0)
+
+
+def test_covariance_outlier_outside_pilot_sample(hsc, ctx):
+    """One pixel ~10^4 times further from its band's mean than any other, at a
+    position the pilot sample skips (its runs start at r(N - 256)/15): its
+    scaled value leaves FP16's range, so that CTA recomputes its partial on the
+    FP32 pipe. Both the outlier band's row and the rest of C match the oracle,
+    each against its own scale."""
+    import torch
+    B, H, W = 64, 128, 128
+    cube = synth.make_frame(77, H, W, B, sigma=0.03).cube.copy()
+    ob, p = 5, 700
+    cube[ob].flat[p] += np.float32(5e3)
+    c = torch.as_tensor(cube, device="cuda")
+    mu, C = hsc.hsc_pca_covariance(ctx, c)
+    ctx.sync()
+    C = C.cpu().numpy()
+    mu_ref = oracle.band_means(cube)
+    C_ref = oracle.covariance(cube, mu_ref)
+    np.testing.assert_allclose(mu.cpu().numpy(), mu_ref, atol=MU_TOL, rtol=1e-7)
+    rest = np.ones(B, bool)
+    rest[ob] = False
+    sub, sub_ref = C[np.ix_(rest, rest)], C_ref[np.ix_(rest, rest)]
+    assert np.abs(sub - sub_ref).max() < C_TOL * np.abs(sub_ref).max()
+    row, row_ref = C[ob], C_ref[ob]
+    assert np.abs(row - row_ref).max() < C_TOL * np.abs(row_ref).max()
