@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "hsc_internal.cuh"
 
 namespace hsc {
@@ -53,6 +55,28 @@ struct JacParams {
 // j-slices of the double-float C v: each thread sums at most 16 products
 __host__ __device__ inline int jac_slices(int n) { return (n + 15) / 16 < 8 ? 8 : (n + 15) / 16; }
 
+// The first sweep with the matrix moving (sweep_pos, 3 <= P <= kPosMaxP):
+// each of its two exchange buffers holds 4 planes of kPS floats (a
+// compile-time plane stride, so a block's four entries are one base address
+// plus constants) and a spare word.
+constexpr int kPosMaxP = 64;
+constexpr int kPS = 2016;
+constexpr int kPosBuf = 4 * kPS + 4;  // floats per exchange buffer
+static_assert(kPosMaxP * (kPosMaxP - 1) / 2 <= kPS, "plane stride too small");
+
+// Floats of the first-sweep region: A (n rows of ld) and the rotation log,
+// or the exchange buffers and the log.
+__host__ __device__ inline size_t jac_phase0_floats(int n)
+{
+    const size_t ld = (size_t)n + 1, P = (size_t)n / 2;
+    size_t f = 2 * (size_t)n * ld;
+    if (P >= 3 && P <= (size_t)kPosMaxP) {
+        const size_t g = 2 * (size_t)kPosBuf + 2 * ((size_t)n - 1) * P;
+        if (g > f) f = g;
+    }
+    return f;
+}
+
 // Work area (floats, row stride ld = n + 1): A (n rows), then the rotation
 // log of the first sweep ((n - 1) rounds x n/2 (c, s) pairs), whose space
 // the fallback reuses for V^T (n rows), then the kBasis rebuilt columns,
@@ -61,7 +85,7 @@ __host__ __device__ inline int jac_slices(int n) { return (n + 15) / 16 < 8 ? 8 
 __host__ __device__ inline size_t jac_work_floats(int n)
 {
     const size_t ld = (size_t)n + 1;
-    return 2 * (size_t)n * ld + (size_t)kBasis * ld + 2 * (size_t)jac_slices(n) * n;
+    return jac_phase0_floats(n) + (size_t)kBasis * ld + 2 * (size_t)jac_slices(n) * n;
 }
 
 // Packed form for larger n: A as its packed upper triangle (rounded up to a
@@ -173,6 +197,63 @@ __device__ __forceinline__ void tri_of(int idx, int P, int &k, int &l)
     l = k + (idx - (k * P - k * (k - 1) / 2));
 }
 
+// Shared-memory accesses at a 32-bit shared address plus a constant offset
+// (the positional sweep's addresses are fixed registers; which of its two
+// buffers a round uses is a compile-time offset).
+template <int kOff>
+__device__ __forceinline__ float ld_sh(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(kOff) : "memory");
+    return v;
+}
+template <int kOff>
+__device__ __forceinline__ float2 ld_sh2(uint32_t a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(a), "n"(kOff)
+                 : "memory");
+    return v;
+}
+template <int kOff>
+__device__ __forceinline__ void st_sh(uint32_t a, float v)
+{
+    asm volatile("st.shared.f32 [%0+%1], %2;" ::"r"(a), "n"(kOff), "f"(v) : "memory");
+}
+template <int kOff>
+__device__ __forceinline__ void st_sh2(uint32_t a, float x, float y)
+{
+    asm volatile("st.shared.v2.f32 [%0+%1], {%2, %3};" ::"r"(a), "n"(kOff), "f"(x), "f"(y)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t sh_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Symmetric Schur rotation of the 2x2 block [[app, apq], [apq, aqq]]: (c, s)
+// zero a_pq (when |a_pq| > tol; else the identity) and (dp, dq) are the new
+// diagonal entries a_pp - t a_pq, a_qq + t a_pq. FP32 intrinsics are enough
+// here: the leading vector is refined to FP64 accuracy afterwards.
+__device__ __forceinline__ void schur_angle(float app, float aqq, float apq, float tol, float &c,
+                                            float &s, float &dp, float &dq)
+{
+    c = 1.f;
+    s = 0.f;
+    dp = app;
+    dq = aqq;
+    if (fabsf(apq) > tol) {
+        const float tau = __fdividef(aqq - app, 2.f * apq);
+        float tt;
+        if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
+        else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
+        c = rsqrtf(fmaf(tt, tt, 1.f));
+        s = tt * c;
+        dp = fmaf(-tt, apq, app);
+        dq = fmaf(tt, apq, aqq);
+    }
+}
+
 __device__ float block_maxf(float v, float *red)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -220,7 +301,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         A = work;                                      // n x ld, upper triangle
         rlog = reinterpret_cast<float2 *>(work + (size_t)n * ld);  // (n-1) x P
         Vt = work + (size_t)n * ld;                    // fallback: V^T, n x ld
-        X = work + 2 * (size_t)n * ld;                 // kBasis x ld, rebuilt columns
+        X = work + jac_phase0_floats(n);               // kBasis x ld, rebuilt columns
         part = reinterpret_cast<float2 *>(X + (size_t)kBasis * ld);  // slices x n
     }
     float2 *Cs2 = reinterpret_cast<float2 *>(work);    // refinement: C as (hi, lo), B x B
@@ -233,6 +314,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     __shared__ float2 cs2[2][kMaxPairs];   // (c, s) of the round's pairs, double-buffered
     __shared__ int2 ab2[2][kMaxPairs];     // (a, b) of the round's pairs
+    __shared__ float2 pcs[2][kPosMaxP];    // sweep_pos: (c, s) per pair
+    __shared__ float2 pdd[2][kPosMaxP];    // sweep_pos: new (a_pp, a_qq) per pair
     __shared__ float fred[32];
     __shared__ float vh[HSC_MAX_BANDS], vl[HSC_MAX_BANDS];   // v = vh + vl
     __shared__ float wh[HSC_MAX_BANDS], wl[HSC_MAX_BANDS];   // w = C v (scaled)
@@ -262,7 +345,12 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
             A[aix(i, j)] = (i < B && j < B) ? C2[(size_t)i * B + j].x * inv_p2 : 0.f;
         }
     };
-    load_A();
+    // the first sweep moves the matrix (sweep_pos below) when it fits
+    const int nno = P * (P - 1) / 2 - P;             // off-diagonal blocks owning no angle
+    const int OW = (P + 31) & ~31;                   // threads of the owner / diagonal blocks
+    const bool pos_sweep = !kPacked && prm.use_smem && P >= 3 && P <= kPosMaxP &&
+                           nno <= 2 * (nthr - OW) + OW;
+    if (!pos_sweep) load_A();  // sweep_pos loads its own blocks
     __syncthreads();
 
     // Work items fixed for the whole run: up to kBlk off-diagonal 2x2 blocks
@@ -336,18 +424,11 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         pair_ab(t, k, n, a, b);
         const int iab = aix(a, b), iaa = aix(a, a), ibb = aix(b, b);
         const float app = A[iaa], aqq = A[ibb], apq = A[iab];
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) > prm.rot_tol) {
-            // FP32 intrinsics are enough here: the leading vector is refined
-            // to FP64 accuracy afterwards
-            float tau = __fdividef(aqq - app, 2.f * apq);
-            float tt;
-            if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
-            else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
-            c = rsqrtf(fmaf(tt, tt, 1.f));
-            s = tt * c;
-            A[iaa] = fmaf(-tt, apq, app);
-            A[ibb] = fmaf(tt, apq, aqq);
+        float c, s, dp, dq;
+        schur_angle(app, aqq, apq, prm.rot_tol, c, s, dp, dq);
+        if (s != 0.f || c != 1.f) {
+            A[iaa] = dp;
+            A[ibb] = dq;
             A[iab] = 0.f;
         }
         cs2[buf][k] = make_float2(c, s);
@@ -418,6 +499,211 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         return offmax;
     };
 
+    // ---- The first sweep with the matrix moving instead of the indices
+    // (shared-memory form, 3 <= P <= kPosMaxP): the same rotations in the
+    // same order as sweep(true, false). In round t position i holds the index
+    // the circle pairing puts there (pair k at positions 2k, 2k+1), so a pair
+    // is always (2k, 2k+1); after each round the positions advance by one
+    // fixed permutation sigma (even positions one pair down, odd ones one
+    // pair up, 1 fixed, 0 -> 3, 2P-1 -> 2P-2: a single cycle of length n-1,
+    // so the sweep ends where it began). Only the off-diagonal 2x2 blocks
+    // (k < l) are stored: a pair's own block is known from its angle (its
+    // diagonal entries a_pp - t a_pq, a_qq + t a_pq travel with (c, s); its
+    // a_pq becomes 0). Each round a thread reads its (at most two) blocks
+    // from one exchange buffer, rotates them with the angles of pairs k and
+    // l and writes each entry where sigma sends it in the other buffer
+    // (addresses fixed for the whole sweep; entries kept as four planes, so
+    // that a warp's reads and writes are conflict-free). One barrier per
+    // round: the block that holds the next round's a_pq of a pair, (k'-1,
+    // k'+1) as in sweep(), computes that pair's angle and diagonal, keeps
+    // its a_pq in registers and writes the zero that the pair's own block
+    // sends to the entry sigma maps it to. These owner blocks sit in the
+    // first warps, which hold at most one other block. A pair whose
+    // |a_pq| <= rot_tol is not rotated and its a_pq is dropped, a change
+    // below the sweep's own FP32 rounding (the leading vector is refined
+    // against the FP64 covariance afterwards).
+    float2 *rlog_s = reinterpret_cast<float2 *>(smem + 2 * kPosBuf);  // shared-memory log
+    if (pos_sweep) rlog = rlog_s;
+    auto sweep_pos = [&]() {
+        auto sigma = [P](int i) -> int {
+            if (i == 1) return 1;
+            if (i == 0) return 3;
+            if ((i & 1) == 0) return i - 2;
+            return i == 2 * P - 1 ? 2 * P - 2 : i + 2;
+        };
+        auto sigma_inv = [P](int j) -> int {
+            if (j == 1) return 1;
+            if (j == 3) return 0;
+            if ((j & 1) == 0) return j == 2 * P - 2 ? 2 * P - 1 : j + 2;
+            return j - 2;
+        };
+        // storage order of the off-diagonal blocks: those owning no angle
+        // (row-major), then the owners (by the pair they serve)
+        auto store_of = [&](int k, int l) -> int {
+            const int o = owner_of(k, l);
+            if (o >= 0) return nno + o;
+            const int rm = rowstart(k) + (l - k - 1);
+            int c = k == 0 ? 0 : (k <= P - 2 ? k + 1 : P);  // owners in rows < k
+            if (k == 0) c += (l >= 1) + (l >= 2);
+            else if (k <= P - 3) c += (l >= k + 2);
+            else if (k == P - 2) c += (l >= P - 1);
+            return rm - c;
+        };
+        constexpr int kPlane = 4 * kPS, kBuf = 4 * kPosBuf;  // bytes
+        constexpr int kJunk = 4 * kPlane;                    // the spare word of a buffer
+        constexpr int kCsBuf = 8 * kPosMaxP;                 // bytes between angle buffers
+        const int T = nthr - OW;
+        const uint32_t e_base = sh_addr(smem), cs_base = sh_addr(&pcs[0][0]);
+        const uint32_t dd_off = sh_addr(&pdd[0][0]) - cs_base;  // (a_pp, a_qq) beside (c, s)
+        // the shared address of an entry (i, j), i < j in different pairs, in buffer 0
+        auto entry = [&](int i, int j) -> uint32_t {
+            if (i > j) {
+                const int tmp = i;
+                i = j;
+                j = tmp;
+            }
+            return e_base + 4u * (uint32_t)(((i & 1) * 2 + (j & 1)) * kPS + store_of(i >> 1, j >> 1));
+        };
+        // slot 0: the owner block of pair tid (tid < OW) or a plain block;
+        // slot 1: a plain block. Per slot: the address of its plane-0 entry
+        // in buffer 0, its four destinations, the addresses of its pairs'
+        // angles; ok = holds a block.
+        uint32_t ga[2], dst[2][4], csk[2], csl[2];
+        bool ok[2];
+        int own_e = 0;
+        uint32_t zero_dst = e_base + kJunk;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            ok[s] = false;
+            ga[s] = csk[s] = csl[s] = e_base;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[s][q] = e_base + kJunk;
+            int k, l, idx;
+            bool owner = false;
+            if (tid < OW && s == 0) {
+                if (tid >= P) continue;
+                const int i1 = sigma_inv(2 * tid), i2 = sigma_inv(2 * tid + 1);  // i1 in pair l
+                k = i2 >> 1;
+                l = i1 >> 1;
+                own_e = (i2 & 1) * 2 + (i1 & 1);
+                idx = nno + tid;
+                owner = true;
+                zero_dst = entry(sigma(2 * tid), sigma(2 * tid + 1));
+            } else {
+                idx = tid < OW ? 2 * T + tid : tid - OW + s * T;
+                if (idx >= nno) continue;
+                int rm = idx;
+                for (int it = 0; it < 8; ++it) {  // fixed point: rm = idx + owners_upto(rm)
+                    const int nx = idx + owners_upto(rm);
+                    if (nx == rm) break;
+                    rm = nx;
+                }
+                tri_of(rm, P - 1, k, l);
+                l += 1;
+            }
+            ok[s] = true;
+            ga[s] = e_base + 4u * (uint32_t)idx;
+            csk[s] = cs_base + 8u * (uint32_t)k;
+            csl[s] = cs_base + 8u * (uint32_t)l;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                dst[s][q] = (owner && q == own_e)
+                                ? e_base + kJunk  // the next pair's a_pq stays in registers
+                                : entry(sigma(2 * k + (q >> 1)), sigma(2 * l + (q & 1)));
+            // initial positional block: positions 2k+r, 2l+c hold the indices
+            // of round 0's pairs k and l
+            int ak, bk, al, bl;
+            pair_ab(0, k, n, ak, bk);
+            pair_ab(0, l, n, al, bl);
+            const int rows[2] = {ak, bk}, cols[2] = {al, bl};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int pi = rows[q >> 1], pj = cols[q & 1];
+                smem[q * kPS + idx] = (pi < B && pj < B) ? C2[(size_t)pi * B + pj].x * inv_p2 : 0.f;
+            }
+        }
+        if (tid < P) {  // round 0's angle of pair tid
+            int a, b;
+            pair_ab(0, tid, n, a, b);
+            auto c2 = [&](int i, int j) { return (i < B && j < B) ? C2[(size_t)i * B + j].x * inv_p2 : 0.f; };
+            float c, sn, dp, dq;
+            schur_angle(c2(a, a), c2(b, b), c2(a, b), prm.rot_tol, c, sn, dp, dq);
+            pcs[0][tid] = make_float2(c, sn);
+            pdd[0][tid] = make_float2(dp, dq);
+            rlog_s[tid] = make_float2(c, sn);
+        }
+        __syncthreads();
+        // one round reading buffer kCur and writing the other
+        auto round = [&](auto cur_tag, int t) {
+            constexpr int kCur = decltype(cur_tag)::value, kNxt = kCur ^ 1;
+            auto rotate = [&](int s, float &z0, float &z1, float &z2, float &z3) {
+                const uint32_t g = ga[s];
+                const float x00 = ld_sh<kCur * kBuf>(g);
+                const float x01 = ld_sh<kCur * kBuf + kPlane>(g);
+                const float x10 = ld_sh<kCur * kBuf + 2 * kPlane>(g);
+                const float x11 = ld_sh<kCur * kBuf + 3 * kPlane>(g);
+                const float2 rk = ld_sh2<kCur * kCsBuf>(csk[s]);
+                const float2 rl = ld_sh2<kCur * kCsBuf>(csl[s]);
+                const float ck = rk.x, sk = rk.y, cl = rl.x, sl = rl.y;
+                const float y00 = ck * x00 - sk * x10, y01 = ck * x01 - sk * x11;
+                const float y10 = sk * x00 + ck * x10, y11 = sk * x01 + ck * x11;
+                z0 = cl * y00 - sl * y01;
+                z1 = sl * y00 + cl * y01;
+                z2 = cl * y10 - sl * y11;
+                z3 = sl * y10 + cl * y11;
+            };
+            auto put = [&](int s, float z0, float z1, float z2, float z3) {
+                st_sh<kNxt * kBuf>(dst[s][0], z0);
+                st_sh<kNxt * kBuf>(dst[s][1], z1);
+                st_sh<kNxt * kBuf>(dst[s][2], z2);
+                st_sh<kNxt * kBuf>(dst[s][3], z3);
+            };
+            float z0, z1, z2, z3;
+            if (tid < OW) {  // warp-uniform: the owner warps
+                if (ok[0]) {
+                    rotate(0, z0, z1, z2, z3);
+                    if (t + 1 < n - 1) {
+                        const float apq = own_e == 0 ? z0 : (own_e == 1 ? z1 : (own_e == 2 ? z2 : z3));
+                        const float2 dl = ld_sh2<kCur * kCsBuf>(csl[0] + dd_off);
+                        const float2 dk = ld_sh2<kCur * kCsBuf>(csk[0] + dd_off);
+                        const float app = (own_e & 1) ? dl.y : dl.x, aqq = (own_e >> 1) ? dk.y : dk.x;
+                        float c, sn, dp, dq;
+                        schur_angle(app, aqq, apq, prm.rot_tol, c, sn, dp, dq);
+                        const uint32_t ca = cs_base + 8u * (uint32_t)tid;
+                        st_sh2<kNxt * kCsBuf>(ca, c, sn);
+                        st_sh2<kNxt * kCsBuf>(ca + dd_off, dp, dq);
+                        rlog_s[(t + 1) * P + tid] = make_float2(c, sn);
+                    }
+                    put(0, z0, z1, z2, z3);
+                    st_sh<kNxt * kBuf>(zero_dst, 0.f);
+                }
+            } else {
+                rotate(0, z0, z1, z2, z3);
+                put(0, z0, z1, z2, z3);
+            }
+            if (ok[1]) {
+                rotate(1, z0, z1, z2, z3);
+                put(1, z0, z1, z2, z3);
+            }
+            __syncthreads();
+        };
+        int t = 0;
+        for (; t + 1 < n - 1; t += 2) {
+            round(std::integral_constant<int, 0>(), t);
+            round(std::integral_constant<int, 1>(), t + 1);
+        }
+        if (t < n - 1) round(std::integral_constant<int, 0>(), t);
+        // the diagonal after the last round, by index
+        for (int k = tid; k < P; k += nthr) {
+            int a, b;
+            pair_ab(n - 2, k, n, a, b);
+            const float2 d = pdd[(n - 2) & 1][k];
+            sr[a] = d.x;
+            sr[b] = d.y;
+        }
+        __syncthreads();
+    };
+
     // Refinement of the leading vector to FP64-level accuracy on m basis
     // columns (column c at basis + c * ld, its theta in th[c], the lead at
     // column lc), C given as (hi, lo) pairs c2 (shared or global), v = vh + vl
@@ -435,7 +721,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // between steps; the correction's direction and length are FP32 and are
     // added to v exactly (TwoSum). All in the scaled units of A.
     auto refine = [&](const float *basis, int m, int lc, bool deflate, float theta_c,
-                      const float2 *c2) -> int {
+                      const float2 *c2, float2 *part) -> int {
         const int nchunk = (B + 31) / 32;  // warps holding rows i = tid < B
         const int i = tid;
         const bool row = i < B;
@@ -558,17 +844,23 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     // ---- phase 0: one logged sweep, rebuilt leading columns, refinement
     long long t0 = clock64();
-    sweep(true, false);
+    if (pos_sweep) {
+        sweep_pos();
+    } else {
+        sweep(true, false);
+        for (int j = tid; j < B; j += nthr) sr[j] = A[aix(j, j)];
+        __syncthreads();
+    }
     sweeps = 1;
     const int m = B < kBasis ? B : kBasis;
     // rank the diagonal (ties: smaller index first); the m largest form the
     // basis, the mean of the rest is theta_c
     float rest = 0.f;
     for (int j = tid; j < B; j += nthr) {
-        const float dj = A[aix(j, j)];
+        const float dj = sr[j];
         int rank = 0;
         for (int i = 0; i < B; ++i) {
-            const float di = A[aix(i, i)];
+            const float di = sr[i];
             rank += (di > dj || (di == dj && i < j)) ? 1 : 0;
         }
         if (rank < m) {
@@ -582,9 +874,68 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     const bool deflate = B > m;
     const float theta_c = deflate ? rest / (float)(B - m) : 0.f;
     // X_c = J_0 J_1 ... J_{n-2} e_{basis_idx[c]}: one warp per column applies
-    // the logged rounds last to first, x <- J_t x on rows (a, b); a lane's
-    // two pairs of a round are disjoint, so both are loaded before either
-    // is stored
+    // the logged rounds last to first, x <- J_t x on rows (a, b).
+    if (pos_sweep) {
+        // In the positions of the round being undone: lane L holds the
+        // entries of pairs L and L + 32 (even and odd position), rotates
+        // them, then takes the entries that sigma^-1 brings from the pair
+        // before (even) and after (odd) by four shuffles, with the fixed
+        // ends of the circle (positions 0, 1, 2P-2, 2P-1) patched in place.
+        for (int c = warp; c < m; c += nwarps) {
+            const int j0 = basis_idx[c];
+            int p0;  // position of index j0 in round n-2
+            if (j0 == n - 1) {
+                p0 = 1;
+            } else {
+                const int ka = ((j0 - (n - 2)) % (n - 1) + (n - 1)) % (n - 1);
+                p0 = ka <= P - 1 ? 2 * ka : 2 * ((((n - 2) - j0) % (n - 1) + (n - 1)) % (n - 1)) + 1;
+            }
+            float eA = 0.f, oA = 0.f, eB = 0.f, oB = 0.f;
+            if ((p0 >> 1) == lane) (p0 & 1 ? oA : eA) = 1.f;
+            if ((p0 >> 1) == lane + 32) (p0 & 1 ? oB : eB) = 1.f;
+            const bool vA = lane < P, vB = lane + 32 < P;
+            for (int t = n - 2; t >= 0; --t) {
+                const float2 rA = vA ? rlog_s[t * P + lane] : make_float2(1.f, 0.f);
+                const float2 rB = vB ? rlog_s[t * P + lane + 32] : make_float2(1.f, 0.f);
+                float a0 = eA, b0 = oA;
+                eA = rA.x * a0 + rA.y * b0;
+                oA = rA.x * b0 - rA.y * a0;
+                a0 = eB;
+                b0 = oB;
+                eB = rB.x * a0 + rB.y * b0;
+                oB = rB.x * b0 - rB.y * a0;
+                if (t == 0) break;
+                const float tA = __shfl_sync(0xffffffffu, eA, (lane + 31) & 31);
+                const float tB = __shfl_sync(0xffffffffu, eB, (lane + 31) & 31);
+                const float tC = __shfl_sync(0xffffffffu, oA, (lane + 1) & 31);
+                const float tD = __shfl_sync(0xffffffffu, oB, (lane + 1) & 31);
+                const float neA = lane >= 1 ? tA : tC;  // lane 0: position 3's entry
+                const float neB = lane >= 1 ? tB : tA;
+                float noA = lane == 0 ? oA : (lane <= 30 ? tC : tD);
+                if (lane == P - 1) noA = eA;              // position 2P-2's entry
+                const float noB = (lane + 32 == P - 1) ? eB : tD;
+                eA = vA ? neA : 0.f;
+                oA = vA ? noA : 0.f;
+                eB = vB ? neB : 0.f;
+                oB = vB ? noB : 0.f;
+            }
+            float *x = smem + jac_phase0_floats(n) + (size_t)c * ld;  // = X (shared memory)
+            if (vA) {
+                int a, b;
+                pair_ab(0, lane, n, a, b);
+                x[a] = eA;
+                x[b] = oA;
+            }
+            if (vB) {
+                int a, b;
+                pair_ab(0, lane + 32, n, a, b);
+                x[a] = eB;
+                x[b] = oB;
+            }
+        }
+    } else
+    // a lane's two pairs of a round are disjoint, so both are loaded before
+    // either is stored
     for (int c = warp; c < m; c += nwarps) {
         float *x = X + (size_t)c * ld;
         const int j0 = basis_idx[c];
@@ -639,7 +990,15 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     __syncthreads();
     long long t1 = clock64();
     t_sweep += t1 - t0;
-    refine_iters = refine(X, m, 0, deflate, theta_c, prm.use_smem ? Cs2 : C2);
+    if (prm.use_smem && !kPacked) {
+        // the same pointers, formed from the shared array itself so that
+        // the refinement's accesses compile to shared-memory instructions
+        const size_t xo = jac_phase0_floats(n);
+        refine_iters = refine(smem + xo, m, 0, deflate, theta_c, reinterpret_cast<const float2 *>(smem),
+                              reinterpret_cast<float2 *>(smem + xo + (size_t)kBasis * ld));
+    } else {
+        refine_iters = refine(X, m, 0, deflate, theta_c, prm.use_smem ? Cs2 : C2, part);
+    }
     converged = refine_iters <= kMaxRefine;
     t_refine += clock64() - t1;
 
@@ -673,30 +1032,59 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         __syncthreads();
         t1 = clock64();
         t_sweep += t1 - t0;
-        refine_iters = refine(Vt, B, lead, false, 0.f, C2);
+        refine_iters = refine(Vt, B, lead, false, 0.f, C2, part);
         converged = refine_iters <= kMaxRefine;
         t_refine += clock64() - t1;
     }
 
     // ---- outputs: v / ||v|| (||v||^2 = the last v^T v, which belongs to the
-    // returned v), the sign rule (largest |v_i| positive), lambda1 = rho 2^e
-    if (tid == 0) {
-        const double vv = (double)s_vv.h + (double)s_vv.l;
-        s_inv_norm = vv > 0.0 ? 1.0 / sqrt(vv) : 1.0;
-        double bv = 0.0;  // the first component of largest magnitude
-        for (int ii = 0; ii < B; ++ii) {
-            const double x = (double)vh[ii] + (double)vl[ii];
-            if (fabs(x) > fabs(bv)) bv = x;
+    // returned v), the sign rule (largest |v_i| positive, the smaller band on
+    // a tie), lambda1 = rho 2^e. v_i = vh + vl is exact in FP64; |v_i| is
+    // ordered by the integer value of its bits, so the arg-max is an integer
+    // reduction (FP64 arithmetic on GB300 has a 64-cycle latency).
+    {
+        unsigned long long key = 0ull;
+        int arg = 0x7fffffff;
+        if (tid < B) {
+            const double x = (double)vh[tid] + (double)vl[tid];
+            key = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+            arg = tid;
         }
-        s_sign = (bv < 0.0) ? -1 : 1;
-        *lambda1_out = ldexp((double)s_rho.h + (double)s_rho.l, e2);
-        if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
-        ctl->jacobi_sweeps = (unsigned)sweeps;
-        ctl->refine_iters = (unsigned)(refine_iters > kMaxRefine ? kMaxRefine : refine_iters);
-        ctl->jacobi_sweep_cycles = (unsigned long long)t_sweep;
-        ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
-        ctl->imin_key = float_to_key(INFINITY);
-        ctl->imax_key = float_to_key(-INFINITY);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+            const int a2 = __shfl_xor_sync(0xffffffffu, arg, o);
+            if (k2 > key || (k2 == key && a2 < arg)) {
+                key = k2;
+                arg = a2;
+            }
+        }
+        __shared__ unsigned long long s_key[32];
+        __shared__ int s_arg[32];
+        if (lane == 0) {
+            s_key[warp] = key;
+            s_arg[warp] = arg;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 1; w < nwarps; ++w)
+                if (s_key[w] > key || (s_key[w] == key && s_arg[w] < arg)) {
+                    key = s_key[w];
+                    arg = s_arg[w];
+                }
+            const double bv = arg < B ? (double)vh[arg] + (double)vl[arg] : 0.0;
+            s_sign = (bv < 0.0) ? -1 : 1;
+            const double vv = (double)s_vv.h + (double)s_vv.l;
+            s_inv_norm = vv > 0.0 ? 1.0 / sqrt(vv) : 1.0;
+            *lambda1_out = ldexp((double)s_rho.h + (double)s_rho.l, e2);
+            if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
+            ctl->jacobi_sweeps = (unsigned)sweeps;
+            ctl->refine_iters = (unsigned)(refine_iters > kMaxRefine ? kMaxRefine : refine_iters);
+            ctl->jacobi_sweep_cycles = (unsigned long long)t_sweep;
+            ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
+            ctl->imin_key = float_to_key(INFINITY);
+            ctl->imax_key = float_to_key(-INFINITY);
+        }
     }
     __syncthreads();
     const double scl = (double)s_sign * s_inv_norm;

@@ -97,12 +97,15 @@ def decaying_spectrum_cube(B=96, H=64, W=64, seed=9):
     return x.reshape(B, H, W).astype(np.float32)
 
 
-@pytest.mark.parametrize("case", ["cfg1", "cfg2", "snapshot", "b37", "b200", "decay"])
+@pytest.mark.parametrize("case", ["cfg1", "cfg2", "snapshot", "b37", "b200", "decay", "b5", "b6",
+                                  "b7", "b139", "b140", "b141"])
 def test_eigenpair_fp64_residual(hsc, ctx, case):
     """The refinement's claim: (v1, lambda1) is an eigenpair of the GPU's own
     FP64 covariance to ||C v - lambda v|| <= 2e-13 ||C|| (checked in FP64 on
-    the host), whether the work area sits in shared memory (B <= 142) or in
-    global memory (B = 200), and on a slowly decaying spectrum."""
+    the host), and lambda1 is its largest eigenvalue: whether the work area
+    sits in shared memory (B <= 142) or in global memory (B = 200), on a
+    slowly decaying spectrum, and at the band counts where the first sweep
+    changes form (3 pairs, 70 pairs, 71 pairs)."""
     if case.startswith("cfg"):
         cube = synth.make_config(int(case[3])).cube
     elif case == "snapshot":
@@ -111,6 +114,9 @@ def test_eigenpair_fp64_residual(hsc, ctx, case):
         cube = synth.make_frame(5, 31, 33, 37, sigma=0.03).cube
     elif case == "b200":
         cube = synth.make_frame(6, 40, 48, 200, sigma=0.03).cube
+    elif case.startswith("b"):
+        B = int(case[1:])
+        cube = synth.make_frame(B, 36, 40, B, sigma=0.03).cube
     else:
         cube = decaying_spectrum_cube()
     _, v, lam = gpu_pca(hsc, ctx, cube)
@@ -121,6 +127,7 @@ def test_eigenpair_fp64_residual(hsc, ctx, case):
     cn = max(abs(lam), np.abs(np.diag(C)).max())
     assert abs(np.linalg.norm(v) - 1.0) < 1e-14
     assert np.linalg.norm(r) <= 2e-13 * cn, np.linalg.norm(r) / cn
+    assert abs(lam - np.linalg.eigvalsh(C).max()) <= 1e-12 * cn
 
 
 def gpu_svm(hsc, ctx, cube, model, flags=0):
