@@ -254,6 +254,32 @@ __device__ __forceinline__ void schur_angle(float app, float aqq, float apq, flo
     }
 }
 
+// schur_angle with the multi-function unit's reciprocal and reciprocal
+// square root in place of the correctly rounded ones: for the small
+// Rayleigh-Ritz problem, whose eigenvectors only seed the refinement.
+__device__ __forceinline__ void schur_angle_fast(float app, float aqq, float apq, float tol,
+                                                 float &c, float &s, float &dp, float &dq)
+{
+    c = 1.f;
+    s = 0.f;
+    dp = app;
+    dq = aqq;
+    if (fabsf(apq) > tol) {
+        const float tau = __fdividef(aqq - app, 2.f * apq);
+        float tt;
+        if (fabsf(tau) > 1e18f) {
+            tt = __fdividef(0.5f, tau);
+        } else {
+            const float q = fmaf(tau, tau, 1.f);
+            tt = copysignf(__fdividef(1.f, fabsf(tau) + q * rsqrtf(q)), tau);
+        }
+        c = rsqrtf(fmaf(tt, tt, 1.f));
+        s = tt * c;
+        dp = fmaf(-tt, apq, app);
+        dq = fmaf(tt, apq, aqq);
+    }
+}
+
 __device__ float block_maxf(float v, float *red)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -990,6 +1016,165 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     __syncthreads();
     long long t1 = clock64();
     t_sweep += t1 - t0;
+    // ---- Rayleigh-Ritz on the rebuilt columns (B <= 128): H = X^T C X in
+    // FP32, two cyclic Jacobi sweeps of H (padded to 16 x 16), X <- X W and
+    // the theta's <- H's diagonal. After one sweep of A the columns are only
+    // rough eigenvectors; the Ritz vectors of their span are far closer (the
+    // leading one to ~4e-3 on the synthetic workloads, from several percent),
+    // which takes the refinement from 8-13 steps to 4-5.
+    if (pos_sweep && m >= 2) {
+        constexpr int kR = 16, kRl = kR + 1;
+        float *Xs = smem + jac_phase0_floats(n);  // the basis (column-major, stride ld)
+        const float2 *Cs = reinterpret_cast<const float2 *>(smem);  // staged C (hi, lo)
+        float *Ys = smem + jac_phase0_floats(n) + (size_t)kBasis * ld;  // C X, m x B
+        float *Hs = coef, *Ws = coef + kR * kRl;  // 16 x 17 each
+        // X^T in two halves (columns 0-7 in wh, 8-15 in wl), 8 floats per row
+        for (int idx = tid; idx < B * kR; idx += nthr) {
+            const int j = idx >> 4, c = idx & 15;
+            (c < 8 ? wh : wl)[j * 8 + (c & 7)] = c < m ? Xs[(size_t)c * ld + j] : 0.f;
+        }
+        __syncthreads();
+        if (tid < B) {  // Y = C X, row tid (C symmetric: column tid of row j)
+            float acc[kR];
+#pragma unroll
+            for (int c = 0; c < kR; ++c) acc[c] = 0.f;
+            const float4 *xa = reinterpret_cast<const float4 *>(wh);
+            const float4 *xb = reinterpret_cast<const float4 *>(wl);
+            for (int j = 0; j < B; ++j) {
+                const float cj = Cs[(size_t)j * B + tid].x;
+                const float4 a0 = xa[2 * j], a1 = xa[2 * j + 1], b0 = xb[2 * j], b1 = xb[2 * j + 1];
+                const float xr[kR] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w,
+                                      b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int c = 0; c < kR; ++c) acc[c] = fmaf(cj, xr[c], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < kR; ++c)
+                if (c < m) Ys[c * B + tid] = acc[c];
+        }
+        for (int idx = tid; idx < kR * kR; idx += nthr)
+            Ws[(idx >> 4) * kRl + (idx & 15)] = (idx >> 4) == (idx & 15) ? 1.f : 0.f;
+        __syncthreads();
+        // H = X^T Y: its upper triangle (zero outside m x m); a warp takes up to
+        // kPer entries, its lanes stride the rows (conflict-free), and the
+        // entries' shuffle reductions run side by side
+        {
+            constexpr int kEnt = kR * (kR + 1) / 2, kPer = (kEnt + 31) / 32;  // 136, 5
+            float acc[kPer];
+            int ea[kPer], eb[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int e = warp + q * nwarps;
+                int a = 0, rem = e < kEnt ? e : 0;
+                while (rem >= kR - a) {
+                    rem -= kR - a;
+                    ++a;
+                }
+                ea[q] = a;
+                eb[q] = a + rem;
+                acc[q] = 0.f;
+                if (e < kEnt && eb[q] < m)
+                    for (int i = lane; i < B; i += 32)
+                        acc[q] = fmaf(Xs[(size_t)a * ld + i], Ys[eb[q] * B + i], acc[q]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+#pragma unroll
+            for (int q = 0; q < kPer; ++q)
+                if (lane == 0 && warp + q * nwarps < kEnt) {  // in the units of A (C / 2^e, exact)
+                    Hs[ea[q] * kRl + eb[q]] = acc[q] * inv_p2;
+                    Hs[eb[q] * kRl + ea[q]] = acc[q] * inv_p2;
+                }
+        }
+        __syncthreads();
+        if (warp == 0) {  // two sweeps, circle pairing of the 16 indices
+            float2 *ang = reinterpret_cast<float2 *>(sr);
+            for (int sw = 0; sw < 2; ++sw)
+                for (int t = 0; t < kR - 1; ++t) {
+                    // this lane's pair: k = lane & 7 in the update loops
+                    int pa, pb;
+                    pair_ab(t, lane & 7, kR, pa, pb);
+                    float dp = 0.f, dq = 0.f;
+                    bool rot = false;
+                    if (lane < kR / 2) {
+                        float c, sn;
+                        schur_angle_fast(Hs[pa * kRl + pa], Hs[pb * kRl + pb], Hs[pa * kRl + pb],
+                                         prm.rot_tol, c, sn, dp, dq);
+                        ang[lane] = make_float2(c, sn);
+                        rot = sn != 0.f || c != 1.f;
+                    }
+                    __syncwarp();
+                    const float2 r = ang[lane & 7];
+                    float x[4], y[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {  // rows pa, pb (J^T H), columns (lane >> 3) + 4q
+                        const int j = (lane >> 3) + 4 * q;
+                        x[q] = Hs[pa * kRl + j];
+                        y[q] = Hs[pb * kRl + j];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = (lane >> 3) + 4 * q;
+                        Hs[pa * kRl + j] = r.x * x[q] - r.y * y[q];
+                        Hs[pb * kRl + j] = r.y * x[q] + r.x * y[q];
+                    }
+                    __syncwarp();
+                    float u[4], w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {  // columns pa, pb of H and W (H J, W J)
+                        const int i = (lane >> 3) + 4 * q;
+                        x[q] = Hs[i * kRl + pa];
+                        y[q] = Hs[i * kRl + pb];
+                        u[q] = Ws[i * kRl + pa];
+                        w[q] = Ws[i * kRl + pb];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int i = (lane >> 3) + 4 * q;
+                        Hs[i * kRl + pa] = r.x * x[q] - r.y * y[q];
+                        Hs[i * kRl + pb] = r.y * x[q] + r.x * y[q];
+                        Ws[i * kRl + pa] = r.x * u[q] - r.y * w[q];
+                        Ws[i * kRl + pb] = r.y * u[q] + r.x * w[q];
+                    }
+                    __syncwarp();
+                    if (rot) {  // the pair's own block in closed form
+                        Hs[pa * kRl + pa] = dp;
+                        Hs[pb * kRl + pb] = dq;
+                        Hs[pa * kRl + pb] = 0.f;
+                        Hs[pb * kRl + pa] = 0.f;
+                    }
+                    __syncwarp();
+                }
+            if (lane < m) {  // Ritz values in decreasing order (ties: smaller index)
+                const float d = Hs[lane * kRl + lane];
+                int rank = 0;
+                for (int c = 0; c < m; ++c) {
+                    const float dc = Hs[c * kRl + c];
+                    rank += (dc > d || (dc == d && c < lane)) ? 1 : 0;
+                }
+                basis_idx[rank] = lane;
+                th[rank] = d;
+            }
+        }
+        __syncthreads();
+        if (tid < B) {  // X <- X W (columns in Ritz order), row by row in place
+            float x[kR];
+#pragma unroll
+            for (int k = 0; k < kR; ++k) x[k] = k < m ? Xs[(size_t)k * ld + tid] : 0.f;
+            for (int c = 0; c < m; ++c) {
+                const int q = basis_idx[c];
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < kR; ++k) acc = fmaf(x[k], Ws[k * kRl + q], acc);
+                Xs[(size_t)c * ld + tid] = acc;
+            }
+            vh[tid] = Xs[tid];  // the leading Ritz vector starts the refinement
+            vl[tid] = 0.f;
+        }
+        __syncthreads();
+    }
     if (prm.use_smem && !kPacked) {
         // the same pointers, formed from the shared array itself so that
         // the refinement's accesses compile to shared-memory instructions
