@@ -19,7 +19,6 @@ independent replica on its own GPU (frames are independent: weak scaling).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -176,10 +175,8 @@ def fp32_pipe_peak_tops(sm_count, mhz):
 
 
 def kernel_source_sha(stage):
-    files = {"knn": "k_knn.cu", "project_svm": "k_project_svm.cu", "moments": "k_moments.cu",
-             "jacobi": "k_jacobi.cu", "normalize": "k_project_svm.cu"}
-    path = os.path.join(ROOT, "paper_2404_10631_gb300", "csrc", files[stage])
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    from paper_2404_10631_gb300.ncu_summary import source_sha
+    return source_sha(stage)
 
 
 def traffic_from_profiles(stage):

@@ -28,14 +28,16 @@ STAGE_OF = (("pilot_shift_kernel", "moments"), ("gram_tc_kernel", "moments"),
             ("project_svm_kernel", "project_svm"), ("normalize_kernel", "normalize"),
             ("knn_pruned_kernel", "knn"), ("knn_redo_kernel", "knn"),
             ("knn_kernel", "knn_full"))
-SOURCE_OF = {"moments": "k_moments.cu", "jacobi": "k_jacobi.cu",
-             "project_svm": "k_project_svm.cu", "normalize": "k_project_svm.cu",
-             "knn": "k_knn.cu", "knn_full": "k_knn.cu"}
+SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu"), "jacobi": ("k_jacobi.cu",),
+             "project_svm": ("k_project_svm.cu",), "normalize": ("k_project_svm.cu",),
+             "knn": ("k_knn.cu",), "knn_full": ("k_knn.cu",)}
 
 
 def source_sha(stage: str) -> str:
-    path = os.path.join(HERE, "csrc", SOURCE_OF[stage])
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in SOURCE_OF[stage]:
+        h.update(open(os.path.join(HERE, "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def kernel_base(name: str) -> str:
