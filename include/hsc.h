@@ -296,6 +296,12 @@ hsc_status hsc_profile_enable(hsc_ctx *ctx, int enable);
  * SM clock cycles spent in each part (cycle pointers nullable). */
 hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_iters,
                                int64_t *sweep_cycles, int64_t *refine_cycles);
+/* Measured issue rate of device's FP32 (fp64 = 0: FFMA) or FP64 (fp64 = 1:
+ * DFMA) pipe over all its SMs, in lane-operations per second (one multiply-
+ * add per thread per instruction): the denominator of the non-tensor
+ * rooflines. Runs two short kernels on a private stream (tens of ms) and
+ * synchronises it. HSC_ERR_CUDA if a launch fails. */
+hsc_status hsc_measure_fma_rate(int device, int fp64, double *lane_ops_per_s);
 /* Diagnostics of the pruned KNN search (waits for the stream): candidates
  * whose distance it computed since the previous call (then reset to 0). */
 hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated);

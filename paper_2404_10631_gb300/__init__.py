@@ -35,7 +35,7 @@ HSC_SVM_COUPLE_F64 = 2
 EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_error",
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
             "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
-            "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics",
+            "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics", "hsc_measure_fma_rate",
             "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics",
             "hsc_classify_batch", "hsc_server_create", "hsc_server_submit",
             "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy")
@@ -139,6 +139,7 @@ def lib():
         L.hsc_pca_covariance.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp]
         L.hsc_pca_one_band_noalloc.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_profile_enable.argtypes = [vp, i32]
+        L.hsc_measure_fma_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int64),
@@ -272,6 +273,15 @@ class Context:
     @property
     def scratch_bytes(self) -> int:
         return int(lib().hsc_scratch_bytes(self.handle))
+
+
+def hsc_measure_fma_rate(device: int = 0, fp64: bool = False) -> float:
+    """FP32 (or FP64) multiply-add lane-operations per second over all SMs."""
+    r = ctypes.c_double(0.0)
+    st = lib().hsc_measure_fma_rate(device, 1 if fp64 else 0, ctypes.byref(r))
+    if st:
+        raise HscError(st, "hsc_measure_fma_rate: " + _status_name(st))
+    return r.value
 
 
 def hsc_pca_one_band(ctx: Context, cube, flags: int = HSC_PCA_MINMAX, one_band=None,
