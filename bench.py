@@ -401,8 +401,15 @@ def run_ours(args, f):
         hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam, out_probs=O, labels=lab,
                            search=hsc.HSC_KNN_SEARCH_FULL)
     full_ms, _, _ = ctx.profile_read()
+    # the paper's heap selection (partial heapsort) on the same maps: an A/B point
+    n_heap = min(args.steps, 3)
+    for i in range(n_heap):
+        hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam, out_probs=O, labels=lab,
+                           search=hsc.HSC_KNN_SEARCH_HEAP)
+    heap_ms, _, _ = ctx.profile_read()
     ctx.profile(False)
     full_ms_launch = full_ms["knn"] / args.steps
+    heap_ms_launch = heap_ms["knn"] / n_heap
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     elapsed = ev[0].elapsed_time(ev[args.steps])
     t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
@@ -498,6 +505,9 @@ def run_ours(args, f):
                 "work_per_launch": full_ops,
                 "traffic": traffic_from_profiles("knn"),
                 "note": "same neighbour sets as the pruned walk used in the step"}
+    knn_heap = {"search": "heap selection (the paper's partial heapsort: every window candidate "
+                          "keyed, the K smallest kept in a max-heap)", "ms_per_launch": heap_ms_launch,
+                "note": "same neighbour sets as the other searches; an A/B point, not the step"}
     knn_pruned = {"search": "pruned walk (exact)", "candidates_per_launch": knn_evals_per_launch,
                   "window_pairs_per_launch": knn_pairs(H, W, f.window_rows),
                   "ms_per_launch": stages["knn"]["ms_per_launch"],
@@ -515,6 +525,7 @@ def run_ours(args, f):
             "stages": stages,
             "knn_full_window": knn_full,
             "knn_pruned": knn_pruned,
+            "knn_heap": knn_heap,
             "batch": batch,
             "serving": serving,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

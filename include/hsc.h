@@ -74,11 +74,14 @@ typedef struct {
  *               row r, truncated at the image edges, all columns (the paper
  *               uses 14); the pixel itself is a candidate
  *   lambda      >= 0: d = (I_p - I_q)^2 + lambda^2 ((r-i)^2 + (c-j)^2)
- *   search      how the K nearest are found; both give the same neighbour sets:
+ *   search      how the K nearest are found; all give the same neighbour sets:
  *               HSC_KNN_SEARCH_FULL evaluates every window candidate (the
- *               paper's procedure); HSC_KNN_SEARCH_PRUNED walks only the
- *               candidates whose spatial term alone does not exceed a proven
- *               bound on the K-th distance (needs lambda > 0);
+ *               paper's procedure) against a running bound; HSC_KNN_SEARCH_PRUNED
+ *               walks only the candidates whose spatial term alone does not
+ *               exceed a proven bound on the K-th distance (needs lambda > 0);
+ *               HSC_KNN_SEARCH_HEAP keys every window candidate and keeps the
+ *               K smallest in a max-heap (the paper's partial heapsort,
+ *               Section III.B.3 a; an A/B point, slower);
  *               HSC_KNN_SEARCH_AUTO (0) = PRUNED when lambda > 0, else FULL.
  * Distance ties are broken by the smaller linear index; K must not exceed the
  * smallest window, min(ceil(R/2), H) * W, or the call returns
@@ -93,6 +96,7 @@ typedef struct {
 #define HSC_KNN_SEARCH_AUTO 0
 #define HSC_KNN_SEARCH_FULL 1
 #define HSC_KNN_SEARCH_PRUNED 2
+#define HSC_KNN_SEARCH_HEAP 3
 
 #define HSC_MAX_CLASSES 8
 #define HSC_MAX_K 64
@@ -105,6 +109,16 @@ typedef struct {
 #define HSC_COV_FP32_PIPE 4u     /* compute the Gram on the FP32 pipe instead of the tensor cores */
 /* flags for hsc_svm_probs / hsc_classify */
 #define HSC_SVM_COUPLE_F64 2u    /* solve the per-pixel coupling system in FP64 */
+/* flag for hsc_classify / hsc_classify_batch / server requests: the KNN runs
+ * on the raw projection I instead of (I - min I)/(max I - min I) (a method
+ * variant; one_band then receives the raw I) */
+#define HSC_CLASSIFY_RAW_I 16u
+/* flag for hsc_pca_one_band / hsc_classify: the cube is pixel-interleaved
+ * (BIP: H x W x B, the B bands of a pixel contiguous) instead of band-
+ * sequential (B x H x W); it is transposed on the device into the context's
+ * scratch (4 B H W more bytes; the copy is timed with the moments stage) and
+ * the results equal those of the band-sequential call */
+#define HSC_CUBE_BIP 32u
 
 /* Create a context on `device`. cuda_stream: a cudaStream_t to launch on, or
  * NULL for a new stream owned by the context. scratch_cap_bytes: upper bound
@@ -135,6 +149,7 @@ size_t hsc_scratch_bytes(const hsc_ctx *ctx);
  *   cube     B x H x W float32 (device)
  *   flags    HSC_PCA_MINMAX: one_band = (I - min I)/(max I - min I), or all
  *            zeros when I is constant; otherwise the raw projection I.
+ *            HSC_CUBE_BIP: the cube is H x W x B (see the flag).
  *   one_band H x W float32 (device, required)
  *   eigvec   B float64 (device, nullable): leading eigenvector v1
  *   eigval   1 float64 (device, nullable): its eigenvalue lambda1 */
@@ -188,7 +203,7 @@ hsc_status hsc_knn_filter(hsc_ctx *ctx, const float *one_band, const float *prob
  *   out_probs k x H x W float32 (device, nullable): O
  *   one_band  H x W float32 (device, nullable): the normalised one-band image
  *   probs     k x H x W float32 (device, nullable): the SVM maps P
- *   flags     0 or HSC_SVM_COUPLE_F64 */
+ *   flags     0, HSC_SVM_COUPLE_F64, HSC_CLASSIFY_RAW_I, HSC_CUBE_BIP (combinable) */
 hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                         const hsc_svm_model *model, const hsc_knn_params *params,
                         unsigned flags, int32_t *labels, float *out_probs,

@@ -31,6 +31,8 @@ HSC_MAX_WINDOW_ROWS = 32
 HSC_MAX_BANDS = 1024
 HSC_PCA_MINMAX = 1
 HSC_SVM_COUPLE_F64 = 2
+HSC_CLASSIFY_RAW_I = 16
+HSC_CUBE_BIP = 32
 
 EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_error",
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
@@ -59,6 +61,7 @@ class hsc_knn_params(ctypes.Structure):
 HSC_KNN_SEARCH_AUTO = 0
 HSC_KNN_SEARCH_FULL = 1
 HSC_KNN_SEARCH_PRUNED = 2
+HSC_KNN_SEARCH_HEAP = 3
 
 
 class hsc_frame(ctypes.Structure):
@@ -275,6 +278,14 @@ class Context:
         return int(lib().hsc_scratch_bytes(self.handle))
 
 
+def _bhw(cube, flags):
+    """(B, H, W) of a band-sequential cube, or of a pixel-interleaved one."""
+    if flags & HSC_CUBE_BIP:
+        H, W, B = cube.shape
+        return B, H, W
+    return tuple(cube.shape)
+
+
 def hsc_measure_fma_rate(device: int = 0, fp64: bool = False) -> float:
     """FP32 (or FP64) multiply-add lane-operations per second over all SMs."""
     r = ctypes.c_double(0.0)
@@ -286,9 +297,10 @@ def hsc_measure_fma_rate(device: int = 0, fp64: bool = False) -> float:
 
 def hsc_pca_one_band(ctx: Context, cube, flags: int = HSC_PCA_MINMAX, one_band=None,
                      eigvec=None, eigval=None):
-    """Returns the H x W one-band image (allocated when not given)."""
+    """Returns the H x W one-band image (allocated when not given). With
+    HSC_CUBE_BIP the cube is H x W x B."""
     import torch
-    B, H, W = cube.shape
+    B, H, W = _bhw(cube, flags)
     if one_band is None:
         one_band = torch.empty((H, W), dtype=torch.float32, device=cube.device)
     ctx.check(lib().hsc_pca_one_band(ctx.handle, _ptr(cube), B, H, W, flags, _ptr(one_band),
@@ -357,7 +369,7 @@ def hsc_classify(ctx: Context, cube, model: Model, K: int, window_rows: int, lam
                  flags: int = 0, labels=None, out_probs=None, one_band=None, probs=None,
                  search: int = HSC_KNN_SEARCH_AUTO):
     import torch
-    B, H, W = cube.shape
+    B, H, W = _bhw(cube, flags)
     if labels is None:
         labels = torch.empty((H, W), dtype=torch.int32, device=cube.device)
     ms = model.struct()

@@ -111,12 +111,12 @@ hsc_status cuda_fail(hsc_ctx *ctx, cudaError_t e, const char *where)
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, total;
+    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, bsq, total;
     int n_part;
 };
 
 Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool need_I,
-                   bool need_P)
+                   bool need_P, bool need_bsq = false)
 {
     Layout L{};
     size_t off = 0;
@@ -152,6 +152,7 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
     }
     if (need_I) L.tmpI = take(sizeof(float) * (size_t)N);
     if (need_P) L.tmpP = take(sizeof(float) * (size_t)k * N);
+    if (need_bsq) L.bsq = take(sizeof(float) * (size_t)B * N);  // band-sequential copy of a BIP cube
     L.total = off;
     return L;
 }
@@ -260,7 +261,7 @@ hsc_status check_knn(hsc_ctx *ctx, const hsc_knn_params *p, int n_classes, int H
         return fail(ctx, HSC_ERR_UNSUPPORTED, "KNN: window_rows exceeds HSC_MAX_WINDOW_ROWS%s");
     if (!(p->lambda >= 0.f) || !isfinite(p->lambda) || p->lambda > 1e6f)
         return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: lambda must be finite, >= 0 and <= 1e6%s");
-    if (p->search < HSC_KNN_SEARCH_AUTO || p->search > HSC_KNN_SEARCH_PRUNED)
+    if (p->search < HSC_KNN_SEARCH_AUTO || p->search > HSC_KNN_SEARCH_HEAP)
         return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: unknown search mode%s");
     if (p->search == HSC_KNN_SEARCH_PRUNED && !(p->lambda > 0.f))
         return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: the pruned search needs lambda > 0%s");
@@ -299,7 +300,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
                                     (flags & HSC_SVM_COUPLE_F64) != 0, Pm, nullptr, s.ctl,
                                     ctx->sm_count, st);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !(flags & HSC_CLASSIFY_RAW_I)) {
         StageTimer t(tc, HSC_STAGE_NORMALIZE, 1, st);
         e = hsc::launch_normalize(I, I, N, s.ctl, st);
     }
@@ -307,7 +308,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
         StageTimer t(tc, HSC_STAGE_KNN, 2, st);
         e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
                             out_probs, labels, nullptr, s.ctl, st,
-                            params->search != HSC_KNN_SEARCH_FULL);
+                            params->search);
     }
     return e;
 }
@@ -544,13 +545,21 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     if (st) return st;
     if ((st = check_cube(ctx, cube, B, H, W))) return st;
     if (!one_band) return fail(ctx, HSC_ERR_INVALID_ARG, "one_band is NULL%s");
-    if (flags & ~(unsigned)HSC_PCA_MINMAX) return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
+    if (flags & ~(unsigned)(HSC_PCA_MINMAX | HSC_CUBE_BIP))
+        return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     const long N = (long)H * W;
-    Layout L = make_layout(ctx, B, N, 0, true, false, false);
+    const bool bip = (flags & HSC_CUBE_BIP) != 0;
+    Layout L = make_layout(ctx, B, N, 0, true, false, false, bip);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
-    cudaError_t e;
-    {
+    cudaError_t e = cudaSuccess;
+    if (bip) {
+        float *bsq = reinterpret_cast<float *>(static_cast<char *>(ctx->scratch) + L.bsq);
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, 1);
+        e = hsc::launch_bip_to_bsq(cube, B, N, bsq, ctx->stream);
+        cube = bsq;
+    }
+    if (e == cudaSuccess) {
         StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
         e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
     }
@@ -638,7 +647,7 @@ hsc_status hsc_knn_filter(hsc_ctx *ctx, const float *one_band, const float *prob
     StageTimer t(ctx, HSC_STAGE_KNN, 1);
     cudaError_t e = hsc::launch_knn(one_band, probs, n_classes, H, W, params->k,
                                     params->window_rows, params->lambda, out_probs, labels, nbr_idx,
-                                    s.ctl, ctx->stream, params->search != HSC_KNN_SEARCH_FULL);
+                                    s.ctl, ctx->stream, params->search);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_knn_filter launch");
     return HSC_OK;
 }
@@ -653,17 +662,27 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     if ((st = check_model(ctx, model, B))) return st;
     if ((st = check_knn(ctx, params, model->n_classes, H, W))) return st;
     if (!labels) return fail(ctx, HSC_ERR_INVALID_ARG, "labels is NULL%s");
-    if (flags & ~(unsigned)HSC_SVM_COUPLE_F64) return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
+    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_CLASSIFY_RAW_I | HSC_CUBE_BIP))
+        return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     const long N = (long)H * W;
     const int k = model->n_classes;
-    Layout L = make_layout(ctx, B, N, k, true, one_band == nullptr, probs == nullptr);
+    const bool bip = (flags & HSC_CUBE_BIP) != 0;
+    Layout L = make_layout(ctx, B, N, k, true, one_band == nullptr, probs == nullptr, bip);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
     char *base = static_cast<char *>(ctx->scratch);
     float *I = one_band ? one_band : reinterpret_cast<float *>(base + L.tmpI);
     float *Pm = probs ? probs : reinterpret_cast<float *>(base + L.tmpP);
-    cudaError_t e = launch_classify_frame(ctx, s, cube, B, H, W, model, params, flags, labels,
-                                          out_probs, I, Pm, ctx->stream, true);
+    cudaError_t e = cudaSuccess;
+    if (bip) {  // timed with the moments stage
+        float *bsq = reinterpret_cast<float *>(base + L.bsq);
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, 1);
+        e = hsc::launch_bip_to_bsq(cube, B, N, bsq, ctx->stream);
+        cube = bsq;
+    }
+    if (e == cudaSuccess)
+        e = launch_classify_frame(ctx, s, cube, B, H, W, model, params, flags, labels, out_probs, I,
+                                  Pm, ctx->stream, true);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_classify launch");
     return HSC_OK;
 }
@@ -676,7 +695,7 @@ hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frame
     hsc_status st = check_ctx(ctx);
     if (st) return st;
     if (!frames || n_frames < 1) return fail(ctx, HSC_ERR_INVALID_ARG, "no frames%s");
-    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_BATCH_GRAPH))
+    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_BATCH_GRAPH | HSC_CLASSIFY_RAW_I))
         return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     if ((st = check_model(ctx, model, B))) return st;
     const int k = model->n_classes;
@@ -1090,7 +1109,7 @@ hsc_status hsc_server_submit(hsc_server *srv, const hsc_request *req, uint64_t *
     if ((st = check_model(c, &req->model, req->B))) return st;
     if ((st = check_knn(c, &req->params, req->model.n_classes, req->H, req->W))) return st;
     if (!req->labels) return HSC_ERR_INVALID_ARG;
-    if (req->flags & ~(unsigned)HSC_SVM_COUPLE_F64) return HSC_ERR_INVALID_ARG;
+    if (req->flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_CLASSIFY_RAW_I)) return HSC_ERR_INVALID_ARG;
     auto q = std::make_shared<ServerReq>();
     q->req = *req;
     q->bytes = request_layout(srv, *req).total;

@@ -97,13 +97,18 @@ cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,
                              cudaStream_t st);
 
-// KNN filter (Eq. 1, Eq. 2) over all pixels: the full-window scan, or (pruned
-// and lambda > 0) the exact spatially pruned walk; both select the same sets.
+// Pixel-interleaved cube (N pixels x B bands, bands contiguous) -> band-
+// sequential (B x N) copy.
+cudaError_t launch_bip_to_bsq(const float *bip, int B, long N, float *bsq, cudaStream_t st);
+
+// KNN filter (Eq. 1, Eq. 2) over all pixels; search (HSC_KNN_SEARCH_*): the
+// full-window scan, the exact spatially pruned walk (AUTO or PRUNED with
+// lambda > 0), or the heap selection; all select the same sets.
 // Uploads the pruned walk's offset table to the current device (once).
 cudaError_t knn_init(int device);
 
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr,
-                       Control *ctl, cudaStream_t st, bool pruned);
+                       Control *ctl, cudaStream_t st, int search);
 
 }  // namespace hsc

@@ -283,6 +283,90 @@ knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int 
     (void)lane;
 }
 
+// ---- the paper's heap selection (Section III.B.3 a): a partial heapsort in
+// an online setting, built as an A/B point of the same search. Every window
+// candidate is keyed exactly (make_key: the TwoSum pair and the index, the
+// same total order as above); the first K are made a max-heap (heapify), and
+// every later candidate below the root replaces it and is sifted down:
+// O(n log K) per pixel over the n window candidates. It selects the same K
+// as the other two searches. One lane per pixel, 128 pixels of a row per CTA,
+// the window rows staged in shared memory as in knn_kernel; the heap lives
+// in the lane's local memory (it is indexed at run time).
+constexpr int kHeapThreads = 128;
+
+__device__ __forceinline__ void heap_sift_down(Key *h, int i, int K)
+{
+    for (;;) {
+        const int l = 2 * i + 1;
+        if (l >= K) return;
+        const int m = (l + 1 < K && key_lt(h[l], h[l + 1])) ? l + 1 : l;
+        if (!key_lt(h[i], h[m])) return;
+        const Key t = h[i];
+        h[i] = h[m];
+        h[m] = t;
+        i = m;
+    }
+}
+
+__global__ void __launch_bounds__(kHeapThreads)
+knn_heap_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int H, int W,
+                int K, int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
+                int32_t *__restrict__ nbr, Control *ctl)
+{
+    extern __shared__ float win[];  // [rows][kStride]
+    const int r = blockIdx.y;
+    const int c = blockIdx.x * kHeapThreads + threadIdx.x;
+    const bool active = c < W;
+    const int lo_r = max(0, r - R / 2);
+    const int hi_r = min(H - 1, r + (R + 1) / 2 - 1);
+    const int nrows = hi_r - lo_r + 1;
+    const float l2 = lam * lam;
+    const long N = (long)H * W;
+    const float Ip = active ? I[(long)r * W + c] : 0.f;
+    Key heap[HSC_MAX_K];
+    Key root;
+    root.hi = INFINITY;
+    root.lo = 0.f;
+    root.q = 0x7fffffff;
+    int n = 0;
+    bool bad = false;
+    for (int c0 = 0; c0 < W; c0 += kChunk) {
+        const int cw = min(kChunk, W - c0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nrows * cw; idx += kHeapThreads) {
+            const int ii = idx / cw, jj = idx - ii * cw;
+            const float v = I[(long)(lo_r + ii) * W + c0 + jj];
+            bad |= !isfinite(v);
+            win[ii * kStride + jj] = v;
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int ii = 0; ii < nrows; ++ii) {
+            const int dr = lo_r + ii - r;
+            const int rowq = (lo_r + ii) * W;
+            for (int jj = 0; jj < cw; ++jj) {
+                const int j = c0 + jj;
+                const Key kk = make_key(Ip, win[ii * kStride + jj], dr, c - j, l2, rowq + j);
+                if (n < K) {
+                    heap[n++] = kk;
+                    if (n == K) {  // heapify the first K
+                        for (int i = K / 2 - 1; i >= 0; --i) heap_sift_down(heap, i, K);
+                        root = heap[0];
+                    }
+                } else if (key_lt(kk, root)) {
+                    heap[0] = kk;
+                    heap_sift_down(heap, 0, K);
+                    root = heap[0];
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_MAP);
+    if (!active) return;
+    if (n < K) atomicOr(&ctl->status, ST_KNN_SHORT);
+    finish_pixel(heap, n, K, P, k, N, (long)r * W + c, O, labels, nbr);
+}
+
 // ---- exact, spatially pruned variant (lambda > 0)
 //
 // Every key is at least s_term = fl(lambda^2 (dr^2 + dc^2)), which grows with
@@ -845,8 +929,20 @@ cudaError_t knn_init(int device)
 
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr, Control *ctl,
-                       cudaStream_t st, bool pruned)
+                       cudaStream_t st, int search)
 {
+    if (search == HSC_KNN_SEARCH_HEAP) {
+        const int nrows_max = R < H ? R : H;
+        const size_t smem = sizeof(float) * (size_t)nrows_max * kStride;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(knn_heap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        dim3 grid((W + kHeapThreads - 1) / kHeapThreads, H);
+        knn_heap_kernel<<<grid, kHeapThreads, smem, st>>>(I, P, k, H, W, K, R, lambda, O, labels,
+                                                          nbr, ctl);
+        return cudaGetLastError();
+    }
+    const bool pruned = search != HSC_KNN_SEARCH_FULL;
     if (pruned && lambda > 0.f) {
         switch (k) {
         case 1: return launch_pruned<1>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);

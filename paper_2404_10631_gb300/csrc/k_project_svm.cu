@@ -294,4 +294,42 @@ cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control 
     return cudaGetLastError();
 }
 
+// ---- pixel-interleaved (BIP, H x W x B) input: one tiled transpose into the
+// band-sequential layout the other kernels read. 32 x 32 tiles through shared
+// memory (one padded column against bank conflicts): reads coalesced along
+// the bands of a pixel, writes along the pixels of a band. Two cube-sized HBM
+// passes (read + write).
+namespace {
+constexpr int kTile = 32, kTileRows = 8;
+
+__global__ void __launch_bounds__(kTile * kTileRows)
+bip_to_bsq_kernel(const float *__restrict__ in, int B, long N, float *__restrict__ out)
+{
+    __shared__ float t[kTile][kTile + 1];
+    const long p0 = (long)blockIdx.x * kTile;
+    const int b0 = blockIdx.y * kTile;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < kTile; i += kTileRows) {
+        const long p = p0 + ty + i;
+        const int b = b0 + tx;
+        if (p < N && b < B) t[ty + i][tx] = in[p * B + b];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kTile; i += kTileRows) {
+        const int b = b0 + ty + i;
+        const long p = p0 + tx;
+        if (p < N && b < B) out[(size_t)b * (size_t)N + p] = t[tx][ty + i];
+    }
+}
+}  // namespace
+
+cudaError_t launch_bip_to_bsq(const float *bip, int B, long N, float *bsq, cudaStream_t st)
+{
+    dim3 grid((unsigned)((N + kTile - 1) / kTile), (unsigned)((B + kTile - 1) / kTile));
+    bip_to_bsq_kernel<<<grid, dim3(kTile, kTileRows), 0, st>>>(bip, B, N, bsq);
+    return cudaGetLastError();
+}
+
 }  // namespace hsc

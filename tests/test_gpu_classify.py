@@ -98,3 +98,47 @@ def test_classify_without_optional_outputs(hsc, ctx):
     lab = hsc.hsc_classify(ctx, c, m, f.K, f.window_rows, f.lam)
     ctx.sync()
     np.testing.assert_array_equal(lab.cpu().numpy(), lab_ref)
+
+
+def test_classify_on_raw_one_band(hsc, ctx):
+    """Method variant HSC_CLASSIFY_RAW_I: the KNN runs on the raw projection I
+    (no min-max). one_band is that I, and labels and O equal the oracle's KNN
+    on the same map (selection on the float terms of Eq. 1, as the kernels)."""
+    f = synth.make_config(1)
+    lab, O, I, P = gpu_classify(hsc, ctx, f, flags=hsc.HSC_CLASSIFY_RAW_I)
+    ref = oracle.pca_one_band(f.cube)
+    assert np.abs(I - ref["I_raw"]).max() < 2e-5 * max(1.0, np.abs(ref["I_raw"]).max())
+    k = f.model.n_classes
+    out = oracle.knn(I, P, f.K, f.window_rows, f.lam, 0, I.size, float_keys=True)
+    clear = out["gapO"] > 2e-5
+    np.testing.assert_array_equal(lab.reshape(-1)[clear], out["labels"][clear])
+    assert np.abs(O.reshape(k, -1) - out["O"]).max() < 1e-5
+    # and it differs from the normalised form (the map's scale enters Eq. 1)
+    lab_n, _, I_n, _ = gpu_classify(hsc, ctx, f)
+    assert not np.allclose(I, I_n)
+
+
+def test_bip_cube_equals_band_sequential(hsc, ctx):
+    """Method variant HSC_CUBE_BIP: the same frame stored pixel-interleaved
+    (H x W x B) gives results identical, bit for bit, to the band-sequential
+    call (the cube is transposed on the device, then the same kernels run);
+    the PCA entry point likewise. Ragged sizes (not multiples of the 32 x 32
+    transpose tile)."""
+    import torch
+    f = synth.make_frame(11, 45, 37, 70, sigma=0.02)
+    B, H, W = f.cube.shape
+    k = f.model.n_classes
+    m = hsc.Model.from_host(f.model)
+    bsq = torch.as_tensor(f.cube, device="cuda")
+    bip = torch.as_tensor(np.ascontiguousarray(np.transpose(f.cube, (1, 2, 0))), device="cuda")
+    outs = []
+    for cube, flags in ((bsq, 0), (bip, hsc.HSC_CUBE_BIP)):
+        I = torch.empty((H, W), device="cuda")
+        O = torch.empty((k, H, W), device="cuda")
+        lab = hsc.hsc_classify(ctx, cube, m, f.K, f.window_rows, f.lam, flags=flags, out_probs=O,
+                               one_band=I)
+        I2 = hsc.hsc_pca_one_band(ctx, cube, flags=hsc.HSC_PCA_MINMAX | flags)
+        ctx.sync()
+        outs.append([t.cpu().numpy() for t in (lab, O, I, I2)])
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)

@@ -15,7 +15,7 @@ from parity import check_knn, sample_rows
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-SEARCHES = [1, 2]  # full-window scan, pruned walk
+SEARCHES = [1, 2, 3]  # full-window scan, pruned walk, heap selection
 
 
 def run_knn(hsc, ctx, I, P, K, R, lam, search=1):
@@ -135,17 +135,19 @@ def test_neuro_size_sampled_rows(hsc, ctx, search):
     assert st["pixels"] == 8 * W
 
 
-def test_pruned_equals_full_window(hsc, ctx):
-    """Both searches select the same sets: identical outputs bit for bit."""
+def test_pruned_and_heap_equal_full_window(hsc, ctx):
+    """All three searches select the same sets: identical outputs bit for bit
+    (neighbour lists nearest first, so O sums in the same order)."""
     f = synth.make_config(2)
     pca = oracle.pca_one_band(f.cube)
     P, _, _ = oracle.svm_probs(f.cube, f.model)
     I32 = pca["I_norm"].astype(np.float32)
     P32 = P.astype(np.float32)
     a = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0, 1)
-    b = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0, 2)
-    for x, y in zip(a, b):
-        np.testing.assert_array_equal(x, y)
+    for search in (2, 3):
+        b = run_knn(hsc, ctx, I32, P32, 40, 14, 1.0, search)
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x, y)
 
 
 def test_pruned_search_rejects_lambda_zero(hsc, ctx):
