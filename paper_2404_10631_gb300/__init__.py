@@ -38,6 +38,7 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
             "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
             "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics", "hsc_measure_fma_rate",
+            "hsc_autotune", "hsc_set_tuning",
             "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics",
             "hsc_classify_batch", "hsc_server_create", "hsc_server_submit",
             "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy")
@@ -143,6 +144,9 @@ def lib():
         L.hsc_pca_one_band_noalloc.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_profile_enable.argtypes = [vp, i32]
         L.hsc_measure_fma_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
+        L.hsc_autotune.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
+                                   ctypes.POINTER(ctypes.c_int32)]
+        L.hsc_set_tuning.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32)]
         L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int64),
@@ -272,6 +276,24 @@ class Context:
         v = ctypes.c_int64(0)
         self.check(lib().hsc_knn_diagnostics(self.handle, ctypes.byref(v)))
         return int(v.value)
+
+    def autotune(self, cube, model) -> dict:
+        """Times the launch-shape candidates on this cube (B x H x W) and keeps
+        the fastest for frames of its shape; returns the chosen parameters."""
+        B, H, W = cube.shape
+        cfg = (ctypes.c_int32 * 3)()
+        ms = model.struct()
+        self.check(lib().hsc_autotune(self.handle, _ptr(cube), B, H, W, ctypes.byref(ms), cfg))
+        return {"gram_stages": cfg[0], "svm_px": cfg[1], "svm_blocks_per_sm": cfg[2]}
+
+    def set_tuning(self, B, H, W, n_classes, config=None):
+        """Sets (gram_stages, svm_px, svm_blocks_per_sm) for that frame shape, or
+        clears the tuning (config None)."""
+        if config is None:
+            self.check(lib().hsc_set_tuning(self.handle, B, H, W, n_classes, None))
+            return
+        cfg = (ctypes.c_int32 * 3)(*config)
+        self.check(lib().hsc_set_tuning(self.handle, B, H, W, n_classes, cfg))
 
     @property
     def scratch_bytes(self) -> int:

@@ -51,6 +51,12 @@ struct hsc_ctx {
     // cached CUDA graph of the last graph-mode batch and its signature
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<long long> batch_sig;
+    // autotuned launch parameters and the frame shape (B, N, k) they were
+    // chosen for; other shapes use the defaults
+    bool tuned = false;
+    int tune_B = 0, tune_k = 0;
+    long tune_N = 0;
+    hsc::Tuning tune;
 };
 
 namespace {
@@ -276,6 +282,13 @@ hsc_status check_knn(hsc_ctx *ctx, const hsc_knn_params *p, int n_classes, int H
 constexpr int kMaxSlots = 64;
 
 // The whole path for one frame on one stream with one scratch carve-up.
+// The tuned launch parameters when they were chosen for this frame shape.
+hsc::Tuning tuning_for(const hsc_ctx *ctx, int B, long N, int k)
+{
+    if (ctx->tuned && ctx->tune_B == B && ctx->tune_N == N && ctx->tune_k == k) return ctx->tune;
+    return hsc::Tuning{};
+}
+
 cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float *cube, int B,
                                   int H, int W, const hsc_svm_model *model,
                                   const hsc_knn_params *params, unsigned flags, int32_t *labels,
@@ -285,10 +298,11 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
     const long N = (long)H * W;
     const int k = model->n_classes;
     hsc_ctx *tc = timed ? ctx : &g_untimed;
+    const hsc::Tuning tu = tuning_for(ctx, B, N, k);
     cudaError_t e;
     {
         StageTimer t(tc, HSC_STAGE_MOMENTS, 4, st);
-        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, st);
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, st, false, tu.gram_stages);
     }
     if (e == cudaSuccess) {
         StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);
@@ -298,7 +312,8 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
         StageTimer t(tc, HSC_STAGE_PROJECT_SVM, 1, st);
         e = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model,
                                     (flags & HSC_SVM_COUPLE_F64) != 0, Pm, nullptr, s.ctl,
-                                    ctx->sm_count, st);
+                                    ctx->sm_count, st, tu.svm_blocks_per_sm * ctx->sm_count,
+                                    tu.svm_px);
     }
     if (e == cudaSuccess && !(flags & HSC_CLASSIFY_RAW_I)) {
         StageTimer t(tc, HSC_STAGE_NORMALIZE, 1, st);
@@ -380,6 +395,111 @@ hsc_status hsc_profile_enable(hsc_ctx *ctx, int enable)
         }
     }
     ctx->profiling = enable != 0 && ctx->ev != nullptr;
+    return HSC_OK;
+}
+
+hsc_status hsc_set_tuning(hsc_ctx *ctx, int B, int H, int W, int n_classes,
+                          const int32_t *config)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if (!config) {
+        ctx->tuned = false;
+        return HSC_OK;
+    }
+    if (B < 1 || H < 1 || W < 1 || n_classes < 1)
+        return fail(ctx, HSC_ERR_INVALID_ARG, "hsc_set_tuning: sizes must be >= 1%s");
+    if ((config[0] != 0 && config[0] != 3 && config[0] != 4) ||
+        (config[1] != 0 && config[1] != 1 && config[1] != 4) || config[2] < 0 || config[2] > 64)
+        return fail(ctx, HSC_ERR_INVALID_ARG, "hsc_set_tuning: value out of range%s");
+    ctx->tuned = true;
+    ctx->tune_B = B;
+    ctx->tune_N = (long)H * W;
+    ctx->tune_k = n_classes;
+    ctx->tune.gram_stages = config[0];
+    ctx->tune.svm_px = config[1];
+    ctx->tune.svm_blocks_per_sm = config[2];
+    return HSC_OK;
+}
+
+hsc_status hsc_autotune(hsc_ctx *ctx, const float *cube, int B, int H, int W,
+                        const hsc_svm_model *model, int32_t *config)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if ((st = check_cube(ctx, cube, B, H, W))) return st;
+    if ((st = check_model(ctx, model, B))) return st;
+    const long N = (long)H * W;
+    const int k = model->n_classes;
+    Layout L = make_layout(ctx, B, N, k, true, true, true);
+    if ((st = ensure_scratch(ctx, L.total))) return st;
+    PcaScratch s = carve(ctx, L);
+    char *base = static_cast<char *>(ctx->scratch);
+    float *I = reinterpret_cast<float *>(base + L.tmpI);
+    float *Pm = reinterpret_cast<float *>(base + L.tmpP);
+    cudaStream_t str = ctx->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    // median of three timed runs after one untimed run
+    auto time_ms = [&](auto &&launch) -> float {
+        float t[3] = {0.f, 0.f, 0.f};
+        if (err == cudaSuccess) err = launch();
+        for (int i = 0; i < 3 && err == cudaSuccess; ++i) {
+            cudaEventRecord(e0, str);
+            err = launch();
+            cudaEventRecord(e1, str);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&t[i], e0, e1);
+        }
+        std::sort(t, t + 3);
+        return t[1];
+    };
+    hsc::Tuning best;
+    // the tensor-core Gram's staging depth (B <= 128 form)
+    if (B <= 128 && hsc::gram_tc_supported(cube, B, N)) {
+        float bt = 1e30f;
+        for (int stg : {3, 4}) {
+            const float t = time_ms([&] {
+                return hsc::launch_moments(cube, B, N, s, ctx->sm_count, str, false, stg);
+            });
+            if (t < bt) {
+                bt = t;
+                best.gram_stages = stg;
+            }
+        }
+    }
+    // v1 for the projection pass
+    if (err == cudaSuccess) err = hsc::launch_moments(cube, B, N, s, ctx->sm_count, str);
+    if (err == cudaSuccess) err = hsc::launch_jacobi(B, s, str);
+    // projection + SVM: pixels per thread x CTAs per SM of the grid-stride launch
+    float bt = 1e30f;
+    for (int px : {1, 4})
+        for (int bps : {2, 4, 8, 16}) {
+            const float t = time_ms([&] {
+                return hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model, false, Pm,
+                                               nullptr, s.ctl, ctx->sm_count, str,
+                                               bps * ctx->sm_count, px);
+            });
+            if (t < bt) {
+                bt = t;
+                best.svm_px = px;
+                best.svm_blocks_per_sm = bps;
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(ctx, err, "hsc_autotune");
+    ctx->tuned = true;
+    ctx->tune_B = B;
+    ctx->tune_N = N;
+    ctx->tune_k = k;
+    ctx->tune = best;
+    if (config) {
+        config[0] = best.gram_stages;
+        config[1] = best.svm_px;
+        config[2] = best.svm_blocks_per_sm;
+    }
     return HSC_OK;
 }
 
@@ -559,9 +679,10 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
         e = hsc::launch_bip_to_bsq(cube, B, N, bsq, ctx->stream);
         cube = bsq;
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess) {  // the tuned Gram staging depth for frames of this size
+        const int stg = (ctx->tuned && ctx->tune_B == B && ctx->tune_N == N) ? ctx->tune.gram_stages : 0;
         StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
-        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream, false, stg);
     }
     if (e == cudaSuccess) {
         StageTimer t(ctx, HSC_STAGE_JACOBI, 1);

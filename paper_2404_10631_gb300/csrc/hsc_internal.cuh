@@ -76,11 +76,23 @@ struct PcaScratch {
 // C (covariance / N) and mu. Sets ST_NONFINITE_CUBE on NaN/Inf. The Gram runs
 // on the tensor cores (k_gram_tc.cu) when gram_tc_supported(), unless
 // force_simt; otherwise on the FP32 pipe.
+// Launch parameters that change only the speed of a pass, never its results
+// (an autotuner picks them per frame shape): the tensor-core Gram's TMA
+// staging depth (3 or 4; 0 = default), and the projection/SVM pass's pixels
+// per thread (1 or 4; 0 = 4 when the cube allows 16-byte loads) and CTAs per
+// SM of its grid-stride launch (0 = 8).
+struct Tuning {
+    int gram_stages = 0;
+    int svm_px = 0;
+    int svm_blocks_per_sm = 0;
+};
+
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s,
-                           int sm_count, cudaStream_t st, bool force_simt = false);
+                           int sm_count, cudaStream_t st, bool force_simt = false,
+                           int gram_stages = 0);
 bool gram_tc_supported(const float *cube, int B, long N);
 cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s,
-                           cudaStream_t st);
+                           cudaStream_t st, int stages = 0);
 
 // Jacobi eigen-decomposition of C, FP64 refinement of the leading vector,
 // sign rule; writes v1, lambda1, v1f, muf and resets the I min/max keys.
@@ -91,7 +103,8 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st);
 cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
                                const float *muf, float *I_raw, const hsc_svm_model *model,
                                bool couple_f64, float *probs, int32_t *svm_labels,
-                               Control *ctl, int sm_count, cudaStream_t st, int max_blocks = 0);
+                               Control *ctl, int sm_count, cudaStream_t st, int max_blocks = 0,
+                               int px = 0);
 
 // I_norm = (I - min)/(max - min) (0 if max == min), min/max from ctl keys.
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,

@@ -60,10 +60,10 @@ constexpr int kFbLd = kChunk + 1;        // FP32 recompute: padded staging row
 // hi.hi^T accumulators (columns 0, 128, 256) and the cross terms at 384, 8
 // converter warps. 128 < B <= 256: 256 rows, 2 + 1 stages, hi.hi^T at 0 and
 // cross at 256, 4 converter warps (one thread per band row and half).
-template <bool kWide>
+template <bool kWide, int kSt = (kWide ? 2 : 4)>
 struct Cfg {
     static constexpr int kRows = kWide ? 256 : 128;
-    static constexpr int kStages = kWide ? 2 : 4;
+    static constexpr int kStages = kSt;
     static constexpr int kOpStages = kWide ? 1 : 2;
     static constexpr int kAccHH = kWide ? 1 : 3;
     static constexpr int kConvWarps = kWide ? 4 : 8;
@@ -187,10 +187,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <bool kWide>
+template <bool kWide, int kSt>
 struct __align__(8) Bars {
-    uint64_t full[Cfg<kWide>::kStages], empty[Cfg<kWide>::kStages];
-    uint64_t op_full[Cfg<kWide>::kOpStages], op_empty[Cfg<kWide>::kOpStages];
+    uint64_t full[Cfg<kWide, kSt>::kStages], empty[Cfg<kWide, kSt>::kStages];
+    uint64_t op_full[Cfg<kWide, kSt>::kOpStages], op_empty[Cfg<kWide, kSt>::kOpStages];
     uint64_t done;     // a segment's MMAs have completed (one commit per segment)
     uint64_t drained;  // the epilogue has read a segment's accumulators (128 arrivals)
 };
@@ -233,14 +233,14 @@ __device__ __forceinline__ void convert_unit(const float4 xa, const float4 xb, f
 // Rows row_base..row_base+127 of this launch's block of G times columns
 // col_base..col_base+Nn-1 (Nn a multiple of 16); band sums when write_sums.
 // shift: 2B floats, the pilot shift s_b then the scale c_b of each band.
-template <bool kWide>
-__global__ void __launch_bounds__(Cfg<kWide>::kThreads, 1)
+template <bool kWide, int kSt>
+__global__ void __launch_bounds__(Cfg<kWide, kSt>::kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ cube, int B,
                int row_base, int col_base, int Nn, int write_sums, long N, long total_chunks,
                const float *__restrict__ shift, float *__restrict__ gram_part,
                float *__restrict__ sum_part, Control *ctl)
 {
-    using G = Cfg<kWide>;
+    using G = Cfg<kWide, kSt>;
     constexpr int kRows = G::kRows, kStages = G::kStages, kOpStages = G::kOpStages;
     constexpr int kAccHH = G::kAccHH, kThreads = G::kThreads, kParts = G::kParts;
     constexpr int kConv = 32 * G::kConvWarps;
@@ -251,7 +251,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *staging = base;                                 // kStages x 2 boxes
     unsigned char *ops = base + kStages * kStageBytes;             // kOpStages x (hi, lo)
-    __shared__ Bars<kWide> bars;
+    __shared__ Bars<kWide, kSt> bars;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, range_flag;
     __shared__ float sh[kRows], sc[kRows], isc[kRows];
@@ -608,7 +608,24 @@ bool gram_tc_supported(const float *cube, int B, long N)
 
 size_t gram_tc_smem_bytes() { return Cfg<false>::kSmem; }
 
-cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s, cudaStream_t st)
+namespace {
+template <int kSt>
+void launch_narrow(const CUtensorMap &map, const float *cube, int B, int Np, long N, long total,
+                   const PcaScratch &s, cudaStream_t st)
+{
+    const size_t smem = Cfg<false, kSt>::kSmem;
+    cudaFuncSetAttribute(gram_tc_kernel<false, kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    gram_tc_kernel<false, kSt><<<s.n_part, Cfg<false, kSt>::kThreads, smem, st>>>(
+        map, cube, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+}
+}  // namespace
+
+// stages: TMA staging depth of the B <= 128 form (3 or 4; 0 = 4). The result
+// does not depend on it (the same chunks reach the same accumulators in the
+// same order); only the overlap of loads and conversion does.
+cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s, cudaStream_t st,
+                           int stages)
 {
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)B};
@@ -623,20 +640,17 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
     const int Np = (B + 15) / 16 * 16;
     const long total = (N + kChunk - 1) / kChunk;
     if (B <= 128) {
-        const size_t smem = Cfg<false>::kSmem;
-        cudaFuncSetAttribute(gram_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        gram_tc_kernel<false><<<s.n_part, Cfg<false>::kThreads, smem, st>>>(
-            map, cube, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+        if (stages == 3) launch_narrow<3>(map, cube, B, Np, N, total, s, st);
+        else launch_narrow<4>(map, cube, B, Np, N, total, s, st);
         return cudaGetLastError();
     }
     const size_t smem = Cfg<true>::kSmem;
-    cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(gram_tc_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     // rows 0-127 x every column, then rows 128-255 x columns 128-255
-    gram_tc_kernel<true><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
+    gram_tc_kernel<true, 2><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
         map, cube, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
-    gram_tc_kernel<true><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
+    gram_tc_kernel<true, 2><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
         map, cube, B, 128, 128, Np - 128, 0, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
     return cudaGetLastError();
 }

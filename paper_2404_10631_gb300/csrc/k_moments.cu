@@ -277,13 +277,13 @@ static cudaError_t launch_reductions(int B, long N, int n_part, const PcaScratch
 }
 
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s, int sm_count,
-                           cudaStream_t st, bool force_simt)
+                           cudaStream_t st, bool force_simt, int gram_stages)
 {
     pilot_shift_kernel<<<B, 256, 0, st>>>(cube, B, N, s.shift, s.ctl);
     if (!force_simt && gram_tc_supported(cube, B, N)) {
         PcaScratch t = s;
         t.n_part = s.n_part < sm_count ? s.n_part : sm_count;  // one CTA per SM
-        cudaError_t e = launch_gram_tc(cube, B, N, t, st);
+        cudaError_t e = launch_gram_tc(cube, B, N, t, st, gram_stages);
         if (e != cudaSuccess) return e;
         return launch_reductions(B, N, t.n_part, s, st);
     }

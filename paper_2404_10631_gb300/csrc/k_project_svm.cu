@@ -274,10 +274,10 @@ cudaError_t dispatch_k(int k, const float *cube, int B, long N, const float *v1f
 cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
                                const float *muf, float *I_raw, const hsc_svm_model *model,
                                bool couple_f64, float *probs, int32_t *svm_labels, Control *ctl,
-                               int sm_count, cudaStream_t st, int max_blocks)
+                               int sm_count, cudaStream_t st, int max_blocks, int px)
 {
     const int k = (probs != nullptr && model != nullptr) ? model->n_classes : 0;
-    const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0);
+    const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0) && px != 1;
     if (vec)
         return dispatch_k<4>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs, svm_labels,
                              ctl, sm_count, st, max_blocks);

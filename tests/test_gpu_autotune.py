@@ -1,0 +1,62 @@
+"""hsc_autotune / hsc_set_tuning: the tuned launch parameters (Gram staging
+depth, projection/SVM pixels per thread and CTAs per SM) change speed only:
+every candidate gives outputs identical bit for bit to the defaults."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def classify(hsc, ctx, f, cube, m):
+    import torch
+    B, H, W = f.cube.shape
+    k = f.model.n_classes
+    I = torch.empty((H, W), device="cuda")
+    P = torch.empty((k, H, W), device="cuda")
+    O = torch.empty((k, H, W), device="cuda")
+    lab = hsc.hsc_classify(ctx, cube, m, f.K, f.window_rows, f.lam, out_probs=O, one_band=I,
+                           probs=P)
+    ctx.sync()
+    return [t.cpu().numpy() for t in (lab, O, I, P)]
+
+
+@pytest.mark.parametrize("shape", [(128, 64, 96), (125, 37, 41)])
+def test_every_candidate_gives_identical_outputs(hsc, ctx, shape):
+    import torch
+    B, H, W = shape
+    f = synth.make_frame(B + H, H, W, B, sigma=0.02)
+    cube = torch.as_tensor(f.cube, device="cuda")
+    m = hsc.Model.from_host(f.model)
+    k = f.model.n_classes
+    ctx.set_tuning(B, H, W, k, None)
+    ref = classify(hsc, ctx, f, cube, m)
+    for stg, px, bps in itertools.product((3, 4), (1, 4), (2, 16)):
+        ctx.set_tuning(B, H, W, k, (stg, px, bps))
+        out = classify(hsc, ctx, f, cube, m)
+        for a, b in zip(ref, out):
+            np.testing.assert_array_equal(a, b)
+    ctx.set_tuning(B, H, W, k, None)
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(hsc, ctx):
+    import torch
+    f = synth.make_config(2)
+    cube = torch.as_tensor(f.cube, device="cuda")
+    m = hsc.Model.from_host(f.model)
+    B, H, W = f.cube.shape
+    ctx.set_tuning(B, H, W, f.model.n_classes, None)
+    ref = classify(hsc, ctx, f, cube, m)
+    cfg = ctx.autotune(cube, m)
+    assert cfg["gram_stages"] in (3, 4)
+    assert cfg["svm_px"] in (1, 4) and cfg["svm_blocks_per_sm"] in (2, 4, 8, 16)
+    out = classify(hsc, ctx, f, cube, m)
+    for a, b in zip(ref, out):
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(hsc.HscError):
+        ctx.set_tuning(B, H, W, f.model.n_classes, (5, 1, 2))
+    ctx.set_tuning(B, H, W, f.model.n_classes, None)
