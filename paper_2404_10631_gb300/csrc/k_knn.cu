@@ -396,7 +396,7 @@ constexpr int kTabR2 = 400;            // table: dr^2 + dc^2 <= 400
 constexpr int kTabDr = 16;             // |dr| <= 16: windows of up to 32 rows
 constexpr int kTabDc = 20;             // |dc| <= 20 follows from kTabR2
 constexpr int kTabCap = 1200;
-constexpr int kBnd = 32;               // undecided keys per lane
+constexpr int kBnd = 12;               // undecided keys per lane (occupancy: 15 KB per CTA)
 constexpr int kRedoLabel = -2147483647 - 1;
 constexpr int kRedoThreads = 32;
 constexpr int kRedoExtra = 32;         // redo buffer slots beyond K
