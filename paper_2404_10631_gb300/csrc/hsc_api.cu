@@ -301,7 +301,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
     const hsc::Tuning tu = tuning_for(ctx, B, N, k);
     cudaError_t e;
     {
-        StageTimer t(tc, HSC_STAGE_MOMENTS, 4, st);
+        StageTimer t(tc, HSC_STAGE_MOMENTS, hsc::moments_kernel_count(cube, B, N), st);
         e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, st, false, tu.gram_stages);
     }
     if (e == cudaSuccess) {
@@ -681,7 +681,7 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     }
     if (e == cudaSuccess) {  // the tuned Gram staging depth for frames of this size
         const int stg = (ctx->tuned && ctx->tune_B == B && ctx->tune_N == N) ? ctx->tune.gram_stages : 0;
-        StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, hsc::moments_kernel_count(cube, B, N));
         e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream, false, stg);
     }
     if (e == cudaSuccess) {
@@ -719,7 +719,8 @@ hsc_status hsc_pca_covariance(hsc_ctx *ctx, const float *cube, int B, int H, int
     PcaScratch s = carve(ctx, L);
     cudaError_t e;
     {
-        StageTimer t(ctx, HSC_STAGE_MOMENTS, 4);
+        StageTimer t(ctx, HSC_STAGE_MOMENTS,
+                     hsc::moments_kernel_count(cube, B, N, (flags & HSC_COV_FP32_PIPE) != 0));
         e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream,
                                 (flags & HSC_COV_FP32_PIPE) != 0);
     }

@@ -91,6 +91,7 @@ cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s
                            int sm_count, cudaStream_t st, bool force_simt = false,
                            int gram_stages = 0);
 bool gram_tc_supported(const float *cube, int B, long N);
+int moments_kernel_count(const float *cube, int B, long N, bool force_simt = false);
 cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s,
                            cudaStream_t st, int stages = 0);
 

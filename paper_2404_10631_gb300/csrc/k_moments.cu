@@ -198,53 +198,64 @@ gram_partial_kernel(const float *__restrict__ cube, int B, int Bp, long N,
     if (do_sums && tid < B) sum_part[(size_t)blockIdx.x * B + tid] = bsum;
 }
 
-// delta_b = (1/N) sum of partial sums; mu_b = shift_b + delta_b. One warp
-// per band: the partials are summed in double-float, then scaled in FP64.
-constexpr int kMeanWarps = 8;
-__global__ void __launch_bounds__(32 * kMeanWarps)
-band_mean_kernel(int B, double inv_N, int n_part, const float *__restrict__ shift,
-                 const float *__restrict__ sum_part, double *__restrict__ delta,
-                 double *__restrict__ mu)
-{
-    const int b = blockIdx.x * kMeanWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (b >= B) return;
-    float s = 0.f, lo = 0.f;
-    for (int i = lane; i < n_part; i += 32) df_acc(s, lo, sum_part[(size_t)i * B + b]);
-    for (int o = 16; o > 0; o >>= 1)
-        df_acc2(s, lo, __shfl_xor_sync(0xffffffffu, s, o), __shfl_xor_sync(0xffffffffu, lo, o));
-    if (lane == 0) {
-        const double d = ((double)s + (double)lo) * inv_N;
-        delta[b] = d;
-        mu[b] = (double)shift[b] + d;
-    }
-}
-
 // C_bc = (sum_i G_i[b][c]) / N - delta_b delta_c for b <= c, mirrored, in
-// FP64 and as FP32 (hi, lo) pairs. Each partial holds entry (b, c) at
-// c * B + b (the tensor-core Gram writes that half of its block; the FP32
-// version writes the whole symmetric matrix). A CTA takes 32 consecutive
-// positions e = c*B + b; its 8 warps each sum every 8th partial (coalesced
-// across the 32 positions) in double-float, then the 8 slices are added.
-constexpr int kRedEntries = 32, kRedSlices = 8;
+// FP64 and as FP32 (hi, lo) pairs, and mu_b = s_b + delta_b with delta_b =
+// (1/N) sum_i S_i[b] (S_i the partial sums of y). Each partial holds entry
+// (b, c) at c * B + b (the tensor-core Gram writes that half of its block;
+// the FP32 version writes the whole symmetric matrix). A CTA takes 32
+// consecutive positions e = c*B + b; its 8 warps each sum every 8th partial
+// of G, and of S for the entry's two bands, in double-float with eight loads
+// of each issued ahead of the additions (coalesced across the 32 positions); then the
+// 8 slices are added in order. delta_b is formed the same way wherever it is
+// used, so C is consistent; the CTA holding (b, b) writes mu_b.
+constexpr int kRedEntries = 32, kRedSlices = 8, kRedAhead = 8;
+
 __global__ void __launch_bounds__(kRedEntries * kRedSlices)
 gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gram_part,
-                   const double *__restrict__ delta, double *__restrict__ C,
-                   float2 *__restrict__ C2)
+                   const float *__restrict__ sum_part, const float *__restrict__ shift,
+                   double *__restrict__ mu, double *__restrict__ C, float2 *__restrict__ C2)
 {
     const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
     const long e = (long)blockIdx.x * kRedEntries + lane;
     const long BB = (long)B * B;
     const int c = e < BB ? (int)(e / B) : 0, b = e < BB ? (int)(e % B) : 0;
     const bool active = e < BB && c >= b;
-    float s = 0.f, lo = 0.f;
-    if (active)
-        for (int i = slice; i < n_part; i += kRedSlices) df_acc(s, lo, gram_part[(size_t)i * BB + e]);
-    __shared__ float2 part[kRedSlices][kRedEntries];
-    part[slice][lane] = make_float2(s, lo);
+    float g = 0.f, gl = 0.f, sb = 0.f, lb = 0.f, sc = 0.f, lc = 0.f;
+    if (active) {
+        // the three sums side by side, kRedAhead loads of each in flight
+        for (int i = slice; i < n_part; i += kRedSlices * kRedAhead) {
+            float vg[kRedAhead], vb[kRedAhead], vc[kRedAhead];
+#pragma unroll
+            for (int u = 0; u < kRedAhead; ++u) {
+                const int k = i + u * kRedSlices;
+                const bool in = k < n_part;
+                vg[u] = in ? gram_part[(size_t)k * BB + e] : 0.f;
+                vb[u] = in ? sum_part[(size_t)k * B + b] : 0.f;
+                vc[u] = in ? sum_part[(size_t)k * B + c] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kRedAhead; ++u)
+                if (i + u * kRedSlices < n_part) {
+                    df_acc(g, gl, vg[u]);
+                    df_acc(sb, lb, vb[u]);
+                    df_acc(sc, lc, vc[u]);
+                }
+        }
+    }
+    __shared__ float2 part[3][kRedSlices][kRedEntries];
+    part[0][slice][lane] = make_float2(g, gl);
+    part[1][slice][lane] = make_float2(sb, lb);
+    part[2][slice][lane] = make_float2(sc, lc);
     __syncthreads();
     if (slice == 0 && active) {
-        for (int k = 1; k < kRedSlices; ++k) df_acc2(s, lo, part[k][lane].x, part[k][lane].y);
-        const double v = fma(-delta[b], delta[c], ((double)s + (double)lo) * inv_N);
+        for (int k = 1; k < kRedSlices; ++k) {
+            df_acc2(g, gl, part[0][k][lane].x, part[0][k][lane].y);
+            df_acc2(sb, lb, part[1][k][lane].x, part[1][k][lane].y);
+            df_acc2(sc, lc, part[2][k][lane].x, part[2][k][lane].y);
+        }
+        const double db = ((double)sb + (double)lb) * inv_N;
+        const double dc = ((double)sc + (double)lc) * inv_N;
+        const double v = fma(-db, dc, ((double)g + (double)gl) * inv_N);
         C[(size_t)b * B + c] = v;
         C[(size_t)c * B + b] = v;
         // the same value as an unevaluated FP32 sum hi + lo (for the
@@ -253,6 +264,7 @@ gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gr
         const float2 pr = make_float2(hi, __double2float_rn(v - (double)hi));
         C2[(size_t)b * B + c] = pr;
         C2[(size_t)c * B + b] = pr;
+        if (b == c) mu[b] = (double)shift[b] + db;
     }
 }
 
@@ -263,17 +275,23 @@ gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gr
 // the larger count.
 int moments_partitions(int sm_count) { return 2 * sm_count; }
 
-// FP64 means and covariance from n_part partials (delta lives in v1 until
-// the Jacobi kernel overwrites it with the eigenvector).
+// FP64 means and covariance from n_part partials (one kernel).
 static cudaError_t launch_reductions(int B, long N, int n_part, const PcaScratch &s, cudaStream_t st)
 {
     const double inv_N = 1.0 / (double)N;
-    band_mean_kernel<<<(B + kMeanWarps - 1) / kMeanWarps, 32 * kMeanWarps, 0, st>>>(
-        B, inv_N, n_part, s.shift, s.sum_part, s.v1, s.mu);
     const long BB = (long)B * B;
     gram_reduce_kernel<<<(unsigned)((BB + kRedEntries - 1) / kRedEntries), kRedEntries * kRedSlices,
-                         0, st>>>(B, inv_N, n_part, s.gram_part, s.v1, s.C, s.C2);
+                         0, st>>>(B, inv_N, n_part, s.gram_part, s.sum_part, s.shift, s.mu, s.C,
+                                  s.C2);
     return cudaGetLastError();
+}
+
+// Kernels launch_moments issues: the pilot, the Gram (two launches for
+// 128 < B <= 256 on the tensor cores), the reduction.
+int moments_kernel_count(const float *cube, int B, long N, bool force_simt)
+{
+    if (!force_simt && gram_tc_supported(cube, B, N)) return B > 128 ? 4 : 3;
+    return 3;
 }
 
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s, int sm_count,

@@ -23,7 +23,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel name prefix -> pipeline stage, and the source file each stage's
 # kernels live in (its hash tags the numbers with the code they measured)
 STAGE_OF = (("pilot_shift_kernel", "moments"), ("gram_tc_kernel", "moments"),
-            ("gram_partial_kernel", "moments"), ("band_mean_kernel", "moments"),
+            ("gram_partial_kernel", "moments"),
             ("gram_reduce_kernel", "moments"), ("jacobi_kernel", "jacobi"),
             ("project_svm_kernel", "project_svm"), ("normalize_kernel", "normalize"),
             ("knn_pruned_kernel", "knn"), ("knn_redo_kernel", "knn"),
