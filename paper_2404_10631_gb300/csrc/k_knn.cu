@@ -391,7 +391,7 @@ knn_heap_kernel(const float *__restrict__ I, const float *__restrict__ P, int k,
 // cannot hold the undecided keys, fewer than K valid offsets in the table,
 // or neighbour-index output) gets the sentinel label kRedoLabel and
 // knn_redo_kernel completes it with an unbounded walk.
-constexpr int kWalkThreads = 64;
+constexpr int kWalkThreads = 32;
 constexpr int kTabR2 = 400;            // table: dr^2 + dc^2 <= 400
 constexpr int kTabDr = 16;             // |dr| <= 16: windows of up to 32 rows
 constexpr int kTabDc = 20;             // |dc| <= 20 follows from kTabR2
@@ -517,7 +517,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     const float l2 = lam * lam;
     const long N = (long)H * W;
 
-    // stage the window rows x (64 + 2 * 20) columns: asynchronous 4-byte
+    // stage the window rows x (kWalkThreads + 2 * 20) columns: asynchronous 4-byte
     // copies, all in flight at once (out-of-image columns are zero-filled)
     for (int ii = 0; ii < nrows; ++ii) {
         const float *row = I + (long)(lo_r + ii) * W;
