@@ -102,6 +102,7 @@ typedef struct {
 #define HSC_MAX_K 64
 #define HSC_MAX_WINDOW_ROWS 32
 #define HSC_MAX_BANDS 1024
+#define HSC_MAX_PC 8
 
 /* flags for hsc_pca_one_band */
 #define HSC_PCA_MINMAX 1u        /* write (I - min)/(max - min) in [0,1] (what the KNN uses) */
@@ -156,6 +157,23 @@ size_t hsc_scratch_bytes(const hsc_ctx *ctx);
 hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                             unsigned flags, float *one_band, double *eigvec,
                             double *eigval);
+
+/* Projection on several principal components (Section III.A.2 d: with more
+ * than one component the projection is a matrix-matrix product): the
+ * n_pc leading eigenvectors of the covariance, each refined to the residual
+ * bound of hsc_pca_one_band and signed by the same rule (v_1 is
+ * hsc_pca_one_band's), and out_j = v_j^T (x - mu). The eigenvectors beyond
+ * the first are refined from the 16 basis columns of the first sweep, so a
+ * component whose eigenvalue is not separated from its neighbours may not
+ * converge (HSC_ERR_NOT_CONVERGED at hsc_sync).
+ *   n_pc     1 .. min(HSC_MAX_PC, B)
+ *   flags    0 or HSC_CUBE_BIP
+ *   out      n_pc x H x W float32 (device, required); out_0 equals the raw
+ *            one-band projection
+ *   eigvecs  n_pc x B float64 (device, nullable), row j = v_{j+1}
+ *   eigvals  n_pc float64 (device, nullable), decreasing */
+hsc_status hsc_pca_project(hsc_ctx *ctx, const float *cube, int B, int H, int W, int n_pc,
+                           unsigned flags, float *out, double *eigvecs, double *eigvals);
 
 /* Steps (i) and (ii) of the PCA alone (Section II.C.2, III.A.2.a-b): band
  * means and the covariance of the centred cube divided by the pixel count.

@@ -29,6 +29,7 @@ HSC_MAX_CLASSES = 8
 HSC_MAX_K = 64
 HSC_MAX_WINDOW_ROWS = 32
 HSC_MAX_BANDS = 1024
+HSC_MAX_PC = 8
 HSC_PCA_MINMAX = 1
 HSC_SVM_COUPLE_F64 = 2
 HSC_CLASSIFY_RAW_I = 16
@@ -38,7 +39,7 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",
             "hsc_pca_one_band", "hsc_svm_probs", "hsc_knn_filter", "hsc_classify",
             "hsc_profile_enable", "hsc_profile_read", "hsc_pca_diagnostics", "hsc_measure_fma_rate",
-            "hsc_autotune", "hsc_set_tuning",
+            "hsc_autotune", "hsc_set_tuning", "hsc_pca_project",
             "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics",
             "hsc_classify_batch", "hsc_server_create", "hsc_server_submit",
             "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy")
@@ -147,6 +148,7 @@ def lib():
         L.hsc_autotune.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
                                    ctypes.POINTER(ctypes.c_int32)]
         L.hsc_set_tuning.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32)]
+        L.hsc_pca_project.argtypes = [vp, vp, i32, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int64),
@@ -328,6 +330,19 @@ def hsc_pca_one_band(ctx: Context, cube, flags: int = HSC_PCA_MINMAX, one_band=N
     ctx.check(lib().hsc_pca_one_band(ctx.handle, _ptr(cube), B, H, W, flags, _ptr(one_band),
                                      _ptr(eigvec), _ptr(eigval)))
     return one_band
+
+
+def hsc_pca_project(ctx: Context, cube, n_pc: int, flags: int = 0, out=None, eigvecs=None,
+                    eigvals=None):
+    """Projections on the n_pc leading principal components: n_pc x H x W
+    (allocated when not given)."""
+    import torch
+    B, H, W = _bhw(cube, flags)
+    if out is None:
+        out = torch.empty((n_pc, H, W), dtype=torch.float32, device=cube.device)
+    ctx.check(lib().hsc_pca_project(ctx.handle, _ptr(cube), B, H, W, n_pc, flags, _ptr(out),
+                                    _ptr(eigvecs), _ptr(eigvals)))
+    return out
 
 
 def hsc_pca_covariance(ctx: Context, cube, flags: int = 0, mean=None, cov=None):

@@ -117,12 +117,13 @@ hsc_status cuda_fail(hsc_ctx *ctx, cudaError_t e, const char *where)
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, bsq, total;
+    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, bsq, vk, lamk,
+        vkf, total;
     int n_part;
 };
 
 Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool need_I,
-                   bool need_P, bool need_bsq = false)
+                   bool need_P, bool need_bsq = false, int n_pc = 0)
 {
     Layout L{};
     size_t off = 0;
@@ -159,6 +160,11 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
     if (need_I) L.tmpI = take(sizeof(float) * (size_t)N);
     if (need_P) L.tmpP = take(sizeof(float) * (size_t)k * N);
     if (need_bsq) L.bsq = take(sizeof(float) * (size_t)B * N);  // band-sequential copy of a BIP cube
+    if (n_pc > 1) {  // multi-PC: the leading eigenvectors, their eigenvalues, float copies
+        L.vk = take(sizeof(double) * (size_t)n_pc * B);
+        L.lamk = take(sizeof(double) * (size_t)n_pc);
+        L.vkf = take(sizeof(float) * (size_t)n_pc * B);
+    }
     L.total = off;
     return L;
 }
@@ -702,6 +708,58 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     if (e == cudaSuccess && eigval)
         e = cudaMemcpyAsync(eigval, s.lambda1, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_pca_one_band launch");
+    return HSC_OK;
+}
+
+hsc_status hsc_pca_project(hsc_ctx *ctx, const float *cube, int B, int H, int W, int n_pc,
+                           unsigned flags, float *out, double *eigvecs, double *eigvals)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    if ((st = check_cube(ctx, cube, B, H, W))) return st;
+    if (!out) return fail(ctx, HSC_ERR_INVALID_ARG, "out is NULL%s");
+    if (n_pc < 1 || n_pc > HSC_MAX_PC || n_pc > B)
+        return fail(ctx, HSC_ERR_INVALID_ARG, "n_pc must be 1 .. min(HSC_MAX_PC, B)%s");
+    if (flags & ~(unsigned)HSC_CUBE_BIP) return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
+    const long N = (long)H * W;
+    const bool bip = (flags & HSC_CUBE_BIP) != 0;
+    const bool multi = n_pc > 1;  // one component: hsc_pca_one_band's own outputs
+    Layout L = make_layout(ctx, B, N, 0, true, false, false, bip, multi ? n_pc : 0);
+    if ((st = ensure_scratch(ctx, L.total))) return st;
+    PcaScratch s = carve(ctx, L);
+    char *base = static_cast<char *>(ctx->scratch);
+    if (multi) {
+        s.vk = reinterpret_cast<double *>(base + L.vk);
+        s.lamk = reinterpret_cast<double *>(base + L.lamk);
+        s.vkf = reinterpret_cast<float *>(base + L.vkf);
+    }
+    cudaError_t e = cudaSuccess;
+    if (bip) {
+        float *bsq = reinterpret_cast<float *>(base + L.bsq);
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, 1);
+        e = hsc::launch_bip_to_bsq(cube, B, N, bsq, ctx->stream);
+        cube = bsq;
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_MOMENTS, hsc::moments_kernel_count(cube, B, N));
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_JACOBI, 1);
+        e = hsc::launch_jacobi(B, s, ctx->stream, n_pc);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(ctx, HSC_STAGE_PROJECT_SVM, 1);
+        e = hsc::launch_project_multi(cube, B, N, multi ? s.vkf : s.v1f, s.muf, n_pc, out, s.ctl,
+                                      ctx->sm_count, ctx->stream);
+    }
+    if (e == cudaSuccess && eigvecs)
+        e = cudaMemcpyAsync(eigvecs, multi ? s.vk : s.v1, sizeof(double) * (size_t)n_pc * B,
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess && eigvals)
+        e = cudaMemcpyAsync(eigvals, multi ? s.lamk : s.lambda1, sizeof(double) * (size_t)n_pc,
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_pca_project launch");
     return HSC_OK;
 }
 

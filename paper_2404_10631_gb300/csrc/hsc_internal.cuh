@@ -67,6 +67,9 @@ struct PcaScratch {
     float *v1f;          // B
     float *muf;          // B
     float *jac_A;        // Jacobi work area (only when it does not fit in shared memory)
+    double *vk = nullptr;    // multi-PC: n_vec x B leading eigenvectors (row 0 = v1)
+    double *lamk = nullptr;  // multi-PC: n_vec eigenvalues
+    float *vkf = nullptr;    // multi-PC: float copies of vk
     int n_part;
 };
 
@@ -97,7 +100,9 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
 
 // Jacobi eigen-decomposition of C, FP64 refinement of the leading vector,
 // sign rule; writes v1, lambda1, v1f, muf and resets the I min/max keys.
-cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st);
+// n_vec > 1 (with s.vk, s.lamk, s.vkf set): also the next n_vec - 1 leading
+// eigenvectors, refined the same way (multi-PC projection).
+cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec = 1);
 
 // Pass 2 over the cube: projection (if v1f != nullptr) + SVM decision values,
 // Platt, coupling (if probs != nullptr). I_raw min/max into ctl keys.
@@ -106,6 +111,11 @@ cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1
                                bool couple_f64, float *probs, int32_t *svm_labels,
                                Control *ctl, int sm_count, cudaStream_t st, int max_blocks = 0,
                                int px = 0);
+
+// out_j = v_j^T (x - mu) for the n_pc (1..8) rows of vkf, n_pc x N.
+cudaError_t launch_project_multi(const float *cube, int B, long N, const float *vkf,
+                                 const float *muf, int n_pc, float *out, Control *ctl,
+                                 int sm_count, cudaStream_t st);
 
 // I_norm = (I - min)/(max - min) (0 if max == min), min/max from ctl keys.
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,

@@ -50,6 +50,11 @@ struct JacParams {
     float rot_tol;       // rotate (p,q) when |a_pq| > rot_tol (A scaled to max diag 1)
     float stop_tol_final;  // fallback sweeps end once every |a_pq| seen in one is below
     int use_smem;          // 1: the whole work area in shared memory (n <= 140)
+    // multi-PC form: n_vec >= 1 leading eigenvectors (rows of vk, float copies
+    // in vkf, eigenvalues in lamk; unused when n_vec == 1 and they are null)
+    int n_vec;
+    double *vk, *lamk;
+    float *vkf;
 };
 
 // j-slices of the double-float C v: each thread sums at most 16 products
@@ -835,7 +840,11 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
             if (it == kMaxRefine) break;
             // g_c = basis_c^T r (one warp per column), then the column's
             // coefficient
-            const float inv_dc = deflate ? 1.f / (rho_s - theta_c) : 0.f;
+            // the unrebuilt cluster's term (dropped when rho sits in that
+            // cluster: a further eigenvector among the small eigenvalues)
+            const float den_c = rho_s - theta_c;
+            const float inv_dc =
+                (deflate && fabsf(den_c) > 1e-3f * fabsf(rho_s)) ? 1.f / den_c : 0.f;
             for (int c = warp; c < m; c += nwarps) {
                 float g = 0.f;
                 for (int ii = lane; ii < B; ii += 32) g = fmaf(basis[(size_t)c * ld + ii], sr[ii], g);
@@ -1224,10 +1233,12 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     // ---- outputs: v / ||v|| (||v||^2 = the last v^T v, which belongs to the
     // returned v), the sign rule (largest |v_i| positive, the smaller band on
-    // a tie), lambda1 = rho 2^e. v_i = vh + vl is exact in FP64; |v_i| is
+    // a tie), lambda = rho 2^e. v_i = vh + vl is exact in FP64; |v_i| is
     // ordered by the integer value of its bits, so the arg-max is an integer
     // reduction (FP64 arithmetic on GB300 has a 64-cycle latency).
-    {
+    __shared__ unsigned long long s_key[32];
+    __shared__ int s_arg[32];
+    auto finish = [&](double *vout, float *vfout, double *lamout) {
         unsigned long long key = 0ull;
         int arg = 0x7fffffff;
         if (tid < B) {
@@ -1244,8 +1255,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
                 arg = a2;
             }
         }
-        __shared__ unsigned long long s_key[32];
-        __shared__ int s_arg[32];
+        __syncthreads();  // s_key / s_arg may hold the previous vector's
         if (lane == 0) {
             s_key[warp] = key;
             s_arg[warp] = arg;
@@ -1261,23 +1271,74 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
             s_sign = (bv < 0.0) ? -1 : 1;
             const double vv = (double)s_vv.h + (double)s_vv.l;
             s_inv_norm = vv > 0.0 ? 1.0 / sqrt(vv) : 1.0;
-            *lambda1_out = ldexp((double)s_rho.h + (double)s_rho.l, e2);
-            if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
-            ctl->jacobi_sweeps = (unsigned)sweeps;
-            ctl->refine_iters = (unsigned)(refine_iters > kMaxRefine ? kMaxRefine : refine_iters);
-            ctl->jacobi_sweep_cycles = (unsigned long long)t_sweep;
-            ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
-            ctl->imin_key = float_to_key(INFINITY);
-            ctl->imax_key = float_to_key(-INFINITY);
+            *lamout = ldexp((double)s_rho.h + (double)s_rho.l, e2);
         }
+        __syncthreads();
+        const double scl = (double)s_sign * s_inv_norm;
+        for (int ii = tid; ii < B; ii += nthr) {
+            const double v = scl * ((double)vh[ii] + (double)vl[ii]);
+            vout[ii] = v;
+            if (vfout) vfout[ii] = (float)v;
+        }
+    };
+    finish(v1_out, v1f, lambda1_out);
+    if (prm.n_vec > 1) {  // row 0 of the multi-PC output is v1
+        for (int ii = tid; ii < B; ii += nthr) {
+            prm.vk[ii] = v1_out[ii];
+            prm.vkf[ii] = v1f[ii];
+        }
+        if (tid == 0) prm.lamk[0] = *lambda1_out;
     }
-    __syncthreads();
-    const double scl = (double)s_sign * s_inv_norm;
-    for (int ii = tid; ii < B; ii += nthr) {
-        const double v = scl * ((double)vh[ii] + (double)vl[ii]);
-        v1_out[ii] = v;
-        v1f[ii] = (float)v;
-        muf[ii] = (float)mu[ii];
+    for (int ii = tid; ii < B; ii += nthr) muf[ii] = (float)mu[ii];
+    if (tid == 0) {
+        if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
+        ctl->jacobi_sweeps = (unsigned)sweeps;
+        ctl->refine_iters = (unsigned)(refine_iters > kMaxRefine ? kMaxRefine : refine_iters);
+        ctl->jacobi_sweep_cycles = (unsigned long long)t_sweep;
+        ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
+        ctl->imin_key = float_to_key(INFINITY);
+        ctl->imax_key = float_to_key(-INFINITY);
+    }
+
+    // ---- further eigenvectors (multi-PC projection): v_j for j = 1 .. n_vec-1,
+    // each refined from basis column j (the j-th Ritz vector, or the j-th
+    // largest diagonal's column after the sweep) by the same deflated
+    // correction aimed at column j, then the same sign rule. Phase 0's basis
+    // only (the fallback rebuilds none).
+    if (prm.n_vec > 1 && sweeps == 1) {
+        const bool sm_basis = prm.use_smem && !kPacked;
+        const size_t xo = jac_phase0_floats(n);
+        const float *bas = sm_basis ? smem + xo : X;
+        const float2 *c2p = sm_basis ? reinterpret_cast<const float2 *>(smem)
+                                     : (prm.use_smem ? Cs2 : C2);
+        float2 *partp = sm_basis ? reinterpret_cast<float2 *>(smem + xo + (size_t)kBasis * ld) : part;
+        for (int j = 1; j < prm.n_vec && j < m; ++j) {
+            __syncthreads();
+            for (int ii = tid; ii < B; ii += nthr) {
+                vh[ii] = bas[(size_t)j * ld + ii];
+                vl[ii] = 0.f;
+            }
+            __syncthreads();
+            const int it = refine(bas, m, j, deflate, theta_c, c2p, partp);
+            if (it > kMaxRefine) {
+                // not converged (an eigenvalue inside a cluster): report it and
+                // return the basis column itself, finite, with its estimate
+                if (tid == 0) atomicOr(&ctl->status, ST_NOT_CONVERGED);
+                __syncthreads();
+                for (int ii = tid; ii < B; ii += nthr) {
+                    vh[ii] = bas[(size_t)j * ld + ii];
+                    vl[ii] = 0.f;
+                }
+                float sq = 0.f;
+                for (int ii = tid; ii < B; ii += nthr) sq = fmaf(vh[ii], vh[ii], sq);
+                sq = block_sumf(sq, fred);
+                if (tid == 0) {
+                    s_vv = dfl{sq, 0.f};
+                    s_rho = dfl{th[j], 0.f};
+                }
+            }
+            finish(prm.vk + (size_t)j * B, prm.vkf + (size_t)j * B, prm.lamk + j);
+        }
     }
 }
 
@@ -1295,9 +1356,13 @@ size_t jacobi_global_floats(int B)
     return f;
 }
 
-cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st)
+cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec)
 {
     JacParams prm;
+    prm.n_vec = n_vec > 1 && s.vk && s.lamk && s.vkf ? n_vec : 1;
+    prm.vk = s.vk;
+    prm.lamk = s.lamk;
+    prm.vkf = s.vkf;
     prm.B = B;
     prm.n = B + (B & 1);
     if (prm.n < 2) prm.n = 2;

@@ -294,6 +294,109 @@ cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control 
     return cudaGetLastError();
 }
 
+// ---- multi-PC projection (Section III.A.2 d with more than one principal
+// component): out_j(p) = v_j^T (x_p - mu) for the NP leading eigenvectors,
+// one pass over the cube with the one-band projection's arithmetic per
+// component (component 0 equals that projection bit for bit).
+namespace {
+template <int NP, int PX>
+__global__ void __launch_bounds__(kThreads)
+project_multi_kernel(const float *__restrict__ cube, int B, long N, const float *__restrict__ vkf,
+                     const float *__restrict__ muf, float *__restrict__ out, Control *ctl)
+{
+    constexpr int S = NP + 1;  // per band: v_0..v_{NP-1}, mu
+    extern __shared__ float ws[];
+    for (int idx = threadIdx.x; idx < B * S; idx += blockDim.x) {
+        const int b = idx / S, j = idx % S;
+        ws[idx] = j < NP ? vkf[(size_t)j * B + b] : muf[b];
+    }
+    __syncthreads();
+    bool bad = false;
+    const long ngroups = (N + PX - 1) / PX;
+    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
+         g += (long)gridDim.x * blockDim.x) {
+        const long p0 = g * PX;
+        float acc[NP][PX];
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+#pragma unroll
+            for (int u = 0; u < PX; ++u) acc[j][u] = 0.f;
+#pragma unroll 8
+        for (int b = 0; b < B; ++b) {
+            float x[PX];
+            const float *src = cube + (size_t)b * (size_t)N + p0;
+            if constexpr (PX == 4) {
+                const float4 v = __ldcs(reinterpret_cast<const float4 *>(src));
+                x[0] = v.x;
+                x[1] = v.y;
+                x[2] = v.z;
+                x[3] = v.w;
+            } else {
+                x[0] = __ldcs(src);
+            }
+            const float *wr = ws + b * S;
+            const float mb = wr[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j)
+#pragma unroll
+                for (int u = 0; u < PX; ++u) acc[j][u] = fmaf(wr[j], x[u] - mb, acc[j][u]);
+        }
+#pragma unroll
+        for (int u = 0; u < PX; ++u) {
+            const long p = p0 + u;
+            if (p >= N) break;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                bad |= !isfinite(acc[j][u]);
+                out[(size_t)j * (size_t)N + p] = acc[j][u];
+            }
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+}
+
+template <int NP, int PX>
+cudaError_t launch_multi(const float *cube, int B, long N, const float *vkf, const float *muf,
+                         float *out, Control *ctl, int sm_count, cudaStream_t st)
+{
+    const size_t smem = sizeof(float) * (size_t)B * (NP + 1);
+    auto kern = project_multi_kernel<NP, PX>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    long blocks = ((N + PX - 1) / PX + kThreads - 1) / kThreads;
+    if (blocks > (long)sm_count * 8) blocks = (long)sm_count * 8;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, kThreads, smem, st>>>(cube, B, N, vkf, muf, out, ctl);
+    return cudaGetLastError();
+}
+
+template <int PX>
+cudaError_t dispatch_multi(int np, const float *cube, int B, long N, const float *vkf,
+                           const float *muf, float *out, Control *ctl, int sm, cudaStream_t st)
+{
+    switch (np) {
+    case 1: return launch_multi<1, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    case 2: return launch_multi<2, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    case 3: return launch_multi<3, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    case 4: return launch_multi<4, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    case 5: return launch_multi<5, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    case 6: return launch_multi<6, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    case 7: return launch_multi<7, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    case 8: return launch_multi<8, PX>(cube, B, N, vkf, muf, out, ctl, sm, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
+cudaError_t launch_project_multi(const float *cube, int B, long N, const float *vkf,
+                                 const float *muf, int n_pc, float *out, Control *ctl,
+                                 int sm_count, cudaStream_t st)
+{
+    const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0);
+    return vec ? dispatch_multi<4>(n_pc, cube, B, N, vkf, muf, out, ctl, sm_count, st)
+               : dispatch_multi<1>(n_pc, cube, B, N, vkf, muf, out, ctl, sm_count, st);
+}
+
 // ---- pixel-interleaved (BIP, H x W x B) input: one tiled transpose into the
 // band-sequential layout the other kernels read. 32 x 32 tiles through shared
 // memory (one padded column against bank conflicts): reads coalesced along
