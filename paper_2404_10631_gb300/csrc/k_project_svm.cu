@@ -142,7 +142,7 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
             for (int m = 0; m < MA; ++m) acc[m][u] = 0.f;
         }
         // deep unrolling keeps many independent loads in flight per thread
-        constexpr int kUnroll = PX == 1 ? 16 : 8;
+        constexpr int kUnroll = 16;
 #pragma unroll kUnroll
         for (int b = 0; b < B; ++b) {
             float x[PX];
