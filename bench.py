@@ -582,6 +582,10 @@ def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
         hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
                                flags=hsc.HSC_BATCH_GRAPH, labels=labs)
 
+    def pooled():
+        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
+                               flags=hsc.HSC_BATCH_GRAPH | hsc.HSC_BATCH_POOL, labels=labs)
+
     def per_frame():
         for c, l in zip(cubes, labs):
             hsc.hsc_classify(ctx, c, model, f0.K, f0.window_rows, f0.lam, labels=l)
@@ -601,13 +605,28 @@ def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
         return ev[0].elapsed_time(ev[n]) / n, per
 
     b_ms, b_per = timed(batched, reps)
+    o_ms, _ = timed(pooled, 3)
     p_ms, p_per = timed(per_frame, 3)
+    # per-stage device time of the stage-major form (calls without a graph)
+    ctx.profile(True)
+    ctx.profile_read()
+    for _ in range(3):
+        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, labels=labs)
+    ctx.sync()
+    st_ms, st_k, _ = ctx.profile_read()
+    ctx.profile(False)
+    stages = {n: round(ms / 3, 4) for n, ms in st_ms.items() if ms > 0}
     return {"workload": "%d square snapshot frames, sides 40-64 px, 125 bands float32, "
                         "4 classes (shared model), K=16, 7-row window, lambda=1" % n_frames,
             "pixels_per_batch": px,
             "batched": {"value": px / (b_ms / 1e3), "unit": UNIT, "ms_per_batch": b_ms,
                         "p50_ms": b_per[len(b_per) // 2], "p99_ms": b_per[-1],
-                        "api": "hsc_classify_batch, CUDA-graph replay"},
+                        "api": "hsc_classify_batch, stage-major (one launch per stage over "
+                               "every frame), CUDA-graph replay",
+                        "stages_ms": stages},
+            "stream_pool": {"value": px / (o_ms / 1e3), "unit": UNIT, "ms_per_batch": o_ms,
+                            "api": "hsc_classify_batch with HSC_BATCH_POOL (frames on 64 "
+                                   "streams), CUDA-graph replay"},
             "plain_per_frame": {"value": px / (p_ms / 1e3), "unit": UNIT, "ms_per_batch": p_ms,
                                 "api": "hsc_classify once per frame, one stream"},
             "speedup": p_ms / b_ms}

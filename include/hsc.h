@@ -230,17 +230,26 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
 /* ---- many frames in one call (batching; an extension beyond the paper,
  * which processes one image at a time). Every frame gets the whole path of
  * hsc_classify: its own PCA (means, covariance, Jacobi, projection), the SVM
- * with the shared model, the KNN filter. Frames run concurrently on up to 64
+ * with the shared model, the KNN filter. A frame's outputs are bit-identical
+ * to what hsc_classify gives for it alone.
+ * Stage-major form (B <= 128, pruned KNN search: AUTO or PRUNED with
+ * lambda > 0, up to 65535 frames): one launch per stage covers every frame,
+ * from a frame table and work-item tables the call uploads with one copy
+ * (8 kernel launches per call, whatever the frame count): the pilots, one
+ * persistent tensor-core Gram over every frame's chunk ranges, the
+ * reductions, one Jacobi CTA per frame, the projection/SVM, normalisation
+ * and KNN over per-frame work items.
+ * Otherwise (or with HSC_BATCH_POOL) frames run concurrently on up to 64
  * library-owned streams that fork from and join back into the context's
- * stream, each with its own scratch slot, so one frame's single-SM Jacobi
- * overlaps the other frames' work. A frame's outputs are bit-identical to
- * what hsc_classify gives for it alone.
+ * stream, each with its own scratch slot.
  *   frames    host array of n_frames descriptors (device pointers inside)
  *   B, model, params, flags: shared by all frames (as hsc_classify)
  *   flags     also HSC_BATCH_GRAPH: capture the batch's launches in a CUDA
- *             graph; while later calls pass the same frames (pointers and
- *             sizes) and parameters, the graph is replayed instead of
- *             relaunching, which removes the per-launch host cost. */
+ *             graph and replay it while later calls have the same launch
+ *             configuration (stage-major: frame count, work-item counts,
+ *             parameters; the frames' pointers travel in the tables. Stream
+ *             pool: the same frames, pointers and sizes), which removes the
+ *             per-launch host cost; HSC_BATCH_POOL: the stream-pool form. */
 typedef struct {
     const float *cube;   /* B x H x W float32 */
     int32_t H, W;
@@ -251,6 +260,7 @@ typedef struct {
 } hsc_frame;
 
 #define HSC_BATCH_GRAPH 8u
+#define HSC_BATCH_POOL 64u
 
 hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frames, int B,
                               const hsc_svm_model *model, const hsc_knn_params *params,

@@ -44,6 +44,7 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_classify_batch", "hsc_server_create", "hsc_server_submit",
             "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy")
 HSC_BATCH_GRAPH = 8
+HSC_BATCH_POOL = 64
 HSC_COV_FP32_PIPE = 4
 HSC_NOALLOC_MAX_BANDS = 128
 STAGES = ("moments", "jacobi", "project_svm", "normalize", "knn")

@@ -51,6 +51,17 @@ struct hsc_ctx {
     // cached CUDA graph of the last graph-mode batch and its signature
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<long long> batch_sig;
+    // stage-major batch: scratch (sm_ctl_cap control blocks first), pinned
+    // staging of the frame and work-item tables, the cached graph of its
+    // launches and their signature
+    void *sm_scratch = nullptr;
+    size_t sm_scratch_size = 0;
+    int sm_ctl_cap = 0;
+    void *sm_host = nullptr;
+    size_t sm_host_size = 0;
+    cudaEvent_t sm_upload = nullptr;
+    cudaGraphExec_t sm_exec = nullptr;
+    std::vector<long long> sm_sig;
     // autotuned launch parameters and the frame shape (B, N, k) they were
     // chosen for; other shapes use the defaults
     bool tuned = false;
@@ -590,6 +601,10 @@ void hsc_ctx_destroy(hsc_ctx *ctx)
     if (ctx->fork_event) cudaEventDestroy(ctx->fork_event);
     if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
     if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);
+    if (ctx->sm_exec) cudaGraphExecDestroy(ctx->sm_exec);
+    if (ctx->sm_scratch) cudaFree(ctx->sm_scratch);
+    if (ctx->sm_upload) cudaEventDestroy(ctx->sm_upload);
+    if (ctx->sm_host) cudaFreeHost(ctx->sm_host);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -640,6 +655,19 @@ hsc_status hsc_sync(hsc_ctx *ctx)
                                         sizeof(unsigned), ctx->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch status readback");
+    }
+    if (ctx->sm_scratch && ctx->sm_ctl_cap > 0) {
+        std::vector<Control> ctl((size_t)ctx->sm_ctl_cap);
+        e = cudaMemcpy(ctl.data(), ctx->sm_scratch, sizeof(Control) * ctl.size(),
+                       cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < ctl.size() && e == cudaSuccess; ++i)
+            if (ctl[i].status) {
+                bits |= ctl[i].status;
+                e = cudaMemsetAsync(&reinterpret_cast<Control *>(ctx->sm_scratch)[i].status, 0,
+                                    sizeof(unsigned), ctx->stream);
+            }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batch status readback");
     }
     if (bits & (hsc::ST_NONFINITE_CUBE | hsc::ST_NONFINITE_MAP))
@@ -868,6 +896,289 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
 }
 
 
+}  // extern "C"
+
+namespace {
+
+// Stage-major form of hsc_classify_batch (B <= 128, pruned KNN): the frame
+// table and the work items are built here and uploaded with one copy; then
+// one launch per stage covers every frame (8 launches per call, whatever the
+// frame count). Each frame gets the scratch a single-frame call would carve
+// and its Gram partials cover the same chunk ranges, so its results equal
+// hsc_classify's bit for bit.
+bool staged_batch_ok(const hsc_frame *frames, int n_frames, int B, const hsc_knn_params *params)
+{
+    if (B > 128 || n_frames > 65535) return false;
+    if (!(params->search == HSC_KNN_SEARCH_AUTO || params->search == HSC_KNN_SEARCH_PRUNED))
+        return false;
+    if (!(params->lambda > 0.f)) return false;
+    long ctas = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const long N = (long)frames[f].H * frames[f].W;
+        if (!hsc::gram_tc_usable(frames[f].cube, B, N)) return false;
+        ctas += (long)frames[f].H * ((frames[f].W + 31) / 32);
+    }
+    return ctas < (1L << 31);
+}
+
+hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_frames, int B,
+                                 const hsc_svm_model *model, const hsc_knn_params *params,
+                                 unsigned flags)
+{
+    using hsc::BatchFrame;
+    using hsc::GramItem;
+    using hsc::PixItem;
+    const int k = model->n_classes;
+    const int sm = ctx->sm_count;
+    const int R = params->window_rows;
+    constexpr int kPixPerItem = 1024;
+    // ---- layout: control blocks, per-frame buffers, tables
+    struct FrameLay {
+        size_t shift, gram, sums, C, C2, mu, v1, lam, v1f, muf, I, P;
+        long per;
+        int parts, vec;
+    };
+    std::vector<FrameLay> fl((size_t)n_frames);
+    const int ctl_cap = std::max(n_frames, std::max(64, ctx->sm_ctl_cap));
+    size_t off = align_up((size_t)ctl_cap * sizeof(Control));
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    int n_gram = 0, n_pix = 0, n_ctas = 0, max_rows = 1;
+    for (int f = 0; f < n_frames; ++f) {
+        const hsc_frame &fr = frames[f];
+        const long N = (long)fr.H * fr.W;
+        FrameLay &L = fl[(size_t)f];
+        const Layout one = make_layout(ctx, B, N, k, true, false, false);
+        const int n_tc = std::min(one.n_part, sm);
+        L.per = hsc::gram_tc_per(N, n_tc, sm);
+        L.parts = hsc::gram_tc_parts(N, L.per);
+        L.vec = (N % 4 == 0 && (reinterpret_cast<uintptr_t>(fr.cube) & 15u) == 0) ? 1 : 0;
+        L.shift = take(sizeof(float) * 2 * B);
+        L.gram = take((size_t)L.parts * B * B * sizeof(float));
+        L.sums = take(sizeof(float) * (size_t)L.parts * B);
+        L.C = take(sizeof(double) * (size_t)B * B);
+        L.C2 = take(sizeof(float) * 2 * (size_t)B * B);
+        L.mu = take(sizeof(double) * B);
+        L.v1 = take(sizeof(double) * B);
+        L.lam = take(sizeof(double));
+        L.v1f = take(sizeof(float) * B);
+        L.muf = take(sizeof(float) * B);
+        L.I = fr.one_band ? 0 : take(sizeof(float) * (size_t)N);
+        L.P = fr.probs ? 0 : take(sizeof(float) * (size_t)k * N);
+        n_gram += L.parts;
+        n_pix += (int)((N + kPixPerItem - 1) / kPixPerItem);
+        n_ctas += fr.H * ((fr.W + 31) / 32);
+        max_rows = std::max(max_rows, std::min(R, fr.H));
+    }
+    long n_px = 0;
+    for (int f = 0; f < n_frames; ++f) n_px += (long)frames[f].H * frames[f].W;
+    const size_t redo = take(sizeof(int2) * (size_t)n_px);  // the KNN redo list
+    int n_large = 0;  // frames whose pilot takes a CTA per band
+    for (int f = 0; f < n_frames; ++f) n_large += (long)frames[f].H * frames[f].W > 4096 ? 1 : 0;
+    const size_t tab_frames = sizeof(BatchFrame) * (size_t)n_frames;
+    const size_t tab_gram = align_up(sizeof(GramItem) * (size_t)n_gram);
+    const size_t tab_pix = align_up(sizeof(PixItem) * (size_t)n_pix);
+    const size_t tab_bytes = align_up(tab_frames) + tab_gram + tab_pix + sizeof(int) * (size_t)n_large;
+    const size_t tab = take(tab_bytes);
+    const size_t total = off;
+    cudaError_t e;
+    // ---- scratch and pinned staging
+    if (total > ctx->sm_scratch_size || ctl_cap > ctx->sm_ctl_cap) {
+        if (ctx->cap && total + ctx->scratch_size > ctx->cap) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "batch scratch of %zu bytes exceeds the cap", total);
+            ctx->last_error = buf;
+            return HSC_ERR_OOM;
+        }
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch scratch sync");
+        if (ctx->sm_scratch) {
+            std::vector<Control> old((size_t)ctx->sm_ctl_cap);
+            e = cudaMemcpy(old.data(), ctx->sm_scratch, sizeof(Control) * old.size(),
+                           cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "batch status readback");
+            for (const Control &c : old) ctx->host_status |= c.status;
+            cudaFree(ctx->sm_scratch);
+            ctx->sm_scratch = nullptr;
+            ctx->sm_scratch_size = 0;
+            ctx->sm_ctl_cap = 0;
+        }
+        if (ctx->sm_exec) {
+            cudaGraphExecDestroy(ctx->sm_exec);
+            ctx->sm_exec = nullptr;
+            ctx->sm_sig.clear();
+        }
+        void *p = nullptr;
+        if (cudaMalloc(&p, total) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HSC_ERR_OOM, "cudaMalloc of the batch scratch failed%s");
+        }
+        e = cudaMemsetAsync(p, 0, (size_t)ctl_cap * sizeof(Control), ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemsetAsync");
+        ctx->sm_scratch = p;
+        ctx->sm_scratch_size = total;
+        ctx->sm_ctl_cap = ctl_cap;
+    }
+    if (!ctx->sm_upload) {
+        e = cudaEventCreateWithFlags(&ctx->sm_upload, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload event");
+    } else {
+        e = cudaEventSynchronize(ctx->sm_upload);  // the staging buffer is free again
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch upload wait");
+    }
+    if (tab_bytes > ctx->sm_host_size) {
+        if (ctx->sm_host) cudaFreeHost(ctx->sm_host);
+        ctx->sm_host = nullptr;
+        ctx->sm_host_size = 0;
+        if (cudaMallocHost(&ctx->sm_host, tab_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HSC_ERR_OOM, "pinned batch table staging%s");
+        }
+        ctx->sm_host_size = tab_bytes;
+    }
+    // ---- the tables
+    char *dev = static_cast<char *>(ctx->sm_scratch);
+    char *host = static_cast<char *>(ctx->sm_host);
+    BatchFrame *hf = reinterpret_cast<BatchFrame *>(host);
+    GramItem *hg = reinterpret_cast<GramItem *>(host + align_up(tab_frames));
+    PixItem *hp = reinterpret_cast<PixItem *>(host + align_up(tab_frames) + tab_gram);
+    int *hl = reinterpret_cast<int *>(host + align_up(tab_frames) + tab_gram + tab_pix);
+    int ig = 0, ip = 0, cta = 0, il = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        const hsc_frame &fr = frames[f];
+        const FrameLay &L = fl[(size_t)f];
+        const long N = (long)fr.H * fr.W;
+        BatchFrame b{};
+        b.cube = fr.cube;
+        b.I = fr.one_band ? fr.one_band : reinterpret_cast<float *>(dev + L.I);
+        b.P = fr.probs ? fr.probs : reinterpret_cast<float *>(dev + L.P);
+        b.O = fr.out_probs;
+        b.labels = fr.labels;
+        b.shift = reinterpret_cast<float *>(dev + L.shift);
+        b.gram_part = reinterpret_cast<float *>(dev + L.gram);
+        b.sum_part = reinterpret_cast<float *>(dev + L.sums);
+        b.C = reinterpret_cast<double *>(dev + L.C);
+        b.C2 = reinterpret_cast<float2 *>(dev + L.C2);
+        b.mu = reinterpret_cast<double *>(dev + L.mu);
+        b.v1 = reinterpret_cast<double *>(dev + L.v1);
+        b.lambda1 = reinterpret_cast<double *>(dev + L.lam);
+        b.v1f = reinterpret_cast<float *>(dev + L.v1f);
+        b.muf = reinterpret_cast<float *>(dev + L.muf);
+        b.ctl = reinterpret_cast<Control *>(dev) + f;
+        b.N = N;
+        b.H = fr.H;
+        b.W = fr.W;
+        b.n_part = L.parts;
+        b.per = (int)L.per;
+        b.vec = L.vec;
+        b.knn_cta0 = cta;
+        hf[f] = b;
+        const long total_chunks = (N + 63) / 64;
+        for (int j = 0; j < L.parts; ++j) {
+            GramItem g;
+            g.frame = f;
+            g.part = j;
+            g.c0 = (int)(j * L.per);
+            g.c1 = (int)std::min<long>((j + 1) * L.per, total_chunks);
+            hg[ig++] = g;
+        }
+        const int px = 4;  // groups of 4 pixels (16-byte loads when the frame allows them)
+        const long groups = (N + px - 1) / px;
+        const long gpi = kPixPerItem / px;
+        for (long g0 = 0; g0 < groups; g0 += gpi) {
+            PixItem it;
+            it.frame = f;
+            it.g0 = (int)g0;
+            it.g1 = (int)std::min(groups, g0 + gpi);
+            it.px = px;
+            hp[ip++] = it;
+        }
+        cta += fr.H * ((fr.W + 31) / 32);
+        if (N > 4096) hl[il++] = f;
+    }
+    e = cudaMemcpyAsync(dev + tab, host, tab_bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_upload, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch table upload");
+    const BatchFrame *df = reinterpret_cast<const BatchFrame *>(dev + tab);
+    const GramItem *dg = reinterpret_cast<const GramItem *>(dev + tab + align_up(tab_frames));
+    const PixItem *dp = reinterpret_cast<const PixItem *>(dev + tab + align_up(tab_frames) + tab_gram);
+    const int *dl = reinterpret_cast<const int *>(dev + tab + align_up(tab_frames) + tab_gram + tab_pix);
+    // ---- the launches: replayed from a graph when the launch configuration
+    // is the one captured (the tables above carry the frames' pointers)
+    const bool graph = (flags & HSC_BATCH_GRAPH) != 0;
+    std::vector<long long> sig;
+    if (graph) {
+        int lam_bits;
+        memcpy(&lam_bits, &params->lambda, sizeof lam_bits);
+        sig = {n_frames, B, (long long)flags, k, params->k, R, lam_bits, n_gram, n_pix, n_ctas,
+               max_rows, n_large, reinterpret_cast<long long>(model->w), reinterpret_cast<long long>(model->b),
+               reinterpret_cast<long long>(model->platt_a),
+               reinterpret_cast<long long>(model->platt_b),
+               reinterpret_cast<long long>(ctx->stream), reinterpret_cast<long long>(dev),
+               (long long)tab};
+        if (ctx->sm_exec && sig == ctx->sm_sig) {
+            e = cudaGraphLaunch(ctx->sm_exec, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphLaunch");
+            return HSC_OK;
+        }
+        e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamBeginCapture");
+    }
+    cudaStream_t st = ctx->stream;
+    hsc_ctx *tc = graph ? &g_untimed : ctx;  // stage events only outside a capture
+    {
+        StageTimer t(tc, HSC_STAGE_MOMENTS, 3, st);
+        e = hsc::launch_batch_moments(df, n_frames, dg, n_gram, dl, n_large, B, sm, st);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);
+        e = hsc::launch_batch_jacobi(df, n_frames, B, st);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(tc, HSC_STAGE_PROJECT_SVM, 1, st);
+        e = hsc::launch_batch_project_svm(df, dp, n_pix, B, model,
+                                          (flags & HSC_SVM_COUPLE_F64) != 0, st);
+    }
+    if (e == cudaSuccess && !(flags & HSC_CLASSIFY_RAW_I)) {
+        StageTimer t(tc, HSC_STAGE_NORMALIZE, 1, st);
+        e = hsc::launch_batch_normalize(df, dp, n_pix, st);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(tc, HSC_STAGE_KNN, 2, st);
+        e = hsc::launch_batch_knn(df, n_frames, n_ctas, k, params->k, R, params->lambda,
+                                  max_rows, reinterpret_cast<int2 *>(dev + redo),
+                                  (unsigned)n_px, st);
+    }
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) {
+            if (ctx->sm_exec) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(ctx->sm_exec, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(ctx->sm_exec);
+                    ctx->sm_exec = nullptr;
+                }
+            }
+            if (!ctx->sm_exec) e = cudaGraphInstantiate(&ctx->sm_exec, g, 0);
+            if (e == cudaSuccess) e = cudaGraphLaunch(ctx->sm_exec, ctx->stream);
+            if (e == cudaSuccess) ctx->sm_sig = sig;
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_classify_batch launch");
+    return HSC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frames, int B,
                               const hsc_svm_model *model, const hsc_knn_params *params,
                               unsigned flags)
@@ -875,7 +1186,8 @@ hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frame
     hsc_status st = check_ctx(ctx);
     if (st) return st;
     if (!frames || n_frames < 1) return fail(ctx, HSC_ERR_INVALID_ARG, "no frames%s");
-    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_BATCH_GRAPH | HSC_CLASSIFY_RAW_I))
+    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_BATCH_GRAPH | HSC_CLASSIFY_RAW_I |
+                            HSC_BATCH_POOL))
         return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     if ((st = check_model(ctx, model, B))) return st;
     const int k = model->n_classes;
@@ -888,6 +1200,9 @@ hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frame
         Layout L = make_layout(ctx, B, (long)fr.H * fr.W, k, true, true, true);
         slot_bytes = std::max(slot_bytes, L.total);
     }
+    if (!(flags & HSC_BATCH_POOL) && staged_batch_ok(frames, n_frames, B, params))
+        return classify_batch_staged(ctx, frames, n_frames, B, model, params,
+                                     flags & ~(unsigned)HSC_BATCH_POOL);
     const int S = std::min(n_frames, kMaxSlots);
     const size_t ctl_bytes = align_up((size_t)kMaxSlots * sizeof(Control));
     const size_t need = ctl_bytes + (size_t)S * slot_bytes;

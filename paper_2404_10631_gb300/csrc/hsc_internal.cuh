@@ -31,7 +31,8 @@ struct Control {
     unsigned long long jacobi_refine_cycles;  // SM clock cycles in the FP64 refinement
     unsigned knn_redo;        // pixels the pruned KNN left to its redo pass (reset by it)
     unsigned knn_redo_ctas;   // redo CTAs finished (reset with knn_redo)
-    unsigned pad[50];
+    unsigned knn_redo_list;   // stage-major batch: entries of the redo list (reset by its redo pass)
+    unsigned pad[49];
 };
 
 // Float <-> order-preserving unsigned key (for atomic min/max of floats).
@@ -73,6 +74,44 @@ struct PcaScratch {
     int n_part;
 };
 
+// One frame of a stage-major batch as its kernels see it (a device copy of a
+// table the host fills per call): the frame's inputs and outputs and its
+// share of the batch scratch, laid out like a single frame's.
+struct BatchFrame {
+    const float *cube;   // B x N, band-sequential
+    float *I;            // N: the projection, then the normalised map
+    float *P;            // k x N probabilities
+    float *O;            // k x N filtered probabilities (nullable)
+    int32_t *labels;     // N
+    float *shift;        // 2B
+    float *gram_part;    // n_part x B x B
+    float *sum_part;     // n_part x B
+    double *C;
+    float2 *C2;
+    double *mu, *v1, *lambda1;
+    float *v1f, *muf;
+    Control *ctl;
+    long N;
+    int H, W;
+    int n_part;          // partial Grams (tensor-core items of the frame)
+    int per;             // 64-pixel chunks per partial
+    int vec;             // 16-byte loads: cube 16-byte aligned and N % 4 == 0
+    int knn_cta0;        // first CTA of the frame in the batched KNN grid
+};
+
+// A tensor-core Gram work item: frame, partial index, chunk range [c0, c1).
+// A frame's items are the pixel ranges a single-frame launch gives its CTAs,
+// so batched and single-frame partials are the same numbers.
+struct GramItem {
+    int frame, part, c0, c1;
+};
+
+// A projection/SVM (and normalisation) work item: frame, groups [g0, g1) of
+// px = 4 pixels (16-byte loads when the frame's vec flag allows them).
+struct PixItem {
+    int frame, g0, g1, px;
+};
+
 // ---- launchers (each returns cudaGetLastError() of its launches) ----
 
 // Pass 1 over the cube: pilot shift, partial Gram + sums, FP64 reduction into
@@ -82,8 +121,8 @@ struct PcaScratch {
 // Launch parameters that change only the speed of a pass, never its results
 // (an autotuner picks them per frame shape): the tensor-core Gram's TMA
 // staging depth (3 or 4; 0 = default), and the projection/SVM pass's pixels
-// per thread (1 or 4; 0 = 4 when the cube allows 16-byte loads) and CTAs per
-// SM of its grid-stride launch (0 = 8).
+// per thread (1 or 4; 0 = 4, with 16-byte loads when the cube allows them)
+// and CTAs per SM of its grid-stride launch (0 = 8).
 struct Tuning {
     int gram_stages = 0;
     int svm_px = 0;
@@ -93,10 +132,35 @@ struct Tuning {
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s,
                            int sm_count, cudaStream_t st, bool force_simt = false,
                            int gram_stages = 0);
-bool gram_tc_supported(const float *cube, int B, long N);
+bool gram_tc_supported(const float *cube, int B, long N);  // through a tensor map
+bool gram_tc_usable(const float *cube, int B, long N);     // tensor map or work items
 int moments_kernel_count(const float *cube, int B, long N, bool force_simt = false);
 cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s,
                            cudaStream_t st, int stages = 0);
+// Chunks per partial Gram of the tensor-core path for a frame whose scratch
+// holds n_part partials, and the number of partials that receive chunks.
+long gram_tc_per(long N, int n_part, int sm_count);
+int gram_tc_parts(long N, long per);
+
+// ---- stage-major batch (B <= 128): one launch per stage over every frame.
+// frames / items are device tables; results per frame are bit-identical to
+// the single-frame launches.
+cudaError_t launch_gram_items(const BatchFrame *frames, const GramItem *items, int n_items, int B,
+                              int sm_count, cudaStream_t st);
+// large: indices of the frames of more than 4096 pixels (their pilot takes a
+// CTA per band), n_large of them.
+cudaError_t launch_batch_moments(const BatchFrame *frames, int n_frames, const GramItem *items,
+                                 int n_items, const int *large, int n_large, int B, int sm_count,
+                                 cudaStream_t st);
+cudaError_t launch_batch_jacobi(const BatchFrame *frames, int n_frames, int B, cudaStream_t st);
+cudaError_t launch_batch_project_svm(const BatchFrame *frames, const PixItem *items, int n_items,
+                                     int B, const hsc_svm_model *model, bool couple_f64,
+                                     cudaStream_t st);
+cudaError_t launch_batch_normalize(const BatchFrame *frames, const PixItem *items, int n_items,
+                                   cudaStream_t st);
+cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas, int k, int K,
+                             int R, float lambda, int max_rows, int2 *redo_list,
+                             unsigned redo_cap, cudaStream_t st);
 
 // Jacobi eigen-decomposition of C, FP64 refinement of the leading vector,
 // sign rule; writes v1, lambda1, v1f, muf and resets the I min/max keys.

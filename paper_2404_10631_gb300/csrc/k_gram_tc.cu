@@ -55,6 +55,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr float kFp16Max = 65504.f;
 constexpr int kFbAcc = 8;                // FP32 recompute: entries per thread per pass
 constexpr int kFbLd = kChunk + 1;        // FP32 recompute: padded staging row
+constexpr int kNarrowConvWarps = 8;      // B <= 128: converter warps (two per band row)
 
 // B <= 128: 128 converted rows, 4 staging stages, 2 operand stages, three
 // hi.hi^T accumulators (columns 0, 128, 256) and the cross terms at 384, 8
@@ -66,7 +67,7 @@ struct Cfg {
     static constexpr int kStages = kSt;
     static constexpr int kOpStages = kWide ? 1 : 2;
     static constexpr int kAccHH = kWide ? 1 : 3;
-    static constexpr int kConvWarps = kWide ? 4 : 8;
+    static constexpr int kConvWarps = kWide ? 4 : kNarrowConvWarps;
     static constexpr int kThreads = 64 + 32 * kConvWarps;
     static constexpr int kParts = kConvWarps / 4;           // threads per band row
     static constexpr uint32_t kXCol = kWide ? 256u : 384u;
@@ -230,20 +231,153 @@ __device__ __forceinline__ void convert_unit(const float4 xa, const float4 xb, f
                     pack_half2(l[6], l[7]));
 }
 
+// The MMAs of one chunk: 4 K-steps of hi.hi^T into the hi.hi^T accumulator
+// j % kAccHH (j = the chunk's index within its segment) and of hi.lo^T and
+// lo.hi^T into the cross-term accumulator; the first use of an accumulator
+// in a segment overwrites it.
+template <int kAccHH, uint32_t kXCol>
+__device__ __forceinline__ void issue_chunk_mmas(uint32_t tmem, uint32_t hi, uint32_t lo,
+                                                 int row_base, int col_base, uint32_t idesc,
+                                                 int j)
+{
+    // A: this launch's 128 rows; B: its Nn columns (rows of the tile)
+    const uint64_t ah = smem_desc(hi + (uint32_t)row_base * 128u);
+    const uint64_t al = smem_desc(lo + (uint32_t)row_base * 128u);
+    const uint64_t bh = smem_desc(hi + (uint32_t)col_base * 128u);
+    const uint64_t bl = smem_desc(lo + (uint32_t)col_base * 128u);
+    const uint32_t d_hh = tmem + (uint32_t)(j % kAccHH) * 128u;
+    const uint32_t d_x = tmem + kXCol;
+#pragma unroll
+    for (int k = 0; k < kChunk / 16; ++k) {
+        const uint64_t off = (uint64_t)((k * 32) >> 4);  // 16 fp16 = 32 bytes along K
+        mma_f16(d_hh, ah + off, bh + off, idesc, (j >= kAccHH || k > 0) ? 1u : 0u);
+        mma_f16(d_x, ah + off, bl + off, idesc, (j > 0 || k > 0) ? 1u : 0u);
+        mma_f16(d_x, al + off, bh + off, idesc, 1u);
+    }
+}
+
+// Epilogue of one segment, run by each converter warp: waits for the
+// segment's MMAs, reads its accumulators (the cross terms plus the n_acc
+// hi.hi^T accumulators the segment used, the two warps of a TMEM lane
+// quarter taking alternate 16-column blocks), removes the band scales and
+// writes (accumulate = false) or adds them into the partial Gram out, entry
+// (b, c) at c * B + b, for c >= b only: the reduction reads nothing else.
+template <int kAccHH, int kParts, uint32_t kXCol>
+__device__ __forceinline__ bool drain_segment(uint32_t tmem, int warp, int lane, int B, int Nn,
+                                              int row_base, int col_base, int n_acc,
+                                              bool accumulate, const float *isc, float *out,
+                                              uint64_t *done, uint32_t parity, uint64_t *drained,
+                                              volatile int *abort_p)
+{
+    const int q = warp & 3;             // TMEM lane quarter this warp may read
+    const int cpart = (warp - 2) >> 2;  // which alternate 16-column blocks it drains
+    const int mlo = row_base + q * 32;  // the warp's first accumulator row
+    const int m = mlo + lane;           // the band of this lane's row
+    const float isc_m = m < B ? isc[m] : 0.f;
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(done, parity, abort_p));
+    tc_fence_after();
+    for (int c0 = 16 * cpart; c0 < Nn; c0 += 16 * kParts) {
+        if (col_base + c0 + 15 < mlo) continue;  // below the diagonal for the whole warp
+        float v[16];
+        if (ok) {
+            tmem_ld16(lane_addr + kXCol + (uint32_t)c0, v);  // cross terms
+            for (int a = 0; a < kAccHH && a < n_acc; ++a) {
+                float w[16];
+                tmem_ld16(lane_addr + (uint32_t)a * 128u + (uint32_t)c0, w);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] += w[e];
+            }
+        }
+        if (m < B) {
+            // transposed (G symmetric): lanes = consecutive rows m hit
+            // consecutive words; the 16 earlier values are loaded together,
+            // then added and stored
+            float prev[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int col = col_base + c0 + e;
+                prev[e] = (accumulate && col < B && col >= m) ? out[(size_t)col * B + m] : 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int col = col_base + c0 + e;
+                if (col < B && col >= m)
+                    out[(size_t)col * B + m] = prev[e] + (ok ? v[e] * (isc_m * isc[col]) : 0.f);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(drained);
+    return ok;
+}
+
+// FP32-pipe recompute of one partial (rows row_base.., columns col_base..
+// col_base+Nn-1) and, when write_sums, its band sums, over pixels [p_begin,
+// p_end): 64-pixel chunks of x - s staged in ys (B x kFbLd floats), kFbAcc
+// entries per thread per pass. Every thread of the CTA calls it.
+__device__ void fp32_recompute(const float *__restrict__ cube, int B, long N,
+                               const float *sh, int row_base, int col_base, int Nn,
+                               int write_sums, long p_begin, long p_end, float *ys,
+                               float *__restrict__ out, float *__restrict__ sums)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nrow = B - row_base < kM ? B - row_base : kM;
+    const int ncol = B - col_base < Nn ? B - col_base : Nn;
+    const int ent = nrow * ncol;
+    for (int e0 = 0; e0 < ent; e0 += nthr * kFbAcc) {
+        float acc[kFbAcc];
+#pragma unroll
+        for (int k = 0; k < kFbAcc; ++k) acc[k] = 0.f;
+        for (long p0 = p_begin; p0 < p_end; p0 += kChunk) {
+            __syncthreads();
+            for (int i = tid; i < B * kChunk; i += nthr) {
+                const int b = i / kChunk, j = i % kChunk;
+                const long p = p0 + j;
+                ys[b * kFbLd + j] = p < p_end ? cube[(size_t)b * N + p] - sh[b] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kFbAcc; ++k) {
+                const int e = e0 + k * nthr + tid;
+                if (e < ent) {
+                    const float *ya = ys + (row_base + e / ncol) * kFbLd;
+                    const float *yb = ys + (col_base + e % ncol) * kFbLd;
+                    float a = acc[k];
+                    for (int j = 0; j < kChunk; ++j) a = fmaf(ya[j], yb[j], a);
+                    acc[k] = a;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kFbAcc; ++k) {
+            const int e = e0 + k * nthr + tid;
+            if (e < ent) out[(size_t)(col_base + e % ncol) * B + row_base + e / ncol] = acc[k];
+        }
+    }
+    if (write_sums)
+        for (int b = tid; b < B; b += nthr) {
+            float t = 0.f;
+            for (long p = p_begin; p < p_end; ++p) t += cube[(size_t)b * N + p] - sh[b];
+            sums[b] = t;
+        }
+}
+
 // Rows row_base..row_base+127 of this launch's block of G times columns
 // col_base..col_base+Nn-1 (Nn a multiple of 16); band sums when write_sums.
 // shift: 2B floats, the pilot shift s_b then the scale c_b of each band.
+// CTA i takes chunks [i * per, (i + 1) * per).
 template <bool kWide, int kSt>
 __global__ void __launch_bounds__(Cfg<kWide, kSt>::kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ cube, int B,
                int row_base, int col_base, int Nn, int write_sums, long N, long total_chunks,
-               const float *__restrict__ shift, float *__restrict__ gram_part,
+               long per, const float *__restrict__ shift, float *__restrict__ gram_part,
                float *__restrict__ sum_part, Control *ctl)
 {
     using G = Cfg<kWide, kSt>;
     constexpr int kRows = G::kRows, kStages = G::kStages, kOpStages = G::kOpStages;
     constexpr int kAccHH = G::kAccHH, kThreads = G::kThreads, kParts = G::kParts;
-    constexpr int kConv = 32 * G::kConvWarps;
     constexpr uint32_t kBoxBytes = G::kBoxBytes, kStageBytes = G::kStageBytes;
     constexpr uint32_t kOpBytes = G::kOpBytes;
     extern __shared__ unsigned char smem_raw[];
@@ -255,10 +389,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, range_flag;
     __shared__ float sh[kRows], sc[kRows], isc[kRows];
-    __shared__ float bsum_sh[kParts > 1 ? kRows : 1];
+    __shared__ float bsum_sh[kParts > 1 ? kParts - 1 : 1][kRows];  // parts 1.. of the band sums
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long per = (total_chunks + gridDim.x - 1) / gridDim.x;
     const long c_begin = (long)blockIdx.x * per;
     long c_end = c_begin + per;
     if (c_end > total_chunks) c_end = total_chunks;
@@ -344,26 +477,12 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
                     ++seg;
                     seg_start = i;
                 }
-                const int j = i - seg_start;  // chunk within the segment
                 const int t = i % kOpStages;
                 if (!mbar_wait(&bars.op_full[t], (i / kOpStages) & 1, abort_p)) break;
                 tc_fence_after();
                 const uint32_t hi = smem_u32(ops + t * 2 * kOpBytes);
-                const uint32_t lo = hi + kOpBytes;
-                // A: this launch's 128 rows; B: its Nn columns (rows of the tile)
-                const uint64_t ah = smem_desc(hi + (uint32_t)row_base * 128u);
-                const uint64_t al = smem_desc(lo + (uint32_t)row_base * 128u);
-                const uint64_t bh = smem_desc(hi + (uint32_t)col_base * 128u);
-                const uint64_t bl = smem_desc(lo + (uint32_t)col_base * 128u);
-                const uint32_t d_hh = tmem + (uint32_t)(j % kAccHH) * 128u;
-                const uint32_t d_x = tmem + G::kXCol;
-#pragma unroll
-                for (int k = 0; k < kChunk / 16; ++k) {
-                    const uint64_t off = (uint64_t)((k * 32) >> 4);  // 16 fp16 = 32 bytes along K
-                    mma_f16(d_hh, ah + off, bh + off, idesc, (j >= kAccHH || k > 0) ? 1u : 0u);
-                    mma_f16(d_x, ah + off, bl + off, idesc, (j > 0 || k > 0) ? 1u : 0u);
-                    mma_f16(d_x, al + off, bh + off, idesc, 1u);
-                }
+                issue_chunk_mmas<kAccHH, G::kXCol>(tmem, hi, hi + kOpBytes, row_base, col_base,
+                                                   idesc, i - seg_start);
                 mma_commit(&bars.op_empty[t]);
             }
             mma_commit(&bars.done);  // arrives when every MMA issued above has completed
@@ -390,49 +509,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
             }
         }
         float *out = gram_part + (size_t)blockIdx.x * B * B;
-        const int q = warp & 3;           // TMEM lane quarter this warp may read
-        const int cpart = (warp - 2) >> 2;  // which alternate 16-column blocks it drains
-        const int m = row_base + q * 32 + lane;  // the band of this accumulator row
-        const float isc_m = m < B ? isc[m] : 0.f;
-        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
-        // accumulators of segment seg (chunks seg_start..i-1) -> out (= or +=)
         auto drain = [&](int seg, int seg_start, int i) -> bool {
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars.done, seg & 1, abort_p));
-            tc_fence_after();
-            for (int c0 = 16 * cpart; c0 < Nn; c0 += 16 * kParts) {
-                float v[16];
-                if (ok) {
-                    tmem_ld16(lane_addr + G::kXCol + (uint32_t)c0, v);  // cross terms
-                    for (int a = 0; a < kAccHH && a < i - seg_start; ++a) {
-                        float w[16];
-                        tmem_ld16(lane_addr + (uint32_t)a * 128u + (uint32_t)c0, w);
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) v[e] += w[e];
-                    }
-                }
-                if (m < B) {
-                    // transposed (G symmetric): lanes = consecutive rows m hit
-                    // consecutive words; the 16 earlier values are loaded
-                    // together, then added and stored
-                    float prev[16];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int col = col_base + c0 + e;
-                        prev[e] = (seg > 0 && col < B) ? out[(size_t)col * B + m] : 0.f;
-                    }
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int col = col_base + c0 + e;
-                        if (col < B)
-                            out[(size_t)col * B + m] =
-                                prev[e] + (ok ? v[e] * (isc_m * isc[col]) : 0.f);
-                    }
-                }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bars.drained);
-            return ok;
+            return drain_segment<kAccHH, kParts, G::kXCol>(tmem, warp, lane, B, Nn, row_base,
+                                                           col_base, i - seg_start, seg > 0, isc,
+                                                           out, &bars.done, seg & 1,
+                                                           &bars.drained, abort_p);
         };
         int seg = 0, seg_start = 0, done_i = 0;
         for (int i = 0; i < nchunks; ++i) {
@@ -490,15 +571,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
         for (int r = 0; r < kRpt; ++r) bad |= !isfinite(bsum[r]);
         if (bad) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
         if (!(ymax < kFp16Max)) range_flag = 1;
-        // ---------------- the last segment (or zeros when there are no chunks)
-        if (nchunks > 0 && done_i == nchunks) {
-            drain(seg, seg_start, nchunks);
-        } else if (nchunks == 0 && m < B) {
-            for (int col = col_base + 16 * cpart; col < col_base + Nn && col < B; ++col)
-                if (((col - col_base) >> 4) % kParts == cpart) out[(size_t)col * B + m] = 0.f;
-        }
-        if (kParts > 1 && part == 1 && write_sums)
-            for (int r = 0; r < kRpt; ++r) bsum_sh[b0 + 128 * r] = bsum[r];
+        // ---------------- the last segment
+        if (nchunks > 0 && done_i == nchunks) drain(seg, seg_start, nchunks);
+        if (kParts > 1 && part >= 1 && write_sums)
+            for (int r = 0; r < kRpt; ++r) bsum_sh[part - 1][b0 + 128 * r] = bsum[r];
     }
     if (*abort_p && tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
     if (tid == 32 && ncommit > 0) {
@@ -519,60 +595,410 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
 #pragma unroll
         for (int r = 0; r < kRpt; ++r) {
             const int b = b0 + 128 * r;
-            if (b < B)
-                sum_part[(size_t)blockIdx.x * B + b] =
-                    (kParts > 1 ? bsum[r] + bsum_sh[b] : bsum[r]) * isc[b];
+            if (b < B) {
+                float t = bsum[r];
+                for (int q = 1; q < kParts; ++q) t += bsum_sh[q - 1][b];
+                sum_part[(size_t)blockIdx.x * B + b] = t * isc[b];
+            }
         }
     }
     if (!range_flag || *abort_p || nchunks == 0) return;
 
-    // ---------------- FP32 recompute of this CTA's block (rare): 64-pixel
-    // chunks of x - s staged in the TMA ring, kFbAcc entries per thread per
-    // pass over the CTA's pixels (which L2 still holds)
+    // ---------------- FP32 recompute of this CTA's block (rare), over the
+    // CTA's pixels (which L2 still holds), staged in the TMA ring
     __syncthreads();
-    float *ys = reinterpret_cast<float *>(staging);
-    float *out = gram_part + (size_t)blockIdx.x * B * B;
-    const long p_begin = c_begin * kChunk;
     const long p_end = c_end * kChunk < N ? c_end * kChunk : N;
-    const int nrow = B - row_base < kM ? B - row_base : kM;
-    const int ncol = B - col_base < Nn ? B - col_base : Nn;
-    const int ent = nrow * ncol;
-    for (int e0 = 0; e0 < ent; e0 += kThreads * kFbAcc) {
-        float acc[kFbAcc];
+    fp32_recompute(cube, B, N, sh, row_base, col_base, Nn, write_sums, c_begin * kChunk, p_end,
+                   reinterpret_cast<float *>(staging), gram_part + (size_t)blockIdx.x * B * B,
+                   sum_part + (size_t)blockIdx.x * B);
+}
+
+// ---------------------------------------------------------------- work items
+
+// L2 policy for the cube's chunks: read once, evicted first, so that the
+// partial Grams written meanwhile stay in L2 for the reduction.
+__device__ __forceinline__ uint64_t evict_first_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float *src, bool in, uint64_t pol)
+{
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2, %3;" ::"r"(dst),
+                 "l"(src), "r"(in ? 4 : 0), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float *src, bool in, uint64_t pol)
+{
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2, %3;" ::"r"(dst),
+                 "l"(src), "r"(in ? 16 : 0), "l"(pol)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int kPending>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(kPending) : "memory");
+}
+
+// Named barrier of the converter warps that also ORs a predicate over them.
+__device__ __forceinline__ bool conv_bar_or(int nthreads, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void conv_bar(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// One 64-pixel chunk (pixels p0.., every band row b < B) into a staging slot
+// in the layout a 128-byte-swizzled TMA box would give it (two 32-pixel
+// boxes; in each, band row b at b * 128 with its 16-byte units permuted by
+// b & 7), issued by the kConv converter threads cv: 16-byte copies (row
+// b = f / 16, 4-pixel unit f % 16 for f = cv + kConv i) when the frame allows
+// them, else 4-byte copies (rows cv / 32 + (kConv / 32) i, pixels lane and
+// lane + 32). Pixels at or past N are zero-filled.
+template <uint32_t kBoxBytes, int kConv>
+__device__ __forceinline__ void fetch_chunk(unsigned char *slot, const float *cube, long N,
+                                            bool vec, long p0, int B, int cv)
+{
+    constexpr int kW = kConv / 32;
+    const uint32_t sbase = smem_u32(slot);
+    const uint64_t pol = evict_first_policy();
+    if (vec) {
 #pragma unroll
-        for (int k = 0; k < kFbAcc; ++k) acc[k] = 0.f;
-        for (long p0 = p_begin; p0 < p_end; p0 += kChunk) {
-            __syncthreads();
-            for (int i = tid; i < B * kChunk; i += kThreads) {
-                const int b = i / kChunk, j = i % kChunk;
-                const long p = p0 + j;
-                ys[b * kFbLd + j] = p < p_end ? cube[(size_t)b * N + p] - sh[b] : 0.f;
+        for (int i = 0; i < 2048 / kConv; ++i) {
+            const int f = cv + kConv * i;
+            const int b = f >> 4, u4 = f & 15;
+            if (b < B) {
+                const long p = p0 + 4 * u4;
+                const bool in = p < N;
+                cp_async16(sbase + (uint32_t)(u4 >> 3) * kBoxBytes + (uint32_t)b * 128u +
+                               (uint32_t)(((u4 & 7) ^ (b & 7)) << 4),
+                           in ? cube + (size_t)b * N + p : cube, in, pol);
             }
-            __syncthreads();
+        }
+    } else {
+        const int w = cv >> 5, lane = cv & 31;
 #pragma unroll
-            for (int k = 0; k < kFbAcc; ++k) {
-                const int e = e0 + k * kThreads + tid;
-                if (e < ent) {
-                    const float *ya = ys + (row_base + e / ncol) * kFbLd;
-                    const float *yb = ys + (col_base + e % ncol) * kFbLd;
-                    float a = acc[k];
-                    for (int j = 0; j < kChunk; ++j) a = fmaf(ya[j], yb[j], a);
-                    acc[k] = a;
+        for (int i = 0; i < 128 / kW; ++i) {
+            const int b = w + kW * i;
+            if (b < B) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const long p = p0 + lane + 32 * h;
+                    const bool in = p < N;
+                    cp_async4(sbase + (uint32_t)h * kBoxBytes + (uint32_t)b * 128u +
+                                  (uint32_t)(((lane >> 2) ^ (b & 7)) << 4) + (uint32_t)(lane & 3) * 4u,
+                              in ? cube + (size_t)b * N + p : cube, in, pol);
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < kFbAcc; ++k) {
-            const int e = e0 + k * kThreads + tid;
-            if (e < ent) out[(size_t)(col_base + e % ncol) * B + row_base + e / ncol] = acc[k];
-        }
     }
-    if (write_sums)
-        for (int b = tid; b < B; b += kThreads) {
-            float t = 0.f;
-            for (long p = p_begin; p < p_end; ++p) t += cube[(size_t)b * N + p] - sh[b];
-            sum_part[(size_t)blockIdx.x * B + b] = t;
+}
+
+constexpr int kMaxLocalItems = 256;  // work items per CTA (the range flags' bitmask)
+
+// The frame fields the Gram items need.
+struct ItemFrame {
+    const float *cube;
+    const float *shift;
+    float *gram_part, *sum_part;
+    Control *ctl;
+    long N;
+    int vec;
+};
+
+__device__ __forceinline__ ItemFrame item_frame(const BatchFrame &one,
+                                                const BatchFrame *__restrict__ frames, int f)
+{
+    const BatchFrame *fr = frames ? frames + f : &one;
+    ItemFrame r;
+    r.cube = fr->cube;
+    r.shift = fr->shift;
+    r.gram_part = fr->gram_part;
+    r.sum_part = fr->sum_part;
+    r.ctl = fr->ctl;
+    r.N = fr->N;
+    r.vec = fr->vec;
+    return r;
+}
+
+__device__ __forceinline__ GramItem get_item(const BatchFrame &one,
+                                             const GramItem *__restrict__ items, int it)
+{
+    if (items) return items[it];
+    GramItem g;
+    const long total = (one.N + kChunk - 1) / kChunk;
+    g.frame = 0;
+    g.part = it;
+    g.c0 = it * one.per;
+    g.c1 = (int)((long)(it + 1) * one.per < total ? (long)(it + 1) * one.per : total);
+    return g;
+}
+
+// Work-item form of the B <= 128 Gram (stage-major batches, and single
+// frames the tensor map cannot describe: N % 4 != 0 or an unaligned cube).
+// A persistent CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; each
+// item is a frame's chunk range, the range gram_tc_kernel's CTA would take,
+// and gets the same partial Gram and sums, bit for bit: the same conversion,
+// MMA sequence, segments and epilogue. With items == nullptr the items are
+// the chunk ranges of the single frame one (one.per chunks each).
+// Warp 1 owns TMEM and issues the MMAs; the 8 converter warps fetch their
+// chunks themselves with asynchronous copies, kSt - 1 chunks ahead, into the
+// staging layout the TMA would write, and one named barrier per chunk among
+// them orders the copies with their readers (and makes every exit uniform).
+template <int kSt>
+__global__ void __launch_bounds__(Cfg<false, kSt>::kThreads, 1)
+gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames,
+                     const GramItem *__restrict__ items, int n_items, int B)
+{
+    using G = Cfg<false, kSt>;
+    constexpr int kStages = G::kStages, kOpStages = G::kOpStages, kAccHH = G::kAccHH;
+    constexpr int kParts = G::kParts, kConv = 32 * G::kConvWarps;
+    constexpr uint32_t kBoxBytes = G::kBoxBytes, kStageBytes = G::kStageBytes;
+    constexpr uint32_t kOpBytes = G::kOpBytes;
+    constexpr int kUnits = 8 / kParts;  // 8-pixel fp16 units per thread per chunk
+    static_assert(kParts >= 2 && kConv == 128 * kParts, "kParts converter threads per band row");
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char *staging = base;
+    unsigned char *ops = base + kStages * kStageBytes;
+    __shared__ Bars<false, kSt> bars;  // full / empty unused: copies complete by groups
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag, range_item;
+    __shared__ float isc_sh[128], bsum_sh[kParts - 1][128];
+    __shared__ unsigned long long flagged[kMaxLocalItems / 64];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Np = (B + 15) / 16 * 16;
+
+    if (tid == 0) {
+        for (int t = 0; t < kOpStages; ++t) {
+            mbar_init(&bars.op_full[t], G::kConvWarps);
+            mbar_init(&bars.op_empty[t], 1);
         }
+        mbar_init(&bars.done, 1);
+        mbar_init(&bars.drained, G::kConvWarps);
+        abort_flag = 0;
+        for (int i = 0; i < kMaxLocalItems / 64; ++i) flagged[i] = 0ull;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const int cv = tid - 64;          // converter index
+    const int b0 = cv & 127;          // its band row
+    const int part = cv >> 7;         // which 32-pixel box of a chunk it converts
+    const int sw = b0 & 7;
+    const int u0 = part * kUnits;     // its 8-pixel fp16 units
+    if (warp >= 2 && b0 >= B)  // rows beyond B stay zero in every operand stage
+        for (int t = 0; t < kOpStages; ++t)
+            for (int u = u0; u < u0 + kUnits; ++u) {
+                const uint4 z = make_uint4(0, 0, 0, 0);
+                *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + b0 * 128 + ((u ^ sw) << 4)) = z;
+                *reinterpret_cast<uint4 *>(ops + t * 2 * kOpBytes + kOpBytes + b0 * 128 +
+                                           ((u ^ sw) << 4)) = z;
+            }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int *abort_p = &abort_flag;
+    int ncommit = 0;
+
+    if (warp == 1) {
+        // ---------------- MMA issuer over every chunk of every item
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | ((uint32_t)(Np >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            long g = 0;  // chunks so far
+            int s = 0;   // segments closed so far
+            bool stop = false;
+            for (int it = blockIdx.x; it < n_items && !stop; it += gridDim.x) {
+                const GramItem item = get_item(one, items, it);
+                const int nch = item.c1 - item.c0;
+                for (int ji = 0; ji < nch; ++ji, ++g) {
+                    const int j = ji % G::kSegChunks;
+                    if (j == 0 && g > 0) {  // a new segment: the last one drained?
+                        mma_commit(&bars.done);
+                        ++ncommit;
+                        if (!mbar_wait(&bars.drained, s & 1, abort_p)) {
+                            stop = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        ++s;
+                    }
+                    const int t = (int)(g % kOpStages);
+                    if (!mbar_wait(&bars.op_full[t], (uint32_t)((g / kOpStages) & 1), abort_p)) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t hi = smem_u32(ops + t * 2 * kOpBytes);
+                    issue_chunk_mmas<kAccHH, G::kXCol>(tmem, hi, hi + kOpBytes, 0, 0, idesc, j);
+                    mma_commit(&bars.op_empty[t]);
+                }
+            }
+            if (g > 0) {
+                mma_commit(&bars.done);
+                ++ncommit;
+            }
+        }
+    } else if (warp >= 2) {
+        // ---------------- converters: copies, conversion, epilogue
+        // prefetch cursor: chunk pf_j of item pf_it
+        int pf_it = blockIdx.x, pf_j = 0, pf_n = 0, pf_c0 = 0;
+        ItemFrame pf{};
+        auto pf_item = [&]() {
+            if (pf_it < n_items) {
+                const GramItem gi = get_item(one, items, pf_it);
+                pf = item_frame(one, frames, gi.frame);
+                pf_c0 = gi.c0;
+                pf_n = gi.c1 - gi.c0;
+            }
+        };
+        auto fetch_next = [&](long slot) {
+            if (pf_it < n_items) {
+                fetch_chunk<kBoxBytes, kConv>(staging + slot * kStageBytes, pf.cube, pf.N,
+                                              pf.vec != 0, (long)(pf_c0 + pf_j) * kChunk, B, cv);
+                if (++pf_j == pf_n) {
+                    pf_j = 0;
+                    pf_it += gridDim.x;
+                    pf_item();
+                }
+            }
+            cp_async_commit();  // one group per chunk slot, empty past the last chunk
+        };
+        pf_item();
+        for (int k = 0; k < kStages - 1; ++k) fetch_next(k);
+
+        long g = 0;
+        int s = 0;
+        bool stop = false;
+        for (int l = 0, it = blockIdx.x; it < n_items && !stop; ++l, it += gridDim.x) {
+            const GramItem item = get_item(one, items, it);
+            const ItemFrame fr = item_frame(one, frames, item.frame);
+            const float c = b0 < B ? fr.shift[B + b0] : 1.f;
+            const float nsc = -(b0 < B ? fr.shift[b0] : 0.f) * c;  // exact: c is a power of two
+            if (cv < 128) isc_sh[cv] = __frcp_rn(cv < B ? fr.shift[B + cv] : 1.f);
+            if (cv == 0) range_item = 0;
+            float *out = fr.gram_part + (size_t)item.part * B * B;
+            float bsum = 0.f, ymax = 0.f;
+            const int nch = item.c1 - item.c0;
+            for (int ji = 0; ji < nch; ++ji, ++g) {
+                const int slot = (int)(g % kStages), t = (int)(g % kOpStages);
+                cp_async_wait<kStages - 2>();  // this thread's copies of chunk g landed
+                bool ok = true;
+                if (g >= kOpStages)
+                    ok = mbar_wait(&bars.op_empty[t], (uint32_t)(((g / kOpStages) - 1) & 1), abort_p);
+                // every converter's copies of chunk g landed and chunk g - 1 is converted
+                if (conv_bar_or(kConv, !ok || *abort_p)) {
+                    stop = true;
+                    break;
+                }
+                fetch_next((g + kStages - 1) % kStages);
+                const long px0 = (long)(item.c0 + ji) * kChunk;
+                const bool tail = px0 + kChunk > fr.N;
+                const int lim = tail ? (int)(fr.N - px0) : kChunk;
+                if (b0 < B) {
+                    const unsigned char *st = staging + slot * kStageBytes;
+                    unsigned char *ohi = ops + t * 2 * kOpBytes + b0 * 128;
+                    unsigned char *olo = ohi + kOpBytes;
+#pragma unroll
+                    for (int uu = 0; uu < kUnits; ++uu) {
+                        const int u = u0 + uu;
+                        const int box = u >> 2;
+                        const int j0 = (u & 3) * 2;
+                        const unsigned char *row = st + box * kBoxBytes + b0 * 128;
+                        const float4 xa = *reinterpret_cast<const float4 *>(row + ((j0 ^ sw) << 4));
+                        const float4 xb =
+                            *reinterpret_cast<const float4 *>(row + (((j0 + 1) ^ sw) << 4));
+                        uint4 hv, lv;
+                        if (tail)
+                            convert_unit<true>(xa, xb, c, nsc, u, lim, bsum, ymax, hv, lv);
+                        else
+                            convert_unit<false>(xa, xb, c, nsc, u, lim, bsum, ymax, hv, lv);
+                        *reinterpret_cast<uint4 *>(ohi + ((u ^ sw) << 4)) = hv;
+                        *reinterpret_cast<uint4 *>(olo + ((u ^ sw) << 4)) = lv;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.op_full[t]);
+                const int j = ji % G::kSegChunks;
+                if (j == G::kSegChunks - 1 || ji == nch - 1) {
+                    drain_segment<kAccHH, kParts, G::kXCol>(tmem, warp, lane, B, Np, 0, 0, j + 1,
+                                                            ji >= G::kSegChunks, isc_sh, out,
+                                                            &bars.done, s & 1, &bars.drained,
+                                                            abort_p);
+                    ++s;
+                }
+            }
+            if (stop) break;
+            // end of the item: flags and band sums
+            if (!isfinite(bsum)) atomicOr(&fr.ctl->status, ST_NONFINITE_CUBE);
+            if (!(ymax < kFp16Max)) range_item = 1;
+            if (part >= 1) bsum_sh[part - 1][b0] = bsum;
+            conv_bar(kConv);
+            if (part == 0 && b0 < B) {
+                float t = bsum;
+                for (int q = 1; q < kParts; ++q) t += bsum_sh[q - 1][b0];
+                fr.sum_part[(size_t)item.part * B + b0] = t * isc_sh[b0];
+            }
+            if (cv == 0 && range_item && l < kMaxLocalItems) flagged[l >> 6] |= 1ull << (l & 63);
+            conv_bar(kConv);  // isc_sh, bsum_sh and range_item are the next item's now
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    if (*abort_p && tid == 0) {
+        Control *ctl = frames ? frames[0].ctl : one.ctl;
+        atomicOr(&ctl->status, ST_TIMEOUT);
+    }
+    if (tid == 32 && ncommit > 0) {
+        for (uint32_t k = 0; k < kWaitLimit; ++k)
+            if (mbar_try(&bars.done, (ncommit - 1) & 1)) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+    if (*abort_p) return;
+    // ---------------- FP32 recompute of the items whose values left FP16's range (rare)
+    for (int l = 0, it = blockIdx.x; it < n_items && l < kMaxLocalItems; ++l, it += gridDim.x) {
+        if (!((flagged[l >> 6] >> (l & 63)) & 1ull)) continue;
+        const GramItem item = get_item(one, items, it);
+        const ItemFrame fr = item_frame(one, frames, item.frame);
+        const long p_end = (long)item.c1 * kChunk < fr.N ? (long)item.c1 * kChunk : fr.N;
+        fp32_recompute(fr.cube, B, fr.N, fr.shift, 0, 0, Np, 1, (long)item.c0 * kChunk, p_end,
+                       reinterpret_cast<float *>(staging), fr.gram_part + (size_t)item.part * B * B,
+                       fr.sum_part + (size_t)item.part * B);
+    }
 }
 
 // cuTensorMapEncodeTiled, fetched from the driver at run time (the library
@@ -606,27 +1032,86 @@ bool gram_tc_supported(const float *cube, int B, long N)
            (reinterpret_cast<uintptr_t>(cube) & 15u) == 0 && encode_fn() != nullptr;
 }
 
+// The tensor-core Gram takes the frame: through the tensor map, or (B <= 128)
+// through the work-item kernel's own copies.
+bool gram_tc_usable(const float *cube, int B, long N)
+{
+    if (gram_tc_supported(cube, B, N)) return true;
+    return B >= 1 && B <= 128 && N >= 1 && N < (1L << 31) &&
+           (reinterpret_cast<uintptr_t>(cube) & 3u) == 0;
+}
+
 size_t gram_tc_smem_bytes() { return Cfg<false>::kSmem; }
+
+// One tensor-core CTA per SM at most, each on a contiguous chunk range of
+// `per` chunks; the last partial may hold fewer.
+long gram_tc_per(long N, int n_part, int sm_count)
+{
+    const long total = (N + kChunk - 1) / kChunk;
+    long n = n_part < sm_count ? n_part : sm_count;
+    if (n < 1) n = 1;
+    const long per = (total + n - 1) / n;
+    return per > 0 ? per : 1;
+}
+
+int gram_tc_parts(long N, long per)
+{
+    const long total = (N + kChunk - 1) / kChunk;
+    return (int)((total + per - 1) / per);
+}
 
 namespace {
 template <int kSt>
 void launch_narrow(const CUtensorMap &map, const float *cube, int B, int Np, long N, long total,
-                   const PcaScratch &s, cudaStream_t st)
+                   long per, int parts, const PcaScratch &s, cudaStream_t st)
 {
     const size_t smem = Cfg<false, kSt>::kSmem;
     cudaFuncSetAttribute(gram_tc_kernel<false, kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    gram_tc_kernel<false, kSt><<<s.n_part, Cfg<false, kSt>::kThreads, smem, st>>>(
-        map, cube, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+    gram_tc_kernel<false, kSt><<<parts, Cfg<false, kSt>::kThreads, smem, st>>>(
+        map, cube, B, 0, 0, Np, 1, N, total, per, s.shift, s.gram_part, s.sum_part, s.ctl);
+}
+
+template <int kSt>
+void launch_items(const BatchFrame &one, const BatchFrame *frames, const GramItem *items,
+                  int n_items, int B, int grid, cudaStream_t st)
+{
+    const size_t smem = Cfg<false, kSt>::kSmem;
+    cudaFuncSetAttribute(gram_tc_items_kernel<kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    gram_tc_items_kernel<kSt><<<grid, Cfg<false, kSt>::kThreads, smem, st>>>(one, frames, items,
+                                                                            n_items, B);
 }
 }  // namespace
 
 // stages: TMA staging depth of the B <= 128 form (3 or 4; 0 = 4). The result
 // does not depend on it (the same chunks reach the same accumulators in the
-// same order); only the overlap of loads and conversion does.
+// same order); only the overlap of loads and conversion does. B <= 128
+// frames the tensor map cannot describe take the work-item kernel (one item
+// per CTA), which gives the same partials.
 cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s, cudaStream_t st,
                            int stages)
 {
+    const long per = gram_tc_per(N, s.n_part, 1 << 30);
+    const int parts = gram_tc_parts(N, per);
+    const long total = (N + kChunk - 1) / kChunk;
+    const int Np = (B + 15) / 16 * 16;
+    if (!gram_tc_supported(cube, B, N)) {
+        if (B > 128 || N >= (1L << 31) || (reinterpret_cast<uintptr_t>(cube) & 3u) != 0)
+            return cudaErrorInvalidValue;
+        BatchFrame one{};
+        one.cube = cube;
+        one.shift = s.shift;
+        one.gram_part = s.gram_part;
+        one.sum_part = s.sum_part;
+        one.ctl = s.ctl;
+        one.N = N;
+        one.per = (int)per;
+        one.vec = 0;
+        if (stages == 3) launch_items<3>(one, nullptr, nullptr, parts, B, parts, st);
+        else launch_items<4>(one, nullptr, nullptr, parts, B, parts, st);
+        return cudaGetLastError();
+    }
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)B};
     cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float)};
@@ -637,21 +1122,34 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
                              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const int Np = (B + 15) / 16 * 16;
-    const long total = (N + kChunk - 1) / kChunk;
     if (B <= 128) {
-        if (stages == 3) launch_narrow<3>(map, cube, B, Np, N, total, s, st);
-        else launch_narrow<4>(map, cube, B, Np, N, total, s, st);
+        if (stages == 3) launch_narrow<3>(map, cube, B, Np, N, total, per, parts, s, st);
+        else launch_narrow<4>(map, cube, B, Np, N, total, per, parts, s, st);
         return cudaGetLastError();
     }
     const size_t smem = Cfg<true>::kSmem;
     cudaFuncSetAttribute(gram_tc_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     // rows 0-127 x every column, then rows 128-255 x columns 128-255
-    gram_tc_kernel<true, 2><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
-        map, cube, B, 0, 0, Np, 1, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
-    gram_tc_kernel<true, 2><<<s.n_part, Cfg<true>::kThreads, smem, st>>>(
-        map, cube, B, 128, 128, Np - 128, 0, N, total, s.shift, s.gram_part, s.sum_part, s.ctl);
+    gram_tc_kernel<true, 2><<<parts, Cfg<true>::kThreads, smem, st>>>(
+        map, cube, B, 0, 0, Np, 1, N, total, per, s.shift, s.gram_part, s.sum_part, s.ctl);
+    gram_tc_kernel<true, 2><<<parts, Cfg<true>::kThreads, smem, st>>>(
+        map, cube, B, 128, 128, Np - 128, 0, N, total, per, s.shift, s.gram_part, s.sum_part,
+        s.ctl);
+    return cudaGetLastError();
+}
+
+// Every item of a stage-major batch (B <= 128) in one persistent launch:
+// one CTA per SM, or more when a CTA would get over kMaxLocalItems items.
+cudaError_t launch_gram_items(const BatchFrame *frames, const GramItem *items, int n_items, int B,
+                              int sm_count, cudaStream_t st)
+{
+    if (B < 1 || B > 128 || n_items < 1) return cudaErrorInvalidValue;
+    int grid = n_items < sm_count ? n_items : sm_count;
+    const int need = (n_items + kMaxLocalItems - 1) / kMaxLocalItems;
+    if (grid < need) grid = need;
+    BatchFrame none{};
+    launch_items<4>(none, frames, items, n_items, B, grid, st);
     return cudaGetLastError();
 }
 

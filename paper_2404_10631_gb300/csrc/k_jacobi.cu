@@ -307,13 +307,25 @@ __device__ float block_sumf(float v, float *red)
     return t;
 }
 
-template <bool kPacked>
+template <bool kPacked, bool kBatch = false>
 __global__ void __launch_bounds__(kJacThreads, 1)
 jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restrict__ C2,
               const double *__restrict__ mu,
               double *__restrict__ v1_out, double *__restrict__ lambda1_out,
-              float *__restrict__ v1f, float *__restrict__ muf, float *gwork, Control *ctl)
+              float *__restrict__ v1f, float *__restrict__ muf, float *gwork, Control *ctl,
+              const BatchFrame *__restrict__ frames)
 {
+    if (kBatch) {  // a stage-major batch: one CTA per frame (work area in shared memory)
+        const BatchFrame &fr = frames[blockIdx.x];
+        C = fr.C;
+        C2 = fr.C2;
+        mu = fr.mu;
+        v1_out = fr.v1;
+        lambda1_out = fr.lambda1;
+        v1f = fr.v1f;
+        muf = fr.muf;
+        ctl = fr.ctl;
+    }
     extern __shared__ float smem[];
     const int B = prm.B, n = prm.n, P = n / 2;
     const int ld = n + 1;  // odd row stride: column walks hit distinct banks
@@ -1378,7 +1390,7 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec
         cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)need_packed);
         jacobi_kernel<true><<<1, kJacThreads, need_packed, st>>>(
-            prm, s.C, s.C2, s.mu, s.v1, s.lambda1, s.v1f, s.muf, s.jac_A, s.ctl);
+            prm, s.C, s.C2, s.mu, s.v1, s.lambda1, s.v1f, s.muf, s.jac_A, s.ctl, nullptr);
         return cudaGetLastError();
     }
     const size_t smem = prm.use_smem ? need : 0;
@@ -1386,7 +1398,34 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec
         cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     jacobi_kernel<false><<<1, kJacThreads, smem, st>>>(prm, s.C, s.C2, s.mu, s.v1, s.lambda1,
-                                                       s.v1f, s.muf, s.jac_A, s.ctl);
+                                                       s.v1f, s.muf, s.jac_A, s.ctl, nullptr);
+    return cudaGetLastError();
+}
+
+// Stage-major batch: one CTA per frame, the single-frame launch's parameters
+// (B <= 128: the work area always fits in shared memory).
+cudaError_t launch_batch_jacobi(const BatchFrame *frames, int n_frames, int B, cudaStream_t st)
+{
+    JacParams prm;
+    prm.n_vec = 1;
+    prm.vk = nullptr;
+    prm.lamk = nullptr;
+    prm.vkf = nullptr;
+    prm.B = B;
+    prm.n = B + (B & 1);
+    if (prm.n < 2) prm.n = 2;
+    prm.max_sweeps = 30;
+    prm.rot_tol = 1e-7f;
+    prm.stop_tol_final = 1e-2f;
+    const size_t need = jac_work_floats(prm.n) * sizeof(float);
+    prm.use_smem = need <= kJacSmemLimit;
+    if (!prm.use_smem || n_frames < 1 || B > 128) return cudaErrorInvalidValue;
+    if (need > 48 * 1024)
+        cudaFuncSetAttribute(jacobi_kernel<false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    jacobi_kernel<false, true><<<n_frames, kJacThreads, need, st>>>(prm, nullptr, nullptr, nullptr,
+                                                              nullptr, nullptr, nullptr, nullptr,
+                                                              nullptr, nullptr, frames);
     return cudaGetLastError();
 }
 

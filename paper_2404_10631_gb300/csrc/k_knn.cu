@@ -398,6 +398,7 @@ constexpr int kTabDc = 20;             // |dc| <= 20 follows from kTabR2
 constexpr int kTabCap = 1200;
 constexpr int kBnd = 12;               // undecided keys per lane (occupancy: 15 KB per CTA)
 constexpr int kRedoLabel = -2147483647 - 1;
+constexpr int kBatchRedoCtas = 1024;  // the batched redo pass's grid (exits at once when idle)
 constexpr int kRedoThreads = 32;
 constexpr int kRedoExtra = 32;         // redo buffer slots beyond K
 __constant__ char2 c_knn_tab[kTabCap];
@@ -493,16 +494,40 @@ __device__ __forceinline__ void write_pixel(const float (&acc)[KC], int K, long 
     labels[p] = best;
 }
 
-template <int KC>
+template <int KC, bool kBatch = false>
 __global__ void __launch_bounds__(kWalkThreads)
 knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
                   int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
-                  bool redo_all, Control *ctl)
+                  bool redo_all, Control *ctl, const BatchFrame *__restrict__ frames,
+                  int n_frames, int2 *__restrict__ redo_list, unsigned redo_cap)
 {
     extern __shared__ float sm[];
     __shared__ float s_min[kWalkThreads / 32], s_max[kWalkThreads / 32];
-    const int r = blockIdx.y, lane = threadIdx.x;
-    const int c0 = blockIdx.x * kWalkThreads, c = c0 + lane;
+    int r = blockIdx.y, bx = blockIdx.x;
+    int frame = 0;
+    if (kBatch) {  // a stage-major batch: the frame whose CTA range holds blockIdx.x
+        int lo = 0, hi = n_frames - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (frames[mid].knn_cta0 <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        frame = lo;
+        const BatchFrame &fr = frames[lo];
+        I = fr.I;
+        P = fr.P;
+        H = fr.H;
+        W = fr.W;
+        O = fr.O;
+        labels = fr.labels;
+        ctl = fr.ctl;
+        const int t = (int)blockIdx.x - fr.knn_cta0;
+        const int tpr = (W + kWalkThreads - 1) / kWalkThreads;
+        r = t / tpr;
+        bx = t - r * tpr;
+    }
+    const int lane = threadIdx.x;
+    const int c0 = bx * kWalkThreads, c = c0 + lane;
     const bool active = c < W;
     const int lo_r = max(0, r - R / 2);
     const int hi_r = min(H - 1, r + (R + 1) / 2 - 1);
@@ -658,7 +683,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     bad |= active && !isfinite(Ip);
     if (__syncthreads_or(bad) && lane == 0) atomicOr(&ctl->status, ST_NONFINITE_MAP);
     const unsigned nredo = __syncthreads_count(redo);
-    if (lane == 0 && nredo) atomicAdd(&ctl->knn_redo, nredo);
+    if (!kBatch && lane == 0 && nredo) atomicAdd(&ctl->knn_redo, nredo);
     {
         unsigned long long e = evals;
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -666,14 +691,22 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     }
     if (!active) return;
     const long p = (long)r * W + c;
-    if (redo) {
+    // a stage-major batch lists the pixels for its redo pass (frame, pixel)
+    auto to_redo = [&]() {
         labels[p] = kRedoLabel;
+        if (kBatch) {
+            const unsigned i = atomicAdd(&frames[0].ctl->knn_redo_list, 1u);
+            if (i < redo_cap) redo_list[i] = make_int2(frame, (int)p);
+        }
+    };
+    if (redo) {
+        to_redo();
         return;
     }
     const int need = K - m;
     if (need > nb) {  // cannot happen: the K-th smallest key is <= tau
-        labels[p] = kRedoLabel;
-        atomicAdd(&ctl->knn_redo, 1u);
+        to_redo();
+        if (!kBatch) atomicAdd(&ctl->knn_redo, 1u);
         return;
     }
     // the need smallest undecided keys: need passes of a minimum search
@@ -842,6 +875,37 @@ knn_redo_kernel(const float *__restrict__ I, const float *__restrict__ P, int H,
     }
 }
 
+// Stage-major batch: the redo pass over the pixels the pruned kernel listed
+// (frame, pixel), spread over the whole grid; the last CTA resets the list
+// and the CTA count (both in frame 0's control block).
+template <int KC>
+__global__ void __launch_bounds__(kRedoThreads)
+knn_redo_batch_kernel(const BatchFrame *__restrict__ frames, int K, int R, float lam,
+                      const int2 *__restrict__ redo_list, unsigned redo_cap)
+{
+    extern __shared__ float sm[];
+    Control *c0 = frames[0].ctl;
+    unsigned n = *(volatile unsigned *)&c0->knn_redo_list;
+    if (n > redo_cap) n = redo_cap;  // cannot happen: one entry per pixel at most
+    if (n == 0u) return;
+    for (unsigned i = blockIdx.x * kRedoThreads + threadIdx.x; i < n;
+         i += gridDim.x * kRedoThreads) {
+        const int2 fp = redo_list[i];
+        const BatchFrame &fr = frames[fp.x];
+        redo_pixel<KC>(fr.I, fr.P, fr.H, fr.W, K, R, lam, fr.O, fr.labels, nullptr, fr.ctl,
+                       (long)fp.y, sm);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&c0->knn_redo_ctas, 1u) == gridDim.x - 1) {
+            c0->knn_redo_list = 0u;
+            c0->knn_redo_ctas = 0u;
+            __threadfence();
+        }
+    }
+}
+
 size_t pruned_smem_bytes(int R, int H)
 {
     const int nrows = R < H ? R : H;
@@ -861,7 +925,8 @@ cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, i
                              (int)smem);
     dim3 grid((W + kWalkThreads - 1) / kWalkThreads, H);
     knn_pruned_kernel<KC><<<grid, kWalkThreads, smem, st>>>(I, P, H, W, K, R, lam, O, labels,
-                                                            nbr != nullptr, ctl);
+                                                            nbr != nullptr, ctl, nullptr, 0,
+                                                            nullptr, 0u);
     const long N = (long)H * W;
     const size_t rsmem = redo_smem_bytes(K);
     if (rsmem > 48 * 1024)
@@ -870,6 +935,27 @@ cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, i
     const long rgrid = (N + kRedoThreads - 1) / kRedoThreads;  // persistent: at most 64 CTAs
     knn_redo_kernel<KC><<<(unsigned)(rgrid < 64 ? rgrid : 64), kRedoThreads, rsmem, st>>>(
         I, P, H, W, K, R, lam, O, labels, nbr, ctl);
+    return cudaGetLastError();
+}
+
+template <int KC>
+cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ctas, int K, int R,
+                                float lam, int max_rows, int2 *redo_list, unsigned redo_cap,
+                                cudaStream_t st)
+{
+    const size_t smem = pruned_smem_bytes(R, max_rows);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(knn_pruned_kernel<KC, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    knn_pruned_kernel<KC, true><<<n_ctas, kWalkThreads, smem, st>>>(
+        nullptr, nullptr, 0, 0, K, R, lam, nullptr, nullptr, false, nullptr, frames, n_frames,
+        redo_list, redo_cap);
+    const size_t rsmem = redo_smem_bytes(K);
+    if (rsmem > 48 * 1024)
+        cudaFuncSetAttribute(knn_redo_batch_kernel<KC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+    knn_redo_batch_kernel<KC><<<kBatchRedoCtas, kRedoThreads, rsmem, st>>>(frames, K, R, lam,
+                                                                        redo_list, redo_cap);
     return cudaGetLastError();
 }
 
@@ -925,6 +1011,26 @@ cudaError_t knn_init(int device)
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_knn_pref, pref.data(), sizeof(char4) * pref.size());
     if (e == cudaSuccess) done[device] = true;
     return e;
+}
+
+// Stage-major batch, pruned search (lambda > 0): n_ctas = sum over frames of
+// H * ceil(W / 32), frame f's CTAs from frames[f].knn_cta0; max_rows = the
+// largest min(R, H).
+cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas, int k, int K,
+                             int R, float lambda, int max_rows, int2 *redo_list,
+                             unsigned redo_cap, cudaStream_t st)
+{
+    if (n_frames < 1 || n_ctas < 1 || !(lambda > 0.f) || !redo_list) return cudaErrorInvalidValue;
+    switch (k) {
+    case 2: return launch_batch_pruned<2>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 3: return launch_batch_pruned<3>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 4: return launch_batch_pruned<4>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 5: return launch_batch_pruned<5>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 6: return launch_batch_pruned<6>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 7: return launch_batch_pruned<7>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 8: return launch_batch_pruned<8>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,

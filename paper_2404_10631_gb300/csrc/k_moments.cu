@@ -19,65 +19,66 @@ constexpr int kGramThreads = 256;
 constexpr int kGramChunk = 32;   // pixels staged per step
 constexpr int kTile = 8;         // 8x8 accumulator tile per thread
 
-// Pilot shift: the mean of a 4096-pixel sample of each band, read as 16
-// runs of 256 consecutive pixels spread over the band (coalesced). Any shift
-// close to the mean works (the moments are exact in it), so the sample is
-// summed in FP32, with its 16 loads per thread issued together.
+// Pilot shift s_b: the mean of a sample of each band. Any shift close to the
+// mean works (the moments are exact in it), so the sample is summed in FP32.
+// A frame of more than 4096 pixels: 16 runs of 256 consecutive pixels spread
+// over the band (one CTA per band, 16 loads per thread issued together).
+// Up to 4096 pixels: every pixel of a frame of up to 1024, else 4 runs of 256
+// (one warp per band, 32 loads per lane issued together).
 // shift[B + b] receives the tensor-core path's scale for band b: the power of
 // two that brings the sample's largest |x - s_b| into [128, 256), so that a
 // pixel must deviate 256 times further than anything in the sample before its
 // scaled value leaves FP16's range (65504); the Gram kernel checks every value
 // and recomputes a partial on the FP32 pipe when one does.
-__global__ void __launch_bounds__(256)
-pilot_shift_kernel(const float *__restrict__ cube, int B, long N, float *__restrict__ shift,
-                   Control *ctl)
+constexpr long kPilotSmall = 4096;
+
+__device__ __forceinline__ float pilot_scale(float m, float s)
 {
-    const int b = blockIdx.x;
+    // a constant sample says nothing about the spread: take |s| (or 1)
+    const float ref = m > 0.f ? m : (fabsf(s) > 0.f ? fabsf(s) : 1.f);
+    int e = 4;  // 16 for a non-finite band (flagged by the caller)
+    if (isfinite(ref)) {
+        int ex;
+        frexpf(ref, &ex);  // ref in [2^(ex-1), 2^ex)
+        e = 8 - ex;
+        e = e < -60 ? -60 : (e > 60 ? 60 : e);
+    }
+    return ldexpf(1.f, e);
+}
+
+// One band of a frame of more than kPilotSmall pixels, by a CTA of 256
+// threads; red: 8 floats of shared memory, s_sh: one.
+__device__ __forceinline__ void pilot_band_block(const float *__restrict__ band, long N, int B,
+                                                 int b, float *__restrict__ shift, Control *ctl,
+                                                 float *red, float *s_sh)
+{
     constexpr int kRuns = 16, kRun = 256;
-    const float *band = cube + (size_t)b * (size_t)N;
-    const bool small = N <= (long)kRuns * kRun;
     float acc = 0.f;
-    long count;
     bool bad = false;
     float x[kRuns];
-    if (small) {
-        for (long p = threadIdx.x; p < N; p += blockDim.x) {
-            const float v = band[p];
-            bad |= !isfinite(v);
-            acc += v;
-        }
-        count = N;
-    } else {
 #pragma unroll
-        for (int r = 0; r < kRuns; ++r)
-            x[r] = __ldg(band + ((long)r * (N - kRun)) / (kRuns - 1) + threadIdx.x);
+    for (int r = 0; r < kRuns; ++r)
+        x[r] = __ldg(band + ((long)r * (N - kRun)) / (kRuns - 1) + threadIdx.x);
 #pragma unroll
-        for (int r = 0; r < kRuns; ++r) {
-            bad |= !isfinite(x[r]);
-            acc += x[r];
-        }
-        count = (long)kRuns * kRun;
+    for (int r = 0; r < kRuns; ++r) {
+        bad |= !isfinite(x[r]);
+        acc += x[r];
     }
-    __shared__ float red[8];
-    __shared__ float s_sh;
+    const long count = (long)kRuns * kRun;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < 8; ++w) t += red[w];
-        s_sh = t / (float)count;
-        shift[b] = s_sh;
+        *s_sh = t / (float)count;
+        shift[b] = *s_sh;
     }
     __syncthreads();
-    const float s = s_sh;
+    const float s = *s_sh;
     float dev = 0.f;
-    if (small) {
-        for (long p = threadIdx.x; p < N; p += blockDim.x) dev = fmaxf(dev, fabsf(band[p] - s));
-    } else {
 #pragma unroll
-        for (int r = 0; r < kRuns; ++r) dev = fmaxf(dev, fabsf(x[r] - s));
-    }
+    for (int r = 0; r < kRuns; ++r) dev = fmaxf(dev, fabsf(x[r] - s));
     for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
     __syncthreads();  // red[] is reused
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dev;
@@ -85,17 +86,100 @@ pilot_shift_kernel(const float *__restrict__ cube, int B, long N, float *__restr
     if (threadIdx.x == 0) {
         float m = 0.f;
         for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w]);
-        // a constant sample says nothing about the spread: take |s| (or 1)
-        const float ref = m > 0.f ? m : (fabsf(s) > 0.f ? fabsf(s) : 1.f);
-        int e = 4;  // 16 for a non-finite band (flagged above)
-        if (isfinite(ref)) {
-            int ex;
-            frexpf(ref, &ex);  // ref in [2^(ex-1), 2^ex)
-            e = 8 - ex;
-            e = e < -60 ? -60 : (e > 60 ? 60 : e);
-        }
-        shift[B + b] = ldexpf(1.f, e);
+        shift[B + b] = pilot_scale(m, s);
     }
+    __syncthreads();  // red[] and s_sh are free again
+}
+
+// One band of a frame of at most kPilotSmall pixels, by one warp.
+__device__ __forceinline__ void pilot_band_warp(const float *__restrict__ band, long N, int B,
+                                                int b, float *__restrict__ shift, Control *ctl)
+{
+    constexpr int kPer = 32, kRun = 256;  // 1024 samples at most: 4 runs of 256
+    const int lane = threadIdx.x & 31;
+    const bool all = N <= kPer * 32;
+    const long cnt = all ? N : (long)kPer * 32;
+    float x[kPer];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        // run r starts at r * 256 (every pixel) or r (N - 256) / 3
+        const float *run = band + (all ? (long)r * kRun : ((long)r * (N - kRun)) / 3) + lane;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int i = r * kRun + lane + 32 * j;  // sample index
+            x[r * 8 + j] = i < cnt ? __ldg(run + 32 * j) : 0.f;
+        }
+    }
+    float acc = 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j)  // x[j] is sample lane + 32 j
+        if (lane + 32 * j < cnt) {
+            bad |= !isfinite(x[j]);
+            acc += x[j];
+        }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const float s = acc / (float)cnt;
+    float dev = 0.f;  // the sample again (from L1): nothing held across the reduction
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float *run = band + (all ? (long)r * kRun : ((long)r * (N - kRun)) / 3) + lane;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (r * kRun + lane + 32 * j < cnt) dev = fmaxf(dev, fabsf(__ldg(run + 32 * j) - s));
+    }
+    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+    if (lane == 0) {
+        shift[b] = s;
+        shift[B + b] = pilot_scale(dev, s);
+    }
+}
+
+// Frames of more than kPilotSmall pixels: one CTA per band.
+__global__ void __launch_bounds__(256)
+pilot_shift_kernel(const float *__restrict__ cube, int B, long N, float *__restrict__ shift,
+                   Control *ctl)
+{
+    __shared__ float red[8];
+    __shared__ float s_sh;
+    const int b = blockIdx.x;
+    pilot_band_block(cube + (size_t)b * (size_t)N, N, B, b, shift, ctl, red, &s_sh);
+}
+
+// Frames of at most kPilotSmall pixels: one warp per band.
+__global__ void __launch_bounds__(256)
+pilot_small_kernel(const float *__restrict__ cube, int B, long N, float *__restrict__ shift,
+                   Control *ctl)
+{
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (b < B) pilot_band_warp(cube + (size_t)b * (size_t)N, N, B, b, shift, ctl);
+}
+
+// Stage-major batch, frames of at most kPilotSmall pixels: bands
+// 8 x blockIdx.x .. + 7 of frame blockIdx.y (larger frames are skipped).
+__global__ void __launch_bounds__(256)
+pilot_batch_kernel(int B, const BatchFrame *__restrict__ frames)
+{
+    const BatchFrame *fp = frames + blockIdx.y;
+    const long N = fp->N;
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (N <= kPilotSmall && b < B)
+        pilot_band_warp(fp->cube + (size_t)b * (size_t)N, N, B, b, fp->shift, fp->ctl);
+}
+
+// Stage-major batch, the frames of more than kPilotSmall pixels (their
+// indices in large[]): band blockIdx.x of frame large[blockIdx.y].
+__global__ void __launch_bounds__(256)
+pilot_batch_large_kernel(int B, const BatchFrame *__restrict__ frames,
+                         const int *__restrict__ large)
+{
+    __shared__ float red[8];
+    __shared__ float s_sh;
+    const BatchFrame *fp = frames + large[blockIdx.y];
+    const long N = fp->N;
+    const int b = blockIdx.x;
+    pilot_band_block(fp->cube + (size_t)b * (size_t)N, N, B, b, fp->shift, fp->ctl, red, &s_sh);
 }
 
 // Double-float accumulation (Knuth's TwoSum keeps each addition's rounding
@@ -268,6 +352,105 @@ gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gr
     }
 }
 
+// Stage-major batch form of gram_reduce_kernel: CTA (t, f) takes the t-th
+// 32 x 32 tile (b-block <= c-block) of frame f's matrix, each thread four
+// entries (b, c), b <= c, replaying gram_reduce_kernel's arithmetic: slice s
+// sums the partials s, s + 8, ... in double-float and slices 1..7 are then
+// added to slice 0. With at most 8 partials (a frame of at most 8192 pixels)
+// every slice holds one partial or none, and since these sums never produce
+// -0, adding an empty slice changes nothing: the result is the double-float
+// sum of the partials in order, which is what is formed here. C2 (the pairs
+// the eigensolver reads) and mu are written, the tile and its mirror image
+// both coalesced through shared memory; the FP64 C is not needed by the batch.
+__global__ void __launch_bounds__(256)
+gram_reduce_batch_kernel(int B, const BatchFrame *__restrict__ frames)
+{
+    __shared__ float2 tile[32][33];
+    const BatchFrame *fp = frames + blockIdx.y;
+    const double inv_N = 1.0 / (double)fp->N;
+    const int n_part = fp->n_part;
+    const float *__restrict__ gram_part = fp->gram_part;
+    const float *__restrict__ sum_part = fp->sum_part;
+    const float *__restrict__ shift = fp->shift;
+    float2 *__restrict__ C2 = fp->C2;
+    double *__restrict__ mu = fp->mu;
+    const long BB = (long)B * B;
+    // tile t -> (tb, tc), tb <= tc, row-major over the upper triangle of blocks
+    const int T = (B + 31) / 32;
+    int t = blockIdx.x, tb = 0;
+    while (t >= T - tb) {
+        t -= T - tb;
+        ++tb;
+    }
+    const int tc = tb + t;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int b = tb * 32 + lane;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int cl = w + 8 * j;
+        const int c = tc * 32 + cl;
+        float2 pr = make_float2(0.f, 0.f);
+        if (b < B && c < B && c >= b) {
+            const long e = (long)c * B + b;
+            float g = 0.f, gl = 0.f, sb = 0.f, lb = 0.f, sc = 0.f, lc = 0.f;
+            if (n_part <= kRedSlices) {
+                float vg[kRedSlices], vb[kRedSlices], vc[kRedSlices];
+#pragma unroll
+                for (int k = 0; k < kRedSlices; ++k) {
+                    const bool in = k < n_part;
+                    vg[k] = in ? gram_part[(size_t)k * BB + e] : 0.f;
+                    vb[k] = in ? sum_part[(size_t)k * B + b] : 0.f;
+                    vc[k] = in ? sum_part[(size_t)k * B + c] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < kRedSlices; ++k)
+                    if (k < n_part) {
+                        df_acc(g, gl, vg[k]);
+                        df_acc(sb, lb, vb[k]);
+                        df_acc(sc, lc, vc[k]);
+                    }
+            } else {
+                for (int sl = 0; sl < kRedSlices; ++sl) {
+                    float g1 = 0.f, gl1 = 0.f, sb1 = 0.f, lb1 = 0.f, sc1 = 0.f, lc1 = 0.f;
+                    for (int k = sl; k < n_part; k += kRedSlices) {
+                        df_acc(g1, gl1, gram_part[(size_t)k * BB + e]);
+                        df_acc(sb1, lb1, sum_part[(size_t)k * B + b]);
+                        df_acc(sc1, lc1, sum_part[(size_t)k * B + c]);
+                    }
+                    if (sl == 0) {
+                        g = g1;
+                        gl = gl1;
+                        sb = sb1;
+                        lb = lb1;
+                        sc = sc1;
+                        lc = lc1;
+                    } else {
+                        df_acc2(g, gl, g1, gl1);
+                        df_acc2(sb, lb, sb1, lb1);
+                        df_acc2(sc, lc, sc1, lc1);
+                    }
+                }
+            }
+            const double db = ((double)sb + (double)lb) * inv_N;
+            const double dc = ((double)sc + (double)lc) * inv_N;
+            const double v = fma(-db, dc, ((double)g + (double)gl) * inv_N);
+            const float hi = __double2float_rn(v);
+            pr = make_float2(hi, __double2float_rn(v - (double)hi));
+            C2[(size_t)c * B + b] = pr;  // row c: lanes on consecutive b
+            if (b == c) mu[b] = (double)shift[b] + db;
+        }
+        tile[cl][lane] = pr;
+    }
+    __syncthreads();
+    // the mirror image: row b = tb * 32 + r, columns tc * 32 + lane
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int r = w + 8 * j;
+        const int bb = tb * 32 + r, c = tc * 32 + lane;
+        if (bb < B && c < B && c >= bb) C2[(size_t)bb * B + c] = tile[lane][r];
+    }
+}
+
 }  // namespace
 
 // Partial-Gram partitions: one CTA per SM for the tensor-core Gram (it holds
@@ -290,20 +473,21 @@ static cudaError_t launch_reductions(int B, long N, int n_part, const PcaScratch
 // 128 < B <= 256 on the tensor cores), the reduction.
 int moments_kernel_count(const float *cube, int B, long N, bool force_simt)
 {
-    if (!force_simt && gram_tc_supported(cube, B, N)) return B > 128 ? 4 : 3;
+    if (!force_simt && gram_tc_usable(cube, B, N)) return B > 128 ? 4 : 3;
     return 3;
 }
 
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s, int sm_count,
                            cudaStream_t st, bool force_simt, int gram_stages)
 {
-    pilot_shift_kernel<<<B, 256, 0, st>>>(cube, B, N, s.shift, s.ctl);
-    if (!force_simt && gram_tc_supported(cube, B, N)) {
+    if (N <= kPilotSmall) pilot_small_kernel<<<(B + 7) / 8, 256, 0, st>>>(cube, B, N, s.shift, s.ctl);
+    else pilot_shift_kernel<<<B, 256, 0, st>>>(cube, B, N, s.shift, s.ctl);
+    if (!force_simt && gram_tc_usable(cube, B, N)) {
         PcaScratch t = s;
         t.n_part = s.n_part < sm_count ? s.n_part : sm_count;  // one CTA per SM
         cudaError_t e = launch_gram_tc(cube, B, N, t, st, gram_stages);
         if (e != cudaSuccess) return e;
-        return launch_reductions(B, N, t.n_part, s, st);
+        return launch_reductions(B, N, gram_tc_parts(N, gram_tc_per(N, t.n_part, sm_count)), s, st);
     }
     const int Bp = (B + kTile - 1) / kTile * kTile;
     const int nt = Bp / kTile;
@@ -316,6 +500,24 @@ cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s
     gram_partial_kernel<<<grid, kGramThreads, smem, st>>>(cube, B, Bp, N, s.shift, s.gram_part,
                                                           s.sum_part, s.ctl);
     return launch_reductions(B, N, s.n_part, s, st);
+}
+
+// Stage-major batch (B <= 128): the pilots of every frame, every Gram item
+// in one persistent launch, the reductions of every frame.
+cudaError_t launch_batch_moments(const BatchFrame *frames, int n_frames, const GramItem *items,
+                                 int n_items, const int *large, int n_large, int B, int sm_count,
+                                 cudaStream_t st)
+{
+    if (n_frames < 1 || n_frames > 65535) return cudaErrorInvalidValue;
+    pilot_batch_kernel<<<dim3((B + 7) / 8, n_frames), 256, 0, st>>>(B, frames);
+    if (n_large > 0)
+        pilot_batch_large_kernel<<<dim3(B, n_large), 256, 0, st>>>(B, frames, large);
+    cudaError_t e = launch_gram_items(frames, items, n_items, B, sm_count, st);
+    if (e != cudaSuccess) return e;
+    const int T = (B + 31) / 32;
+    gram_reduce_batch_kernel<<<dim3((unsigned)(T * (T + 1) / 2), n_frames), 256, 0, st>>>(B,
+                                                                                        frames);
+    return cudaGetLastError();
 }
 
 }  // namespace hsc

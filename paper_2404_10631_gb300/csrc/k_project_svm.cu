@@ -94,45 +94,25 @@ __device__ __forceinline__ void couple_solve(const float *r /* M, pair order */,
     for (int i = 0; i < KC; ++i) p[i] = (float)(y[i] * inv);
 }
 
-// KC = 0: projection only. PX = pixels per thread (4 with 16-byte loads).
-template <int KC, int PX>
-__global__ void __launch_bounds__(kThreads)
-project_svm_kernel(const float *__restrict__ cube, int B, long N,
-                   const float *__restrict__ v1f, const float *__restrict__ muf,
-                   const float *__restrict__ w, const float *__restrict__ bias,
-                   const float *__restrict__ pa, const float *__restrict__ pb,
-                   float *__restrict__ I_raw, float *__restrict__ probs,
-                   int32_t *__restrict__ labels, int couple_f64, Control *ctl)
+// The per-pixel work of the pass for groups g_begin, g_begin + g_step, ...
+// below g_end of PX pixels: group g holds pixels g * PX + u (one 16-byte
+// load per band when kVec, else PX 4-byte loads), or, kStrided, pixels
+// p_base + g + u * kThreads (4-byte loads, each coalesced across the warp).
+// ws holds per band w_0..w_{M-1}, v1, mu. The arithmetic of a pixel does not
+// depend on the grouping or the loads.
+template <int KC, int PX, bool kVec, bool kStrided = false>
+__device__ __forceinline__ void project_svm_groups(
+    const float *__restrict__ cube, int B, long N, const float *ws, const float *sbias,
+    const float *sa, const float *sb, bool do_pca, long g_begin, long g_end, long g_step,
+    float *__restrict__ I_raw, float *__restrict__ probs, int32_t *__restrict__ labels,
+    int couple_f64, float &lmin, float &lmax, bool &bad, long p_base = 0)
 {
     constexpr int M = KC * (KC - 1) / 2;
     constexpr int MA = M > 0 ? M : 1;
-    constexpr int S = M + 2;  // per band: w_0..w_{M-1}, v1, mu
-    extern __shared__ float ws[];
-    __shared__ float sbias[MA], sa[MA], sb[MA];
-    const bool do_pca = (v1f != nullptr);
-
-    for (int idx = threadIdx.x; idx < B * S; idx += blockDim.x) {
-        int b = idx / S, m = idx % S;
-        float v;
-        if (m < M) v = w[(size_t)m * B + b];
-        else if (m == M) v = do_pca ? v1f[b] : 0.f;
-        else v = do_pca ? muf[b] : 0.f;
-        ws[idx] = v;
-    }
-    if constexpr (M > 0)
-        for (int m = threadIdx.x; m < M; m += blockDim.x) {
-            sbias[m] = bias[m];
-            sa[m] = pa[m];
-            sb[m] = pb[m];
-        }
-    __syncthreads();
-
-    float lmin = INFINITY, lmax = -INFINITY;
-    bool bad = false;
-    const long ngroups = (N + PX - 1) / PX;
-    for (long g = (long)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups;
-         g += (long)gridDim.x * blockDim.x) {
-        const long p0 = g * PX;
+    constexpr int S = M + 2;
+    constexpr long kPs = kStrided ? kThreads : 1;  // pixel stride within a group
+    for (long g = g_begin; g < g_end; g += g_step) {
+        const long p0 = kStrided ? p_base + g : g * PX;
         float acc[MA][PX];
         float accI[PX];
 #pragma unroll
@@ -147,7 +127,7 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
         for (int b = 0; b < B; ++b) {
             float x[PX];
             const float *src = cube + (size_t)b * (size_t)N + p0;
-            if constexpr (PX == 4) {
+            if constexpr (PX == 4 && kVec) {
                 float4 v = __ldcs(reinterpret_cast<const float4 *>(src));
                 x[0] = v.x;
                 x[1] = v.y;
@@ -155,7 +135,8 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
                 x[3] = v.w;
             } else {
 #pragma unroll
-                for (int u = 0; u < PX; ++u) x[u] = (p0 + u < N) ? __ldcs(src + u) : 0.f;
+                for (int u = 0; u < PX; ++u)
+                    x[u] = (p0 + u * kPs < N) ? __ldcs(src + u * kPs) : 0.f;
             }
             const float *wr = ws + b * S;
 #pragma unroll
@@ -170,7 +151,7 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
         }
 #pragma unroll
         for (int u = 0; u < PX; ++u) {
-            const long p = p0 + u;
+            const long p = p0 + u * kPs;
             if (p >= N) break;
             if (do_pca) {
                 float I = accI[u];
@@ -205,7 +186,41 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
             }
         }
     }
-    // block min/max of I -> ordered-int atomics
+}
+
+// Stages per band w_0..w_{M-1}, v1, mu and the Platt constants in shared memory.
+template <int KC>
+__device__ __forceinline__ void stage_weights(int B, const float *__restrict__ v1f,
+                                              const float *__restrict__ muf,
+                                              const float *__restrict__ w,
+                                              const float *__restrict__ bias,
+                                              const float *__restrict__ pa,
+                                              const float *__restrict__ pb, float *ws,
+                                              float *sbias, float *sa, float *sb)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    constexpr int S = M + 2;
+    const bool do_pca = (v1f != nullptr);
+    for (int idx = threadIdx.x; idx < B * S; idx += blockDim.x) {
+        int b = idx / S, m = idx % S;
+        float v;
+        if (m < M) v = w[(size_t)m * B + b];
+        else if (m == M) v = do_pca ? v1f[b] : 0.f;
+        else v = do_pca ? muf[b] : 0.f;
+        ws[idx] = v;
+    }
+    if constexpr (M > 0)
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            sbias[m] = bias[m];
+            sa[m] = pa[m];
+            sb[m] = pb[m];
+        }
+}
+
+// Block min/max of I into the ordered-int keys, the non-finite flag.
+__device__ __forceinline__ void finish_block(bool do_pca, float lmin, float lmax, bool bad,
+                                             Control *ctl)
+{
     if (do_pca) {
         for (int o = 16; o > 0; o >>= 1) {
             lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
@@ -219,6 +234,65 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
 }
 
+// KC = 0: projection only. PX = pixels per thread (4, with 16-byte loads
+// when kVec, or 1).
+template <int KC, int PX, bool kVec>
+__global__ void __launch_bounds__(kThreads)
+project_svm_kernel(const float *__restrict__ cube, int B, long N,
+                   const float *__restrict__ v1f, const float *__restrict__ muf,
+                   const float *__restrict__ w, const float *__restrict__ bias,
+                   const float *__restrict__ pa, const float *__restrict__ pb,
+                   float *__restrict__ I_raw, float *__restrict__ probs,
+                   int32_t *__restrict__ labels, int couple_f64, Control *ctl)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    constexpr int MA = M > 0 ? M : 1;
+    extern __shared__ float ws[];
+    __shared__ float sbias[MA], sa[MA], sb[MA];
+    stage_weights<KC>(B, v1f, muf, w, bias, pa, pb, ws, sbias, sa, sb);
+    __syncthreads();
+    float lmin = INFINITY, lmax = -INFINITY;
+    bool bad = false;
+    const long ngroups = (N + PX - 1) / PX;
+    project_svm_groups<KC, PX, kVec>(cube, B, N, ws, sbias, sa, sb, v1f != nullptr,
+                               (long)blockIdx.x * blockDim.x + threadIdx.x, ngroups,
+                               (long)gridDim.x * blockDim.x, I_raw, probs, labels, couple_f64,
+                               lmin, lmax, bad);
+    finish_block(v1f != nullptr, lmin, lmax, bad, ctl);
+}
+
+// Stage-major batch: CTA i takes work item i (one frame's groups of 4
+// pixels, 16-byte loads where the frame allows them); labels are not
+// written (the KNN gives them).
+template <int KC>
+__global__ void __launch_bounds__(kThreads)
+project_svm_batch_kernel(const BatchFrame *__restrict__ frames, const PixItem *__restrict__ items,
+                         int B, const float *__restrict__ w, const float *__restrict__ bias,
+                         const float *__restrict__ pa, const float *__restrict__ pb,
+                         int couple_f64)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    constexpr int MA = M > 0 ? M : 1;
+    extern __shared__ float ws[];
+    __shared__ float sbias[MA], sa[MA], sb[MA];
+    const PixItem it = items[blockIdx.x];
+    const BatchFrame &fr = frames[it.frame];
+    stage_weights<KC>(B, fr.v1f, fr.muf, w, bias, pa, pb, ws, sbias, sa, sb);
+    __syncthreads();
+    float lmin = INFINITY, lmax = -INFINITY;
+    bool bad = false;
+    if (fr.vec)
+        project_svm_groups<KC, 4, true>(fr.cube, B, fr.N, ws, sbias, sa, sb, true,
+                                        it.g0 + threadIdx.x, it.g1, blockDim.x, fr.I, fr.P,
+                                        nullptr, couple_f64, lmin, lmax, bad);
+    else  // pixels g0 * 4 + t + 256 u of thread t: every load coalesced
+        project_svm_groups<KC, 4, false, true>(fr.cube, B, fr.N, ws, sbias, sa, sb, true,
+                                               threadIdx.x, threadIdx.x + 1, 1, fr.I, fr.P,
+                                               nullptr, couple_f64, lmin, lmax, bad,
+                                               (long)it.g0 * 4);
+    finish_block(true, lmin, lmax, bad, fr.ctl);
+}
+
 __global__ void normalize_kernel(const float *__restrict__ I_raw, float *__restrict__ I_norm,
                                  long N, const Control *__restrict__ ctl)
 {
@@ -229,14 +303,28 @@ __global__ void normalize_kernel(const float *__restrict__ I_raw, float *__restr
         I_norm[p] = (range > 0.f) ? (I_raw[p] - mn) / range : 0.f;
 }
 
-template <int KC, int PX>
+// Stage-major batch: CTA i normalises the pixels of work item i.
+__global__ void normalize_batch_kernel(const BatchFrame *__restrict__ frames,
+                                       const PixItem *__restrict__ items)
+{
+    const PixItem it = items[blockIdx.x];
+    const BatchFrame &fr = frames[it.frame];
+    const float mn = key_to_float(fr.ctl->imin_key), mx = key_to_float(fr.ctl->imax_key);
+    const float range = mx - mn;
+    long p1 = (long)it.g1 * it.px;
+    if (p1 > fr.N) p1 = fr.N;
+    for (long p = (long)it.g0 * it.px + threadIdx.x; p < p1; p += blockDim.x)
+        fr.I[p] = (range > 0.f) ? (fr.I[p] - mn) / range : 0.f;
+}
+
+template <int KC, int PX, bool kVec>
 cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const float *muf,
                       float *I_raw, const hsc_svm_model *m, bool f64, float *probs,
                       int32_t *labels, Control *ctl, int sm_count, cudaStream_t st, int max_blocks)
 {
     constexpr int M = KC * (KC - 1) / 2;
     size_t smem = sizeof(float) * (size_t)B * (M + 2);
-    auto kern = project_svm_kernel<KC, PX>;
+    auto kern = project_svm_kernel<KC, PX, kVec>;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     long groups = (N + PX - 1) / PX;
@@ -250,21 +338,21 @@ cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const 
     return cudaGetLastError();
 }
 
-template <int PX>
+template <int PX, bool kVec>
 cudaError_t dispatch_k(int k, const float *cube, int B, long N, const float *v1f,
                        const float *muf, float *I_raw, const hsc_svm_model *m, bool f64,
                        float *probs, int32_t *labels, Control *ctl, int sm, cudaStream_t st,
                        int mb)
 {
     switch (k) {
-    case 0: return launch_kc<0, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 2: return launch_kc<2, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 3: return launch_kc<3, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 4: return launch_kc<4, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 5: return launch_kc<5, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 6: return launch_kc<6, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 7: return launch_kc<7, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 8: return launch_kc<8, PX>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 0: return launch_kc<0, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 2: return launch_kc<2, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 3: return launch_kc<3, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 4: return launch_kc<4, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 5: return launch_kc<5, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 6: return launch_kc<6, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 7: return launch_kc<7, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 8: return launch_kc<8, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -277,12 +365,15 @@ cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1
                                int sm_count, cudaStream_t st, int max_blocks, int px)
 {
     const int k = (probs != nullptr && model != nullptr) ? model->n_classes : 0;
-    const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0) && px != 1;
+    const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0);
+    if (px == 1)
+        return dispatch_k<1, false>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs,
+                                    svm_labels, ctl, sm_count, st, max_blocks);
     if (vec)
-        return dispatch_k<4>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs, svm_labels,
-                             ctl, sm_count, st, max_blocks);
-    return dispatch_k<1>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs, svm_labels, ctl,
-                         sm_count, st, max_blocks);
+        return dispatch_k<4, true>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs,
+                                   svm_labels, ctl, sm_count, st, max_blocks);
+    return dispatch_k<4, false>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs,
+                                svm_labels, ctl, sm_count, st, max_blocks);
 }
 
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,
@@ -291,6 +382,47 @@ cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control 
     long blocks = (N + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     normalize_kernel<<<(unsigned)blocks, 256, 0, st>>>(I_raw, I_norm, N, ctl);
+    return cudaGetLastError();
+}
+
+namespace {
+template <int KC>
+cudaError_t launch_batch_kc(const BatchFrame *frames, const PixItem *items, int n_items, int B,
+                            const hsc_svm_model *m, bool f64, cudaStream_t st)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    const size_t smem = sizeof(float) * (size_t)B * (M + 2);
+    auto kern = project_svm_batch_kernel<KC>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<n_items, kThreads, smem, st>>>(frames, items, B, m->w, m->b, m->platt_a, m->platt_b,
+                                          f64 ? 1 : 0);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_batch_project_svm(const BatchFrame *frames, const PixItem *items, int n_items,
+                                     int B, const hsc_svm_model *m, bool couple_f64,
+                                     cudaStream_t st)
+{
+    if (n_items < 1 || !m) return cudaErrorInvalidValue;
+    switch (m->n_classes) {
+    case 2: return launch_batch_kc<2>(frames, items, n_items, B, m, couple_f64, st);
+    case 3: return launch_batch_kc<3>(frames, items, n_items, B, m, couple_f64, st);
+    case 4: return launch_batch_kc<4>(frames, items, n_items, B, m, couple_f64, st);
+    case 5: return launch_batch_kc<5>(frames, items, n_items, B, m, couple_f64, st);
+    case 6: return launch_batch_kc<6>(frames, items, n_items, B, m, couple_f64, st);
+    case 7: return launch_batch_kc<7>(frames, items, n_items, B, m, couple_f64, st);
+    case 8: return launch_batch_kc<8>(frames, items, n_items, B, m, couple_f64, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_normalize(const BatchFrame *frames, const PixItem *items, int n_items,
+                                   cudaStream_t st)
+{
+    if (n_items < 1) return cudaErrorInvalidValue;
+    normalize_batch_kernel<<<n_items, 256, 0, st>>>(frames, items);
     return cudaGetLastError();
 }
 

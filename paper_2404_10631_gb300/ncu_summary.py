@@ -22,12 +22,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 # kernel name prefix -> pipeline stage, and the source file each stage's
 # kernels live in (its hash tags the numbers with the code they measured)
-STAGE_OF = (("pilot_shift_kernel", "moments"), ("gram_tc_kernel", "moments"),
-            ("gram_partial_kernel", "moments"),
+STAGE_OF = (("pilot_", "moments"), ("gram_tc_kernel", "moments"),
+            ("gram_tc_items_kernel", "moments"), ("gram_partial_kernel", "moments"),
             ("gram_reduce_kernel", "moments"), ("jacobi_kernel", "jacobi"),
-            ("project_svm_kernel", "project_svm"), ("normalize_kernel", "normalize"),
+            ("project_svm_kernel", "project_svm"), ("project_svm_batch_kernel", "project_svm"),
+            ("normalize_kernel", "normalize"), ("normalize_batch_kernel", "normalize"),
             ("knn_pruned_kernel", "knn"), ("knn_redo_kernel", "knn"),
-            ("knn_kernel", "knn_full"))
+            ("knn_redo_batch_kernel", "knn"), ("knn_kernel", "knn_full"))
 SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu"), "jacobi": ("k_jacobi.cu",),
              "project_svm": ("k_project_svm.cu",), "normalize": ("k_project_svm.cu",),
              "knn": ("k_knn.cu",), "knn_full": ("k_knn.cu",)}

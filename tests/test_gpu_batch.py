@@ -1,6 +1,9 @@
 """hsc_classify_batch: every frame's outputs are bit-identical to what
 hsc_classify gives for that frame alone (uneven snapshot frames, shared
-model), with and without CUDA-graph replay."""
+model), in the stage-major form and the stream-pool form, with and without
+CUDA-graph replay; long work items (two accumulator segments), pixel counts
+that are not a multiple of 4, a cube that is not 16-byte aligned and an
+out-of-range pixel (the FP32 recompute) included."""
 
 import numpy as np
 import pytest
@@ -43,7 +46,8 @@ def assert_same(a, b):
 
 
 @pytest.mark.parametrize("graph", [False, True])
-def test_batch_equals_frames_alone(hsc, ctx, graph):
+@pytest.mark.parametrize("pool", [False, True])
+def test_batch_equals_frames_alone(hsc, ctx, graph, pool):
     frames = synth.make_batch(12)
     # two frames whose pixel count is not a multiple of 4 (scalar loads,
     # FP32-pipe covariance)
@@ -55,7 +59,7 @@ def test_batch_equals_frames_alone(hsc, ctx, graph):
     model = hsc.Model.from_host(f0.model)
     cubes = frames_to_device(frames)
     labs, O, I, P = outputs(frames, 4)
-    flags = hsc.HSC_BATCH_GRAPH if graph else 0
+    flags = (hsc.HSC_BATCH_GRAPH if graph else 0) | (hsc.HSC_BATCH_POOL if pool else 0)
     for rep in range(2):  # the second call replays the graph
         hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, flags=flags,
                                labels=labs, out_probs=O, one_bands=I, probs=P)
@@ -112,3 +116,68 @@ def test_batch_rejects_bad_frame(hsc, ctx):
     cubes[1] = cubes[1][:100].contiguous()  # band count differs
     with pytest.raises(ValueError):
         hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam)
+
+
+def _alone_vs_batch(hsc, ctx, frames, cubes, flags=0):
+    import torch
+    f0 = frames[0]
+    k = f0.model.n_classes
+    model = hsc.Model.from_host(f0.model)
+    labs, O, I, P = outputs(frames, k)
+    hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, flags=flags,
+                           labels=labs, out_probs=O, one_bands=I, probs=P)
+    ctx.sync()
+    for i, f in enumerate(frames):
+        lab = torch.empty(f.cube.shape[1:], dtype=torch.int32, device="cuda")
+        Oa = torch.empty((k,) + f.cube.shape[1:], device="cuda")
+        Ia = torch.empty(f.cube.shape[1:], device="cuda")
+        Pa = torch.empty((k,) + f.cube.shape[1:], device="cuda")
+        hsc.hsc_classify(ctx, cubes[i], model, f.K, f.window_rows, f.lam, flags=flags,
+                         labels=lab, out_probs=Oa, one_band=Ia, probs=Pa)
+        ctx.sync()
+        assert_same((labs[i], O[i], I[i], P[i]), (lab, Oa, Ia, Pa))
+
+
+def test_staged_batch_long_items_and_alignment(hsc, ctx):
+    """A 768 x 1024 frame (81 chunks per Gram item: two accumulator segments;
+    alone it takes the tensor-map kernel), a 331 x 257 frame (odd pixel
+    count: 4-byte copies, and alone the work-item kernel), a cube 4 bytes off
+    16-byte alignment, and small frames, 32 bands, in one stage-major batch."""
+    import torch
+    B = 32
+    big = synth.make_frame(501, 768, 1024, B, sigma=0.03, K=16, window_rows=7)
+    sp = big.spectra
+    frames = [big,
+              synth.make_frame(502, 331, 257, B, sigma=0.03, K=16, window_rows=7, spectra=sp),
+              synth.make_frame(503, 48, 64, B, sigma=0.03, K=16, window_rows=7, spectra=sp),
+              synth.make_frame(504, 40, 40, B, sigma=0.03, K=16, window_rows=7, spectra=sp),
+              synth.make_frame(505, 9, 61, B, sigma=0.03, K=16, window_rows=7, spectra=sp)]
+    cubes = frames_to_device(frames)
+    # frame 3 from a buffer one float past a 16-byte boundary
+    n3 = frames[3].cube.size
+    buf = torch.empty(n3 + 1, device="cuda")
+    buf[1:].copy_(torch.as_tensor(frames[3].cube.ravel(), device="cuda"))
+    cubes[3] = buf[1:].view(frames[3].cube.shape)
+    assert cubes[3].data_ptr() % 16 != 0
+    _alone_vs_batch(hsc, ctx, frames, cubes)
+
+
+def test_staged_batch_out_of_range_pixel(hsc, ctx):
+    """One pixel of one frame far outside FP16's range after scaling: its
+    Gram item is recomputed on the FP32 pipe in the batch as it is alone."""
+    frames = synth.make_batch(4, seed=777)
+    # 128 x 128: the pilot samples runs of 256 pixels starting at r (N - 256) / 15,
+    # so pixel 700 is outside it
+    frames.insert(2, synth.make_frame(779, 128, 128, 125, sigma=0.03, K=16, window_rows=7,
+                                      spectra=frames[0].spectra))
+    cubes = frames_to_device(frames)
+    cubes[2][5].view(-1)[700] += 5e3
+    _alone_vs_batch(hsc, ctx, frames, cubes)
+
+
+@pytest.mark.parametrize("flags", ["raw", "f64"])
+def test_staged_batch_flags(hsc, ctx, flags):
+    """HSC_CLASSIFY_RAW_I and HSC_SVM_COUPLE_F64 in the stage-major batch."""
+    frames = synth.make_batch(6, seed=778)
+    fl = hsc.HSC_CLASSIFY_RAW_I if flags == "raw" else hsc.HSC_SVM_COUPLE_F64
+    _alone_vs_batch(hsc, ctx, frames, frames_to_device(frames), flags=fl)
