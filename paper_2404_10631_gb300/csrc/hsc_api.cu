@@ -12,6 +12,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <thread>
 #include <vector>
@@ -981,7 +982,10 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     const size_t tab_frames = sizeof(BatchFrame) * (size_t)n_frames;
     const size_t tab_gram = align_up(sizeof(GramItem) * (size_t)n_gram);
     const size_t tab_pix = align_up(sizeof(PixItem) * (size_t)n_pix);
-    const size_t tab_bytes = align_up(tab_frames) + tab_gram + tab_pix + sizeof(int) * (size_t)n_large;
+    const int g_grid = hsc::gram_items_grid(n_gram, sm);  // the Gram items' persistent CTAs
+    const size_t tab_large = align_up(sizeof(int) * (size_t)n_large);
+    const size_t tab_bytes =
+        align_up(tab_frames) + tab_gram + tab_pix + tab_large + sizeof(int) * (size_t)(g_grid + 1);
     const size_t tab = take(tab_bytes);
     const size_t total = off;
     cudaError_t e;
@@ -1046,6 +1050,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     GramItem *hg = reinterpret_cast<GramItem *>(host + align_up(tab_frames));
     PixItem *hp = reinterpret_cast<PixItem *>(host + align_up(tab_frames) + tab_gram);
     int *hl = reinterpret_cast<int *>(host + align_up(tab_frames) + tab_gram + tab_pix);
+    int *hc = reinterpret_cast<int *>(host + align_up(tab_frames) + tab_gram + tab_pix + tab_large);
     int ig = 0, ip = 0, cta = 0, il = 0;
     for (int f = 0; f < n_frames; ++f) {
         const hsc_frame &fr = frames[f];
@@ -1099,6 +1104,39 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         cta += fr.H * ((fr.W + 31) / 32);
         if (N > 4096) hl[il++] = f;
     }
+    {
+        // Gram items to CTAs, longest first to the least loaded CTA (at most
+        // gram_items_max_per_cta() each), then the table in CTA order
+        const int cap = hsc::gram_items_max_per_cta();
+        std::vector<int> order((size_t)n_gram);
+        for (int i = 0; i < n_gram; ++i) order[(size_t)i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return hg[a].c1 - hg[a].c0 > hg[b].c1 - hg[b].c0;
+        });
+        typedef std::pair<long, int> Load;  // (chunks, CTA)
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int c = 0; c < g_grid; ++c) heap.push(Load(0, c));
+        std::vector<std::vector<int>> per((size_t)g_grid);
+        for (int i : order) {
+            Load l = heap.top();
+            heap.pop();
+            while ((int)per[(size_t)l.second].size() >= cap) {  // full: retire it
+                l = heap.top();
+                heap.pop();
+            }
+            per[(size_t)l.second].push_back(i);
+            l.first += hg[i].c1 - hg[i].c0;
+            heap.push(l);
+        }
+        std::vector<GramItem> sorted((size_t)n_gram);
+        int k = 0;
+        for (int c = 0; c < g_grid; ++c) {
+            hc[c] = k;
+            for (int i : per[(size_t)c]) sorted[(size_t)k++] = hg[i];
+        }
+        hc[g_grid] = k;
+        std::copy(sorted.begin(), sorted.end(), hg);
+    }
     e = cudaMemcpyAsync(dev + tab, host, tab_bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_upload, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch table upload");
@@ -1106,6 +1144,8 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     const GramItem *dg = reinterpret_cast<const GramItem *>(dev + tab + align_up(tab_frames));
     const PixItem *dp = reinterpret_cast<const PixItem *>(dev + tab + align_up(tab_frames) + tab_gram);
     const int *dl = reinterpret_cast<const int *>(dev + tab + align_up(tab_frames) + tab_gram + tab_pix);
+    const int *dc = reinterpret_cast<const int *>(dev + tab + align_up(tab_frames) + tab_gram + tab_pix +
+                                                  tab_large);
     // ---- the launches: replayed from a graph when the launch configuration
     // is the one captured (the tables above carry the frames' pointers)
     const bool graph = (flags & HSC_BATCH_GRAPH) != 0;
@@ -1131,7 +1171,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     hsc_ctx *tc = graph ? &g_untimed : ctx;  // stage events only outside a capture
     {
         StageTimer t(tc, HSC_STAGE_MOMENTS, 3, st);
-        e = hsc::launch_batch_moments(df, n_frames, dg, n_gram, dl, n_large, B, sm, st);
+        e = hsc::launch_batch_moments(df, n_frames, dg, dc, n_gram, dl, n_large, B, sm, st);
     }
     if (e == cudaSuccess) {
         StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);

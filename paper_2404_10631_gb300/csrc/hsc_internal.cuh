@@ -145,13 +145,18 @@ int gram_tc_parts(long N, long per);
 // ---- stage-major batch (B <= 128): one launch per stage over every frame.
 // frames / items are device tables; results per frame are bit-identical to
 // the single-frame launches.
-cudaError_t launch_gram_items(const BatchFrame *frames, const GramItem *items, int n_items, int B,
-                              int sm_count, cudaStream_t st);
+int gram_items_grid(int n_items, int sm_count);
+int gram_items_max_per_cta();
+cudaError_t launch_gram_items(const BatchFrame *frames, const GramItem *items,
+                              const int *cta_items, int n_items, int B, int sm_count,
+                              cudaStream_t st);
+// cta_items: gram_items_grid(n_items, sm_count) + 1 offsets, CTA i taking
+// items [cta_items[i], cta_items[i + 1]) (at most gram_items_max_per_cta());
 // large: indices of the frames of more than 4096 pixels (their pilot takes a
 // CTA per band), n_large of them.
 cudaError_t launch_batch_moments(const BatchFrame *frames, int n_frames, const GramItem *items,
-                                 int n_items, const int *large, int n_large, int B, int sm_count,
-                                 cudaStream_t st);
+                                 const int *cta_items, int n_items, const int *large, int n_large,
+                                 int B, int sm_count, cudaStream_t st);
 cudaError_t launch_batch_jacobi(const BatchFrame *frames, int n_frames, int B, cudaStream_t st);
 cudaError_t launch_batch_project_svm(const BatchFrame *frames, const PixItem *items, int n_items,
                                      int B, const hsc_svm_model *model, bool couple_f64,

@@ -755,7 +755,8 @@ __device__ __forceinline__ GramItem get_item(const BatchFrame &one,
 
 // Work-item form of the B <= 128 Gram (stage-major batches, and single
 // frames the tensor map cannot describe: N % 4 != 0 or an unaligned cube).
-// A persistent CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; each
+// A persistent CTA takes its run of items from cta_items (one item per CTA
+// when cta_items is null); each
 // item is a frame's chunk range, the range gram_tc_kernel's CTA would take,
 // and gets the same partial Gram and sums, bit for bit: the same conversion,
 // MMA sequence, segments and epilogue. With items == nullptr the items are
@@ -767,7 +768,8 @@ __device__ __forceinline__ GramItem get_item(const BatchFrame &one,
 template <int kSt>
 __global__ void __launch_bounds__(Cfg<false, kSt>::kThreads, 1)
 gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames,
-                     const GramItem *__restrict__ items, int n_items, int B)
+                     const GramItem *__restrict__ items, const int *__restrict__ cta_items,
+                     int n_items, int B)
 {
     using G = Cfg<false, kSt>;
     constexpr int kStages = G::kStages, kOpStages = G::kOpStages, kAccHH = G::kAccHH;
@@ -789,6 +791,11 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Np = (B + 15) / 16 * 16;
+    // this CTA's items: [cta_items[i], cta_items[i + 1]) of the table (a
+    // load-balanced assignment made by the host), or item blockIdx.x
+    const int it_begin = cta_items ? cta_items[blockIdx.x] : (int)blockIdx.x;
+    const int it_end = cta_items ? cta_items[blockIdx.x + 1] : (int)blockIdx.x + 1;
+    (void)n_items;
 
     if (tid == 0) {
         for (int t = 0; t < kOpStages; ++t) {
@@ -835,7 +842,7 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
             long g = 0;  // chunks so far
             int s = 0;   // segments closed so far
             bool stop = false;
-            for (int it = blockIdx.x; it < n_items && !stop; it += gridDim.x) {
+            for (int it = it_begin; it < it_end && !stop; ++it) {
                 const GramItem item = get_item(one, items, it);
                 const int nch = item.c1 - item.c0;
                 for (int ji = 0; ji < nch; ++ji, ++g) {
@@ -869,10 +876,10 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
     } else if (warp >= 2) {
         // ---------------- converters: copies, conversion, epilogue
         // prefetch cursor: chunk pf_j of item pf_it
-        int pf_it = blockIdx.x, pf_j = 0, pf_n = 0, pf_c0 = 0;
+        int pf_it = it_begin, pf_j = 0, pf_n = 0, pf_c0 = 0;
         ItemFrame pf{};
         auto pf_item = [&]() {
-            if (pf_it < n_items) {
+            if (pf_it < it_end) {
                 const GramItem gi = get_item(one, items, pf_it);
                 pf = item_frame(one, frames, gi.frame);
                 pf_c0 = gi.c0;
@@ -880,12 +887,12 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
             }
         };
         auto fetch_next = [&](long slot) {
-            if (pf_it < n_items) {
+            if (pf_it < it_end) {
                 fetch_chunk<kBoxBytes, kConv>(staging + slot * kStageBytes, pf.cube, pf.N,
                                               pf.vec != 0, (long)(pf_c0 + pf_j) * kChunk, B, cv);
                 if (++pf_j == pf_n) {
                     pf_j = 0;
-                    pf_it += gridDim.x;
+                    ++pf_it;
                     pf_item();
                 }
             }
@@ -897,7 +904,7 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
         long g = 0;
         int s = 0;
         bool stop = false;
-        for (int l = 0, it = blockIdx.x; it < n_items && !stop; ++l, it += gridDim.x) {
+        for (int l = 0, it = it_begin; it < it_end && !stop; ++l, ++it) {
             const GramItem item = get_item(one, items, it);
             const ItemFrame fr = item_frame(one, frames, item.frame);
             const float c = b0 < B ? fr.shift[B + b0] : 1.f;
@@ -990,7 +997,7 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
     }
     if (*abort_p) return;
     // ---------------- FP32 recompute of the items whose values left FP16's range (rare)
-    for (int l = 0, it = blockIdx.x; it < n_items && l < kMaxLocalItems; ++l, it += gridDim.x) {
+    for (int l = 0, it = it_begin; it < it_end && l < kMaxLocalItems; ++l, ++it) {
         if (!((flagged[l >> 6] >> (l & 63)) & 1ull)) continue;
         const GramItem item = get_item(one, items, it);
         const ItemFrame fr = item_frame(one, frames, item.frame);
@@ -1074,13 +1081,13 @@ void launch_narrow(const CUtensorMap &map, const float *cube, int B, int Np, lon
 
 template <int kSt>
 void launch_items(const BatchFrame &one, const BatchFrame *frames, const GramItem *items,
-                  int n_items, int B, int grid, cudaStream_t st)
+                  const int *cta_items, int n_items, int B, int grid, cudaStream_t st)
 {
     const size_t smem = Cfg<false, kSt>::kSmem;
     cudaFuncSetAttribute(gram_tc_items_kernel<kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    gram_tc_items_kernel<kSt><<<grid, Cfg<false, kSt>::kThreads, smem, st>>>(one, frames, items,
-                                                                            n_items, B);
+    gram_tc_items_kernel<kSt><<<grid, Cfg<false, kSt>::kThreads, smem, st>>>(
+        one, frames, items, cta_items, n_items, B);
 }
 }  // namespace
 
@@ -1108,8 +1115,8 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
         one.N = N;
         one.per = (int)per;
         one.vec = 0;
-        if (stages == 3) launch_items<3>(one, nullptr, nullptr, parts, B, parts, st);
-        else launch_items<4>(one, nullptr, nullptr, parts, B, parts, st);
+        if (stages == 3) launch_items<3>(one, nullptr, nullptr, nullptr, parts, B, parts, st);
+        else launch_items<4>(one, nullptr, nullptr, nullptr, parts, B, parts, st);
         return cudaGetLastError();
     }
     CUtensorMap map;
@@ -1139,17 +1146,28 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
     return cudaGetLastError();
 }
 
-// Every item of a stage-major batch (B <= 128) in one persistent launch:
-// one CTA per SM, or more when a CTA would get over kMaxLocalItems items.
-cudaError_t launch_gram_items(const BatchFrame *frames, const GramItem *items, int n_items, int B,
-                              int sm_count, cudaStream_t st)
+// CTAs of the persistent launch over n_items items: one per SM, or more when
+// a CTA would get over kMaxLocalItems items.
+int gram_items_grid(int n_items, int sm_count)
 {
-    if (B < 1 || B > 128 || n_items < 1) return cudaErrorInvalidValue;
     int grid = n_items < sm_count ? n_items : sm_count;
     const int need = (n_items + kMaxLocalItems - 1) / kMaxLocalItems;
-    if (grid < need) grid = need;
+    return grid < need ? need : grid;
+}
+
+int gram_items_max_per_cta() { return kMaxLocalItems; }
+
+// Every item of a stage-major batch (B <= 128) in one persistent launch of
+// gram_items_grid(n_items, sm_count) CTAs, CTA i taking items
+// [cta_items[i], cta_items[i + 1]).
+cudaError_t launch_gram_items(const BatchFrame *frames, const GramItem *items,
+                              const int *cta_items, int n_items, int B, int sm_count,
+                              cudaStream_t st)
+{
+    if (B < 1 || B > 128 || n_items < 1 || !cta_items) return cudaErrorInvalidValue;
     BatchFrame none{};
-    launch_items<4>(none, frames, items, n_items, B, grid, st);
+    launch_items<4>(none, frames, items, cta_items, n_items, B, gram_items_grid(n_items, sm_count),
+                    st);
     return cudaGetLastError();
 }
 

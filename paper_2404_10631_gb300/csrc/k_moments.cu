@@ -352,28 +352,56 @@ gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gr
     }
 }
 
-// Stage-major batch form of gram_reduce_kernel: CTA (t, f) takes the t-th
-// 32 x 32 tile (b-block <= c-block) of frame f's matrix, each thread four
-// entries (b, c), b <= c, replaying gram_reduce_kernel's arithmetic: slice s
-// sums the partials s, s + 8, ... in double-float and slices 1..7 are then
-// added to slice 0. With at most 8 partials (a frame of at most 8192 pixels)
+// The double-float sum gram_reduce_kernel forms for one entry from the
+// partials base[k * stride], k < n_part: slice s sums the partials s, s + 8,
+// ... and slices 1..7 are then added to slice 0. With at most 8 partials
 // every slice holds one partial or none, and since these sums never produce
 // -0, adding an empty slice changes nothing: the result is the double-float
-// sum of the partials in order, which is what is formed here. C2 (the pairs
-// the eigensolver reads) and mu are written, the tile and its mirror image
-// both coalesced through shared memory; the FP64 C is not needed by the batch.
+// sum of the partials in order, with every load issued first.
+__device__ __forceinline__ void slice_sum(const float *__restrict__ base, size_t stride,
+                                          int n_part, float &s, float &l)
+{
+    s = 0.f;
+    l = 0.f;
+    if (n_part <= kRedSlices) {
+        float v[kRedSlices];
+#pragma unroll
+        for (int k = 0; k < kRedSlices; ++k) v[k] = k < n_part ? base[(size_t)k * stride] : 0.f;
+#pragma unroll
+        for (int k = 0; k < kRedSlices; ++k)
+            if (k < n_part) df_acc(s, l, v[k]);
+        return;
+    }
+    for (int sl = 0; sl < kRedSlices; ++sl) {
+        float s1 = 0.f, l1 = 0.f;
+        for (int k = sl; k < n_part; k += kRedSlices) df_acc(s1, l1, base[(size_t)k * stride]);
+        if (sl == 0) {
+            s = s1;
+            l = l1;
+        } else {
+            df_acc2(s, l, s1, l1);
+        }
+    }
+}
+
+// Stage-major batch form of gram_reduce_kernel: CTA (t, f) takes the t-th
+// 32 x 32 tile (b-block <= c-block) of frame f's matrix, each thread four
+// entries (b, c), b <= c, with gram_reduce_kernel's arithmetic (slice_sum;
+// delta of a band formed once per tile, the same double for every entry).
+// FP64 is the narrow pipe here: each entry costs 9 FP64 operations. C2 (the
+// pairs the eigensolver reads) and mu are written, the tile and its mirror
+// image both coalesced through shared memory; the batch needs no FP64 C.
 __global__ void __launch_bounds__(256)
 gram_reduce_batch_kernel(int B, const BatchFrame *__restrict__ frames)
 {
     __shared__ float2 tile[32][33];
+    __shared__ double dlt[64];  // delta of the tile's 32 rows b, then of its 32 columns c
     const BatchFrame *fp = frames + blockIdx.y;
     const double inv_N = 1.0 / (double)fp->N;
     const int n_part = fp->n_part;
     const float *__restrict__ gram_part = fp->gram_part;
     const float *__restrict__ sum_part = fp->sum_part;
-    const float *__restrict__ shift = fp->shift;
     float2 *__restrict__ C2 = fp->C2;
-    double *__restrict__ mu = fp->mu;
     const long BB = (long)B * B;
     // tile t -> (tb, tc), tb <= tc, row-major over the upper triangle of blocks
     const int T = (B + 31) / 32;
@@ -384,6 +412,18 @@ gram_reduce_batch_kernel(int B, const BatchFrame *__restrict__ frames)
     }
     const int tc = tb + t;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < 64) {
+        const int band = threadIdx.x < 32 ? tb * 32 + threadIdx.x : tc * 32 + threadIdx.x - 32;
+        double d = 0.0;
+        if (band < B) {
+            float sv, lv;
+            slice_sum(sum_part + band, (size_t)B, n_part, sv, lv);
+            d = ((double)sv + (double)lv) * inv_N;
+            if (threadIdx.x < 32 && tb == tc) fp->mu[band] = (double)fp->shift[band] + d;
+        }
+        dlt[threadIdx.x] = d;
+    }
+    __syncthreads();
     const int b = tb * 32 + lane;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -391,53 +431,12 @@ gram_reduce_batch_kernel(int B, const BatchFrame *__restrict__ frames)
         const int c = tc * 32 + cl;
         float2 pr = make_float2(0.f, 0.f);
         if (b < B && c < B && c >= b) {
-            const long e = (long)c * B + b;
-            float g = 0.f, gl = 0.f, sb = 0.f, lb = 0.f, sc = 0.f, lc = 0.f;
-            if (n_part <= kRedSlices) {
-                float vg[kRedSlices], vb[kRedSlices], vc[kRedSlices];
-#pragma unroll
-                for (int k = 0; k < kRedSlices; ++k) {
-                    const bool in = k < n_part;
-                    vg[k] = in ? gram_part[(size_t)k * BB + e] : 0.f;
-                    vb[k] = in ? sum_part[(size_t)k * B + b] : 0.f;
-                    vc[k] = in ? sum_part[(size_t)k * B + c] : 0.f;
-                }
-#pragma unroll
-                for (int k = 0; k < kRedSlices; ++k)
-                    if (k < n_part) {
-                        df_acc(g, gl, vg[k]);
-                        df_acc(sb, lb, vb[k]);
-                        df_acc(sc, lc, vc[k]);
-                    }
-            } else {
-                for (int sl = 0; sl < kRedSlices; ++sl) {
-                    float g1 = 0.f, gl1 = 0.f, sb1 = 0.f, lb1 = 0.f, sc1 = 0.f, lc1 = 0.f;
-                    for (int k = sl; k < n_part; k += kRedSlices) {
-                        df_acc(g1, gl1, gram_part[(size_t)k * BB + e]);
-                        df_acc(sb1, lb1, sum_part[(size_t)k * B + b]);
-                        df_acc(sc1, lc1, sum_part[(size_t)k * B + c]);
-                    }
-                    if (sl == 0) {
-                        g = g1;
-                        gl = gl1;
-                        sb = sb1;
-                        lb = lb1;
-                        sc = sc1;
-                        lc = lc1;
-                    } else {
-                        df_acc2(g, gl, g1, gl1);
-                        df_acc2(sb, lb, sb1, lb1);
-                        df_acc2(sc, lc, sc1, lc1);
-                    }
-                }
-            }
-            const double db = ((double)sb + (double)lb) * inv_N;
-            const double dc = ((double)sc + (double)lc) * inv_N;
-            const double v = fma(-db, dc, ((double)g + (double)gl) * inv_N);
+            float g, gl;
+            slice_sum(gram_part + (long)c * B + b, (size_t)BB, n_part, g, gl);
+            const double v = fma(-dlt[lane], dlt[32 + cl], ((double)g + (double)gl) * inv_N);
             const float hi = __double2float_rn(v);
             pr = make_float2(hi, __double2float_rn(v - (double)hi));
             C2[(size_t)c * B + b] = pr;  // row c: lanes on consecutive b
-            if (b == c) mu[b] = (double)shift[b] + db;
         }
         tile[cl][lane] = pr;
     }
@@ -505,14 +504,14 @@ cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s
 // Stage-major batch (B <= 128): the pilots of every frame, every Gram item
 // in one persistent launch, the reductions of every frame.
 cudaError_t launch_batch_moments(const BatchFrame *frames, int n_frames, const GramItem *items,
-                                 int n_items, const int *large, int n_large, int B, int sm_count,
-                                 cudaStream_t st)
+                                 const int *cta_items, int n_items, const int *large, int n_large,
+                                 int B, int sm_count, cudaStream_t st)
 {
     if (n_frames < 1 || n_frames > 65535) return cudaErrorInvalidValue;
     pilot_batch_kernel<<<dim3((B + 7) / 8, n_frames), 256, 0, st>>>(B, frames);
     if (n_large > 0)
         pilot_batch_large_kernel<<<dim3(B, n_large), 256, 0, st>>>(B, frames, large);
-    cudaError_t e = launch_gram_items(frames, items, n_items, B, sm_count, st);
+    cudaError_t e = launch_gram_items(frames, items, cta_items, n_items, B, sm_count, st);
     if (e != cudaSuccess) return e;
     const int T = (B + 31) / 32;
     gram_reduce_batch_kernel<<<dim3((unsigned)(T * (T + 1) / 2), n_frames), 256, 0, st>>>(B,
