@@ -2,8 +2,11 @@
 
     python -m paper_2404_10631_gb300.profile_case --op classify --reps 2
 
---op: classify | covariance | pca | svm | knn. The first call is a warm-up; an
-ncu capture of the second launch of a kernel uses ``-s 1 -c 1``.
+--op: classify | covariance | pca | svm | knn | batch. The first call is a
+warm-up; an ncu capture of the second launch of a kernel uses ``-s 1 -c 1``.
+--op batch: hsc_classify_batch over the 256 uneven snapshot frames (125
+bands, sides 40-64 px, shared model, K = 16, 7-row window), stage-major
+(8 launches per call), --reps calls after the same number of warm-up calls.
 """
 
 from __future__ import annotations
@@ -16,7 +19,7 @@ import sys
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", default="classify",
-                    choices=("classify", "covariance", "pca", "svm", "knn"))
+                    choices=("classify", "covariance", "pca", "svm", "knn", "batch"))
     ap.add_argument("--config", type=int, default=2, help="synthetic workload (1 tiny, 2 neuro)")
     ap.add_argument("--reps", type=int, default=2)
     a = ap.parse_args(argv)
@@ -28,6 +31,18 @@ def main(argv=None):
     from paper_2404_10631_gb300 import build
 
     build.build()
+    if a.op == "batch":
+        frames = synth.make_batch(256)
+        f0 = frames[0]
+        ctx = hsc.Context(0)
+        model = hsc.Model.from_host(f0.model)
+        cubes = [torch.as_tensor(fr.cube, device="cuda") for fr in frames]
+        labs = [torch.empty(fr.cube.shape[1:], dtype=torch.int32, device="cuda") for fr in frames]
+        for _ in range(2 * a.reps):
+            hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, labels=labs)
+        ctx.sync()
+        print("ok batch: %d frames, %d calls" % (len(frames), 2 * a.reps))
+        return
     f = synth.make_config(a.config)
     ctx = hsc.Context(0)
     cube = torch.as_tensor(f.cube, device="cuda")
