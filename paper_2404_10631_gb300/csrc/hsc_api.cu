@@ -130,7 +130,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, bsq, vk, lamk,
-        vkf, total;
+        vkf, p4, total;
     int n_part;
 };
 
@@ -168,6 +168,8 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
         L.v1f = take(sizeof(float) * B);
         L.muf = take(sizeof(float) * B);
         L.jA = take(sizeof(float) * hsc::jacobi_global_floats(B));
+        if (k > 0)  // the whole path: P pixel-interleaved for the KNN's gathers
+            L.p4 = take(sizeof(float4) * (size_t)((k + 3) / 4) * (size_t)N);
     }
     if (need_I) L.tmpI = take(sizeof(float) * (size_t)N);
     if (need_P) L.tmpP = take(sizeof(float) * (size_t)k * N);
@@ -233,6 +235,7 @@ PcaScratch carve(hsc_ctx *ctx, const Layout &L)
     s.v1f = reinterpret_cast<float *>(b + L.v1f);
     s.muf = reinterpret_cast<float *>(b + L.muf);
     s.jac_A = reinterpret_cast<float *>(b + L.jA);
+    s.P4 = L.p4 ? reinterpret_cast<float4 *>(b + L.p4) : nullptr;
     s.n_part = L.n_part;
     return s;
 }
@@ -331,7 +334,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
         e = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model,
                                     (flags & HSC_SVM_COUPLE_F64) != 0, Pm, nullptr, s.ctl,
                                     ctx->sm_count, st, tu.svm_blocks_per_sm * ctx->sm_count,
-                                    tu.svm_px);
+                                    tu.svm_px, s.P4);
     }
     if (e == cudaSuccess && !(flags & HSC_CLASSIFY_RAW_I)) {
         StageTimer t(tc, HSC_STAGE_NORMALIZE, 1, st);
@@ -341,7 +344,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
         StageTimer t(tc, HSC_STAGE_KNN, 2, st);
         e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
                             out_probs, labels, nullptr, s.ctl, st,
-                            params->search);
+                            params->search, s.P4);
     }
     return e;
 }
@@ -935,7 +938,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     constexpr int kPixPerItem = 1024;
     // ---- layout: control blocks, per-frame buffers, tables
     struct FrameLay {
-        size_t shift, gram, sums, C, C2, mu, v1, lam, v1f, muf, I, P;
+        size_t shift, gram, sums, C, C2, mu, v1, lam, v1f, muf, I, P, P4;
         long per;
         int parts, vec;
     };
@@ -969,6 +972,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         L.muf = take(sizeof(float) * B);
         L.I = fr.one_band ? 0 : take(sizeof(float) * (size_t)N);
         L.P = fr.probs ? 0 : take(sizeof(float) * (size_t)k * N);
+        L.P4 = take(sizeof(float4) * (size_t)((k + 3) / 4) * (size_t)N);
         n_gram += L.parts;
         n_pix += (int)((N + kPixPerItem - 1) / kPixPerItem);
         n_ctas += fr.H * ((fr.W + 31) / 32);
@@ -1060,6 +1064,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         b.cube = fr.cube;
         b.I = fr.one_band ? fr.one_band : reinterpret_cast<float *>(dev + L.I);
         b.P = fr.probs ? fr.probs : reinterpret_cast<float *>(dev + L.P);
+        b.P4 = reinterpret_cast<float4 *>(dev + L.P4);
         b.O = fr.out_probs;
         b.labels = fr.labels;
         b.shift = reinterpret_cast<float *>(dev + L.shift);

@@ -71,6 +71,7 @@ struct PcaScratch {
     double *vk = nullptr;    // multi-PC: n_vec x B leading eigenvectors (row 0 = v1)
     double *lamk = nullptr;  // multi-PC: n_vec eigenvalues
     float *vkf = nullptr;    // multi-PC: float copies of vk
+    float4 *P4 = nullptr;    // classify: the probabilities pixel-interleaved for the KNN
     int n_part;
 };
 
@@ -81,6 +82,7 @@ struct BatchFrame {
     const float *cube;   // B x N, band-sequential
     float *I;            // N: the projection, then the normalised map
     float *P;            // k x N probabilities
+    float4 *P4;          // the same, pixel-interleaved ((k + 3) / 4 float4 per pixel)
     float *O;            // k x N filtered probabilities (nullable)
     int32_t *labels;     // N
     float *shift;        // 2B
@@ -175,11 +177,13 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec
 
 // Pass 2 over the cube: projection (if v1f != nullptr) + SVM decision values,
 // Platt, coupling (if probs != nullptr). I_raw min/max into ctl keys.
+// P4 (nullable): also write the probabilities pixel-interleaved, (k + 3) / 4
+// float4 per pixel (classes past k zero), for the pruned KNN's gathers.
 cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
                                const float *muf, float *I_raw, const hsc_svm_model *model,
                                bool couple_f64, float *probs, int32_t *svm_labels,
                                Control *ctl, int sm_count, cudaStream_t st, int max_blocks = 0,
-                               int px = 0);
+                               int px = 0, float4 *P4 = nullptr);
 
 // out_j = v_j^T (x - mu) for the n_pc (1..8) rows of vkf, n_pc x N.
 cudaError_t launch_project_multi(const float *cube, int B, long N, const float *vkf,
@@ -200,8 +204,11 @@ cudaError_t launch_bip_to_bsq(const float *bip, int B, long N, float *bsq, cudaS
 // Uploads the pruned walk's offset table to the current device (once).
 cudaError_t knn_init(int device);
 
+// P4 (nullable): P pixel-interleaved, (k + 3) / 4 float4 per pixel, which
+// the pruned search gathers from (one 16-byte load per 4 classes).
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr,
-                       Control *ctl, cudaStream_t st, int search);
+                       Control *ctl, cudaStream_t st, int search,
+                       const float4 *P4 = nullptr);
 
 }  // namespace hsc

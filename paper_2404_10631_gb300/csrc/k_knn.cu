@@ -466,13 +466,38 @@ __device__ __noinline__ Key buf_max(const LaneBuf &buf, int n)
     return m;
 }
 
-// Adds the probabilities of the KC classes of candidate q to acc.
+// Adds the probabilities of the KC classes of candidate q to acc: from the
+// k x N planes P, or (P4 != nullptr) from the pixel-interleaved copy the
+// projection/SVM pass writes beside them, (KC + 3) / 4 16-byte loads per
+// candidate (the same values, added in the same order).
 template <int KC>
 __device__ __forceinline__ void add_probs(float (&acc)[KC], const float *__restrict__ P, long N,
                                           int q)
 {
 #pragma unroll
     for (int cl = 0; cl < KC; ++cl) acc[cl] += __ldg(P + (size_t)cl * (size_t)N + q);
+}
+
+template <int KC>
+__device__ __forceinline__ void add_probs4(float (&acc)[KC], const float4 *__restrict__ P4, int q)
+{
+    constexpr int NQ = (KC + 3) / 4;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        const float4 v = __ldg(P4 + (size_t)q * NQ + i);
+        const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (4 * i + e < KC) acc[4 * i + e] += w[e];
+    }
+}
+
+template <int KC, bool kP4>
+__device__ __forceinline__ void gather_probs(float (&acc)[KC], const float *__restrict__ P, long N,
+                                             const float4 *__restrict__ P4, int q)
+{
+    if (kP4) add_probs4(acc, P4, q);
+    else add_probs(acc, P, N, q);
 }
 
 template <int KC>
@@ -494,12 +519,13 @@ __device__ __forceinline__ void write_pixel(const float (&acc)[KC], int K, long 
     labels[p] = best;
 }
 
-template <int KC, bool kBatch = false>
+template <int KC, bool kBatch = false, bool kP4 = false>
 __global__ void __launch_bounds__(kWalkThreads)
 knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
                   int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
                   bool redo_all, Control *ctl, const BatchFrame *__restrict__ frames,
-                  int n_frames, int2 *__restrict__ redo_list, unsigned redo_cap)
+                  int n_frames, int2 *__restrict__ redo_list, unsigned redo_cap,
+                  const float4 *__restrict__ P4)
 {
     extern __shared__ float sm[];
     __shared__ float s_min[kWalkThreads / 32], s_max[kWalkThreads / 32];
@@ -516,6 +542,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         const BatchFrame &fr = frames[lo];
         I = fr.I;
         P = fr.P;
+        P4 = fr.P4;
         H = fr.H;
         W = fr.W;
         O = fr.O;
@@ -653,7 +680,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                 const float h = __fadd_rn(st, e);
                 if (h < L) {  // one of the K nearest
                     ++m;
-                    add_probs(acc, P, N, qrow + j);
+                    gather_probs<KC, kP4>(acc, P, N, P4, qrow + j);
                     continue;
                 }
                 if (h > tau.hi) continue;
@@ -662,7 +689,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                 const Key kk = {h, lo, qrow + j};
                 if (h == L && lo < 0.f) {
                     ++m;
-                    add_probs(acc, P, N, qrow + j);
+                    gather_probs<KC, kP4>(acc, P, N, P4, qrow + j);
                     continue;
                 }
                 if (!key_le(kk, tau)) continue;
@@ -724,7 +751,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
             }
         }
         if (im != a) bnd.put(im, bnd.get(a));
-        add_probs(acc, P, N, best.q);
+        gather_probs<KC, kP4>(acc, P, N, P4, best.q);
     }
     write_pixel(acc, K, N, p, O, labels);
 }
@@ -733,7 +760,8 @@ template <int KC>
 __device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float *__restrict__ P,
                                         int H, int W, int K, int R, float lam,
                                         float *__restrict__ O, int32_t *__restrict__ labels,
-                                        int32_t *__restrict__ nbr, Control *ctl, long p, float *sm)
+                                        int32_t *__restrict__ nbr, Control *ctl, long p, float *sm,
+                                        const float4 *__restrict__ P4)
 {
     const long N = (long)H * W;
     const int cap = K + kRedoExtra;
@@ -837,7 +865,10 @@ __device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float
     float acc[KC];
 #pragma unroll
     for (int cl = 0; cl < KC; ++cl) acc[cl] = 0.f;
-    for (int a = 0; a < n; ++a) add_probs(acc, P, N, buf.q[a * kRedoThreads]);
+    for (int a = 0; a < n; ++a) {
+        if (P4) add_probs4(acc, P4, buf.q[a * kRedoThreads]);
+        else add_probs(acc, P, N, buf.q[a * kRedoThreads]);
+    }
     write_pixel(acc, K, N, p, O, labels);
 }
 
@@ -853,7 +884,7 @@ template <int KC>
 __global__ void __launch_bounds__(kRedoThreads)
 knn_redo_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
                 int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
-                int32_t *__restrict__ nbr, Control *ctl)
+                int32_t *__restrict__ nbr, Control *ctl, const float4 *__restrict__ P4)
 {
     extern __shared__ float sm[];
     const long N = (long)H * W;
@@ -862,7 +893,7 @@ knn_redo_kernel(const float *__restrict__ I, const float *__restrict__ P, int H,
          base += (long)gridDim.x * kRedoThreads) {
         const long p = base + threadIdx.x;
         if (p < N && labels[p] == kRedoLabel)
-            redo_pixel<KC>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, p, sm);
+            redo_pixel<KC>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, p, sm, P4);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -893,7 +924,7 @@ knn_redo_batch_kernel(const BatchFrame *__restrict__ frames, int K, int R, float
         const int2 fp = redo_list[i];
         const BatchFrame &fr = frames[fp.x];
         redo_pixel<KC>(fr.I, fr.P, fr.H, fr.W, K, R, lam, fr.O, fr.labels, nullptr, fr.ctl,
-                       (long)fp.y, sm);
+                       (long)fp.y, sm, fr.P4);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -917,16 +948,25 @@ size_t redo_smem_bytes(int K) { return sizeof(float) * 3 * (size_t)(K + kRedoExt
 
 template <int KC>
 cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, int R, float lam,
-                          float *O, int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st)
+                          float *O, int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st,
+                          const float4 *P4)
 {
     const size_t smem = pruned_smem_bytes(R, H);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(knn_pruned_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
     dim3 grid((W + kWalkThreads - 1) / kWalkThreads, H);
-    knn_pruned_kernel<KC><<<grid, kWalkThreads, smem, st>>>(I, P, H, W, K, R, lam, O, labels,
-                                                            nbr != nullptr, ctl, nullptr, 0,
-                                                            nullptr, 0u);
+    if (P4) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(knn_pruned_kernel<KC, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        knn_pruned_kernel<KC, false, true><<<grid, kWalkThreads, smem, st>>>(
+            I, P, H, W, K, R, lam, O, labels, nbr != nullptr, ctl, nullptr, 0, nullptr, 0u, P4);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(knn_pruned_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        knn_pruned_kernel<KC><<<grid, kWalkThreads, smem, st>>>(I, P, H, W, K, R, lam, O, labels,
+                                                                nbr != nullptr, ctl, nullptr, 0,
+                                                                nullptr, 0u, nullptr);
+    }
     const long N = (long)H * W;
     const size_t rsmem = redo_smem_bytes(K);
     if (rsmem > 48 * 1024)
@@ -934,7 +974,7 @@ cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, i
                              (int)rsmem);
     const long rgrid = (N + kRedoThreads - 1) / kRedoThreads;  // persistent: at most 64 CTAs
     knn_redo_kernel<KC><<<(unsigned)(rgrid < 64 ? rgrid : 64), kRedoThreads, rsmem, st>>>(
-        I, P, H, W, K, R, lam, O, labels, nbr, ctl);
+        I, P, H, W, K, R, lam, O, labels, nbr, ctl, P4);
     return cudaGetLastError();
 }
 
@@ -945,11 +985,11 @@ cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ct
 {
     const size_t smem = pruned_smem_bytes(R, max_rows);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(knn_pruned_kernel<KC, true>,
+        cudaFuncSetAttribute(knn_pruned_kernel<KC, true, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    knn_pruned_kernel<KC, true><<<n_ctas, kWalkThreads, smem, st>>>(
+    knn_pruned_kernel<KC, true, true><<<n_ctas, kWalkThreads, smem, st>>>(
         nullptr, nullptr, 0, 0, K, R, lam, nullptr, nullptr, false, nullptr, frames, n_frames,
-        redo_list, redo_cap);
+        redo_list, redo_cap, nullptr);
     const size_t rsmem = redo_smem_bytes(K);
     if (rsmem > 48 * 1024)
         cudaFuncSetAttribute(knn_redo_batch_kernel<KC>,
@@ -1035,7 +1075,7 @@ cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas,
 
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr, Control *ctl,
-                       cudaStream_t st, int search)
+                       cudaStream_t st, int search, const float4 *P4)
 {
     if (search == HSC_KNN_SEARCH_HEAP) {
         const int nrows_max = R < H ? R : H;
@@ -1051,14 +1091,14 @@ cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int 
     const bool pruned = search != HSC_KNN_SEARCH_FULL;
     if (pruned && lambda > 0.f) {
         switch (k) {
-        case 1: return launch_pruned<1>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
-        case 2: return launch_pruned<2>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
-        case 3: return launch_pruned<3>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
-        case 4: return launch_pruned<4>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
-        case 5: return launch_pruned<5>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
-        case 6: return launch_pruned<6>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
-        case 7: return launch_pruned<7>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
-        case 8: return launch_pruned<8>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st);
+        case 1: return launch_pruned<1>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 2: return launch_pruned<2>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 3: return launch_pruned<3>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 4: return launch_pruned<4>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 5: return launch_pruned<5>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 6: return launch_pruned<6>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 7: return launch_pruned<7>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 8: return launch_pruned<8>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
         default: return cudaErrorInvalidValue;
         }
     }

@@ -105,7 +105,8 @@ __device__ __forceinline__ void project_svm_groups(
     const float *__restrict__ cube, int B, long N, const float *ws, const float *sbias,
     const float *sa, const float *sb, bool do_pca, long g_begin, long g_end, long g_step,
     float *__restrict__ I_raw, float *__restrict__ probs, int32_t *__restrict__ labels,
-    int couple_f64, float &lmin, float &lmax, bool &bad, long p_base = 0)
+    int couple_f64, float &lmin, float &lmax, bool &bad, long p_base = 0,
+    float4 *__restrict__ P4 = nullptr)
 {
     constexpr int M = KC * (KC - 1) / 2;
     constexpr int MA = M > 0 ? M : 1;
@@ -183,6 +184,16 @@ __device__ __forceinline__ void project_svm_groups(
                     }
                 }
                 if (labels) labels[p] = best;
+                if (P4) {  // pixel-interleaved copy for the KNN's gathers
+                    constexpr int NQ = (KC + 3) / 4;
+#pragma unroll
+                    for (int i = 0; i < NQ; ++i) {
+                        float v[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = 4 * i + e < KC ? pr[4 * i + e] : 0.f;
+                        P4[(size_t)p * NQ + i] = make_float4(v[0], v[1], v[2], v[3]);
+                    }
+                }
             }
         }
     }
@@ -243,7 +254,8 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
                    const float *__restrict__ w, const float *__restrict__ bias,
                    const float *__restrict__ pa, const float *__restrict__ pb,
                    float *__restrict__ I_raw, float *__restrict__ probs,
-                   int32_t *__restrict__ labels, int couple_f64, Control *ctl)
+                   int32_t *__restrict__ labels, int couple_f64, Control *ctl,
+                   float4 *__restrict__ P4)
 {
     constexpr int M = KC * (KC - 1) / 2;
     constexpr int MA = M > 0 ? M : 1;
@@ -257,7 +269,7 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
     project_svm_groups<KC, PX, kVec>(cube, B, N, ws, sbias, sa, sb, v1f != nullptr,
                                (long)blockIdx.x * blockDim.x + threadIdx.x, ngroups,
                                (long)gridDim.x * blockDim.x, I_raw, probs, labels, couple_f64,
-                               lmin, lmax, bad);
+                               lmin, lmax, bad, 0, P4);
     finish_block(v1f != nullptr, lmin, lmax, bad, ctl);
 }
 
@@ -284,12 +296,12 @@ project_svm_batch_kernel(const BatchFrame *__restrict__ frames, const PixItem *_
     if (fr.vec)
         project_svm_groups<KC, 4, true>(fr.cube, B, fr.N, ws, sbias, sa, sb, true,
                                         it.g0 + threadIdx.x, it.g1, blockDim.x, fr.I, fr.P,
-                                        nullptr, couple_f64, lmin, lmax, bad);
+                                        nullptr, couple_f64, lmin, lmax, bad, 0, fr.P4);
     else  // pixels g0 * 4 + t + 256 u of thread t: every load coalesced
         project_svm_groups<KC, 4, false, true>(fr.cube, B, fr.N, ws, sbias, sa, sb, true,
                                                threadIdx.x, threadIdx.x + 1, 1, fr.I, fr.P,
                                                nullptr, couple_f64, lmin, lmax, bad,
-                                               (long)it.g0 * 4);
+                                               (long)it.g0 * 4, fr.P4);
     finish_block(true, lmin, lmax, bad, fr.ctl);
 }
 
@@ -320,7 +332,8 @@ __global__ void normalize_batch_kernel(const BatchFrame *__restrict__ frames,
 template <int KC, int PX, bool kVec>
 cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const float *muf,
                       float *I_raw, const hsc_svm_model *m, bool f64, float *probs,
-                      int32_t *labels, Control *ctl, int sm_count, cudaStream_t st, int max_blocks)
+                      int32_t *labels, Control *ctl, int sm_count, cudaStream_t st, int max_blocks,
+                      float4 *P4)
 {
     constexpr int M = KC * (KC - 1) / 2;
     size_t smem = sizeof(float) * (size_t)B * (M + 2);
@@ -334,7 +347,7 @@ cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const 
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, kThreads, smem, st>>>(
         cube, B, N, v1f, muf, m ? m->w : nullptr, m ? m->b : nullptr, m ? m->platt_a : nullptr,
-        m ? m->platt_b : nullptr, I_raw, probs, labels, f64 ? 1 : 0, ctl);
+        m ? m->platt_b : nullptr, I_raw, probs, labels, f64 ? 1 : 0, ctl, P4);
     return cudaGetLastError();
 }
 
@@ -342,17 +355,17 @@ template <int PX, bool kVec>
 cudaError_t dispatch_k(int k, const float *cube, int B, long N, const float *v1f,
                        const float *muf, float *I_raw, const hsc_svm_model *m, bool f64,
                        float *probs, int32_t *labels, Control *ctl, int sm, cudaStream_t st,
-                       int mb)
+                       int mb, float4 *P4)
 {
     switch (k) {
-    case 0: return launch_kc<0, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 2: return launch_kc<2, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 3: return launch_kc<3, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 4: return launch_kc<4, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 5: return launch_kc<5, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 6: return launch_kc<6, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 7: return launch_kc<7, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
-    case 8: return launch_kc<8, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb);
+    case 0: return launch_kc<0, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
+    case 2: return launch_kc<2, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
+    case 3: return launch_kc<3, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
+    case 4: return launch_kc<4, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
+    case 5: return launch_kc<5, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
+    case 6: return launch_kc<6, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
+    case 7: return launch_kc<7, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
+    case 8: return launch_kc<8, PX, kVec>(cube, B, N, v1f, muf, I_raw, m, f64, probs, labels, ctl, sm, st, mb, P4);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -362,18 +375,18 @@ cudaError_t dispatch_k(int k, const float *cube, int B, long N, const float *v1f
 cudaError_t launch_project_svm(const float *cube, int B, long N, const float *v1f,
                                const float *muf, float *I_raw, const hsc_svm_model *model,
                                bool couple_f64, float *probs, int32_t *svm_labels, Control *ctl,
-                               int sm_count, cudaStream_t st, int max_blocks, int px)
+                               int sm_count, cudaStream_t st, int max_blocks, int px, float4 *P4)
 {
     const int k = (probs != nullptr && model != nullptr) ? model->n_classes : 0;
     const bool vec = (N % 4 == 0) && ((reinterpret_cast<uintptr_t>(cube) & 15u) == 0);
     if (px == 1)
         return dispatch_k<1, false>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs,
-                                    svm_labels, ctl, sm_count, st, max_blocks);
+                                    svm_labels, ctl, sm_count, st, max_blocks, P4);
     if (vec)
         return dispatch_k<4, true>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs,
-                                   svm_labels, ctl, sm_count, st, max_blocks);
+                                   svm_labels, ctl, sm_count, st, max_blocks, P4);
     return dispatch_k<4, false>(k, cube, B, N, v1f, muf, I_raw, model, couple_f64, probs,
-                                svm_labels, ctl, sm_count, st, max_blocks);
+                                svm_labels, ctl, sm_count, st, max_blocks, P4);
 }
 
 cudaError_t launch_normalize(const float *I_raw, float *I_norm, long N, Control *ctl,
