@@ -22,6 +22,8 @@ def main(argv=None):
                     choices=("classify", "covariance", "pca", "svm", "knn", "batch"))
     ap.add_argument("--config", type=int, default=2, help="synthetic workload (1 tiny, 2 neuro)")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--search", default="auto", choices=("auto", "full", "pruned", "heap"),
+                    help="KNN search of --op knn")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -59,7 +61,9 @@ def main(argv=None):
         elif a.op == "svm":
             hsc.hsc_svm_probs(ctx, cube, model, probs=P)
         else:
-            hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam)
+            search = {"auto": hsc.HSC_KNN_SEARCH_AUTO, "full": hsc.HSC_KNN_SEARCH_FULL,
+                      "pruned": hsc.HSC_KNN_SEARCH_PRUNED, "heap": hsc.HSC_KNN_SEARCH_HEAP}[a.search]
+            hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam, search=search)
     ctx.sync()
     print("ok", a.op, "jacobi sweeps, refine iters, sweep cycles, refine cycles:",
           ctx.pca_diagnostics(cycles=True))
