@@ -396,7 +396,7 @@ constexpr int kTabR2 = 400;            // table: dr^2 + dc^2 <= 400
 constexpr int kTabDr = 16;             // |dr| <= 16: windows of up to 32 rows
 constexpr int kTabDc = 20;             // |dc| <= 20 follows from kTabR2
 constexpr int kTabCap = 1200;
-constexpr int kBnd = 12;               // undecided keys per lane (occupancy: 15 KB per CTA)
+constexpr int kBnd = 8;                // undecided keys per lane
 constexpr int kRedoLabel = -2147483647 - 1;
 constexpr int kBatchRedoCtas = 1024;  // the batched redo pass's grid (exits at once when idle)
 constexpr int kRedoThreads = 32;
