@@ -23,6 +23,10 @@ namespace hsc {
 namespace {
 
 constexpr int kThreads = 256;
+// Single-frame launch: one 4-pixel group per thread and 128-thread CTAs, so
+// the ~400 CTAs of a 416 x 512 frame spread within 10% of evenly over the
+// SMs (with 256-thread CTAs a third of the SMs took two CTAs, the rest one).
+constexpr int kFrameThreads = 128;
 
 template <int KC, typename CT>
 __device__ __forceinline__ void couple_solve(const float *r /* M, pair order */, float *p)
@@ -341,11 +345,11 @@ cudaError_t launch_kc(const float *cube, int B, long N, const float *v1f, const 
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     long groups = (N + PX - 1) / PX;
-    long blocks = (groups + kThreads - 1) / kThreads;
+    long blocks = (groups + kFrameThreads - 1) / kFrameThreads;
     long cap = max_blocks > 0 ? (long)max_blocks : (long)sm_count * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, kThreads, smem, st>>>(
+    kern<<<(unsigned)blocks, kFrameThreads, smem, st>>>(
         cube, B, N, v1f, muf, m ? m->w : nullptr, m ? m->b : nullptr, m ? m->platt_a : nullptr,
         m ? m->platt_b : nullptr, I_raw, probs, labels, f64 ? 1 : 0, ctl, P4);
     return cudaGetLastError();
