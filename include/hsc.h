@@ -47,7 +47,7 @@ typedef enum {
     HSC_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in last_error) */
     HSC_ERR_NOT_CONVERGED = 4, /* Jacobi / eigenvector refinement did not converge */
     HSC_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
-    HSC_ERR_UNSUPPORTED = 6,   /* valid request outside this build's limits */
+    HSC_ERR_UNSUPPORTED = 6,   /* valid request outside the library's limits */
     HSC_ERR_NONFINITE = 7      /* NaN or Inf met in an input map */
 } hsc_status;
 

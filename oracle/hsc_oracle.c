@@ -24,7 +24,7 @@
  *           (distance, linear index), the first K kept, their probabilities
  *           averaged, argmax label.
  *
- * Readings where the paper is silent or garbled (also listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - Eq. 1's third term is printed (r-j)^2; it is read as (c-j)^2.
  *   - lambda scales the spatial coordinates: d = dI^2 + lambda^2 (dr^2 + dc^2).
  *   - the window holds rows r-floor(R/2) .. r+ceil(R/2)-1, truncated at the
