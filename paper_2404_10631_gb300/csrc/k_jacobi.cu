@@ -1368,22 +1368,36 @@ size_t jacobi_global_floats(int B)
     return f;
 }
 
-cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec)
+namespace {
+// The launch parameters of one frame's eigensolver (single or batched: the
+// same numbers, so a batched frame gets the single call's results).
+JacParams jac_params(int B)
 {
     JacParams prm;
-    prm.n_vec = n_vec > 1 && s.vk && s.lamk && s.vkf ? n_vec : 1;
-    prm.vk = s.vk;
-    prm.lamk = s.lamk;
-    prm.vkf = s.vkf;
+    prm.n_vec = 1;
+    prm.vk = nullptr;
+    prm.lamk = nullptr;
+    prm.vkf = nullptr;
     prm.B = B;
     prm.n = B + (B & 1);
     if (prm.n < 2) prm.n = 2;
     prm.max_sweeps = 30;
     prm.rot_tol = 1e-7f;
     prm.stop_tol_final = 1e-2f;
+    prm.use_smem = jac_work_floats(prm.n) * sizeof(float) <= kJacSmemLimit;
+    return prm;
+}
+}  // namespace
+
+cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec)
+{
+    JacParams prm = jac_params(B);
+    prm.n_vec = n_vec > 1 && s.vk && s.lamk && s.vkf ? n_vec : 1;
+    prm.vk = s.vk;
+    prm.lamk = s.lamk;
+    prm.vkf = s.vkf;
     const size_t need = jac_work_floats(prm.n) * sizeof(float);
     const size_t need_packed = jac_packed_smem_floats(prm.n) * sizeof(float);
-    prm.use_smem = need <= kJacSmemLimit;
     const bool packed = !prm.use_smem && need_packed <= kJacSmemLimit;
     if (!prm.use_smem && !s.jac_A) return cudaErrorInvalidValue;
     if (packed) {
@@ -1406,19 +1420,8 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec
 // (B <= 128: the work area always fits in shared memory).
 cudaError_t launch_batch_jacobi(const BatchFrame *frames, int n_frames, int B, cudaStream_t st)
 {
-    JacParams prm;
-    prm.n_vec = 1;
-    prm.vk = nullptr;
-    prm.lamk = nullptr;
-    prm.vkf = nullptr;
-    prm.B = B;
-    prm.n = B + (B & 1);
-    if (prm.n < 2) prm.n = 2;
-    prm.max_sweeps = 30;
-    prm.rot_tol = 1e-7f;
-    prm.stop_tol_final = 1e-2f;
+    const JacParams prm = jac_params(B);
     const size_t need = jac_work_floats(prm.n) * sizeof(float);
-    prm.use_smem = need <= kJacSmemLimit;
     if (!prm.use_smem || n_frames < 1 || B > 128) return cudaErrorInvalidValue;
     if (need > 48 * 1024)
         cudaFuncSetAttribute(jacobi_kernel<false, true>,

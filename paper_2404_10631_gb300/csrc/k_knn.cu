@@ -569,31 +569,56 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     const float l2 = lam * lam;
     const long N = (long)H * W;
 
-    // stage the window rows x (kWalkThreads + 2 * 20) columns: asynchronous 4-byte
-    // copies, all in flight at once (out-of-image columns are zero-filled)
-    for (int ii = 0; ii < nrows; ++ii) {
-        const float *row = I + (long)(lo_r + ii) * W;
-        for (int jj = lane; jj < tw; jj += kWalkThreads) {
-            const int col = tcol0 + jj;
-            const bool in = col >= 0 && col < W;
-            const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ii * tw + jj);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst),
-                         "l"(in ? row + col : row), "r"(in ? 4 : 0)
+    // stage the window rows x (kWalkThreads + 2 * 20) columns, all copies in
+    // flight at once: 16-byte copies when the tile lies inside the image and
+    // its rows start on 16-byte boundaries, else 4-byte copies with the
+    // out-of-image columns zero-filled
+    constexpr int kV = (kWalkThreads + 2 * kTabDc) / 4;  // 16-byte units per tile row
+    static_assert((kWalkThreads + 2 * kTabDc) % 4 == 0 && kTabDc % 4 == 0, "tile rows of float4");
+    const bool vec = tcol0 >= 0 && tcol0 + tw <= W && (W & 3) == 0 &&
+                     (reinterpret_cast<uintptr_t>(I) & 15u) == 0;
+    if (vec) {
+        for (int idx = lane; idx < nrows * kV; idx += kWalkThreads) {
+            const int ii = idx / kV, v = idx - ii * kV;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ii * tw + 4 * v);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                         "l"(I + (long)(lo_r + ii) * W + tcol0 + 4 * v)
                          : "memory");
+        }
+    } else {
+        for (int ii = 0; ii < nrows; ++ii) {
+            const float *row = I + (long)(lo_r + ii) * W;
+            for (int jj = lane; jj < tw; jj += kWalkThreads) {
+                const int col = tcol0 + jj;
+                const bool in = col >= 0 && col < W;
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ii * tw + jj);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst),
+                             "l"(in ? row + col : row), "r"(in ? 4 : 0)
+                             : "memory");
+            }
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     bool bad = false;
     float vmin = INFINITY, vmax = -INFINITY;
-    for (int ii = 0; ii < nrows; ++ii) {
-        for (int jj = lane; jj < tw; jj += kWalkThreads) {
-            const int col = tcol0 + jj;
-            if (col < 0 || col >= W) continue;
-            const float v = tile[ii * tw + jj];
-            bad |= !isfinite(v);
-            vmin = fminf(vmin, v);
-            vmax = fmaxf(vmax, v);
+    if (vec) {
+        for (int idx = lane; idx < nrows * kV; idx += kWalkThreads) {
+            const float4 t4 = reinterpret_cast<const float4 *>(tile)[idx / kV * (tw / 4) + idx % kV];
+            bad |= !isfinite(t4.x) || !isfinite(t4.y) || !isfinite(t4.z) || !isfinite(t4.w);
+            vmin = fminf(vmin, fminf(fminf(t4.x, t4.y), fminf(t4.z, t4.w)));
+            vmax = fmaxf(vmax, fmaxf(fmaxf(t4.x, t4.y), fmaxf(t4.z, t4.w)));
+        }
+    } else {
+        for (int ii = 0; ii < nrows; ++ii) {
+            for (int jj = lane; jj < tw; jj += kWalkThreads) {
+                const int col = tcol0 + jj;
+                if (col < 0 || col >= W) continue;
+                const float v = tile[ii * tw + jj];
+                bad |= !isfinite(v);
+                vmin = fminf(vmin, v);
+                vmax = fmaxf(vmax, v);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
