@@ -63,6 +63,8 @@ struct hsc_ctx {
     cudaEvent_t sm_upload = nullptr;
     cudaGraphExec_t sm_exec = nullptr;
     std::vector<long long> sm_sig;
+    cudaStream_t sm_hi = nullptr;  // high-priority stream of the second frame group
+    cudaEvent_t sm_ev[3] = {};     // moments done, first group's Jacobi done, second group done
     // autotuned launch parameters and the frame shape (B, N, k) they were
     // chosen for; other shapes use the defaults
     bool tuned = false;
@@ -606,6 +608,12 @@ void hsc_ctx_destroy(hsc_ctx *ctx)
     if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
     if (ctx->batch_scratch) cudaFree(ctx->batch_scratch);
     if (ctx->sm_exec) cudaGraphExecDestroy(ctx->sm_exec);
+    if (ctx->sm_hi) {
+        cudaStreamSynchronize(ctx->sm_hi);
+        cudaStreamDestroy(ctx->sm_hi);
+    }
+    for (cudaEvent_t ev : ctx->sm_ev)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->sm_scratch) cudaFree(ctx->sm_scratch);
     if (ctx->sm_upload) cudaEventDestroy(ctx->sm_upload);
     if (ctx->sm_host) cudaFreeHost(ctx->sm_host);
@@ -1055,11 +1063,20 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     PixItem *hp = reinterpret_cast<PixItem *>(host + align_up(tab_frames) + tab_gram);
     int *hl = reinterpret_cast<int *>(host + align_up(tab_frames) + tab_gram + tab_pix);
     int *hc = reinterpret_cast<int *>(host + align_up(tab_frames) + tab_gram + tab_pix + tab_large);
+    // frame groups: the first sm frames (one wave of Jacobi CTAs) and the rest
+    const int F1 = n_frames > sm ? sm : n_frames;
+    int ip_split = 0, cta_split = 0;
+    long px_split = 0;
     int ig = 0, ip = 0, cta = 0, il = 0;
     for (int f = 0; f < n_frames; ++f) {
         const hsc_frame &fr = frames[f];
         const FrameLay &L = fl[(size_t)f];
         const long N = (long)fr.H * fr.W;
+        if (f == F1) {
+            ip_split = ip;
+            cta_split = cta;
+        }
+        if (f < F1) px_split += N;
         BatchFrame b{};
         b.cube = fr.cube;
         b.I = fr.one_band ? fr.one_band : reinterpret_cast<float *>(dev + L.I);
@@ -1174,28 +1191,67 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     }
     cudaStream_t st = ctx->stream;
     hsc_ctx *tc = graph ? &g_untimed : ctx;  // stage events only outside a capture
+    int2 *redo_list = reinterpret_cast<int2 *>(dev + redo);
+    const bool f64 = (flags & HSC_SVM_COUPLE_F64) != 0;
+    // the stages after the moments for frames [f0, f1) of the table: the
+    // eigensolvers, then projection/SVM, normalisation and KNN over the
+    // group's work items, CTAs and redo-list share
+    auto tail = [&](int f0, int f1, int ip0, int ip1, int cta0, int cta1, long px0, long px1,
+                    cudaStream_t s, bool with_jacobi) -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        if (with_jacobi) {
+            StageTimer t(tc, HSC_STAGE_JACOBI, 1, s);
+            r = hsc::launch_batch_jacobi(df + f0, f1 - f0, B, s);
+        }
+        if (r == cudaSuccess) {
+            StageTimer t(tc, HSC_STAGE_PROJECT_SVM, 1, s);
+            r = hsc::launch_batch_project_svm(df, dp + ip0, ip1 - ip0, B, model, f64, s);
+        }
+        if (r == cudaSuccess && !(flags & HSC_CLASSIFY_RAW_I)) {
+            StageTimer t(tc, HSC_STAGE_NORMALIZE, 1, s);
+            r = hsc::launch_batch_normalize(df, dp + ip0, ip1 - ip0, s);
+        }
+        if (r == cudaSuccess) {
+            StageTimer t(tc, HSC_STAGE_KNN, 2, s);
+            r = hsc::launch_batch_knn(df + f0, f1 - f0, cta1 - cta0, cta0, k, params->k, R,
+                                      params->lambda, max_rows, redo_list + px0,
+                                      (unsigned)(px1 - px0), s);
+        }
+        return r;
+    };
     {
         StageTimer t(tc, HSC_STAGE_MOMENTS, 3, st);
         e = hsc::launch_batch_moments(df, n_frames, dg, dc, n_gram, dl, n_large, B, sm, st);
     }
-    if (e == cudaSuccess) {
-        StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);
-        e = hsc::launch_batch_jacobi(df, n_frames, B, st);
-    }
-    if (e == cudaSuccess) {
-        StageTimer t(tc, HSC_STAGE_PROJECT_SVM, 1, st);
-        e = hsc::launch_batch_project_svm(df, dp, n_pix, B, model,
-                                          (flags & HSC_SVM_COUPLE_F64) != 0, st);
-    }
-    if (e == cudaSuccess && !(flags & HSC_CLASSIFY_RAW_I)) {
-        StageTimer t(tc, HSC_STAGE_NORMALIZE, 1, st);
-        e = hsc::launch_batch_normalize(df, dp, n_pix, st);
-    }
-    if (e == cudaSuccess) {
-        StageTimer t(tc, HSC_STAGE_KNN, 2, st);
-        e = hsc::launch_batch_knn(df, n_frames, n_ctas, k, params->k, R, params->lambda,
-                                  max_rows, reinterpret_cast<int2 *>(dev + redo),
-                                  (unsigned)n_px, st);
+    if (e == cudaSuccess && F1 == n_frames) {
+        e = tail(0, n_frames, 0, n_pix, 0, n_ctas, 0, n_px, st, true);
+    } else if (e == cudaSuccess) {
+        // more frames than SMs: the eigensolvers take two waves. The second
+        // group's chain runs on a high-priority stream (its Jacobi CTAs take
+        // the SMs the first wave frees, right after it), while the first
+        // group's projection, SVM and KNN fill the remaining SMs.
+        if (!ctx->sm_hi) {
+            int least = 0, greatest = 0;
+            e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            if (e == cudaSuccess)
+                e = cudaStreamCreateWithPriority(&ctx->sm_hi, cudaStreamNonBlocking, greatest);
+            for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+                e = cudaEventCreateWithFlags(&ctx->sm_ev[i], cudaEventDisableTiming);
+        }
+        cudaStream_t hi = ctx->sm_hi;
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_ev[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hi, ctx->sm_ev[0], 0);
+        if (e == cudaSuccess) {
+            StageTimer t(tc, HSC_STAGE_JACOBI, 1, hi);
+            e = hsc::launch_batch_jacobi(df, F1, B, hi);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_ev[1], hi);
+        if (e == cudaSuccess)
+            e = tail(F1, n_frames, ip_split, n_pix, cta_split, n_ctas, px_split, n_px, hi, true);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_ev[2], hi);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->sm_ev[1], 0);
+        if (e == cudaSuccess) e = tail(0, F1, 0, ip_split, 0, cta_split, 0, px_split, st, false);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->sm_ev[2], 0);
     }
     if (graph) {
         cudaGraph_t g = nullptr;

@@ -165,8 +165,8 @@ cudaError_t launch_batch_project_svm(const BatchFrame *frames, const PixItem *it
                                      cudaStream_t st);
 cudaError_t launch_batch_normalize(const BatchFrame *frames, const PixItem *items, int n_items,
                                    cudaStream_t st);
-cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas, int k, int K,
-                             int R, float lambda, int max_rows, int2 *redo_list,
+cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas, int cta_base,
+                             int k, int K, int R, float lambda, int max_rows, int2 *redo_list,
                              unsigned redo_cap, cudaStream_t st);
 
 // Jacobi eigen-decomposition of C, FP64 refinement of the leading vector,

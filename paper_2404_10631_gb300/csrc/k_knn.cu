@@ -525,17 +525,18 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                   int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
                   bool redo_all, Control *ctl, const BatchFrame *__restrict__ frames,
                   int n_frames, int2 *__restrict__ redo_list, unsigned redo_cap,
-                  const float4 *__restrict__ P4)
+                  const float4 *__restrict__ P4, int cta_base = 0)
 {
     extern __shared__ float sm[];
     __shared__ float s_min[kWalkThreads / 32], s_max[kWalkThreads / 32];
     int r = blockIdx.y, bx = blockIdx.x;
     int frame = 0;
-    if (kBatch) {  // a stage-major batch: the frame whose CTA range holds blockIdx.x
+    if (kBatch) {  // a stage-major batch: the frame whose CTA range holds this CTA
+        const int cta = (int)blockIdx.x + cta_base;
         int lo = 0, hi = n_frames - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (frames[mid].knn_cta0 <= (int)blockIdx.x) lo = mid;
+            if (frames[mid].knn_cta0 <= cta) lo = mid;
             else hi = mid - 1;
         }
         frame = lo;
@@ -548,7 +549,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         O = fr.O;
         labels = fr.labels;
         ctl = fr.ctl;
-        const int t = (int)blockIdx.x - fr.knn_cta0;
+        const int t = cta - fr.knn_cta0;
         const int tpr = (W + kWalkThreads - 1) / kWalkThreads;
         r = t / tpr;
         bx = t - r * tpr;
@@ -1004,9 +1005,9 @@ cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, i
 }
 
 template <int KC>
-cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ctas, int K, int R,
-                                float lam, int max_rows, int2 *redo_list, unsigned redo_cap,
-                                cudaStream_t st)
+cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ctas, int cta_base,
+                                int K, int R, float lam, int max_rows, int2 *redo_list,
+                                unsigned redo_cap, cudaStream_t st)
 {
     const size_t smem = pruned_smem_bytes(R, max_rows);
     if (smem > 48 * 1024)
@@ -1014,7 +1015,7 @@ cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ct
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     knn_pruned_kernel<KC, true, true><<<n_ctas, kWalkThreads, smem, st>>>(
         nullptr, nullptr, 0, 0, K, R, lam, nullptr, nullptr, false, nullptr, frames, n_frames,
-        redo_list, redo_cap, nullptr);
+        redo_list, redo_cap, nullptr, cta_base);
     const size_t rsmem = redo_smem_bytes(K);
     if (rsmem > 48 * 1024)
         cudaFuncSetAttribute(knn_redo_batch_kernel<KC>,
@@ -1078,22 +1079,22 @@ cudaError_t knn_init(int device)
     return e;
 }
 
-// Stage-major batch, pruned search (lambda > 0): n_ctas = sum over frames of
-// H * ceil(W / 32), frame f's CTAs from frames[f].knn_cta0; max_rows = the
-// largest min(R, H).
-cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas, int k, int K,
-                             int R, float lambda, int max_rows, int2 *redo_list,
+// Stage-major batch, pruned search (lambda > 0): n_ctas = sum over the
+// frames of H * ceil(W / 32), frame f's CTAs from frames[f].knn_cta0, the
+// first of them numbered cta_base; max_rows = the largest min(R, H).
+cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas, int cta_base,
+                             int k, int K, int R, float lambda, int max_rows, int2 *redo_list,
                              unsigned redo_cap, cudaStream_t st)
 {
     if (n_frames < 1 || n_ctas < 1 || !(lambda > 0.f) || !redo_list) return cudaErrorInvalidValue;
     switch (k) {
-    case 2: return launch_batch_pruned<2>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
-    case 3: return launch_batch_pruned<3>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
-    case 4: return launch_batch_pruned<4>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
-    case 5: return launch_batch_pruned<5>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
-    case 6: return launch_batch_pruned<6>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
-    case 7: return launch_batch_pruned<7>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
-    case 8: return launch_batch_pruned<8>(frames, n_frames, n_ctas, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 2: return launch_batch_pruned<2>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 3: return launch_batch_pruned<3>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 4: return launch_batch_pruned<4>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 5: return launch_batch_pruned<5>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 6: return launch_batch_pruned<6>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 7: return launch_batch_pruned<7>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
+    case 8: return launch_batch_pruned<8>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
     default: return cudaErrorInvalidValue;
     }
 }

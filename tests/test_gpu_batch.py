@@ -118,14 +118,15 @@ def test_batch_rejects_bad_frame(hsc, ctx):
         hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam)
 
 
-def _alone_vs_batch(hsc, ctx, frames, cubes, flags=0):
+def _alone_vs_batch(hsc, ctx, frames, cubes, flags=0, batch_flags=0):
     import torch
     f0 = frames[0]
     k = f0.model.n_classes
     model = hsc.Model.from_host(f0.model)
     labs, O, I, P = outputs(frames, k)
-    hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, flags=flags,
-                           labels=labs, out_probs=O, one_bands=I, probs=P)
+    hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
+                           flags=flags | batch_flags, labels=labs, out_probs=O, one_bands=I,
+                           probs=P)
     ctx.sync()
     for i, f in enumerate(frames):
         lab = torch.empty(f.cube.shape[1:], dtype=torch.int32, device="cuda")
@@ -181,3 +182,18 @@ def test_staged_batch_flags(hsc, ctx, flags):
     frames = synth.make_batch(6, seed=778)
     fl = hsc.HSC_CLASSIFY_RAW_I if flags == "raw" else hsc.HSC_SVM_COUPLE_F64
     _alone_vs_batch(hsc, ctx, frames, frames_to_device(frames), flags=fl)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_staged_batch_more_frames_than_sms(hsc, ctx, graph):
+    """More frames than SMs: the first wave's frames and the rest run their
+    eigensolver-to-KNN chains on two streams (the second on a high-priority
+    one); every frame still equals its single-frame call."""
+    import torch
+    frames = synth.make_batch(170, seed=780)
+    assert len(frames) > torch.cuda.get_device_properties(0).multi_processor_count
+    cubes = frames_to_device(frames)
+    bflags = hsc.HSC_BATCH_GRAPH if graph else 0
+    _alone_vs_batch(hsc, ctx, frames, cubes, batch_flags=bflags)
+    if graph:  # the replay
+        _alone_vs_batch(hsc, ctx, frames, cubes, batch_flags=bflags)
