@@ -478,9 +478,21 @@ def run_ours(args, f):
     # per context: its device cube and its own model copy (the copies of one
     # step and the kernels of another never share a buffer)
     e2e_models = [hsc.Model.from_host(f.model, device=dev) for _ in range(F)]
+    e2e_cubes = [torch.empty((B, H, W), dtype=torch.float32, device=dev) for _ in range(F)]
     h2d = host_cube.numel() * 4 + sum(a.numel() * 4 for a in host_model)
     d2h = host_labs[0].numel() * 4
-    n_e2e = max(F, min(args.steps, 20))
+    # the host link's own rate for this copy (pinned cube -> device, CUDA
+    # events), the ceiling of the end-to-end number
+    for r in range(8):
+        if r == 3:
+            l0 = torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+        e2e_cubes[0].copy_(host_cube, non_blocking=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    l1.record(stream)
+    l1.synchronize()
+    link_gbs = host_cube.numel() * 4 * 5 / (l0.elapsed_time(l1) / 1e3) / 1e9
+    n_e2e = max(F, args.steps)
     done = [None] * F
     if world > 1:
         dist.barrier()
@@ -491,7 +503,7 @@ def run_ours(args, f):
         if done[j] is not None:
             done[j].synchronize()  # context j's last frame is out: its host labels are read
         with torch.cuda.stream(streams[j]):
-            dcube, mj = cubes[j % N_ROTATING], e2e_models[j]
+            dcube, mj = e2e_cubes[j], e2e_models[j]
             dcube.copy_(host_cube, non_blocking=True)
             for d, h in zip((mj.w, mj.b, mj.platt_a, mj.platt_b), host_model):
                 d.copy_(h, non_blocking=True)
@@ -602,7 +614,13 @@ def run_ours(args, f):
             "batch": batch,
             "serving": serving,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": n_e2e},
+                    "d2h_bytes_per_step": d2h, "steps": n_e2e,
+                    "h2d_link_gbs": link_gbs,
+                    "link_bound": world * link_gbs * 1e9 / h2d * N,
+                    "frac_of_link_bound": e2e_value / (world * link_gbs * 1e9 / h2d * N),
+                    "note": "each frame's cube crosses the host link once (pinned host -> device); "
+                            "h2d_link_gbs is that copy alone, timed in this run (rank 0), and "
+                            "link_bound the pixels/s it allows on every rank's own link"},
             "gpu_launches": int(sum(stage_kernels.values())),
             "autotune": tune,
             "fp_peaks": {"fp32_lane_ops_per_s": fp32_rate * 1e12, "fp64_lane_ops_per_s": fp64_rate * 1e12,
