@@ -537,6 +537,8 @@ def run_ours(args, f):
     work = stage_work(f, knn_evals_per_launch, refine_iters)
     stages = {}
     for name, ms in stage_ms.items():
+        if stage_kernels[name] == 0:  # the min-max normalisation runs inside the pruned KNN
+            continue
         launches = max(1, args.steps)
         avg_ms = ms / launches
         bound, units = work[name]
