@@ -23,6 +23,8 @@
 // conservative FP32 bound; every candidate that might pass is re-checked on
 // the exact key.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <math.h>
 
 #include <algorithm>
@@ -972,6 +974,29 @@ size_t pruned_smem_bytes(int R, int H)
 
 size_t redo_smem_bytes(int K) { return sizeof(float) * 3 * (size_t)(K + kRedoExtra) * kRedoThreads; }
 
+// CTAs of the redo pass that the current device holds at once: SMs x the
+// CTAs per SM its shared memory allows (each CTA also holds 1 KB the
+// hardware reserves), at least 64; looked up once per device.
+long redo_resident_ctas(size_t smem)
+{
+    static std::atomic<int> sm_of[64], smem_of[64];  // zero-initialised (static storage)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 64;
+    if (!sm_of[dev].load()) {
+        int sm = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess)
+            return 64;
+        smem_of[dev].store(per_sm);
+        sm_of[dev].store(sm);
+    }
+    long per = (long)smem_of[dev].load() / (long)(smem + 1024);
+    if (per > 32) per = 32;
+    const long n = (long)sm_of[dev].load() * (per > 1 ? per : 1);
+    return n > 64 ? n : 64;
+}
+
 template <int KC>
 cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, int R, float lam,
                           float *O, int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st,
@@ -998,8 +1023,12 @@ cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, i
     if (rsmem > 48 * 1024)
         cudaFuncSetAttribute(knn_redo_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)rsmem);
-    const long rgrid = (N + kRedoThreads - 1) / kRedoThreads;  // persistent: at most 64 CTAs
-    knn_redo_kernel<KC><<<(unsigned)(rgrid < 64 ? rgrid : 64), kRedoThreads, rsmem, st>>>(
+    // persistent over the whole GPU (the CTAs its shared memory lets every SM
+    // hold), so that a map on which many pixels overflow their buffers is
+    // completed in parallel; with nothing flagged every CTA exits at once
+    const long rgrid = (N + kRedoThreads - 1) / kRedoThreads;
+    const long rcap = (long)redo_resident_ctas(rsmem);
+    knn_redo_kernel<KC><<<(unsigned)(rgrid < rcap ? rgrid : rcap), kRedoThreads, rsmem, st>>>(
         I, P, H, W, K, R, lam, O, labels, nbr, ctl, P4);
     return cudaGetLastError();
 }
