@@ -311,8 +311,9 @@ def run_reference(args, f):
     """The oracle arm: the FP64 oracle as it stands, on every host core (one
     spawned process per core on its own rows; each step one round of that,
     scaled to the frame; the per-frame Jacobi timed whole)."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    from paper_2404_10631_gb300 import replicas
+    _, rank, _ = replicas.env_ranks()
+    if not replicas.reports(rank):  # under torchrun rank 0 alone times the oracle
         return
     B, H, W = f.cube.shape
     N = H * W
@@ -336,21 +337,17 @@ def run_reference(args, f):
 # -------------------------------------------------------------------- ours --
 def run_ours(args, f):
     import torch
-    import torch.distributed as dist
 
     import paper_2404_10631_gb300 as hsc
+    from paper_2404_10631_gb300 import replicas
     from paper_2404_10631_gb300 import build as hbuild
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replicas.env_ranks()
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    replicas.init(world, local, "nccl")
     if rank == 0:
         hbuild.build()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
 
     dev = torch.device("cuda", local)
     B, H, W = f.cube.shape
@@ -399,8 +396,7 @@ def run_ours(args, f):
             step(i, nf)
         for c in ctxs[:nf]:
             c.sync()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier(world)
         torch.cuda.synchronize(dev)
         if clocks:
             clocks.start()
@@ -420,8 +416,7 @@ def run_ours(args, f):
             tstream.wait_event(ev_s)
         e1.record(tstream)
         torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
+        replicas.barrier(world)
         clk = clocks.stop() if clocks else None
         return e0.elapsed_time(e1), [st[i].elapsed_time(en[i]) for i in range(args.steps)], clk
 
@@ -462,12 +457,9 @@ def run_ours(args, f):
     ctx.profile(False)
     full_ms_launch = full_ms["knn"] / args.steps
     heap_ms_launch = heap_ms["knn"] / n_heap
-    t = torch.tensor([elapsed, elapsed1], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_max, elapsed1_max = float(t[0].item()), float(t[1].item())
-    value = world * N * args.steps / (elapsed_max / 1e3)
-    value1 = world * N * args.steps / (elapsed1_max / 1e3)
+    elapsed_max, elapsed1_max = replicas.max_over_ranks([elapsed, elapsed1], world, dev)
+    value = replicas.whole_job_rate(N * args.steps, world, elapsed_max / 1e3)
+    value1 = replicas.whole_job_rate(N * args.steps, world, elapsed1_max / 1e3)
 
     # ---- end to end through the public API with host buffers
     host_cube = torch.empty((B, H, W), dtype=torch.float32).pin_memory()
@@ -494,8 +486,7 @@ def run_ours(args, f):
     link_gbs = host_cube.numel() * 4 * 5 / (l0.elapsed_time(l1) / 1e3) / 1e9
     n_e2e = max(F, args.steps)
     done = [None] * F
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for i in range(n_e2e):
@@ -514,10 +505,8 @@ def run_ours(args, f):
     for s in streams:
         s.synchronize()
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * N * n_e2e / float(t.item())
+    e2e_value = replicas.whole_job_rate(N * n_e2e, world,
+                                        replicas.max_over_ranks([e2e_s], world, dev)[0])
     ctx.sync()
 
     # ---- batched uneven frames vs the plain per-frame path (same GPU)
@@ -640,13 +629,12 @@ def run_ours(args, f):
                                 "kind": "oracle", "sample": desc_par,
                                 "single_core": {"value": N / t_frame, "unit": UNIT, "cores": 1,
                                                 "sample": desc}}
-    if rank == 0:
+    if replicas.reports(rank):
         print(json.dumps(line), flush=True)
     for c in ctxs[1:]:
         c.close()
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finalize(world)
 
 
 def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
