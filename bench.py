@@ -516,6 +516,9 @@ def run_ours(args, f):
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(hsc, ctx, stream, dev, args)
+    mixed = None
+    if not args.no_mixed and world == 1:
+        mixed = run_mixed(hsc, ctx, stream, dev, args)
 
     # ---- roofline of the dominant stage
     peaks, peak_src = load_peaks()
@@ -604,6 +607,7 @@ def run_ours(args, f):
             "knn_heap": knn_heap,
             "batch": batch,
             "serving": serving,
+            "mixed_precision": mixed,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": n_e2e,
                     "h2d_link_gbs": link_gbs,
@@ -635,6 +639,67 @@ def run_ours(args, f):
         c.close()
     ctx.close()
     replicas.finalize(world)
+
+
+def run_mixed(hsc, ctx, stream, dev, args, reps=5):
+    """The 1024 x 1024 x 256-band frame (two wide Gaussians per class
+    spectrum, sigma 0.01; 1 GiB float32): the covariance on the tensor cores
+    as FP16 hi/lo parts with FP32 accumulation, the eigenvector refined in
+    double-float, the rest FP32. hsc_classify one frame at a time on one
+    context (the cube is 8x L2), with per-stage device times and the HBM
+    fraction of the two passes over the cube."""
+    import torch
+    f = synth.make_config(4)
+    B, H, W = f.cube.shape
+    N = H * W
+    k = f.model.n_classes
+    cube = torch.as_tensor(f.cube, device=dev)
+    model = hsc.Model.from_host(f.model, device=dev)
+    lab = torch.empty((H, W), dtype=torch.int32, device=dev)
+    ctx.reserve(B, H, W, k)
+
+    def one():
+        hsc.hsc_classify(ctx, cube, model, f.K, f.window_rows, f.lam, labels=lab)
+
+    for _ in range(3):
+        one()
+    ctx.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(stream)
+    for i in range(reps):
+        one()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.sync()
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(reps))
+    ms = ev[0].elapsed_time(ev[reps]) / reps
+    ctx.profile(True)
+    ctx.profile_read()
+    for _ in range(reps):
+        one()
+    ctx.sync()
+    st_ms, _, _ = ctx.profile_read()
+    ctx.profile(False)
+    stages = {n: round(v / reps, 4) for n, v in st_ms.items() if v > 0}
+    peaks, _ = load_peaks()
+    cube_bytes = 4.0 * B * N
+
+    def hbm_frac(stage, nbytes):
+        t = stages.get(stage)
+        return None if not t else nbytes / (t / 1e3) / 1e9 / peaks["hbm_gbs"]
+
+    del cube
+    torch.cuda.empty_cache()
+    return {"workload": "mixed-precision frame 1024x1024x256 float32 (1 GiB), 4 classes, K=40, "
+                        "14-row window, lambda=1: FP16 hi/lo tensor-core covariance with FP32 "
+                        "accumulation, double-float eigen-refinement, FP32 SVM and KNN",
+            "value": N / (ms / 1e3), "unit": UNIT, "ms_per_frame": ms,
+            "p50_ms": per[len(per) // 2], "p99_ms": per[-1], "frames": reps,
+            "stages_ms": stages,
+            "hbm_frac": {"moments": hbm_frac("moments", cube_bytes),
+                         "project_svm": hbm_frac("project_svm",
+                                                 cube_bytes + 4.0 * N + 4.0 * k * N)},
+            "errors": "per-stage errors against the FP64 oracle: tests/test_gpu_mixed.py"}
 
 
 def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
@@ -814,6 +879,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the 1024x1024x256 mixed-precision frame")
     ap.add_argument("--frames-in-flight", type=int, default=8,
                     help="contexts (streams) the steps rotate over; 1 = one frame at a time")
     args = ap.parse_args()
