@@ -361,9 +361,26 @@ hsc_status hsc_set_tuning(hsc_ctx *ctx, int B, int H, int W, int n_classes,
  * rooflines. Runs two short kernels on a private stream (tens of ms) and
  * synchronises it. HSC_ERR_CUDA if a launch fails. */
 hsc_status hsc_measure_fma_rate(int device, int fp64, double *lane_ops_per_s);
-/* Diagnostics of the pruned KNN search (waits for the stream): candidates
- * whose distance it computed since the previous call (then reset to 0). */
-hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated);
+/* Diagnostics of the pruned KNN search (waits for the stream), both counted
+ * since the previous call and then reset to 0:
+ *   candidates_evaluated  candidates whose distance it computed (required)
+ *   redo_pixels           pixels its walk could not finish and handed to the
+ *                         redo pass (nullable): the disk of a pixel left the
+ *                         staged tile, its undecided-key buffer overflowed,
+ *                         the offset table held fewer than K valid offsets,
+ *                         or nbr_idx was requested (then every pixel) */
+hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated,
+                               int64_t *redo_pixels);
+/* Testing aid for the device-side timeout path (no counterpart in the
+ * paper). The context's next moments stage (hsc_pca_one_band,
+ * hsc_pca_covariance, hsc_classify) that runs the tensor-core Gram through a
+ * tensor map (B <= 256, H*W a multiple of 4, a 16-byte-aligned cube) issues
+ * none of its loads, so the first bounded wait of each CTA runs out after a
+ * short bound with no copy or MMA in flight; the kernel then takes the path a
+ * real timeout takes (flags the status, frees its tensor memory, returns).
+ * The following hsc_sync returns HSC_ERR_TIMEOUT; that call's outputs are
+ * unspecified; the context stays usable. Applies to one call, then clears. */
+hsc_status hsc_test_stall_next_gram(hsc_ctx *ctx);
 /* ms[HSC_N_STAGES]: summed milliseconds; kernels[HSC_N_STAGES]: kernel
  * launches per stage; dropped (nullable): records lost to the cap. */
 hsc_status hsc_profile_read(hsc_ctx *ctx, double *ms, int64_t *kernels, int64_t *dropped);
@@ -374,21 +391,25 @@ hsc_status hsc_profile_read(hsc_ctx *ctx, double *ms, int64_t *kernels, int64_t 
  * device memory, a real-time loop where cudaMalloc could stall on the device,
  * a plugin that does not own the allocator. Same computation and outputs as
  * hsc_pca_one_band, but no context: the scratch lives in one fixed
- * __device__ array inside libhsc.so (about 4.3 MB, held on every GPU that
- * loads the library until the process exits), sized for at most
- * HSC_NOALLOC_MAX_BANDS bands (any H, W with H*W < 2^31).
+ * __device__ array inside libhsc.so (4,493,824 bytes = 4.49 MB or 4.29 MiB,
+ * held on every GPU that loads the library until the process exits), sized
+ * for at most HSC_NOALLOC_MAX_BANDS bands (any H, W with H*W < 2^31).
  *   cuda_stream  cudaStream_t to launch on (NULL = the legacy default stream)
  *   other arguments as hsc_pca_one_band (device pointers, caller-owned).
  * Returns HSC_ERR_UNSUPPORTED when B > HSC_NOALLOC_MAX_BANDS, HSC_ERR_INVALID_ARG
- * for bad arguments, HSC_ERR_CUDA when a launch fails. Calls no cudaMalloc,
- * cudaFree or allocating library routine. The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture. Every call
+ * for bad arguments, HSC_ERR_CUDA when a launch fails; all of these before
+ * anything is enqueued except a failed launch. Calls no cudaMalloc, cudaFree
+ * or allocating library routine. Every call looks up the array's device
+ * address in the current context (cudaGetSymbolAddress): the first call on a
+ * device (and the first after a cudaDeviceReset) loads the library's device
+ * code there, so make that first call before any stream capture. Every call
  * shares the one array and each call clears the part that must start at
  * zero, so calls whose GPU work overlaps (two streams, two host threads)
  * race and give undefined results; order them on one stream. Device-side
- * conditions (NaN input, eigenvector not converged) are not reported by this
- * entry point: the outputs are then unspecified. */
+ * conditions are not reported by this entry point (it has no status word the
+ * caller can read): NaN or Inf input, an eigenvector that did not converge,
+ * or a bounded wait inside the tensor-core Gram that ran out (which leaves
+ * partial covariance sums) all return HSC_OK with unspecified outputs. */
 #define HSC_NOALLOC_MAX_BANDS 128
 hsc_status hsc_pca_one_band_noalloc(void *cuda_stream, const float *cube, int B, int H, int W,
                                     unsigned flags, float *one_band, double *eigvec,

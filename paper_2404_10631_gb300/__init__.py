@@ -42,7 +42,8 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_autotune", "hsc_set_tuning", "hsc_pca_project",
             "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics",
             "hsc_classify_batch", "hsc_server_create", "hsc_server_submit",
-            "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy")
+            "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy",
+            "hsc_test_stall_next_gram")
 HSC_BATCH_GRAPH = 8
 HSC_BATCH_POOL = 64
 HSC_COV_FP32_PIPE = 4
@@ -141,7 +142,9 @@ def lib():
         L.hsc_server_stats_get.argtypes = [vp, ctypes.POINTER(hsc_server_stats)]
         L.hsc_server_destroy.argtypes = [vp]
         L.hsc_server_destroy.restype = None
-        L.hsc_knn_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.hsc_test_stall_next_gram.argtypes = [vp]
+        L.hsc_knn_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64)]
         L.hsc_pca_covariance.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp]
         L.hsc_pca_one_band_noalloc.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_profile_enable.argtypes = [vp, i32]
@@ -274,11 +277,22 @@ class Context:
             return int(a.value), int(b.value), int(c.value), int(d.value)
         return int(a.value), int(b.value)
 
+    def test_stall_next_gram(self):
+        """Testing aid: the next tensor-core Gram of this context runs out its
+        first bounded wait (see hsc_test_stall_next_gram)."""
+        self.check(lib().hsc_test_stall_next_gram(self.handle))
+
     def knn_candidates_evaluated(self) -> int:
-        """Candidates the pruned KNN search evaluated since the last call."""
-        v = ctypes.c_int64(0)
-        self.check(lib().hsc_knn_diagnostics(self.handle, ctypes.byref(v)))
-        return int(v.value)
+        """Candidates the pruned KNN search evaluated since the last call
+        (resets the counters of knn_diagnostics too)."""
+        return self.knn_diagnostics()[0]
+
+    def knn_diagnostics(self):
+        """(candidates evaluated, pixels handed to the redo pass) of the pruned
+        KNN search since the last call; both counters are then reset."""
+        v, r = ctypes.c_int64(0), ctypes.c_int64(0)
+        self.check(lib().hsc_knn_diagnostics(self.handle, ctypes.byref(v), ctypes.byref(r)))
+        return int(v.value), int(r.value)
 
     def autotune(self, cube, model) -> dict:
         """Times the launch-shape candidates on this cube (B x H x W) and keeps

@@ -67,6 +67,9 @@ struct hsc_ctx {
     cudaEvent_t sm_ev[3] = {};     // moments done, first group's Jacobi done, second group done
     // autotuned launch parameters and the frame shape (B, N, k) they were
     // chosen for; other shapes use the defaults
+    // testing aid: the next moments stage runs the tensor-core Gram with
+    // Control::test_stall set (hsc_test_stall_next_gram)
+    bool test_stall = false;
     bool tuned = false;
     int tune_B = 0, tune_k = 0;
     long tune_N = 0;
@@ -129,6 +132,26 @@ hsc_status cuda_fail(hsc_ctx *ctx, cudaError_t e, const char *where)
 }
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The moments stage with the context's test stall applied (once): the flag
+// in the frame's control block is set before the launches and cleared after
+// them, both in stream order, so only this stage's Gram kernel sees it.
+cudaError_t moments_with_stall(hsc_ctx *ctx, const float *cube, int B, long N,
+                               const PcaScratch &s, cudaStream_t st, bool force_simt,
+                               int gram_stages)
+{
+    const bool stall = ctx->test_stall;
+    ctx->test_stall = false;
+    cudaError_t e = cudaSuccess;
+    if (stall) e = cudaMemsetAsync(&s.ctl->test_stall, 0xff, sizeof(unsigned), st);
+    if (e == cudaSuccess)
+        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, st, force_simt, gram_stages);
+    if (stall) {
+        const cudaError_t e2 = cudaMemsetAsync(&s.ctl->test_stall, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e;
+}
 
 struct Layout {
     size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, bsq, vk, lamk,
@@ -325,7 +348,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
     cudaError_t e;
     {
         StageTimer t(tc, HSC_STAGE_MOMENTS, hsc::moments_kernel_count(cube, B, N), st);
-        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, st, false, tu.gram_stages);
+        e = moments_with_stall(ctx, cube, B, N, s, st, false, tu.gram_stages);
     }
     if (e == cudaSuccess) {
         StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);
@@ -547,21 +570,34 @@ hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_it
     return HSC_OK;
 }
 
-hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated)
+hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated,
+                               int64_t *redo_pixels)
 {
     hsc_status st = check_ctx(ctx);
     if (st) return st;
     if (!candidates_evaluated) return fail(ctx, HSC_ERR_INVALID_ARG, "output pointer is NULL%s");
     *candidates_evaluated = 0;
+    if (redo_pixels) *redo_pixels = 0;
     if (!ctx->scratch) return HSC_OK;
     Control c;
-    unsigned long long *dev = &reinterpret_cast<Control *>(ctx->scratch)->knn_evals;
+    Control *dev = reinterpret_cast<Control *>(ctx->scratch);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpy(&c, ctx->scratch, sizeof c, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dev, 0, sizeof(*dev), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&dev->knn_evals, 0, sizeof(dev->knn_evals), ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(&dev->knn_redo_total, 0, sizeof(dev->knn_redo_total), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "hsc_knn_diagnostics");
     *candidates_evaluated = (int64_t)c.knn_evals;
+    if (redo_pixels) *redo_pixels = (int64_t)c.knn_redo_total;
+    return HSC_OK;
+}
+
+hsc_status hsc_test_stall_next_gram(hsc_ctx *ctx)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    ctx->test_stall = true;
     return HSC_OK;
 }
 
@@ -682,13 +718,15 @@ hsc_status hsc_sync(hsc_ctx *ctx)
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "batch status readback");
     }
+    // a wait that ran out leaves partial sums behind it, so whatever the later
+    // stages flagged follows from it: it is reported first
+    if (bits & hsc::ST_TIMEOUT)
+        return fail(ctx, HSC_ERR_TIMEOUT, "a bounded wait inside a kernel ran out%s");
     if (bits & (hsc::ST_NONFINITE_CUBE | hsc::ST_NONFINITE_MAP))
         return fail(ctx, HSC_ERR_NONFINITE, "a NaN or Inf was found in an input map%s");
     if (bits & hsc::ST_NOT_CONVERGED)
         return fail(ctx, HSC_ERR_NOT_CONVERGED,
                     "the leading eigenvector did not converge (degenerate or tiny eigengap)%s");
-    if (bits & hsc::ST_TIMEOUT)
-        return fail(ctx, HSC_ERR_TIMEOUT, "a bounded wait inside a kernel ran out%s");
     if (bits & hsc::ST_KNN_SHORT)
         return fail(ctx, HSC_ERR_INVALID_ARG, "KNN: a pixel found fewer than K candidates%s");
     return HSC_OK;
@@ -728,7 +766,7 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     if (e == cudaSuccess) {  // the tuned Gram staging depth for frames of this size
         const int stg = (ctx->tuned && ctx->tune_B == B && ctx->tune_N == N) ? ctx->tune.gram_stages : 0;
         StageTimer t(ctx, HSC_STAGE_MOMENTS, hsc::moments_kernel_count(cube, B, N));
-        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream, false, stg);
+        e = moments_with_stall(ctx, cube, B, N, s, ctx->stream, false, stg);
     }
     if (e == cudaSuccess) {
         StageTimer t(ctx, HSC_STAGE_JACOBI, 1);
@@ -819,8 +857,8 @@ hsc_status hsc_pca_covariance(hsc_ctx *ctx, const float *cube, int B, int H, int
     {
         StageTimer t(ctx, HSC_STAGE_MOMENTS,
                      hsc::moments_kernel_count(cube, B, N, (flags & HSC_COV_FP32_PIPE) != 0));
-        e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream,
-                                (flags & HSC_COV_FP32_PIPE) != 0);
+        e = moments_with_stall(ctx, cube, B, N, s, ctx->stream, (flags & HSC_COV_FP32_PIPE) != 0,
+                               0);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(mean, s.mu, sizeof(double) * B, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -1176,7 +1214,8 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         int lam_bits;
         memcpy(&lam_bits, &params->lambda, sizeof lam_bits);
         sig = {n_frames, B, (long long)flags, k, params->k, R, lam_bits, n_gram, n_pix, n_ctas,
-               max_rows, n_large, reinterpret_cast<long long>(model->w), reinterpret_cast<long long>(model->b),
+               max_rows, n_large, F1, ip_split, cta_split, (long long)px_split,
+               reinterpret_cast<long long>(model->w), reinterpret_cast<long long>(model->b),
                reinterpret_cast<long long>(model->platt_a),
                reinterpret_cast<long long>(model->platt_b),
                reinterpret_cast<long long>(ctx->stream), reinterpret_cast<long long>(dev),

@@ -32,8 +32,12 @@ struct Control {
     unsigned knn_redo;        // pixels the pruned KNN left to its redo pass (reset by it)
     unsigned knn_redo_ctas;   // redo CTAs finished (reset with knn_redo)
     unsigned knn_redo_list;   // stage-major batch: entries of the redo list (reset by its redo pass)
-    unsigned pad[49];
+    unsigned test_stall;      // testing aid: the tensor-core Gram issues no loads and gives up
+                              // its first wait after a short bound (set and cleared by the host)
+    unsigned long long knn_redo_total;  // pixels the pruned KNN left to its redo pass since last read
+    unsigned pad[46];
 };
+static_assert(sizeof(Control) == 256, "control block: one 256-byte slot");
 
 // Float <-> order-preserving unsigned key (for atomic min/max of floats).
 __host__ __device__ inline unsigned float_to_key(float f) {

@@ -6,7 +6,6 @@
 // scratch carved out of a fixed array in the library's own device memory
 // instead of a context's allocation.
 #include <cuda_runtime.h>
-#include <mutex>
 
 #include "hsc_internal.cuh"
 
@@ -22,8 +21,6 @@ using hsc::PcaScratch;
 
 constexpr int kMaxBands = HSC_NOALLOC_MAX_BANDS;  // 128: Jacobi stays in shared memory
 constexpr int kParts = 64;                         // partial-Gram partitions
-
-size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of the carved regions for the largest supported B.
 constexpr size_t kCtl = 0;
@@ -42,22 +39,18 @@ constexpr size_t kTotal = kMuf + 256 * ((kMaxBands * 4 + 255) / 256);
 // The fixed scratch: every GPU that loads the library holds it until exit.
 static __device__ __align__(256) unsigned char g_pca_scratch[kTotal];
 
-// Device address of g_pca_scratch per device (host code may not use the
-// symbol itself as a device address).
-constexpr int kMaxDevices = 64;
-unsigned char *g_addr[kMaxDevices] = {nullptr};
-std::mutex g_mutex;
-
-cudaError_t scratch_address(int device, unsigned char **out)
+// Device address of g_pca_scratch in the current context. Host code may not
+// use the symbol itself as a device address. The lookup runs on every call
+// instead of being cached per device: after a cudaDeviceReset (or a release
+// of the primary context) the library's device code is loaded again and the
+// array may sit at another address. Once the code is loaded, the lookup
+// allocates nothing.
+cudaError_t scratch_address(unsigned char **out)
 {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_pca_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[device] = static_cast<unsigned char *>(p);
-    }
-    *out = g_addr[device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_pca_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 
@@ -72,8 +65,11 @@ extern "C" hsc_status hsc_pca_one_band_noalloc(void *cuda_stream, const float *c
     if (B > kMaxBands) return HSC_ERR_UNSUPPORTED;  // the fixed scratch holds B <= 128
     if ((long)H * (long)W >= (1L << 31)) return HSC_ERR_UNSUPPORTED;
     static_assert(kTotal < (16u << 20), "fixed scratch must stay modest");
+    // the Jacobi work area must fit in shared memory: this entry point has no
+    // global-memory work area (checked before anything is enqueued)
+    if (hsc::jacobi_global_floats(B) != 0) return HSC_ERR_UNSUPPORTED;
     int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices) {
+    if (cudaGetDevice(&device) != cudaSuccess) {
         cudaGetLastError();
         return HSC_ERR_CUDA;
     }
@@ -81,7 +77,7 @@ extern "C" hsc_status hsc_pca_one_band_noalloc(void *cuda_stream, const float *c
     if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return HSC_ERR_CUDA;
     unsigned char *base = nullptr;
-    if (scratch_address(device, &base) != cudaSuccess) {
+    if (scratch_address(&base) != cudaSuccess) {
         cudaGetLastError();
         return HSC_ERR_CUDA;
     }
@@ -98,9 +94,8 @@ extern "C" hsc_status hsc_pca_one_band_noalloc(void *cuda_stream, const float *c
     s.lambda1 = reinterpret_cast<double *>(base + kLam);
     s.v1f = reinterpret_cast<float *>(base + kV1f);
     s.muf = reinterpret_cast<float *>(base + kMuf);
-    s.jac_A = nullptr;  // B <= 128: the Jacobi work area lives in shared memory
+    s.jac_A = nullptr;  // checked above: the Jacobi work area lives in shared memory
     s.n_part = kParts;
-    (void)up256;
     // the control block keeps the previous call's contents: start from zero
     cudaError_t e = cudaMemsetAsync(s.ctl, 0, sizeof(Control), st);
     const long N = (long)H * W;

@@ -51,6 +51,7 @@ constexpr int kChunk = 64;               // pixels per chunk (one 128-byte fp16 
 constexpr int kBoxPx = 32;               // pixels per TMA box (128 bytes of fp32)
 constexpr int kM = 128;                  // MMA M (bands of one half, zero padded)
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kTestWaitLimit = 1u << 10;  // the wait bound while Control::test_stall is set
 constexpr uint32_t kTmemCols = 512;
 constexpr float kFp16Max = 65504.f;
 constexpr int kFbAcc = 8;                // FP32 recompute: entries per thread per pass
@@ -126,9 +127,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 }
 
 // Bounded wait for the phase of the given parity; false on expiry or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint32_t limit = kWaitLimit)
 {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
     }
@@ -389,7 +391,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
     unsigned char *ops = base + kStages * kStageBytes;             // kOpStages x (hi, lo)
     __shared__ Bars<kWide, kSt> bars;
     __shared__ uint32_t tmem_base;
-    __shared__ int abort_flag, range_flag;
+    __shared__ int abort_flag, range_flag, stall_flag;
     __shared__ float sh[kRows], sc[kRows], isc[kRows];
     __shared__ float bsum_sh[kParts > 1 ? kParts - 1 : 1][kRows];  // parts 1.. of the band sums
 
@@ -412,6 +414,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
         mbar_init(&bars.drained, G::kConvWarps);
         abort_flag = 0;
         range_flag = 0;
+        stall_flag = ctl->test_stall != 0u ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int r = tid; r < kRows; r += kThreads) {
@@ -431,6 +434,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
     tc_fence_after();
     const uint32_t tmem = tmem_base;
     volatile int *abort_p = &abort_flag;
+    // testing aid (Control::test_stall): no loads are issued, so the first
+    // wait of the converters runs out after kTestWaitLimit tries, with no copy
+    // or MMA in flight, and the kernel takes its timeout path
+    const bool stall = stall_flag != 0;
+    const uint32_t wl = stall ? kTestWaitLimit : kWaitLimit;
     int ncommit = 0;  // commits to bars.done by the MMA issuer
     // converter state, kept past the final barrier for the band sums
     constexpr int kRpt = kRows / 128;      // band rows per converter thread
@@ -445,7 +453,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
         // ---------------- TMA producer
         if (lane == 0) {
             int issued = 0;
-            for (int i = 0; i < nchunks && !*abort_p; ++i) {
+            for (int i = 0; i < nchunks && !*abort_p && !stall; ++i) {
                 const int s = i % kStages;
                 if (i >= kStages && !mbar_wait(&bars.empty[s], ((i / kStages) - 1) & 1, abort_p))
                     break;
@@ -480,7 +488,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
                     seg_start = i;
                 }
                 const int t = i % kOpStages;
-                if (!mbar_wait(&bars.op_full[t], (i / kOpStages) & 1, abort_p)) break;
+                if (!mbar_wait(&bars.op_full[t], (i / kOpStages) & 1, abort_p, wl)) break;
                 tc_fence_after();
                 const uint32_t hi = smem_u32(ops + t * 2 * kOpBytes);
                 issue_chunk_mmas<kAccHH, G::kXCol>(tmem, hi, hi + kOpBytes, row_base, col_base,
@@ -526,7 +534,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
             }
             const int s = i % kStages, t = i % kOpStages;
             // warp-uniform exits: the drains below use warp-collective TMEM loads
-            if (!__all_sync(0xffffffffu, mbar_wait(&bars.full[s], (i / kStages) & 1, abort_p)))
+            if (!__all_sync(0xffffffffu, mbar_wait(&bars.full[s], (i / kStages) & 1, abort_p, wl)))
                 break;
             if (i >= kOpStages &&
                 !__all_sync(0xffffffffu,

@@ -738,7 +738,10 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     bad |= active && !isfinite(Ip);
     if (__syncthreads_or(bad) && lane == 0) atomicOr(&ctl->status, ST_NONFINITE_MAP);
     const unsigned nredo = __syncthreads_count(redo);
-    if (!kBatch && lane == 0 && nredo) atomicAdd(&ctl->knn_redo, nredo);
+    if (lane == 0 && nredo) {
+        if (!kBatch) atomicAdd(&ctl->knn_redo, nredo);
+        atomicAdd(&ctl->knn_redo_total, (unsigned long long)nredo);
+    }
     {
         unsigned long long e = evals;
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -762,6 +765,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     if (need > nb) {  // cannot happen: the K-th smallest key is <= tau
         to_redo();
         if (!kBatch) atomicAdd(&ctl->knn_redo, 1u);
+        atomicAdd(&ctl->knn_redo_total, 1ull);
         return;
     }
     // the need smallest undecided keys: need passes of a minimum search

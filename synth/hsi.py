@@ -53,7 +53,7 @@ class Frame:
     cube: np.ndarray
     truth: np.ndarray
     spectra: np.ndarray  # k x B float64 class spectra
-    model: SvmModel
+    model: Optional[SvmModel]  # None when two class spectra coincide (B = 1)
     K: int
     window_rows: int
     lam: float
@@ -136,7 +136,11 @@ def svm_from_endmembers(spectra: np.ndarray, platt_a: float = -5.0,
     b = np.empty(len(pairs), dtype=np.float64)
     for m, (i, j) in enumerate(pairs):
         d = spectra[i] - spectra[j]
-        w[m] = d / np.linalg.norm(d)
+        nd = np.linalg.norm(d)
+        if not nd > 0.0:
+            raise ValueError("classes %d and %d have identical spectra: no separating "
+                             "hyperplane" % (i, j))
+        w[m] = d / nd
         b[m] = -w[m] @ (0.5 * (spectra[i] + spectra[j]))
     M = len(pairs)
     return SvmModel(
@@ -168,8 +172,11 @@ def make_frame(seed: int, H: int, W: int, B: int, k: int = 4,
     for band in range(B):
         noise = rng.standard_normal((H, W), dtype=np.float32) * np.float32(sigma)
         np.clip(base[truth, band] + noise, 0.0, 1.0, out=cube[band])
+    # a one-band cube rescales every class spectrum to the same value: such a
+    # frame serves the PCA alone and carries no SVM model
+    distinct = all(np.linalg.norm(spectra[i] - spectra[j]) > 0.0 for i, j in ovo_pairs(k))
     return Frame(cube=cube, truth=truth, spectra=spectra,
-                 model=svm_from_endmembers(spectra), K=K,
+                 model=svm_from_endmembers(spectra) if distinct else None, K=K,
                  window_rows=window_rows, lam=lam, sigma=sigma, seed=seed)
 
 

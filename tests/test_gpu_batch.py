@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity import e2e_check
 
 pytestmark = pytest.mark.gpu
 
@@ -197,3 +198,55 @@ def test_staged_batch_more_frames_than_sms(hsc, ctx, graph):
     _alone_vs_batch(hsc, ctx, frames, cubes, batch_flags=bflags)
     if graph:  # the replay
         _alone_vs_batch(hsc, ctx, frames, cubes, batch_flags=bflags)
+
+
+def test_staged_graph_replay_with_frames_permuted(hsc, ctx):
+    """More frames than SMs, graph mode, then the same frames in another
+    order: the frame counts, work-item counts and window rows match, but the
+    split between the two frame groups (first wave of eigensolvers, the rest
+    on the high-priority stream) moves. The replay must not reuse the old
+    split; every frame must still equal its single-frame call."""
+    import torch
+    frames = synth.make_batch(170, seed=781)
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert len(frames) > sm
+    cubes = frames_to_device(frames)
+    _alone_vs_batch(hsc, ctx, frames, cubes, batch_flags=hsc.HSC_BATCH_GRAPH)
+    perm = np.random.default_rng(5).permutation(len(frames))
+    # the first wave now holds other frames (another pixel split)
+    assert sum(frames[i].cube[0].size for i in perm[:sm]) != \
+        sum(f.cube[0].size for f in frames[:sm])
+    _alone_vs_batch(hsc, ctx, [frames[i] for i in perm], [cubes[i] for i in perm],
+                    batch_flags=hsc.HSC_BATCH_GRAPH)
+
+
+def test_batch_frames_against_oracle(hsc, ctx):
+    """The 256 uneven snapshot frames (40-64 px square, 125 bands, K = 16,
+    7-row window) through one stage-major call with graph capture; a sample
+    of frames from both eigensolver waves checked against the FP64 oracle at
+    every pixel (the near-tie rule of the end-to-end checks)."""
+    import torch
+    frames = synth.make_batch(256)
+    f0 = frames[0]
+    k = f0.model.n_classes
+    model = hsc.Model.from_host(f0.model)
+    cubes = frames_to_device(frames)
+    labs, O, I, P = outputs(frames, k)
+    for rep in range(2):  # capture, then replay
+        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
+                               flags=hsc.HSC_BATCH_GRAPH, labels=labs, out_probs=O, one_bands=I,
+                               probs=P)
+        ctx.sync()
+    n_all = agree_all = ties_all = 0
+    for i in (0, 1, 37, 100, 151, 152, 153, 200, 254, 255):
+        f = frames[i]
+        N = f.cube.shape[1] * f.cube.shape[2]
+        n, agree, ties = e2e_check(f, labs[i].cpu().numpy(), O[i].cpu().numpy(),
+                                   I[i].cpu().numpy(), P[i].cpu().numpy(), [(0, N)])
+        assert agree >= n - ties
+        n_all += n
+        agree_all += agree
+        ties_all += ties
+    print("\nbatch frames vs oracle: %d pixels, %d labels agree, %d near-ties"
+          % (n_all, agree_all, ties_all))
+    assert agree_all >= 0.995 * n_all

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from parity import sample_rows
+from parity import e2e_check, sample_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -24,34 +24,6 @@ def gpu_classify(hsc, ctx, f, flags=0):
                            one_band=I, probs=P)
     ctx.sync()
     return lab.cpu().numpy(), O.cpu().numpy(), I.cpu().numpy(), P.cpu().numpy()
-
-
-def e2e_check(f, lab, O, I, P, ranges):
-    """The oracle's FP64 path from the cube; the GPU's one-band image differs
-    by dI, which moves each distance by at most 4 dI (|I_p - I_q| <= 1), so a
-    pixel is a near-tie when d_K+1 - d_K < max(1e-6 d_K+1, 8 dI)."""
-    ref = oracle.pca_one_band(f.cube)
-    Pref, _, _ = oracle.svm_probs(f.cube, f.model)
-    dI = float(np.abs(I - ref["I_norm"]).max())
-    assert dI < 2e-5
-    assert np.abs(P - Pref).max() < 1e-4
-    I32 = ref["I_norm"].astype(np.float32)
-    P32 = Pref.astype(np.float32)
-    H, W = I.shape
-    n = agree = ties = 0
-    for p0, p1 in ranges:
-        out = oracle.knn(I32, P32, f.K, f.window_rows, f.lam, p0, p1)
-        gap = out["dK1"] - out["dK"]
-        tie = gap < np.maximum(1e-6 * out["dK1"], 8 * dI)
-        labg = lab.reshape(-1)[p0:p1]
-        Og = O.reshape(O.shape[0], -1)[:, p0:p1]
-        clear = ~tie & (out["gapO"] > 2e-4)
-        np.testing.assert_array_equal(labg[clear], out["labels"][clear])
-        assert np.abs(Og[:, ~tie] - out["O"][:, ~tie]).max(initial=0.0) < 1e-4
-        n += p1 - p0
-        ties += int(tie.sum())
-        agree += int((labg == out["labels"]).sum())
-    return n, agree, ties
 
 
 def test_tiny_frame_all_pixels(hsc, ctx):
@@ -102,17 +74,36 @@ def test_classify_without_optional_outputs(hsc, ctx):
 
 def test_classify_on_raw_one_band(hsc, ctx):
     """Method variant HSC_CLASSIFY_RAW_I: the KNN runs on the raw projection I
-    (no min-max). one_band is that I, and labels and O equal the oracle's KNN
-    on the same map (selection on the float terms of Eq. 1, as the kernels)."""
+    (no min-max). one_band is that I; labels and O equal the oracle's chain
+    on its own raw projection and probabilities outside near-ties (the GPU's
+    I differs by dI, which moves a distance by at most 4 dI (range + dI)),
+    and equal, bit for bit, hsc_knn_filter on the GPU's own maps."""
+    import torch
     f = synth.make_config(1)
     lab, O, I, P = gpu_classify(hsc, ctx, f, flags=hsc.HSC_CLASSIFY_RAW_I)
     ref = oracle.pca_one_band(f.cube)
-    assert np.abs(I - ref["I_raw"]).max() < 2e-5 * max(1.0, np.abs(ref["I_raw"]).max())
+    Pref = oracle.svm_probs(f.cube, f.model)[0]
+    I_raw = ref["I_raw"]
+    dI = float(np.abs(I - I_raw).max())
+    assert dI < 2e-5 * max(1.0, np.abs(I_raw).max())
+    assert np.abs(P - Pref).max() < 1e-4
     k = f.model.n_classes
-    out = oracle.knn(I, P, f.K, f.window_rows, f.lam, 0, I.size, float_keys=True)
-    clear = out["gapO"] > 2e-5
+    out = oracle.knn(I_raw.astype(np.float32), Pref.astype(np.float32), f.K, f.window_rows,
+                     f.lam, 0, I.size)
+    rng_I = float(I_raw.max() - I_raw.min())
+    tie = (out["dK1"] - out["dK"]) < np.maximum(1e-6 * out["dK1"], 8 * dI * (rng_I + dI))
+    clear = ~tie & (out["gapO"] > 2e-4)
     np.testing.assert_array_equal(lab.reshape(-1)[clear], out["labels"][clear])
-    assert np.abs(O.reshape(k, -1) - out["O"]).max() < 1e-5
+    assert np.abs(O.reshape(k, -1)[:, ~tie] - out["O"][:, ~tie]).max(initial=0.0) < 1e-4
+    assert tie.mean() < 0.5
+    # the same KNN call on the GPU's own maps gives the same outputs
+    O2 = torch.empty((k,) + I.shape, device="cuda")
+    lab2 = hsc.hsc_knn_filter(ctx, torch.as_tensor(I, device="cuda"),
+                              torch.as_tensor(P, device="cuda"), f.K, f.window_rows, f.lam,
+                              out_probs=O2)
+    ctx.sync()
+    np.testing.assert_array_equal(lab2.cpu().numpy(), lab)
+    np.testing.assert_array_equal(O2.cpu().numpy(), O)
     # and it differs from the normalised form (the map's scale enters Eq. 1)
     lab_n, _, I_n, _ = gpu_classify(hsc, ctx, f)
     assert not np.allclose(I, I_n)

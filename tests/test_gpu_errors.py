@@ -86,3 +86,41 @@ def test_torch_stream(hsc):
     cx.sync()
     np.testing.assert_array_equal(lab.cpu().numpy(), lab2.cpu().numpy())
     cx.close()
+
+
+@pytest.mark.parametrize("shape", [(16, 32, 32), (128, 96, 128), (200, 40, 48)])
+def test_gram_wait_timeout_is_reported(hsc, shape):
+    """The device-side timeout path: the tensor-core Gram told to issue no
+    loads gives up its first bounded wait (no copy or MMA in flight), flags
+    the status and frees its tensor memory; hsc_sync returns HSC_ERR_TIMEOUT
+    and the same context then classifies the frame as a fresh one does."""
+    import torch
+    B, H, W = shape
+    f = synth.make_frame(B + H, H, W, B, sigma=0.02, K=8, window_rows=5)
+    c = torch.as_tensor(f.cube, device="cuda")
+    m = hsc.Model.from_host(f.model)
+    fresh = hsc.Context(0)
+    ref = hsc.hsc_classify(fresh, c, m, 8, 5, 1.0)
+    fresh.sync()
+    cx = hsc.Context(0)
+    cx.test_stall_next_gram()
+    hsc.hsc_classify(cx, c, m, 8, 5, 1.0)
+    with pytest.raises(hsc.HscError) as e:
+        cx.sync()
+    assert e.value.status == hsc.HSC_ERR_TIMEOUT
+    lab = hsc.hsc_classify(cx, c, m, 8, 5, 1.0)  # the knob applied to one call only
+    cx.sync()
+    np.testing.assert_array_equal(lab.cpu().numpy(), ref.cpu().numpy())
+    # the covariance entry point takes the same path
+    cx.test_stall_next_gram()
+    hsc.hsc_pca_covariance(cx, c)
+    with pytest.raises(hsc.HscError) as e:
+        cx.sync()
+    assert e.value.status == hsc.HSC_ERR_TIMEOUT
+    mu, C = hsc.hsc_pca_covariance(cx, c)
+    mu2, C2 = hsc.hsc_pca_covariance(fresh, c)
+    cx.sync()
+    fresh.sync()
+    np.testing.assert_array_equal(C.cpu().numpy(), C2.cpu().numpy())
+    cx.close()
+    fresh.close()

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from parity import check_knn, sample_rows
+from parity import check_knn, check_knn_outputs, sample_rows
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -156,3 +156,83 @@ def test_pruned_search_rejects_lambda_zero(hsc, ctx):
         run_knn(hsc, ctx, I, P, 4, 3, 0.0, 2)
     assert e.value.status == hsc.HSC_ERR_INVALID_ARG
     run_knn(hsc, ctx, I, P, 4, 3, 0.0, 0)  # auto falls back to the full scan
+
+
+# ---- the path the classifier runs: no neighbour-index output. The pruned
+# walk then finishes most pixels itself (keys below its lower bound summed
+# as they are found, the rest from its undecided-key buffer); only the
+# pixels it cannot finish go to the redo pass, which the counter shows.
+
+def run_knn_outputs(hsc, ctx, I, P, K, R, lam, search):
+    """O and labels of hsc_knn_filter without nbr_idx, and the pixels the
+    pruned walk handed to its redo pass."""
+    import torch
+    dev = torch.device("cuda")
+    It = torch.as_tensor(np.ascontiguousarray(I, dtype=np.float32), device=dev)
+    Pt = torch.as_tensor(np.ascontiguousarray(P, dtype=np.float32), device=dev)
+    k, H, W = Pt.shape
+    O = torch.full((k, H, W), -1.0, dtype=torch.float32, device=dev)
+    lab = torch.full((H, W), -1, dtype=torch.int32, device=dev)
+    ctx.knn_diagnostics()  # reset the counters
+    hsc.hsc_knn_filter(ctx, It, Pt, K, R, lam, out_probs=O, labels=lab, search=search)
+    ctx.sync()
+    _, redo = ctx.knn_diagnostics()
+    return O.cpu().numpy(), lab.cpu().numpy(), redo
+
+
+def rand_probs(k, H, W, seed):
+    """Probability maps independent of the image: any neighbour taken in
+    place of another moves O by about 0.3 / K, far above the O tolerance, so
+    O fingerprints the selected set."""
+    rng = np.random.default_rng(seed)
+    P = rng.random((k, H, W))
+    return (P / P.sum(axis=0)).astype(np.float32)
+
+
+@pytest.mark.parametrize("search", [0, 2])  # AUTO (pruned for lambda > 0), PRUNED
+@pytest.mark.parametrize("H,W,K,R,lam,k", [
+    (32, 32, 8, 5, 1.0, 4),      # the tiny configuration's sizes
+    (37, 45, 40, 14, 1.0, 4),    # paper's K and window, ragged width
+    (20, 130, 64, 32, 1.0, 3),   # maximum K and window
+    (9, 600, 17, 7, 0.5, 5),     # lambda below 1
+    (5, 1030, 3, 3, 2.0, 2),     # lambda above 1, ragged tail
+    (1, 70, 4, 1, 1.0, 8),       # one row, eight classes
+    (40, 7, 12, 4, 1.0, 4),      # narrower than a warp, even window
+    (48, 300, 40, 14, 0.5, 4),   # the paper's K and window, lambda 0.5
+    (48, 300, 40, 14, 2.0, 4),   # and lambda 2
+    (64, 512, 40, 14, 0.25, 4),  # small lambda: the FP64 rule decides most pixels
+])
+def test_fast_path_random_maps_against_oracle(hsc, ctx, H, W, K, R, lam, k, search):
+    I, P = rand_maps(H, W, k, seed=H * 1000 + W + K + int(lam * 8))
+    O, lab, redo = run_knn_outputs(hsc, ctx, I, P, K, R, lam, search)
+    st = check_knn_outputs(I, P, K, R, lam, O, lab)
+    assert st["pixels"] == H * W
+    if lam == 0.25:
+        print("\nrandom %dx%d map, lambda %.2f: FP64 rule decided %d of %d pixels, "
+              "%d handed to the redo pass" % (H, W, lam, st["fp64_checked"], H * W, redo))
+        assert st["fp64_checked"] >= 0.9 * H * W
+
+
+@pytest.fixture(scope="module")
+def neuro_map():
+    """The oracle's normalised one-band image of the 416 x 512 x 128 frame
+    with probability maps independent of it (see rand_probs)."""
+    f = synth.make_config(2)
+    I32 = oracle.pca_one_band(f.cube)["I_norm"].astype(np.float32)
+    return I32, rand_probs(4, *I32.shape, seed=2024)
+
+
+@pytest.mark.parametrize("lam", [1.0, 0.5, 2.0])
+def test_fast_path_neuro_full_map(hsc, ctx, neuro_map, lam):
+    """Every pixel of the 416 x 512 map (K = 40, 14-row window) through the
+    classifier's KNN call against the oracle; the pruned walk must have
+    finished nearly all of them itself."""
+    I, P = neuro_map
+    H, W = I.shape
+    O, lab, redo = run_knn_outputs(hsc, ctx, I, P, 40, 14, lam, 0)
+    st = check_knn_outputs(I, P, 40, 14, lam, O, lab)
+    print("\n416x512 map, lambda %.1f: O max error %.2e; FP64 rule decided %d of %d pixels "
+          "(the rest are its near-ties); %d pixels handed to the redo pass"
+          % (lam, st["o_max_err"], st["fp64_checked"], H * W, redo))
+    assert st["pixels"] == H * W
+    assert redo <= 0.05 * H * W

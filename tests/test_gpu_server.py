@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import synth
+from parity import e2e_labels, sample_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -134,3 +135,33 @@ def test_server_rejects_bad_requests(hsc, pool):
             srv.wait(12345)
     with pytest.raises(hsc.HscError):
         hsc.Server(0, max_inflight=0)
+
+
+def test_server_full_size_pushbroom_against_oracle(hsc):
+    """Two full-size pushbroom requests of the serving stream (128 bands,
+    H 384-640 x W 320-512, their own models and K) in the mix with snapshot
+    requests: labels and O read back to the host checked against the FP64
+    oracle on rows at both edges and inside (near-tie margin for a one-band
+    image within 2e-5 of the oracle's, the bound the PCA tests assert)."""
+    full = synth.make_serving_pool()
+    push = [f for f in full if f.cube.shape[0] == 128][:2]
+    snaps = full[:6]
+    assert all(f.cube.shape[1] >= 384 and f.cube.shape[2] >= 320 for f in push)
+    reqs = push + snaps
+    models = [hsc.Model.from_host(f.model) for f in reqs]
+    cubes = [pinned(f.cube) for f in reqs]
+    with hsc.Server(0, max_inflight=8) as srv:
+        outs = [outputs(f) for f in reqs]
+        tickets = [srv.submit(cubes[i], models[i], f.K, f.window_rows, f.lam, *outs[i])
+                   for i, f in enumerate(reqs)]
+        for t in tickets:
+            srv.wait(t)
+    for i, f in enumerate(push):
+        _, H, W = f.cube.shape
+        lab, O = outs[i][0].numpy(), outs[i][1].numpy()
+        rows = [0, 1, 6, 7, H // 3, H // 2, H - 8, H - 7, H - 1]
+        n, agree, ties = e2e_labels(f, lab, O, 2e-5, sample_rows(H, W, rows))
+        print("\npushbroom %dx%d K=%d: %d pixels, %d labels agree, %d near-ties"
+              % (H, W, f.K, n, agree, ties))
+        assert agree >= n - ties
+        assert (lab == f.truth).mean() > 0.99
