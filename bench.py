@@ -2,17 +2,20 @@
 """Throughput of the spatial-spectral classification hot path on GB300.
 
 One step = one hsc_classify call (PCA one-band, SVM probabilities, KNN
-filter, labels) on a 416 x 512 x 128 float32 neurosurgery-scale frame,
-K = 40, 14-row window, lambda = 1, with the library's default (pruned, exact)
-KNN search. The steps are a stream of frames: step i runs on context i % F
+filter, labels) on a 1024 x 1024 x 256-band float32 frame (1 GiB; class
+spectra of two wide Gaussians, sigma 0.01), K = 40, 14-row window,
+lambda = 1, with the library's defaults: the covariance on the tensor cores
+(FP16 hi/lo parts, FP32 accumulation), the exact pruned KNN search. The
+steps are a stream of frames: step i runs on context i % F
 (--frames-in-flight F, default 8; each context has its own CUDA stream,
 scratch and outputs), so while one frame's eigensolver occupies one SM the
-other frames' GPU-wide stages run beside it; "value" is pixels/s over the K
-steps, "latency_ms" the per-frame latency in that stream, and
-"one_in_flight" the same steps on one context, one frame at a time. The full-window KNN (every window candidate, the paper's
-procedure; same neighbour sets) is timed on the same maps afterwards and
-reported with its FP32-pipe roofline under "knn_full_window". Prints one
-JSON line.
+other frames' GPU-wide stages run beside it. "value" is pixels/s over the K
+steps, "latency_ms" the per-frame latency in that stream, "one_in_flight"
+the same steps on one context, and "plain_fp32" the plain per-frame FP32
+path on the same GPU: the covariance on the FP32 pipe (HSC_COV_FP32_PIPE),
+one frame at a time. The same measurements on the 416 x 512 x 128
+neurosurgery-scale frame are under "neuro"; the batched and served forms
+under "batch" and "serving". Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,20 +42,34 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-CFG = 2
+HEADLINE_CFG = 4
+NEURO_CFG = 2
 METRIC = "KNN-filtered pixels/s (whole classification path) on 1 GB300"
 UNIT = "pixels/s"
-N_ROTATING = 4  # distinct cube copies (4 x 109 MB > 129 MB L2)
+L2_BYTES = 129e6
+
+
+def workload_name(f):
+    B, H, W = f.cube.shape
+    kind = {256: "mixed-precision-scale frame", 128: "neurosurgery-scale frame"}.get(B, "frame")
+    return ("%s %dx%dx%d float32, %d classes, K=%d, %d-row window, lambda=%g"
+            % (kind, H, W, B, f.model.n_classes, f.K, f.window_rows, f.lam))
+
+
+def n_rotating(f):
+    """Distinct device copies of the cube the steps rotate over, so that
+    together they exceed L2 (one copy when a single cube already does)."""
+    return max(1, min(4, int(np.ceil(1.5 * L2_BYTES / f.cube.nbytes))))
 
 
 def workload_config(f, extra=None):
     B, H, W = f.cube.shape
-    cfg = {"workload": "neurosurgery-scale frame %dx%dx%d float32, 4 classes, K=%d, %d-row "
-                       "window, lambda=%g" % (H, W, B, f.K, f.window_rows, f.lam),
+    nr = n_rotating(f)
+    cfg = {"workload": workload_name(f),
            "H": H, "W": W, "B": B, "classes": f.model.n_classes, "K": f.K,
            "window_rows": f.window_rows, "lambda": f.lam,
-           "l2": "%d rotating cube copies (%.0f MB) > 129 MB L2" % (
-               N_ROTATING, N_ROTATING * f.cube.nbytes / 1e6),
+           "l2": "%d rotating cube cop%s of %.0f MB (%.0f MB > 129 MB L2)" % (
+               nr, "y" if nr == 1 else "ies", f.cube.nbytes / 1e6, nr * f.cube.nbytes / 1e6),
            "parallelism": "replicas"}
     if extra:
         cfg.update(extra)
@@ -127,28 +144,14 @@ def knn_pairs(H, W, R):
     return rows * W * W
 
 
-def jacobi_lane_ops(B, refine_iters, basis=16):
-    """FP32 lane-operations (an FMA counts once) of one Jacobi launch: one
-    sweep of (n-1) rounds, each rotating P(P-1)/2 off-diagonal 2x2 blocks (16
-    ops) and P diagonal blocks with their angles (~12 ops); the rebuild of the
-    basis columns (4 ops per logged rotation and column); the Rayleigh-Ritz
-    step on them (C X, X^T (C X), two sweeps of the 16 x 16 problem, X W; B
-    <= 128); and the double-float refinement, ~12 ops per term of C v."""
-    n = B + (B & 1)
-    P = n // 2
-    m = min(basis, B)
-    sweep = (n - 1) * (P * (P - 1) // 2 * 16 + P * 12)
-    rebuild = m * (n - 1) * P * 4
-    rr = (m * B * B + m * (m + 1) // 2 * B + 2 * 15 * 8 * 16 * 12 + m * m * B) if B <= 128 else 0
-    refine = refine_iters * B * B * 12
-    return float(sweep + rebuild + rr + refine)
-
-
-def stage_work(f, knn_pairs_per_launch=None, refine_iters=13):
-    """Algorithmic work per launch of each stage (bytes for HBM-bound stages,
-    FP32 lane-ops for the KNN and the one-CTA Jacobi) and its bound. The KNN
-    counts 4 ops per (pixel, candidate) pair it evaluates: the whole window
-    for the full scan, the measured count for the pruned walk."""
+def stage_work(f, knn_pairs_per_launch=None):
+    """Algorithmic work per launch of each stage and the roofline that bounds
+    it: HBM bytes for the two passes over the cube and the normalisation,
+    FP32-pipe lane-ops for the KNN (4 per (pixel, candidate) pair it
+    evaluates: the whole window for the full scan, the measured count for the
+    pruned walk), and no roofline for the one-CTA eigensolver (a latency,
+    reported in microseconds). The covariance also carries its tensor work
+    (2 B^2 flops per pixel)."""
     B, H, W = f.cube.shape
     N = H * W
     k = f.model.n_classes
@@ -163,8 +166,7 @@ def stage_work(f, knn_pairs_per_launch=None, refine_iters=13):
         "normalize": ("hbm", 8.0 * N),
         # 4 FP32-pipe ops per (pixel, candidate) pair evaluated
         "knn": ("alu", 4.0 * knn_pairs_per_launch),
-        # one CTA on one SM: its bound is that SM's FP32 pipe
-        "jacobi": ("alu_sm", jacobi_lane_ops(B, refine_iters)),
+        "jacobi": ("latency", None),
     }
 
 
@@ -183,59 +185,77 @@ def fp32_pipe_peak_tops(sm_count, mhz):
 
 
 def kernel_source_sha(stage):
-    from paper_2404_10631_gb300.ncu_summary import source_sha
+    from ncu_summary import source_sha
     return source_sha(stage)
 
 
-def traffic_from_profiles(stage):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel."""
+def traffic_from_profiles(stage, workload):
+    """DRAM bytes per launch of a stage from the committed ncu summary, if it
+    was taken on this workload and on the current source of that stage."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
     sha = kernel_source_sha(stage)
     for ln in open(path):
         parts = ln.split()
-        if len(parts) >= 3 and parts[0] == stage and parts[1] == sha:
+        if (len(parts) >= 4 and parts[0] == stage and parts[1] == sha
+                and parts[3] == workload):
             return float(parts[2])
     return None
 
 
 # ----------------------------------------------------------------- oracle --
-def oracle_sample(f, rows, state=None):
-    """FP64 oracle on a row sample of the frame; returns (seconds per frame,
-    description). Per-pixel stages are timed on the sampled rows and scaled
-    by H / len(rows); the per-frame Jacobi is timed whole."""
+def oracle_state(f):
+    """Frame-wide inputs of the oracle's per-pixel stages and the time of its
+    per-frame eigensolver. The band means and covariance (their timing comes
+    from the row samples) use the oracle's C means and, above a million
+    pixels, the same definition contracted by a library matmul per pixel
+    chunk; the Jacobi is the oracle's own and is timed whole; the projection
+    and probabilities are the oracle's, the latter computed in row blocks on
+    all host cores."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import oracle
     B, H, W = f.cube.shape
-    if state is None:
-        state = {}
-    if "C" not in state:  # full-frame inputs of the per-frame / later stages
-        mu = oracle.band_means(f.cube)
-        state["C"] = oracle.covariance(f.cube, mu)
-        pca = oracle.pca_one_band(f.cube)
-        P, _, _ = oracle.svm_probs(f.cube, f.model)
-        state.update(mu=mu, v1=pca["v1"], I32=pca["I_norm"].astype(np.float32),
-                     P32=P.astype(np.float32))
+    mu = oracle.band_means(f.cube)
+    C = (oracle.covariance_matmul(f.cube, mu) if H * W >= (1 << 20)
+         else oracle.covariance(f.cube, mu))
+    t0 = time.perf_counter()
+    ev, V, _, st = oracle.jacobi(C)
+    t_jac = time.perf_counter() - t0
+    v1 = V[:, int(np.argmax(ev))]
+    v1 = v1 if v1[int(np.argmax(np.abs(v1)))] > 0 else -v1
+    _, I_norm = oracle.project(f.cube, mu, v1)
+    blocks = [(r, min(H, r + 32)) for r in range(0, H, 32)]
+
+    def probs(rr):
+        return oracle.svm_probs(np.ascontiguousarray(f.cube[:, rr[0]:rr[1], :]), f.model)[0]
+
+    with ThreadPoolExecutor(max_workers=host_cores()) as ex:
+        P = np.concatenate(list(ex.map(probs, blocks)), axis=1)
+    return {"mu": mu, "v1": v1, "t_jacobi": t_jac,
+            "I32": I_norm.reshape(H, W).astype(np.float32), "P32": P.astype(np.float32)}
+
+
+def oracle_rows_single(f, state, rows):
+    """The oracle's per-pixel stages on a row sample, one core; seconds per
+    frame (scaled by H / rows, plus the per-frame Jacobi) and a description."""
+    import oracle
+    B, H, W = f.cube.shape
     sub = np.ascontiguousarray(f.cube[:, rows, :])
     t0 = time.perf_counter()
     mu_s = oracle.band_means(sub)
     oracle.covariance(sub, mu_s)
-    t1 = time.perf_counter()
-    oracle.jacobi(state["C"])
-    t2 = time.perf_counter()
     oracle.project(sub, state["mu"], state["v1"])
     oracle.svm_probs(sub, f.model)
-    t3 = time.perf_counter()
     for r in rows:
         oracle.knn(state["I32"], state["P32"], f.K, f.window_rows, f.lam, r * W, (r + 1) * W)
-    t4 = time.perf_counter()
+    t = time.perf_counter() - t0
     scale = H / float(len(rows))
-    per_frame = (t1 - t0 + t3 - t2 + t4 - t3) * scale + (t2 - t1)
     desc = ("oracle (single-threaded C, FP64) on %d of %d rows: band means + covariance, "
             "projection, SVM + coupling and KNN timed on the rows and scaled by %.1f; "
-            "full-frame Jacobi timed whole" % (len(rows), H, scale))
-    return per_frame, desc, state
+            "full-frame Jacobi timed whole (%.2f s)" % (len(rows), H, scale, state["t_jacobi"]))
+    return t * scale + state["t_jacobi"], desc
 
 
 # ------------------------------------------------ oracle on all host cores --
@@ -271,24 +291,24 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_parallel(f, state, rows_per_core=4, rounds=2, warmup=1):
+def oracle_parallel(f, state, rows_per_core=2, rounds=2, warmup=1):
     """The oracle as it stands, on every host core at once: one spawned
     process per core, each running the per-pixel stages (band means +
-    covariance, projection, SVM + coupling, KNN) on its own block of rows;
-    the per-frame Jacobi is timed whole on one core. Returns (seconds per
-    frame, cores, description)."""
+    covariance, projection, SVM + coupling, KNN) on its own rows of the
+    frame. Each round is one such sample; its pixels are charged the
+    per-frame Jacobi pro rata. Returns (pixels/s, cores, per-round walls in
+    seconds including the Jacobi share, sample pixels per round, description)."""
     import multiprocessing as mp
-    import oracle
     B, H, W = f.cube.shape
+    N = H * W
     cores = host_cores()
     init = {"mu": state["mu"], "v1": state["v1"], "model": f.model, "I32": state["I32"],
             "P32": state["P32"], "K": f.K, "R": f.window_rows, "lam": f.lam, "W": W}
     rng = np.random.default_rng(1)
-    t0 = time.perf_counter()
-    oracle.jacobi(state["C"])
-    t_jac = time.perf_counter() - t0
+    sample_px = cores * rows_per_core * W
+    jac_share = state["t_jacobi"] * sample_px / float(N)
+    walls = []
     with mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(init,)) as pool:
-        walls = []
         for rnd in range(warmup + rounds):  # the first rounds warm the workers up
             blocks = []
             for c in range(cores):
@@ -297,81 +317,82 @@ def oracle_parallel(f, state, rows_per_core=4, rounds=2, warmup=1):
             t0 = time.perf_counter()
             pool.map(_oracle_rows, blocks, chunksize=1)
             if rnd >= warmup:
-                walls.append(time.perf_counter() - t0)
-    wall = float(np.median(walls))
-    per_frame = wall * H / float(cores * rows_per_core) + t_jac
+                walls.append(time.perf_counter() - t0 + jac_share)
+    rate = sample_px / float(np.median(walls))
     desc = ("oracle (C, FP64) as it stands on %d host cores at once: %d spawned processes, each "
             "running band means + covariance, projection, SVM + coupling and KNN on %d random rows "
-            "(median wall time of %d rounds, scaled to %d rows); the full-frame Jacobi timed whole "
-            "on one core (%.2f s)" % (cores, cores, rows_per_core, rounds, H, t_jac))
-    return per_frame, cores, desc
+            "of the frame per round (%d pixels per round), each round charged the per-frame "
+            "Jacobi pro rata (%.2f s per frame, timed whole on one core); median of %d rounds"
+            % (cores, cores, rows_per_core, sample_px, state["t_jacobi"], len(walls)))
+    return rate, cores, walls, sample_px, desc
 
 
 def run_reference(args, f):
-    """The oracle arm: the FP64 oracle as it stands, on every host core (one
-    spawned process per core on its own rows; each step one round of that,
-    scaled to the frame; the per-frame Jacobi timed whole)."""
+    """The oracle arm: the FP64 oracle as it stands on every host core, on the
+    same workload; each step is one round of the row sample (one spawned
+    process per core on its own rows), so the steps' time is what they ran."""
     from paper_2404_10631_gb300 import replicas
     _, rank, _ = replicas.env_ranks()
     if not replicas.reports(rank):  # under torchrun rank 0 alone times the oracle
         return
-    B, H, W = f.cube.shape
-    N = H * W
-    rows = np.linspace(0, H - 1, 2).astype(int)
-    _, _, state = oracle_sample(f, rows)  # frame-wide inputs (untimed here)
-    t_frame, cores, desc = oracle_parallel(f, state, rows_per_core=2, rounds=max(1, args.steps),
-                                           warmup=max(1, min(args.warmup, 3)))
-    value = N / t_frame
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+    state = oracle_state(f)  # frame-wide inputs (untimed but for the Jacobi)
+    rate, cores, walls, sample_px, desc = oracle_parallel(
+        f, state, rows_per_core=1, rounds=max(1, args.steps), warmup=max(1, min(args.warmup, 3)))
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t_frame, "higher_is_better": True,
+            "ms_per_step": 1e3 * float(np.mean(walls)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(f),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "config": workload_config(f, {"pixels_per_step": sample_px}),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # -------------------------------------------------------------------- ours --
-def run_ours(args, f):
+def pct(v):
+    v = sorted(v)
+    return {"p50": v[len(v) // 2], "p99": v[min(len(v) - 1, int(0.99 * len(v)))]}
+
+
+def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2e=True,
+                 clocks=None):
+    """Everything timed on one single-frame workload; returns a dict.
+
+    value        K steps with F frames in flight (F contexts), cubes resident
+    one_in_flight, plain_fp32
+                 the same steps one frame at a time; plain_fp32 with the
+                 covariance on the FP32 pipe (the plain per-frame FP32 path)
+    coupling_f64 one frame at a time with the coupling solved in FP64
+    stages       per-stage device time (CUDA events around each stage launch)
+                 and its roofline fraction
+    knn_*        the full-window scan and the heap selection on the same maps
+    e2e          the steps through the public API with the cube copied from
+                 pinned host memory and the labels read back every step"""
     import torch
 
-    import paper_2404_10631_gb300 as hsc
     from paper_2404_10631_gb300 import replicas
-    from paper_2404_10631_gb300 import build as hbuild
-
-    world, rank, local = replicas.env_ranks()
-    torch.cuda.set_device(local)
-    replicas.init(world, local, "nccl")
-    if rank == 0:
-        hbuild.build()
-    replicas.barrier(world)
-
-    dev = torch.device("cuda", local)
     B, H, W = f.cube.shape
     N = H * W
     k = f.model.n_classes
+    nr = n_rotating(f)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    ctx = hsc.Context(local, stream=stream)
+    ctx = hsc.Context(dev.index or 0, stream=stream)
     ctx.reserve(B, H, W, k)
-    cubes = [torch.as_tensor(f.cube, device=dev).clone() for _ in range(N_ROTATING)]
+    cubes = [torch.as_tensor(f.cube, device=dev)]
+    cubes += [cubes[0].clone() for _ in range(nr - 1)]
     model = hsc.Model.from_host(f.model, device=dev)
     # launch shapes for this frame shape, picked by the library's autotuner
     t0 = time.perf_counter()
     tune_cfg = ctx.autotune(cubes[0], model)
     tune = {"config": tune_cfg, "seconds": time.perf_counter() - t0,
-            "how": "hsc_autotune on the first cube: Gram TMA staging depth {3, 4} x projection/SVM "
-                   "{1, 4} pixels per thread x {2, 4, 8, 16} CTAs per SM, median of 3 runs each; "
-                   "results do not depend on them"}
-    # frames in flight: F contexts, each with its own stream, scratch and
-    # outputs; step i runs on context i % F, so one frame's single-SM Jacobi
-    # overlaps the other frames' GPU-wide stages
-    F = max(1, args.frames_in_flight)
+            "how": "hsc_autotune on the first cube: Gram TMA staging depth {3, 4} (B <= 128) x "
+                   "projection/SVM {1, 4} pixels per thread x {2, 4, 8, 16} CTAs per SM, median of "
+                   "3 runs each; results do not depend on them"}
     streams = [stream] + [torch.cuda.Stream(dev) for _ in range(F - 1)]
-    ctxs = [ctx] + [hsc.Context(local, stream=s) for s in streams[1:]]
+    ctxs = [ctx] + [hsc.Context(dev.index or 0, stream=s) for s in streams[1:]]
     for c in ctxs[1:]:
         c.reserve(B, H, W, k)
         c.set_tuning(B, H, W, k, (tune_cfg["gram_stages"], tune_cfg["svm_px"],
@@ -382,24 +403,24 @@ def run_ours(args, f):
              torch.empty((H, W), dtype=torch.int32, device=dev)) for _ in range(F)]
     I, P, O, lab = outs[0]
 
-    def step(i, nf=F):
+    def step(i, nf=F, flags=0):
         j = i % nf
         Ij, Pj, Oj, labj = outs[j]
-        hsc.hsc_classify(ctxs[j], cubes[i % N_ROTATING], model, f.K, f.window_rows, f.lam,
+        hsc.hsc_classify(ctxs[j], cubes[i % nr], model, f.K, f.window_rows, f.lam, flags=flags,
                          labels=labj, out_probs=Oj, one_band=Ij, probs=Pj)
 
     tstream = torch.cuda.Stream(dev)  # brackets the timed region across the F streams
 
-    def timed(nf, clocks=None):
-        """K steps with nf frames in flight: (elapsed ms, per-frame latencies)."""
+    def timed(nf, flags=0, clk=None):
+        """K steps with nf frames in flight: (elapsed ms, per-frame latencies, clocks)."""
         for i in range(args.warmup):
-            step(i, nf)
+            step(i, nf, flags)
         for c in ctxs[:nf]:
             c.sync()
         replicas.barrier(world)
         torch.cuda.synchronize(dev)
-        if clocks:
-            clocks.start()
+        if clk:
+            clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -408,7 +429,7 @@ def run_ours(args, f):
             s.wait_event(e0)
         for i in range(args.steps):
             st[i].record(streams[i % nf])
-            step(i, nf)
+            step(i, nf, flags)
             en[i].record(streams[i % nf])
         for s in streams[:nf]:
             ev_s = torch.cuda.Event()
@@ -417,289 +438,314 @@ def run_ours(args, f):
         e1.record(tstream)
         torch.cuda.synchronize(dev)
         replicas.barrier(world)
-        clk = clocks.stop() if clocks else None
-        return e0.elapsed_time(e1), [st[i].elapsed_time(en[i]) for i in range(args.steps)], clk
+        for c in ctxs[:nf]:
+            c.sync()  # raises on a device-side error of the timed steps
+        return (e0.elapsed_time(e1), [st[i].elapsed_time(en[i]) for i in range(args.steps)],
+                clk.stop() if clk else None)
 
-    # ---- device-resident timed region: F frames in flight, then one at a time
-    clocks = ClockSampler(local)
-    elapsed, per_step, clk = timed(F, clocks)
+    # ---- device-resident timed regions: F frames in flight, one at a time,
+    # the plain FP32 path one at a time
+    elapsed, per_step, clk = timed(F, 0, clocks)
     elapsed1, per_step1, _ = timed(1) if F > 1 else (elapsed, per_step, None)
-    ctx.sync()
+    elapsed_p, per_step_p, _ = timed(1, hsc.HSC_COV_FP32_PIPE)
     sweeps, refine_iters, sweep_cyc, refine_cyc = ctx.pca_diagnostics(cycles=True)
-    # ---- per-stage times: the same steps again on the first context, one
-    # frame at a time, with CUDA events around each stage
-    for c in ctxs:
-        c.sync()
-    ctx.knn_candidates_evaluated()  # reset the pruned walk's counter
-    ctx.profile(True)
-    ctx.profile_read()
-    for i in range(args.steps):
-        step(i, 1)
-    ctx.sync()
-    stage_ms, stage_kernels, dropped = ctx.profile_read()
-    ctx.profile(False)
-    knn_evals = ctx.knn_candidates_evaluated()  # the profiled steps
-    knn_evals_per_launch = knn_evals / float(args.steps)
 
-    # ---- the paper's full-window KNN on the same maps (timed on its own)
+    def profiled(flags=0):
+        """Per-stage device ms per launch over the steps, one frame at a time
+        on the first context, CUDA events around each stage launch."""
+        ctx.profile(True)
+        ctx.profile_read()
+        for i in range(args.steps):
+            step(i, 1, flags)
+        ctx.sync()
+        ms, kern, _ = ctx.profile_read()
+        ctx.profile(False)
+        return {n: v / args.steps for n, v in ms.items()}, kern
+
+    ctx.knn_diagnostics()  # reset the pruned walk's counters
+    stage_ms, stage_kernels = profiled()
+    knn_evals, knn_redo = ctx.knn_diagnostics()  # the profiled steps
+    knn_evals_per_launch = knn_evals / float(args.steps)
+    plain_ms, _ = profiled(hsc.HSC_COV_FP32_PIPE)
+    f64_ms, _ = profiled(hsc.HSC_SVM_COUPLE_F64)
+
+    # ---- the paper's full-window KNN on the same maps (timed on its own),
+    # and its heap selection as an A/B point
     ctx.profile(True)
     ctx.profile_read()
-    for i in range(args.steps):
+    n_full = min(args.steps, 16)
+    for i in range(n_full):
         hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam, out_probs=O, labels=lab,
                            search=hsc.HSC_KNN_SEARCH_FULL)
     full_ms, _, _ = ctx.profile_read()
-    # the paper's heap selection (partial heapsort) on the same maps: an A/B point
-    n_heap = min(args.steps, 3)
+    n_heap = min(args.steps, 2)
     for i in range(n_heap):
         hsc.hsc_knn_filter(ctx, I, P, f.K, f.window_rows, f.lam, out_probs=O, labels=lab,
                            search=hsc.HSC_KNN_SEARCH_HEAP)
     heap_ms, _, _ = ctx.profile_read()
     ctx.profile(False)
-    full_ms_launch = full_ms["knn"] / args.steps
-    heap_ms_launch = heap_ms["knn"] / n_heap
-    elapsed_max, elapsed1_max = replicas.max_over_ranks([elapsed, elapsed1], world, dev)
-    value = replicas.whole_job_rate(N * args.steps, world, elapsed_max / 1e3)
-    value1 = replicas.whole_job_rate(N * args.steps, world, elapsed1_max / 1e3)
-
-    # ---- end to end through the public API with host buffers
-    host_cube = torch.empty((B, H, W), dtype=torch.float32).pin_memory()
-    host_cube.copy_(torch.from_numpy(f.cube))
-    host_labs = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(F)]
-    host_model = [torch.from_numpy(a).pin_memory() for a in
-                  (f.model.w, f.model.b, f.model.platt_a, f.model.platt_b)]
-    # per context: its device cube and its own model copy (the copies of one
-    # step and the kernels of another never share a buffer)
-    e2e_models = [hsc.Model.from_host(f.model, device=dev) for _ in range(F)]
-    e2e_cubes = [torch.empty((B, H, W), dtype=torch.float32, device=dev) for _ in range(F)]
-    h2d = host_cube.numel() * 4 + sum(a.numel() * 4 for a in host_model)
-    d2h = host_labs[0].numel() * 4
-    # the host link's own rate for this copy (pinned cube -> device, CUDA
-    # events), the ceiling of the end-to-end number
-    for r in range(8):
-        if r == 3:
-            l0 = torch.cuda.Event(enable_timing=True)
-            l0.record(stream)
-        e2e_cubes[0].copy_(host_cube, non_blocking=True)
-    l1 = torch.cuda.Event(enable_timing=True)
-    l1.record(stream)
-    l1.synchronize()
-    link_gbs = host_cube.numel() * 4 * 5 / (l0.elapsed_time(l1) / 1e3) / 1e9
-    n_e2e = max(F, args.steps)
-    done = [None] * F
-    replicas.barrier(world)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for i in range(n_e2e):
-        j = i % F
-        if done[j] is not None:
-            done[j].synchronize()  # context j's last frame is out: its host labels are read
-        with torch.cuda.stream(streams[j]):
-            dcube, mj = e2e_cubes[j], e2e_models[j]
-            dcube.copy_(host_cube, non_blocking=True)
-            for d, h in zip((mj.w, mj.b, mj.platt_a, mj.platt_b), host_model):
-                d.copy_(h, non_blocking=True)
-            hsc.hsc_classify(ctxs[j], dcube, mj, f.K, f.window_rows, f.lam, labels=outs[j][3])
-            host_labs[j].copy_(outs[j][3], non_blocking=True)
-            done[j] = torch.cuda.Event()
-            done[j].record(streams[j])
-    for s in streams:
-        s.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = replicas.whole_job_rate(N * n_e2e, world,
-                                        replicas.max_over_ranks([e2e_s], world, dev)[0])
     ctx.sync()
+    full_ms_launch = full_ms["knn"] / n_full
+    heap_ms_launch = heap_ms["knn"] / n_heap
+    e_max, e1_max, ep_max = replicas.max_over_ranks([elapsed, elapsed1, elapsed_p], world, dev)
+    value = replicas.whole_job_rate(N * args.steps, world, e_max / 1e3)
+    value1 = replicas.whole_job_rate(N * args.steps, world, e1_max / 1e3)
+    value_p = replicas.whole_job_rate(N * args.steps, world, ep_max / 1e3)
 
-    # ---- batched uneven frames vs the plain per-frame path (same GPU)
+    # ---- per-stage rooflines (SURVEY-style bounds: HBM for the passes over
+    # the cube, FP32 pipe for the KNN, latency for the one-CTA eigensolver)
+    peaks, peak_src = load_peaks()
+    work = stage_work(f, knn_evals_per_launch)
+    wname = workload_name(f)
+    stages = {}
+    for name, ms in stage_ms.items():
+        if stage_kernels[name] == 0:
+            continue
+        bound, units = work[name]
+        entry = {"ms_per_launch": ms, "share": ms / max(1e-12, sum(stage_ms.values())),
+                 "kernels_per_launch": stage_kernels[name] / float(args.steps), "bound": bound}
+        if bound == "hbm":
+            ach = units / (ms / 1e3) / 1e9
+            entry.update(achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                         frac=ach / peaks["hbm_gbs"], algorithmic=units,
+                         traffic=traffic_from_profiles(name, wname))
+        elif bound == "alu":
+            ach = units / (ms / 1e3) / 1e12
+            entry.update(achieved=ach, peak=fp32_rate, unit="TFLOP/s", frac=ach / fp32_rate,
+                         algorithmic=units, traffic=traffic_from_profiles(name, wname),
+                         note="4 FP32-pipe ops per (pixel, candidate) pair the pruned walk "
+                              "evaluated; peak: " + fp32_peak_note)
+        else:
+            entry["us_per_launch"] = 1e3 * ms
+            entry["note"] = ("one CTA (one SM) per frame: a latency, no roofline; with frames in "
+                             "flight the other frames' GPU-wide stages run beside it")
+        if name == "moments":
+            flops = 2.0 * B * B * N
+            entry["tensor"] = {"algorithmic_flops": flops,
+                               "achieved_tflops": flops / (ms / 1e3) / 1e12,
+                               "frac_of_bf16_burst": flops / (ms / 1e3) / 1e12 / peaks["bf16_tflops"],
+                               "note": "the Gram's 2 B^2 flops per pixel (the hi/lo split issues "
+                                       "three MMAs per product)"}
+        stages[name] = entry
+    # the roofline object: the dominant stage among those with a roofline
+    # (the eigensolver holds one SM and overlaps other frames' stages)
+    dom = max((n for n in stages if stages[n]["bound"] in ("hbm", "alu")),
+              key=lambda n: stages[n]["ms_per_launch"])
+    d = stages[dom]
+    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
+                "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
+                "traffic": d.get("traffic"),
+                "peak_source": ("FP32 FFMA issue rate measured in this run (hsc_measure_fma_rate)"
+                                if d["bound"] == "alu" else
+                                "hbm_gbs (burst copy) of MEASURED_PEAKS.json, %s" % peak_src),
+                "work_per_launch": d["algorithmic"],
+                "ms_per_launch": d["ms_per_launch"],
+                "rule": "the stage with the largest device time among those with a roofline "
+                        "(moments, projection + SVM, normalisation: HBM; KNN: FP32 pipe); the "
+                        "one-CTA eigensolver is a latency, reported in stages.jacobi"}
+    full_ops = 4.0 * knn_pairs(H, W, f.window_rows)
+    full_ach = full_ops / (full_ms_launch / 1e3) / 1e12
+    knn_full = {"search": "full window (the paper's procedure: every window candidate)",
+                "bound": "alu", "ms_per_launch": full_ms_launch, "achieved": full_ach,
+                "peak": fp32_rate, "unit": "TFLOP/s", "frac": full_ach / fp32_rate,
+                "work_per_launch": full_ops,
+                "traffic": traffic_from_profiles("knn_full", wname),
+                "note": "same neighbour sets as the pruned walk used in the step"}
+    knn_heap = {"search": "heap selection (the paper's partial heapsort: every window candidate "
+                          "keyed, the K smallest kept in a max-heap)",
+                "ms_per_launch": heap_ms_launch,
+                "note": "same neighbour sets as the other searches; an A/B point, not the step"}
+    pruned_ms = stages["knn"]["ms_per_launch"]
+    knn_pruned = {"search": "pruned walk (exact)", "candidates_per_launch": knn_evals_per_launch,
+                  "window_pairs_per_launch": knn_pairs(H, W, f.window_rows),
+                  "redo_pixels_per_launch": knn_redo / float(args.steps),
+                  "ms_per_launch": pruned_ms,
+                  "frac_on_evaluated_pairs": stages["knn"].get("frac"),
+                  # the full window's work (4 FP32 ops per window pair) over the pruned
+                  # walk's time, against the FP32 pipe: the same neighbour sets in less
+                  # time than the full scan could take at the pipe's peak when above 1
+                  "window_equivalent_frac": full_ops / (pruned_ms / 1e3) / 1e12 / fp32_rate}
+
+    out = {"workload": wname, "config": workload_config(f, {"frames_in_flight": F}),
+           "value": value, "unit": UNIT, "ms_per_step": e_max / args.steps,
+           "latency_ms": pct(per_step),
+           "one_in_flight": {"value": value1, "unit": UNIT, "ms_per_step": e1_max / args.steps,
+                             "latency_ms": pct(per_step1),
+                             "note": "the same steps on one context, one frame at a time"},
+           "plain_fp32": {"value": value_p, "unit": UNIT, "ms_per_step": ep_max / args.steps,
+                          "latency_ms": pct(per_step_p),
+                          "stages_ms": {n: v for n, v in plain_ms.items() if v > 0},
+                          "note": "the plain per-frame FP32 path: covariance Gram on the FP32 "
+                                  "pipe (HSC_COV_FP32_PIPE), FP32 SVM and KNN, one frame at a "
+                                  "time on one context",
+                          "speedup_in_flight": value / value_p,
+                          "speedup_one_in_flight": value1 / value_p,
+                          "p99_ratio_in_flight": pct(per_step)["p99"] / pct(per_step_p)["p99"]},
+           "coupling_f64": {"project_svm_ms": f64_ms.get("project_svm"),
+                            "project_svm_ms_fp32": stage_ms.get("project_svm"),
+                            "frame_ms": sum(f64_ms.values()),
+                            "note": "HSC_SVM_COUPLE_F64: the per-pixel coupling solve in FP64, "
+                                    "one frame at a time (stage device times)"},
+           "roofline": roofline, "stages": stages,
+           "knn_full_window": knn_full, "knn_pruned": knn_pruned, "knn_heap": knn_heap,
+           "gpu_launches": int(round(sum(stage_kernels.values()))),
+           "autotune": tune,
+           "jacobi": {"fp32_sweeps": sweeps, "refine_iters": refine_iters,
+                      "sweep_cycles": sweep_cyc, "refine_cycles": refine_cyc},
+           "clocks": clk}
+
+    if with_e2e:
+        # ---- end to end through the public API with host buffers
+        host_cube = torch.empty((B, H, W), dtype=torch.float32).pin_memory()
+        host_cube.copy_(torch.from_numpy(f.cube))
+        host_labs = [torch.empty((H, W), dtype=torch.int32).pin_memory() for _ in range(F)]
+        host_model = [torch.from_numpy(a).pin_memory() for a in
+                      (f.model.w, f.model.b, f.model.platt_a, f.model.platt_b)]
+        # per context: its device cube and its own model copy (the copies of one
+        # step and the kernels of another never share a buffer)
+        e2e_models = [hsc.Model.from_host(f.model, device=dev) for _ in range(F)]
+        e2e_cubes = [cubes[j] if j < nr else torch.empty((B, H, W), dtype=torch.float32,
+                                                           device=dev) for j in range(F)]
+        h2d = host_cube.numel() * 4 + sum(a.numel() * 4 for a in host_model)
+        d2h = host_labs[0].numel() * 4
+        # the host link's own rate for this copy (pinned cube -> device, CUDA
+        # events), the ceiling of the end-to-end number
+        for r in range(6):
+            if r == 2:
+                l0 = torch.cuda.Event(enable_timing=True)
+                l0.record(stream)
+            e2e_cubes[0].copy_(host_cube, non_blocking=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l1.record(stream)
+        l1.synchronize()
+        link_gbs = host_cube.numel() * 4 * 4 / (l0.elapsed_time(l1) / 1e3) / 1e9
+        n_e2e = max(F, args.steps)
+        done = [None] * F
+        replicas.barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for i in range(n_e2e):
+            j = i % F
+            if done[j] is not None:
+                done[j].synchronize()  # context j's last frame is out: its host labels are read
+            with torch.cuda.stream(streams[j]):
+                dcube, mj = e2e_cubes[j], e2e_models[j]
+                dcube.copy_(host_cube, non_blocking=True)
+                for d_, h in zip((mj.w, mj.b, mj.platt_a, mj.platt_b), host_model):
+                    d_.copy_(h, non_blocking=True)
+                hsc.hsc_classify(ctxs[j], dcube, mj, f.K, f.window_rows, f.lam,
+                                 labels=outs[j][3])
+                host_labs[j].copy_(outs[j][3], non_blocking=True)
+                done[j] = torch.cuda.Event()
+                done[j].record(streams[j])
+        for s_ in streams:
+            s_.synchronize()
+        e2e_s = time.perf_counter() - t0
+        for c in ctxs:
+            c.sync()
+        e2e_value = replicas.whole_job_rate(N * n_e2e, world,
+                                            replicas.max_over_ranks([e2e_s], world, dev)[0])
+        bound = world * link_gbs * 1e9 / h2d * N
+        out["e2e"] = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "steps": n_e2e, "h2d_link_gbs": link_gbs,
+                      "link_bound": bound, "frac_of_link_bound": e2e_value / bound,
+                      "note": "each frame's cube crosses the host link once (pinned host -> "
+                              "device); h2d_link_gbs is that copy alone, timed in this run, and "
+                              "link_bound the pixels/s it allows on every rank's own link"}
+        del host_cube, e2e_cubes
+    for c in ctxs[1:]:
+        c.close()
+    ctx.close()
+    del cubes, outs
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args, f):
+    import torch
+
+    import paper_2404_10631_gb300 as hsc
+    from paper_2404_10631_gb300 import build as hbuild
+    from paper_2404_10631_gb300 import replicas
+
+    world, rank, local = replicas.env_ranks()
+    torch.cuda.set_device(local)
+    replicas.init(world, local, "nccl")
+    if rank == 0:
+        hbuild.build()
+    replicas.barrier(world)
+    dev = torch.device("cuda", local)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, peak_src = load_peaks()
+    # FP32 / FP64 multiply-add issue rates of this GPU, measured here (T lane-ops/s)
+    fp32_rate = hsc.hsc_measure_fma_rate(dev.index) / 1e12
+    fp64_rate = hsc.hsc_measure_fma_rate(dev.index, fp64=True) / 1e12
+    note = "FP32 FFMA issue rate measured in this run (hsc_measure_fma_rate)"
+    F = max(1, args.frames_in_flight)
+
+    head = frame_stream(hsc, f, dev, args, world, F, fp32_rate, note, clocks=ClockSampler(local))
+    neuro = None
+    if not args.no_neuro:
+        fn = synth.make_config(NEURO_CFG)
+        neuro = frame_stream(hsc, fn, dev, args, world, F, fp32_rate, note)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = hsc.Context(local, stream=stream)
     batch = None
     if not args.no_batch:
         batch = run_batch(hsc, ctx, stream, dev, args)
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(hsc, ctx, stream, dev, args)
-    mixed = None
-    if not args.no_mixed and world == 1:
-        mixed = run_mixed(hsc, ctx, stream, dev, args)
+    ctx.close()
 
-    # ---- roofline of the dominant stage
-    peaks, peak_src = load_peaks()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    # FP32 / FP64 multiply-add issue rates of this GPU, measured here (T lane-ops/s)
-    fp32_rate = hsc.hsc_measure_fma_rate(dev.index) / 1e12
-    fp64_rate = hsc.hsc_measure_fma_rate(dev.index, fp64=True) / 1e12
-    work = stage_work(f, knn_evals_per_launch, refine_iters)
-    stages = {}
-    for name, ms in stage_ms.items():
-        if stage_kernels[name] == 0:  # the min-max normalisation runs inside the pruned KNN
-            continue
-        launches = max(1, args.steps)
-        avg_ms = ms / launches
-        bound, units = work[name]
-        entry = {"ms_per_launch": avg_ms, "share": ms / max(1e-12, sum(stage_ms.values())),
-                 "kernels_per_launch": stage_kernels[name] / launches, "bound": bound}
-        if bound == "hbm":
-            ach = units / (avg_ms / 1e3) / 1e9
-            entry.update(achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
-                         frac=ach / peaks["hbm_gbs"], algorithmic=units)
-        elif bound in ("alu", "alu_sm"):
-            sms = sm_count if bound == "alu" else 1
-            peak = fp32_rate * sms / sm_count
-            ach = units / (avg_ms / 1e3) / 1e12
-            entry.update(achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                         algorithmic=units, bound="alu")
-            if bound == "alu_sm":
-                entry["note"] = "one CTA: peak of the one SM it runs on (FP32 lane-ops)"
-        stages[name] = entry
-    # the dominant kernel: the stage with the largest time per launch
-    dom = max(stages, key=lambda s: stages[s]["ms_per_launch"])
-    d = stages[dom]
-    one_sm = d.get("note") is not None
-    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
-                "peak": d["peak"], "unit": d["unit"], "frac": d["frac"],
-                "traffic": traffic_from_profiles(dom),
-                "peak_source": ("FP32 FFMA issue rate measured in this run (hsc_measure_fma_rate)%s"
-                                % (", per SM" if one_sm else "")
-                                if d["bound"] == "alu" else "hbm_gbs, %s" % peak_src),
-                "work_per_launch": d["algorithmic"]}
-    if one_sm:
-        roofline["note"] = d["note"]
-
-    fp32_peak = fp32_rate
-    full_ops = 4.0 * knn_pairs(H, W, f.window_rows)
-    full_ach = full_ops / (full_ms_launch / 1e3) / 1e12
-    knn_full = {"search": "full window (the paper's procedure: every window candidate)",
-                "bound": "alu", "ms_per_launch": full_ms_launch, "achieved": full_ach,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": full_ach / fp32_peak,
-                "work_per_launch": full_ops,
-                "traffic": traffic_from_profiles("knn"),
-                "note": "same neighbour sets as the pruned walk used in the step"}
-    knn_heap = {"search": "heap selection (the paper's partial heapsort: every window candidate "
-                          "keyed, the K smallest kept in a max-heap)", "ms_per_launch": heap_ms_launch,
-                "note": "same neighbour sets as the other searches; an A/B point, not the step"}
-    pruned_ms = stages["knn"]["ms_per_launch"]
-    knn_pruned = {"search": "pruned walk (exact)", "candidates_per_launch": knn_evals_per_launch,
-                  "window_pairs_per_launch": knn_pairs(H, W, f.window_rows),
-                  "ms_per_launch": pruned_ms,
-                  "frac_on_evaluated_pairs": stages["knn"].get("frac"),
-                  # the full window's work (4 FP32 ops per window pair) over the pruned
-                  # walk's time, against the FP32 pipe: the same neighbour sets in less
-                  # time than the full scan could take at the pipe's peak when above 1
-                  "window_equivalent_frac": full_ops / (pruned_ms / 1e3) / 1e12 / fp32_peak}
-
-    def pct(v):
-        v = sorted(v)
-        return {"p50": v[len(v) // 2], "p99": v[min(len(v) - 1, int(0.99 * len(v)))]}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_max / args.steps,
+    B, H, W = f.cube.shape
+    N = H * W
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": workload_config(f, {"frames_per_step_per_gpu": 1,
-                                          "frames_in_flight": F}),
-            "latency_ms": pct(per_step),
-            "one_in_flight": {"value": value1, "unit": UNIT,
-                              "ms_per_step": elapsed1_max / args.steps,
-                              "latency_ms": pct(per_step1),
-                              "note": "the same steps on one context, one frame at a time"},
-            "roofline": roofline,
-            "stages": stages,
-            "knn_full_window": knn_full,
-            "knn_pruned": knn_pruned,
-            "knn_heap": knn_heap,
+            "config": workload_config(f, {"frames_per_step_per_gpu": 1, "frames_in_flight": F,
+                                          "precision": "cube float32; covariance Gram FP16 hi/lo "
+                                                       "on tensor cores, FP32 accumulation; "
+                                                       "eigenpair refined to an FP64-level "
+                                                       "residual; SVM, coupling and KNN FP32"}),
+            "latency_ms": head["latency_ms"],
+            "one_in_flight": head["one_in_flight"],
+            "plain_fp32": head["plain_fp32"],
+            "coupling_f64": head["coupling_f64"],
+            "roofline": head["roofline"],
+            "stages": head["stages"],
+            "knn_full_window": head["knn_full_window"],
+            "knn_pruned": head["knn_pruned"],
+            "knn_heap": head["knn_heap"],
+            "e2e": head["e2e"],
+            "gpu_launches": head["gpu_launches"],
+            "autotune": head["autotune"],
+            "jacobi": head["jacobi"],
+            "neuro": neuro,
             "batch": batch,
             "serving": serving,
-            "mixed_precision": mixed,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "steps": n_e2e,
-                    "h2d_link_gbs": link_gbs,
-                    "link_bound": world * link_gbs * 1e9 / h2d * N,
-                    "frac_of_link_bound": e2e_value / (world * link_gbs * 1e9 / h2d * N),
-                    "note": "each frame's cube crosses the host link once (pinned host -> device); "
-                            "h2d_link_gbs is that copy alone, timed in this run (rank 0), and "
-                            "link_bound the pixels/s it allows on every rank's own link"},
-            "gpu_launches": int(sum(stage_kernels.values())),
-            "autotune": tune,
-            "fp_peaks": {"fp32_lane_ops_per_s": fp32_rate * 1e12, "fp64_lane_ops_per_s": fp64_rate * 1e12,
-                         "fp32_nominal": fp32_pipe_peak_tops(sm_count, peaks.get("sm_max_mhz", 2070.0)) * 1e12,
-                         "how": "hsc_measure_fma_rate: 8 independent FFMA / DFMA chains per thread, "
-                                "1024 threads per SM, CUDA events"},
-            "jacobi": {"fp32_sweeps": sweeps, "refine_iters": refine_iters,
-                       "sweep_cycles": sweep_cyc, "refine_cycles": refine_cyc},
-            "clocks": clk}
+            "fp_peaks": {"fp32_lane_ops_per_s": fp32_rate * 1e12,
+                         "fp64_lane_ops_per_s": fp64_rate * 1e12,
+                         "fp32_nominal": fp32_pipe_peak_tops(sm_count,
+                                                             peaks.get("sm_max_mhz", 2070.0)) * 1e12,
+                         "how": "hsc_measure_fma_rate: 8 independent FFMA / DFMA chains per "
+                                "thread, 1024 threads per SM, CUDA events"},
+            "clocks": head["clocks"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rows = np.linspace(0, H - 1, 16).astype(int)
-        t_frame, desc, state = oracle_sample(f, rows)
-        t_par, cores, desc_par = oracle_parallel(f, state)
-        line["cpu_baseline"] = {"value": N / t_par, "unit": UNIT, "cores": cores,
+        state = oracle_state(f)
+        rows = np.linspace(0, H - 1, 4).astype(int)
+        t_frame, desc = oracle_rows_single(f, state, rows)
+        rate, cores, walls, sample_px, desc_par = oracle_parallel(f, state)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores,
                                 "kind": "oracle", "sample": desc_par,
                                 "single_core": {"value": N / t_frame, "unit": UNIT, "cores": 1,
                                                 "sample": desc}}
     if replicas.reports(rank):
         print(json.dumps(line), flush=True)
-    for c in ctxs[1:]:
-        c.close()
-    ctx.close()
     replicas.finalize(world)
-
-
-def run_mixed(hsc, ctx, stream, dev, args, reps=5):
-    """The 1024 x 1024 x 256-band frame (two wide Gaussians per class
-    spectrum, sigma 0.01; 1 GiB float32): the covariance on the tensor cores
-    as FP16 hi/lo parts with FP32 accumulation, the eigenvector refined in
-    double-float, the rest FP32. hsc_classify one frame at a time on one
-    context (the cube is 8x L2), with per-stage device times and the HBM
-    fraction of the two passes over the cube."""
-    import torch
-    f = synth.make_config(4)
-    B, H, W = f.cube.shape
-    N = H * W
-    k = f.model.n_classes
-    cube = torch.as_tensor(f.cube, device=dev)
-    model = hsc.Model.from_host(f.model, device=dev)
-    lab = torch.empty((H, W), dtype=torch.int32, device=dev)
-    ctx.reserve(B, H, W, k)
-
-    def one():
-        hsc.hsc_classify(ctx, cube, model, f.K, f.window_rows, f.lam, labels=lab)
-
-    for _ in range(3):
-        one()
-    ctx.sync()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
-    ev[0].record(stream)
-    for i in range(reps):
-        one()
-        ev[i + 1].record(stream)
-    torch.cuda.synchronize(dev)
-    ctx.sync()
-    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(reps))
-    ms = ev[0].elapsed_time(ev[reps]) / reps
-    ctx.profile(True)
-    ctx.profile_read()
-    for _ in range(reps):
-        one()
-    ctx.sync()
-    st_ms, _, _ = ctx.profile_read()
-    ctx.profile(False)
-    stages = {n: round(v / reps, 4) for n, v in st_ms.items() if v > 0}
-    peaks, _ = load_peaks()
-    cube_bytes = 4.0 * B * N
-
-    def hbm_frac(stage, nbytes):
-        t = stages.get(stage)
-        return None if not t else nbytes / (t / 1e3) / 1e9 / peaks["hbm_gbs"]
-
-    del cube
-    torch.cuda.empty_cache()
-    return {"workload": "mixed-precision frame 1024x1024x256 float32 (1 GiB), 4 classes, K=40, "
-                        "14-row window, lambda=1: FP16 hi/lo tensor-core covariance with FP32 "
-                        "accumulation, double-float eigen-refinement, FP32 SVM and KNN",
-            "value": N / (ms / 1e3), "unit": UNIT, "ms_per_frame": ms,
-            "p50_ms": per[len(per) // 2], "p99_ms": per[-1], "frames": reps,
-            "stages_ms": stages,
-            "hbm_frac": {"moments": hbm_frac("moments", cube_bytes),
-                         "project_svm": hbm_frac("project_svm",
-                                                 cube_bytes + 4.0 * N + 4.0 * k * N)},
-            "errors": "per-stage errors against the FP64 oracle: tests/test_gpu_mixed.py"}
 
 
 def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
@@ -879,14 +925,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true",
-                    help="skip the 1024x1024x256 mixed-precision frame")
+    ap.add_argument("--no-neuro", action="store_true",
+                    help="skip the 416x512x128 neurosurgery-scale frame")
     ap.add_argument("--frames-in-flight", type=int, default=8,
                     help="contexts (streams) the steps rotate over; 1 = one frame at a time")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    f = synth.make_config(CFG)
+    f = synth.make_config(HEADLINE_CFG)
     if args.impl == "reference":
         run_reference(args, f)
     else:

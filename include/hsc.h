@@ -106,7 +106,7 @@ typedef struct {
 
 /* flags for hsc_pca_one_band */
 #define HSC_PCA_MINMAX 1u        /* write (I - min)/(max - min) in [0,1] (what the KNN uses) */
-/* flags for hsc_pca_covariance */
+/* flag for hsc_pca_covariance / hsc_classify */
 #define HSC_COV_FP32_PIPE 4u     /* compute the Gram on the FP32 pipe instead of the tensor cores */
 /* flags for hsc_svm_probs / hsc_classify */
 #define HSC_SVM_COUPLE_F64 2u    /* solve the per-pixel coupling system in FP64 */
@@ -221,7 +221,9 @@ hsc_status hsc_knn_filter(hsc_ctx *ctx, const float *one_band, const float *prob
  *   out_probs k x H x W float32 (device, nullable): O
  *   one_band  H x W float32 (device, nullable): the normalised one-band image
  *   probs     k x H x W float32 (device, nullable): the SVM maps P
- *   flags     0, HSC_SVM_COUPLE_F64, HSC_CLASSIFY_RAW_I, HSC_CUBE_BIP (combinable) */
+ *   flags     0, HSC_SVM_COUPLE_F64, HSC_CLASSIFY_RAW_I, HSC_CUBE_BIP,
+ *             HSC_COV_FP32_PIPE (the covariance Gram on the FP32 pipe instead of
+ *             the tensor cores: the plain FP32 path), combinable */
 hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                         const hsc_svm_model *model, const hsc_knn_params *params,
                         unsigned flags, int32_t *labels, float *out_probs,

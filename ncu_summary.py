@@ -1,8 +1,8 @@
 """Summaries of ncu CSV logs for the profiles folder.
 
-    python -m paper_2404_10631_gb300.ncu_summary launches LOG.csv
+    python ncu_summary.py launches LOG.csv
         per kernel: launches, total time, time per launch, share (markdown)
-    python -m paper_2404_10631_gb300.ncu_summary traffic LOG.csv STAGE_LAUNCHES
+    python ncu_summary.py traffic LOG.csv STAGE_LAUNCHES
         per pipeline stage: DRAM bytes (read + write) per stage launch, as
         "stage source_sha bytes" lines (the format bench.py reads), with
         STAGE_LAUNCHES the number of times each stage ran in the capture
@@ -37,7 +37,7 @@ SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu"), "jacobi": ("k_jacobi.c
 def source_sha(stage: str) -> str:
     h = hashlib.sha256()
     for f in SOURCE_OF[stage]:
-        h.update(open(os.path.join(HERE, "csrc", f), "rb").read())
+        h.update(open(os.path.join(HERE, "paper_2404_10631_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -347,8 +347,9 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
     const hsc::Tuning tu = tuning_for(ctx, B, N, k);
     cudaError_t e;
     {
-        StageTimer t(tc, HSC_STAGE_MOMENTS, hsc::moments_kernel_count(cube, B, N), st);
-        e = moments_with_stall(ctx, cube, B, N, s, st, false, tu.gram_stages);
+        const bool fp32_pipe = (flags & HSC_COV_FP32_PIPE) != 0;
+        StageTimer t(tc, HSC_STAGE_MOMENTS, hsc::moments_kernel_count(cube, B, N, fp32_pipe), st);
+        e = moments_with_stall(ctx, cube, B, N, s, st, fp32_pipe, tu.gram_stages);
     }
     if (e == cudaSuccess) {
         StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);
@@ -920,7 +921,8 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     if ((st = check_model(ctx, model, B))) return st;
     if ((st = check_knn(ctx, params, model->n_classes, H, W))) return st;
     if (!labels) return fail(ctx, HSC_ERR_INVALID_ARG, "labels is NULL%s");
-    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_CLASSIFY_RAW_I | HSC_CUBE_BIP))
+    if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_CLASSIFY_RAW_I | HSC_CUBE_BIP |
+                            HSC_COV_FP32_PIPE))
         return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     const long N = (long)H * W;
     const int k = model->n_classes;

@@ -586,7 +586,6 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
         if (kParts > 1 && part >= 1 && write_sums)
             for (int r = 0; r < kRpt; ++r) bsum_sh[part - 1][b0 + 128 * r] = bsum[r];
     }
-    if (*abort_p && tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
     if (tid == 32 && ncommit > 0) {
         // every MMA must have completed before the accumulator is freed, also
         // after an abort: wait (bounded) for the final commit
@@ -595,6 +594,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
     }
     tc_fence_before();
     __syncthreads();
+    // after the barrier: a role that finished early (the producer) must still
+    // see an abort another role set later
+    if (*abort_p && tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -989,16 +991,16 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     }
-    if (*abort_p && tid == 0) {
-        Control *ctl = frames ? frames[0].ctl : one.ctl;
-        atomicOr(&ctl->status, ST_TIMEOUT);
-    }
     if (tid == 32 && ncommit > 0) {
         for (uint32_t k = 0; k < kWaitLimit; ++k)
             if (mbar_try(&bars.done, (ncommit - 1) & 1)) break;
     }
     tc_fence_before();
     __syncthreads();
+    if (*abort_p && tid == 0) {  // after the barrier, as in gram_tc_kernel
+        Control *ctl = frames ? frames[0].ctl : one.ctl;
+        atomicOr(&ctl->status, ST_TIMEOUT);
+    }
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),

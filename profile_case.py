@@ -1,6 +1,6 @@
 """Repeat one entry point on a synthetic workload, for profilers (ncu).
 
-    python -m paper_2404_10631_gb300.profile_case --op classify --reps 2
+    python profile_case.py --op classify --reps 2
 
 --op: classify | covariance | pca | svm | knn | batch. The first call is a
 warm-up; an ncu capture of the second launch of a kernel uses ``-s 1 -c 1``.
@@ -25,7 +25,7 @@ def main(argv=None):
     ap.add_argument("--search", default="auto", choices=("auto", "full", "pruned", "heap"),
                     help="KNN search of --op knn")
     a = ap.parse_args(argv)
-    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
     import torch
 
     import paper_2404_10631_gb300 as hsc
