@@ -625,6 +625,422 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
                    sum_part + (size_t)blockIdx.x * B);
 }
 
+// ---------------------------------------------------------------- 128 < B <= 256, one read
+
+// The Gram of a 129-256-band frame in ONE launch: every CTA reads each of its
+// chunks once (two {32 pixel, B band} TMA boxes) and converts every band row
+// once, in place: band row b of the two FP32 boxes (pixels 0-31, 32-63) is
+// read by its converter thread, which writes the row's FP16 hi part over the
+// first box and its lo part over the second (the 128-byte-swizzled box rows
+// and the K-major operand rows have the same geometry), so a 64 KB stage is
+// first the TMA destination, then the MMA operands (three stages in flight).
+// The upper triangle of G is three 128-column blocks: G00 (bands 0-127 x
+// 0-127), G01 (0-127 x 128-B) and G11 (128-B x 128-B), each accumulating
+// hi.hi^T + hi.lo^T + lo.hi^T (M = 128, N = 128 or B - 128 rounded up to 16)
+// in one FP32 TMEM block. The four 128-column TMEM slots hold the three
+// blocks and a spare: every kWideFlushEvery chunks one block (round robin)
+// moves to the spare slot and its old slot is drained by four epilogue
+// warps (one per TMEM lane quarter) into the CTA's partial Gram while the
+// MMAs go on, so no block takes more than 3 kWideFlushEvery chunks of
+// additions (the tensor cores' FP32 accumulation error grows with them) and
+// the drains never stall the tensor pipe.
+constexpr int kWideStages = 3;
+constexpr int kWideConvWarps = 8;                       // one thread per band row (256 rows)
+constexpr int kWideEpiWarps = 4;                        // one per TMEM lane quarter
+constexpr int kWideThreads = 64 + 32 * (kWideConvWarps + kWideEpiWarps);  // 448
+constexpr uint32_t kWideBoxBytes = 256u * 128u;         // one 32-pixel box slot (256 rows)
+constexpr uint32_t kWideStageBytes = 2u * kWideBoxBytes;  // FP32 boxes, then hi | lo operands
+constexpr size_t kWideSmem = 1024 + (size_t)kWideStages * kWideStageBytes;
+constexpr int kWideFlushEvery = 4;                      // chunks between two block drains
+
+// One block of the wide Gram: its first band row (TMEM lane 0), first column
+// and column count.
+__device__ __forceinline__ void wide_block(int j, int Np, int &row0, int &col0, int &ncol)
+{
+    row0 = j == 2 ? 128 : 0;
+    col0 = j == 0 ? 0 : 128;
+    ncol = j == 0 ? 128 : Np - 128;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ float ld_hint(const float *p, uint64_t pol)
+{
+    float v;
+    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void st_hint(float *p, float v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol)
+                 : "memory");
+}
+
+// The cube's boxes with an L2 policy: read once, evicted first, so that the
+// partial Grams the drains read back stay in L2.
+__device__ __forceinline__ void tma_load_2d_hint(void *dst, const CUtensorMap *map, int x, int y,
+                                                 uint64_t *bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+// Epilogue warp: TMEM slot `slot` holding block j (this warp's lane quarter
+// q) added into (written = true) or written to (false) the partial Gram out,
+// entry (b, c) at c * B + b for c >= b, the band scales removed; 32 columns
+// at a time (32 loads of the earlier sums in flight per lane), the partial
+// Gram kept in L2 (evict-last policy).
+__device__ __forceinline__ void wide_drain(uint32_t tmem, int q, int lane, int j, int slot,
+                                           bool written, int B, int Np, const float *isc,
+                                           float *__restrict__ out, uint64_t pol)
+{
+    int row0, col0, ncol;
+    wide_block(j, Np, row0, col0, ncol);
+    const int mlo = row0 + q * 32;
+    const int m = mlo + lane;
+    const float isc_m = m < B ? isc[m] : 0.f;
+    const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)slot * 128u;
+    for (int c0 = 0; c0 < ncol; c0 += 32) {
+        if (col0 + c0 + 31 < mlo) continue;  // below the diagonal for the whole warp
+        float v[32];
+        if (c0 + 32 <= ncol) {
+            tmem_ld32(base + (uint32_t)c0, v);
+        } else {  // ncol is a multiple of 16
+            tmem_ld16(base + (uint32_t)c0, v);
+#pragma unroll
+            for (int e = 16; e < 32; ++e) v[e] = 0.f;
+        }
+        if (m < B) {
+            // entry (m, col0 + c0 + e) at base_p + e * B
+            float *base_p = out + (size_t)(col0 + c0) * B + m;
+            const int lim = min(min(ncol - c0, B - (col0 + c0)), 32);  // columns in range
+            const int first = max(0, m - (col0 + c0));                  // columns >= m from here
+            float prev[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                prev[e] = (written && e < lim && e >= first) ? ld_hint(base_p + e * B, pol) : 0.f;
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                if (e < lim && e >= first)
+                    st_hint(base_p + e * B, prev[e] + v[e] * (isc_m * isc[col0 + c0 + e]), pol);
+        }
+    }
+}
+
+// Band rows 0..B-1 of chunks [blockIdx.x * per, ...) of the cube; shift: 2B
+// floats (pilot shift s_b, then the power-of-two scale c_b per band). Np = B
+// rounded up to 16 (129 <= B <= 256).
+__global__ void __launch_bounds__(kWideThreads, 1)
+gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ cube,
+                    int B, int Np, long N, long total_chunks, long per,
+                    const float *__restrict__ shift, float *__restrict__ gram_part,
+                    float *__restrict__ sum_part, Control *ctl)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *stages = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kWideStages], conv[kWideStages], empty[kWideStages];
+    __shared__ __align__(8) uint64_t flush_bar, drained_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag, range_flag, stall_flag;
+    __shared__ float sh[256], sc[256], isc[256];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long c_begin = (long)blockIdx.x * per;
+    long c_end = c_begin + per;
+    if (c_end > total_chunks) c_end = total_chunks;
+    const int nchunks = c_end > c_begin ? (int)(c_end - c_begin) : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kWideStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], kWideConvWarps);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&flush_bar, 1);
+        mbar_init(&drained_bar, kWideEpiWarps);
+        abort_flag = 0;
+        range_flag = 0;
+        stall_flag = ctl->test_stall != 0u ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int r = tid; r < 256; r += kWideThreads) {
+        sh[r] = r < B ? shift[r] : 0.f;
+        sc[r] = r < B ? shift[B + r] : 1.f;
+        isc[r] = __frcp_rn(sc[r]);  // exact: a power of two
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    volatile int *abort_p = &abort_flag;
+    const bool stall = stall_flag != 0;  // testing aid, as in gram_tc_kernel
+    const uint32_t wl = stall ? kTestWaitLimit : kWaitLimit;
+    // flush events: before chunks kWideFlushEvery, 2 kWideFlushEvery, ... < nchunks
+    const int n_ev = nchunks > 0 ? (nchunks - 1) / kWideFlushEvery : 0;
+    int ncommit = 0;  // commits to flush_bar by the MMA issuer
+    const int cv = tid - 64;  // converter thread: band row cv
+    float bsum = 0.f;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            const uint64_t pol = l2_policy_evict_first();
+            int issued = 0;
+            for (int i = 0; i < nchunks && !*abort_p && !stall; ++i) {
+                const int s = i % kWideStages;
+                if (i >= kWideStages &&
+                    !mbar_wait(&empty[s], ((i / kWideStages) - 1) & 1, abort_p))
+                    break;
+                mbar_arrive_tx(&full[s], 2u * kBoxPx * (uint32_t)B * 4u);
+                const int x = (int)((c_begin + i) * kChunk);
+                unsigned char *dst = stages + (size_t)s * kWideStageBytes;
+                tma_load_2d_hint(dst, &tmap, x, 0, &full[s], pol);
+                tma_load_2d_hint(dst + kWideBoxBytes, &tmap, x + kBoxPx, 0, &full[s], pol);
+                ++issued;
+            }
+            // never leave with copies in flight: wait (bounded) for the last ones
+            for (int i = issued - kWideStages; i < issued; ++i) {
+                if (i < 0) continue;
+                const int s = i % kWideStages;
+                for (uint32_t k = 0; k < kWaitLimit; ++k)
+                    if (mbar_try(&full[s], (i / kWideStages) & 1)) break;
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0 && nchunks > 0) {
+            const uint32_t id128 = (1u << 4) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            const uint32_t idN = (1u << 4) | ((uint32_t)((Np - 128) >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
+            // TMEM slot of block j in bits 2j..2j+1 (registers, no local memory)
+            uint32_t slots = 0u | (1u << 2) | (2u << 4), spare = 3u;
+            uint32_t fresh = 7u;  // bit j: block j's next MMA starts its accumulator
+            int ev = 0;
+            bool ok = true;
+            for (int i = 0; i < nchunks && ok; ++i) {
+                if (i > 0 && i % kWideFlushEvery == 0) {
+                    // the spare slot was drained (previous event) before the
+                    // next block moves into it; then the MMAs so far are
+                    // committed and the block's old slot handed to the epilogue
+                    if (ev > 0 && !mbar_wait(&drained_bar, (ev - 1) & 1, abort_p)) break;
+                    tc_fence_after();
+                    mma_commit(&flush_bar);
+                    ++ncommit;
+                    const int j = ev % 3;
+                    const uint32_t old = (slots >> (2 * j)) & 3u;
+                    slots = (slots & ~(3u << (2 * j))) | (spare << (2 * j));
+                    spare = old;
+                    fresh |= 1u << j;
+                    ++ev;
+                }
+                const int s = i % kWideStages;
+                if (!mbar_wait(&conv[s], (i / kWideStages) & 1, abort_p, wl)) break;
+                tc_fence_after();
+                const uint32_t hi = smem_u32(stages + (size_t)s * kWideStageBytes);
+                const uint32_t lo = hi + kWideBoxBytes;
+                const uint64_t h0 = smem_desc(hi), l0 = smem_desc(lo);
+                const uint64_t h1 = smem_desc(hi + 128u * 128u), l1 = smem_desc(lo + 128u * 128u);
+#pragma unroll
+                for (int k = 0; k < kChunk / 16; ++k) {
+                    const uint64_t off = (uint64_t)((k * 32) >> 4);  // 16 fp16 = 32 bytes along K
+                    const uint32_t d0 = tmem + (slots & 3u) * 128u;
+                    const uint32_t d1 = tmem + ((slots >> 2) & 3u) * 128u;
+                    const uint32_t d2 = tmem + ((slots >> 4) & 3u) * 128u;
+                    // G00: rows 0-127 x columns 0-127
+                    mma_f16(d0, h0 + off, h0 + off, id128, ((fresh & 1u) && k == 0) ? 0u : 1u);
+                    mma_f16(d0, h0 + off, l0 + off, id128, 1u);
+                    mma_f16(d0, l0 + off, h0 + off, id128, 1u);
+                    // G01: rows 0-127 x columns 128..Np-1
+                    mma_f16(d1, h0 + off, h1 + off, idN, ((fresh & 2u) && k == 0) ? 0u : 1u);
+                    mma_f16(d1, h0 + off, l1 + off, idN, 1u);
+                    mma_f16(d1, l0 + off, h1 + off, idN, 1u);
+                    // G11: rows 128..255 x columns 128..Np-1
+                    mma_f16(d2, h1 + off, h1 + off, idN, ((fresh & 4u) && k == 0) ? 0u : 1u);
+                    mma_f16(d2, h1 + off, l1 + off, idN, 1u);
+                    mma_f16(d2, l1 + off, h1 + off, idN, 1u);
+                }
+                fresh = 0u;
+                mma_commit(&empty[s]);
+            }
+            // the final drain of all three blocks: after the last event's drain
+            if (ev > 0) mbar_wait(&drained_bar, (ev - 1) & 1, abort_p);
+            tc_fence_after();
+            mma_commit(&flush_bar);  // arrives when every MMA issued above has completed
+            ++ncommit;
+        }
+    } else if (warp < 2 + kWideConvWarps) {
+        // ---------------- converters: band row cv of every chunk, in place
+        const int b = cv;
+        const int sw = b & 7;
+        if (b >= B) {  // rows past B stay zero in every stage (TMA writes rows < B only)
+            for (int s = 0; s < kWideStages; ++s)
+                for (int u = 0; u < 8; ++u) {
+                    unsigned char *r0 = stages + (size_t)s * kWideStageBytes + (size_t)b * 128;
+                    *reinterpret_cast<uint4 *>(r0 + (u << 4)) = make_uint4(0, 0, 0, 0);
+                    *reinterpret_cast<uint4 *>(r0 + kWideBoxBytes + (u << 4)) = make_uint4(0, 0, 0, 0);
+                }
+        }
+        const float c = b < B ? sc[b] : 1.f, nsc = b < B ? -sh[b] * c : 0.f;
+        float ymax = 0.f;
+        for (int i = 0; i < nchunks; ++i) {
+            const int s = i % kWideStages;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (i / kWideStages) & 1, abort_p, wl)))
+                break;
+            if (b < B) {
+                unsigned char *r0 = stages + (size_t)s * kWideStageBytes + (size_t)b * 128;
+                unsigned char *r1 = r0 + kWideBoxBytes;
+                const long px0 = (c_begin + i) * kChunk;
+                const int lim = px0 + kChunk > N ? (int)(N - px0) : kChunk;
+                // pixels 32-63 (the second box) into registers first: the lo parts
+                // of pixels 0-31 overwrite them. Then unit v (pixels 8v..8v+7):
+                // for v < 4 from the first box's 16-byte units 2v and 2v + 1,
+                // which its hi part (written at unit v <= 2v) no longer needs
+                float x1[32];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float4 d = *reinterpret_cast<const float4 *>(r1 + ((u ^ sw) << 4));
+                    x1[4 * u] = d.x;
+                    x1[4 * u + 1] = d.y;
+                    x1[4 * u + 2] = d.z;
+                    x1[4 * u + 3] = d.w;
+                }
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {  // 8-pixel fp16 units of the operand rows
+                    float x[8];
+                    if (v < 4) {
+                        const float4 a0 = *reinterpret_cast<const float4 *>(r0 + (((2 * v) ^ sw) << 4));
+                        const float4 a1 = *reinterpret_cast<const float4 *>(r0 + (((2 * v + 1) ^ sw) << 4));
+                        x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
+                        x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[e] = x1[8 * (v - 4) + e];
+                    }
+                    float h[8], l[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        float y = fmaf(x[e], c, nsc);
+                        if (8 * v + e >= lim) y = 0.f;
+                        ymax = fmaxf(ymax, fabsf(y));
+                        bsum += y;
+                        const float t = __fmul_rn(y, 8193.f);
+                        h[e] = __fsub_rn(t, __fsub_rn(t, y));
+                        l[e] = __fsub_rn(y, h[e]);
+                    }
+                    *reinterpret_cast<uint4 *>(r0 + ((v ^ sw) << 4)) =
+                        make_uint4(pack_half2(h[0], h[1]), pack_half2(h[2], h[3]),
+                                   pack_half2(h[4], h[5]), pack_half2(h[6], h[7]));
+                    *reinterpret_cast<uint4 *>(r1 + ((v ^ sw) << 4)) =
+                        make_uint4(pack_half2(l[0], l[1]), pack_half2(l[2], l[3]),
+                                   pack_half2(l[4], l[5]), pack_half2(l[6], l[7]));
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&conv[s]);
+        }
+        if (b < B && !isfinite(bsum)) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+        if (!(ymax < kFp16Max)) range_flag = 1;
+    } else {
+        // ---------------- epilogue: drains, one block per flush event, then all three
+        const int q = warp & 3;  // the TMEM lane quarter this warp may read
+        float *out = gram_part + (size_t)blockIdx.x * B * B;
+        const uint64_t pol = l2_policy_evict_last();
+        uint32_t slots = 0u | (1u << 2) | (2u << 4), spare = 3u;  // as the issuer's
+        uint32_t written = 0u;  // bit j: block j's entries hold an earlier drain
+        bool ok = true;
+        for (int e = 0; e < n_ev && ok; ++e) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&flush_bar, e & 1, abort_p));
+            if (!ok) break;
+            tc_fence_after();
+            const int j = e % 3;
+            const uint32_t old = (slots >> (2 * j)) & 3u;
+            wide_drain(tmem, q, lane, j, (int)old, (written >> j) & 1u, B, Np, isc, out, pol);
+            written |= 1u << j;
+            slots = (slots & ~(3u << (2 * j))) | (spare << (2 * j));
+            spare = old;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&drained_bar);
+        }
+        if (ok && nchunks > 0 && __all_sync(0xffffffffu, mbar_wait(&flush_bar, n_ev & 1, abort_p))) {
+            tc_fence_after();
+            for (int j = 0; j < 3; ++j)
+                wide_drain(tmem, q, lane, j, (int)((slots >> (2 * j)) & 3u), (written >> j) & 1u,
+                           B, Np, isc, out, pol);
+        }
+    }
+    if (tid == 32 && ncommit > 0) {
+        // every MMA must have completed before the accumulators are freed,
+        // also after an abort: wait (bounded) for the final commit
+        for (uint32_t k = 0; k < kWaitLimit; ++k)
+            if (mbar_try(&flush_bar, (ncommit - 1) & 1)) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_p && tid == 0) atomicOr(&ctl->status, ST_TIMEOUT);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+    if (warp >= 2 && warp < 2 + kWideConvWarps && cv < B)
+        sum_part[(size_t)blockIdx.x * B + cv] = bsum * isc[cv];
+    if (!range_flag || *abort_p || nchunks == 0) return;
+
+    // ---------------- FP32 recompute of this CTA's partial (rare), over the
+    // CTA's pixels (which L2 still holds), staged in the stage memory
+    __syncthreads();
+    const long p_end = c_end * kChunk < N ? c_end * kChunk : N;
+    float *ys = reinterpret_cast<float *>(stages);
+    fp32_recompute(cube, B, N, sh, 0, 0, Np, 1, c_begin * kChunk, p_end, ys,
+                   gram_part + (size_t)blockIdx.x * B * B, sum_part + (size_t)blockIdx.x * B);
+    fp32_recompute(cube, B, N, sh, 128, 128, Np - 128, 0, c_begin * kChunk, p_end, ys,
+                   gram_part + (size_t)blockIdx.x * B * B, sum_part + (size_t)blockIdx.x * B);
+}
+
 // ---------------------------------------------------------------- work items
 
 // L2 policy for the cube's chunks: read once, evicted first, so that the
@@ -1146,15 +1562,11 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
         else launch_narrow<4>(map, cube, B, Np, N, total, per, parts, s, st);
         return cudaGetLastError();
     }
-    const size_t smem = Cfg<true>::kSmem;
-    cudaFuncSetAttribute(gram_tc_kernel<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    // rows 0-127 x every column, then rows 128-255 x columns 128-255
-    gram_tc_kernel<true, 2><<<parts, Cfg<true>::kThreads, smem, st>>>(
-        map, cube, B, 0, 0, Np, 1, N, total, per, s.shift, s.gram_part, s.sum_part, s.ctl);
-    gram_tc_kernel<true, 2><<<parts, Cfg<true>::kThreads, smem, st>>>(
-        map, cube, B, 128, 128, Np - 128, 0, N, total, per, s.shift, s.gram_part, s.sum_part,
-        s.ctl);
+    // 128 < B <= 256: one launch, each chunk read and converted once
+    cudaFuncSetAttribute(gram_tc_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kWideSmem);
+    gram_tc_wide_kernel<<<parts, kWideThreads, kWideSmem, st>>>(
+        map, cube, B, Np, N, total, per, s.shift, s.gram_part, s.sum_part, s.ctl);
     return cudaGetLastError();
 }
 

@@ -468,11 +468,10 @@ static cudaError_t launch_reductions(int B, long N, int n_part, const PcaScratch
     return cudaGetLastError();
 }
 
-// Kernels launch_moments issues: the pilot, the Gram (two launches for
-// 128 < B <= 256 on the tensor cores), the reduction.
+// Kernels launch_moments issues: the pilot, the Gram, the reduction.
 int moments_kernel_count(const float *cube, int B, long N, bool force_simt)
 {
-    if (!force_simt && gram_tc_usable(cube, B, N)) return B > 128 ? 4 : 3;
+    if (!force_simt && gram_tc_usable(cube, B, N)) return 3;
     return 3;
 }
 

@@ -22,6 +22,10 @@ def main(argv=None):
                     choices=("classify", "covariance", "pca", "svm", "knn", "batch"))
     ap.add_argument("--config", type=int, default=2, help="synthetic workload (1 tiny, 2 neuro)")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--shape", default=None,
+                    help="B,H,W: a frame of the 1024x1024x256 workload's generator (two wide "
+                         "Gaussians per class spectrum, sigma 0.01) at this size instead of "
+                         "--config")
     ap.add_argument("--search", default="auto", choices=("auto", "full", "pruned", "heap"),
                     help="KNN search of --op knn")
     a = ap.parse_args(argv)
@@ -45,7 +49,12 @@ def main(argv=None):
         ctx.sync()
         print("ok batch: %d frames, %d calls" % (len(frames), 2 * a.reps))
         return
-    f = synth.make_config(a.config)
+    if a.shape:
+        B, H, W = (int(v) for v in a.shape.split(","))
+        f = synth.make_frame(synth.SEEDS[4], H, W, B, sigma=0.01, n_seeds=32, n_gauss=2,
+                             wide=True, K=40, window_rows=14, lam=1.0)
+    else:
+        f = synth.make_config(a.config)
     ctx = hsc.Context(0)
     cube = torch.as_tensor(f.cube, device="cuda")
     model = hsc.Model.from_host(f.model)
