@@ -50,8 +50,13 @@ namespace {
 constexpr int kChunk = 64;               // pixels per chunk (one 128-byte fp16 row)
 constexpr int kBoxPx = 32;               // pixels per TMA box (128 bytes of fp32)
 constexpr int kM = 128;                  // MMA M (bands of one half, zero padded)
-constexpr uint32_t kWaitLimit = 1u << 22;
-constexpr uint32_t kTestWaitLimit = 1u << 10;  // the wait bound while Control::test_stall is set
+// mbarrier waits: each try suspends the thread until the phase completes or
+// kSuspendNs pass (so waiting warps take no issue slots or shared-memory
+// bandwidth from the others), and gives up after kWaitLimit tries (about
+// 2.6 s; kTestWaitLimit, about 1.3 ms, while Control::test_stall is set)
+constexpr uint32_t kSuspendNs = 10000;
+constexpr uint32_t kWaitLimit = 1u << 18;
+constexpr uint32_t kTestWaitLimit = 1u << 7;
 constexpr uint32_t kTmemCols = 512;
 constexpr float kFp16Max = 65504.f;
 constexpr int kFbAcc = 8;                // FP32 recompute: entries per thread per pass
@@ -118,10 +123,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -145,6 +150,17 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One box of a 3-D tensor map (coordinates innermost first).
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -372,14 +388,21 @@ __device__ void fp32_recompute(const float *__restrict__ cube, int B, long N,
 // col_base..col_base+Nn-1 (Nn a multiple of 16); band sums when write_sums.
 // shift: 2B floats, the pilot shift s_b then the scale c_b of each band.
 // CTA i takes chunks [i * per, (i + 1) * per).
-template <bool kWide, int kSt>
-__global__ void __launch_bounds__(Cfg<kWide, kSt>::kThreads, 1)
+// k3D: the tensor map is the 3-D view {32 pixels, N / 32 groups, B bands}
+// (N % 32 == 0) and each chunk is ONE box {32, 2, B}: a band's 64 pixels
+// (256 contiguous bytes) are fetched together, which streams at nearly the
+// HBM copy rate, where two {32, B} boxes per chunk (the 2-D map, any N % 4
+// == 0) fetch 128-byte rows 256 rows apart and reach about 70% of it. The
+// staging layout differs (band b's two 32-pixel rows at 128-byte rows 2b
+// and 2b + 1, against b and kRows + b); the arithmetic does not.
+template <bool k3D, int kSt>
+__global__ void __launch_bounds__(Cfg<false, kSt>::kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ cube, int B,
                int row_base, int col_base, int Nn, int write_sums, long N, long total_chunks,
                long per, const float *__restrict__ shift, float *__restrict__ gram_part,
                float *__restrict__ sum_part, Control *ctl)
 {
-    using G = Cfg<kWide, kSt>;
+    using G = Cfg<false, kSt>;
     constexpr int kRows = G::kRows, kStages = G::kStages, kOpStages = G::kOpStages;
     constexpr int kAccHH = G::kAccHH, kThreads = G::kThreads, kParts = G::kParts;
     constexpr uint32_t kBoxBytes = G::kBoxBytes, kStageBytes = G::kStageBytes;
@@ -389,7 +412,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *staging = base;                                 // kStages x 2 boxes
     unsigned char *ops = base + kStages * kStageBytes;             // kOpStages x (hi, lo)
-    __shared__ Bars<kWide, kSt> bars;
+    __shared__ Bars<false, kSt> bars;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, range_flag, stall_flag;
     __shared__ float sh[kRows], sc[kRows], isc[kRows];
@@ -443,8 +466,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
     // converter state, kept past the final barrier for the band sums
     constexpr int kRpt = kRows / 128;      // band rows per converter thread
     const int cv = tid - 64;               // converter index
-    const int b0 = cv & 127;               // its first band row
-    const int part = cv >> 7;              // which 32-pixel box of a chunk it converts
+    // band row and 32-pixel half of a chunk: the two halves of a band on
+    // adjacent lanes, so a warp's 16-byte staging reads and operand writes
+    // spread over every bank in either staging layout
+    const int b0 = cv >> 1;
+    const int part = cv & 1;
     float bsum[kRpt];
 #pragma unroll
     for (int r = 0; r < kRpt; ++r) bsum[r] = 0.f;
@@ -458,10 +484,15 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
                 if (i >= kStages && !mbar_wait(&bars.empty[s], ((i / kStages) - 1) & 1, abort_p))
                     break;
                 mbar_arrive_tx(&bars.full[s], 2u * kBoxPx * (uint32_t)B * 4u);
-                const int x = (int)((c_begin + i) * kChunk);
-                tma_load_2d(staging + s * kStageBytes, &tmap, x, 0, &bars.full[s]);
-                tma_load_2d(staging + s * kStageBytes + kBoxBytes, &tmap, x + kBoxPx, 0,
-                            &bars.full[s]);
+                if (k3D) {
+                    tma_load_3d(staging + s * kStageBytes, &tmap, 0, (int)((c_begin + i) * 2), 0,
+                                &bars.full[s]);
+                } else {
+                    const int x = (int)((c_begin + i) * kChunk);
+                    tma_load_2d(staging + s * kStageBytes, &tmap, x, 0, &bars.full[s]);
+                    tma_load_2d(staging + s * kStageBytes + kBoxBytes, &tmap, x + kBoxPx, 0,
+                                &bars.full[s]);
+                }
                 ++issued;
             }
             // never leave with copies in flight: wait (bounded) for the last ones
@@ -551,14 +582,17 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
                 const unsigned char *st = staging + s * kStageBytes;
                 unsigned char *ohi = ops + t * 2 * kOpBytes + b * 128;
                 unsigned char *olo = ohi + kOpBytes;
+                // this thread's 32-pixel half (u >> 2 == part for all its units):
+                // its 128-byte staging row
+                const int srow = k3D ? 2 * b + part : part * kRows + b;
+                const int ssw = srow & 7;
+                const unsigned char *row = st + srow * 128;
 #pragma unroll
                 for (int uu = 0; uu < kUnits; ++uu) {
                     const int u = u0 + uu;
-                    const int box = u >> 2;
                     const int j0 = (u & 3) * 2;  // 16-byte units (4 px) within the box row
-                    const unsigned char *row = st + box * kBoxBytes + b * 128;
-                    const float4 xa = *reinterpret_cast<const float4 *>(row + ((j0 ^ sw) << 4));
-                    const float4 xb = *reinterpret_cast<const float4 *>(row + (((j0 + 1) ^ sw) << 4));
+                    const float4 xa = *reinterpret_cast<const float4 *>(row + ((j0 ^ ssw) << 4));
+                    const float4 xb = *reinterpret_cast<const float4 *>(row + (((j0 + 1) ^ ssw) << 4));
                     uint4 hv, lv;
                     if (tail)
                         convert_unit<true>(xa, xb, c, nsc, u, lim, bsum[r], ymax, hv, lv);
@@ -653,6 +687,52 @@ constexpr uint32_t kWideStageBytes = 2u * kWideBoxBytes;  // FP32 boxes, then hi
 constexpr size_t kWideSmem = 1024 + (size_t)kWideStages * kWideStageBytes;
 constexpr int kWideFlushEvery = 4;                      // chunks between two block drains
 
+// The in-place conversion of one converter thread's two half rows (pixels
+// 32h..32h+31 of bands bA and bB, in registers xa, xb) into the operand
+// rows: y = c (x - s) with one FMA (c a power of two), hi = y rounded to 11
+// significant bits by rounding its FP32 bit pattern (add half a unit of the
+// 12th bit, clear the 13 bits below: two integer operations, exact in FP16),
+// lo = y - hi exactly (then rounded to FP16), band sums of y. A scaled value
+// beyond FP16's range becomes an infinite hi, which the drains see as a
+// non-finite accumulator. kTail: pixels at or past lim are zero.
+template <bool kTail>
+__device__ __forceinline__ void wide_convert(unsigned char *st, int h, int bA, int bB, int B,
+                                             float cA, float nA, float cB, float nB, int lim,
+                                             const float (&xa)[32], const float (&xb)[32],
+                                             float &sA, float &sB)
+{
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int b = k ? bB : bA;
+        const float c = k ? cB : cA, nsc = k ? nB : nA;
+        unsigned char *ohi = st + b * 128, *olo = st + kWideBoxBytes + b * 128;
+        const int sw = b & 7;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {  // the 8-pixel fp16 units 4h + v of row b
+            uint4 hv = make_uint4(0, 0, 0, 0), lv = make_uint4(0, 0, 0, 0);
+            if (b < B) {
+                float hh[8], ll[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float xv = k ? xb[8 * v + e] : xa[8 * v + e];
+                    float y = fmaf(xv, c, nsc);
+                    if (kTail && 32 * h + 8 * v + e >= lim) y = 0.f;
+                    if (k) sB += y;
+                    else sA += y;
+                    hh[e] = __uint_as_float((__float_as_uint(y) + 0x1000u) & 0xFFFFE000u);
+                    ll[e] = __fsub_rn(y, hh[e]);
+                }
+                hv = make_uint4(pack_half2(hh[0], hh[1]), pack_half2(hh[2], hh[3]),
+                                pack_half2(hh[4], hh[5]), pack_half2(hh[6], hh[7]));
+                lv = make_uint4(pack_half2(ll[0], ll[1]), pack_half2(ll[2], ll[3]),
+                                pack_half2(ll[4], ll[5]), pack_half2(ll[6], ll[7]));
+            }
+            *reinterpret_cast<uint4 *>(ohi + (((4 * h + v) ^ sw) << 4)) = hv;
+            *reinterpret_cast<uint4 *>(olo + (((4 * h + v) ^ sw) << 4)) = lv;
+        }
+    }
+}
+
 // One block of the wide Gram: its first band row (TMEM lane 0), first column
 // and column count.
 __device__ __forceinline__ void wide_block(int j, int Np, int &row0, int &col0, int &ncol)
@@ -660,24 +740,6 @@ __device__ __forceinline__ void wide_block(int j, int Np, int &row0, int &col0, 
     row0 = j == 2 ? 128 : 0;
     col0 = j == 0 ? 0 : 128;
     ncol = j == 0 ? 128 : Np - 128;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint64_t l2_policy_evict_last()
@@ -707,58 +769,73 @@ __device__ __forceinline__ void st_hint(float *p, float v, uint64_t pol)
                  : "memory");
 }
 
-// The cube's boxes with an L2 policy: read once, evicted first, so that the
-// partial Grams the drains read back stay in L2.
-__device__ __forceinline__ void tma_load_2d_hint(void *dst, const CUtensorMap *map, int x, int y,
-                                                 uint64_t *bar, uint64_t pol)
+// A box of the cube's 3-D map with an L2 policy: read once, evicted first,
+// so that the partial Grams the drains read back stay in L2.
+__device__ __forceinline__ void tma_load_3d_hint(void *dst, const CUtensorMap *map, int x, int y,
+                                                 int z, uint64_t *bar, uint64_t pol)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(pol)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)),
+        "l"(pol)
         : "memory");
+}
+
+// Named barrier 1 of the converter warps (nthreads threads) that also ORs a
+// predicate over them.
+__device__ __forceinline__ bool conv_bar_or1(int nthreads, bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 // Epilogue warp: TMEM slot `slot` holding block j (this warp's lane quarter
 // q) added into (written = true) or written to (false) the partial Gram out,
-// entry (b, c) at c * B + b for c >= b, the band scales removed; 32 columns
-// at a time (32 loads of the earlier sums in flight per lane), the partial
-// Gram kept in L2 (evict-last policy).
+// entry (b, c) at c * B + b for c >= b, the band scales removed; 16 columns
+// at a time, the partial Gram kept in L2 (evict-last policy).
 __device__ __forceinline__ void wide_drain(uint32_t tmem, int q, int lane, int j, int slot,
                                            bool written, int B, int Np, const float *isc,
-                                           float *__restrict__ out, uint64_t pol)
+                                           float *__restrict__ out, uint64_t pol,
+                                           int *range_flag)
 {
+    bool bad = false;
     int row0, col0, ncol;
     wide_block(j, Np, row0, col0, ncol);
     const int mlo = row0 + q * 32;
     const int m = mlo + lane;
     const float isc_m = m < B ? isc[m] : 0.f;
     const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)slot * 128u;
-    for (int c0 = 0; c0 < ncol; c0 += 32) {
-        if (col0 + c0 + 31 < mlo) continue;  // below the diagonal for the whole warp
-        float v[32];
-        if (c0 + 32 <= ncol) {
-            tmem_ld32(base + (uint32_t)c0, v);
-        } else {  // ncol is a multiple of 16
-            tmem_ld16(base + (uint32_t)c0, v);
+    for (int c0 = 0; c0 < ncol; c0 += 16) {
+        if (col0 + c0 + 15 < mlo) continue;  // below the diagonal for the whole warp
+        float v[16];
+        tmem_ld16(base + (uint32_t)c0, v);
 #pragma unroll
-            for (int e = 16; e < 32; ++e) v[e] = 0.f;
-        }
+        for (int e = 0; e < 16; ++e) bad |= !isfinite(v[e]);
         if (m < B) {
             // entry (m, col0 + c0 + e) at base_p + e * B
             float *base_p = out + (size_t)(col0 + c0) * B + m;
-            const int lim = min(min(ncol - c0, B - (col0 + c0)), 32);  // columns in range
-            const int first = max(0, m - (col0 + c0));                  // columns >= m from here
-            float prev[32];
+            const int lim = min(B - (col0 + c0), 16);       // columns in range (ncol % 16 == 0)
+            const int first = max(0, m - (col0 + c0));      // columns >= m from here
+            float prev[16];
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
+            for (int e = 0; e < 16; ++e)
                 prev[e] = (written && e < lim && e >= first) ? ld_hint(base_p + e * B, pol) : 0.f;
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
+            for (int e = 0; e < 16; ++e)
                 if (e < lim && e >= first)
                     st_hint(base_p + e * B, prev[e] + v[e] * (isc_m * isc[col0 + c0 + e]), pol);
         }
     }
+    // a scaled value beyond FP16's range (an infinite hi part) or a NaN in
+    // the cube: the CTA recomputes its partial on the FP32 pipe
+    if (bad) *range_flag = 1;
 }
 
 // Band rows 0..B-1 of chunks [blockIdx.x * per, ...) of the cube; shift: 2B
@@ -820,8 +897,8 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
     // flush events: before chunks kWideFlushEvery, 2 kWideFlushEvery, ... < nchunks
     const int n_ev = nchunks > 0 ? (nchunks - 1) / kWideFlushEvery : 0;
     int ncommit = 0;  // commits to flush_bar by the MMA issuer
-    const int cv = tid - 64;  // converter thread: band row cv
-    float bsum = 0.f;
+    const int cv = tid - 64;  // converter thread index
+    float bsum = 0.f, bsum2 = 0.f;  // band sums of bands cv / 2 and 128 + cv / 2 (even cv)
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -834,10 +911,8 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
                     !mbar_wait(&empty[s], ((i / kWideStages) - 1) & 1, abort_p))
                     break;
                 mbar_arrive_tx(&full[s], 2u * kBoxPx * (uint32_t)B * 4u);
-                const int x = (int)((c_begin + i) * kChunk);
-                unsigned char *dst = stages + (size_t)s * kWideStageBytes;
-                tma_load_2d_hint(dst, &tmap, x, 0, &full[s], pol);
-                tma_load_2d_hint(dst + kWideBoxBytes, &tmap, x + kBoxPx, 0, &full[s], pol);
+                tma_load_3d_hint(stages + (size_t)s * kWideStageBytes, &tmap, 0,
+                                 (int)((c_begin + i) * 2), 0, &full[s], pol);
                 ++issued;
             }
             // never leave with copies in flight: wait (bounded) for the last ones
@@ -910,78 +985,62 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
             ++ncommit;
         }
     } else if (warp < 2 + kWideConvWarps) {
-        // ---------------- converters: band row cv of every chunk, in place
-        const int b = cv;
-        const int sw = b & 7;
-        if (b >= B) {  // rows past B stay zero in every stage (TMA writes rows < B only)
-            for (int s = 0; s < kWideStages; ++s)
-                for (int u = 0; u < 8; ++u) {
-                    unsigned char *r0 = stages + (size_t)s * kWideStageBytes + (size_t)b * 128;
-                    *reinterpret_cast<uint4 *>(r0 + (u << 4)) = make_uint4(0, 0, 0, 0);
-                    *reinterpret_cast<uint4 *>(r0 + kWideBoxBytes + (u << 4)) = make_uint4(0, 0, 0, 0);
-                }
-        }
-        const float c = b < B ? sc[b] : 1.f, nsc = b < B ? -sh[b] * c : 0.f;
-        float ymax = 0.f;
+        // ---------------- converters, in place. The stage holds the chunk as
+        // 128-byte rows r = 2 band + half (pixels 32 half .. 32 half + 31),
+        // the operands as hi rows b at b * 128 and lo rows at 32 KB + b * 128:
+        // a band's operand rows overwrite other bands' pixels, so every
+        // converter reads its rows, then all meet at a barrier, then write.
+        // Thread t reads rows t and t + 256: band bA = t / 2 and band
+        // bB = 128 + t / 2, half h = t % 2.
+        const int t = cv;
+        const int h = t & 1;
+        const int bA = t >> 1, bB = 128 + (t >> 1);
+        const float cA = bA < B ? sc[bA] : 1.f, nA = bA < B ? -sh[bA] * cA : 0.f;
+        const float cB = bB < B ? sc[bB] : 1.f, nB = bB < B ? -sh[bB] * cB : 0.f;
+        const int ph = t & 7;  // swizzle phase of rows t and t + 256
+        float sA = 0.f, sB = 0.f;
         for (int i = 0; i < nchunks; ++i) {
             const int s = i % kWideStages;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[s], (i / kWideStages) & 1, abort_p, wl)))
-                break;
-            if (b < B) {
-                unsigned char *r0 = stages + (size_t)s * kWideStageBytes + (size_t)b * 128;
-                unsigned char *r1 = r0 + kWideBoxBytes;
-                const long px0 = (c_begin + i) * kChunk;
-                const int lim = px0 + kChunk > N ? (int)(N - px0) : kChunk;
-                // pixels 32-63 (the second box) into registers first: the lo parts
-                // of pixels 0-31 overwrite them. Then unit v (pixels 8v..8v+7):
-                // for v < 4 from the first box's 16-byte units 2v and 2v + 1,
-                // which its hi part (written at unit v <= 2v) no longer needs
-                float x1[32];
+            const bool ok = mbar_wait(&full[s], (i / kWideStages) & 1, abort_p, wl);
+            unsigned char *st = stages + (size_t)s * kWideStageBytes;
+            float xa[32], xb[32];
+            if (ok) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const float4 d = *reinterpret_cast<const float4 *>(r1 + ((u ^ sw) << 4));
-                    x1[4 * u] = d.x;
-                    x1[4 * u + 1] = d.y;
-                    x1[4 * u + 2] = d.z;
-                    x1[4 * u + 3] = d.w;
+                    const float4 a = *reinterpret_cast<const float4 *>(st + t * 128 + ((u ^ ph) << 4));
+                    const float4 d =
+                        *reinterpret_cast<const float4 *>(st + (t + 256) * 128 + ((u ^ ph) << 4));
+                    xa[4 * u] = a.x;
+                    xa[4 * u + 1] = a.y;
+                    xa[4 * u + 2] = a.z;
+                    xa[4 * u + 3] = a.w;
+                    xb[4 * u] = d.x;
+                    xb[4 * u + 1] = d.y;
+                    xb[4 * u + 2] = d.z;
+                    xb[4 * u + 3] = d.w;
                 }
-#pragma unroll
-                for (int v = 0; v < 8; ++v) {  // 8-pixel fp16 units of the operand rows
-                    float x[8];
-                    if (v < 4) {
-                        const float4 a0 = *reinterpret_cast<const float4 *>(r0 + (((2 * v) ^ sw) << 4));
-                        const float4 a1 = *reinterpret_cast<const float4 *>(r0 + (((2 * v + 1) ^ sw) << 4));
-                        x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w;
-                        x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) x[e] = x1[8 * (v - 4) + e];
-                    }
-                    float h[8], l[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        float y = fmaf(x[e], c, nsc);
-                        if (8 * v + e >= lim) y = 0.f;
-                        ymax = fmaxf(ymax, fabsf(y));
-                        bsum += y;
-                        const float t = __fmul_rn(y, 8193.f);
-                        h[e] = __fsub_rn(t, __fsub_rn(t, y));
-                        l[e] = __fsub_rn(y, h[e]);
-                    }
-                    *reinterpret_cast<uint4 *>(r0 + ((v ^ sw) << 4)) =
-                        make_uint4(pack_half2(h[0], h[1]), pack_half2(h[2], h[3]),
-                                   pack_half2(h[4], h[5]), pack_half2(h[6], h[7]));
-                    *reinterpret_cast<uint4 *>(r1 + ((v ^ sw) << 4)) =
-                        make_uint4(pack_half2(l[0], l[1]), pack_half2(l[2], l[3]),
-                                   pack_half2(l[4], l[5]), pack_half2(l[6], l[7]));
-                }
+            }
+            // every converter has read its rows, or one of them gave up (then
+            // all leave together)
+            if (conv_bar_or1(32 * kWideConvWarps, !ok)) break;
+            const long px0 = (c_begin + i) * kChunk;
+            const int lim = px0 + kChunk > N ? (int)(N - px0) : kChunk;
+            if (lim == kChunk) {
+                wide_convert<false>(st, h, bA, bB, B, cA, nA, cB, nB, lim, xa, xb, sA, sB);
+            } else {
+                wide_convert<true>(st, h, bA, bB, B, cA, nA, cB, nB, lim, xa, xb, sA, sB);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&conv[s]);
         }
-        if (b < B && !isfinite(bsum)) atomicOr(&ctl->status, ST_NONFINITE_CUBE);
-        if (!(ymax < kFp16Max)) range_flag = 1;
+        // a band's two halves are on adjacent lanes: its sum is theirs
+        sA += __shfl_xor_sync(0xffffffffu, sA, 1);
+        sB += __shfl_xor_sync(0xffffffffu, sB, 1);
+        if ((bA < B && !isfinite(sA)) || (bB < B && !isfinite(sB)))
+            atomicOr(&ctl->status, ST_NONFINITE_CUBE);
+        bsum = h == 0 ? sA : 0.f;
+        bsum2 = h == 0 ? sB : 0.f;
     } else {
         // ---------------- epilogue: drains, one block per flush event, then all three
         const int q = warp & 3;  // the TMEM lane quarter this warp may read
@@ -996,7 +1055,8 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
             tc_fence_after();
             const int j = e % 3;
             const uint32_t old = (slots >> (2 * j)) & 3u;
-            wide_drain(tmem, q, lane, j, (int)old, (written >> j) & 1u, B, Np, isc, out, pol);
+            wide_drain(tmem, q, lane, j, (int)old, (written >> j) & 1u, B, Np, isc, out, pol,
+                       &range_flag);
             written |= 1u << j;
             slots = (slots & ~(3u << (2 * j))) | (spare << (2 * j));
             spare = old;
@@ -1008,7 +1068,7 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
             tc_fence_after();
             for (int j = 0; j < 3; ++j)
                 wide_drain(tmem, q, lane, j, (int)((slots >> (2 * j)) & 3u), (written >> j) & 1u,
-                           B, Np, isc, out, pol);
+                           B, Np, isc, out, pol, &range_flag);
         }
     }
     if (tid == 32 && ncommit > 0) {
@@ -1026,8 +1086,11 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
                      "r"(kTmemCols)
                      : "memory");
     }
-    if (warp >= 2 && warp < 2 + kWideConvWarps && cv < B)
-        sum_part[(size_t)blockIdx.x * B + cv] = bsum * isc[cv];
+    if (warp >= 2 && warp < 2 + kWideConvWarps && (cv & 1) == 0) {
+        const int bA = cv >> 1, bB = 128 + (cv >> 1);
+        if (bA < B) sum_part[(size_t)blockIdx.x * B + bA] = bsum * isc[bA];
+        if (bB < B) sum_part[(size_t)blockIdx.x * B + bB] = bsum2 * isc[bB];
+    }
     if (!range_flag || *abort_p || nchunks == 0) return;
 
     // ---------------- FP32 recompute of this CTA's partial (rare), over the
@@ -1463,7 +1526,9 @@ EncodeTiledFn encode_fn()
 
 bool gram_tc_supported(const float *cube, int B, long N)
 {
-    return B >= 1 && B <= 256 && N % 4 == 0 && N < (1L << 31) &&
+    // B <= 128: the 3-D map when N % 32 == 0, else the 2-D one (N % 4 == 0);
+    // 129-256 bands: the 3-D map only
+    return B >= 1 && B <= 256 && N % (B <= 128 ? 4 : 32) == 0 && N < (1L << 31) &&
            (reinterpret_cast<uintptr_t>(cube) & 15u) == 0 && encode_fn() != nullptr;
 }
 
@@ -1496,15 +1561,39 @@ int gram_tc_parts(long N, long per)
 }
 
 namespace {
-template <int kSt>
+template <bool k3D, int kSt>
 void launch_narrow(const CUtensorMap &map, const float *cube, int B, int Np, long N, long total,
                    long per, int parts, const PcaScratch &s, cudaStream_t st)
 {
     const size_t smem = Cfg<false, kSt>::kSmem;
-    cudaFuncSetAttribute(gram_tc_kernel<false, kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(gram_tc_kernel<k3D, kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    gram_tc_kernel<false, kSt><<<parts, Cfg<false, kSt>::kThreads, smem, st>>>(
+    gram_tc_kernel<k3D, kSt><<<parts, Cfg<false, kSt>::kThreads, smem, st>>>(
         map, cube, B, 0, 0, Np, 1, N, total, per, s.shift, s.gram_part, s.sum_part, s.ctl);
+}
+
+// The cube's tensor map: 3-D {32 pixels, N / 32 groups, B bands} with boxes
+// {32, 2, B} (one per 64-pixel chunk) when N % 32 == 0, else 2-D {N, B} with
+// boxes {32, B}; 128-byte swizzle, out-of-range pixels read as zero.
+CUresult encode_cube_map(CUtensorMap *map, const float *cube, int B, long N, bool three_d)
+{
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (three_d) {
+        cuuint64_t dims[3] = {(cuuint64_t)kBoxPx, (cuuint64_t)(N / kBoxPx), (cuuint64_t)B};
+        cuuint64_t strides[2] = {(cuuint64_t)kBoxPx * sizeof(float), (cuuint64_t)N * sizeof(float)};
+        cuuint32_t box[3] = {(cuuint32_t)kBoxPx, 2u, (cuuint32_t)B};
+        return encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(cube), dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)B};
+    cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)kBoxPx, (cuuint32_t)B};
+    return encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(cube), dims,
+                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
 template <int kSt>
@@ -1548,18 +1637,17 @@ cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s
         return cudaGetLastError();
     }
     CUtensorMap map;
-    cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)B};
-    cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)kBoxPx, (cuuint32_t)B};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(cube),
-                             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const bool three_d = N % kBoxPx == 0;
+    if (B > 128 && !three_d) return cudaErrorInvalidValue;  // excluded by gram_tc_supported
+    if (encode_cube_map(&map, cube, B, N, three_d) != CUDA_SUCCESS) return cudaErrorInvalidValue;
     if (B <= 128) {
-        if (stages == 3) launch_narrow<3>(map, cube, B, Np, N, total, per, parts, s, st);
-        else launch_narrow<4>(map, cube, B, Np, N, total, per, parts, s, st);
+        if (three_d) {
+            if (stages == 3) launch_narrow<true, 3>(map, cube, B, Np, N, total, per, parts, s, st);
+            else launch_narrow<true, 4>(map, cube, B, Np, N, total, per, parts, s, st);
+        } else {
+            if (stages == 3) launch_narrow<false, 3>(map, cube, B, Np, N, total, per, parts, s, st);
+            else launch_narrow<false, 4>(map, cube, B, Np, N, total, per, parts, s, st);
+        }
         return cudaGetLastError();
     }
     // 128 < B <= 256: one launch, each chunk read and converted once

@@ -72,16 +72,18 @@ def test_covariance_raw_counts(hsc, ctx):
     check(hsc, ctx, cube, 0)
 
 
-def test_covariance_outlier_outside_pilot_sample(hsc, ctx):
+@pytest.mark.parametrize("B,ob", [(64, 5), (200, 5), (200, 170)])
+def test_covariance_outlier_outside_pilot_sample(hsc, ctx, B, ob):
     """One pixel ~10^4 times further from its band's mean than any other, at a
     position the pilot sample skips (its runs start at r(N - 256)/15): its
     scaled value leaves FP16's range, so that CTA recomputes its partial on the
-    FP32 pipe. Both the outlier band's row and the rest of C match the oracle,
-    each against its own scale."""
+    FP32 pipe (B = 200: the one-read 129-256-band kernel, the outlier in either
+    half of the bands). Both the outlier band's row and the rest of C match
+    the oracle, each against its own scale."""
     import torch
-    B, H, W = 64, 128, 128
+    H, W = 128, 128
     cube = synth.make_frame(77, H, W, B, sigma=0.03).cube.copy()
-    ob, p = 5, 700
+    p = 700
     cube[ob].flat[p] += np.float32(5e3)
     c = torch.as_tensor(cube, device="cuda")
     mu, C = hsc.hsc_pca_covariance(ctx, c)
