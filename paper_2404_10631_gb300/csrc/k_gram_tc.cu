@@ -43,6 +43,7 @@
 #include <cuda_runtime.h>
 
 #include "hsc_internal.cuh"
+#include "tma_util.cuh"
 
 namespace hsc {
 namespace {
@@ -50,12 +51,21 @@ namespace {
 constexpr int kChunk = 64;               // pixels per chunk (one 128-byte fp16 row)
 constexpr int kBoxPx = 32;               // pixels per TMA box (128 bytes of fp32)
 constexpr int kM = 128;                  // MMA M (bands of one half, zero padded)
-// mbarrier waits: each try suspends the thread until the phase completes or
-// kSuspendNs pass (so waiting warps take no issue slots or shared-memory
-// bandwidth from the others), and gives up after kWaitLimit tries (about
-// 2.6 s; kTestWaitLimit, about 1.3 ms, while Control::test_stall is set)
-constexpr uint32_t kSuspendNs = 10000;
-constexpr uint32_t kWaitLimit = 1u << 18;
+// mbarrier waits (tma_util.cuh): each try suspends the thread until the
+// phase completes or 10 us pass, and gives up after tma::kWaitLimit tries
+// (about 2.6 s; kTestWaitLimit, about 1.3 ms, while Control::test_stall is set)
+using tma::kWaitLimit;
+using tma::mbar_arrive;
+using tma::mbar_arrive_tx;
+using tma::mbar_init;
+using tma::mbar_try;
+using tma::mbar_wait;
+using tma::smem_u32;
+using tma::tma_load_2d;
+using tma::tma_load_3d;
+using tma::tma_load_3d_hint;
+using tma::l2_policy_evict_first;
+using tma::l2_policy_evict_last;
 constexpr uint32_t kTestWaitLimit = 1u << 7;
 constexpr uint32_t kTmemCols = 512;
 constexpr float kFp16Max = 65504.f;
@@ -91,78 +101,6 @@ struct Cfg {
     static_assert((size_t)kRows * kFbLd * 4 <= (size_t)kStages * kStageBytes,
                   "the FP32 recompute stages into the TMA ring");
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-            smem_u32(bar)),
-        "r"(bytes)
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of the given parity; false on expiry or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          uint32_t limit = kWaitLimit)
-{
-    for (uint32_t i = 0; i < limit; ++i) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-    }
-    *abort_flag = 1;
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// One box of a 3-D tensor map (coordinates innermost first).
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
-                                            uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // groups 1024 bytes apart (stride byte offset), leading offset unused (16).
@@ -742,20 +680,6 @@ __device__ __forceinline__ void wide_block(int j, int Np, int &row0, int &col0, 
     ncol = j == 0 ? 128 : Np - 128;
 }
 
-__device__ __forceinline__ uint64_t l2_policy_evict_last()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ uint64_t l2_policy_evict_first()
-{
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
 __device__ __forceinline__ float ld_hint(const float *p, uint64_t pol)
 {
     float v;
@@ -767,19 +691,6 @@ __device__ __forceinline__ void st_hint(float *p, float v, uint64_t pol)
 {
     asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol)
                  : "memory");
-}
-
-// A box of the cube's 3-D map with an L2 policy: read once, evicted first,
-// so that the partial Grams the drains read back stay in L2.
-__device__ __forceinline__ void tma_load_3d_hint(void *dst, const CUtensorMap *map, int x, int y,
-                                                 int z, uint64_t *bar, uint64_t pol)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)),
-        "l"(pol)
-        : "memory");
 }
 
 // Named barrier 1 of the converter warps (nthreads threads) that also ORs a

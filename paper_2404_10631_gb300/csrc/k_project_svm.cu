@@ -98,6 +98,63 @@ __device__ __forceinline__ void couple_solve(const float *r /* M, pair order */,
     for (int i = 0; i < KC; ++i) p[i] = (float)(y[i] * inv);
 }
 
+// The end of one pixel's work, common to every form of the pass: I (and its
+// running min/max), the M decision values f = acc + bias, Platt, coupling, the
+// k probabilities, the label and the pixel-interleaved copy.
+template <int KC>
+__device__ __forceinline__ void finish_pixel(const float (&acc)[KC * (KC - 1) / 2 > 0 ? KC * (KC - 1) / 2 : 1],
+                                             float accI, long p, long N, bool do_pca,
+                                             const float *sbias, const float *sa, const float *sb,
+                                             float *__restrict__ I_raw, float *__restrict__ probs,
+                                             int32_t *__restrict__ labels, int couple_f64,
+                                             float &lmin, float &lmax, bool &bad,
+                                             float4 *__restrict__ P4)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    constexpr int MA = M > 0 ? M : 1;
+    if (do_pca) {
+        const float I = accI;
+        bad |= !isfinite(I);
+        I_raw[p] = I;
+        lmin = fminf(lmin, I);
+        lmax = fmaxf(lmax, I);
+    }
+    if constexpr (M > 0) {
+        float r[MA];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            float f = acc[m] + sbias[m];
+            bad |= !isfinite(f);
+            float rr = 1.f / (1.f + expf(fmaf(sa[m], f, sb[m])));
+            r[m] = fminf(fmaxf(rr, 1e-7f), 1.f - 1e-7f);
+        }
+        float pr[KC > 0 ? KC : 1];
+        if (couple_f64) couple_solve<KC, double>(r, pr);
+        else couple_solve<KC, float>(r, pr);
+        int best = 0;
+        float bv = pr[0];
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+            probs[(size_t)c * (size_t)N + p] = pr[c];
+            if (pr[c] > bv) {
+                bv = pr[c];
+                best = c;
+            }
+        }
+        if (labels) labels[p] = best;
+        if (P4) {  // pixel-interleaved copy for the KNN's gathers
+            constexpr int NQ = (KC + 3) / 4;
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e] = 4 * i + e < KC ? pr[4 * i + e] : 0.f;
+                P4[(size_t)p * NQ + i] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    }
+}
+
 // The per-pixel work of the pass for groups g_begin, g_begin + g_step, ...
 // below g_end of PX pixels: group g holds pixels g * PX + u (one 16-byte
 // load per band when kVec, else PX 4-byte loads), or, kStrided, pixels
@@ -158,47 +215,11 @@ __device__ __forceinline__ void project_svm_groups(
         for (int u = 0; u < PX; ++u) {
             const long p = p0 + u * kPs;
             if (p >= N) break;
-            if (do_pca) {
-                float I = accI[u];
-                bad |= !isfinite(I);
-                I_raw[p] = I;
-                lmin = fminf(lmin, I);
-                lmax = fmaxf(lmax, I);
-            }
-            if constexpr (M > 0) {
-                float r[MA];
+            float a[MA];
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    float f = acc[m][u] + sbias[m];
-                    bad |= !isfinite(f);
-                    float rr = 1.f / (1.f + expf(fmaf(sa[m], f, sb[m])));
-                    r[m] = fminf(fmaxf(rr, 1e-7f), 1.f - 1e-7f);
-                }
-                float pr[KC > 0 ? KC : 1];
-                if (couple_f64) couple_solve<KC, double>(r, pr);
-                else couple_solve<KC, float>(r, pr);
-                int best = 0;
-                float bv = pr[0];
-#pragma unroll
-                for (int c = 0; c < KC; ++c) {
-                    probs[(size_t)c * (size_t)N + p] = pr[c];
-                    if (pr[c] > bv) {
-                        bv = pr[c];
-                        best = c;
-                    }
-                }
-                if (labels) labels[p] = best;
-                if (P4) {  // pixel-interleaved copy for the KNN's gathers
-                    constexpr int NQ = (KC + 3) / 4;
-#pragma unroll
-                    for (int i = 0; i < NQ; ++i) {
-                        float v[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) v[e] = 4 * i + e < KC ? pr[4 * i + e] : 0.f;
-                        P4[(size_t)p * NQ + i] = make_float4(v[0], v[1], v[2], v[3]);
-                    }
-                }
-            }
+            for (int m = 0; m < MA; ++m) a[m] = acc[m][u];
+            finish_pixel<KC>(a, accI[u], p, N, do_pca, sbias, sa, sb, I_raw, probs, labels,
+                             couple_f64, lmin, lmax, bad, P4);
         }
     }
 }

@@ -39,6 +39,12 @@ def hsc(torch_cuda):
 
 @pytest.fixture(scope="session")
 def ctx(hsc):
-    c = hsc.Context(0)
+    """A context launching on torch's current stream: torch's fills, copies
+    and edits of the test tensors and the library's kernels are then ordered
+    on one stream (a context with a stream of its own does not wait for them)."""
+    import torch
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    c = hsc.Context(0, stream=s)
     yield c
     c.close()

@@ -87,6 +87,7 @@ def test_graph_replay_sees_new_data(hsc, ctx):
             c.copy_(torch.as_tensor(f2.cube, device="cuda"))
         else:
             c.copy_(torch.flip(c, dims=[1]))
+    torch.cuda.synchronize()  # the edits are done before the library reads the cubes
     hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, **args)
     ctx.sync()
     for i, f in enumerate(frames):
@@ -160,6 +161,7 @@ def test_staged_batch_long_items_and_alignment(hsc, ctx):
     buf = torch.empty(n3 + 1, device="cuda")
     buf[1:].copy_(torch.as_tensor(frames[3].cube.ravel(), device="cuda"))
     cubes[3] = buf[1:].view(frames[3].cube.shape)
+    torch.cuda.synchronize()
     assert cubes[3].data_ptr() % 16 != 0
     _alone_vs_batch(hsc, ctx, frames, cubes)
 
@@ -174,6 +176,8 @@ def test_staged_batch_out_of_range_pixel(hsc, ctx):
                                       spectra=frames[0].spectra))
     cubes = frames_to_device(frames)
     cubes[2][5].view(-1)[700] += 5e3
+    import torch
+    torch.cuda.synchronize()  # the outlier is in place before the library reads the cube
     _alone_vs_batch(hsc, ctx, frames, cubes)
 
 

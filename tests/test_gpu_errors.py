@@ -43,6 +43,7 @@ def test_nan_in_cube_is_reported(hsc, ctx):
     f, c, m = frame_tensors(hsc)
     bad = c.clone()
     bad[3, 5, 7] = float("nan")
+    torch.cuda.synchronize()
     hsc.hsc_classify(ctx, bad, m, 8, 5, 1.0)
     with pytest.raises(hsc.HscError) as e:
         ctx.sync()

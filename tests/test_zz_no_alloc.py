@@ -70,6 +70,7 @@ def _offset_cube(torch, cube_np, offset_floats):
     flat = torch.zeros(cube_np.size + offset_floats, dtype=torch.float32, device="cuda")
     view = flat[offset_floats:].view(cube_np.shape)
     view.copy_(torch.as_tensor(cube_np))
+    torch.cuda.synchronize()
     return flat, view
 
 
