@@ -386,17 +386,19 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
     model = hsc.Model.from_host(f.model, device=dev)
     # launch shapes for this frame shape, picked by the library's autotuner
     t0 = time.perf_counter()
-    tune_cfg = ctx.autotune(cubes[0], model)
+    tune_cfg = ctx.autotune(cubes[0], model, f.K, f.window_rows, f.lam)
     tune = {"config": tune_cfg, "seconds": time.perf_counter() - t0,
-            "how": "hsc_autotune on the first cube: Gram TMA staging depth {3, 4} (B <= 128) x "
-                   "projection/SVM {1, 4} pixels per thread x {2, 4, 8, 16} CTAs per SM, median of "
-                   "3 runs each; results do not depend on them"}
+            "how": "hsc_autotune on the first cube: Gram TMA staging depth {3, 4} (B <= 128), "
+                   "projection/SVM {1, 4} pixels per thread x {2, 4, 8, 16} CTAs per SM, pruned "
+                   "KNN walk {32 px x 8, 32 x 6, 32 x 12, 64 x 8} (pixels per CTA x undecided "
+                   "keys per lane), median of 3 runs each; results do not depend on them"}
     streams = [stream] + [torch.cuda.Stream(dev) for _ in range(F - 1)]
     ctxs = [ctx] + [hsc.Context(dev.index or 0, stream=s) for s in streams[1:]]
     for c in ctxs[1:]:
         c.reserve(B, H, W, k)
         c.set_tuning(B, H, W, k, (tune_cfg["gram_stages"], tune_cfg["svm_px"],
-                                  tune_cfg["svm_blocks_per_sm"]))  # the same launch shapes
+                                  tune_cfg["svm_blocks_per_sm"],
+                                  tune_cfg["knn_variant"]))  # the same launch shapes
     outs = [(torch.empty((H, W), dtype=torch.float32, device=dev),
              torch.empty((k, H, W), dtype=torch.float32, device=dev),
              torch.empty((k, H, W), dtype=torch.float32, device=dev),

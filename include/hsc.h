@@ -343,15 +343,23 @@ hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_it
                                int64_t *sweep_cycles, int64_t *refine_cycles);
 /* Autotuner (launch parameters that change speed, never results): times the
  * candidates of the tensor-core Gram's TMA staging depth (3 or 4 stages;
- * B <= 128) and of the projection/SVM pass's launch shape (1 or 4 pixels per
- * thread x 2, 4, 8 or 16 CTAs per SM) on this cube and model (median of 3
- * runs each, CUDA events on the context's stream, which it synchronises),
- * and keeps the fastest for frames of this shape (B, H*W, n_classes) in the
- * context: hsc_classify, hsc_classify_batch and hsc_pca_one_band use it for
- * frames of that shape, the defaults for others. Retuning replaces it.
- *   config  3 int32 (host, nullable): stages, pixels per thread, CTAs per SM */
+ * B <= 128), of the projection/SVM pass's launch shape (1 or 4 pixels per
+ * thread x 2, 4, 8 or 16 CTAs per SM) and, given KNN parameters with
+ * lambda > 0 and the pruned search, of the pruned walk's pixels per CTA and
+ * undecided keys per lane (variants 0: 32 and 8, 1: 32 and 6, 2: 32 and 12,
+ * 3: 64 and 8; every pixel's neighbour probabilities are added in one
+ * canonical order whichever pass completes it, so O is the same) on this cube
+ * and model (median of 3 runs each, CUDA events on the context's stream,
+ * which it synchronises), and keeps the fastest for frames of this shape (B,
+ * H*W, n_classes) in the context: hsc_classify, hsc_classify_batch and
+ * hsc_pca_one_band use it for frames of that shape, the defaults for others.
+ * Retuning replaces it.
+ *   params  KNN parameters (nullable: the walk is not tuned)
+ *   config  4 int32 (host, nullable): stages, pixels per thread, CTAs per SM,
+ *           walk variant */
 hsc_status hsc_autotune(hsc_ctx *ctx, const float *cube, int B, int H, int W,
-                        const hsc_svm_model *model, int32_t *config);
+                        const hsc_svm_model *model, const hsc_knn_params *params,
+                        int32_t *config);
 /* Sets the tuned parameters for frames of shape (B, H, W, n_classes) by hand
  * (config as hsc_autotune's; 0 = default for each), or clears them
  * (config NULL). HSC_ERR_INVALID_ARG for values outside the candidates. */

@@ -150,7 +150,7 @@ def lib():
         L.hsc_profile_enable.argtypes = [vp, i32]
         L.hsc_measure_fma_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.hsc_autotune.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(hsc_svm_model),
-                                   ctypes.POINTER(ctypes.c_int32)]
+                                   ctypes.POINTER(hsc_knn_params), ctypes.POINTER(ctypes.c_int32)]
         L.hsc_set_tuning.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_int32)]
         L.hsc_pca_project.argtypes = [vp, vp, i32, i32, i32, i32, ctypes.c_uint, vp, vp, vp]
         L.hsc_pca_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
@@ -294,22 +294,30 @@ class Context:
         self.check(lib().hsc_knn_diagnostics(self.handle, ctypes.byref(v), ctypes.byref(r)))
         return int(v.value), int(r.value)
 
-    def autotune(self, cube, model) -> dict:
+    def autotune(self, cube, model, K=None, window_rows=None, lam=None,
+                 search: int = HSC_KNN_SEARCH_AUTO) -> dict:
         """Times the launch-shape candidates on this cube (B x H x W) and keeps
-        the fastest for frames of its shape; returns the chosen parameters."""
+        the fastest for frames of its shape; with K, window_rows and lam also
+        the pruned KNN walk's variant. Returns the chosen parameters."""
         B, H, W = cube.shape
-        cfg = (ctypes.c_int32 * 3)()
+        cfg = (ctypes.c_int32 * 4)()
         ms = model.struct()
-        self.check(lib().hsc_autotune(self.handle, _ptr(cube), B, H, W, ctypes.byref(ms), cfg))
-        return {"gram_stages": cfg[0], "svm_px": cfg[1], "svm_blocks_per_sm": cfg[2]}
+        prm = None
+        if K is not None:
+            prm = ctypes.byref(hsc_knn_params(K, window_rows, lam, search))
+        self.check(lib().hsc_autotune(self.handle, _ptr(cube), B, H, W, ctypes.byref(ms), prm,
+                                      cfg))
+        return {"gram_stages": cfg[0], "svm_px": cfg[1], "svm_blocks_per_sm": cfg[2],
+                "knn_variant": cfg[3]}
 
     def set_tuning(self, B, H, W, n_classes, config=None):
-        """Sets (gram_stages, svm_px, svm_blocks_per_sm) for that frame shape, or
-        clears the tuning (config None)."""
+        """Sets (gram_stages, svm_px, svm_blocks_per_sm[, knn_variant]) for that
+        frame shape, or clears the tuning (config None)."""
         if config is None:
             self.check(lib().hsc_set_tuning(self.handle, B, H, W, n_classes, None))
             return
-        cfg = (ctypes.c_int32 * 3)(*config)
+        config = tuple(config) + (0,) * (4 - len(config))
+        cfg = (ctypes.c_int32 * 4)(*config)
         self.check(lib().hsc_set_tuning(self.handle, B, H, W, n_classes, cfg))
 
     @property

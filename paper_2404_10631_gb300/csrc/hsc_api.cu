@@ -370,7 +370,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
         StageTimer t(tc, HSC_STAGE_KNN, 2, st);
         e = hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows, params->lambda,
                             out_probs, labels, nullptr, s.ctl, st,
-                            params->search, s.P4);
+                            params->search, s.P4, tu.knn_variant);
     }
     return e;
 }
@@ -457,7 +457,8 @@ hsc_status hsc_set_tuning(hsc_ctx *ctx, int B, int H, int W, int n_classes,
     if (B < 1 || H < 1 || W < 1 || n_classes < 1)
         return fail(ctx, HSC_ERR_INVALID_ARG, "hsc_set_tuning: sizes must be >= 1%s");
     if ((config[0] != 0 && config[0] != 3 && config[0] != 4) ||
-        (config[1] != 0 && config[1] != 1 && config[1] != 4) || config[2] < 0 || config[2] > 64)
+        (config[1] != 0 && config[1] != 1 && config[1] != 4) || config[2] < 0 || config[2] > 64 ||
+        config[3] < 0 || config[3] >= hsc::kKnnVariants)
         return fail(ctx, HSC_ERR_INVALID_ARG, "hsc_set_tuning: value out of range%s");
     ctx->tuned = true;
     ctx->tune_B = B;
@@ -466,16 +467,19 @@ hsc_status hsc_set_tuning(hsc_ctx *ctx, int B, int H, int W, int n_classes,
     ctx->tune.gram_stages = config[0];
     ctx->tune.svm_px = config[1];
     ctx->tune.svm_blocks_per_sm = config[2];
+    ctx->tune.knn_variant = config[3];
     return HSC_OK;
 }
 
 hsc_status hsc_autotune(hsc_ctx *ctx, const float *cube, int B, int H, int W,
-                        const hsc_svm_model *model, int32_t *config)
+                        const hsc_svm_model *model, const hsc_knn_params *params,
+                        int32_t *config)
 {
     hsc_status st = check_ctx(ctx);
     if (st) return st;
     if ((st = check_cube(ctx, cube, B, H, W))) return st;
     if ((st = check_model(ctx, model, B))) return st;
+    if (params && (st = check_knn(ctx, params, model->n_classes, H, W))) return st;
     const long N = (long)H * W;
     const int k = model->n_classes;
     Layout L = make_layout(ctx, B, N, k, true, true, true);
@@ -534,6 +538,30 @@ hsc_status hsc_autotune(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                 best.svm_blocks_per_sm = bps;
             }
         }
+    // the pruned KNN walk's variant (with the KNN parameters, lambda > 0), on
+    // this frame's own normalised map and probabilities
+    if (params && params->lambda > 0.f && params->search != HSC_KNN_SEARCH_FULL &&
+        params->search != HSC_KNN_SEARCH_HEAP) {
+        if (err == cudaSuccess)
+            err = hsc::launch_project_svm(cube, B, N, s.v1f, s.muf, I, model, false, Pm, nullptr,
+                                          s.ctl, ctx->sm_count, str, 0, 0, s.P4);
+        if (err == cudaSuccess) err = hsc::launch_normalize(I, I, N, s.ctl, str);
+        float btk = 1e30f;
+        // the labels go over the P planes: the walk and its redo pass read the
+        // probabilities from the pixel-interleaved copy
+        int32_t *lab = reinterpret_cast<int32_t *>(Pm);
+        for (int v = 0; v < hsc::kKnnVariants && err == cudaSuccess; ++v) {
+            const float t = time_ms([&] {
+                return hsc::launch_knn(I, Pm, k, H, W, params->k, params->window_rows,
+                                       params->lambda, nullptr, lab, nullptr, s.ctl, str,
+                                       params->search, s.P4, v);
+            });
+            if (t < btk) {
+                btk = t;
+                best.knn_variant = v;
+            }
+        }
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (err != cudaSuccess) return cuda_fail(ctx, err, "hsc_autotune");
@@ -546,6 +574,7 @@ hsc_status hsc_autotune(hsc_ctx *ctx, const float *cube, int B, int H, int W,
         config[0] = best.gram_stages;
         config[1] = best.svm_px;
         config[2] = best.svm_blocks_per_sm;
+        config[3] = best.knn_variant;
     }
     return HSC_OK;
 }

@@ -128,11 +128,13 @@ struct PixItem {
 // (an autotuner picks them per frame shape): the tensor-core Gram's TMA
 // staging depth (3 or 4; 0 = default), and the projection/SVM pass's pixels
 // per thread (1 or 4; 0 = 4, with 16-byte loads when the cube allows them)
-// and CTAs per SM of its grid-stride launch (0 = 8).
+// and CTAs per SM of its grid-stride launch (0 = 8), and the pruned KNN walk's
+// variant (launch_knn).
 struct Tuning {
     int gram_stages = 0;
     int svm_px = 0;
     int svm_blocks_per_sm = 0;
+    int knn_variant = 0;  // launch_knn's variant of the pruned walk
 };
 
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s,
@@ -210,9 +212,13 @@ cudaError_t knn_init(int device);
 
 // P4 (nullable): P pixel-interleaved, (k + 3) / 4 float4 per pixel, which
 // the pruned search gathers from (one 16-byte load per 4 classes).
+// variant (pruned search with P4): the walk's pixels per CTA and undecided
+// keys per lane, 0 = 32 and 8, 1 = 32 and 6, 2 = 32 and 12, 3 = 64 and 8;
+// the outputs do not depend on it.
+constexpr int kKnnVariants = 4;
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr,
                        Control *ctl, cudaStream_t st, int search,
-                       const float4 *P4 = nullptr);
+                       const float4 *P4 = nullptr, int variant = 0);
 
 }  // namespace hsc

@@ -44,6 +44,18 @@ constexpr int kStride = kChunk + 4;         // shared row stride (floats)
 constexpr int kCap = HSC_MAX_K + 32;        // per-lane candidate buffer
 constexpr float kMargin = 1.0f / 262144.f;  // 2^-18 relative filter slack
 
+// Offsets (dr, dc) with dr^2 + dc^2 <= 400 and |dr| <= 16, sorted by
+// s = dr^2 + dc^2 (then dr, dc), built on the host once per device.
+constexpr int kTabR2 = 400;            // table: dr^2 + dc^2 <= 400
+constexpr int kTabDr = 16;             // |dr| <= 16: windows of up to 32 rows
+constexpr int kTabDc = 20;             // |dc| <= 20 follows from kTabR2
+constexpr int kTabCap = 1200;
+__constant__ char2 c_knn_tab[kTabCap];
+__constant__ int c_knn_tab_n;
+// extent of the first K table offsets (K = 1..64): max |dr| above and below,
+// max |dc|, and s of the K-th
+__constant__ char4 c_knn_pref[HSC_MAX_K + 1];
+
 struct Key {
     float hi, lo;
     int q;
@@ -100,11 +112,49 @@ __device__ __noinline__ Key max_key(const Key *buf, int n)
 }
 
 
+// The canonical summation order of a pixel's K neighbours, the same in every
+// search and in the redo pass, so that O does not depend on how the set was
+// found: with s_K the K-th smallest spatial term dr^2 + dc^2 of the pixel's
+// valid candidates and L = fl(lambda^2 s_K) (when the offset table holds K
+// valid offsets of the pixel; else L = -inf), the keys whose exact value is
+// below L come first, by increasing linear index, then the others by
+// increasing key. (At most K - 1 keys lie below L, and all of them are among
+// the K nearest. The pruned walk adds them as its row-major walk meets them,
+// i.e. by increasing index, then the rest from its buffer in key order.)
+__device__ float canonical_L(int r, int c, int lo_r, int hi_r, int W, int K, float l2, int &sK)
+{
+    const int ntab = c_knn_tab_n;
+    int cnt = 0;
+    for (int t = 0; t < ntab; ++t) {
+        const char2 o = c_knn_tab[t];
+        const int i = r + o.x, j = c + o.y;
+        if (i < lo_r || i > hi_r || j < 0 || j >= W) continue;
+        if (++cnt == K) {
+            sK = o.x * o.x + o.y * o.y;
+            return __fmul_rn(l2, (float)sK);
+        }
+    }
+    sK = 0;
+    return -INFINITY;
+}
+
+__device__ __forceinline__ bool below_L(const Key &a, float L)
+{
+    return a.hi < L || (a.hi == L && a.lo < 0.f);
+}
+
 // Writes the pixel's outputs from its K selected keys: neighbour indices
-// nearest first (optional), O = mean of the neighbours' probabilities, label.
+// nearest first (optional), O = mean of the neighbours' probabilities added
+// in the canonical order (canonical_L), label. The keys below L are the
+// window candidates of spatial term s < s_K whose key is below L (every one
+// of them is selected): they are met again here by walking that disk row by
+// row, i.e. by increasing linear index, with no sort; the other selected
+// keys (few) are added by increasing key.
 __device__ __noinline__ void finish_pixel(Key *buf, int n, int K, const float *__restrict__ P, int k,
                                           long N, long p, float *__restrict__ O,
-                                          int32_t *__restrict__ labels, int32_t *__restrict__ nbr)
+                                          int32_t *__restrict__ labels, int32_t *__restrict__ nbr,
+                                          const float *__restrict__ I, float Ip, int r, int c,
+                                          int lo_r, int hi_r, int W, float l2)
 {
     if (nbr) {  // nearest first (selection sort; debug output)
         for (int a = 0; a < n; ++a) {
@@ -118,13 +168,42 @@ __device__ __noinline__ void finish_pixel(Key *buf, int n, int K, const float *_
         }
         for (int a = n; a < K; ++a) nbr[p * K + a] = -1;
     }
+    int sK;
+    const float L = canonical_L(r, c, lo_r, hi_r, W, K, l2, sK);
+    int qa[HSC_MAX_K];
+    int na = 0;
+    for (int dr = lo_r - r; dr <= hi_r - r && sK > 0; ++dr) {
+        const int rem = sK - 1 - dr * dr;
+        if (rem < 0) continue;
+        int cm = (int)sqrtf((float)rem);
+        while (cm * cm > rem) --cm;
+        while ((cm + 1) * (cm + 1) <= rem) ++cm;
+        const int j0 = max(0, c - cm), j1 = min(W - 1, c + cm);
+        const int rowq = (r + dr) * W;
+        for (int j = j0; j <= j1; ++j) {
+            const Key kk = make_key(Ip, __ldg(I + rowq + j), dr, c - j, l2, rowq + j);
+            if (below_L(kk, L) && na < HSC_MAX_K) qa[na++] = kk.q;
+        }
+    }
+    int nb = 0;  // the other selected keys, by increasing key
+    for (int a = 0; a < n; ++a)
+        if (!below_L(buf[a], L)) buf[nb++] = buf[a];
+    for (int a = 0; a < nb; ++a) {
+        int im = a;
+        for (int b = a + 1; b < nb; ++b)
+            if (key_lt(buf[b], buf[im])) im = b;
+        Key t = buf[a];
+        buf[a] = buf[im];
+        buf[im] = t;
+    }
     const float invK = 1.f / (float)K;
     int best = 0;
     float bestv = -INFINITY;
     for (int cl = 0; cl < k; ++cl) {
         const float *Pc = P + (size_t)cl * (size_t)N;
         float s = 0.f;
-        for (int a = 0; a < n; ++a) s += __ldg(Pc + buf[a].q);
+        for (int a = 0; a < na; ++a) s += __ldg(Pc + qa[a]);
+        for (int a = 0; a < nb; ++a) s += __ldg(Pc + buf[a].q);
         float o = s * invK;
         if (O) O[(size_t)cl * (size_t)N + p] = o;
         if (o > bestv) {
@@ -281,7 +360,8 @@ knn_kernel(const float *__restrict__ I, const float *__restrict__ P, int k, int 
     if (n < K) atomicOr(&ctl->status, ST_KNN_SHORT);
     shrink(buf, n, K);
 
-    finish_pixel(buf, n, K, P, k, N, (long)r * W + c, O, labels, nbr);
+    finish_pixel(buf, n, K, P, k, N, (long)r * W + c, O, labels, nbr, I, Ip, r, c, lo_r, hi_r, W,
+                 l2);
     (void)lane;
 }
 
@@ -366,7 +446,8 @@ knn_heap_kernel(const float *__restrict__ I, const float *__restrict__ P, int k,
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->status, ST_NONFINITE_MAP);
     if (!active) return;
     if (n < K) atomicOr(&ctl->status, ST_KNN_SHORT);
-    finish_pixel(heap, n, K, P, k, N, (long)r * W + c, O, labels, nbr);
+    finish_pixel(heap, n, K, P, k, N, (long)r * W + c, O, labels, nbr, I, Ip, r, c, lo_r, hi_r,
+                 W, l2);
 }
 
 // ---- exact, spatially pruned variant (lambda > 0)
@@ -394,20 +475,11 @@ knn_heap_kernel(const float *__restrict__ I, const float *__restrict__ P, int k,
 // or neighbour-index output) gets the sentinel label kRedoLabel and
 // knn_redo_kernel completes it with an unbounded walk.
 constexpr int kWalkThreads = 32;
-constexpr int kTabR2 = 400;            // table: dr^2 + dc^2 <= 400
-constexpr int kTabDr = 16;             // |dr| <= 16: windows of up to 32 rows
-constexpr int kTabDc = 20;             // |dc| <= 20 follows from kTabR2
-constexpr int kTabCap = 1200;
 constexpr int kBnd = 8;                // undecided keys per lane
 constexpr int kRedoLabel = -2147483647 - 1;
 constexpr int kBatchRedoCtas = 1024;  // the batched redo pass's grid (exits at once when idle)
 constexpr int kRedoThreads = 32;
 constexpr int kRedoExtra = 32;         // redo buffer slots beyond K
-__constant__ char2 c_knn_tab[kTabCap];
-__constant__ int c_knn_tab_n;
-// extent of the first K table offsets (K = 1..64): max |dr| above and below,
-// max |dc|, and s of the K-th
-__constant__ char4 c_knn_pref[HSC_MAX_K + 1];
 
 // Key buffer of one lane: column `lane` of [cap][stride] arrays in shared
 // memory (consecutive lanes, consecutive words).
@@ -521,8 +593,12 @@ __device__ __forceinline__ void write_pixel(const float (&acc)[KC], int K, long 
     labels[p] = best;
 }
 
-template <int KC, bool kBatch = false, bool kP4 = false>
-__global__ void __launch_bounds__(kWalkThreads)
+// kWT: pixels per CTA (one row segment, a lane per pixel); kBN: undecided
+// keys per lane. Neither changes a result (the canonical summation order
+// makes O independent of which pixels the redo pass completes); an
+// autotuner picks them per frame shape.
+template <int KC, bool kBatch = false, bool kP4 = false, int kWT = kWalkThreads, int kBN = kBnd>
+__global__ void __launch_bounds__(kWT)
 knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
                   int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
                   bool redo_all, Control *ctl, const BatchFrame *__restrict__ frames,
@@ -530,7 +606,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                   const float4 *__restrict__ P4, int cta_base = 0)
 {
     extern __shared__ float sm[];
-    __shared__ float s_min[kWalkThreads / 32], s_max[kWalkThreads / 32];
+    __shared__ float s_min[kWT / 32], s_max[kWT / 32];
     int r = blockIdx.y, bx = blockIdx.x;
     int frame = 0;
     if (kBatch) {  // a stage-major batch: the frame whose CTA range holds this CTA
@@ -552,36 +628,36 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         labels = fr.labels;
         ctl = fr.ctl;
         const int t = cta - fr.knn_cta0;
-        const int tpr = (W + kWalkThreads - 1) / kWalkThreads;
+        const int tpr = (W + kWT - 1) / kWT;
         r = t / tpr;
         bx = t - r * tpr;
     }
     const int lane = threadIdx.x;
-    const int c0 = bx * kWalkThreads, c = c0 + lane;
+    const int c0 = bx * kWT, c = c0 + lane;
     const bool active = c < W;
     const int lo_r = max(0, r - R / 2);
     const int hi_r = min(H - 1, r + (R + 1) / 2 - 1);
     const int nrows = hi_r - lo_r + 1;
-    const int tw = kWalkThreads + 2 * kTabDc, tcol0 = c0 - kTabDc;
+    const int tw = kWT + 2 * kTabDc, tcol0 = c0 - kTabDc;
     float *tile = sm;  // nrows x tw
     LaneBuf bnd;
-    bnd.stride = kWalkThreads;
+    bnd.stride = kWT;
     bnd.hi = tile + nrows * tw + lane;
-    bnd.lo = bnd.hi + kBnd * kWalkThreads;
-    bnd.q = reinterpret_cast<int *>(bnd.lo + kBnd * kWalkThreads);
+    bnd.lo = bnd.hi + kBN * kWT;
+    bnd.q = reinterpret_cast<int *>(bnd.lo + kBN * kWT);
     const float l2 = lam * lam;
     const long N = (long)H * W;
 
-    // stage the window rows x (kWalkThreads + 2 * 20) columns, all copies in
+    // stage the window rows x (kWT + 2 * 20) columns, all copies in
     // flight at once: 16-byte copies when the tile lies inside the image and
     // its rows start on 16-byte boundaries, else 4-byte copies with the
     // out-of-image columns zero-filled
-    constexpr int kV = (kWalkThreads + 2 * kTabDc) / 4;  // 16-byte units per tile row
-    static_assert((kWalkThreads + 2 * kTabDc) % 4 == 0 && kTabDc % 4 == 0, "tile rows of float4");
+    constexpr int kV = (kWT + 2 * kTabDc) / 4;  // 16-byte units per tile row
+    static_assert((kWT + 2 * kTabDc) % 4 == 0 && kTabDc % 4 == 0, "tile rows of float4");
     const bool vec = tcol0 >= 0 && tcol0 + tw <= W && (W & 3) == 0 &&
                      (reinterpret_cast<uintptr_t>(I) & 15u) == 0;
     if (vec) {
-        for (int idx = lane; idx < nrows * kV; idx += kWalkThreads) {
+        for (int idx = lane; idx < nrows * kV; idx += kWT) {
             const int ii = idx / kV, v = idx - ii * kV;
             const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ii * tw + 4 * v);
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
@@ -591,7 +667,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     } else {
         for (int ii = 0; ii < nrows; ++ii) {
             const float *row = I + (long)(lo_r + ii) * W;
-            for (int jj = lane; jj < tw; jj += kWalkThreads) {
+            for (int jj = lane; jj < tw; jj += kWT) {
                 const int col = tcol0 + jj;
                 const bool in = col >= 0 && col < W;
                 const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ii * tw + jj);
@@ -606,7 +682,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     bool bad = false;
     float vmin = INFINITY, vmax = -INFINITY;
     if (vec) {
-        for (int idx = lane; idx < nrows * kV; idx += kWalkThreads) {
+        for (int idx = lane; idx < nrows * kV; idx += kWT) {
             const float4 t4 = reinterpret_cast<const float4 *>(tile)[idx / kV * (tw / 4) + idx % kV];
             bad |= !isfinite(t4.x) || !isfinite(t4.y) || !isfinite(t4.z) || !isfinite(t4.w);
             vmin = fminf(vmin, fminf(fminf(t4.x, t4.y), fminf(t4.z, t4.w)));
@@ -614,7 +690,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         }
     } else {
         for (int ii = 0; ii < nrows; ++ii) {
-            for (int jj = lane; jj < tw; jj += kWalkThreads) {
+            for (int jj = lane; jj < tw; jj += kWT) {
                 const int col = tcol0 + jj;
                 if (col < 0 || col >= W) continue;
                 const float v = tile[ii * tw + jj];
@@ -635,7 +711,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     __syncthreads();
     vmin = s_min[0];
     vmax = s_max[0];
-    for (int w = 1; w < kWalkThreads / 32; ++w) {
+    for (int w = 1; w < kWT / 32; ++w) {
         vmin = fminf(vmin, s_min[w]);
         vmax = fmaxf(vmax, s_max[w]);
     }
@@ -721,8 +797,8 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                     continue;
                 }
                 if (!key_le(kk, tau)) continue;
-                if (nb == kBnd) {
-                    if (K - m >= kBnd) {  // cannot make room: leave the pixel to the redo pass
+                if (nb == kBN) {
+                    if (K - m >= kBN) {  // cannot make room: leave the pixel to the redo pass
                         redo = true;
                         break;
                     }
@@ -774,7 +850,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         int im = a;
         Key best = bnd.get(a);
         for (int b = a + 1; b < nb; ++b) {
-            const float hb = bnd.hi[b * kWalkThreads];
+            const float hb = bnd.hi[b * kWT];
             if (hb > best.hi) continue;
             const Key kb = bnd.get(b);
             if (key_lt(kb, best)) {
@@ -831,6 +907,8 @@ __device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float
     };
     bool stopped = false;
     const int ntab = c_knn_tab_n;
+    int valid = 0;
+    float Lc = -INFINITY;  // the canonical order's bound (canonical_L)
     for (int t = 0; t < ntab; ++t) {
         const char2 o = c_knn_tab[t];
         const int dr = o.x, dc = o.y;
@@ -840,6 +918,7 @@ __device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float
         }
         const int i = r + dr, j = c + dc;
         if (i < lo_r || i > hi_r || j < 0 || j >= W) continue;
+        if (++valid == K) Lc = __fmul_rn(l2, (float)(dr * dr + dc * dc));
         const int q = i * W + j;
         const float Iq = __ldg(I + q);
         bad |= !isfinite(Iq);
@@ -894,12 +973,42 @@ __device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float
         }
         for (int a = n; a < K; ++a) nbr[p * K + a] = -1;
     }
+    // the canonical order (as finish_pixel): the sorted indices of the keys
+    // below Lc, then the other keys by key
+    int qa[HSC_MAX_K];
+    int na = 0, nb = 0;
+    for (int a = 0; a < n; ++a) {
+        const Key ka = buf.get(a);
+        if (below_L(ka, Lc)) {
+            int i = na++;
+            for (; i > 0 && qa[i - 1] > ka.q; --i) qa[i] = qa[i - 1];
+            qa[i] = ka.q;
+        } else {
+            buf.put(nb++, ka);
+        }
+    }
+    for (int a = 0; a < nb; ++a) {
+        int im = a;
+        Key best = buf.get(a);
+        for (int b = a + 1; b < nb; ++b) {
+            const Key kb = buf.get(b);
+            if (key_lt(kb, best)) {
+                best = kb;
+                im = b;
+            }
+        }
+        if (im != a) {
+            buf.put(im, buf.get(a));
+            buf.put(a, best);
+        }
+    }
     float acc[KC];
 #pragma unroll
     for (int cl = 0; cl < KC; ++cl) acc[cl] = 0.f;
-    for (int a = 0; a < n; ++a) {
-        if (P4) add_probs4(acc, P4, buf.q[a * kRedoThreads]);
-        else add_probs(acc, P, N, buf.q[a * kRedoThreads]);
+    for (int a = 0; a < na + nb; ++a) {
+        const int q = a < na ? qa[a] : buf.q[(a - na) * kRedoThreads];
+        if (P4) add_probs4(acc, P4, q);
+        else add_probs(acc, P, N, q);
     }
     write_pixel(acc, K, N, p, O, labels);
 }
@@ -969,11 +1078,11 @@ knn_redo_batch_kernel(const BatchFrame *__restrict__ frames, int K, int R, float
     }
 }
 
+template <int kWT = kWalkThreads, int kBN = kBnd>
 size_t pruned_smem_bytes(int R, int H)
 {
     const int nrows = R < H ? R : H;
-    return sizeof(float) *
-           ((size_t)nrows * (kWalkThreads + 2 * kTabDc) + 3 * (size_t)kBnd * kWalkThreads);
+    return sizeof(float) * ((size_t)nrows * (kWT + 2 * kTabDc) + 3 * (size_t)kBN * kWT);
 }
 
 size_t redo_smem_bytes(int K) { return sizeof(float) * 3 * (size_t)(K + kRedoExtra) * kRedoThreads; }
@@ -1001,26 +1110,36 @@ long redo_resident_ctas(size_t smem)
     return n > 64 ? n : 64;
 }
 
+template <int KC, bool kP4, int kWT, int kBN>
+void launch_walk(const float *I, const float *P, int H, int W, int K, int R, float lam, float *O,
+                 int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st, const float4 *P4)
+{
+    const size_t smem = pruned_smem_bytes<kWT, kBN>(R, H);
+    auto kern = knn_pruned_kernel<KC, false, kP4, kWT, kBN>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((W + kWT - 1) / kWT, H);
+    kern<<<grid, kWT, smem, st>>>(I, P, H, W, K, R, lam, O, labels, nbr != nullptr, ctl, nullptr, 0,
+                                  nullptr, 0u, P4, 0);
+}
+
+// variant (with the pixel-interleaved probabilities only): 0 = 32 pixels
+// per CTA and 8 undecided keys per lane (the default), 1 = 32 and 6,
+// 2 = 32 and 12, 3 = 64 and 8.
 template <int KC>
 cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, int R, float lam,
                           float *O, int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st,
-                          const float4 *P4)
+                          const float4 *P4, int variant = 0)
 {
-    const size_t smem = pruned_smem_bytes(R, H);
-    dim3 grid((W + kWalkThreads - 1) / kWalkThreads, H);
     if (P4) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(knn_pruned_kernel<KC, false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        knn_pruned_kernel<KC, false, true><<<grid, kWalkThreads, smem, st>>>(
-            I, P, H, W, K, R, lam, O, labels, nbr != nullptr, ctl, nullptr, 0, nullptr, 0u, P4);
+        switch (variant) {
+        case 1: launch_walk<KC, true, 32, 6>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
+        case 2: launch_walk<KC, true, 32, 12>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
+        case 3: launch_walk<KC, true, 64, 8>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
+        default: launch_walk<KC, true, 32, 8>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
+        }
     } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(knn_pruned_kernel<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        knn_pruned_kernel<KC><<<grid, kWalkThreads, smem, st>>>(I, P, H, W, K, R, lam, O, labels,
-                                                                nbr != nullptr, ctl, nullptr, 0,
-                                                                nullptr, 0u, nullptr);
+        launch_walk<KC, false, 32, 8>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, nullptr);
     }
     const long N = (long)H * W;
     const size_t rsmem = redo_smem_bytes(K);
@@ -1042,7 +1161,7 @@ cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ct
                                 int K, int R, float lam, int max_rows, int2 *redo_list,
                                 unsigned redo_cap, cudaStream_t st)
 {
-    const size_t smem = pruned_smem_bytes(R, max_rows);
+    const size_t smem = pruned_smem_bytes<>(R, max_rows);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(knn_pruned_kernel<KC, true, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1134,7 +1253,7 @@ cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas,
 
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr, Control *ctl,
-                       cudaStream_t st, int search, const float4 *P4)
+                       cudaStream_t st, int search, const float4 *P4, int variant)
 {
     if (search == HSC_KNN_SEARCH_HEAP) {
         const int nrows_max = R < H ? R : H;
@@ -1150,14 +1269,14 @@ cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int 
     const bool pruned = search != HSC_KNN_SEARCH_FULL;
     if (pruned && lambda > 0.f) {
         switch (k) {
-        case 1: return launch_pruned<1>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
-        case 2: return launch_pruned<2>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
-        case 3: return launch_pruned<3>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
-        case 4: return launch_pruned<4>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
-        case 5: return launch_pruned<5>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
-        case 6: return launch_pruned<6>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
-        case 7: return launch_pruned<7>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
-        case 8: return launch_pruned<8>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4);
+        case 1: return launch_pruned<1>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
+        case 2: return launch_pruned<2>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
+        case 3: return launch_pruned<3>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
+        case 4: return launch_pruned<4>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
+        case 5: return launch_pruned<5>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
+        case 6: return launch_pruned<6>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
+        case 7: return launch_pruned<7>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
+        case 8: return launch_pruned<8>(I, P, H, W, K, R, lambda, O, labels, nbr, ctl, st, P4, variant);
         default: return cudaErrorInvalidValue;
         }
     }
