@@ -14,7 +14,9 @@ import os
 from typing import Optional
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhsc.so")
+# HSC_LIBRARY names another build to load (e.g. libhsc_checked.so, the build
+# with index checks); by default the library built beside this file
+LIB_PATH = os.environ.get("HSC_LIBRARY") or os.path.join(HERE, "libhsc.so")
 
 HSC_OK = 0
 HSC_ERR_INVALID_ARG = 1
@@ -110,7 +112,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libhsc.so is not built (run paper_2404_10631_gb300.build.build())")
+            raise RuntimeError("%s is not built (run paper_2404_10631_gb300.build.build())"
+                               % LIB_PATH)
         L = ctypes.CDLL(LIB_PATH)
         vp, i32, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
         L.hsc_ctx_create.argtypes = [i32, vp, sz, ctypes.POINTER(vp)]

@@ -17,6 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhsc.so")
+# the debug build: every kernel's index checks compiled in (-DHSC_BOUNDS_CHECK);
+# a failed check sets a status bit (hsc_sync reports it) and skips the access
+CHECKED_OUT_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(HERE, "libhsc_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
@@ -46,14 +50,24 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), bounds_check: bool = False,
+          sources_only=None) -> str:
+    """Compile libhsc.so (or, bounds_check, libhsc_checked.so: the debug build
+    with index checks). sources_only: compile just these translation units
+    (file names) to objects, with no link (a quick check that they build)."""
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
+    out_dir = CHECKED_OUT_DIR if bounds_check else OUT_DIR
+    lib = CHECKED_LIB if bounds_check else LIB
+    if bounds_check:
+        extra_flags = tuple(extra_flags) + ("-DHSC_BOUNDS_CHECK",)
+    os.makedirs(out_dir, exist_ok=True)
     hdrs = _headers()
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        if sources_only is not None and os.path.basename(src) not in sources_only:
+            continue
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
             cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
@@ -71,12 +85,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for out in ex.map(run, jobs):
             if verbose and out:
                 print(out, flush=True)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if sources_only is not None:
+        return out_dir
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

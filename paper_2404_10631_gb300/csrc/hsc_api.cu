@@ -752,6 +752,9 @@ hsc_status hsc_sync(hsc_ctx *ctx)
     // stages flagged follows from it: it is reported first
     if (bits & hsc::ST_TIMEOUT)
         return fail(ctx, HSC_ERR_TIMEOUT, "a bounded wait inside a kernel ran out%s");
+    if (bits & hsc::ST_BOUNDS)
+        return fail(ctx, HSC_ERR_CUDA,
+                    "an index check of the bounds-checking build failed (access skipped)%s");
     if (bits & (hsc::ST_NONFINITE_CUBE | hsc::ST_NONFINITE_MAP))
         return fail(ctx, HSC_ERR_NONFINITE, "a NaN or Inf was found in an input map%s");
     if (bits & hsc::ST_NOT_CONVERGED)

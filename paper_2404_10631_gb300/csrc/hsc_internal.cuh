@@ -16,7 +16,19 @@ enum : unsigned {
     ST_KNN_SHORT = 4u,        // a pixel found fewer than K candidates (must not happen)
     ST_NONFINITE_MAP = 8u,    // NaN/Inf in one_band given to the KNN
     ST_TIMEOUT = 16u,         // a bounded wait inside a kernel ran out
+    ST_BOUNDS = 32u,          // an index check of the HSC_BOUNDS_CHECK build failed
 };
+
+// Index checks of the debug build (-DHSC_BOUNDS_CHECK): HSC_IN_BOUNDS(cond,
+// ctl) is cond, and when cond is false it also sets ST_BOUNDS in the status
+// word, so that the caller skips the access and hsc_sync reports it; never a
+// trap. In the normal build it is true and costs nothing.
+#ifdef HSC_BOUNDS_CHECK
+#define HSC_IN_BOUNDS(cond, ctl) \
+    ((cond) ? true : (atomicOr(&(ctl)->status, ::hsc::ST_BOUNDS), false))
+#else
+#define HSC_IN_BOUNDS(cond, ctl) true
+#endif
 
 // Small control block at the start of the scratch.
 struct Control {

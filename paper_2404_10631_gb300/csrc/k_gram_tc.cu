@@ -714,8 +714,9 @@ __device__ __forceinline__ bool conv_bar_or1(int nthreads, bool pred)
 __device__ __forceinline__ void wide_drain(uint32_t tmem, int q, int lane, int j, int slot,
                                            bool written, int B, int Np, const float *isc,
                                            float *__restrict__ out, uint64_t pol,
-                                           int *range_flag)
+                                           int *range_flag, Control *ctl)
 {
+    (void)ctl;  // index checks of the bounds-checking build
     bool bad = false;
     int row0, col0, ncol;
     wide_block(j, Np, row0, col0, ncol);
@@ -733,6 +734,7 @@ __device__ __forceinline__ void wide_drain(uint32_t tmem, int q, int lane, int j
             // entry (m, col0 + c0 + e) at base_p + e * B
             float *base_p = out + (size_t)(col0 + c0) * B + m;
             const int lim = min(B - (col0 + c0), 16);       // columns in range (ncol % 16 == 0)
+            if (!HSC_IN_BOUNDS(col0 + c0 + lim <= B && m < B, ctl)) continue;
             const int first = max(0, m - (col0 + c0));      // columns >= m from here
             float prev[16];
 #pragma unroll
@@ -967,7 +969,7 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
             const int j = e % 3;
             const uint32_t old = (slots >> (2 * j)) & 3u;
             wide_drain(tmem, q, lane, j, (int)old, (written >> j) & 1u, B, Np, isc, out, pol,
-                       &range_flag);
+                       &range_flag, ctl);
             written |= 1u << j;
             slots = (slots & ~(3u << (2 * j))) | (spare << (2 * j));
             spare = old;
@@ -979,7 +981,7 @@ gram_tc_wide_kernel(const __grid_constant__ CUtensorMap tmap, const float *__res
             tc_fence_after();
             for (int j = 0; j < 3; ++j)
                 wide_drain(tmem, q, lane, j, (int)((slots >> (2 * j)) & 3u), (written >> j) & 1u,
-                           B, Np, isc, out, pol, &range_flag);
+                           B, Np, isc, out, pol, &range_flag, ctl);
         }
     }
     if (tid == 32 && ncommit > 0) {

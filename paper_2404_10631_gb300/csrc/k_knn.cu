@@ -741,6 +741,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
             const int dr = o.x, dc = o.y;
             const int i = r + dr, j = c + dc;
             if (i < lo_r || i > hi_r || j < 0 || j >= W) continue;
+            if (!HSC_IN_BOUNDS(j - tcol0 >= 0 && j - tcol0 < tw && i - lo_r < nrows, ctl)) continue;
             const Key kk = make_key(Ip, tile[(i - lo_r) * tw + (j - tcol0)], dr, dc, l2, i * W + j);
             if (cnt == 0 || key_lt(tau, kk)) tau = kk;
             if (++cnt == K) {
@@ -778,6 +779,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
             for (int j = j0; j <= j1; ++j) {
                 ++evals;
                 const int dc = c - j;
+                if (!HSC_IN_BOUNDS(j - tcol0 >= 0 && j - tcol0 < tw, ctl)) continue;
                 const float dI = __fsub_rn(Ip, trow[j]);
                 const float e = __fmul_rn(dI, dI);
                 const float st = __fmul_rn(l2, (float)(dr2 + dc * dc));
@@ -920,6 +922,7 @@ __device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float
         if (i < lo_r || i > hi_r || j < 0 || j >= W) continue;
         if (++valid == K) Lc = __fmul_rn(l2, (float)(dr * dr + dc * dc));
         const int q = i * W + j;
+        if (!HSC_IN_BOUNDS(q >= 0 && q < N, ctl)) continue;
         const float Iq = __ldg(I + q);
         bad |= !isfinite(Iq);
         consider(make_key(Ip, Iq, dr, dc, l2, q));
@@ -941,6 +944,7 @@ __device__ __noinline__ void redo_pixel(const float *__restrict__ I, const float
                 const int dc = j - c;
                 if (dr >= -kTabDr && dr <= kTabDr && dr * dr + dc * dc <= kTabR2) continue;
                 const int q = i * W + j;
+                if (!HSC_IN_BOUNDS(q >= 0 && q < N, ctl)) continue;
                 const float Iq = __ldg(I + q);
                 bad |= !isfinite(Iq);
                 consider(make_key(Ip, Iq, dr, dc, l2, q));

@@ -23,8 +23,9 @@ constexpr int kTile = 8;         // 8x8 accumulator tile per thread
 // mean works (the moments are exact in it), so the sample is summed in FP32.
 // A frame of more than 4096 pixels: 16 runs of 256 consecutive pixels spread
 // over the band (one CTA per band, 16 loads per thread issued together).
-// Up to 4096 pixels: every pixel of a frame of up to 1024, else 4 runs of 256
-// (one warp per band, 32 loads per lane issued together).
+// Up to 4096 pixels: every pixel of a frame of up to 256, else 4 runs of 64
+// (one warp per band, 8 loads per lane issued together; a snapshot frame's
+// pilot reads under a tenth of its bytes).
 // shift[B + b] receives the tensor-core path's scale for band b: the power of
 // two that brings the sample's largest |x - s_b| into [128, 256), so that a
 // pixel must deviate 256 times further than anything in the sample before its
@@ -95,19 +96,20 @@ __device__ __forceinline__ void pilot_band_block(const float *__restrict__ band,
 __device__ __forceinline__ void pilot_band_warp(const float *__restrict__ band, long N, int B,
                                                 int b, float *__restrict__ shift, Control *ctl)
 {
-    constexpr int kPer = 32, kRun = 256;  // 1024 samples at most: 4 runs of 256
+    constexpr int kPer = 8, kRun = 64;  // 256 samples at most: 4 runs of 64
+    constexpr int kJ = kRun / 32;       // loads per lane and run
     const int lane = threadIdx.x & 31;
     const bool all = N <= kPer * 32;
     const long cnt = all ? N : (long)kPer * 32;
     float x[kPer];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        // run r starts at r * 256 (every pixel) or r (N - 256) / 3
+        // run r starts at r * 64 (every pixel) or r (N - 64) / 3
         const float *run = band + (all ? (long)r * kRun : ((long)r * (N - kRun)) / 3) + lane;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < kJ; ++j) {
             const int i = r * kRun + lane + 32 * j;  // sample index
-            x[r * 8 + j] = i < cnt ? __ldg(run + 32 * j) : 0.f;
+            x[r * kJ + j] = i < cnt ? __ldg(run + 32 * j) : 0.f;
         }
     }
     float acc = 0.f;
@@ -125,7 +127,7 @@ __device__ __forceinline__ void pilot_band_warp(const float *__restrict__ band, 
     for (int r = 0; r < 4; ++r) {
         const float *run = band + (all ? (long)r * kRun : ((long)r * (N - kRun)) / 3) + lane;
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
+        for (int j = 0; j < kJ; ++j)
             if (r * kRun + lane + 32 * j < cnt) dev = fmaxf(dev, fabsf(__ldg(run + 32 * j) - s));
     }
     for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));

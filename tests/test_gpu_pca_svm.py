@@ -179,3 +179,23 @@ def test_svm_consistent_closed_form(hsc, ctx):
     np.testing.assert_allclose(P.reshape(3, -1), np.repeat(np.asarray(g["p"])[:, None], 16, 1),
                                atol=g["tol"])
     assert np.all(lab == 0)
+
+
+def test_coupling_fp32_and_fp64_errors(hsc, ctx):
+    """The per-pixel coupling solve in FP32 (the default) and in FP64
+    (HSC_SVM_COUPLE_F64) on the 416 x 512 x 128 frame, each against the FP64
+    oracle, and against each other. Both stay far inside the 1e-4 FP32 bar:
+    the error comes from the FP32 decision values, not from the solve (Q + ee^T
+    has a condition number below 25), so the FP32 solve costs nothing in
+    accuracy that the bar can see; the measured cost of the FP64 solve is
+    reported by the benchmark (coupling_f64)."""
+    f = synth.make_config(2)
+    Pref, _, _ = oracle.svm_probs(f.cube, f.model)
+    P32, _ = gpu_svm(hsc, ctx, f.cube, f.model, 0)
+    P64, _ = gpu_svm(hsc, ctx, f.cube, f.model, hsc.HSC_SVM_COUPLE_F64)
+    e32 = float(np.abs(P32 - Pref).max())
+    e64 = float(np.abs(P64 - Pref).max())
+    d = float(np.abs(P32 - P64).max())
+    print("\ncoupling: FP32 solve %.2e, FP64 solve %.2e from the oracle; %.2e apart" % (e32, e64, d))
+    assert e32 < P_TOL and e64 < P_TOL
+    assert d < 1e-5
