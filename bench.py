@@ -191,7 +191,8 @@ def kernel_source_sha(stage):
 
 def traffic_from_profiles(stage, workload):
     """DRAM bytes per launch of a stage from the committed ncu summary, if it
-    was taken on this workload and on the current source of that stage."""
+    was taken on this frame shape (workload: HxWxB) and on the current source
+    of that stage."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -498,7 +499,7 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
     # the cube, FP32 pipe for the KNN, latency for the one-CTA eigensolver)
     peaks, peak_src = load_peaks()
     work = stage_work(f, knn_evals_per_launch)
-    wname = workload_name(f)
+    wname = "%dx%dx%d" % (H, W, B)  # the shape tag of the committed traffic lines
     stages = {}
     for name, ms in stage_ms.items():
         if stage_kernels[name] == 0:
@@ -568,7 +569,7 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
                   # time than the full scan could take at the pipe's peak when above 1
                   "window_equivalent_frac": full_ops / (pruned_ms / 1e3) / 1e12 / fp32_rate}
 
-    out = {"workload": wname, "config": workload_config(f, {"frames_in_flight": F}),
+    out = {"workload": workload_name(f), "config": workload_config(f, {"frames_in_flight": F}),
            "value": value, "unit": UNIT, "ms_per_step": e_max / args.steps,
            "latency_ms": pct(per_step),
            "one_in_flight": {"value": value1, "unit": UNIT, "ms_per_step": e1_max / args.steps,

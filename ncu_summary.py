@@ -2,10 +2,11 @@
 
     python ncu_summary.py launches LOG.csv
         per kernel: launches, total time, time per launch, share (markdown)
-    python ncu_summary.py traffic LOG.csv STAGE_LAUNCHES
+    python ncu_summary.py traffic LOG.csv STAGE_LAUNCHES HxWxB
         per pipeline stage: DRAM bytes (read + write) per stage launch, as
-        "stage source_sha bytes" lines (the format bench.py reads), with
-        STAGE_LAUNCHES the number of times each stage ran in the capture
+        "stage source_sha bytes HxWxB" lines (the format bench.py reads), with
+        STAGE_LAUNCHES the number of times each stage ran in the capture and
+        HxWxB the frame it ran on
 
 LOG.csv comes from ``ncu --csv --log-file LOG.csv --metrics ...``.
 """
@@ -23,7 +24,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # kernel name prefix -> pipeline stage, and the source file each stage's
 # kernels live in (its hash tags the numbers with the code they measured)
 STAGE_OF = (("pilot_", "moments"), ("gram_tc_kernel", "moments"),
-            ("gram_tc_items_kernel", "moments"), ("gram_partial_kernel", "moments"),
+            ("gram_tc_items_kernel", "moments"), ("gram_tc_wide_kernel", "moments"),
+            ("gram_partial_kernel", "moments"),
             ("gram_reduce_kernel", "moments"), ("jacobi_kernel", "jacobi"),
             ("project_svm_kernel", "project_svm"), ("project_svm_batch_kernel", "project_svm"),
             ("normalize_kernel", "normalize"), ("normalize_batch_kernel", "normalize"),
@@ -87,22 +89,22 @@ def launches_table(path: str) -> str:
     return "\n".join(out)
 
 
-def traffic_lines(path: str, stage_launches: int) -> str:
+def traffic_lines(path: str, stage_launches: int, tag: str) -> str:
     tot = collections.defaultdict(float)
     for d in read(path):
         st = stage_of(d["kernel"])
         if st is None:
             continue
         tot[st] += d.get("dram__bytes_read.sum", 0.0) + d.get("dram__bytes_write.sum", 0.0)
-    return "\n".join("%s %s %.0f" % (st, source_sha(st), b / stage_launches)
+    return "\n".join("%s %s %.0f %s" % (st, source_sha(st), b / stage_launches, tag)
                      for st, b in sorted(tot.items()))
 
 
 def main(argv):
     if len(argv) >= 2 and argv[0] == "launches":
         print(launches_table(argv[1]))
-    elif len(argv) >= 3 and argv[0] == "traffic":
-        print(traffic_lines(argv[1], int(argv[2])))
+    elif len(argv) >= 4 and argv[0] == "traffic":
+        print(traffic_lines(argv[1], int(argv[2]), argv[3]))
     else:
         print(__doc__)
         return 2
