@@ -36,6 +36,7 @@ HSC_PCA_MINMAX = 1
 HSC_SVM_COUPLE_F64 = 2
 HSC_CLASSIFY_RAW_I = 16
 HSC_CUBE_BIP = 32
+HSC_JACOBI_ONE_CTA = 128
 
 EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_error",
             "hsc_status_string", "hsc_sync", "hsc_reserve", "hsc_scratch_bytes",

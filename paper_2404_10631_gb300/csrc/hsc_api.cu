@@ -154,8 +154,8 @@ cudaError_t moments_with_stall(hsc_ctx *ctx, const float *cube, int B, long N,
 }
 
 struct Layout {
-    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, C2, tmpI, tmpP, bsq, vk, lamk,
-        vkf, p4, total;
+    size_t ctl, shift, gram, sums, C, mu, v1, lambda1, v1f, muf, jA, jV, C2, tmpI, tmpP, bsq, vk,
+        lamk, vkf, p4, total;
     int n_part;
 };
 
@@ -193,6 +193,8 @@ Layout make_layout(const hsc_ctx *ctx, int B, long N, int k, bool need_pca, bool
         L.v1f = take(sizeof(float) * B);
         L.muf = take(sizeof(float) * B);
         L.jA = take(sizeof(float) * hsc::jacobi_global_floats(B));
+        if (hsc::jacobi_cluster_floats(B))  // the cluster sweep's V and diagonal
+            L.jV = take(sizeof(float) * hsc::jacobi_cluster_floats(B));
         if (k > 0)  // the whole path: P pixel-interleaved for the KNN's gathers
             L.p4 = take(sizeof(float4) * (size_t)((k + 3) / 4) * (size_t)N);
     }
@@ -260,6 +262,7 @@ PcaScratch carve(hsc_ctx *ctx, const Layout &L)
     s.v1f = reinterpret_cast<float *>(b + L.v1f);
     s.muf = reinterpret_cast<float *>(b + L.muf);
     s.jac_A = reinterpret_cast<float *>(b + L.jA);
+    s.jac_V = L.jV ? reinterpret_cast<float *>(b + L.jV) : nullptr;
     s.P4 = L.p4 ? reinterpret_cast<float4 *>(b + L.p4) : nullptr;
     s.n_part = L.n_part;
     return s;
@@ -329,6 +332,13 @@ constexpr int kMaxSlots = 64;
 
 // The whole path for one frame on one stream with one scratch carve-up.
 // The tuned launch parameters when they were chosen for this frame shape.
+// Kernels of one eigensolver call: the cluster sweep, when it runs, and the
+// one-CTA kernel.
+int jacobi_launches(int B, const PcaScratch &s)
+{
+    return (s.jac_V && hsc::jacobi_cluster_usable(B)) ? 2 : 1;
+}
+
 hsc::Tuning tuning_for(const hsc_ctx *ctx, int B, long N, int k)
 {
     if (ctx->tuned && ctx->tune_B == B && ctx->tune_N == N && ctx->tune_k == k) return ctx->tune;
@@ -352,7 +362,7 @@ cudaError_t launch_classify_frame(hsc_ctx *ctx, const PcaScratch &s, const float
         e = moments_with_stall(ctx, cube, B, N, s, st, fp32_pipe, tu.gram_stages);
     }
     if (e == cudaSuccess) {
-        StageTimer t(tc, HSC_STAGE_JACOBI, 1, st);
+        StageTimer t(tc, HSC_STAGE_JACOBI, jacobi_launches(B, s), st);
         e = hsc::launch_jacobi(B, s, st);
     }
     if (e == cudaSuccess) {
@@ -782,13 +792,14 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     if (st) return st;
     if ((st = check_cube(ctx, cube, B, H, W))) return st;
     if (!one_band) return fail(ctx, HSC_ERR_INVALID_ARG, "one_band is NULL%s");
-    if (flags & ~(unsigned)(HSC_PCA_MINMAX | HSC_CUBE_BIP))
+    if (flags & ~(unsigned)(HSC_PCA_MINMAX | HSC_CUBE_BIP | HSC_JACOBI_ONE_CTA))
         return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     const long N = (long)H * W;
     const bool bip = (flags & HSC_CUBE_BIP) != 0;
     Layout L = make_layout(ctx, B, N, 0, true, false, false, bip);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
+    if (flags & HSC_JACOBI_ONE_CTA) s.jac_V = nullptr;
     cudaError_t e = cudaSuccess;
     if (bip) {
         float *bsq = reinterpret_cast<float *>(static_cast<char *>(ctx->scratch) + L.bsq);
@@ -802,7 +813,7 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
         e = moments_with_stall(ctx, cube, B, N, s, ctx->stream, false, stg);
     }
     if (e == cudaSuccess) {
-        StageTimer t(ctx, HSC_STAGE_JACOBI, 1);
+        StageTimer t(ctx, HSC_STAGE_JACOBI, jacobi_launches(B, s));
         e = hsc::launch_jacobi(B, s, ctx->stream);
     }
     if (e == cudaSuccess) {
@@ -856,7 +867,7 @@ hsc_status hsc_pca_project(hsc_ctx *ctx, const float *cube, int B, int H, int W,
         e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
     }
     if (e == cudaSuccess) {
-        StageTimer t(ctx, HSC_STAGE_JACOBI, 1);
+        StageTimer t(ctx, HSC_STAGE_JACOBI, jacobi_launches(B, s));
         e = hsc::launch_jacobi(B, s, ctx->stream, n_pc);
     }
     if (e == cudaSuccess) {
@@ -954,7 +965,7 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     if ((st = check_knn(ctx, params, model->n_classes, H, W))) return st;
     if (!labels) return fail(ctx, HSC_ERR_INVALID_ARG, "labels is NULL%s");
     if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_CLASSIFY_RAW_I | HSC_CUBE_BIP |
-                            HSC_COV_FP32_PIPE))
+                            HSC_COV_FP32_PIPE | HSC_JACOBI_ONE_CTA))
         return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     const long N = (long)H * W;
     const int k = model->n_classes;
@@ -962,6 +973,7 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     Layout L = make_layout(ctx, B, N, k, true, one_band == nullptr, probs == nullptr, bip);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
+    if (flags & HSC_JACOBI_ONE_CTA) s.jac_V = nullptr;
     char *base = static_cast<char *>(ctx->scratch);
     float *I = one_band ? one_band : reinterpret_cast<float *>(base + L.tmpI);
     float *Pm = probs ? probs : reinterpret_cast<float *>(base + L.tmpP);

@@ -47,7 +47,8 @@ struct Control {
     unsigned test_stall;      // testing aid: the tensor-core Gram issues no loads and gives up
                               // its first wait after a short bound (set and cleared by the host)
     unsigned long long knn_redo_total;  // pixels the pruned KNN left to its redo pass since last read
-    unsigned pad[46];
+    unsigned long long jacobi_cluster_cycles;  // SM clock cycles of the cluster sweep (its CTA 0)
+    unsigned pad[44];
 };
 static_assert(sizeof(Control) == 256, "control block: one 256-byte slot");
 
@@ -84,6 +85,7 @@ struct PcaScratch {
     float *v1f;          // B
     float *muf;          // B
     float *jac_A;        // Jacobi work area (only when it does not fit in shared memory)
+    float *jac_V = nullptr;  // cluster sweep's output (V and its diagonal; null: one-CTA sweep)
     double *vk = nullptr;    // multi-PC: n_vec x B leading eigenvectors (row 0 = v1)
     double *lamk = nullptr;  // multi-PC: n_vec eigenvalues
     float *vkf = nullptr;    // multi-PC: float copies of vk
@@ -192,6 +194,13 @@ cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas,
 // n_vec > 1 (with s.vk, s.lamk, s.vkf set): also the next n_vec - 1 leading
 // eigenvectors, refined the same way (multi-PC projection).
 cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec = 1);
+// The first Jacobi sweep on a thread-block cluster (129 <= B <= 256): its
+// output (floats), whether the device runs it, and the padded band count.
+size_t jacobi_cluster_floats(int B);
+bool jacobi_cluster_usable(int B);
+int jacobi_cluster_n(int B);
+cudaError_t launch_jacobi_cluster(int B, const float2 *C2, float *vout, Control *ctl, float rot_tol,
+                                  cudaStream_t st);
 
 // Pass 2 over the cube: projection (if v1f != nullptr) + SVM decision values,
 // Platt, coupling (if probs != nullptr). I_raw min/max into ctl keys.

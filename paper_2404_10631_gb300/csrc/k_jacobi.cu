@@ -34,6 +34,7 @@
 #include <type_traits>
 
 #include "hsc_internal.cuh"
+#include "jacobi_rot.cuh"
 
 namespace hsc {
 namespace {
@@ -41,7 +42,7 @@ namespace {
 constexpr int kJacThreads = 1024;
 constexpr int kMaxPairs = 512;           // n <= 1024
 constexpr int kMaxRefine = 64;
-constexpr int kBasis = 16;               // columns of V rebuilt for the refinement
+constexpr int kBasis = kJacBasis;        // columns of V rebuilt for the refinement
 constexpr size_t kJacSmemLimit = 176 * 1024;  // + ~49 KB static shared <= 227 KB
 
 struct JacParams {
@@ -55,6 +56,11 @@ struct JacParams {
     int n_vec;
     double *vk, *lamk;
     float *vkf;
+    // the first sweep already run on a cluster: the basis columns in rank
+    // order (column c at pre + c pre_n) and the diagonal after it (at
+    // pre + kBasis pre_n), pre_n >= n
+    const float *pre;
+    int pre_n;
 };
 
 // j-slices of the double-float C v: each thread sums at most 16 products
@@ -168,26 +174,6 @@ __device__ __forceinline__ dfl df_warp_sum(dfl x)
     return x;
 }
 
-// Round-robin ("circle") pairing: in round t (0 <= t < n-1) pair k joins
-// a = (t + k) and b = (t - k) modulo n-1, and pair 0 joins t with n-1; every
-// pair of indices meets exactly once per sweep. The pair is kept in this
-// (a, b) orientation, not sorted: then a warp's blocks (k, l..l+31) touch
-// A entries whose banks (a_k + a_l, a_k + b_l, ... mod 32 for an odd row
-// stride) are consecutive, i.e. conflict-free.
-__device__ __forceinline__ void pair_ab(int t, int k, int n, int &a, int &b)
-{
-    if (k == 0) {
-        a = t;
-        b = n - 1;
-        return;
-    }
-    a = t + k;
-    if (a >= n - 1) a -= n - 1;
-    b = t - k + n - 1;
-    if (b >= n - 1) b -= n - 1;
-}
-
-
 // block index idx in [0, P(P+1)/2) -> (k, l), k <= l < P, row-major upper
 // triangle (with P - 1 and l + 1: the strict upper triangle of P)
 __device__ __forceinline__ void tri_of(int idx, int P, int &k, int &l)
@@ -234,55 +220,6 @@ __device__ __forceinline__ void st_sh2(uint32_t a, float x, float y)
 __device__ __forceinline__ uint32_t sh_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Symmetric Schur rotation of the 2x2 block [[app, apq], [apq, aqq]]: (c, s)
-// zero a_pq (when |a_pq| > tol; else the identity) and (dp, dq) are the new
-// diagonal entries a_pp - t a_pq, a_qq + t a_pq. FP32 intrinsics are enough
-// here: the leading vector is refined to FP64 accuracy afterwards.
-__device__ __forceinline__ void schur_angle(float app, float aqq, float apq, float tol, float &c,
-                                            float &s, float &dp, float &dq)
-{
-    c = 1.f;
-    s = 0.f;
-    dp = app;
-    dq = aqq;
-    if (fabsf(apq) > tol) {
-        const float tau = __fdividef(aqq - app, 2.f * apq);
-        float tt;
-        if (fabsf(tau) > 1e18f) tt = __fdividef(0.5f, tau);
-        else tt = copysignf(__frcp_rn(fabsf(tau) + __fsqrt_rn(fmaf(tau, tau, 1.f))), tau);
-        c = rsqrtf(fmaf(tt, tt, 1.f));
-        s = tt * c;
-        dp = fmaf(-tt, apq, app);
-        dq = fmaf(tt, apq, aqq);
-    }
-}
-
-// schur_angle with the multi-function unit's reciprocal and reciprocal
-// square root in place of the correctly rounded ones: for the small
-// Rayleigh-Ritz problem, whose eigenvectors only seed the refinement.
-__device__ __forceinline__ void schur_angle_fast(float app, float aqq, float apq, float tol,
-                                                 float &c, float &s, float &dp, float &dq)
-{
-    c = 1.f;
-    s = 0.f;
-    dp = app;
-    dq = aqq;
-    if (fabsf(apq) > tol) {
-        const float tau = __fdividef(aqq - app, 2.f * apq);
-        float tt;
-        if (fabsf(tau) > 1e18f) {
-            tt = __fdividef(0.5f, tau);
-        } else {
-            const float q = fmaf(tau, tau, 1.f);
-            tt = copysignf(__fdividef(1.f, fabsf(tau) + q * rsqrtf(q)), tau);
-        }
-        c = rsqrtf(fmaf(tt, tt, 1.f));
-        s = tt * c;
-        dp = fmaf(-tt, apq, app);
-        dq = fmaf(tt, apq, aqq);
-    }
 }
 
 __device__ float block_maxf(float v, float *red)
@@ -391,9 +328,12 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // the first sweep moves the matrix (sweep_pos below) when it fits
     const int nno = P * (P - 1) / 2 - P;             // off-diagonal blocks owning no angle
     const int OW = (P + 31) & ~31;                   // threads of the owner / diagonal blocks
-    const bool pos_sweep = !kPacked && prm.use_smem && P >= 3 && P <= kPosMaxP &&
+    const bool presweep = prm.pre != nullptr;
+    const bool pos_sweep = !presweep && !kPacked && prm.use_smem && P >= 3 && P <= kPosMaxP &&
                            nno <= 2 * (nthr - OW) + OW;
-    if (!pos_sweep) load_A();  // sweep_pos loads its own blocks
+    // Rayleigh-Ritz on the basis (below): the shared-memory form, B <= 128
+    const bool ritz = !kPacked && prm.use_smem && B <= 128 && (pos_sweep || presweep);
+    if (!pos_sweep && !presweep) load_A();  // sweep_pos loads its own blocks
     __syncthreads();
 
     // Work items fixed for the whole run: up to kBlk off-diagonal 2x2 blocks
@@ -891,7 +831,11 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     // ---- phase 0: one logged sweep, rebuilt leading columns, refinement
     long long t0 = clock64();
-    if (pos_sweep) {
+    if (presweep) {  // the diagonal after the cluster's sweep (same scaling)
+        const float *dg = prm.pre + (size_t)kBasis * prm.pre_n;
+        for (int j = tid; j < B; j += nthr) sr[j] = dg[j];
+        __syncthreads();
+    } else if (pos_sweep) {
         sweep_pos();
     } else {
         sweep(true, false);
@@ -921,8 +865,15 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     const bool deflate = B > m;
     const float theta_c = deflate ? rest / (float)(B - m) : 0.f;
     // X_c = J_0 J_1 ... J_{n-2} e_{basis_idx[c]}: one warp per column applies
-    // the logged rounds last to first, x <- J_t x on rows (a, b).
-    if (pos_sweep) {
+    // the logged rounds last to first, x <- J_t x on rows (a, b); after the
+    // cluster's sweep, the column it rebuilt (the same ranking).
+    if (presweep) {
+        for (int c = warp; c < m; c += nwarps) {
+            const float *src = prm.pre + (size_t)c * prm.pre_n;
+            float *x = X + (size_t)c * ld;
+            for (int ii = lane; ii < n; ii += 32) x[ii] = ii < B ? src[ii] : 0.f;
+        }
+    } else if (pos_sweep) {
         // In the positions of the round being undone: lane L holds the
         // entries of pairs L and L + 32 (even and odd position), rotates
         // them, then takes the entries that sigma^-1 brings from the pair
@@ -1043,7 +994,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // rough eigenvectors; the Ritz vectors of their span are far closer (the
     // leading one to ~4e-3 on the synthetic workloads, from several percent),
     // which takes the refinement from 8-13 steps to 4-5.
-    if (pos_sweep && m >= 2) {
+    if (ritz && m >= 2) {
         constexpr int kR = 16, kRl = kR + 1;
         float *Xs = smem + jac_phase0_floats(n);  // the basis (column-major, stride ld)
         const float2 *Cs = reinterpret_cast<const float2 *>(smem);  // staged C (hi, lo)
@@ -1306,7 +1257,8 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         if (!converged) atomicOr(&ctl->status, ST_NOT_CONVERGED);
         ctl->jacobi_sweeps = (unsigned)sweeps;
         ctl->refine_iters = (unsigned)(refine_iters > kMaxRefine ? kMaxRefine : refine_iters);
-        ctl->jacobi_sweep_cycles = (unsigned long long)t_sweep;
+        ctl->jacobi_sweep_cycles =
+            (unsigned long long)t_sweep + (presweep ? ctl->jacobi_cluster_cycles : 0ull);
         ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
         ctl->imin_key = float_to_key(INFINITY);
         ctl->imax_key = float_to_key(-INFINITY);
@@ -1385,6 +1337,8 @@ JacParams jac_params(int B)
     prm.rot_tol = 1e-7f;
     prm.stop_tol_final = 1e-2f;
     prm.use_smem = jac_work_floats(prm.n) * sizeof(float) <= kJacSmemLimit;
+    prm.pre = nullptr;
+    prm.pre_n = 0;
     return prm;
 }
 }  // namespace
@@ -1400,6 +1354,13 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec
     const size_t need_packed = jac_packed_smem_floats(prm.n) * sizeof(float);
     const bool packed = !prm.use_smem && need_packed <= kJacSmemLimit;
     if (!prm.use_smem && !s.jac_A) return cudaErrorInvalidValue;
+    if (s.jac_V && jacobi_cluster_floats(B) && jacobi_cluster_usable(B)) {
+        // the first sweep on a cluster; this kernel continues from its V
+        const cudaError_t e = launch_jacobi_cluster(B, s.C2, s.jac_V, s.ctl, prm.rot_tol, st);
+        if (e != cudaSuccess) return e;
+        prm.pre = s.jac_V;
+        prm.pre_n = jacobi_cluster_n(B);
+    }
     if (packed) {
         cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)need_packed);

@@ -97,15 +97,19 @@ def decaying_spectrum_cube(B=96, H=64, W=64, seed=9):
     return x.reshape(B, H, W).astype(np.float32)
 
 
+@pytest.mark.parametrize("one_cta", [False, True])
 @pytest.mark.parametrize("case", ["cfg1", "cfg2", "snapshot", "b37", "b200", "decay", "b5", "b6",
-                                  "b7", "b139", "b140", "b141"])
-def test_eigenpair_fp64_residual(hsc, ctx, case):
+                                  "b7", "b139", "b140", "b141", "b97", "b112", "b250", "b256"])
+def test_eigenpair_fp64_residual(hsc, ctx, case, one_cta):
     """The refinement's claim: (v1, lambda1) is an eigenpair of the GPU's own
     FP64 covariance to ||C v - lambda v|| <= 2e-13 ||C|| (checked in FP64 on
     the host), and lambda1 is its largest eigenvalue: whether the work area
     sits in shared memory (B <= 142) or in global memory (B = 200), on a
-    slowly decaying spectrum, and at the band counts where the first sweep
-    changes form (3 pairs, 70 pairs, 71 pairs)."""
+    slowly decaying spectrum, at the band counts where the first sweep
+    changes form (3 pairs, 70 pairs, 71 pairs), and for 129 <= B <= 256 after
+    the first sweep on a thread-block cluster (band counts padded to the
+    cluster's multiple: 139, 141, 200, 250; none: 256) as well as on one CTA
+    (HSC_JACOBI_ONE_CTA)."""
     if case.startswith("cfg"):
         cube = synth.make_config(int(case[3])).cube
     elif case == "snapshot":
@@ -119,7 +123,9 @@ def test_eigenpair_fp64_residual(hsc, ctx, case):
         cube = synth.make_frame(B, 36, 40, B, sigma=0.03).cube
     else:
         cube = decaying_spectrum_cube()
-    _, v, lam = gpu_pca(hsc, ctx, cube)
+    if one_cta and not 129 <= cube.shape[0] <= 256:
+        pytest.skip("the one-CTA flag changes nothing outside 129 <= B <= 256")
+    _, v, lam = gpu_pca(hsc, ctx, cube, flags=1 | (hsc.HSC_JACOBI_ONE_CTA if one_cta else 0))
     _, C = hsc.hsc_pca_covariance(ctx, to_dev(cube))
     ctx.sync()
     C = C.cpu().numpy()
@@ -128,6 +134,34 @@ def test_eigenpair_fp64_residual(hsc, ctx, case):
     assert abs(np.linalg.norm(v) - 1.0) < 1e-14
     assert np.linalg.norm(r) <= 2e-13 * cn, np.linalg.norm(r) / cn
     assert abs(lam - np.linalg.eigvalsh(C).max()) <= 1e-12 * cn
+
+
+@pytest.mark.parametrize("B", [144, 256])
+def test_cluster_sweep_matches_one_cta(hsc, ctx, B):
+    """For 129 <= B <= 256 the eigensolver's first sweep runs on a thread-block
+    cluster (two kernels in the Jacobi stage), with HSC_JACOBI_ONE_CTA on one
+    CTA (one kernel). The sweeps round differently, but both eigenpairs are
+    refined against the same FP64 covariance, so they agree to its FP64
+    tolerance, and both match the oracle's FP64 Jacobi on the cube."""
+    f = synth.make_frame(31 + B, 48, 56, B, sigma=0.01, n_seeds=32, n_gauss=2, wide=True)
+    ref = oracle.pca_one_band(f.cube)
+    out = {}
+    for one_cta in (False, True):
+        ctx.profile(True)
+        ctx.profile_read()
+        I, v, lam = gpu_pca(hsc, ctx, f.cube, flags=1 | (hsc.HSC_JACOBI_ONE_CTA if one_cta else 0))
+        _, kern, _ = ctx.profile_read()
+        ctx.profile(False)
+        assert kern["jacobi"] == (1 if one_cta else 2)
+        cos = abs(float(v @ ref["v1"]))
+        assert np.sqrt(max(0.0, 1 - cos * cos)) < V1_ANGLE
+        assert lam == pytest.approx(ref["lambda1"], rel=1e-5)
+        assert np.abs(I - ref["I_norm"]).max() < I_TOL
+        out[one_cta] = (v, lam)
+    (v0, l0), (v1, l1) = out[False], out[True]
+    assert float(v0 @ v1) > 0
+    assert np.abs(v0 - v1).max() < 1e-11
+    assert abs(l0 - l1) <= 1e-12 * abs(l1)
 
 
 def gpu_svm(hsc, ctx, cube, model, flags=0):
