@@ -8,8 +8,9 @@ lambda = 1, with the library's defaults: the covariance on the tensor cores
 (FP16 hi/lo parts, FP32 accumulation), the exact pruned KNN search. The
 steps are a stream of frames: step i runs on context i % F
 (--frames-in-flight F, default 8; each context has its own CUDA stream,
-scratch and outputs), so while one frame's eigensolver occupies one SM the
-other frames' GPU-wide stages run beside it. "value" is pixels/s over the K
+scratch and outputs), so while one frame's eigensolver occupies one SM (or,
+for 129-256 bands, its first sweep a cluster of 16) the other frames'
+GPU-wide stages run beside it. "value" is pixels/s over the K
 steps, "latency_ms" the per-frame latency in that stream, "one_in_flight"
 the same steps on one context, and "plain_fp32" the plain per-frame FP32
 path on the same GPU: the covariance on the FP32 pipe (HSC_COV_FP32_PIPE),
@@ -520,8 +521,10 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
                               "evaluated; peak: " + fp32_peak_note)
         else:
             entry["us_per_launch"] = 1e3 * ms
-            entry["note"] = ("one CTA (one SM) per frame: a latency, no roofline; with frames in "
-                             "flight the other frames' GPU-wide stages run beside it")
+            entry["note"] = ("a latency, no roofline: one CTA per frame up to 128 bands; for "
+                             "129-256 bands the first sweep on a 16-CTA cluster, then one CTA; "
+                             "with frames in flight the other frames' GPU-wide stages run "
+                             "beside it")
         if name == "moments":
             flops = 2.0 * B * B * N
             entry["tensor"] = {"algorithmic_flops": flops,
@@ -545,7 +548,7 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
                 "ms_per_launch": d["ms_per_launch"],
                 "rule": "the stage with the largest device time among those with a roofline "
                         "(moments, projection + SVM, normalisation: HBM; KNN: FP32 pipe); the "
-                        "one-CTA eigensolver is a latency, reported in stages.jacobi"}
+                        "eigensolver is a latency, reported in stages.jacobi"}
     full_ops = 4.0 * knn_pairs(H, W, f.window_rows)
     full_ach = full_ops / (full_ms_launch / 1e3) / 1e12
     knn_full = {"search": "full window (the paper's procedure: every window candidate)",

@@ -2,11 +2,12 @@
 
     python ncu_summary.py launches LOG.csv
         per kernel: launches, total time, time per launch, share (markdown)
-    python ncu_summary.py traffic LOG.csv STAGE_LAUNCHES HxWxB
+    python ncu_summary.py traffic LOG.csv STAGE_LAUNCHES HxWxB [FIRST-LAST]
         per pipeline stage: DRAM bytes (read + write) per stage launch, as
         "stage source_sha bytes HxWxB" lines (the format bench.py reads), with
-        STAGE_LAUNCHES the number of times each stage ran in the capture and
-        HxWxB the frame it ran on
+        STAGE_LAUNCHES the number of times each stage ran in the captured
+        launches counted (all of them, or the capture's launch IDs FIRST to
+        LAST) and HxWxB the frame it ran on
 
 LOG.csv comes from ``ncu --csv --log-file LOG.csv --metrics ...``.
 """
@@ -27,11 +28,13 @@ STAGE_OF = (("pilot_", "moments"), ("gram_tc_kernel", "moments"),
             ("gram_tc_items_kernel", "moments"), ("gram_tc_wide_kernel", "moments"),
             ("gram_partial_kernel", "moments"),
             ("gram_reduce_kernel", "moments"), ("jacobi_kernel", "jacobi"),
+            ("jacobi_cluster_kernel", "jacobi"),
             ("project_svm_kernel", "project_svm"), ("project_svm_batch_kernel", "project_svm"),
             ("normalize_kernel", "normalize"), ("normalize_batch_kernel", "normalize"),
             ("knn_pruned_kernel", "knn"), ("knn_redo_kernel", "knn"),
             ("knn_redo_batch_kernel", "knn"), ("knn_kernel", "knn_full"))
-SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu"), "jacobi": ("k_jacobi.cu",),
+SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu"),
+             "jacobi": ("k_jacobi.cu", "k_jacobi_cluster.cu", "jacobi_rot.cuh"),
              "project_svm": ("k_project_svm.cu",), "normalize": ("k_project_svm.cu",),
              "knn": ("k_knn.cu",), "knn_full": ("k_knn.cu",)}
 
@@ -60,7 +63,7 @@ def read(path: str):
     launches = collections.OrderedDict()
     for r in rows[1:]:
         key = int(r[idi])
-        d = launches.setdefault(key, {"kernel": kernel_base(r[ki])})
+        d = launches.setdefault(key, {"kernel": kernel_base(r[ki]), "id": key})
         d[r[mi]] = float(r[vi].replace(",", ""))
     return list(launches.values())
 
@@ -89,9 +92,11 @@ def launches_table(path: str) -> str:
     return "\n".join(out)
 
 
-def traffic_lines(path: str, stage_launches: int, tag: str) -> str:
+def traffic_lines(path: str, stage_launches: int, tag: str, ids=None) -> str:
     tot = collections.defaultdict(float)
     for d in read(path):
+        if ids is not None and not ids[0] <= d["id"] <= ids[1]:
+            continue
         st = stage_of(d["kernel"])
         if st is None:
             continue
@@ -104,7 +109,8 @@ def main(argv):
     if len(argv) >= 2 and argv[0] == "launches":
         print(launches_table(argv[1]))
     elif len(argv) >= 4 and argv[0] == "traffic":
-        print(traffic_lines(argv[1], int(argv[2]), argv[3]))
+        ids = tuple(int(v) for v in argv[4].split("-")) if len(argv) >= 5 else None
+        print(traffic_lines(argv[1], int(argv[2]), argv[3], ids))
     else:
         print(__doc__)
         return 2
