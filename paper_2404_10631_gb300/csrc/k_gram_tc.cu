@@ -1,16 +1,13 @@
 // Covariance Gram on the 5th-generation tensor cores (Section II.C.2 step (ii),
 // III.A.2.b): G = sum_p y_p y_p^T over the shifted pixels y = x - s, B <= 256.
 //
-// B <= 128 (the description below): one launch, M = N = B. 128 < B <= 256:
-// two launches, one per 128-band half of the rows of G (rows 0-127 x every
-// column, rows 128-255 x columns 128-255: the upper triangle is all the
-// reduction reads); each converts all B bands of a chunk and multiplies the
-// half's rows by the columns it needs (N <= 256). There a single hi.hi^T
-// accumulator and the cross-term accumulator fill the 512 TMEM columns, the
-// staging ring has 2 stages and the operands 1, to fit 256-row tiles in
-// shared memory; the cube is read once per launch.
+// B <= 128: gram_tc_kernel (described here), M = N = B. 128 < B <= 256:
+// gram_tc_wide_kernel (described where it is defined): one launch, each
+// chunk read and converted once, three 128-column TMEM blocks drained by
+// epilogue warps while the MMAs go on. Frames a tensor map cannot describe
+// take gram_tc_items_kernel (the same arithmetic, cp.async copies).
 //
-// Per CTA (one per SM, a contiguous range of 64-pixel chunks):
+// gram_tc_kernel, per CTA (one per SM, a contiguous range of 64-pixel chunks):
 //   warp 0   TMA producer: each chunk is two 32-pixel x B-band FP32 boxes
 //            (128-byte swizzled) into a 4-stage shared ring;
 //   warp 1   TMEM owner and MMA issuer: for every chunk, 4 K-steps of
@@ -73,22 +70,20 @@ constexpr int kFbAcc = 8;                // FP32 recompute: entries per thread p
 constexpr int kFbLd = kChunk + 1;        // FP32 recompute: padded staging row
 constexpr int kNarrowConvWarps = 8;      // B <= 128: converter warps (two per band row)
 
-// B <= 128: 128 converted rows, 4 staging stages, 2 operand stages, three
-// hi.hi^T accumulators (columns 0, 128, 256) and the cross terms at 384, 8
-// converter warps. 128 < B <= 256: 256 rows, 2 + 1 stages, hi.hi^T at 0 and
-// cross at 256, 8 converter warps (a thread per 32-pixel box of band rows b
-// and b + 128; with 4 warps, one thread per row pair and both boxes, the
-// 1024 x 1024 x 256 frame's moments took 0.95 ms instead of 0.60).
-template <bool kWide, int kSt = (kWide ? 2 : 4)>
+// B <= 128 (gram_tc_kernel and gram_tc_items_kernel): 128 converted rows,
+// kSt staging stages (3 or 4, the autotuner's choice), 2 operand stages,
+// three hi.hi^T accumulators (TMEM columns 0, 128, 256) and the cross terms
+// at 384, 8 converter warps.
+template <int kSt = 4>
 struct Cfg {
-    static constexpr int kRows = kWide ? 256 : 128;
+    static constexpr int kRows = 128;
     static constexpr int kStages = kSt;
-    static constexpr int kOpStages = kWide ? 1 : 2;
-    static constexpr int kAccHH = kWide ? 1 : 3;
-    static constexpr int kConvWarps = kWide ? 8 : kNarrowConvWarps;
+    static constexpr int kOpStages = 2;
+    static constexpr int kAccHH = 3;
+    static constexpr int kConvWarps = kNarrowConvWarps;
     static constexpr int kThreads = 64 + 32 * kConvWarps;
     static constexpr int kParts = kConvWarps / 4;           // threads per band row
-    static constexpr uint32_t kXCol = kWide ? 256u : 384u;
+    static constexpr uint32_t kXCol = 384u;
     static constexpr uint32_t kBoxBytes = kRows * 128;      // one 32-pixel box slot
     static constexpr uint32_t kStageBytes = 2 * kBoxBytes;  // two boxes per chunk
     static constexpr uint32_t kOpBytes = kRows * 128;       // one fp16 operand tile
@@ -146,10 +141,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <bool kWide, int kSt>
+template <int kSt>
 struct __align__(8) Bars {
-    uint64_t full[Cfg<kWide, kSt>::kStages], empty[Cfg<kWide, kSt>::kStages];
-    uint64_t op_full[Cfg<kWide, kSt>::kOpStages], op_empty[Cfg<kWide, kSt>::kOpStages];
+    uint64_t full[Cfg<kSt>::kStages], empty[Cfg<kSt>::kStages];
+    uint64_t op_full[Cfg<kSt>::kOpStages], op_empty[Cfg<kSt>::kOpStages];
     uint64_t done;     // a segment's MMAs have completed (one commit per segment)
     uint64_t drained;  // the epilogue has read a segment's accumulators (128 arrivals)
 };
@@ -334,13 +329,13 @@ __device__ void fp32_recompute(const float *__restrict__ cube, int B, long N,
 // staging layout differs (band b's two 32-pixel rows at 128-byte rows 2b
 // and 2b + 1, against b and kRows + b); the arithmetic does not.
 template <bool k3D, int kSt>
-__global__ void __launch_bounds__(Cfg<false, kSt>::kThreads, 1)
+__global__ void __launch_bounds__(Cfg<kSt>::kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ cube, int B,
                int row_base, int col_base, int Nn, int write_sums, long N, long total_chunks,
                long per, const float *__restrict__ shift, float *__restrict__ gram_part,
                float *__restrict__ sum_part, Control *ctl)
 {
-    using G = Cfg<false, kSt>;
+    using G = Cfg<kSt>;
     constexpr int kRows = G::kRows, kStages = G::kStages, kOpStages = G::kOpStages;
     constexpr int kAccHH = G::kAccHH, kThreads = G::kThreads, kParts = G::kParts;
     constexpr uint32_t kBoxBytes = G::kBoxBytes, kStageBytes = G::kStageBytes;
@@ -350,7 +345,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *staging = base;                                 // kStages x 2 boxes
     unsigned char *ops = base + kStages * kStageBytes;             // kOpStages x (hi, lo)
-    __shared__ Bars<false, kSt> bars;
+    __shared__ Bars<kSt> bars;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, range_flag, stall_flag;
     __shared__ float sh[kRows], sc[kRows], isc[kRows];
@@ -1170,12 +1165,12 @@ __device__ __forceinline__ GramItem get_item(const BatchFrame &one,
 // staging layout the TMA would write, and one named barrier per chunk among
 // them orders the copies with their readers (and makes every exit uniform).
 template <int kSt>
-__global__ void __launch_bounds__(Cfg<false, kSt>::kThreads, 1)
+__global__ void __launch_bounds__(Cfg<kSt>::kThreads, 1)
 gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames,
                      const GramItem *__restrict__ items, const int *__restrict__ cta_items,
                      int n_items, int B)
 {
-    using G = Cfg<false, kSt>;
+    using G = Cfg<kSt>;
     constexpr int kStages = G::kStages, kOpStages = G::kOpStages, kAccHH = G::kAccHH;
     constexpr int kParts = G::kParts, kConv = 32 * G::kConvWarps;
     constexpr uint32_t kBoxBytes = G::kBoxBytes, kStageBytes = G::kStageBytes;
@@ -1187,7 +1182,7 @@ gram_tc_items_kernel(const BatchFrame one, const BatchFrame *__restrict__ frames
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char *staging = base;
     unsigned char *ops = base + kStages * kStageBytes;
-    __shared__ Bars<false, kSt> bars;  // full / empty unused: copies complete by groups
+    __shared__ Bars<kSt> bars;  // full / empty unused: copies complete by groups
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag, range_item;
     __shared__ float isc_sh[128], bsum_sh[kParts - 1][128];
@@ -1454,7 +1449,7 @@ bool gram_tc_usable(const float *cube, int B, long N)
            (reinterpret_cast<uintptr_t>(cube) & 3u) == 0;
 }
 
-size_t gram_tc_smem_bytes() { return Cfg<false>::kSmem; }
+size_t gram_tc_smem_bytes() { return Cfg<>::kSmem; }
 
 // One tensor-core CTA per SM at most, each on a contiguous chunk range of
 // `per` chunks; the last partial may hold fewer.
@@ -1478,10 +1473,10 @@ template <bool k3D, int kSt>
 void launch_narrow(const CUtensorMap &map, const float *cube, int B, int Np, long N, long total,
                    long per, int parts, const PcaScratch &s, cudaStream_t st)
 {
-    const size_t smem = Cfg<false, kSt>::kSmem;
+    const size_t smem = Cfg<kSt>::kSmem;
     cudaFuncSetAttribute(gram_tc_kernel<k3D, kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    gram_tc_kernel<k3D, kSt><<<parts, Cfg<false, kSt>::kThreads, smem, st>>>(
+    gram_tc_kernel<k3D, kSt><<<parts, Cfg<kSt>::kThreads, smem, st>>>(
         map, cube, B, 0, 0, Np, 1, N, total, per, s.shift, s.gram_part, s.sum_part, s.ctl);
 }
 
@@ -1513,10 +1508,10 @@ template <int kSt>
 void launch_items(const BatchFrame &one, const BatchFrame *frames, const GramItem *items,
                   const int *cta_items, int n_items, int B, int grid, cudaStream_t st)
 {
-    const size_t smem = Cfg<false, kSt>::kSmem;
+    const size_t smem = Cfg<kSt>::kSmem;
     cudaFuncSetAttribute(gram_tc_items_kernel<kSt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    gram_tc_items_kernel<kSt><<<grid, Cfg<false, kSt>::kThreads, smem, st>>>(
+    gram_tc_items_kernel<kSt><<<grid, Cfg<kSt>::kThreads, smem, st>>>(
         one, frames, items, cta_items, n_items, B);
 }
 }  // namespace
