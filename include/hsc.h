@@ -120,11 +120,12 @@ typedef struct {
  * scratch (4 B H W more bytes; the copy is timed with the moments stage) and
  * the results equal those of the band-sequential call */
 #define HSC_CUBE_BIP 32u
-/* flag for hsc_pca_one_band / hsc_classify: run the Jacobi eigensolver's
- * first sweep on one CTA even where (129 <= B <= 256) it would run on a
- * thread-block cluster of 16 CTAs (8 where the device schedules no clusters
- * of 16) (an A/B switch: both reach the same eigenpair to the refinement's
- * FP64-level tolerance) */
+/* flag for hsc_pca_one_band / hsc_classify: the eigensolver's plain form,
+ * its basis from one Jacobi sweep on one CTA whatever the band count, where
+ * by default B <= 128 takes two block power steps on C and 129 <= B <= 256 runs
+ * the sweep on a thread-block cluster of 16 CTAs (8 where the device schedules
+ * no clusters of 16). An A/B switch: every form reaches the same eigenpair to
+ * the refinement's FP64-level tolerance. */
 #define HSC_JACOBI_ONE_CTA 128u
 
 /* Create a context on `device`. cuda_stream: a cudaStream_t to launch on, or

@@ -336,7 +336,7 @@ constexpr int kMaxSlots = 64;
 // one-CTA kernel.
 int jacobi_launches(int B, const PcaScratch &s)
 {
-    return (s.jac_V && hsc::jacobi_cluster_usable(B)) ? 2 : 1;
+    return (s.jac_V && !s.jac_plain && hsc::jacobi_cluster_usable(B)) ? 2 : 1;
 }
 
 hsc::Tuning tuning_for(const hsc_ctx *ctx, int B, long N, int k)
@@ -799,7 +799,10 @@ hsc_status hsc_pca_one_band(hsc_ctx *ctx, const float *cube, int B, int H, int W
     Layout L = make_layout(ctx, B, N, 0, true, false, false, bip);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
-    if (flags & HSC_JACOBI_ONE_CTA) s.jac_V = nullptr;
+    if (flags & HSC_JACOBI_ONE_CTA) {
+        s.jac_V = nullptr;
+        s.jac_plain = true;
+    }
     cudaError_t e = cudaSuccess;
     if (bip) {
         float *bsq = reinterpret_cast<float *>(static_cast<char *>(ctx->scratch) + L.bsq);
@@ -973,7 +976,10 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
     Layout L = make_layout(ctx, B, N, k, true, one_band == nullptr, probs == nullptr, bip);
     if ((st = ensure_scratch(ctx, L.total))) return st;
     PcaScratch s = carve(ctx, L);
-    if (flags & HSC_JACOBI_ONE_CTA) s.jac_V = nullptr;
+    if (flags & HSC_JACOBI_ONE_CTA) {
+        s.jac_V = nullptr;
+        s.jac_plain = true;
+    }
     char *base = static_cast<char *>(ctx->scratch);
     float *I = one_band ? one_band : reinterpret_cast<float *>(base + L.tmpI);
     float *Pm = probs ? probs : reinterpret_cast<float *>(base + L.tmpP);

@@ -85,7 +85,8 @@ struct PcaScratch {
     float *v1f;          // B
     float *muf;          // B
     float *jac_A;        // Jacobi work area (only when it does not fit in shared memory)
-    float *jac_V = nullptr;  // cluster sweep's output (V and its diagonal; null: one-CTA sweep)
+    float *jac_V = nullptr;  // cluster sweep's output (basis, diagonal, log; null: no cluster)
+    bool jac_plain = false;  // the eigensolver's basis from one sweep on one CTA, whatever B
     double *vk = nullptr;    // multi-PC: n_vec x B leading eigenvectors (row 0 = v1)
     double *lamk = nullptr;  // multi-PC: n_vec eigenvalues
     float *vkf = nullptr;    // multi-PC: float copies of vk

@@ -61,6 +61,9 @@ struct JacParams {
     // pre + kBasis pre_n), pre_n >= n
     const float *pre;
     int pre_n;
+    // 1: the basis from one Jacobi sweep even where block power steps would
+    // give it (B <= 128)
+    int sweep_basis;
 };
 
 // j-slices of the double-float C v: each thread sums at most 16 products
@@ -329,11 +332,15 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     const int nno = P * (P - 1) / 2 - P;             // off-diagonal blocks owning no angle
     const int OW = (P + 31) & ~31;                   // threads of the owner / diagonal blocks
     const bool presweep = prm.pre != nullptr;
-    const bool pos_sweep = !presweep && !kPacked && prm.use_smem && P >= 3 && P <= kPosMaxP &&
-                           nno <= 2 * (nthr - OW) + OW;
+    // B <= 128 in shared memory: the basis from two block power steps on C
+    // (below) instead of a first sweep; a zero C (a flat cube) keeps the sweep
+    const bool power = !presweep && !kPacked && prm.use_smem && B <= 128 && !prm.sweep_basis &&
+                       dmax > 0.f;
+    const bool pos_sweep = !presweep && !power && !kPacked && prm.use_smem && P >= 3 &&
+                           P <= kPosMaxP && nno <= 2 * (nthr - OW) + OW;
     // Rayleigh-Ritz on the basis (below): the shared-memory form, B <= 128
-    const bool ritz = !kPacked && prm.use_smem && B <= 128 && (pos_sweep || presweep);
-    if (!pos_sweep && !presweep) load_A();  // sweep_pos loads its own blocks
+    const bool ritz = !kPacked && prm.use_smem && B <= 128 && (pos_sweep || presweep || power);
+    if (!pos_sweep && !presweep && !power) load_A();  // sweep_pos loads its own blocks
     __syncthreads();
 
     // Work items fixed for the whole run: up to kBlk off-diagonal 2x2 blocks
@@ -827,11 +834,37 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     long long t_sweep = 0, t_refine = 0;
     int sweeps = 0, refine_iters = 0;
-    bool converged = false;
+    bool converged = false, fell_back = false;
 
-    // ---- phase 0: one logged sweep, rebuilt leading columns, refinement
+    // C's (hi, lo) pairs staged in shared memory (the space of A and the log,
+    // dead once the basis is built) for the Rayleigh-Ritz step and the refinement
+    auto stage_c = [&]() {
+        const float4 *src = reinterpret_cast<const float4 *>(C2);
+        float4 *dst = reinterpret_cast<float4 *>(Cs2);
+        const int n4 = (B * B) / 2;
+        constexpr int kU = 8;
+        for (int q0 = tid; q0 < n4; q0 += kU * nthr) {
+            float4 tmp[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (q0 + u * nthr < n4) tmp[u] = src[q0 + u * nthr];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (q0 + u * nthr < n4) dst[q0 + u * nthr] = tmp[u];
+        }
+        if ((B * B) & 1 && tid == 0) Cs2[B * B - 1] = C2[B * B - 1];
+    };
+
+    // ---- phase 0: the basis (block power steps, or one logged sweep and the
+    // rebuilt leading columns), Rayleigh-Ritz, refinement
     long long t0 = clock64();
-    if (presweep) {  // the diagonal after the cluster's sweep (same scaling)
+    if (power) {  // C's diagonal in the units of A
+        stage_c();
+        __syncthreads();
+        const float2 *Cp = reinterpret_cast<const float2 *>(smem);
+        for (int j = tid; j < B; j += nthr) sr[j] = Cp[(size_t)j * B + j].x * inv_p2;
+        __syncthreads();
+    } else if (presweep) {  // the diagonal after the cluster's sweep (same scaling)
         const float *dg = prm.pre + (size_t)kBasis * prm.pre_n;
         for (int j = tid; j < B; j += nthr) sr[j] = dg[j];
         __syncthreads();
@@ -842,7 +875,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         for (int j = tid; j < B; j += nthr) sr[j] = A[aix(j, j)];
         __syncthreads();
     }
-    sweeps = 1;
+    sweeps = power ? 0 : 1;
     const int m = B < kBasis ? B : kBasis;
     // rank the diagonal (ties: smaller index first); the m largest form the
     // basis, the mean of the rest is theta_c
@@ -863,11 +896,19 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     }
     rest = block_sumf(rest, fred);
     const bool deflate = B > m;
-    const float theta_c = deflate ? rest / (float)(B - m) : 0.f;
+    float theta_c = deflate ? rest / (float)(B - m) : 0.f;  // (power: set after Rayleigh-Ritz)
     // X_c = J_0 J_1 ... J_{n-2} e_{basis_idx[c]}: one warp per column applies
     // the logged rounds last to first, x <- J_t x on rows (a, b); after the
     // cluster's sweep, the column it rebuilt (the same ranking).
-    if (presweep) {
+    if (power) {  // the first power step: X_c = C e_{basis_idx[c]}, C's column
+        const float2 *Cp = reinterpret_cast<const float2 *>(smem);
+        for (int c = warp; c < m; c += nwarps) {
+            const int j0 = basis_idx[c];
+            float *x = smem + jac_phase0_floats(n) + (size_t)c * ld;
+            for (int ii = lane; ii < n; ii += 32)
+                x[ii] = ii < B ? Cp[(size_t)ii * B + j0].x * inv_p2 : 0.f;
+        }
+    } else if (presweep) {
         for (int c = warp; c < m; c += nwarps) {
             const float *src = prm.pre + (size_t)c * prm.pre_n;
             float *x = X + (size_t)c * ld;
@@ -969,23 +1010,58 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         vl[ii] = 0.f;
     }
     // A and the log are dead: stage C's (hi, lo) pairs in their space
-    if (prm.use_smem) {
-        const float4 *src = reinterpret_cast<const float4 *>(C2);
-        float4 *dst = reinterpret_cast<float4 *>(Cs2);
-        const int n4 = (B * B) / 2;
-        constexpr int kU = 8;
-        for (int q0 = tid; q0 < n4; q0 += kU * nthr) {
-            float4 tmp[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (q0 + u * nthr < n4) tmp[u] = src[q0 + u * nthr];
-#pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (q0 + u * nthr < n4) dst[q0 + u * nthr] = tmp[u];
-        }
-        if ((B * B) & 1 && tid == 0) Cs2[B * B - 1] = C2[B * B - 1];
-    }
+    if (prm.use_smem && !power) stage_c();
     __syncthreads();
+    if (power) {
+        // The basis C E (E the coordinate vectors of C's 16 largest diagonal
+        // entries: one power step from them) made orthonormal by classical
+        // Gram-Schmidt applied twice, in FP32 (the columns of C are nearly
+        // parallel, so one pass would leave them far from orthogonal). The
+        // norms ride along with the dot products: x_c's length before the
+        // first pass and after it (for the second pass's Pythagorean update),
+        // so a column takes four barriers. A column left with under 1e-5 of
+        // its length lies in the span of the ones before and is set to zero,
+        // which the Rayleigh-Ritz step and the refinement take as an empty
+        // direction. Pointers are formed from the shared array itself, so the
+        // accesses compile to shared-memory instructions.
+        float *Xp = smem + jac_phase0_floats(n);  // the basis, stride ld
+        __shared__ float s_nrm[2];
+        for (int c = 0; c < m; ++c) {
+            float *xc = Xp + (size_t)c * ld;
+            for (int pass = 0; pass < 2; ++pass) {
+                // dots with the columns before (warp j) and this column's
+                // squared length (warp c)
+                for (int j = warp; j <= c; j += nwarps) {
+                    const float *xj = Xp + (size_t)j * ld;
+                    float d = 0.f;
+                    for (int ii = lane; ii < B; ii += 32) d = fmaf(xj[ii], xc[ii], d);
+                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                    if (lane == 0) {
+                        if (j < c) coef[j] = d;
+                        else s_nrm[pass] = d;
+                    }
+                }
+                __syncthreads();
+                // x_c <- x_c - sum_j (x_j . x_c) x_j; after the second pass
+                // divided by its length, |x|^2 - sum_j (x_j . x)^2
+                float q = s_nrm[pass];
+                for (int j = 0; j < c; ++j) q = fmaf(-coef[j], coef[j], q);
+                const float sc = pass == 0 ? 1.f
+                                           : ((q > 1e-10f * s_nrm[0] && q > 0.f) ? rsqrtf(q) : 0.f);
+                for (int ii = tid; ii < B; ii += nthr) {
+                    float a = xc[ii];
+                    for (int j = 0; j < c; ++j) a = fmaf(-coef[j], Xp[(size_t)j * ld + ii], a);
+                    xc[ii] = a * sc;
+                }
+                __syncthreads();
+            }
+        }
+        for (int ii = tid; ii < B; ii += nthr) {  // column 0 starts the refinement
+            vh[ii] = Xp[ii];
+            vl[ii] = 0.f;
+        }
+        __syncthreads();
+    }
     long long t1 = clock64();
     t_sweep += t1 - t0;
     // ---- Rayleigh-Ritz on the rebuilt columns (B <= 128): H = X^T C X in
@@ -1147,6 +1223,17 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         }
         __syncthreads();
     }
+    if (power && deflate) {
+        // the unrebuilt eigenvalues as one cluster at their mean: C's trace
+        // less the Ritz values, over the other B - m directions
+        float tr = 0.f;
+        for (int j = tid; j < B; j += nthr) tr += sr[j];
+        tr = block_sumf(tr, fred);
+        float ts = 0.f;
+        for (int c = tid; c < m; c += nthr) ts += th[c];
+        ts = block_sumf(ts, fred);
+        theta_c = (tr - ts) / (float)(B - m);
+    }
     if (prm.use_smem && !kPacked) {
         // the same pointers, formed from the shared array itself so that
         // the refinement's accesses compile to shared-memory instructions
@@ -1161,6 +1248,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 
     // ---- fallback: sweeps from C with V accumulated, refinement on all columns
     if (!converged) {
+        fell_back = true;
         t0 = clock64();
         load_A();
         for (int idx = tid; idx < n * ld; idx += nthr) Vt[idx] = (idx % ld == idx / ld) ? 1.f : 0.f;
@@ -1269,7 +1357,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // largest diagonal's column after the sweep) by the same deflated
     // correction aimed at column j, then the same sign rule. Phase 0's basis
     // only (the fallback rebuilds none).
-    if (prm.n_vec > 1 && sweeps == 1) {
+    if (prm.n_vec > 1 && !fell_back) {
         const bool sm_basis = prm.use_smem && !kPacked;
         const size_t xo = jac_phase0_floats(n);
         const float *bas = sm_basis ? smem + xo : X;
@@ -1339,6 +1427,7 @@ JacParams jac_params(int B)
     prm.use_smem = jac_work_floats(prm.n) * sizeof(float) <= kJacSmemLimit;
     prm.pre = nullptr;
     prm.pre_n = 0;
+    prm.sweep_basis = 0;
     return prm;
 }
 }  // namespace
@@ -1354,7 +1443,8 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec
     const size_t need_packed = jac_packed_smem_floats(prm.n) * sizeof(float);
     const bool packed = !prm.use_smem && need_packed <= kJacSmemLimit;
     if (!prm.use_smem && !s.jac_A) return cudaErrorInvalidValue;
-    if (s.jac_V && jacobi_cluster_floats(B) && jacobi_cluster_usable(B)) {
+    prm.sweep_basis = s.jac_plain ? 1 : 0;
+    if (s.jac_V && !s.jac_plain && jacobi_cluster_floats(B) && jacobi_cluster_usable(B)) {
         // the first sweep on a cluster; this kernel continues from its V
         const cudaError_t e = launch_jacobi_cluster(B, s.C2, s.jac_V, s.ctl, prm.rot_tol, st);
         if (e != cudaSuccess) return e;

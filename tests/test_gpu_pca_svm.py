@@ -108,8 +108,9 @@ def test_eigenpair_fp64_residual(hsc, ctx, case, one_cta):
     slowly decaying spectrum, at the band counts where the first sweep
     changes form (3 pairs, 70 pairs, 71 pairs), and for 129 <= B <= 256 after
     the first sweep on a thread-block cluster (band counts padded to the
-    cluster's multiple: 139, 141, 200, 250; none: 256) as well as on one CTA
-    (HSC_JACOBI_ONE_CTA)."""
+    cluster's multiple: 139, 141, 200, 250; none: 256); every case both in the
+    default form (B <= 128: the basis from block power steps) and in the
+    plain one (HSC_JACOBI_ONE_CTA: one sweep on one CTA)."""
     if case.startswith("cfg"):
         cube = synth.make_config(int(case[3])).cube
     elif case == "snapshot":
@@ -123,8 +124,6 @@ def test_eigenpair_fp64_residual(hsc, ctx, case, one_cta):
         cube = synth.make_frame(B, 36, 40, B, sigma=0.03).cube
     else:
         cube = decaying_spectrum_cube()
-    if one_cta and not 129 <= cube.shape[0] <= 256:
-        pytest.skip("the one-CTA flag changes nothing outside 129 <= B <= 256")
     _, v, lam = gpu_pca(hsc, ctx, cube, flags=1 | (hsc.HSC_JACOBI_ONE_CTA if one_cta else 0))
     _, C = hsc.hsc_pca_covariance(ctx, to_dev(cube))
     ctx.sync()
@@ -136,13 +135,15 @@ def test_eigenpair_fp64_residual(hsc, ctx, case, one_cta):
     assert abs(lam - np.linalg.eigvalsh(C).max()) <= 1e-12 * cn
 
 
-@pytest.mark.parametrize("B", [144, 256])
+@pytest.mark.parametrize("B", [128, 144, 256])
 def test_cluster_sweep_matches_one_cta(hsc, ctx, B):
-    """For 129 <= B <= 256 the eigensolver's first sweep runs on a thread-block
-    cluster (two kernels in the Jacobi stage), with HSC_JACOBI_ONE_CTA on one
-    CTA (one kernel). The sweeps round differently, but both eigenpairs are
-    refined against the same FP64 covariance, so they agree to its FP64
-    tolerance, and both match the oracle's FP64 Jacobi on the cube."""
+    """The eigensolver's default forms against its plain one
+    (HSC_JACOBI_ONE_CTA: the basis from one Jacobi sweep on one CTA): for
+    B <= 128 the basis from two block power steps (no sweep, one kernel), for
+    129 <= B <= 256 from the first sweep on a thread-block cluster (two
+    kernels). They round differently, but every eigenpair is refined against
+    the same FP64 covariance, so they agree to its FP64 tolerance, and all
+    match the oracle's FP64 Jacobi on the cube."""
     f = synth.make_frame(31 + B, 48, 56, B, sigma=0.01, n_seeds=32, n_gauss=2, wide=True)
     ref = oracle.pca_one_band(f.cube)
     out = {}
@@ -152,7 +153,8 @@ def test_cluster_sweep_matches_one_cta(hsc, ctx, B):
         I, v, lam = gpu_pca(hsc, ctx, f.cube, flags=1 | (hsc.HSC_JACOBI_ONE_CTA if one_cta else 0))
         _, kern, _ = ctx.profile_read()
         ctx.profile(False)
-        assert kern["jacobi"] == (1 if one_cta else 2)
+        assert kern["jacobi"] == (2 if B > 128 and not one_cta else 1)
+        assert ctx.pca_diagnostics()[0] == (0 if B <= 128 and not one_cta else 1)
         cos = abs(float(v @ ref["v1"]))
         assert np.sqrt(max(0.0, 1 - cos * cos)) < V1_ANGLE
         assert lam == pytest.approx(ref["lambda1"], rel=1e-5)
