@@ -334,9 +334,9 @@ constexpr int kMaxSlots = 64;
 // The tuned launch parameters when they were chosen for this frame shape.
 // Kernels of one eigensolver call: the cluster sweep, when it runs, and the
 // one-CTA kernel.
-int jacobi_launches(int B, const PcaScratch &s)
+int jacobi_launches(int B, const PcaScratch &s, int n_vec = 1)
 {
-    return (s.jac_V && !s.jac_plain && hsc::jacobi_cluster_usable(B)) ? 2 : 1;
+    return hsc::jacobi_kernel_count(B, s, n_vec);
 }
 
 hsc::Tuning tuning_for(const hsc_ctx *ctx, int B, long N, int k)
@@ -870,7 +870,7 @@ hsc_status hsc_pca_project(hsc_ctx *ctx, const float *cube, int B, int H, int W,
         e = hsc::launch_moments(cube, B, N, s, ctx->sm_count, ctx->stream);
     }
     if (e == cudaSuccess) {
-        StageTimer t(ctx, HSC_STAGE_JACOBI, jacobi_launches(B, s));
+        StageTimer t(ctx, HSC_STAGE_JACOBI, jacobi_launches(B, s, n_pc));
         e = hsc::launch_jacobi(B, s, ctx->stream, n_pc);
     }
     if (e == cudaSuccess) {
@@ -1291,7 +1291,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
                     cudaStream_t s, bool with_jacobi) -> cudaError_t {
         cudaError_t r = cudaSuccess;
         if (with_jacobi) {
-            StageTimer t(tc, HSC_STAGE_JACOBI, 1, s);
+            StageTimer t(tc, HSC_STAGE_JACOBI, 2, s);  // the lean form and the guarded full one
             r = hsc::launch_batch_jacobi(df + f0, f1 - f0, B, s);
         }
         if (r == cudaSuccess) {
@@ -1333,7 +1333,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_ev[0], st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(hi, ctx->sm_ev[0], 0);
         if (e == cudaSuccess) {
-            StageTimer t(tc, HSC_STAGE_JACOBI, 1, hi);
+            StageTimer t(tc, HSC_STAGE_JACOBI, 2, hi);  // the lean form and the guarded full one
             e = hsc::launch_batch_jacobi(df, F1, B, hi);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_ev[1], hi);

@@ -48,7 +48,8 @@ struct Control {
                               // its first wait after a short bound (set and cleared by the host)
     unsigned long long knn_redo_total;  // pixels the pruned KNN left to its redo pass since last read
     unsigned long long jacobi_cluster_cycles;  // SM clock cycles of the cluster sweep (its CTA 0)
-    unsigned pad[44];
+    unsigned jac_redo;        // the lean eigensolver left this frame to the full one (reset by it)
+    unsigned pad[43];
 };
 static_assert(sizeof(Control) == 256, "control block: one 256-byte slot");
 
@@ -195,6 +196,8 @@ cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas,
 // n_vec > 1 (with s.vk, s.lamk, s.vkf set): also the next n_vec - 1 leading
 // eigenvectors, refined the same way (multi-PC projection).
 cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec = 1);
+// Kernels launch_jacobi launches for these arguments.
+int jacobi_kernel_count(int B, const PcaScratch &s, int n_vec = 1);
 // The first Jacobi sweep on a thread-block cluster (129 <= B <= 256): its
 // output (floats), whether the device runs it, and the padded band count.
 size_t jacobi_cluster_floats(int B);

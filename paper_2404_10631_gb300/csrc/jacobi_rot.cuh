@@ -13,6 +13,16 @@ namespace {
 // the refinement of the leading vector.
 constexpr int kJacBasis = 16;
 
+// The order in which the basis takes diagonal entries or Ritz values:
+// larger first, a NaN after every number, ties to the smaller index. A strict
+// total order, so the ranks of B entries are a permutation of 0 .. B-1 even
+// when the data hold NaN (the basis indices then stay in range).
+__device__ __forceinline__ bool ranks_before(float di, int i, float dj, int j)
+{
+    const float a = di != di ? -INFINITY : di, b = dj != dj ? -INFINITY : dj;
+    return a > b || (a == b && i < j);
+}
+
 // Round-robin ("circle") pairing: in round t (0 <= t < n-1) pair k joins
 // a = (t + k) and b = (t - k) modulo n-1, and pair 0 joins t with n-1; every
 // pair of indices meets exactly once per sweep. The pair is kept in this

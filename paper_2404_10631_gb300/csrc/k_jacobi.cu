@@ -64,6 +64,9 @@ struct JacParams {
     // 1: the basis from one Jacobi sweep even where block power steps would
     // give it (B <= 128)
     int sweep_basis;
+    // 1: run only for a frame the lean form left (Control::jac_redo), then
+    // clear the flag
+    int only_if_flagged;
 };
 
 // j-slices of the double-float C v: each thread sums at most 16 products
@@ -247,7 +250,13 @@ __device__ float block_sumf(float v, float *red)
     return t;
 }
 
-template <bool kPacked, bool kBatch = false>
+// kLean: the default form for up to 128 bands in shared memory with one
+// eigenvector, compiled without the sweeps, the rebuilds, the fallback and
+// the further eigenvectors, so that its short serial phases stay in the
+// instruction cache (the full kernel spent several cycles per issue waiting
+// for instructions); a frame it cannot finish (a zero C, or a refinement
+// that does not converge) it flags for the full kernel launched after it.
+template <bool kPacked, bool kBatch = false, bool kLean = false>
 __global__ void __launch_bounds__(kJacThreads, 1)
 jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restrict__ C2,
               const double *__restrict__ mu,
@@ -266,6 +275,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         muf = fr.muf;
         ctl = fr.ctl;
     }
+    if (prm.only_if_flagged && *(volatile unsigned *)&ctl->jac_redo == 0u) return;  // uniform
     extern __shared__ float smem[];
     const int B = prm.B, n = prm.n, P = n / 2;
     const int ld = n + 1;  // odd row stride: column walks hit distinct banks
@@ -340,7 +350,9 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
                            P <= kPosMaxP && nno <= 2 * (nthr - OW) + OW;
     // Rayleigh-Ritz on the basis (below): the shared-memory form, B <= 128
     const bool ritz = !kPacked && prm.use_smem && B <= 128 && (pos_sweep || presweep || power);
-    if (!pos_sweep && !presweep && !power) load_A();  // sweep_pos loads its own blocks
+    if constexpr (!kLean) {
+        if (!pos_sweep && !presweep && !power) load_A();  // sweep_pos loads its own blocks
+    }
     __syncthreads();
 
     // Work items fixed for the whole run: up to kBlk off-diagonal 2x2 blocks
@@ -381,7 +393,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     for (int b = 0; b < kBlk; ++b) {
         const int g = tid + b * nthr;
         slot[b] = -1;
-        if (!blocks_in_regs || g >= nblk) continue;
+        if (kLean || !blocks_in_regs || g >= nblk) continue;
         int k, l, o = -1;
         if (!one_sync) {
             tri_of(g, P - 1, k, l);
@@ -858,22 +870,30 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // ---- phase 0: the basis (block power steps, or one logged sweep and the
     // rebuilt leading columns), Rayleigh-Ritz, refinement
     long long t0 = clock64();
+    if constexpr (kLean) {
+        if (!power) {  // a zero C: the full kernel takes the frame
+            if (tid == 0) ctl->jac_redo = 1u;
+            return;
+        }
+    }
     if (power) {  // C's diagonal in the units of A
         stage_c();
         __syncthreads();
         const float2 *Cp = reinterpret_cast<const float2 *>(smem);
         for (int j = tid; j < B; j += nthr) sr[j] = Cp[(size_t)j * B + j].x * inv_p2;
         __syncthreads();
-    } else if (presweep) {  // the diagonal after the cluster's sweep (same scaling)
-        const float *dg = prm.pre + (size_t)kBasis * prm.pre_n;
-        for (int j = tid; j < B; j += nthr) sr[j] = dg[j];
-        __syncthreads();
-    } else if (pos_sweep) {
-        sweep_pos();
-    } else {
-        sweep(true, false);
-        for (int j = tid; j < B; j += nthr) sr[j] = A[aix(j, j)];
-        __syncthreads();
+    } else if constexpr (!kLean) {
+        if (presweep) {  // the diagonal after the cluster's sweep (same scaling)
+            const float *dg = prm.pre + (size_t)kBasis * prm.pre_n;
+            for (int j = tid; j < B; j += nthr) sr[j] = dg[j];
+            __syncthreads();
+        } else if (pos_sweep) {
+            sweep_pos();
+        } else {
+            sweep(true, false);
+            for (int j = tid; j < B; j += nthr) sr[j] = A[aix(j, j)];
+            __syncthreads();
+        }
     }
     sweeps = power ? 0 : 1;
     const int m = B < kBasis ? B : kBasis;
@@ -885,7 +905,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         int rank = 0;
         for (int i = 0; i < B; ++i) {
             const float di = sr[i];
-            rank += (di > dj || (di == dj && i < j)) ? 1 : 0;
+            rank += ranks_before(di, i, dj, j) ? 1 : 0;
         }
         if (rank < m) {
             basis_idx[rank] = j;
@@ -903,12 +923,13 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     if (power) {  // the first power step: X_c = C e_{basis_idx[c]}, C's column
         const float2 *Cp = reinterpret_cast<const float2 *>(smem);
         for (int c = warp; c < m; c += nwarps) {
-            const int j0 = basis_idx[c];
+            const int j0 = min(max(basis_idx[c], 0), B - 1);  // a rank permutation: in range
             float *x = smem + jac_phase0_floats(n) + (size_t)c * ld;
             for (int ii = lane; ii < n; ii += 32)
                 x[ii] = ii < B ? Cp[(size_t)ii * B + j0].x * inv_p2 : 0.f;
         }
-    } else if (presweep) {
+    } else if constexpr (!kLean) {
+if (presweep) {
         for (int c = warp; c < m; c += nwarps) {
             const float *src = prm.pre + (size_t)c * prm.pre_n;
             float *x = X + (size_t)c * ld;
@@ -1003,6 +1024,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
             }
             __syncwarp();
         }
+    }
     }
     __syncthreads();
     for (int ii = tid; ii < B; ii += nthr) {  // column 0: the lead
@@ -1200,7 +1222,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
                 int rank = 0;
                 for (int c = 0; c < m; ++c) {
                     const float dc = Hs[c * kRl + c];
-                    rank += (dc > d || (dc == d && c < lane)) ? 1 : 0;
+                    rank += ranks_before(dc, c, d, lane) ? 1 : 0;
                 }
                 basis_idx[rank] = lane;
                 th[rank] = d;
@@ -1212,7 +1234,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
 #pragma unroll
             for (int k = 0; k < kR; ++k) x[k] = k < m ? Xs[(size_t)k * ld + tid] : 0.f;
             for (int c = 0; c < m; ++c) {
-                const int q = basis_idx[c];
+                const int q = min(max(basis_idx[c], 0), m - 1);  // a rank permutation: in range
                 float acc = 0.f;
 #pragma unroll
                 for (int k = 0; k < kR; ++k) acc = fmaf(x[k], Ws[k * kRl + q], acc);
@@ -1240,14 +1262,19 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         const size_t xo = jac_phase0_floats(n);
         refine_iters = refine(smem + xo, m, 0, deflate, theta_c, reinterpret_cast<const float2 *>(smem),
                               reinterpret_cast<float2 *>(smem + xo + (size_t)kBasis * ld));
-    } else {
+    } else if constexpr (!kLean) {
         refine_iters = refine(X, m, 0, deflate, theta_c, prm.use_smem ? Cs2 : C2, part);
     }
     converged = refine_iters <= kMaxRefine;
     t_refine += clock64() - t1;
 
     // ---- fallback: sweeps from C with V accumulated, refinement on all columns
-    if (!converged) {
+    if constexpr (kLean) {
+        if (!converged) {  // the full kernel takes the frame
+            if (tid == 0) ctl->jac_redo = 1u;
+            return;
+        }
+    } else if (!converged) {
         fell_back = true;
         t0 = clock64();
         load_A();
@@ -1348,6 +1375,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
         ctl->jacobi_sweep_cycles =
             (unsigned long long)t_sweep + (presweep ? ctl->jacobi_cluster_cycles : 0ull);
         ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
+        ctl->jac_redo = 0u;
         ctl->imin_key = float_to_key(INFINITY);
         ctl->imax_key = float_to_key(-INFINITY);
     }
@@ -1357,7 +1385,7 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
     // largest diagonal's column after the sweep) by the same deflated
     // correction aimed at column j, then the same sign rule. Phase 0's basis
     // only (the fallback rebuilds none).
-    if (prm.n_vec > 1 && !fell_back) {
+    if (!kLean && prm.n_vec > 1 && !fell_back) {
         const bool sm_basis = prm.use_smem && !kPacked;
         const size_t xo = jac_phase0_floats(n);
         const float *bas = sm_basis ? smem + xo : X;
@@ -1428,9 +1456,25 @@ JacParams jac_params(int B)
     prm.pre = nullptr;
     prm.pre_n = 0;
     prm.sweep_basis = 0;
+    prm.only_if_flagged = 0;
     return prm;
 }
 }  // namespace
+
+// The lean form serves frames of up to 128 bands whose work area sits in
+// shared memory, for one eigenvector, unless the plain form is asked for.
+bool lean_applies(const JacParams &prm, int n_vec, bool plain)
+{
+    return prm.use_smem && prm.B <= 128 && n_vec <= 1 && !plain;
+}
+
+int jacobi_kernel_count(int B, const PcaScratch &s, int n_vec)
+{
+    const JacParams prm = jac_params(B);
+    if (lean_applies(prm, n_vec, s.jac_plain)) return 2;  // lean + the guarded full kernel
+    if (s.jac_V && !s.jac_plain && jacobi_cluster_floats(B) && jacobi_cluster_usable(B)) return 2;
+    return 1;
+}
 
 cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec)
 {
@@ -1444,6 +1488,24 @@ cudaError_t launch_jacobi(int B, const PcaScratch &s, cudaStream_t st, int n_vec
     const bool packed = !prm.use_smem && need_packed <= kJacSmemLimit;
     if (!prm.use_smem && !s.jac_A) return cudaErrorInvalidValue;
     prm.sweep_basis = s.jac_plain ? 1 : 0;
+    if (lean_applies(prm, prm.n_vec, s.jac_plain)) {
+        // the lean form, then the full kernel for a frame it flagged (the
+        // basis from one sweep; it exits at once otherwise)
+        if (need > 48 * 1024) {
+            cudaFuncSetAttribute(jacobi_kernel<false, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            cudaFuncSetAttribute(jacobi_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)need);
+        }
+        jacobi_kernel<false, false, true><<<1, kJacThreads, need, st>>>(
+            prm, s.C, s.C2, s.mu, s.v1, s.lambda1, s.v1f, s.muf, s.jac_A, s.ctl, nullptr);
+        JacParams full = prm;
+        full.sweep_basis = 1;
+        full.only_if_flagged = 1;
+        jacobi_kernel<false><<<1, kJacThreads, need, st>>>(full, s.C, s.C2, s.mu, s.v1, s.lambda1,
+                                                           s.v1f, s.muf, s.jac_A, s.ctl, nullptr);
+        return cudaGetLastError();
+    }
     if (s.jac_V && !s.jac_plain && jacobi_cluster_floats(B) && jacobi_cluster_usable(B)) {
         // the first sweep on a cluster; this kernel continues from its V
         const cudaError_t e = launch_jacobi_cluster(B, s.C2, s.jac_V, s.ctl, prm.rot_tol, st);
@@ -1474,10 +1536,19 @@ cudaError_t launch_batch_jacobi(const BatchFrame *frames, int n_frames, int B, c
     const JacParams prm = jac_params(B);
     const size_t need = jac_work_floats(prm.n) * sizeof(float);
     if (!prm.use_smem || n_frames < 1 || B > 128) return cudaErrorInvalidValue;
-    if (need > 48 * 1024)
+    // the lean form per frame, then the full kernel for the frames it flagged
+    if (need > 48 * 1024) {
+        cudaFuncSetAttribute(jacobi_kernel<false, true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
         cudaFuncSetAttribute(jacobi_kernel<false, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-    jacobi_kernel<false, true><<<n_frames, kJacThreads, need, st>>>(prm, nullptr, nullptr, nullptr,
+    }
+    jacobi_kernel<false, true, true><<<n_frames, kJacThreads, need, st>>>(
+        prm, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, frames);
+    JacParams full = prm;
+    full.sweep_basis = 1;
+    full.only_if_flagged = 1;
+    jacobi_kernel<false, true><<<n_frames, kJacThreads, need, st>>>(full, nullptr, nullptr, nullptr,
                                                               nullptr, nullptr, nullptr, nullptr,
                                                               nullptr, nullptr, frames);
     return cudaGetLastError();

@@ -425,7 +425,7 @@ jacobi_cluster_kernel(int B, int n, float rot_tol, const float2 *__restrict__ C2
         int rank = 0;
         for (int i = 0; i < B; ++i) {
             const float di = sr[i];
-            rank += (di > dj || (di == dj && i < j)) ? 1 : 0;
+            rank += ranks_before(di, i, dj, j) ? 1 : 0;
         }
         if (rank < m) s_basis[rank] = j;
     }
