@@ -754,11 +754,19 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
             dfl tvv = {0.f, 0.f}, tvw = {0.f, 0.f};
             if (row) {
                 float sum = 0.f, lo = 0.f;
-                for (int sl = 0; sl < nsl; ++sl) {
-                    const float2 q = part[(size_t)sl * n + i];
+                auto slice = [&](float2 q) {
                     float e;
                     two_sum(sum, q.x, sum, e);
                     lo = __fadd_rn(lo, __fadd_rn(e, q.y));
+                };
+                if (nsl == 8) {
+                    float2 q[8];
+#pragma unroll
+                    for (int sl = 0; sl < 8; ++sl) q[sl] = part[(size_t)sl * n + i];
+#pragma unroll
+                    for (int sl = 0; sl < 8; ++sl) slice(q[sl]);
+                } else {
+                    for (int sl = 0; sl < nsl; ++sl) slice(part[(size_t)sl * n + i]);
                 }
                 dfl w = fast_two_sum(sum, lo);
                 w.h = __fmul_rn(w.h, inv_p2);  // exact: a power of two
@@ -818,7 +826,19 @@ jacobi_kernel(JacParams prm, const double *__restrict__ C, const float2 *__restr
                 (deflate && fabsf(den_c) > 1e-3f * fabsf(rho_s)) ? 1.f / den_c : 0.f;
             for (int c = warp; c < m; c += nwarps) {
                 float g = 0.f;
-                for (int ii = lane; ii < B; ii += 32) g = fmaf(basis[(size_t)c * ld + ii], sr[ii], g);
+                if (B <= 128) {
+                    float bq[4], rq[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int ii = lane + 32 * r;
+                        bq[r] = ii < B ? basis[(size_t)c * ld + ii] : 0.f;
+                        rq[r] = ii < B ? sr[ii] : 0.f;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) g = fmaf(bq[r], rq[r], g);
+                } else {
+                    for (int ii = lane; ii < B; ii += 32) g = fmaf(basis[(size_t)c * ld + ii], sr[ii], g);
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
                 if (lane == 0) {
@@ -1044,7 +1064,11 @@ if (presweep) {
         // so a column takes four barriers. A column left with under 1e-5 of
         // its length lies in the span of the ones before and is set to zero,
         // which the Rayleigh-Ritz step and the refinement take as an empty
-        // direction. Pointers are formed from the shared array itself, so the
+        // direction. With B <= 128 and m <= 16 every loop has a compile-time
+        // bound and a predicate: the loads of a phase are issued together
+        // instead of one shared-memory latency per term, which halves this
+        // phase (it is latency-bound: a few hundred instructions between
+        // barriers). Pointers are formed from the shared array itself, so the
         // accesses compile to shared-memory instructions.
         float *Xp = smem + jac_phase0_floats(n);  // the basis, stride ld
         __shared__ float s_nrm[2];
@@ -1052,28 +1076,42 @@ if (presweep) {
             float *xc = Xp + (size_t)c * ld;
             for (int pass = 0; pass < 2; ++pass) {
                 // dots with the columns before (warp j) and this column's
-                // squared length (warp c)
-                for (int j = warp; j <= c; j += nwarps) {
-                    const float *xj = Xp + (size_t)j * ld;
-                    float d = 0.f;
-                    for (int ii = lane; ii < B; ii += 32) d = fmaf(xj[ii], xc[ii], d);
-                    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+                // squared length (warp c); rows lane + 32 r
+                if (warp <= c) {
+                    const float *xj = Xp + (size_t)warp * ld;
+                    float d[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int ii = lane + 32 * r;
+                        d[r] = ii < B ? xj[ii] * xc[ii] : 0.f;
+                    }
+                    float dd = (d[0] + d[1]) + (d[2] + d[3]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
                     if (lane == 0) {
-                        if (j < c) coef[j] = d;
-                        else s_nrm[pass] = d;
+                        if (warp < c) coef[warp] = dd;
+                        else s_nrm[pass] = dd;
                     }
                 }
                 __syncthreads();
                 // x_c <- x_c - sum_j (x_j . x_c) x_j; after the second pass
                 // divided by its length, |x|^2 - sum_j (x_j . x)^2
-                float q = s_nrm[pass];
-                for (int j = 0; j < c; ++j) q = fmaf(-coef[j], coef[j], q);
-                const float sc = pass == 0 ? 1.f
-                                           : ((q > 1e-10f * s_nrm[0] && q > 0.f) ? rsqrtf(q) : 0.f);
-                for (int ii = tid; ii < B; ii += nthr) {
-                    float a = xc[ii];
-                    for (int j = 0; j < c; ++j) a = fmaf(-coef[j], Xp[(size_t)j * ld + ii], a);
-                    xc[ii] = a * sc;
+                if (tid < B) {
+                    float cf[kBasis], xs[kBasis];
+#pragma unroll
+                    for (int j = 0; j < kBasis; ++j) {
+                        cf[j] = j < c ? coef[j] : 0.f;
+                        xs[j] = j < c ? Xp[(size_t)j * ld + tid] : 0.f;
+                    }
+                    float q = s_nrm[pass], a = xc[tid];
+#pragma unroll
+                    for (int j = 0; j < kBasis; ++j) {
+                        q = fmaf(-cf[j], cf[j], q);
+                        a = fmaf(-cf[j], xs[j], a);
+                    }
+                    const float sc =
+                        pass == 0 ? 1.f : ((q > 1e-10f * s_nrm[0] && q > 0.f) ? rsqrtf(q) : 0.f);
+                    xc[tid] = a * sc;
                 }
                 __syncthreads();
             }
