@@ -771,6 +771,10 @@ def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
         hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
                                flags=hsc.HSC_BATCH_GRAPH, labels=labs)
 
+    def fused():
+        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
+                               flags=hsc.HSC_BATCH_GRAPH | hsc.HSC_BATCH_FUSED, labels=labs)
+
     def pooled():
         hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam,
                                flags=hsc.HSC_BATCH_GRAPH | hsc.HSC_BATCH_POOL, labels=labs)
@@ -794,17 +798,23 @@ def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
         return ev[0].elapsed_time(ev[n]) / n, per
 
     b_ms, b_per = timed(batched, reps)
+    s_ms, s_per = timed(fused, reps)
     o_ms, _ = timed(pooled, 3)
     p_ms, p_per = timed(per_frame, 3)
     # per-stage device time of the stage-major form (calls without a graph)
-    ctx.profile(True)
-    ctx.profile_read()
-    for _ in range(3):
-        hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, labels=labs)
-    ctx.sync()
-    st_ms, st_k, _ = ctx.profile_read()
-    ctx.profile(False)
-    stages = {n: round(ms / 3, 4) for n, ms in st_ms.items() if ms > 0}
+    def stage_ms(flags):
+        ctx.profile(True)
+        ctx.profile_read()
+        for _ in range(3):
+            hsc.hsc_classify_batch(ctx, cubes, model, f0.K, f0.window_rows, f0.lam, flags=flags,
+                                   labels=labs)
+        ctx.sync()
+        st_ms, _, _ = ctx.profile_read()
+        ctx.profile(False)
+        return {n: round(ms / 3, 4) for n, ms in st_ms.items() if ms > 0}
+
+    stages = stage_ms(0)
+    stages_fused = stage_ms(hsc.HSC_BATCH_FUSED)
     return {"workload": "%d square snapshot frames, sides 40-64 px, 125 bands float32, "
                         "4 classes (shared model), K=16, 7-row window, lambda=1" % n_frames,
             "pixels_per_batch": px,
@@ -813,6 +823,12 @@ def run_batch(hsc, ctx, stream, dev, args, n_frames=256, reps=10):
                         "api": "hsc_classify_batch, stage-major (one launch per stage over "
                                "every frame), CUDA-graph replay",
                         "stages_ms": stages},
+            "fused": {"value": px / (s_ms / 1e3), "unit": UNIT, "ms_per_batch": s_ms,
+                      "p50_ms": s_per[len(s_per) // 2], "p99_ms": s_per[-1],
+                      "api": "the same with the projection/SVM, normalisation and KNN of each "
+                             "frame group in one persistent kernel (HSC_BATCH_FUSED; booked to "
+                             "the knn stage), CUDA-graph replay",
+                      "stages_ms": stages_fused},
             "stream_pool": {"value": px / (o_ms / 1e3), "unit": UNIT, "ms_per_batch": o_ms,
                             "api": "hsc_classify_batch with HSC_BATCH_POOL (frames on 64 "
                                    "streams), CUDA-graph replay"},

@@ -244,10 +244,11 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
  * Stage-major form (B <= 128, pruned KNN search: AUTO or PRUNED with
  * lambda > 0, up to 65535 frames): one launch per stage covers every frame,
  * from a frame table and work-item tables the call uploads with one copy
- * (8 kernel launches per call, whatever the frame count): the pilots, one
+ * (a fixed number of kernel launches per call, whatever the frame count): the pilots, one
  * persistent tensor-core Gram over every frame's chunk ranges, the
  * reductions, one Jacobi CTA per frame, the projection/SVM, normalisation
- * and KNN over per-frame work items.
+ * and KNN over per-frame work items (or, HSC_BATCH_FUSED, the last three in
+ * one persistent kernel).
  * Otherwise (or with HSC_BATCH_POOL) frames run concurrently on up to 64
  * library-owned streams that fork from and join back into the context's
  * stream, each with its own scratch slot.
@@ -258,7 +259,16 @@ hsc_status hsc_classify(hsc_ctx *ctx, const float *cube, int B, int H, int W,
  *             configuration (stage-major: frame count, work-item counts,
  *             parameters; the frames' pointers travel in the tables. Stream
  *             pool: the same frames, pointers and sizes), which removes the
- *             per-launch host cost; HSC_BATCH_POOL: the stream-pool form. */
+ *             per-launch host cost; HSC_BATCH_POOL: the stream-pool form;
+ *             HSC_BATCH_FUSED: the stage-major form with the projection/SVM,
+ *             normalisation and KNN of each frame group in one persistent
+ *             kernel over a work list (projection/SVM items, then KNN row
+ *             segments that wait, bounded, for their own frame's items and
+ *             normalise I on the fly) instead of three launches: the same
+ *             outputs, bit for bit. On 256 snapshot frames it is slower than
+ *             the three launches (its persistent CTAs hold every SM, so the
+ *             second eigensolver wave, a whole SM per frame, waits for them,
+ *             and its 124 registers leave the KNN half the warps). */
 typedef struct {
     const float *cube;   /* B x H x W float32 */
     int32_t H, W;
@@ -270,6 +280,7 @@ typedef struct {
 
 #define HSC_BATCH_GRAPH 8u
 #define HSC_BATCH_POOL 64u
+#define HSC_BATCH_FUSED 256u
 
 hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frames, int B,
                               const hsc_svm_model *model, const hsc_knn_params *params,

@@ -49,6 +49,7 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_test_stall_next_gram")
 HSC_BATCH_GRAPH = 8
 HSC_BATCH_POOL = 64
+HSC_BATCH_FUSED = 256
 HSC_COV_FP32_PIPE = 4
 HSC_NOALLOC_MAX_BANDS = 128
 STAGES = ("moments", "jacobi", "project_svm", "normalize", "knn")

@@ -1036,7 +1036,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     constexpr int kPixPerItem = 1024;
     // ---- layout: control blocks, per-frame buffers, tables
     struct FrameLay {
-        size_t shift, gram, sums, C, C2, mu, v1, lam, v1f, muf, I, P, P4;
+        size_t shift, gram, sums, C, C2, mu, v1, lam, v1f, muf, I, P, P4, Iraw;
         long per;
         int parts, vec;
     };
@@ -1071,6 +1071,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         L.I = fr.one_band ? 0 : take(sizeof(float) * (size_t)N);
         L.P = fr.probs ? 0 : take(sizeof(float) * (size_t)k * N);
         L.P4 = take(sizeof(float4) * (size_t)((k + 3) / 4) * (size_t)N);
+        L.Iraw = take(sizeof(float) * (size_t)N);
         n_gram += L.parts;
         n_pix += (int)((N + kPixPerItem - 1) / kPixPerItem);
         n_ctas += fr.H * ((fr.W + 31) / 32);
@@ -1079,6 +1080,7 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
     long n_px = 0;
     for (int f = 0; f < n_frames; ++f) n_px += (long)frames[f].H * frames[f].W;
     const size_t redo = take(sizeof(int2) * (size_t)n_px);  // the KNN redo list
+    const size_t claims = take(4 * sizeof(unsigned));  // the fused kernel's work counters, per group
     int n_large = 0;  // frames whose pilot takes a CTA per band
     for (int f = 0; f < n_frames; ++f) n_large += (long)frames[f].H * frames[f].W > 4096 ? 1 : 0;
     const size_t tab_frames = sizeof(BatchFrame) * (size_t)n_frames;
@@ -1192,7 +1194,8 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         b.per = (int)L.per;
         b.vec = L.vec;
         b.knn_cta0 = cta;
-        hf[f] = b;
+        b.Iraw = reinterpret_cast<float *>(dev + L.Iraw);
+        b.svm_items = 0;
         const long total_chunks = (N + 63) / 64;
         for (int j = 0; j < L.parts; ++j) {
             GramItem g;
@@ -1212,7 +1215,9 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
             it.g1 = (int)std::min(groups, g0 + gpi);
             it.px = px;
             hp[ip++] = it;
+            ++b.svm_items;
         }
+        hf[f] = b;
         cta += fr.H * ((fr.W + 31) / 32);
         if (N > 4096) hl[il++] = f;
     }
@@ -1293,6 +1298,17 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         if (with_jacobi) {
             StageTimer t(tc, HSC_STAGE_JACOBI, 2, s);  // the lean form and the guarded full one
             r = hsc::launch_batch_jacobi(df + f0, f1 - f0, B, s);
+        }
+        if (r == cudaSuccess && (flags & HSC_BATCH_FUSED)) {
+            // projection/SVM, normalisation and KNN in one persistent launch
+            // (+ the redo pass); its time is booked to the KNN stage
+            StageTimer t(tc, HSC_STAGE_KNN, 2, s);
+            unsigned *claim = reinterpret_cast<unsigned *>(dev + claims) + (f0 == 0 ? 0 : 2);
+            r = hsc::launch_batch_svm_knn(df, dp + ip0, ip1 - ip0, df + f0, f1 - f0, cta1 - cta0,
+                                          cta0, B, model, f64, params->k, R, params->lambda,
+                                          !(flags & HSC_CLASSIFY_RAW_I), max_rows,
+                                          redo_list + px0, (unsigned)(px1 - px0), claim, sm, s);
+            return r;
         }
         if (r == cudaSuccess) {
             StageTimer t(tc, HSC_STAGE_PROJECT_SVM, 1, s);
@@ -1379,7 +1395,7 @@ hsc_status hsc_classify_batch(hsc_ctx *ctx, const hsc_frame *frames, int n_frame
     if (st) return st;
     if (!frames || n_frames < 1) return fail(ctx, HSC_ERR_INVALID_ARG, "no frames%s");
     if (flags & ~(unsigned)(HSC_SVM_COUPLE_F64 | HSC_BATCH_GRAPH | HSC_CLASSIFY_RAW_I |
-                            HSC_BATCH_POOL))
+                            HSC_BATCH_POOL | HSC_BATCH_FUSED))
         return fail(ctx, HSC_ERR_INVALID_ARG, "unknown flags%s");
     if ((st = check_model(ctx, model, B))) return st;
     const int k = model->n_classes;

@@ -49,7 +49,9 @@ struct Control {
     unsigned long long knn_redo_total;  // pixels the pruned KNN left to its redo pass since last read
     unsigned long long jacobi_cluster_cycles;  // SM clock cycles of the cluster sweep (its CTA 0)
     unsigned jac_redo;        // the lean eigensolver left this frame to the full one (reset by it)
-    unsigned pad[43];
+    unsigned svm_done;        // stage-major batch: projection/SVM items of the frame finished in
+                              // the fused projection/SVM + KNN kernel (reset by the eigensolver)
+    unsigned pad[42];
 };
 static_assert(sizeof(Control) == 256, "control block: one 256-byte slot");
 
@@ -119,6 +121,8 @@ struct BatchFrame {
     int per;             // 64-pixel chunks per partial
     int vec;             // 16-byte loads: cube 16-byte aligned and N % 4 == 0
     int knn_cta0;        // first CTA of the frame in the batched KNN grid
+    float *Iraw;         // N: the raw projection (the fused kernel normalises into I)
+    int svm_items;       // projection/SVM work items of the frame
 };
 
 // A tensor-core Gram work item: frame, partial index, chunk range [c0, c1).
@@ -190,6 +194,17 @@ cudaError_t launch_batch_normalize(const BatchFrame *frames, const PixItem *item
 cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas, int cta_base,
                              int k, int K, int R, float lambda, int max_rows, int2 *redo_list,
                              unsigned redo_cap, cudaStream_t st);
+// The projection/SVM, normalisation and KNN of a group of frames in one
+// persistent launch (work items first, then the KNN row segments, which wait
+// for their frame's items), then the redo pass; normalize false leaves I raw
+// (HSC_CLASSIFY_RAW_I). frames/items: the whole table and the group's items;
+// kframes/n_kframes/n_seg/cta_base: the group's frames, KNN segments and first
+// segment (as launch_batch_knn); claim: two counters of scratch (zeroed here).
+cudaError_t launch_batch_svm_knn(const BatchFrame *frames, const PixItem *items, int n_items,
+                                 const BatchFrame *kframes, int n_kframes, int n_seg, int cta_base,
+                                 int B, const hsc_svm_model *m, bool couple_f64, int K, int R,
+                                 float lambda, bool normalize, int max_rows, int2 *redo_list,
+                                 unsigned redo_cap, unsigned *claim, int sm_count, cudaStream_t st);
 
 // Jacobi eigen-decomposition of C, FP64 refinement of the leading vector,
 // sign rule; writes v1, lambda1, v1f, muf and resets the I min/max keys.

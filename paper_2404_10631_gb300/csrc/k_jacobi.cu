@@ -1414,6 +1414,7 @@ if (presweep) {
             (unsigned long long)t_sweep + (presweep ? ctl->jacobi_cluster_cycles : 0ull);
         ctl->jacobi_refine_cycles = (unsigned long long)t_refine;
         ctl->jac_redo = 0u;
+        ctl->svm_done = 0u;
         ctl->imin_key = float_to_key(INFINITY);
         ctl->imax_key = float_to_key(-INFINITY);
     }

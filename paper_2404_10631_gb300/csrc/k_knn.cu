@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "hsc_internal.cuh"
+#include "svm_pixel.cuh"
 
 namespace hsc {
 namespace {
@@ -566,11 +567,29 @@ __device__ __forceinline__ void add_probs4(float (&acc)[KC], const float4 *__res
     }
 }
 
-template <int KC, bool kP4>
+// add_probs4 with plain (coherent) loads: for maps written earlier in the
+// same launch (the batch's fused projection/SVM + KNN kernel), which the
+// read-only path must not serve.
+template <int KC>
+__device__ __forceinline__ void add_probs4_coherent(float (&acc)[KC], const float4 *P4, int q)
+{
+    constexpr int NQ = (KC + 3) / 4;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+        const float4 v = P4[(size_t)q * NQ + i];
+        const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (4 * i + e < KC) acc[4 * i + e] += w[e];
+    }
+}
+
+template <int KC, bool kP4, bool kCoherent = false>
 __device__ __forceinline__ void gather_probs(float (&acc)[KC], const float *__restrict__ P, long N,
                                              const float4 *__restrict__ P4, int q)
 {
-    if (kP4) add_probs4(acc, P4, q);
+    if (kCoherent) add_probs4_coherent(acc, P4, q);
+    else if (kP4) add_probs4(acc, P4, q);
     else add_probs(acc, P, N, q);
 }
 
@@ -593,46 +612,43 @@ __device__ __forceinline__ void write_pixel(const float (&acc)[KC], int K, long 
     labels[p] = best;
 }
 
-// kWT: pixels per CTA (one row segment, a lane per pixel); kBN: undecided
-// keys per lane. Neither changes a result (the canonical summation order
-// makes O independent of which pixels the redo pass completes); an
-// autotuner picks them per frame shape.
-template <int KC, bool kBatch = false, bool kP4 = false, int kWT = kWalkThreads, int kBN = kBnd>
-__global__ void __launch_bounds__(kWT)
-knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
-                  int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
-                  bool redo_all, Control *ctl, const BatchFrame *__restrict__ frames,
-                  int n_frames, int2 *__restrict__ redo_list, unsigned redo_cap,
-                  const float4 *__restrict__ P4, int cta_base = 0)
+// The pruned walk of one row segment: kWT pixels of row r from column
+// bx * kWT, a lane per pixel (lane in 0 .. kWT-1), the window rows staged in
+// sm (the tile, then the lanes' undecided-key buffers). kWarp: the segment is
+// one warp of a larger CTA (kWT == 32; warp-level synchronisation, no shared
+// reduction). norm: the tile is read from the raw projection I and
+// normalised in shared memory with the frame's minimum nmin and range
+// nrange, the same expression as the normalisation pass, and each lane
+// writes its own pixel's normalised value to I_out. kCoherent: plain loads
+// of the probabilities (written earlier in the same launch). frames, frame:
+// a stage-major batch's table and this segment's index in it (redo list).
+template <int KC, bool kBatch, bool kP4, int kWT, int kBN, bool kWarp = false,
+          bool kCoherent = false>
+__device__ __forceinline__ void knn_walk(const float *__restrict__ I, const float *__restrict__ P,
+                                         int H, int W, int K, int R, float lam,
+                                         float *__restrict__ O, int32_t *__restrict__ labels,
+                                         bool redo_all, Control *ctl,
+                                         const BatchFrame *__restrict__ frames, int frame,
+                                         int2 *__restrict__ redo_list, unsigned redo_cap,
+                                         const float4 *P4, int r, int bx, int lane, float *sm,
+                                         float *s_min, float *s_max, bool norm = false,
+                                         float nmin = 0.f, float nrange = 0.f,
+                                         float *__restrict__ I_out = nullptr)
 {
-    extern __shared__ float sm[];
-    __shared__ float s_min[kWT / 32], s_max[kWT / 32];
-    int r = blockIdx.y, bx = blockIdx.x;
-    int frame = 0;
-    if (kBatch) {  // a stage-major batch: the frame whose CTA range holds this CTA
-        const int cta = (int)blockIdx.x + cta_base;
-        int lo = 0, hi = n_frames - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (frames[mid].knn_cta0 <= cta) lo = mid;
-            else hi = mid - 1;
-        }
-        frame = lo;
-        const BatchFrame &fr = frames[lo];
-        I = fr.I;
-        P = fr.P;
-        P4 = fr.P4;
-        H = fr.H;
-        W = fr.W;
-        O = fr.O;
-        labels = fr.labels;
-        ctl = fr.ctl;
-        const int t = cta - fr.knn_cta0;
-        const int tpr = (W + kWT - 1) / kWT;
-        r = t / tpr;
-        bx = t - r * tpr;
-    }
-    const int lane = threadIdx.x;
+    static_assert(!kWarp || kWT == 32, "a warp-scope segment is one warp");
+    auto sync = [] {
+        if constexpr (kWarp) __syncwarp();
+        else __syncthreads();
+    };
+    auto any = [](bool v) -> bool {
+        if constexpr (kWarp) return __any_sync(0xffffffffu, v) != 0;
+        else return __syncthreads_or(v) != 0;
+    };
+    auto count = [](bool v) -> unsigned {
+        if constexpr (kWarp) return (unsigned)__popc(__ballot_sync(0xffffffffu, v));
+        else return (unsigned)__syncthreads_count(v);
+    };
+    auto nrm = [&](float v) { return (nrange > 0.f) ? (v - nmin) / nrange : 0.f; };
     const int c0 = bx * kWT, c = c0 + lane;
     const bool active = c < W;
     const int lo_r = max(0, r - R / 2);
@@ -678,12 +694,14 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
+    sync();
     bool bad = false;
     float vmin = INFINITY, vmax = -INFINITY;
     if (vec) {
         for (int idx = lane; idx < nrows * kV; idx += kWT) {
-            const float4 t4 = reinterpret_cast<const float4 *>(tile)[idx / kV * (tw / 4) + idx % kV];
+            float4 &t4r = reinterpret_cast<float4 *>(tile)[idx / kV * (tw / 4) + idx % kV];
+            if (norm) t4r = make_float4(nrm(t4r.x), nrm(t4r.y), nrm(t4r.z), nrm(t4r.w));
+            const float4 t4 = t4r;
             bad |= !isfinite(t4.x) || !isfinite(t4.y) || !isfinite(t4.z) || !isfinite(t4.w);
             vmin = fminf(vmin, fminf(fminf(t4.x, t4.y), fminf(t4.z, t4.w)));
             vmax = fmaxf(vmax, fmaxf(fmaxf(t4.x, t4.y), fmaxf(t4.z, t4.w)));
@@ -693,6 +711,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
             for (int jj = lane; jj < tw; jj += kWT) {
                 const int col = tcol0 + jj;
                 if (col < 0 || col >= W) continue;
+                if (norm) tile[ii * tw + jj] = nrm(tile[ii * tw + jj]);
                 const float v = tile[ii * tw + jj];
                 bad |= !isfinite(v);
                 vmin = fminf(vmin, v);
@@ -704,19 +723,24 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
         vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     }
-    if ((lane & 31) == 0) {
-        s_min[lane >> 5] = vmin;
-        s_max[lane >> 5] = vmax;
-    }
-    __syncthreads();
-    vmin = s_min[0];
-    vmax = s_max[0];
-    for (int w = 1; w < kWT / 32; ++w) {
-        vmin = fminf(vmin, s_min[w]);
-        vmax = fmaxf(vmax, s_max[w]);
+    if constexpr (kWarp) {
+        __syncwarp();  // the normalised tile before any lane reads it
+    } else {
+        if ((lane & 31) == 0) {
+            s_min[lane >> 5] = vmin;
+            s_max[lane >> 5] = vmax;
+        }
+        __syncthreads();
+        vmin = s_min[0];
+        vmax = s_max[0];
+        for (int w = 1; w < kWT / 32; ++w) {
+            vmin = fminf(vmin, s_min[w]);
+            vmax = fmaxf(vmax, s_max[w]);
+        }
     }
 
     const float Ip = active ? tile[(r - lo_r) * tw + (c - tcol0)] : 0.f;
+    if (norm && active) I_out[(long)r * W + c] = Ip;
     unsigned evals = 0;
     bool redo = active && redo_all;
 
@@ -786,7 +810,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                 const float h = __fadd_rn(st, e);
                 if (h < L) {  // one of the K nearest
                     ++m;
-                    gather_probs<KC, kP4>(acc, P, N, P4, qrow + j);
+                    gather_probs<KC, kP4, kCoherent>(acc, P, N, P4, qrow + j);
                     continue;
                 }
                 if (h > tau.hi) continue;
@@ -795,7 +819,7 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                 const Key kk = {h, lo, qrow + j};
                 if (h == L && lo < 0.f) {
                     ++m;
-                    gather_probs<KC, kP4>(acc, P, N, P4, qrow + j);
+                    gather_probs<KC, kP4, kCoherent>(acc, P, N, P4, qrow + j);
                     continue;
                 }
                 if (!key_le(kk, tau)) continue;
@@ -814,8 +838,8 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
         }
     }
     bad |= active && !isfinite(Ip);
-    if (__syncthreads_or(bad) && lane == 0) atomicOr(&ctl->status, ST_NONFINITE_MAP);
-    const unsigned nredo = __syncthreads_count(redo);
+    if (any(bad) && lane == 0) atomicOr(&ctl->status, ST_NONFINITE_MAP);
+    const unsigned nredo = count(redo);
     if (lane == 0 && nredo) {
         if (!kBatch) atomicAdd(&ctl->knn_redo, nredo);
         atomicAdd(&ctl->knn_redo_total, (unsigned long long)nredo);
@@ -861,9 +885,54 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
             }
         }
         if (im != a) bnd.put(im, bnd.get(a));
-        gather_probs<KC, kP4>(acc, P, N, P4, best.q);
+        gather_probs<KC, kP4, kCoherent>(acc, P, N, P4, best.q);
     }
     write_pixel(acc, K, N, p, O, labels);
+}
+
+
+// kWT: pixels per CTA (one row segment, a lane per pixel); kBN: undecided
+// keys per lane. Neither changes a result (the canonical summation order
+// makes O independent of which pixels the redo pass completes); an
+// autotuner picks them per frame shape.
+template <int KC, bool kBatch = false, bool kP4 = false, int kWT = kWalkThreads, int kBN = kBnd>
+__global__ void __launch_bounds__(kWT)
+knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int H, int W, int K,
+                  int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
+                  bool redo_all, Control *ctl, const BatchFrame *__restrict__ frames,
+                  int n_frames, int2 *__restrict__ redo_list, unsigned redo_cap,
+                  const float4 *__restrict__ P4, int cta_base = 0)
+{
+    extern __shared__ float sm[];
+    __shared__ float s_min[kWT / 32], s_max[kWT / 32];
+    int r = blockIdx.y, bx = blockIdx.x;
+    int frame = 0;
+    if (kBatch) {  // a stage-major batch: the frame whose CTA range holds this CTA
+        const int cta = (int)blockIdx.x + cta_base;
+        int lo = 0, hi = n_frames - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (frames[mid].knn_cta0 <= cta) lo = mid;
+            else hi = mid - 1;
+        }
+        frame = lo;
+        const BatchFrame &fr = frames[lo];
+        I = fr.I;
+        P = fr.P;
+        P4 = fr.P4;
+        H = fr.H;
+        W = fr.W;
+        O = fr.O;
+        labels = fr.labels;
+        ctl = fr.ctl;
+        const int t = cta - fr.knn_cta0;
+        const int tpr = (W + kWT - 1) / kWT;
+        r = t / tpr;
+        bx = t - r * tpr;
+    }
+    knn_walk<KC, kBatch, kP4, kWT, kBN>(I, P, H, W, K, R, lam, O, labels, redo_all, ctl, frames,
+                                        frame, redo_list, redo_cap, P4, r, bx, (int)threadIdx.x, sm,
+                                        s_min, s_max);
 }
 
 template <int KC>
@@ -1181,6 +1250,167 @@ cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ct
     return cudaGetLastError();
 }
 
+// ---- stage-major batch: projection/SVM fused with the KNN filter ----
+
+constexpr unsigned kSvmWaitLimit = 1u << 23;  // suspends of ~256 ns: about 2 s in all
+
+// Waits until *cnt reaches target (acquire at GPU scope), at most
+// kSvmWaitLimit suspends; after that sets ST_TIMEOUT in ctl and returns false.
+__device__ bool wait_count(const unsigned *cnt, unsigned target, Control *ctl)
+{
+    for (unsigned it = 0;; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(cnt) : "memory");
+        if (v >= target) return true;
+        if (it >= kSvmWaitLimit) {
+            atomicOr(&ctl->status, ST_TIMEOUT);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
+// One persistent launch over a work list of two kinds (Section II.C order:
+// the SVM maps, then the KNN filter of Eq. 1-2 over them):
+//  * projection/SVM items (a frame's groups of pixels, the same items and
+//    arithmetic as project_svm_batch_kernel), a CTA each, claimed from
+//    claim[0]; each ends by adding one to its frame's svm_done counter after
+//    a fence by every thread;
+//  * KNN row segments of 32 pixels (the pruned walk of knn_pruned_kernel), a
+//    warp each, claimed from claim[1] once claim[0] has run past the last
+//    item. A segment first waits (bounded) until svm_done reaches its frame's
+//    item count: the frame's I min/max and maps are then final. Every item it
+//    waits on was claimed before it by a CTA that is running and never
+//    waits, so the wait ends even when the grid is not resident at once.
+// With norm, the projection goes to the frame's Iraw and each segment
+// normalises its tile in shared memory with the frame's min and range (the
+// expression of the normalisation pass) and writes its own pixels of the
+// normalised map I: the normalisation pass and its launch are gone, and a
+// frame's KNN starts while later frames' projection/SVM items still run.
+// Per pixel the arithmetic is that of the three separate launches, so the
+// outputs are bit-identical to them. kframes: the KNN's frame table (the
+// group's frames, indexed like the redo list); frames: the whole table
+// (the items' frame indices).
+template <int KC>
+__global__ void __launch_bounds__(kSvmThreads)
+svm_knn_batch_kernel(const BatchFrame *__restrict__ frames, const PixItem *__restrict__ items,
+                     int n_items, const BatchFrame *__restrict__ kframes, int n_kframes,
+                     int n_seg, int cta_base, int B, const float *__restrict__ w,
+                     const float *__restrict__ bias, const float *__restrict__ pa,
+                     const float *__restrict__ pb, int couple_f64, int K, int R, float lam,
+                     int norm, int2 *__restrict__ redo_list, unsigned redo_cap, unsigned *claim,
+                     int warp_floats)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    constexpr int MA = M > 0 ? M : 1;
+    extern __shared__ float sm[];  // the weights, then the warps' KNN tiles and key buffers
+    __shared__ float sbias[MA], sa[MA], sb[MA];
+    __shared__ int s_item;
+    for (;;) {  // projection/SVM items, a CTA each
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&claim[0], 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;  // uniform
+        const PixItem it = items[item];
+        const BatchFrame &fr = frames[it.frame];
+        stage_weights<KC>(B, fr.v1f, fr.muf, w, bias, pa, pb, sm, sbias, sa, sb);
+        __syncthreads();
+        float lmin = INFINITY, lmax = -INFINITY;
+        bool bad = false;
+        float *Iw = norm ? fr.Iraw : fr.I;
+        if (fr.vec)
+            project_svm_groups<KC, 4, true>(fr.cube, B, fr.N, sm, sbias, sa, sb, true,
+                                            it.g0 + threadIdx.x, it.g1, blockDim.x, Iw, fr.P,
+                                            nullptr, couple_f64, lmin, lmax, bad, 0, fr.P4);
+        else
+            project_svm_groups<KC, 4, false, true>(fr.cube, B, fr.N, sm, sbias, sa, sb, true,
+                                                   threadIdx.x, threadIdx.x + 1, 1, Iw, fr.P,
+                                                   nullptr, couple_f64, lmin, lmax, bad,
+                                                   (long)it.g0 * 4, fr.P4);
+        finish_block(true, lmin, lmax, bad, fr.ctl);
+        __threadfence();  // this thread's maps and min/max before the count
+        __syncthreads();  // (also: every thread has read s_item and the weights)
+        if (threadIdx.x == 0) {
+            __threadfence();  // cumulative over the CTA's writes the barrier ordered
+            atomicAdd(&fr.ctl->svm_done, 1u);
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *wsm = sm + (size_t)warp * (size_t)warp_floats;
+    for (;;) {  // KNN row segments, a warp each
+        int seg = 0;
+        if (lane == 0) seg = (int)atomicAdd(&claim[1], 1u);
+        seg = __shfl_sync(0xffffffffu, seg, 0);
+        if (seg >= n_seg) break;
+        const int cta = cta_base + seg;
+        int lo = 0, hi = n_kframes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (kframes[mid].knn_cta0 <= cta) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchFrame &fr = kframes[lo];
+        const int tpr = (fr.W + 31) / 32;
+        const int t = cta - fr.knn_cta0;
+        const int r = t / tpr, bx = t - r * tpr;
+        int ok = 1;
+        if (lane == 0) ok = wait_count(&fr.ctl->svm_done, (unsigned)fr.svm_items, fr.ctl) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) continue;  // ST_TIMEOUT is set: the call reports it
+        unsigned seen;  // every lane's own acquire of the finished count
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];"
+                     : "=r"(seen)
+                     : "l"(&fr.ctl->svm_done)
+                     : "memory");
+        (void)seen;
+        float nmin = 0.f, nrange = 0.f;
+        if (norm) {
+            nmin = key_to_float(*(volatile const unsigned *)&fr.ctl->imin_key);
+            nrange = key_to_float(*(volatile const unsigned *)&fr.ctl->imax_key) - nmin;
+        }
+        knn_walk<KC, true, true, 32, kBnd, true, true>(
+            norm ? fr.Iraw : fr.I, fr.P, fr.H, fr.W, K, R, lam, fr.O, fr.labels, false, fr.ctl,
+            kframes, lo, redo_list, redo_cap, fr.P4, r, bx, lane, wsm, nullptr, nullptr,
+            norm != 0, nmin, nrange, fr.I);
+        __syncwarp();
+    }
+}
+
+template <int KC>
+cudaError_t launch_batch_svm_knn_kc(const BatchFrame *frames, const PixItem *items, int n_items,
+                                    const BatchFrame *kframes, int n_kframes, int n_seg,
+                                    int cta_base, int B, const hsc_svm_model *m, bool f64, int K,
+                                    int R, float lam, bool norm, int max_rows, int2 *redo_list,
+                                    unsigned redo_cap, unsigned *claim, int sm_count,
+                                    cudaStream_t st)
+{
+    constexpr int M = KC * (KC - 1) / 2;
+    const int wfl = (int)(pruned_smem_bytes<32, kBnd>(R, max_rows) / sizeof(float));
+    const size_t smem = sizeof(float) * std::max((size_t)B * (M + 2), (size_t)(kSvmThreads / 32) * wfl);
+    auto kern = svm_knn_batch_kernel<KC>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSvmThreads, smem) != cudaSuccess)
+        per = 1;
+    long grid = (long)sm_count * (per > 1 ? per : 1);
+    const long work = (long)n_items + (n_seg + kSvmThreads / 32 - 1) / (kSvmThreads / 32);
+    if (grid > work) grid = work;
+    cudaError_t e = cudaMemsetAsync(claim, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, kSvmThreads, smem, st>>>(frames, items, n_items, kframes, n_kframes,
+                                                    n_seg, cta_base, B, m->w, m->b, m->platt_a,
+                                                    m->platt_b, f64 ? 1 : 0, K, R, lam,
+                                                    norm ? 1 : 0, redo_list, redo_cap, claim, wfl);
+    const size_t rsmem = redo_smem_bytes(K);
+    if (rsmem > 48 * 1024)
+        cudaFuncSetAttribute(knn_redo_batch_kernel<KC>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
+    knn_redo_batch_kernel<KC><<<kBatchRedoCtas, kRedoThreads, rsmem, st>>>(kframes, K, R, lam,
+                                                                        redo_list, redo_cap);
+    return cudaGetLastError();
+}
+
 template <int RMAX>
 cudaError_t launch_rmax(const float *I, const float *P, int k, int H, int W, int K, int R,
                         float lam, float *O, int32_t *labels, int32_t *nbr, Control *ctl,
@@ -1253,6 +1483,32 @@ cudaError_t launch_batch_knn(const BatchFrame *frames, int n_frames, int n_ctas,
     case 8: return launch_batch_pruned<8>(frames, n_frames, n_ctas, cta_base, K, R, lambda, max_rows, redo_list, redo_cap, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_batch_svm_knn(const BatchFrame *frames, const PixItem *items, int n_items,
+                                 const BatchFrame *kframes, int n_kframes, int n_seg, int cta_base,
+                                 int B, const hsc_svm_model *m, bool couple_f64, int K, int R,
+                                 float lambda, bool normalize, int max_rows, int2 *redo_list,
+                                 unsigned redo_cap, unsigned *claim, int sm_count, cudaStream_t st)
+{
+    if (n_items < 1 || n_kframes < 1 || n_seg < 1 || !m || !(lambda > 0.f) || !redo_list || !claim)
+        return cudaErrorInvalidValue;
+#define HSC_SVM_KNN_CASE(KC)                                                                       \
+    case KC:                                                                                       \
+        return launch_batch_svm_knn_kc<KC>(frames, items, n_items, kframes, n_kframes, n_seg,      \
+                                           cta_base, B, m, couple_f64, K, R, lambda, normalize,    \
+                                           max_rows, redo_list, redo_cap, claim, sm_count, st);
+    switch (m->n_classes) {
+        HSC_SVM_KNN_CASE(2)
+        HSC_SVM_KNN_CASE(3)
+        HSC_SVM_KNN_CASE(4)
+        HSC_SVM_KNN_CASE(5)
+        HSC_SVM_KNN_CASE(6)
+        HSC_SVM_KNN_CASE(7)
+        HSC_SVM_KNN_CASE(8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef HSC_SVM_KNN_CASE
 }
 
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,

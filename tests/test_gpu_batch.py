@@ -1,7 +1,8 @@
 """hsc_classify_batch: every frame's outputs are bit-identical to what
 hsc_classify gives for that frame alone (uneven snapshot frames, shared
-model), in the stage-major form and the stream-pool form, with and without
-CUDA-graph replay; long work items (two accumulator segments), pixel counts
+model), in the stage-major form (its projection/SVM, normalisation and KNN
+as three launches, or fused in one persistent kernel) and the stream-pool form,
+with and without CUDA-graph replay; long work items (two accumulator segments), pixel counts
 that are not a multiple of 4, a cube that is not 16-byte aligned and an
 out-of-range pixel (the FP32 recompute) included."""
 
@@ -181,26 +182,33 @@ def test_staged_batch_out_of_range_pixel(hsc, ctx):
     _alone_vs_batch(hsc, ctx, frames, cubes)
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("flags", ["raw", "f64"])
-def test_staged_batch_flags(hsc, ctx, flags):
-    """HSC_CLASSIFY_RAW_I and HSC_SVM_COUPLE_F64 in the stage-major batch."""
+def test_staged_batch_flags(hsc, ctx, flags, fused):
+    """HSC_CLASSIFY_RAW_I and HSC_SVM_COUPLE_F64 in the stage-major batch,
+    with the projection/SVM, normalisation and KNN as three launches and
+    fused in one persistent kernel (HSC_BATCH_FUSED)."""
     frames = synth.make_batch(6, seed=778)
     fl = hsc.HSC_CLASSIFY_RAW_I if flags == "raw" else hsc.HSC_SVM_COUPLE_F64
-    _alone_vs_batch(hsc, ctx, frames, frames_to_device(frames), flags=fl)
+    _alone_vs_batch(hsc, ctx, frames, frames_to_device(frames), flags=fl,
+                    batch_flags=hsc.HSC_BATCH_FUSED if fused else 0)
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("graph", [False, True])
-def test_staged_batch_more_frames_than_sms(hsc, ctx, graph):
+def test_staged_batch_more_frames_than_sms(hsc, ctx, graph, fused):
     """More frames than SMs: the first wave's frames and the rest run their
     eigensolver-to-KNN chains on two streams (the second on a high-priority
-    one); every frame still equals its single-frame call."""
+    one), each group's projection/SVM, normalisation and KNN as three
+    launches or (fused) in one persistent kernel with its own work counters;
+    every frame still equals its single-frame call."""
     import torch
     frames = synth.make_batch(170, seed=780)
     assert len(frames) > torch.cuda.get_device_properties(0).multi_processor_count
     cubes = frames_to_device(frames)
-    bflags = hsc.HSC_BATCH_GRAPH if graph else 0
+    bflags = (hsc.HSC_BATCH_GRAPH if graph else 0) | (hsc.HSC_BATCH_FUSED if fused else 0)
     _alone_vs_batch(hsc, ctx, frames, cubes, batch_flags=bflags)
-    if graph:  # the replay
+    if graph:  # the replay (the work counters start from zero again)
         _alone_vs_batch(hsc, ctx, frames, cubes, batch_flags=bflags)
 
 
