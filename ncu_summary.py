@@ -32,11 +32,13 @@ STAGE_OF = (("pilot_", "moments"), ("gram_tc_kernel", "moments"),
             ("project_svm_kernel", "project_svm"), ("project_svm_batch_kernel", "project_svm"),
             ("normalize_kernel", "normalize"), ("normalize_batch_kernel", "normalize"),
             ("knn_pruned_kernel", "knn"), ("knn_redo_kernel", "knn"),
+            ("svm_knn_batch_kernel", "knn"),
             ("knn_redo_batch_kernel", "knn"), ("knn_kernel", "knn_full"))
 SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu"),
              "jacobi": ("k_jacobi.cu", "k_jacobi_cluster.cu", "jacobi_rot.cuh"),
-             "project_svm": ("k_project_svm.cu",), "normalize": ("k_project_svm.cu",),
-             "knn": ("k_knn.cu",), "knn_full": ("k_knn.cu",)}
+             "project_svm": ("k_project_svm.cu", "svm_pixel.cuh"),
+             "normalize": ("k_project_svm.cu", "svm_pixel.cuh"),
+             "knn": ("k_knn.cu", "svm_pixel.cuh"), "knn_full": ("k_knn.cu", "svm_pixel.cuh")}
 
 
 def source_sha(stage: str) -> str:

@@ -6,7 +6,10 @@
 warm-up; an ncu capture of the second launch of a kernel uses ``-s 1 -c 1``.
 --op batch: hsc_classify_batch over the 256 uneven snapshot frames (125
 bands, sides 40-64 px, shared model, K = 16, 7-row window), stage-major
-(8 launches per call), --reps calls after the same number of warm-up calls.
+(15 launches per call: the pilots, the Gram items and the reductions, then
+for each of the two frame groups the eigensolver's two launches and the
+projection/SVM, normalisation, KNN walk and redo pass), --reps calls after the
+same number of warm-up calls.
 """
 
 from __future__ import annotations
