@@ -34,8 +34,8 @@ STAGE_OF = (("pilot_", "moments"), ("gram_tc_kernel", "moments"),
             ("knn_pruned_kernel", "knn"), ("knn_redo_kernel", "knn"),
             ("svm_knn_batch_kernel", "knn"),
             ("knn_redo_batch_kernel", "knn"), ("knn_kernel", "knn_full"))
-SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu"),
-             "jacobi": ("k_jacobi.cu", "k_jacobi_cluster.cu", "jacobi_rot.cuh"),
+SOURCE_OF = {"moments": ("k_moments.cu", "k_gram_tc.cu", "dfloat.cuh"),
+             "jacobi": ("k_jacobi.cu", "k_jacobi_cluster.cu", "jacobi_rot.cuh", "dfloat.cuh"),
              "project_svm": ("k_project_svm.cu", "svm_pixel.cuh"),
              "normalize": ("k_project_svm.cu", "svm_pixel.cuh"),
              "knn": ("k_knn.cu", "svm_pixel.cuh"), "knn_full": ("k_knn.cu", "svm_pixel.cuh")}

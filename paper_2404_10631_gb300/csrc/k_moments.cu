@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "hsc_internal.cuh"
+#include "dfloat.cuh"
 
 namespace hsc {
 namespace {
@@ -200,6 +201,26 @@ __device__ __forceinline__ void df_acc2(float &s, float &lo, float xs, float xlo
     lo = __fadd_rn(lo, xlo);
 }
 
+// The finish of one covariance entry in double-float (FP32 pairs, about
+// 2^-46 relative): with 1/N as the pair inv, delta_b = S_b / N and
+// C_bc = G_bc / N - delta_b delta_c. GB300's FP64 pipe would take nine
+// operations per entry here (conversions included); the reductions of the
+// single frame and of the batch both finish every entry with these same
+// operations, so their pairs are identical.
+__device__ __forceinline__ dfl inv_pair(double inv_N)
+{
+    const float h = __double2float_rn(inv_N);
+    return {h, __double2float_rn(inv_N - (double)h)};
+}
+
+__device__ __forceinline__ dfl band_delta(float s, float l, dfl inv) { return df_mul({s, l}, inv); }
+
+__device__ __forceinline__ dfl cov_entry(float g, float gl, dfl inv, dfl db, dfl dc)
+{
+    const dfl q = df_mul(db, dc);
+    return df_add(df_mul({g, gl}, inv), {-q.h, -q.l});
+}
+
 // grid.x = pixel partitions, grid.y = groups of 256 output tiles (B > 128).
 // Shared: Yt[kGramChunk][Bp + 4] (pixel-major, shifted values).
 __global__ void __launch_bounds__(kGramThreads)
@@ -339,18 +360,17 @@ gram_reduce_kernel(int B, double inv_N, int n_part, const float *__restrict__ gr
             df_acc2(sb, lb, part[1][k][lane].x, part[1][k][lane].y);
             df_acc2(sc, lc, part[2][k][lane].x, part[2][k][lane].y);
         }
-        const double db = ((double)sb + (double)lb) * inv_N;
-        const double dc = ((double)sc + (double)lc) * inv_N;
-        const double v = fma(-db, dc, ((double)g + (double)gl) * inv_N);
-        C[(size_t)b * B + c] = v;
-        C[(size_t)c * B + b] = v;
-        // the same value as an unevaluated FP32 sum hi + lo (for the
-        // eigensolver's double-float products)
-        const float hi = __double2float_rn(v);
-        const float2 pr = make_float2(hi, __double2float_rn(v - (double)hi));
+        const dfl inv = inv_pair(inv_N);
+        const dfl db = band_delta(sb, lb, inv), dc = band_delta(sc, lc, inv);
+        const dfl v = cov_entry(g, gl, inv, db, dc);
+        // C in FP64: the pair's exact sum (the eigensolver reads the pair)
+        const double v64 = (double)v.h + (double)v.l;
+        C[(size_t)b * B + c] = v64;
+        C[(size_t)c * B + b] = v64;
+        const float2 pr = make_float2(v.h, v.l);
         C2[(size_t)b * B + c] = pr;
         C2[(size_t)c * B + b] = pr;
-        if (b == c) mu[b] = (double)shift[b] + db;
+        if (b == c) mu[b] = (double)shift[b] + ((double)db.h + (double)db.l);
     }
 }
 
@@ -389,17 +409,17 @@ __device__ __forceinline__ void slice_sum(const float *__restrict__ base, size_t
 // Stage-major batch form of gram_reduce_kernel: CTA (t, f) takes the t-th
 // 32 x 32 tile (b-block <= c-block) of frame f's matrix, each thread four
 // entries (b, c), b <= c, with gram_reduce_kernel's arithmetic (slice_sum;
-// delta of a band formed once per tile, the same double for every entry).
-// FP64 is the narrow pipe here: each entry costs 9 FP64 operations. C2 (the
-// pairs the eigensolver reads) and mu are written, the tile and its mirror
-// image both coalesced through shared memory; the batch needs no FP64 C.
+// delta of a band formed once per tile, the same pair for every entry, and
+// cov_entry's double-float finish). C2 (the pairs the eigensolver reads) and
+// mu are written, the tile and its mirror image both coalesced through shared
+// memory; the batch needs no FP64 C.
 __global__ void __launch_bounds__(256)
 gram_reduce_batch_kernel(int B, const BatchFrame *__restrict__ frames)
 {
     __shared__ float2 tile[32][33];
-    __shared__ double dlt[64];  // delta of the tile's 32 rows b, then of its 32 columns c
+    __shared__ dfl dlt[64];  // delta of the tile's 32 rows b, then of its 32 columns c
     const BatchFrame *fp = frames + blockIdx.y;
-    const double inv_N = 1.0 / (double)fp->N;
+    const dfl inv = inv_pair(1.0 / (double)fp->N);
     const int n_part = fp->n_part;
     const float *__restrict__ gram_part = fp->gram_part;
     const float *__restrict__ sum_part = fp->sum_part;
@@ -416,12 +436,13 @@ gram_reduce_batch_kernel(int B, const BatchFrame *__restrict__ frames)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x < 64) {
         const int band = threadIdx.x < 32 ? tb * 32 + threadIdx.x : tc * 32 + threadIdx.x - 32;
-        double d = 0.0;
+        dfl d = {0.f, 0.f};
         if (band < B) {
             float sv, lv;
             slice_sum(sum_part + band, (size_t)B, n_part, sv, lv);
-            d = ((double)sv + (double)lv) * inv_N;
-            if (threadIdx.x < 32 && tb == tc) fp->mu[band] = (double)fp->shift[band] + d;
+            d = band_delta(sv, lv, inv);
+            if (threadIdx.x < 32 && tb == tc)
+                fp->mu[band] = (double)fp->shift[band] + ((double)d.h + (double)d.l);
         }
         dlt[threadIdx.x] = d;
     }
@@ -435,9 +456,8 @@ gram_reduce_batch_kernel(int B, const BatchFrame *__restrict__ frames)
         if (b < B && c < B && c >= b) {
             float g, gl;
             slice_sum(gram_part + (long)c * B + b, (size_t)BB, n_part, g, gl);
-            const double v = fma(-dlt[lane], dlt[32 + cl], ((double)g + (double)gl) * inv_N);
-            const float hi = __double2float_rn(v);
-            pr = make_float2(hi, __double2float_rn(v - (double)hi));
+            const dfl v = cov_entry(g, gl, inv, dlt[lane], dlt[32 + cl]);
+            pr = make_float2(v.h, v.l);
             C2[(size_t)c * B + b] = pr;  // row c: lanes on consecutive b
         }
         tile[cl][lane] = pr;

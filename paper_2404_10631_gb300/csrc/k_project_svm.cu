@@ -62,7 +62,7 @@ project_svm_kernel(const float *__restrict__ cube, int B, long N,
 // pixels, 16-byte loads where the frame allows them); labels are not
 // written (the KNN gives them).
 template <int KC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 project_svm_batch_kernel(const BatchFrame *__restrict__ frames, const PixItem *__restrict__ items,
                          int B, const float *__restrict__ w, const float *__restrict__ bias,
                          const float *__restrict__ pa, const float *__restrict__ pb,
