@@ -409,6 +409,16 @@ hsc_status hsc_knn_diagnostics(hsc_ctx *ctx, int64_t *candidates_evaluated,
  * The following hsc_sync returns HSC_ERR_TIMEOUT; that call's outputs are
  * unspecified; the context stays usable. Applies to one call, then clears. */
 hsc_status hsc_test_stall_next_gram(hsc_ctx *ctx);
+/* Testing aid for the fused batch kernel's bounded wait (HSC_BATCH_FUSED; no
+ * counterpart in the paper). In the context's next stage-major
+ * hsc_classify_batch call with HSC_BATCH_FUSED, the first frame's count of
+ * projection/SVM work items in the uploaded frame table is one more than the
+ * items that exist, so the KNN row segments of that frame wait for an item
+ * that never finishes: each wait gives up after its bound (about 1 s of
+ * suspends), sets the timeout status and skips its segment. The following
+ * hsc_sync returns HSC_ERR_TIMEOUT; that call's outputs are unspecified; the
+ * context stays usable. Applies to one such call, then clears. */
+hsc_status hsc_test_stall_next_batch_wait(hsc_ctx *ctx);
 /* ms[HSC_N_STAGES]: summed milliseconds; kernels[HSC_N_STAGES]: kernel
  * launches per stage; dropped (nullable): records lost to the cap. */
 hsc_status hsc_profile_read(hsc_ctx *ctx, double *ms, int64_t *kernels, int64_t *dropped);

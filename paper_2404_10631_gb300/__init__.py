@@ -46,7 +46,7 @@ EXPORTED = ("hsc_ctx_create", "hsc_ctx_destroy", "hsc_set_stream", "hsc_last_err
             "hsc_pca_one_band_noalloc", "hsc_pca_covariance", "hsc_knn_diagnostics",
             "hsc_classify_batch", "hsc_server_create", "hsc_server_submit",
             "hsc_server_wait", "hsc_server_stats_get", "hsc_server_destroy",
-            "hsc_test_stall_next_gram")
+            "hsc_test_stall_next_gram", "hsc_test_stall_next_batch_wait")
 HSC_BATCH_GRAPH = 8
 HSC_BATCH_POOL = 64
 HSC_BATCH_FUSED = 256
@@ -148,6 +148,7 @@ def lib():
         L.hsc_server_destroy.argtypes = [vp]
         L.hsc_server_destroy.restype = None
         L.hsc_test_stall_next_gram.argtypes = [vp]
+        L.hsc_test_stall_next_batch_wait.argtypes = [vp]
         L.hsc_knn_diagnostics.argtypes = [vp, ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64)]
         L.hsc_pca_covariance.argtypes = [vp, vp, i32, i32, i32, ctypes.c_uint, vp, vp]
@@ -286,6 +287,12 @@ class Context:
         """Testing aid: the next tensor-core Gram of this context runs out its
         first bounded wait (see hsc_test_stall_next_gram)."""
         self.check(lib().hsc_test_stall_next_gram(self.handle))
+
+    def test_stall_next_batch_wait(self):
+        """Testing aid: the next fused stage-major batch of this context runs
+        out its KNN segments' bounded waits on its first frame (see
+        hsc_test_stall_next_batch_wait)."""
+        self.check(lib().hsc_test_stall_next_batch_wait(self.handle))
 
     def knn_candidates_evaluated(self) -> int:
         """Candidates the pruned KNN search evaluated since the last call

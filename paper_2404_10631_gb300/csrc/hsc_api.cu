@@ -70,6 +70,9 @@ struct hsc_ctx {
     // testing aid: the next moments stage runs the tensor-core Gram with
     // Control::test_stall set (hsc_test_stall_next_gram)
     bool test_stall = false;
+    // the next fused stage-major batch waits for one projection/SVM item of
+    // its first frame that does not exist (hsc_test_stall_next_batch_wait)
+    bool test_stall_batch = false;
     bool tuned = false;
     int tune_B = 0, tune_k = 0;
     long tune_N = 0;
@@ -638,6 +641,14 @@ hsc_status hsc_test_stall_next_gram(hsc_ctx *ctx)
     hsc_status st = check_ctx(ctx);
     if (st) return st;
     ctx->test_stall = true;
+    return HSC_OK;
+}
+
+hsc_status hsc_test_stall_next_batch_wait(hsc_ctx *ctx)
+{
+    hsc_status st = check_ctx(ctx);
+    if (st) return st;
+    ctx->test_stall_batch = true;
     return HSC_OK;
 }
 
@@ -1253,6 +1264,10 @@ hsc_status classify_batch_staged(hsc_ctx *ctx, const hsc_frame *frames, int n_fr
         }
         hc[g_grid] = k;
         std::copy(sorted.begin(), sorted.end(), hg);
+    }
+    if (ctx->test_stall_batch && (flags & HSC_BATCH_FUSED)) {
+        ++hf[0].svm_items;  // testing aid: frame 0 never reaches its item count
+        ctx->test_stall_batch = false;
     }
     e = cudaMemcpyAsync(dev + tab, host, tab_bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->sm_upload, ctx->stream);

@@ -1252,7 +1252,7 @@ cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ct
 
 // ---- stage-major batch: projection/SVM fused with the KNN filter ----
 
-constexpr unsigned kSvmWaitLimit = 1u << 23;  // suspends of ~256 ns: about 2 s in all
+constexpr unsigned kSvmWaitLimit = 1u << 22;  // suspends of ~256 ns: about 1 s in all
 
 // Waits until *cnt reaches target (acquire at GPU scope), at most
 // kSvmWaitLimit suspends; after that sets ST_TIMEOUT in ctl and returns false.

@@ -125,3 +125,32 @@ def test_gram_wait_timeout_is_reported(hsc, shape):
     np.testing.assert_array_equal(C.cpu().numpy(), C2.cpu().numpy())
     cx.close()
     fresh.close()
+
+
+def test_fused_batch_wait_timeout_is_reported(hsc):
+    """The fused batch kernel's bounded wait (HSC_BATCH_FUSED): with the first
+    frame's projection/SVM item count raised by one in the uploaded table, that
+    frame is never complete, so its KNN row segments give up their waits after
+    the bound and flag the status; hsc_sync returns HSC_ERR_TIMEOUT and the
+    same context's next fused batch equals the frames classified alone."""
+    import torch
+    frames = synth.make_batch(4, seed=790)
+    f0 = frames[0]
+    model = hsc.Model.from_host(f0.model)
+    cubes = [torch.as_tensor(f.cube, device="cuda") for f in frames]
+    labs = [torch.full(f.cube.shape[1:], -1, dtype=torch.int32, device="cuda") for f in frames]
+    cx = hsc.Context(0)
+    cx.test_stall_next_batch_wait()
+    hsc.hsc_classify_batch(cx, cubes, model, f0.K, f0.window_rows, f0.lam,
+                           flags=hsc.HSC_BATCH_FUSED, labels=labs)
+    with pytest.raises(hsc.HscError) as e:
+        cx.sync()
+    assert e.value.status == hsc.HSC_ERR_TIMEOUT
+    hsc.hsc_classify_batch(cx, cubes, model, f0.K, f0.window_rows, f0.lam,
+                           flags=hsc.HSC_BATCH_FUSED, labels=labs)
+    cx.sync()
+    for f, c, lab in zip(frames, cubes, labs):
+        ref = hsc.hsc_classify(cx, c, model, f.K, f.window_rows, f.lam)
+        cx.sync()
+        np.testing.assert_array_equal(lab.cpu().numpy(), ref.cpu().numpy())
+    cx.close()
