@@ -392,8 +392,9 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
     tune = {"config": tune_cfg, "seconds": time.perf_counter() - t0,
             "how": "hsc_autotune on the first cube: Gram TMA staging depth {3, 4} (B <= 128), "
                    "projection/SVM {1, 4} pixels per thread x {2, 4, 8, 16} CTAs per SM, pruned "
-                   "KNN walk {32 px x 8, 32 x 6, 32 x 12, 64 x 8} (pixels per CTA x undecided "
-                   "keys per lane), median of 3 runs each; results do not depend on them"}
+                   "KNN walk {32 px x 8, 32 x 6, 32 x 12, 64 x 8, and 32 x 8 and 64 x 8 with "
+                   "the window tile staged by TMA} (pixels per CTA x undecided keys per lane), "
+                   "median of 3 runs each; results do not depend on them"}
     streams = [stream] + [torch.cuda.Stream(dev) for _ in range(F - 1)]
     ctxs = [ctx] + [hsc.Context(dev.index or 0, stream=s) for s in streams[1:]]
     for c in ctxs[1:]:
@@ -491,6 +492,25 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
     ctx.sync()
     full_ms_launch = full_ms["knn"] / n_full
     heap_ms_launch = heap_ms["knn"] / n_heap
+    # ---- the pruned walk's variants (the autotuner's candidates; 4 and 5
+    # stage the window tile with one TMA box instead of 16-byte asynchronous
+    # copies): the KNN stage of the profiled steps per variant, then the tuned
+    # variant again
+    walk_ms = {}
+    for v in range(6):
+        ctx.set_tuning(B, H, W, k, (tune_cfg["gram_stages"], tune_cfg["svm_px"],
+                                    tune_cfg["svm_blocks_per_sm"], v))
+        v_ms, _ = profiled()
+        walk_ms[v] = v_ms["knn"]
+    ctx.set_tuning(B, H, W, k, (tune_cfg["gram_stages"], tune_cfg["svm_px"],
+                                tune_cfg["svm_blocks_per_sm"], tune_cfg["knn_variant"]))
+    knn_walks = {"ms_per_launch": {("%d: %s" % (v, name)): round(walk_ms[v], 5)
+                                   for v, name in enumerate(("32 px x 8 keys", "32 x 6", "32 x 12",
+                                                             "64 x 8", "32 x 8, TMA tile",
+                                                             "64 x 8, TMA tile"))},
+                 "tuned": tune_cfg["knn_variant"],
+                 "note": "the KNN stage (pruned walk + redo pass) of the profiled steps per walk "
+                         "variant; the outputs are the same bit for bit"}
     e_max, e1_max, ep_max = replicas.max_over_ranks([elapsed, elapsed1, elapsed_p], world, dev)
     value = replicas.whole_job_rate(N * args.steps, world, e_max / 1e3)
     value1 = replicas.whole_job_rate(N * args.steps, world, e1_max / 1e3)
@@ -594,6 +614,7 @@ def frame_stream(hsc, f, dev, args, world, F, fp32_rate, fp32_peak_note, with_e2
                                     "one frame at a time (stage device times)"},
            "roofline": roofline, "stages": stages,
            "knn_full_window": knn_full, "knn_pruned": knn_pruned, "knn_heap": knn_heap,
+           "knn_walk_variants": knn_walks,
            "gpu_launches": int(round(sum(stage_kernels.values()))),
            "autotune": tune,
            "jacobi": {"fp32_sweeps": sweeps, "refine_iters": refine_iters,
@@ -726,6 +747,7 @@ def run_ours(args, f):
             "knn_full_window": head["knn_full_window"],
             "knn_pruned": head["knn_pruned"],
             "knn_heap": head["knn_heap"],
+            "knn_walk_variants": head["knn_walk_variants"],
             "e2e": head["e2e"],
             "gpu_launches": head["gpu_launches"],
             "autotune": head["autotune"],

@@ -365,7 +365,9 @@ hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_it
  * thread x 2, 4, 8 or 16 CTAs per SM) and, given KNN parameters with
  * lambda > 0 and the pruned search, of the pruned walk's pixels per CTA and
  * undecided keys per lane (variants 0: 32 and 8, 1: 32 and 6, 2: 32 and 12,
- * 3: 64 and 8; every pixel's neighbour probabilities are added in one
+ * 3: 64 and 8; 4 and 5: 0 and 3 with each CTA's window tile staged by one
+ * TMA box, where the map allows a tensor map; every pixel's neighbour
+ * probabilities are added in one
  * canonical order whichever pass completes it, so O is the same) on this cube
  * and model (median of 3 runs each, CUDA events on the context's stream,
  * which it synchronises), and keeps the fastest for frames of this shape (B,

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libhsc.so.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -161,6 +162,12 @@ cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s
                            int sm_count, cudaStream_t st, bool force_simt = false,
                            int gram_stages = 0);
 bool gram_tc_supported(const float *cube, int B, long N);  // through a tensor map
+// A 2-D tensor map of a rows x cols float32 array (row-major, no swizzle,
+// out-of-range boxes read as zero) with box_cols x box_rows boxes; false when
+// the array or the box breaks a tensor-map rule (cols * 4 and box_cols * 4
+// multiples of 16 bytes, a 16-byte-aligned base) or the driver lacks the call.
+bool encode_map_2d_f32(CUtensorMap *map, const float *base, long rows, long cols, int box_cols,
+                       int box_rows);
 bool gram_tc_usable(const float *cube, int B, long N);     // tensor map or work items
 int moments_kernel_count(const float *cube, int B, long N, bool force_simt = false);
 cudaError_t launch_gram_tc(const float *cube, int B, long N, const PcaScratch &s,
@@ -253,9 +260,11 @@ cudaError_t knn_init(int device);
 // P4 (nullable): P pixel-interleaved, (k + 3) / 4 float4 per pixel, which
 // the pruned search gathers from (one 16-byte load per 4 classes).
 // variant (pruned search with P4): the walk's pixels per CTA and undecided
-// keys per lane, 0 = 32 and 8, 1 = 32 and 6, 2 = 32 and 12, 3 = 64 and 8;
-// the outputs do not depend on it.
-constexpr int kKnnVariants = 4;
+// keys per lane, 0 = 32 and 8, 1 = 32 and 6, 2 = 32 and 12, 3 = 64 and 8,
+// 4 = 32 and 8 and 5 = 64 and 8 with the window tile staged by one TMA box
+// (where the map allows a tensor map; else as 0 and 3); the outputs do not
+// depend on it.
+constexpr int kKnnVariants = 6;
 cudaError_t launch_knn(const float *I, const float *P, int k, int H, int W, int K, int R,
                        float lambda, float *O, int32_t *labels, int32_t *nbr,
                        Control *ctl, cudaStream_t st, int search,

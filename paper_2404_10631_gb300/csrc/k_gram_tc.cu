@@ -1432,6 +1432,24 @@ EncodeTiledFn encode_fn()
 
 }  // namespace
 
+bool encode_map_2d_f32(CUtensorMap *map, const float *base, long rows, long cols, int box_cols,
+                       int box_rows)
+{
+    if (!map || !base || rows < 1 || cols < 1 || rows >= (1L << 31) || cols >= (1L << 31) ||
+        (cols * (long)sizeof(float)) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0 ||
+        box_cols < 1 || box_cols > 256 || box_rows < 1 || box_rows > 256 ||
+        (box_cols * (int)sizeof(float)) % 16 != 0 || encode_fn() == nullptr)
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims,
+                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool gram_tc_supported(const float *cube, int B, long N)
 {
     // B <= 128: the 3-D map when N % 32 == 0, else the 2-D one (N % 4 == 0);

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstring>
 #include <math.h>
 
 #include <algorithm>
@@ -34,6 +35,7 @@
 
 #include "hsc_internal.cuh"
 #include "svm_pixel.cuh"
+#include "tma_util.cuh"
 
 namespace hsc {
 namespace {
@@ -633,7 +635,9 @@ __device__ __forceinline__ void knn_walk(const float *__restrict__ I, const floa
                                          const float4 *P4, int r, int bx, int lane, float *sm,
                                          float *s_min, float *s_max, bool norm = false,
                                          float nmin = 0.f, float nrange = 0.f,
-                                         float *__restrict__ I_out = nullptr)
+                                         float *__restrict__ I_out = nullptr,
+                                         const CUtensorMap *tmap = nullptr,
+                                         uint64_t *tbar = nullptr)
 {
     static_assert(!kWarp || kWT == 32, "a warp-scope segment is one warp");
     auto sync = [] {
@@ -655,7 +659,10 @@ __device__ __forceinline__ void knn_walk(const float *__restrict__ I, const floa
     const int hi_r = min(H - 1, r + (R + 1) / 2 - 1);
     const int nrows = hi_r - lo_r + 1;
     const int tw = kWT + 2 * kTabDc, tcol0 = c0 - kTabDc;
-    float *tile = sm;  // nrows x tw
+    // nrows x tw (with a tensor map: 128-byte aligned, the launch adds 128 bytes)
+    float *tile = tmap ? reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(sm) + 127) &
+                                                   ~static_cast<uintptr_t>(127))
+                       : sm;
     LaneBuf bnd;
     bnd.stride = kWT;
     bnd.hi = tile + nrows * tw + lane;
@@ -672,7 +679,32 @@ __device__ __forceinline__ void knn_walk(const float *__restrict__ I, const floa
     static_assert((kWT + 2 * kTabDc) % 4 == 0 && kTabDc % 4 == 0, "tile rows of float4");
     const bool vec = tcol0 >= 0 && tcol0 + tw <= W && (W & 3) == 0 &&
                      (reinterpret_cast<uintptr_t>(I) & 15u) == 0;
-    if (vec) {
+    if (tmap) {
+        // one box of the map's tensor map: rows lo_r .. lo_r + box rows - 1,
+        // columns tcol0 .. tcol0 + tw - 1 (tcol0 * 4 bytes is a multiple of
+        // 16: c0 is a multiple of 32 and kTabDc of 4); entries outside the
+        // map read as zero, as the 4-byte copies below zero-fill them
+        static_assert(kTabDc % 4 == 0 && kWT % 4 == 0, "a 16-byte-aligned box start");
+        if (lane == 0) {
+            tma::mbar_init(tbar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        sync();
+        if (lane == 0) {
+            const int box_rows = R < H ? R : H;
+            tma::mbar_arrive_tx(tbar, (uint32_t)(box_rows * tw * (int)sizeof(float)));
+            tma::tma_load_2d(tile, tmap, tcol0, lo_r, tbar);
+        }
+        volatile int gave_up = 0;
+        const bool landed = tma::mbar_wait(tbar, 0, &gave_up);
+        bool all_landed;
+        if constexpr (kWarp) all_landed = __all_sync(0xffffffffu, landed) != 0;
+        else all_landed = __syncthreads_and(landed) != 0;
+        if (!all_landed) {  // the copy did not arrive within the bound: report and stop
+            if (lane == 0) atomicOr(&ctl->status, ST_TIMEOUT);
+            return;
+        }
+    } else if (vec) {
         for (int idx = lane; idx < nrows * kV; idx += kWT) {
             const int ii = idx / kV, v = idx - ii * kV;
             const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ii * tw + 4 * v);
@@ -693,8 +725,10 @@ __device__ __forceinline__ void knn_walk(const float *__restrict__ I, const floa
             }
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    sync();
+    if (!tmap) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        sync();
+    }
     bool bad = false;
     float vmin = INFINITY, vmax = -INFINITY;
     if (vec) {
@@ -901,10 +935,12 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
                   int R, float lam, float *__restrict__ O, int32_t *__restrict__ labels,
                   bool redo_all, Control *ctl, const BatchFrame *__restrict__ frames,
                   int n_frames, int2 *__restrict__ redo_list, unsigned redo_cap,
-                  const float4 *__restrict__ P4, int cta_base = 0)
+                  const float4 *__restrict__ P4, int cta_base,
+                  const __grid_constant__ CUtensorMap tmap, int use_tma)
 {
     extern __shared__ float sm[];
     __shared__ float s_min[kWT / 32], s_max[kWT / 32];
+    __shared__ __align__(8) uint64_t tbar;
     int r = blockIdx.y, bx = blockIdx.x;
     int frame = 0;
     if (kBatch) {  // a stage-major batch: the frame whose CTA range holds this CTA
@@ -932,7 +968,8 @@ knn_pruned_kernel(const float *__restrict__ I, const float *__restrict__ P, int 
     }
     knn_walk<KC, kBatch, kP4, kWT, kBN>(I, P, H, W, K, R, lam, O, labels, redo_all, ctl, frames,
                                         frame, redo_list, redo_cap, P4, r, bx, (int)threadIdx.x, sm,
-                                        s_min, s_max);
+                                        s_min, s_max, false, 0.f, 0.f, nullptr,
+                                        use_tma ? &tmap : nullptr, &tbar);
 }
 
 template <int KC>
@@ -1183,22 +1220,31 @@ long redo_resident_ctas(size_t smem)
     return n > 64 ? n : 64;
 }
 
+// tma: stage each CTA's window tile with one box of a tensor map of I, where
+// I allows one (W a multiple of 4, a 16-byte-aligned map); else 16- and
+// 4-byte asynchronous copies.
 template <int KC, bool kP4, int kWT, int kBN>
 void launch_walk(const float *I, const float *P, int H, int W, int K, int R, float lam, float *O,
-                 int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st, const float4 *P4)
+                 int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st, const float4 *P4,
+                 bool tma = false)
 {
-    const size_t smem = pruned_smem_bytes<kWT, kBN>(R, H);
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    const int rows = R < H ? R : H;
+    const bool use_tma =
+        tma && encode_map_2d_f32(&map, I, H, W, kWT + 2 * kTabDc, rows);
+    const size_t smem = pruned_smem_bytes<kWT, kBN>(R, H) + (use_tma ? 128 : 0);
     auto kern = knn_pruned_kernel<KC, false, kP4, kWT, kBN>;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid((W + kWT - 1) / kWT, H);
     kern<<<grid, kWT, smem, st>>>(I, P, H, W, K, R, lam, O, labels, nbr != nullptr, ctl, nullptr, 0,
-                                  nullptr, 0u, P4, 0);
+                                  nullptr, 0u, P4, 0, map, use_tma ? 1 : 0);
 }
 
 // variant (with the pixel-interleaved probabilities only): 0 = 32 pixels
 // per CTA and 8 undecided keys per lane (the default), 1 = 32 and 6,
-// 2 = 32 and 12, 3 = 64 and 8.
+// 2 = 32 and 12, 3 = 64 and 8, 4 and 5 = 0 and 3 with the tile staged by TMA.
 template <int KC>
 cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, int R, float lam,
                           float *O, int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st,
@@ -1209,6 +1255,8 @@ cudaError_t launch_pruned(const float *I, const float *P, int H, int W, int K, i
         case 1: launch_walk<KC, true, 32, 6>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
         case 2: launch_walk<KC, true, 32, 12>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
         case 3: launch_walk<KC, true, 64, 8>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
+        case 4: launch_walk<KC, true, 32, 8>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4, true); break;
+        case 5: launch_walk<KC, true, 64, 8>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4, true); break;
         default: launch_walk<KC, true, 32, 8>(I, P, H, W, K, R, lam, O, labels, nbr, ctl, st, P4); break;
         }
     } else {
@@ -1238,9 +1286,11 @@ cudaError_t launch_batch_pruned(const BatchFrame *frames, int n_frames, int n_ct
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(knn_pruned_kernel<KC, true, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    CUtensorMap none;
+    memset(&none, 0, sizeof none);
     knn_pruned_kernel<KC, true, true><<<n_ctas, kWalkThreads, smem, st>>>(
         nullptr, nullptr, 0, 0, K, R, lam, nullptr, nullptr, false, nullptr, frames, n_frames,
-        redo_list, redo_cap, nullptr, cta_base);
+        redo_list, redo_cap, nullptr, cta_base, none, 0);
     const size_t rsmem = redo_smem_bytes(K);
     if (rsmem > 48 * 1024)
         cudaFuncSetAttribute(knn_redo_batch_kernel<KC>,

@@ -36,7 +36,7 @@ def test_every_candidate_gives_identical_outputs(hsc, ctx, shape):
     k = f.model.n_classes
     ctx.set_tuning(B, H, W, k, None)
     ref = classify(hsc, ctx, f, cube, m)
-    for stg, px, bps, kv in itertools.product((3, 4), (1, 4), (2, 16), (0, 1, 2, 3)):
+    for stg, px, bps, kv in itertools.product((3, 4), (1, 4), (2, 16), (0, 1, 2, 3, 4, 5)):
         ctx.set_tuning(B, H, W, k, (stg, px, bps, kv))
         out = classify(hsc, ctx, f, cube, m)
         for a, b in zip(ref, out):
@@ -55,14 +55,14 @@ def test_autotune_picks_a_candidate_and_keeps_results(hsc, ctx):
     cfg = ctx.autotune(cube, m, f.K, f.window_rows, f.lam)
     assert cfg["gram_stages"] in (3, 4)
     assert cfg["svm_px"] in (1, 4) and cfg["svm_blocks_per_sm"] in (2, 4, 8, 16)
-    assert cfg["knn_variant"] in (0, 1, 2, 3)
+    assert cfg["knn_variant"] in (0, 1, 2, 3, 4, 5)
     out = classify(hsc, ctx, f, cube, m)
     for a, b in zip(ref, out):
         np.testing.assert_array_equal(a, b)
     with pytest.raises(hsc.HscError):
         ctx.set_tuning(B, H, W, f.model.n_classes, (5, 1, 2))
     with pytest.raises(hsc.HscError):
-        ctx.set_tuning(B, H, W, f.model.n_classes, (3, 1, 2, 4))
+        ctx.set_tuning(B, H, W, f.model.n_classes, (3, 1, 2, 6))
     ctx.set_tuning(B, H, W, f.model.n_classes, None)
 
 
@@ -81,7 +81,7 @@ def test_walk_variants_and_searches_give_identical_outputs(hsc, ctx, lam):
     I = torch.empty((H, W), device="cuda")
     P = torch.empty((k, H, W), device="cuda")
     ref_lab, ref_O = None, None
-    for kv in range(4):
+    for kv in range(6):  # 4 and 5: the window tile staged by TMA
         ctx.set_tuning(B, H, W, k, (0, 0, 0, kv))
         O = torch.empty((k, H, W), device="cuda")
         lab = hsc.hsc_classify(ctx, cube, m, f.K, f.window_rows, lam, out_probs=O, one_band=I,
