@@ -1221,8 +1221,8 @@ long redo_resident_ctas(size_t smem)
 }
 
 // tma: stage each CTA's window tile with one box of a tensor map of I, where
-// I allows one (W a multiple of 4, a 16-byte-aligned map); else 16- and
-// 4-byte asynchronous copies.
+// I allows one (W a multiple of 4 and at least the box width, a
+// 16-byte-aligned map); else 16- and 4-byte asynchronous copies.
 template <int KC, bool kP4, int kWT, int kBN>
 void launch_walk(const float *I, const float *P, int H, int W, int K, int R, float lam, float *O,
                  int32_t *labels, int32_t *nbr, Control *ctl, cudaStream_t st, const float4 *P4,
@@ -1231,8 +1231,9 @@ void launch_walk(const float *I, const float *P, int H, int W, int K, int R, flo
     CUtensorMap map;
     memset(&map, 0, sizeof map);
     const int rows = R < H ? R : H;
+    // (only where the box fits inside the map: narrower maps take the copies)
     const bool use_tma =
-        tma && encode_map_2d_f32(&map, I, H, W, kWT + 2 * kTabDc, rows);
+        tma && W >= kWT + 2 * kTabDc && encode_map_2d_f32(&map, I, H, W, kWT + 2 * kTabDc, rows);
     const size_t smem = pruned_smem_bytes<kWT, kBN>(R, H) + (use_tma ? 128 : 0);
     auto kern = knn_pruned_kernel<KC, false, kP4, kWT, kBN>;
     if (smem > 48 * 1024)
