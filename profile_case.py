@@ -31,6 +31,9 @@ def main(argv=None):
                          "--config")
     ap.add_argument("--search", default="auto", choices=("auto", "full", "pruned", "heap"),
                     help="KNN search of --op knn")
+    ap.add_argument("--knn-variant", type=int, default=None,
+                    help="pruned walk variant of --op classify (hsc_set_tuning; 4 and 5 stage "
+                         "the window tile by TMA); default: the untuned one")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
     import torch
@@ -61,6 +64,9 @@ def main(argv=None):
     ctx = hsc.Context(0)
     cube = torch.as_tensor(f.cube, device="cuda")
     model = hsc.Model.from_host(f.model)
+    if a.knn_variant is not None:
+        B, H, W = f.cube.shape
+        ctx.set_tuning(B, H, W, f.model.n_classes, (0, 0, 0, a.knn_variant))
     I = hsc.hsc_pca_one_band(ctx, cube)
     P = hsc.hsc_svm_probs(ctx, cube, model)
     for _ in range(a.reps):
