@@ -372,7 +372,9 @@ hsc_status hsc_pca_diagnostics(hsc_ctx *ctx, int32_t *sweeps, int32_t *refine_it
  * and model (median of 3 runs each, CUDA events on the context's stream,
  * which it synchronises), and keeps the fastest for frames of this shape (B,
  * H*W, n_classes) in the context: hsc_classify, hsc_classify_batch and
- * hsc_pca_one_band use it for frames of that shape, the defaults for others.
+ * hsc_pca_one_band use it for frames of that shape, the defaults for others
+ * (the walk: variant 4, which takes variant 0's copies where the map does not
+ * allow a tensor map).
  * Retuning replaces it.
  *   params  KNN parameters (nullable: the walk is not tuned)
  *   config  4 int32 (host, nullable): stages, pixels per thread, CTAs per SM,
@@ -381,8 +383,9 @@ hsc_status hsc_autotune(hsc_ctx *ctx, const float *cube, int B, int H, int W,
                         const hsc_svm_model *model, const hsc_knn_params *params,
                         int32_t *config);
 /* Sets the tuned parameters for frames of shape (B, H, W, n_classes) by hand
- * (config as hsc_autotune's; 0 = default for each), or clears them
- * (config NULL). HSC_ERR_INVALID_ARG for values outside the candidates. */
+ * (config as hsc_autotune's; 0 = the default for the first three, the walk
+ * variant as given), or clears them (config NULL). HSC_ERR_INVALID_ARG for
+ * values outside the candidates. */
 hsc_status hsc_set_tuning(hsc_ctx *ctx, int B, int H, int W, int n_classes,
                           const int32_t *config);
 /* Measured issue rate of device's FP32 (fp64 = 0: FFMA) or FP64 (fp64 = 1:

@@ -155,7 +155,7 @@ struct Tuning {
     int gram_stages = 0;
     int svm_px = 0;
     int svm_blocks_per_sm = 0;
-    int knn_variant = 0;  // launch_knn's variant of the pruned walk
+    int knn_variant = 4;  // launch_knn's variant of the pruned walk (4: 32 x 8, TMA tile)
 };
 
 cudaError_t launch_moments(const float *cube, int B, long N, const PcaScratch &s,
